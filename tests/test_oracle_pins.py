@@ -1,0 +1,314 @@
+"""Pins of the FP64 oracle against facts fixed outside it: published known answers, library routines,
+closed forms and invariants of the paper's sampler. None of these retypes the oracle's own formulas."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.stats
+
+import oracle
+from oracle import stats
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ S1: random numbers
+def test_philox_known_answers():
+    """Philox4x32-10 known-answer vectors (Salmon et al., SC'11)."""
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(v, 16) for v in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        out = oracle.philox4x32_10(r[0:4], r[4:6])
+        assert out.tolist() == r[6:10]
+
+
+def test_series_log_and_trig_match_libm():
+    rng = np.random.default_rng(11)
+    words = rng.integers(0, 2 ** 32, 4000, dtype=np.uint64)
+    for w in words:
+        w = int(w)
+        u1 = ((w >> 8) + 1) * 2.0 ** -24
+        assert abs(oracle.ln_u24(w) - math.log(u1)) <= 5e-7 * max(1.0, abs(math.log(u1)))
+        th = 2 * math.pi * ((w >> 8) * 2.0 ** -24)
+        c, s = oracle.cossin_u24(w)
+        assert abs(c - math.cos(th)) < 3e-7 and abs(s - math.sin(th)) < 3e-7
+    # edge words: u1 = 2^-24 and u1 = 1; angle at the quadrant boundaries
+    assert abs(oracle.ln_u24(0) - math.log(2.0 ** -24)) < 1e-5
+    assert oracle.ln_u24(0xFFFFFFFF) == 0.0
+    for q in range(4):
+        c, s = oracle.cossin_u24(q << 30)
+        assert abs(c - math.cos(q * math.pi / 2)) < 1e-7 and abs(s - math.sin(q * math.pi / 2)) < 1e-7
+
+
+def test_normals_are_standard_gaussian():
+    w = np.concatenate([oracle.normals(5, 0, t, p, 997) for t in range(40) for p in range(5)]).astype(np.float64)
+    n = w.size
+    assert abs(w.mean()) < 5 / math.sqrt(n)
+    assert abs(w.var() - 1) < 5 * math.sqrt(2 / n)
+    assert abs(scipy.stats.kurtosis(w, fisher=False) - 3) < 0.1
+    assert scipy.stats.kstest(w, "norm").pvalue > 1e-3
+    # different chains / steps / problems give different streams
+    a = oracle.normals(5, 0, 0, 0, 64)
+    assert not np.array_equal(a, oracle.normals(5, 0, 0, 1, 64))
+    assert not np.array_equal(a, oracle.normals(5, 0, 1, 0, 64))
+    assert not np.array_equal(a, oracle.normals(5, 1, 0, 0, 64))
+    # a prefix of a longer draw is the shorter draw (components are indexed, not sequential)
+    assert np.array_equal(oracle.normals(5, 0, 3, 2, 10), oracle.normals(5, 0, 3, 2, 64)[:10])
+
+
+def test_uniforms():
+    u = np.array([oracle.uniform(9, 0, 1, t, p) for t in range(300) for p in range(20)])
+    assert u.min() > 0 and u.max() <= 1
+    assert scipy.stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+# ------------------------------------------------------------------ quantisation
+def test_bf16_rounding_matches_torch_for_fp32_values():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    v = (rng.standard_normal(5000) * np.exp(rng.uniform(-20, 20, 5000))).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(oracle.round_bf16(v.astype(np.float64)), ref)
+
+
+def test_bf16_rounding_ties_to_even():
+    one = 1.0
+    ulp = 2.0 ** -7       # bf16 spacing in [1, 2)
+    assert oracle.round_bf16(one + ulp / 2) == one                 # tie -> even (1.0)
+    assert oracle.round_bf16(one + 1.5 * ulp) == one + 2 * ulp     # tie -> even
+    assert oracle.round_bf16(one + ulp / 2 + 2.0 ** -40) == one + ulp
+    assert oracle.round_bf16(-3.0) == -3.0
+
+
+# ------------------------------------------------------------------ S11: Cholesky and substitution
+@pytest.mark.parametrize("d", [1, 3, 5, 17, 64])
+def test_cholesky_matches_lapack(d):
+    Cm = workloads.spd_matrix(d, 100 + d, cond=1e4)
+    L = oracle.cholesky(Cm)
+    ref = np.linalg.cholesky(Cm)
+    assert np.allclose(L, ref, rtol=1e-11, atol=1e-13)
+    assert np.linalg.norm(L @ L.T - Cm) / np.linalg.norm(Cm) < 1e-14
+    assert np.all(np.triu(L, 1) == 0)
+
+
+def test_cholesky_rejects_indefinite():
+    Cm = np.diag([1.0, -1.0, 2.0])
+    assert oracle.cholesky(Cm) is None
+    assert oracle.cholesky(np.zeros((4, 4))) is None
+
+
+@pytest.mark.parametrize("d", [1, 5, 33])
+def test_forward_substitution_matches_scipy(d):
+    L = np.linalg.cholesky(workloads.spd_matrix(d, 7 + d, cond=1e3))
+    b = np.random.default_rng(d).standard_normal(d)
+    y = oracle.forward_sub(L, b)
+    assert np.allclose(y, scipy.linalg.solve_triangular(L, b, lower=True), rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------ S5: targets against library densities
+def _spec_target(ts):
+    return oracle.Target(ts.kind, ts.d, ts.d_y, lam=ts.lam, G=ts.G, A=ts.A, y=ts.y, sigma=ts.sigma,
+                         ban_a=ts.ban_a, ban_b=ts.ban_b, ban_c=ts.ban_c)
+
+
+def test_target_diag_and_dense_match_scipy_logpdf():
+    rng = np.random.default_rng(0)
+    for ts in [workloads.diag_gaussian(12), workloads.dense_gaussian(20, 5)]:
+        T = _spec_target(ts)
+        mvn = scipy.stats.multivariate_normal(np.zeros(ts.d), ts.cov)
+        x0 = np.zeros(ts.d)
+        for _ in range(5):
+            x = rng.standard_normal(ts.d) * np.sqrt(np.diag(ts.cov))
+            assert math.isclose(T.logpi(x) - T.logpi(x0), mvn.logpdf(x) - mvn.logpdf(x0), rel_tol=1e-10, abs_tol=1e-10)
+
+
+def test_target_tanh_matches_scipy_logpdf():
+    ts = workloads.tanh_regression(24, 10, 1)
+    T = _spec_target(ts)
+    rng = np.random.default_rng(4)
+
+    def ref(x):
+        prior = scipy.stats.norm.logpdf(x, 0, np.sqrt(ts.lam)).sum()
+        like = scipy.stats.norm.logpdf(ts.y, np.tanh(ts.A @ x), ts.sigma).sum()
+        return prior + like
+
+    x0 = np.zeros(ts.d)
+    for _ in range(5):
+        x = rng.standard_normal(ts.d) * np.sqrt(ts.lam)
+        assert math.isclose(T.logpi(x) - T.logpi(x0), ref(x) - ref(x0), rel_tol=1e-10, abs_tol=1e-9)
+
+
+def test_target_banana_is_a_volume_preserving_transform_of_a_gaussian():
+    ts = workloads.banana(7)
+    T = _spec_target(ts)
+    rng = np.random.default_rng(8)
+
+    def ref(x):
+        u = x[1] + ts.ban_b * x[0] ** 2 - ts.ban_c
+        return (scipy.stats.norm.logpdf(x[0], 0, math.sqrt(ts.ban_a)) + scipy.stats.norm.logpdf(u)
+                + scipy.stats.norm.logpdf(x[2:], 0, np.sqrt(ts.lam[2:])).sum())
+
+    x0 = np.zeros(ts.d)
+    for _ in range(5):
+        x = rng.standard_normal(ts.d) * 2
+        assert math.isclose(T.logpi(x) - T.logpi(x0), ref(x) - ref(x0), rel_tol=1e-10, abs_tol=1e-9)
+    # closed-form moments of the banana used by the multi-problem workload
+    x1 = rng.standard_normal(400000) * 10.0
+    x2 = rng.standard_normal(400000) - 0.1 * x1 ** 2 + 10.0
+    assert abs(x2.mean()) < 0.1 and abs(x2.var() / 201.0 - 1) < 0.03
+    assert math.isclose(ts.cov[1, 1], 201.0, rel_tol=1e-14) and ts.cov[0, 0] == 100.0
+
+
+# ------------------------------------------------------------------ S2-S7: proposal + accept invariants
+def test_reference_gaussian_target_accepts_every_proposal():
+    """Sec. 2.2.2 / 2.2.4: the move of eq. (diam) preserves N(x_ref, A A^T), so with that Gaussian as the
+    target every proposal is accepted - also across factor refreshes (x_ref and A_n both change)."""
+    d, P = 9, 3
+    ts = workloads.diag_gaussian(d)
+    T = oracle.Target(oracle.T_REF, d)
+    cfg = oracle.default_config(d=d, P=P, n_lag=20, beta0=0.4, adapt_beta=1, trace_steps=400,
+                                min_samples_refresh=10, infl=1.3)
+    s = oracle.Sampler(cfg, T, x0=workloads.start_state(d, P, 1))
+    s.run(400)
+    tr = s.trace()
+    assert tr["acc"].all()
+    assert np.abs(tr["loga"]).max() < 1e-9
+    assert s.counts()["refreshes"] >= 5
+    # all accepted => the beta in effect grows by the factor every block until the clamp (Algorithm 1)
+    betas = s.block_betas()
+    expect = [min(0.4 * 1.1 ** k, 0.999) for k in range(len(betas))]
+    assert np.allclose(betas, expect, rtol=1e-12)
+    del ts
+
+
+def test_target_equal_to_fixed_factor_gaussian_accepts_every_proposal():
+    """With A_0 A_0^T equal to the target covariance and no refresh, the chain is pCN on its own invariant
+    Gaussian (eq. (pcn)): log alpha = 0 up to rounding, for every proposal."""
+    for ts in [workloads.diag_gaussian(16), workloads.dense_gaussian(12, 3)]:
+        T = _spec_target(ts)
+        cfg = oracle.default_config(d=ts.d, P=2, n_lag=25, beta0=0.7, adapt_beta=0, trace_steps=200,
+                                    min_samples_refresh=10 ** 12, xref_mode=0)
+        s = oracle.Sampler(cfg, T, C0=ts.cov)
+        s.run(200)
+        tr = s.trace()
+        assert tr["acc"].all() and np.abs(tr["loga"]).max() < 1e-9
+
+
+def test_moments_identity_against_brute_force():
+    """eq. (sampmean), (sampcov): the oracle's C_n equals the plain covariance of every post-step sample."""
+    d, P = 5, 3
+    ts = workloads.diag_gaussian(d, 1.0)
+    s = oracle.Sampler(oracle.default_config(d=d, P=P, n_lag=10, beta0=0.5, min_samples_refresh=8),
+                       _spec_target(ts), x0=workloads.start_state(d, P, 2))
+    s.run(300, record=True)
+    X = s.trajectory().reshape(-1, d)
+    m, Cm = s.moments()
+    assert np.allclose(m, X.mean(0), rtol=1e-12, atol=1e-14)
+    assert np.allclose(Cm, np.cov(X.T, bias=True), rtol=1e-10, atol=1e-13)
+    # the factor in effect after the last refresh is the Cholesky factor of the moments of every sample
+    # up to the end of the previous block (plus the relative jitter of the skip/jitter rule)
+    L, Lq, xr = s.factor()
+    Xb = s.trajectory()[:290].reshape(-1, d)
+    Cb = np.cov(Xb.T, bias=True)
+    Cb += 1e-10 * np.trace(Cb) / d * np.eye(d)
+    assert np.allclose(L, np.linalg.cholesky(Cb), rtol=1e-9, atol=1e-12)
+    assert np.allclose(xr, Xb.mean(0), rtol=1e-12, atol=1e-14)
+    assert np.array_equal(Lq, L)
+
+
+def test_refresh_delay_postpones_the_factor():
+    d, P = 4, 2
+    ts = workloads.diag_gaussian(d, 1.0)
+    mk = lambda D: oracle.Sampler(oracle.default_config(d=d, P=P, n_lag=10, beta0=0.5, min_samples_refresh=5,
+                                                         refresh_delay=D), _spec_target(ts))
+    a, b = mk(0), mk(2)
+    a.run(30, record=True)
+    b.run(50, record=True)
+    # delay 2: the factor built at the end of block 0 is in effect from block 3 (step 30) on
+    Ta, Tb = a.trajectory(), b.trajectory()
+    assert np.array_equal(Ta[:10], Tb[:10])            # block 0 identical (A_0 = Id in both)
+    assert not np.array_equal(Ta[10:20], Tb[10:20])    # a refreshed after block 0, b did not
+    Lb, _, _ = b.factor()
+    Xb = Tb[:10].reshape(-1, d)
+    Cb = np.cov(Xb.T, bias=True)
+    Cb += 1e-10 * np.trace(Cb) / d * np.eye(d)
+    # after 5 blocks, b's factor is the one built at the end of block 1 (in effect from block 4)
+    Xb1 = Tb[:20].reshape(-1, d)
+    Cb1 = np.cov(Xb1.T, bias=True)
+    Cb1 += 1e-10 * np.trace(Cb1) / d * np.eye(d)
+    assert np.allclose(Lb, np.linalg.cholesky(Cb1), rtol=1e-9)
+
+
+def test_bf16_mode_uses_quantised_factor_and_noise():
+    d, P = 6, 2
+    ts = workloads.diag_gaussian(d)
+    T = oracle.Target(oracle.T_REF, d)
+    s = oracle.Sampler(oracle.default_config(d=d, P=P, n_lag=10, beta0=0.4, prec=oracle.BF16, trace_steps=60,
+                                             min_samples_refresh=5), T, x0=workloads.start_state(d, P, 3))
+    s.run(60)
+    L, Lq, xr = s.factor()
+    assert np.array_equal(Lq, oracle.round_bf16(L))
+    assert np.array_equal(xr, xr.astype(np.float32).astype(np.float64))
+    tr = s.trace()
+    # the same quantised factor defines proposal and density: still accepted every time
+    assert tr["acc"].all() and np.abs(tr["loga"]).max() < 1e-9
+    del ts
+
+
+@pytest.mark.slow
+def test_fixed_factor_chain_samples_the_target():
+    """A valid MH chain (fixed factor, fixed beta) on a Gaussian target whose covariance differs from the
+    proposal's: coordinate means and variances within 4 batch-means standard errors of the truth."""
+    d, P, T_ = 8, 4, 40000
+    ts = workloads.diag_gaussian(d, 1.0)
+    C0 = np.diag(ts.lam * np.linspace(0.5, 2.0, d))
+    cfg = oracle.default_config(d=d, P=P, n_lag=100, beta0=0.6, adapt_beta=0, min_samples_refresh=10 ** 12,
+                                xref_mode=0, seed=17)
+    s = oracle.Sampler(cfg, _spec_target(ts), C0=C0)
+    s.run(T_, record=True)
+    X = s.trajectory()[T_ // 4:]
+    chi2 = 0.0
+    for i in range(d):
+        mu, se = stats.mean_and_se(X[:, :, i])
+        assert abs(mu) < 4 * se
+        v, sev = stats.mean_and_se(X[:, :, i] ** 2)
+        assert abs(v - ts.lam[i]) < 4 * sev
+        chi2 += (mu / se) ** 2
+    assert chi2 < scipy.stats.chi2.ppf(0.9999, d)
+
+
+# ------------------------------------------------------------------ diagnostics
+def test_psrf_special_cases():
+    rng = np.random.default_rng(1)
+    P, d, n = 4, 3, 1000
+    var = np.abs(rng.standard_normal((P, d))) + 0.5
+    same = np.tile(rng.standard_normal(d), (P, 1))
+    # identical chain means: B = 0 and R = (n - 1) / n
+    assert np.allclose(stats.psrf(same, var, n), math.sqrt((n - 1) / n))
+    # i.i.d. chains: PSRF close to 1; chains with separated means: far above 1
+    X = rng.standard_normal((P, n, d))
+    r = stats.psrf(X.mean(1), X.var(1), n)
+    assert np.all(np.abs(r - 1) < 0.02)
+    X[0] += 3.0
+    assert np.all(stats.psrf(X.mean(1), X.var(1), n) > 1.2)
+
+
+def test_ess_closed_forms():
+    rng = np.random.default_rng(2)
+    n, P = 200000, 2
+    iid = rng.standard_normal((n, P))
+    assert abs(stats.ess_batch_means(iid, 100) / (n * P) - 1) < 0.35
+    phi = 0.9
+    ar = np.zeros((n, P))
+    e = rng.standard_normal((n, P))
+    for t in range(1, n):
+        ar[t] = phi * ar[t - 1] + e[t]
+    want = n * P * (1 - phi) / (1 + phi)
+    assert abs(stats.ess_batch_means(ar, 100) / want - 1) < 0.35
