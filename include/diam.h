@@ -1,0 +1,184 @@
+/*
+ * diam.h -- C ABI of the B300 (sm_103a) DIAM sampler: dimension-independent adaptive Metropolis over P
+ * concurrent chains (Chen, Law, Ltaief, Keyes: "Accelerated dimension-independent adaptive Metropolis",
+ * arXiv 1506.05741).
+ *
+ * What one call computes, in the paper's terms:
+ *   - the proposal of eq. (diam) / eq. (diamnl):  x* = x_ref + sqrt(1 - beta^2)(x_n - x_ref) + beta*alpha*A_n W_n,
+ *     W_n ~ N(0, Id), for all P chains at once; the n_lag noise products of one interval are one batched
+ *     triangular product (Algorithm 1, "Batch update");
+ *   - the Metropolis-Hastings test of eq. (accept), written as in Algorithm 1:
+ *     log a = log pi(x*) + q(x*) - log pi(x_n) - q(x_n),  q(v) = |A_n^{-1}(v - x_ref)|^2 / (2 alpha^2);
+ *   - every n_lag steps: the beta rule of Algorithm 1, the moments of eq. (sampmean) / eq. (sampcov) pooled
+ *     over all chains (Sec. 2.3.1), and A_n = Cholesky(C_n).
+ *
+ * Conventions (every entry point):
+ *   - Host pointers are owned by the caller and only read/written during the call. Target arrays are
+ *     copied to the device by diam_init; the caller may free them afterwards.
+ *   - The context owns all of its device memory. Calls on one context must not overlap in time (one host
+ *     thread at a time); distinct contexts are independent.
+ *   - Matrices are row-major. Chain states are chain-major: chain p's d-vector is contiguous (P x d).
+ *   - No C++ exception crosses this boundary. Every call returns a diam_status; on failure
+ *     diam_last_error(ctx) holds a one-line reason. DIAM_ENOTSPD is not fatal (the previous factor is
+ *     kept); every other non-zero status leaves the context in DIAM_ESTATE until destroyed.
+ *   - diam_run_batch enqueues its work on the context's stream and synchronises with the host once per
+ *     interval of n_lag steps (to read the acceptance count that drives the beta rule and the refresh
+ *     decision). Device-side errors (a bounded wait that expired) are reported by that synchronisation
+ *     or by the next call that synchronises.
+ */
+#ifndef DIAM_H
+#define DIAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DIAM_ABI_VERSION 1
+
+typedef enum {
+    DIAM_OK = 0,
+    DIAM_EINVAL = 1,     /* bad argument (sizes, null pointers, unsupported combination) */
+    DIAM_ENOMEM = 2,     /* device allocation failed */
+    DIAM_ECUDA = 3,      /* a CUDA runtime / driver call failed */
+    DIAM_ENOTSPD = 4,    /* refresh skipped: C_n + jitter was not positive definite; old factor kept */
+    DIAM_ETIMEOUT = 5,   /* a bounded device-side wait expired; the kernel returned without its result */
+    DIAM_ETARGET = 6,    /* the user log-density callback failed */
+    DIAM_ESTATE = 7      /* the context is in an error state or was not initialised */
+} diam_status;
+
+/* Arithmetic of the chain update. FP64: every step in FP64 (the plain form).
+ * BF16: the factor A_n, the noise W and the target's linear map are rounded once (to nearest even) to
+ * BF16 and those same rounded values define both the proposal and its density; the products run on the
+ * tensor cores with FP32 accumulation, chain states are FP32, and the Cholesky refresh and the moment
+ * accumulation stay in FP64. */
+typedef enum { DIAM_FP64 = 0, DIAM_BF16 = 2 } diam_prec;
+
+/* Synthetic targets (log pi up to a constant, eq. (bayes)).
+ *  DIAG_GAUSS : -sum_i x_i^2 / (2 lam_i)
+ *  DENSE_GAUSS: -|G x|^2 / 2, G is d_y x d
+ *  TANH_REG   : -sum_i x_i^2 / (2 lam_i) - sum_k (y_k - tanh((A x)_k))^2 / (2 sigma^2), A is d_y x d
+ *  BANANA     : -x1^2/(2a) - (x2 + b x1^2 - c)^2 / 2 - sum_{i>=3} x_i^2 / (2 lam_i)
+ *  REF_GAUSS  : the current reference Gaussian N(x_ref, alpha^2 A_n A_n^T), evaluated from x by a
+ *               triangular solve; every proposal is accepted (a test target, Sec. 2.2.2)
+ *  CALLBACK   : user function on device memory (see diam_logpi_fn) */
+typedef enum {
+    DIAM_T_DIAG_GAUSS = 0,
+    DIAM_T_DENSE_GAUSS = 1,
+    DIAM_T_TANH_REG = 2,
+    DIAM_T_BANANA = 3,
+    DIAM_T_REF_GAUSS = 4,
+    DIAM_T_CALLBACK = 5
+} diam_target_kind;
+
+/* User log-density: X is P x d on the device (FP64 when prec = FP64, FP32 when prec = BF16), lp_out is
+ * P doubles on the device, stream is the cudaStream_t the call must use. Return DIAM_OK or
+ * DIAM_ETARGET. The function must not synchronise the device. */
+typedef diam_status (*diam_logpi_fn)(void* user, const void* X, int32_t d, int32_t P, int32_t prec,
+                                     double* lp_out, void* stream);
+
+typedef struct {
+    int32_t kind;           /* diam_target_kind */
+    int32_t d_y;            /* rows of G or A */
+    const double* lam;      /* d (host): lambda_i; unused for DENSE_GAUSS / REF_GAUSS / CALLBACK */
+    const double* G;        /* d_y x d (host), DENSE_GAUSS */
+    const double* A;        /* d_y x d (host), TANH_REG */
+    const double* y;        /* d_y (host), TANH_REG */
+    double sigma;           /* TANH_REG noise std */
+    double ban_a, ban_b, ban_c;
+    diam_logpi_fn fn;       /* CALLBACK */
+    void* user;
+} diam_target;
+
+typedef struct {
+    int32_t d, P;           /* dimension, number of concurrent chains */
+    int32_t n_lag;          /* steps between factor refreshes (Algorithm 1) */
+    int32_t M;              /* intervals per batch between synchronisations (Sec. 2.3.1) */
+    double beta0;           /* initial beta; Algorithm 1 uses min(2.4/sqrt(d), 0.5) */
+    double infl;            /* inflation alpha of eq. (diamnl); 1 = eq. (diam) */
+    int32_t adapt_beta;     /* 1: Algorithm 1's beta rule, pooled over chains */
+    int32_t xref_mode;      /* 0: x_ref = 0 (or xref0); 1: x_ref = running mean, set at each refresh */
+    double acc_lo, acc_hi;  /* acceptance window; Sec. 3.2 uses [0.3, 0.5] for DIAM */
+    double beta_factor;     /* multiplicative beta change (the paper leaves it open; default 1.1) */
+    double beta_min, beta_max;
+    double eps_jitter;      /* refresh factors chol(C_n + eps tr(C_n)/d I), eps x100 per retry (3 retries) */
+    int64_t min_samples_refresh;  /* refresh only after this many accepted moves (< 0: d + 1) */
+    int64_t burnin;         /* n_0: steps kept out of the moments (footnote to Algorithm 1) */
+    int32_t refresh_delay;  /* the factor built at the end of interval k is used from interval k+1+delay */
+    int32_t prec;           /* diam_prec */
+    uint64_t seed;          /* Philox4x32-10 key */
+    uint32_t problem_id;    /* mixed into the key; distinct problems draw distinct streams */
+    int32_t trace_steps;    /* keep a per-step, per-chain trace for the first trace_steps steps (0: off) */
+    int32_t keep_block_sums;/* 1: keep per-interval, per-chain sums of x and log pi (for ESS / PSRF) */
+    int32_t reserved[7];
+} diam_config;
+
+typedef struct {
+    int64_t steps;          /* steps done by every chain */
+    int64_t n;              /* samples in the moments (P per step after burn-in, plus imported ones) */
+    int64_t accepted;       /* accepted moves, all chains */
+    int64_t refreshes;      /* factors built */
+    int64_t notspd;         /* refreshes skipped because C_n was not positive definite */
+    int64_t nonfinite;      /* proposals whose log-density was not finite (always rejected) */
+    double beta;            /* beta in effect */
+} diam_stats;
+
+typedef struct diam_ctx diam_ctx;
+
+/* Fill cfg with the defaults above for dimension d and P chains. */
+diam_status diam_config_default(diam_config* cfg, int32_t d, int32_t P);
+
+/* Create a sampler on the current CUDA device. x0 (P x d, host) may be NULL (all chains start at 0).
+ * C0 (d x d, host) is the covariance whose Cholesky factor is A_0 (NULL: A_0 = Id, Algorithm 1). xref0
+ * (d, host) is the initial x_ref (NULL: 0). stream is a cudaStream_t (NULL: the context creates its own). */
+diam_status diam_init(const diam_config* cfg, const diam_target* target, const double* x0, const double* C0,
+                      const double* xref0, void* stream, diam_ctx** out);
+
+/* Advance every chain n_steps steps (any n_steps >= 0; refreshes happen at multiples of n_lag). */
+diam_status diam_run_batch(diam_ctx* ctx, int64_t n_steps);
+
+/* Synchronisation point of Sec. 2.3.1 (eq. (mom2g), (mom1g)). With the pooled reading used here the
+ * local moments already are the global ones; this call merges moments exported by other samplers (other
+ * processes, other GPUs) into them: ext_mean (d), ext_M2 (d x d, the centred sum
+ * sum_i (x_i - ext_mean)(x_i - ext_mean)^T) and ext_n samples. ext_* may be NULL / 0 (no import).
+ * Synchronises the stream. */
+diam_status diam_sync_moments(diam_ctx* ctx, const double* ext_mean, const double* ext_M2, int64_t ext_n);
+
+/* Pooled moments of eq. (sampmean), (sampcov): mean (d), cov (d x d, may be NULL), n. Synchronises. */
+diam_status diam_get_moments(diam_ctx* ctx, double* mean, double* cov, int64_t* n);
+
+/* The same moments in mergeable form: mean (d), M2 (d x d centred sum), n. Synchronises. */
+diam_status diam_export_moments(diam_ctx* ctx, double* mean, double* M2, int64_t* n);
+
+/* Chain states (P x d) and log pi (P); any output may be NULL. Synchronises. */
+diam_status diam_get_state(diam_ctx* ctx, double* x, double* lp, diam_stats* stats);
+
+/* Factor in effect: L (d x d, FP64 master, lower), Lq (the rounded factor actually used; equals L for
+ * FP64), x_ref (d), beta. Any output may be NULL. Synchronises. */
+diam_status diam_get_factor(diam_ctx* ctx, double* L, double* Lq, double* xref, double* beta);
+
+/* Per-step trace for the first min(steps, trace_steps) steps, each (steps x P): log pi(x*), q(x*), q(x_n),
+ * log a, accepted flag. n_steps is the number of rows the caller's buffers hold. Synchronises. */
+diam_status diam_get_trace(diam_ctx* ctx, double* lp_prop, double* q_prop, double* q_cur, double* loga,
+                           int8_t* acc, int64_t n_steps);
+
+/* Per-interval, per-chain sums (needs keep_block_sums): xsum (n_blocks x P x d), lpsum (n_blocks x P).
+ * *n_blocks is the capacity on input and the count on output. Synchronises. */
+diam_status diam_get_block_sums(diam_ctx* ctx, double* xsum, double* lpsum, int64_t* n_blocks);
+
+/* Checkpoint: the full sampler state (chains, factor, moments, beta, counters, pending factors). Philox
+ * is counter-based, so save + load + run N reproduces run N bit for bit. diam_save with buf = NULL
+ * returns the size in *size. diam_load expects a context created with the same diam_config. */
+diam_status diam_save(diam_ctx* ctx, void* buf, size_t* size);
+diam_status diam_load(diam_ctx* ctx, const void* buf, size_t size);
+
+void diam_destroy(diam_ctx* ctx);
+const char* diam_last_error(const diam_ctx* ctx);
+const char* diam_status_string(diam_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIAM_H */
