@@ -38,6 +38,12 @@ extern "C" {
 
 #define DIAM_ABI_VERSION 1
 
+#if defined(__GNUC__)
+#define DIAM_API __attribute__((visibility("default")))
+#else
+#define DIAM_API
+#endif
+
 typedef enum {
     DIAM_OK = 0,
     DIAM_EINVAL = 1,     /* bad argument (sizes, null pointers, unsupported combination) */
@@ -128,55 +134,55 @@ typedef struct {
 typedef struct diam_ctx diam_ctx;
 
 /* Fill cfg with the defaults above for dimension d and P chains. */
-diam_status diam_config_default(diam_config* cfg, int32_t d, int32_t P);
+DIAM_API diam_status diam_config_default(diam_config* cfg, int32_t d, int32_t P);
 
 /* Create a sampler on the current CUDA device. x0 (P x d, host) may be NULL (all chains start at 0).
  * C0 (d x d, host) is the covariance whose Cholesky factor is A_0 (NULL: A_0 = Id, Algorithm 1). xref0
  * (d, host) is the initial x_ref (NULL: 0). stream is a cudaStream_t (NULL: the context creates its own). */
-diam_status diam_init(const diam_config* cfg, const diam_target* target, const double* x0, const double* C0,
+DIAM_API diam_status diam_init(const diam_config* cfg, const diam_target* target, const double* x0, const double* C0,
                       const double* xref0, void* stream, diam_ctx** out);
 
 /* Advance every chain n_steps steps (any n_steps >= 0; refreshes happen at multiples of n_lag). */
-diam_status diam_run_batch(diam_ctx* ctx, int64_t n_steps);
+DIAM_API diam_status diam_run_batch(diam_ctx* ctx, int64_t n_steps);
 
 /* Synchronisation point of Sec. 2.3.1 (eq. (mom2g), (mom1g)). With the pooled reading used here the
  * local moments already are the global ones; this call merges moments exported by other samplers (other
  * processes, other GPUs) into them: ext_mean (d), ext_M2 (d x d, the centred sum
  * sum_i (x_i - ext_mean)(x_i - ext_mean)^T) and ext_n samples. ext_* may be NULL / 0 (no import).
  * Synchronises the stream. */
-diam_status diam_sync_moments(diam_ctx* ctx, const double* ext_mean, const double* ext_M2, int64_t ext_n);
+DIAM_API diam_status diam_sync_moments(diam_ctx* ctx, const double* ext_mean, const double* ext_M2, int64_t ext_n);
 
 /* Pooled moments of eq. (sampmean), (sampcov): mean (d), cov (d x d, may be NULL), n. Synchronises. */
-diam_status diam_get_moments(diam_ctx* ctx, double* mean, double* cov, int64_t* n);
+DIAM_API diam_status diam_get_moments(diam_ctx* ctx, double* mean, double* cov, int64_t* n);
 
 /* The same moments in mergeable form: mean (d), M2 (d x d centred sum), n. Synchronises. */
-diam_status diam_export_moments(diam_ctx* ctx, double* mean, double* M2, int64_t* n);
+DIAM_API diam_status diam_export_moments(diam_ctx* ctx, double* mean, double* M2, int64_t* n);
 
 /* Chain states (P x d) and log pi (P); any output may be NULL. Synchronises. */
-diam_status diam_get_state(diam_ctx* ctx, double* x, double* lp, diam_stats* stats);
+DIAM_API diam_status diam_get_state(diam_ctx* ctx, double* x, double* lp, diam_stats* stats);
 
 /* Factor in effect: L (d x d, FP64 master, lower), Lq (the rounded factor actually used; equals L for
  * FP64), x_ref (d), beta. Any output may be NULL. Synchronises. */
-diam_status diam_get_factor(diam_ctx* ctx, double* L, double* Lq, double* xref, double* beta);
+DIAM_API diam_status diam_get_factor(diam_ctx* ctx, double* L, double* Lq, double* xref, double* beta);
 
 /* Per-step trace for the first min(steps, trace_steps) steps, each (steps x P): log pi(x*), q(x*), q(x_n),
  * log a, accepted flag. n_steps is the number of rows the caller's buffers hold. Synchronises. */
-diam_status diam_get_trace(diam_ctx* ctx, double* lp_prop, double* q_prop, double* q_cur, double* loga,
+DIAM_API diam_status diam_get_trace(diam_ctx* ctx, double* lp_prop, double* q_prop, double* q_cur, double* loga,
                            int8_t* acc, int64_t n_steps);
 
 /* Per-interval, per-chain sums (needs keep_block_sums): xsum (n_blocks x P x d), lpsum (n_blocks x P).
  * *n_blocks is the capacity on input and the count on output. Synchronises. */
-diam_status diam_get_block_sums(diam_ctx* ctx, double* xsum, double* lpsum, int64_t* n_blocks);
+DIAM_API diam_status diam_get_block_sums(diam_ctx* ctx, double* xsum, double* lpsum, int64_t* n_blocks);
 
 /* Checkpoint: the full sampler state (chains, factor, moments, beta, counters, pending factors). Philox
  * is counter-based, so save + load + run N reproduces run N bit for bit. diam_save with buf = NULL
  * returns the size in *size. diam_load expects a context created with the same diam_config. */
-diam_status diam_save(diam_ctx* ctx, void* buf, size_t* size);
-diam_status diam_load(diam_ctx* ctx, const void* buf, size_t size);
+DIAM_API diam_status diam_save(diam_ctx* ctx, void* buf, size_t* size);
+DIAM_API diam_status diam_load(diam_ctx* ctx, const void* buf, size_t size);
 
-void diam_destroy(diam_ctx* ctx);
-const char* diam_last_error(const diam_ctx* ctx);
-const char* diam_status_string(diam_status s);
+DIAM_API void diam_destroy(diam_ctx* ctx);
+DIAM_API const char* diam_last_error(const diam_ctx* ctx);
+DIAM_API const char* diam_status_string(diam_status s);
 
 #ifdef __cplusplus
 }

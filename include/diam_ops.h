@@ -1,0 +1,45 @@
+/*
+ * diam_ops.h -- op-level entry points of the DIAM library: the building blocks of one sampler step,
+ * callable on caller-owned device buffers (all pointers below are device pointers unless marked host).
+ * They run on the given cudaStream_t (NULL: the default stream) and return a diam_status; none of them
+ * allocates device memory or synchronises the stream except where stated.
+ */
+#ifndef DIAM_OPS_H
+#define DIAM_OPS_H
+
+#include "diam.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The Gaussian draws W of Algorithm 1 for steps t0 .. t0+n_steps-1 and chains 0 .. P-1: row r = s*P + p
+ * of out (row stride ld >= d, entries d .. ld-1 set to 0) holds W for chain p at step t0 + s. Philox4x32-10
+ * (Salmon et al., SC'11) keyed by (seed, problem_id), Box-Muller in IEEE FP32 (bit-reproducible).
+ * kind: 0 = FP32, 1 = FP64 (the FP32 draw widened), 2 = BF16 bits (the FP32 draw rounded to nearest even). */
+DIAM_API diam_status diam_op_normals(uint64_t seed, uint32_t problem_id, int64_t t0, int32_t n_steps, int32_t P, int32_t d,
+                            int32_t ld, int32_t kind, void* out, void* stream);
+
+/* In-place lower Cholesky factor (Algorithm 1, "A_n = Cholesky(C_n)") of the n x n lower triangle of A
+ * (row-major, stride lda, FP64); the strict upper triangle is zeroed. *info_host receives 0, or the
+ * 1-based index of the first non-positive pivot. Synchronises the stream. */
+DIAM_API diam_status diam_op_cholesky_f64(int32_t n, double* A, int32_t lda, int32_t* info_host, void* stream);
+
+/* For nrows right-hand sides stored as rows of B (row r at B + r*ldb, n entries): B_r <- L^{-1} B_r with L
+ * lower triangular (n x n, stride ldl, FP64). This is z = A_n^{-1}(x - x_ref) for every chain. */
+DIAM_API diam_status diam_op_trsm_lower_f64(int32_t n, int32_t nrows, const double* L, int32_t ldl, double* B, int32_t ldb,
+                                   void* stream);
+
+/* D[n*ldd + m] = scale * sum_k A[m*lda + k] (B[n*ldb + k] + B2[n*ldb + k]) on the tensor cores (tcgen05):
+ * A (M x K) and B, B2 (N x K) BF16 bits, K-contiguous, K, lda, ldb multiples of 64, 16-byte aligned
+ * pointers; B2 may be NULL; FP32 accumulation; D FP32. a_lower: A is lower triangular and K blocks past
+ * each 128-row tile are skipped (the batched noise product xi = beta alpha A_n W of Algorithm 1).
+ * Synchronises the stream and reports a device-side timeout as DIAM_ETIMEOUT. */
+DIAM_API diam_status diam_op_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda, const uint16_t* B,
+                              const uint16_t* B2, int32_t ldb, int32_t a_lower, float scale, float* D, int32_t ldd,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIAM_OPS_H */

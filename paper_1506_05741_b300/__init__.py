@@ -1,0 +1,250 @@
+"""B300-native DIAM sampler (dimension-independent adaptive Metropolis, arXiv 1506.05741).
+
+Thin ctypes binding over ``libdiam.so`` (the C ABI declared in ``include/diam.h``). Every step of the
+sampler runs in the library's CUDA kernels; this module only marshals arguments. There is no CPU
+fallback: if the library cannot be built or loaded, importing the binding's entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FP64, BF16 = 0, 2
+T_DIAG, T_DENSE, T_TANH, T_BANANA, T_REF, T_CALLBACK = 0, 1, 2, 3, 4, 5
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+          4: "covariance not positive definite", 5: "device wait timed out", 6: "target callback failed",
+          7: "context in error state"}
+
+_lib = None
+_lock = threading.Lock()
+
+LOGPI_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p)
+
+
+class DiamTarget(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("d_y", C.c_int32), ("lam", C.c_void_p), ("G", C.c_void_p),
+                ("A", C.c_void_p), ("y", C.c_void_p), ("sigma", C.c_double), ("ban_a", C.c_double),
+                ("ban_b", C.c_double), ("ban_c", C.c_double), ("fn", LOGPI_FN), ("user", C.c_void_p)]
+
+
+class DiamConfig(C.Structure):
+    _fields_ = [("d", C.c_int32), ("P", C.c_int32), ("n_lag", C.c_int32), ("M", C.c_int32),
+                ("beta0", C.c_double), ("infl", C.c_double), ("adapt_beta", C.c_int32), ("xref_mode", C.c_int32),
+                ("acc_lo", C.c_double), ("acc_hi", C.c_double), ("beta_factor", C.c_double),
+                ("beta_min", C.c_double), ("beta_max", C.c_double), ("eps_jitter", C.c_double),
+                ("min_samples_refresh", C.c_int64), ("burnin", C.c_int64), ("refresh_delay", C.c_int32),
+                ("prec", C.c_int32), ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("trace_steps", C.c_int32),
+                ("keep_block_sums", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class DiamStats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("n", C.c_int64), ("accepted", C.c_int64), ("refreshes", C.c_int64),
+                ("notspd", C.c_int64), ("nonfinite", C.c_int64), ("beta", C.c_double)]
+
+
+EXPORTS = ["diam_config_default", "diam_init", "diam_run_batch", "diam_sync_moments", "diam_get_moments",
+           "diam_export_moments", "diam_get_state", "diam_get_factor", "diam_get_trace", "diam_get_block_sums",
+           "diam_save", "diam_load", "diam_destroy", "diam_last_error", "diam_status_string"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libdiam.so (building it with nvcc if it is missing or older than its sources)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            l = C.CDLL(path)
+            P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+            sig = {
+                "diam_config_default": (C.c_int, [P, I32, I32]),
+                "diam_init": (C.c_int, [P, P, P, P, P, P, P]),
+                "diam_run_batch": (C.c_int, [P, I64]),
+                "diam_sync_moments": (C.c_int, [P, P, P, I64]),
+                "diam_get_moments": (C.c_int, [P, P, P, P]),
+                "diam_export_moments": (C.c_int, [P, P, P, P]),
+                "diam_get_state": (C.c_int, [P, P, P, P]),
+                "diam_get_factor": (C.c_int, [P, P, P, P, P]),
+                "diam_get_trace": (C.c_int, [P, P, P, P, P, P, I64]),
+                "diam_get_block_sums": (C.c_int, [P, P, P, P]),
+                "diam_save": (C.c_int, [P, P, P]),
+                "diam_load": (C.c_int, [P, P, C.c_size_t]),
+                "diam_destroy": (None, [P]),
+                "diam_last_error": (C.c_char_p, [P]),
+                "diam_status_string": (C.c_char_p, [C.c_int]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(l, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = l
+    return _lib
+
+
+class DiamError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def default_config(d: int, P: int, **kw) -> dict:
+    cs = DiamConfig()
+    rc = lib().diam_config_default(C.byref(cs), d, P)
+    if rc:
+        raise DiamError(rc, "diam_config_default")
+    cfg = {k: getattr(cs, k) for k, _ in DiamConfig._fields_ if k != "reserved"}
+    for k, v in kw.items():
+        if k not in cfg:
+            raise KeyError(k)
+        cfg[k] = v
+    return cfg
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+class Sampler:
+    """P concurrent DIAM chains on one GPU (one context of libdiam.so)."""
+
+    def __init__(self, cfg: dict, target, x0=None, C0=None, xref0=None, stream=None):
+        self._l = lib()
+        self.cfg = dict(cfg)
+        d, P = self.cfg["d"], self.cfg["P"]
+        self.d, self.P = d, P
+        cs = DiamConfig()
+        for k, v in self.cfg.items():
+            setattr(cs, k, v)
+        self._keep = []
+
+        def arr(a, shape=None):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, np.float64)
+            if shape is not None:
+                a = np.ascontiguousarray(np.broadcast_to(a, shape))
+            self._keep.append(a)
+            return a
+
+        ts = DiamTarget()
+        ts.kind = int(target.kind)
+        ts.d_y = int(getattr(target, "d_y", 0) or 0)
+        ts.lam = _p(arr(getattr(target, "lam", None)))
+        ts.G = _p(arr(getattr(target, "G", None)))
+        ts.A = _p(arr(getattr(target, "A", None)))
+        ts.y = _p(arr(getattr(target, "y", None)))
+        ts.sigma = float(getattr(target, "sigma", 0.0) or 0.0)
+        ts.ban_a = float(getattr(target, "ban_a", 100.0))
+        ts.ban_b = float(getattr(target, "ban_b", 0.1))
+        ts.ban_c = float(getattr(target, "ban_c", 10.0))
+        fn = getattr(target, "fn", None)
+        if fn is not None:
+            self._cb = LOGPI_FN(fn)
+            ts.fn = self._cb
+        h = C.c_void_p()
+        x0a = arr(x0, (P, d)) if x0 is not None else None
+        rc = self._l.diam_init(C.byref(cs), C.byref(ts), _p(x0a), _p(arr(C0)), _p(arr(xref0)),
+                               C.c_void_p(_stream_handle(stream)), C.byref(h))
+        if rc:
+            raise DiamError(rc, "diam_init")
+        self._h = h
+        self._keep.clear()
+
+    def _check(self, rc, what):
+        if rc:
+            raise DiamError(rc, f"{what}: {self._l.diam_last_error(self._h).decode()}")
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._l.diam_destroy(h)
+            self._h = None
+
+    __del__ = close
+
+    def run(self, n_steps: int):
+        self._check(self._l.diam_run_batch(self._h, int(n_steps)), "diam_run_batch")
+
+    def moments(self):
+        m = np.zeros(self.d)
+        cov = np.zeros((self.d, self.d))
+        n = C.c_int64()
+        self._check(self._l.diam_get_moments(self._h, _p(m), _p(cov), C.byref(n)), "diam_get_moments")
+        return m, cov, n.value
+
+    def export_moments(self):
+        m = np.zeros(self.d)
+        M2 = np.zeros((self.d, self.d))
+        n = C.c_int64()
+        self._check(self._l.diam_export_moments(self._h, _p(m), _p(M2), C.byref(n)), "diam_export_moments")
+        return m, M2, n.value
+
+    def sync_moments(self, ext_mean=None, ext_M2=None, ext_n=0):
+        em = None if ext_mean is None else np.ascontiguousarray(ext_mean, np.float64)
+        eM = None if ext_M2 is None else np.ascontiguousarray(ext_M2, np.float64)
+        self._check(self._l.diam_sync_moments(self._h, _p(em), _p(eM), int(ext_n)), "diam_sync_moments")
+
+    def state(self):
+        x = np.zeros((self.P, self.d))
+        lp = np.zeros(self.P)
+        st = DiamStats()
+        self._check(self._l.diam_get_state(self._h, _p(x), _p(lp), C.byref(st)), "diam_get_state")
+        return x, lp, {k: getattr(st, k) for k, _ in DiamStats._fields_}
+
+    def stats(self):
+        st = DiamStats()
+        self._check(self._l.diam_get_state(self._h, None, None, C.byref(st)), "diam_get_state")
+        return {k: getattr(st, k) for k, _ in DiamStats._fields_}
+
+    def factor(self):
+        L = np.zeros((self.d, self.d))
+        Lq = np.zeros((self.d, self.d))
+        xr = np.zeros(self.d)
+        b = C.c_double()
+        self._check(self._l.diam_get_factor(self._h, _p(L), _p(Lq), _p(xr), C.byref(b)), "diam_get_factor")
+        return L, Lq, xr, b.value
+
+    def trace(self, n_steps: int):
+        T = int(n_steps)
+        arrs = [np.zeros((T, self.P)) for _ in range(4)]
+        acc = np.zeros((T, self.P), np.int8)
+        self._check(self._l.diam_get_trace(self._h, *[_p(a) for a in arrs], _p(acc), T), "diam_get_trace")
+        return dict(lp_prop=arrs[0], q_prop=arrs[1], q_cur=arrs[2], loga=arrs[3], acc=acc.astype(bool))
+
+    def block_sums(self, n_blocks: int):
+        xs = np.zeros((n_blocks, self.P, self.d))
+        ls = np.zeros((n_blocks, self.P))
+        nb = C.c_int64(n_blocks)
+        self._check(self._l.diam_get_block_sums(self._h, _p(xs), _p(ls), C.byref(nb)), "diam_get_block_sums")
+        return xs[: nb.value], ls[: nb.value]
+
+    def save(self) -> bytes:
+        n = C.c_size_t()
+        self._check(self._l.diam_save(self._h, None, C.byref(n)), "diam_save")
+        buf = (C.c_char * n.value)()
+        self._check(self._l.diam_save(self._h, buf, C.byref(n)), "diam_save")
+        return bytes(buf)
+
+    def load(self, blob: bytes):
+        buf = (C.c_char * len(blob)).from_buffer_copy(blob)
+        self._check(self._l.diam_load(self._h, buf, len(blob)), "diam_load")

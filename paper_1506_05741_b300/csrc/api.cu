@@ -1,0 +1,885 @@
+// api.cu -- the C ABI of include/diam.h: one sampler context, its device buffers and the host-side
+// schedule of Algorithm 1 (arXiv 1506.05741) over P concurrent chains with one pooled factor.
+//
+// Per step (all chains at once): propose (eq. (diamnl), with the z recursion for the proposal density),
+// the target's linear map when it has one (a GEMM with a reducing epilogue), then accept / select /
+// record. Per interval of n_lag steps: fold the recorded samples into the pooled FP64 moments (eq.
+// (sampmean), (sampcov), as a pairwise centred update), apply Algorithm 1's beta rule, and when due
+// factor C_n by FP64 Cholesky; the factor is used from interval k + 1 + refresh_delay on, when the
+// whitened states z are recomputed by a triangular solve. The noise products of an interval are one
+// batched triangular GEMM (Algorithm 1, "Batch update").
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/diam.h"
+#include "gemm_f64.cuh"
+#include "linalg.h"
+#include "step.cuh"
+#include "tc_gemm.h"
+
+using namespace diam;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Pending {
+    double* L = nullptr;
+    double* mean = nullptr;
+    int64_t block = -1;
+};
+
+}  // namespace
+
+struct diam_ctx {
+    diam_config cfg{};
+    int kind = 0, d = 0, P = 0, nl = 0, dy = 0, ldk = 0;
+    bool bf = false;
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    bool bad = false;
+    diam_logpi_fn fn = nullptr;
+    void* user = nullptr;
+    double sigma = 0, ban_a = 0, ban_b = 0, ban_c = 0;
+    Key key{};
+
+    // host mirrors of the schedule
+    int64_t t = 0, n = 0, acc_refresh = 0, acc_all = 0, refreshes = 0, notspd = 0;
+    uint64_t nonfinite = 0;
+    double beta = 0;
+    int64_t xi_block = -1, begun_block = -1;
+    std::vector<Pending> pend;
+
+    std::vector<void*> allocs;
+    Ctl* ctl = nullptr;
+    // chain state (T = double in FP64 mode, float in BF16 mode)
+    void *X = nullptr, *Z = nullptr, *Xp = nullptr, *Zp = nullptr, *xref = nullptr, *cenT = nullptr, *Xi = nullptr;
+    double *lp = nullptr, *q = nullptr, *qp = nullptr, *lpo = nullptr, *lpp = nullptr, *partial = nullptr;
+    double *xref64 = nullptr, *L = nullptr, *Lq64 = nullptr, *mean = nullptr, *M2 = nullptr, *cen64 = nullptr;
+    double *colpart = nullptr, *svec = nullptr, *delta = nullptr, *Cw = nullptr, *work = nullptr;
+    uint16_t *Lq16 = nullptr, *op_hi = nullptr, *op_lo = nullptr, *histT = nullptr;
+    void *W = nullptr, *hist = nullptr;
+    int ldw = 0, ldh = 0, nparts = 0;
+    // target
+    double *inv_lam = nullptr, *Gm = nullptr, *y = nullptr;
+    uint16_t* Gq16 = nullptr;
+    TargetDev tg{};
+    // trace and interval sums
+    TraceDev tr{};
+    double *bsum = nullptr, *lpsum = nullptr;
+    int64_t bcap = 0;
+};
+
+// ------------------------------------------------------------------------------------------------ helpers
+#define CK(expr)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (expr);                                                  \
+        if (e_ != cudaSuccess) return fail(c, DIAM_ECUDA, #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKS(expr)                        \
+    do {                                 \
+        diam_status s_ = (expr);         \
+        if (s_ != DIAM_OK) return s_;    \
+    } while (0)
+
+static diam_status fail(diam_ctx* c, diam_status s, const char* what, const char* why = nullptr) {
+    if (c) {
+        c->err = std::string(what) + (why ? std::string(": ") + why : std::string());
+        if (s != DIAM_ENOTSPD && s != DIAM_EINVAL) c->bad = true;
+    }
+    return s;
+}
+
+template <typename P_>
+static diam_status dalloc(diam_ctx* c, P_** p, size_t bytes) {
+    void* v = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&v, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, DIAM_ENOMEM, "cudaMalloc", "out of device memory");
+    }
+    c->allocs.push_back(v);
+    if (cudaMemsetAsync(v, 0, bytes, c->st) != cudaSuccess) return fail(c, DIAM_ECUDA, "cudaMemset");
+    *p = (P_*)v;
+    return DIAM_OK;
+}
+
+static inline unsigned blocks_for(size_t n, int th = kThreads) { return (unsigned)((n + th - 1) / th); }
+static inline double inv_infl2(const diam_ctx* c) { return 1.0 / (c->cfg.infl * c->cfg.infl); }
+
+static diam_status check_usable(diam_ctx* c) {
+    if (!c) return DIAM_ESTATE;
+    if (c->bad) return DIAM_ESTATE;
+    if (cudaSetDevice(c->dev) != cudaSuccess) return fail(c, DIAM_ECUDA, "cudaSetDevice");
+    return DIAM_OK;
+}
+
+static diam_status sync_and_check(diam_ctx* c) {
+    CK(cudaStreamSynchronize(c->st));
+    int stt = 0;
+    CK(cudaMemcpy(&stt, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (stt == DEV_TIMEOUT) return fail(c, DIAM_ETIMEOUT, "device", "a bounded wait inside a kernel expired");
+    if (stt != 0) return fail(c, DIAM_ECUDA, "device", "kernel reported a bad argument");
+    return DIAM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ pieces
+template <typename T>
+static diam_status linear_target(diam_ctx* c, const T* src) {
+    // the target's linear map over all P chains, reduced to one partial per (m-tile, chain)
+    if (c->kind != TK_DENSE && c->kind != TK_TANH) return DIAM_OK;
+    if (!c->bf) {
+        EpiTargetReduce epi{c->partial, c->y, 1.0 / (2.0 * c->sigma * c->sigma), c->kind == TK_TANH};
+        CK((gemm_f64<true, true>(c->dy, c->P, c->d, c->Gm, c->d, (const double*)src, c->d, TileRange{0, 0}, epi, c->st)));
+    } else {
+        TcEpi epi{};
+        epi.mode = TC_TARGET;
+        epi.partial = c->partial;
+        epi.y = c->y;
+        epi.inv2s2 = 1.0 / (2.0 * c->sigma * c->sigma);
+        epi.tanh_mode = c->kind == TK_TANH;
+        CK(tc_gemm_bf16(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, 0, epi, &c->ctl->status, c->st));
+    }
+    return DIAM_OK;
+}
+
+// log pi of every chain of a state buffer (T), into out (P doubles)
+template <typename T>
+static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
+    const int d = c->d, P = c->P;
+    if (c->kind == TK_REF) {
+        diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, src, (const T*)c->xref, c->work);
+        CK(trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st));
+        set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)nullptr, nullptr, inv_infl2(c), out);
+        return DIAM_OK;
+    }
+    if (c->kind == TK_CALLBACK) {
+        diam_status s = c->fn(c->user, src, d, P, c->cfg.prec, out, (void*)c->st);
+        if (s != DIAM_OK) return fail(c, DIAM_ETARGET, "target callback");
+        return DIAM_OK;
+    }
+    od_terms_kernel<T><<<P, kThreads, 0, c->st>>>(d, src, c->lpo, c->tg, c->bf ? c->op_hi : nullptr,
+                                                  c->bf ? c->op_lo : nullptr, c->ldk);
+    CKS(linear_target<T>(c, src));
+    int np = (c->kind == TK_DENSE || c->kind == TK_TANH) ? c->nparts : 0;
+    sum_lp_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->lpo, c->partial, np, nullptr, out);
+    CK(cudaGetLastError());
+    return DIAM_OK;
+}
+
+// z = Lq^{-1}(x - x_ref) and q for every chain (after a factor change); lp = -q for the reference target.
+template <typename T>
+static diam_status rewhiten(diam_ctx* c) {
+    const int d = c->d, P = c->P;
+    diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, (const T*)c->X, (const T*)c->xref, c->work);
+    CK(trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st));
+    set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)c->Z, c->q, inv_infl2(c),
+                                                c->kind == TK_REF ? c->lp : nullptr);
+    CK(cudaGetLastError());
+    return DIAM_OK;
+}
+
+static void set_xref_from(diam_ctx* c, const double* src_dev) {
+    if (c->bf) {
+        convert_kernel<double, float><<<blocks_for(c->d), kThreads, 0, c->st>>>(c->d, src_dev, (float*)c->xref);
+        convert_kernel<float, double><<<blocks_for(c->d), kThreads, 0, c->st>>>(c->d, (const float*)c->xref, c->xref64);
+    } else {
+        cudaMemcpyAsync(c->xref, src_dev, sizeof(double) * c->d, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(c->xref64, src_dev, sizeof(double) * c->d, cudaMemcpyDeviceToDevice, c->st);
+    }
+}
+
+// Lq from the FP64 master L: the same matrix in FP64 mode, rounded to BF16 (kept as FP64 values and as
+// BF16 bits) in BF16 mode.
+static diam_status quantise(diam_ctx* c) {
+    if (c->bf) {
+        quantise_factor_kernel<<<dim3(blocks_for(c->ldk), c->d), kThreads, 0, c->st>>>(c->d, c->L, c->d, c->Lq64, c->Lq16,
+                                                                                         c->ldk);
+        CK(cudaGetLastError());
+    }
+    return DIAM_OK;
+}
+
+template <typename T>
+static diam_status block_begin(diam_ctx* c, int64_t blk) {
+    for (auto& pd : c->pend) {
+        if (pd.block != blk) continue;
+        CK(cudaMemcpyAsync(c->L, pd.L, sizeof(double) * c->d * c->d, cudaMemcpyDeviceToDevice, c->st));
+        CKS(quantise(c));
+        if (c->cfg.xref_mode == 1) set_xref_from(c, pd.mean);
+        CKS(rewhiten<T>(c));
+        pd.block = -1;
+    }
+    return DIAM_OK;
+}
+
+// W for the n_lag steps of interval blk and their noise products xi = beta alpha Lq W (one GEMM).
+template <typename T>
+static diam_status prepare_block(diam_ctx* c, int64_t blk) {
+    const int d = c->d, P = c->P, nl = c->nl;
+    const int64_t rows = (int64_t)nl * P;
+    dim3 g((unsigned)rows, std::max(1u, std::min(64u, blocks_for(c->ldw / 4, 128))));
+    if (c->bf) {
+        gen_w_kernel<uint16_t><<<g, 128, 0, c->st>>>(c->key, blk * nl, P, d, c->ldw, (uint16_t*)c->W);
+        TcEpi epi{};
+        epi.mode = TC_STORE;
+        epi.D = (float*)c->Xi;
+        epi.ldd = d;
+        epi.scale_dev = &c->ctl->ba;
+        CK(tc_gemm_bf16(d, (int)rows, c->ldk, c->Lq16, c->ldk, (const uint16_t*)c->W, nullptr, c->ldw, 1, epi,
+                        &c->ctl->status, c->st));
+    } else {
+        gen_w_kernel<double><<<g, 128, 0, c->st>>>(c->key, blk * nl, P, d, c->ldw, (double*)c->W);
+        EpiStore epi{(double*)c->Xi, d, 1.0, &c->ctl->ba, 0.0};
+        CK((gemm_f64<true, true>(d, (int)rows, d, c->Lq64, d, (const double*)c->W, c->ldw, TileRange{1, 0}, epi, c->st)));
+    }
+    c->xi_block = blk;
+    return DIAM_OK;
+}
+
+template <typename T>
+static diam_status do_step(diam_ctx* c, int s, int64_t t) {
+    const int d = c->d, P = c->P;
+    const T* Xi = (const T*)c->Xi + (size_t)s * P * d;
+    constexpr bool BF = std::is_same<T, float>::value;
+    if constexpr (BF) {
+        const uint16_t* Ws = (const uint16_t*)c->W + (size_t)s * P * c->ldw;
+        propose_kernel<T, uint16_t><<<P, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
+                                                               (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qp, c->lpo,
+                                                               c->ctl, c->tg, c->op_hi, c->op_lo, c->ldk);
+    } else {
+        const T* Ws = (const T*)c->W + (size_t)s * P * c->ldw;
+        propose_kernel<T, T><<<P, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
+                                                        (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qp, c->lpo, c->ctl,
+                                                        c->tg, nullptr, nullptr, c->ldk);
+    }
+    CK(cudaGetLastError());
+    const double* lpp = c->lpp;
+    if (c->kind == TK_REF || c->kind == TK_CALLBACK) {
+        CKS(eval_lp<T>(c, (const T*)c->Xp, c->lpp));
+    } else {
+        CKS(linear_target<T>(c, (const T*)c->Xp));
+        int np = (c->kind == TK_DENSE || c->kind == TK_TANH) ? c->nparts : 0;
+        sum_lp_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->lpo, c->partial, np, nullptr, c->lpp);
+    }
+    const int64_t blk = t / c->nl;
+    double* bs = nullptr;
+    double* ls = nullptr;
+    if (c->cfg.keep_block_sums) {
+        if (blk >= c->bcap) {
+            int64_t ncap = std::max<int64_t>(2 * c->bcap, blk + 16);
+            double *nb = nullptr, *nlp = nullptr;
+            CKS(dalloc(c, &nb, sizeof(double) * (size_t)ncap * P * d));
+            CKS(dalloc(c, &nlp, sizeof(double) * (size_t)ncap * P));
+            if (c->bcap) {
+                CK(cudaMemcpyAsync(nb, c->bsum, sizeof(double) * (size_t)c->bcap * P * d, cudaMemcpyDeviceToDevice, c->st));
+                CK(cudaMemcpyAsync(nlp, c->lpsum, sizeof(double) * (size_t)c->bcap * P, cudaMemcpyDeviceToDevice, c->st));
+            }
+            c->bsum = nb;
+            c->lpsum = nlp;
+            c->bcap = ncap;
+        }
+        bs = c->bsum + (size_t)blk * P * d;
+        ls = c->lpsum + (size_t)blk * P;
+    }
+    if constexpr (BF) {
+        accept_kernel<T, uint16_t><<<P, kThreads, 0, c->st>>>(
+            d, P, c->key, t, (T*)c->X, (T*)c->Z, (const T*)c->Xp, (const T*)c->Zp, c->lp, c->q, lpp, c->qp, c->ctl,
+            (uint16_t*)c->hist + (size_t)s * P * c->ldh, c->ldh, (const T*)c->cenT, bs, ls, c->tr);
+    } else {
+        accept_kernel<T, double><<<P, kThreads, 0, c->st>>>(
+            d, P, c->key, t, (T*)c->X, (T*)c->Z, (const T*)c->Xp, (const T*)c->Zp, c->lp, c->q, lpp, c->qp, c->ctl,
+            (double*)c->hist + (size_t)s * P * c->ldh, c->ldh, (const T*)c->cenT, bs, ls, c->tr);
+    }
+    CK(cudaGetLastError());
+    return DIAM_OK;
+}
+
+// Fold the samples of interval blk (those past the burn-in) into the pooled moments.
+template <typename T>
+static diam_status fold_block(diam_ctx* c, int64_t blk) {
+    const int d = c->d, P = c->P, nl = c->nl;
+    int64_t tstart = blk * nl;
+    int64_t s0 = std::max<int64_t>(0, std::min<int64_t>(nl, c->cfg.burnin - tstart));
+    int64_t rows = (nl - s0) * P;
+    if (rows <= 0) return DIAM_OK;
+    double nb = (double)rows;
+    int R = (int)std::min<int64_t>(64, rows);
+    constexpr bool BF = std::is_same<T, float>::value;
+    if constexpr (BF) {
+        const uint16_t* H = (const uint16_t*)c->hist + (size_t)s0 * P * c->ldh;
+        colsum_partial_kernel<uint16_t><<<dim3(blocks_for(d), R), kThreads, 0, c->st>>>(H, c->ldh, (int)rows, d, c->colpart);
+    } else {
+        const double* H = (const double*)c->hist + (size_t)s0 * P * c->ldh;
+        colsum_partial_kernel<double><<<dim3(blocks_for(d), R), kThreads, 0, c->st>>>(H, c->ldh, (int)rows, d, c->colpart);
+    }
+    fold_prep_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, R, c->colpart, c->cen64, c->mean, 1.0 / nb, c->svec,
+                                                            c->delta);
+    double w = (double)c->n * nb / ((double)c->n + nb);
+    if constexpr (BF) {
+        // samples as the K index: transpose the interval's records to d x rows (K-contiguous), then the
+        // lower-triangle SYRK on the tensor cores with the FP64 fold in the epilogue
+        int ldt = ((int)rows + 63) / 64 * 64;
+        const uint16_t* H = (const uint16_t*)c->hist + (size_t)s0 * P * c->ldh;
+        CK(transpose_bf16(H, c->ldh, (int)rows, d, c->histT, ldt, c->st));
+        TcEpi epi{};
+        epi.mode = TC_FOLD;
+        epi.M2 = c->M2;
+        epi.ldm = d;
+        epi.s = c->svec;
+        epi.delta = c->delta;
+        epi.inb = 1.0 / nb;
+        epi.w = w;
+        CK(tc_gemm_bf16(d, d, ldt, c->histT, ldt, c->histT, nullptr, ldt, 0, epi, &c->ctl->status, c->st));
+    } else {
+        const double* H = (const double*)c->hist + (size_t)s0 * P * c->ldh;
+        EpiFold epi{c->M2, d, c->svec, c->delta, 1.0 / nb, w};
+        CK((gemm_f64<false, false>(d, d, (int)rows, H, c->ldh, H, c->ldh, TileRange{0, 1}, epi, c->st)));
+    }
+    mean_update_kernel<T><<<blocks_for(d), kThreads, 0, c->st>>>(d, nb / ((double)c->n + nb), c->delta, c->mean,
+                                                                 c->cen64, (T*)c->cenT);
+    CK(cudaGetLastError());
+    c->n += rows;
+    return DIAM_OK;
+}
+
+// Cholesky refresh at the end of interval blk (skip / jitter rule, retries with a larger jitter).
+static diam_status refresh(diam_ctx* c, int64_t blk) {
+    const int d = c->d;
+    trace_kernel<<<1, kThreads, 0, c->st>>>(d, c->M2, d, c->ctl);
+    CKS(sync_and_check(c));
+    double tr = 0;
+    CK(cudaMemcpy(&tr, &c->ctl->trace, sizeof(double), cudaMemcpyDeviceToHost));
+    double inv_n = 1.0 / (double)c->n;
+    double tau = c->cfg.eps_jitter * tr * inv_n / d;
+    bool ok = false;
+    for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
+        build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, inv_n, tau, c->Cw);
+        CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
+        CK(cholesky_f64(c->Cw, d, d, &c->ctl->chol_info, c->st));
+        CKS(sync_and_check(c));
+        int info = 0;
+        CK(cudaMemcpy(&info, &c->ctl->chol_info, sizeof(int), cudaMemcpyDeviceToHost));
+        ok = (info == 0);
+        tau *= 100.0;
+    }
+    if (!ok) {
+        c->notspd++;
+        c->err = "refresh skipped: C_n + jitter not positive definite (previous factor kept)";
+        return DIAM_OK;
+    }
+    Pending& pd = c->pend[(size_t)(blk % (int64_t)c->pend.size())];
+    CK(cudaMemcpyAsync(pd.L, c->Cw, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(pd.mean, c->mean, sizeof(double) * d, cudaMemcpyDeviceToDevice, c->st));
+    pd.block = blk + 1 + c->cfg.refresh_delay;
+    c->refreshes++;
+    return DIAM_OK;
+}
+
+static void push_scalars(diam_ctx* c) {
+    double rho = std::sqrt(1.0 - c->beta * c->beta);
+    set_scalars_kernel<<<1, 1, 0, c->st>>>(c->ctl, c->beta, rho, c->beta * c->cfg.infl, inv_infl2(c));
+}
+
+template <typename T>
+static diam_status block_end(diam_ctx* c, int64_t blk) {
+    CKS(fold_block<T>(c, blk));
+    CKS(sync_and_check(c));
+    unsigned long long acc = 0, nonf = 0;
+    CK(cudaMemcpy(&acc, &c->ctl->acc_block, sizeof(acc), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&nonf, &c->ctl->nonfinite, sizeof(nonf), cudaMemcpyDeviceToHost));
+    c->acc_all += (int64_t)acc;
+    c->nonfinite = nonf;
+    const diam_config& g = c->cfg;
+    if (g.adapt_beta) {  // Algorithm 1: raise beta above the window, lower it below
+        double ahat = (double)acc / ((double)c->P * c->nl);
+        if (ahat > g.acc_hi) c->beta *= g.beta_factor;
+        else if (ahat < g.acc_lo) c->beta /= g.beta_factor;
+        if (c->beta < g.beta_min) c->beta = g.beta_min;
+        if (c->beta > g.beta_max) c->beta = g.beta_max;
+    }
+    if ((blk + 1) * (int64_t)c->nl > g.burnin) c->acc_refresh += (int64_t)acc;
+    if (c->acc_refresh >= g.min_samples_refresh && c->n > 0) CKS(refresh(c, blk));
+    push_scalars(c);
+    CK(cudaGetLastError());
+    return DIAM_OK;
+}
+
+template <typename T>
+static diam_status run_steps(diam_ctx* c, int64_t n_steps) {
+    while (n_steps > 0) {
+        int64_t blk = c->t / c->nl;
+        int s = (int)(c->t % c->nl);
+        if (s == 0 && c->begun_block != blk) {
+            CKS(block_begin<T>(c, blk));
+            c->begun_block = blk;
+        }
+        if (c->xi_block != blk) CKS(prepare_block<T>(c, blk));
+        CKS(do_step<T>(c, s, c->t));
+        c->t++;
+        n_steps--;
+        if (c->t % c->nl == 0) CKS(block_end<T>(c, blk));
+    }
+    return DIAM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ init
+template <typename T>
+static diam_status init_state(diam_ctx* c, const double* x0, const double* C0, const double* xref0) {
+    const int d = c->d, P = c->P;
+    double* tmp = nullptr;
+    CKS(dalloc(c, &tmp, sizeof(double) * (size_t)std::max(P * d, d * d)));
+    if (x0) {
+        CK(cudaMemcpyAsync(tmp, x0, sizeof(double) * (size_t)P * d, cudaMemcpyHostToDevice, c->st));
+        convert_kernel<double, T><<<blocks_for((size_t)P * d), kThreads, 0, c->st>>>((size_t)P * d, tmp, (T*)c->X);
+    }
+    // A_0: Cholesky factor of C0, or the identity (Algorithm 1)
+    if (C0) {
+        CK(cudaMemcpyAsync(c->L, C0, sizeof(double) * d * d, cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
+        CK(cholesky_f64(c->L, d, d, &c->ctl->chol_info, c->st));
+        CKS(sync_and_check(c));
+        int info = 0;
+        CK(cudaMemcpy(&info, &c->ctl->chol_info, sizeof(int), cudaMemcpyDeviceToHost));
+        if (info) return fail(c, DIAM_EINVAL, "diam_init", "C0 is not positive definite");
+    } else {
+        std::vector<double> I((size_t)d * d, 0.0);
+        for (int i = 0; i < d; ++i) I[(size_t)i * d + i] = 1.0;
+        CK(cudaMemcpy(c->L, I.data(), sizeof(double) * d * d, cudaMemcpyHostToDevice));
+    }
+    CKS(quantise(c));
+    if (xref0) {
+        CK(cudaMemcpyAsync(tmp, xref0, sizeof(double) * d, cudaMemcpyHostToDevice, c->st));
+        set_xref_from(c, tmp);
+    }
+    push_scalars(c);
+    CKS(rewhiten<T>(c));
+    if (c->kind != TK_REF) CKS(eval_lp<T>(c, (const T*)c->X, c->lp));
+    CKS(sync_and_check(c));
+    return DIAM_OK;
+}
+
+static diam_status alloc_all(diam_ctx* c) {
+    const int d = c->d, P = c->P, nl = c->nl;
+    const size_t ts = c->bf ? sizeof(float) : sizeof(double);
+    const size_t Pd = (size_t)P * d, rows = (size_t)nl * P;
+    CKS(dalloc(c, &c->ctl, sizeof(Ctl)));
+    CKS(dalloc(c, &c->X, ts * Pd));
+    CKS(dalloc(c, &c->Z, ts * Pd));
+    CKS(dalloc(c, &c->Xp, ts * Pd));
+    CKS(dalloc(c, &c->Zp, ts * Pd));
+    CKS(dalloc(c, &c->xref, ts * d));
+    CKS(dalloc(c, &c->cenT, ts * d));
+    CKS(dalloc(c, &c->Xi, ts * rows * d));
+    for (double** p : {&c->lp, &c->q, &c->qp, &c->lpo, &c->lpp}) CKS(dalloc(c, p, sizeof(double) * P));
+    c->nparts = c->bf ? (c->dy + 127) / 128 : (c->dy + 63) / 64;  // m-tiles of the target product
+    CKS(dalloc(c, &c->partial, sizeof(double) * (size_t)c->nparts * P));
+    for (double** p : {&c->xref64, &c->mean, &c->cen64, &c->svec, &c->delta}) CKS(dalloc(c, p, sizeof(double) * d));
+    CKS(dalloc(c, &c->colpart, sizeof(double) * 64 * d));
+    CKS(dalloc(c, &c->L, sizeof(double) * d * d));
+    CKS(dalloc(c, &c->M2, sizeof(double) * d * d));
+    CKS(dalloc(c, &c->Cw, sizeof(double) * d * d));
+    CKS(dalloc(c, &c->work, sizeof(double) * Pd));
+    c->pend.resize((size_t)c->cfg.refresh_delay + 1);
+    for (auto& pd : c->pend) {
+        CKS(dalloc(c, &pd.L, sizeof(double) * d * d));
+        CKS(dalloc(c, &pd.mean, sizeof(double) * d));
+    }
+    if (c->bf) {
+        CKS(dalloc(c, &c->Lq64, sizeof(double) * d * d));
+        CKS(dalloc(c, &c->Lq16, sizeof(uint16_t) * (size_t)d * c->ldk));
+        CKS(dalloc(c, &c->op_hi, sizeof(uint16_t) * (size_t)P * c->ldk));
+        CKS(dalloc(c, &c->op_lo, sizeof(uint16_t) * (size_t)P * c->ldk));
+        c->ldw = c->ldk;
+        c->ldh = d;
+        CKS(dalloc(c, &c->W, sizeof(uint16_t) * rows * c->ldw));
+        CKS(dalloc(c, &c->hist, sizeof(uint16_t) * rows * c->ldh));
+        CKS(dalloc(c, &c->histT, sizeof(uint16_t) * (size_t)d * ((rows + 63) / 64 * 64)));
+    } else {
+        c->Lq64 = c->L;
+        c->ldw = (d + 3) / 4 * 4;
+        c->ldh = d;
+        CKS(dalloc(c, &c->W, sizeof(double) * rows * c->ldw));
+        CKS(dalloc(c, &c->hist, sizeof(double) * rows * c->ldh));
+    }
+    if (c->cfg.trace_steps > 0) {
+        size_t nt = (size_t)c->cfg.trace_steps * P;
+        CKS(dalloc(c, &c->tr.lp, sizeof(double) * nt));
+        CKS(dalloc(c, &c->tr.q, sizeof(double) * nt));
+        CKS(dalloc(c, &c->tr.qc, sizeof(double) * nt));
+        CKS(dalloc(c, &c->tr.loga, sizeof(double) * nt));
+        CKS(dalloc(c, &c->tr.acc, nt));
+        c->tr.steps = c->cfg.trace_steps;
+    }
+    return DIAM_OK;
+}
+
+static diam_status upload_target(diam_ctx* c, const diam_target* tg) {
+    const int d = c->d, dy = c->dy;
+    c->tg.kind = c->kind;
+    c->tg.d_y = dy;
+    c->tg.ban_a = tg->ban_a;
+    c->tg.ban_b = tg->ban_b;
+    c->tg.ban_c = tg->ban_c;
+    std::vector<double> il((size_t)d, 0.0);
+    if (c->kind == TK_DIAG || c->kind == TK_TANH || c->kind == TK_BANANA) {
+        if (!tg->lam) return fail(c, DIAM_EINVAL, "diam_init", "target needs lam");
+        for (int i = 0; i < d; ++i) {
+            if (c->kind == TK_BANANA && i < 2) continue;
+            if (!(tg->lam[i] > 0)) return fail(c, DIAM_EINVAL, "diam_init", "lam must be positive");
+            il[i] = 1.0 / tg->lam[i];
+        }
+    }
+    CKS(dalloc(c, &c->inv_lam, sizeof(double) * d));
+    CK(cudaMemcpy(c->inv_lam, il.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
+    c->tg.inv_lam = c->inv_lam;
+    if (c->kind == TK_DENSE || c->kind == TK_TANH) {
+        const double* M = c->kind == TK_DENSE ? tg->G : tg->A;
+        if (!M || dy <= 0) return fail(c, DIAM_EINVAL, "diam_init", "target needs its matrix and d_y");
+        if (c->kind == TK_TANH && (!tg->y || !(tg->sigma > 0)))
+            return fail(c, DIAM_EINVAL, "diam_init", "tanh target needs y and sigma > 0");
+        CKS(dalloc(c, &c->Gm, sizeof(double) * (size_t)dy * d));
+        CK(cudaMemcpy(c->Gm, M, sizeof(double) * (size_t)dy * d, cudaMemcpyHostToDevice));
+        if (c->bf) {
+            CKS(dalloc(c, &c->Gq16, sizeof(uint16_t) * (size_t)dy * c->ldk));
+            to_bf16_rows_kernel<<<dim3(blocks_for(c->ldk), dy), kThreads, 0, c->st>>>(dy, d, c->Gm, c->Gq16, c->ldk);
+            CK(cudaGetLastError());
+        }
+        CKS(dalloc(c, &c->y, sizeof(double) * std::max(dy, 1)));
+        if (tg->y) CK(cudaMemcpy(c->y, tg->y, sizeof(double) * dy, cudaMemcpyHostToDevice));
+    }
+    return DIAM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ ABI
+extern "C" {
+
+const char* diam_status_string(diam_status s) {
+    switch (s) {
+        case DIAM_OK: return "ok";
+        case DIAM_EINVAL: return "invalid argument";
+        case DIAM_ENOMEM: return "out of device memory";
+        case DIAM_ECUDA: return "CUDA error";
+        case DIAM_ENOTSPD: return "covariance not positive definite";
+        case DIAM_ETIMEOUT: return "device wait timed out";
+        case DIAM_ETARGET: return "target callback failed";
+        case DIAM_ESTATE: return "context in error state";
+    }
+    return "unknown";
+}
+
+const char* diam_last_error(const diam_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+diam_status diam_config_default(diam_config* cfg, int32_t d, int32_t P) {
+    if (!cfg || d <= 0 || P <= 0) return DIAM_EINVAL;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->d = d;
+    cfg->P = P;
+    cfg->n_lag = 100;
+    cfg->M = 10;
+    cfg->beta0 = std::min(2.4 / std::sqrt((double)d), 0.5);
+    cfg->infl = 1.0;
+    cfg->adapt_beta = 1;
+    cfg->xref_mode = 1;
+    cfg->acc_lo = 0.3;
+    cfg->acc_hi = 0.5;
+    cfg->beta_factor = 1.1;
+    cfg->beta_min = 1e-4;
+    cfg->beta_max = 0.999;
+    cfg->eps_jitter = 1e-10;
+    cfg->min_samples_refresh = -1;
+    cfg->burnin = 0;
+    cfg->refresh_delay = 0;
+    cfg->prec = DIAM_FP64;
+    return DIAM_OK;
+}
+
+diam_status diam_init(const diam_config* cfg, const diam_target* tg, const double* x0, const double* C0,
+                      const double* xref0, void* stream, diam_ctx** out) {
+    if (!cfg || !tg || !out) return DIAM_EINVAL;
+    *out = nullptr;
+    if (cfg->d <= 0 || cfg->P <= 0 || cfg->n_lag <= 0 || !(cfg->infl > 0) || !(cfg->beta0 > 0 && cfg->beta0 < 1) ||
+        cfg->refresh_delay < 0 || cfg->refresh_delay > 8 || (cfg->prec != DIAM_FP64 && cfg->prec != DIAM_BF16) ||
+        tg->kind < 0 || tg->kind > DIAM_T_CALLBACK || (tg->kind == DIAM_T_CALLBACK && !tg->fn) ||
+        (int64_t)cfg->n_lag * cfg->P > (1 << 24) || cfg->trace_steps < 0)
+        return DIAM_EINVAL;
+    diam_ctx* c = new diam_ctx();
+    c->cfg = *cfg;
+    if (c->cfg.min_samples_refresh < 0) c->cfg.min_samples_refresh = cfg->d + 1;
+    c->kind = tg->kind;
+    c->d = cfg->d;
+    c->P = cfg->P;
+    c->nl = cfg->n_lag;
+    c->dy = (tg->kind == DIAM_T_DENSE_GAUSS || tg->kind == DIAM_T_TANH_REG) ? tg->d_y : 0;
+    c->ldk = (cfg->d + 63) / 64 * 64;
+    c->bf = cfg->prec == DIAM_BF16;
+    c->fn = tg->fn;
+    c->user = tg->user;
+    c->sigma = tg->sigma;
+    c->beta = cfg->beta0;
+    c->key = make_key(cfg->seed, cfg->problem_id);
+    cudaGetDevice(&c->dev);
+    if (stream) {
+        c->st = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return DIAM_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    diam_status s = alloc_all(c);
+    if (s == DIAM_OK) s = upload_target(c, tg);
+    if (s == DIAM_OK) s = c->bf ? init_state<float>(c, x0, C0, xref0) : init_state<double>(c, x0, C0, xref0);
+    if (s != DIAM_OK) {
+        diam_destroy(c);
+        return s;
+    }
+    *out = c;
+    return DIAM_OK;
+}
+
+diam_status diam_run_batch(diam_ctx* c, int64_t n_steps) {
+    CKS(check_usable(c));
+    if (n_steps < 0) return fail(c, DIAM_EINVAL, "diam_run_batch", "n_steps < 0");
+    return c->bf ? run_steps<float>(c, n_steps) : run_steps<double>(c, n_steps);
+}
+
+__global__ void merge_moments_kernel(int d, double* M2, const double* extM2, const double* delta, double w) {
+    int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i; j += gridDim.x * blockDim.x)
+        M2[(size_t)i * d + j] += extM2[(size_t)i * d + j] + delta[i] * delta[j] * w;
+}
+
+__global__ void merge_mean_kernel(int d, double* mean, const double* extm, double* delta, double frac) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    double dl = extm[i] - mean[i];
+    delta[i] = dl;
+    mean[i] += dl * frac;
+}
+
+diam_status diam_sync_moments(diam_ctx* c, const double* ext_mean, const double* ext_M2, int64_t ext_n) {
+    CKS(check_usable(c));
+    if (ext_n < 0 || (ext_n > 0 && (!ext_mean || !ext_M2))) return fail(c, DIAM_EINVAL, "diam_sync_moments");
+    if (ext_n > 0) {
+        const int d = c->d;
+        double* em = c->svec;  // interval scratch is free between intervals only: use the refresh buffers
+        CKS(sync_and_check(c));
+        CK(cudaMemcpy(c->Cw, ext_M2, sizeof(double) * d * d, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->work, ext_mean, sizeof(double) * d, cudaMemcpyHostToDevice));
+        double nn = (double)c->n, ne = (double)ext_n;
+        merge_mean_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, c->mean, c->work, em, ne / (nn + ne));
+        merge_moments_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, c->Cw, em, nn * ne / (nn + ne));
+        CK(cudaGetLastError());
+        c->n += ext_n;
+    }
+    return sync_and_check(c);
+}
+
+static diam_status read_moments(diam_ctx* c, double* mean, double* M, int64_t* n, bool as_cov) {
+    CKS(check_usable(c));
+    CKS(sync_and_check(c));
+    const int d = c->d;
+    if (mean) CK(cudaMemcpy(mean, c->mean, sizeof(double) * d, cudaMemcpyDeviceToHost));
+    if (M) {
+        CK(cudaMemcpy(M, c->M2, sizeof(double) * d * d, cudaMemcpyDeviceToHost));
+        double s = (as_cov && c->n > 0) ? 1.0 / (double)c->n : 1.0;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double v = M[(size_t)i * d + j] * s;
+                M[(size_t)i * d + j] = v;
+                M[(size_t)j * d + i] = v;
+            }
+    }
+    if (n) *n = c->n;
+    return DIAM_OK;
+}
+
+diam_status diam_get_moments(diam_ctx* c, double* mean, double* cov, int64_t* n) {
+    return read_moments(c, mean, cov, n, true);
+}
+
+diam_status diam_export_moments(diam_ctx* c, double* mean, double* M2, int64_t* n) {
+    return read_moments(c, mean, M2, n, false);
+}
+
+diam_status diam_get_state(diam_ctx* c, double* x, double* lp, diam_stats* stats) {
+    CKS(check_usable(c));
+    CKS(sync_and_check(c));
+    const size_t Pd = (size_t)c->P * c->d;
+    if (x) {
+        if (c->bf) {
+            convert_kernel<float, double><<<blocks_for(Pd), kThreads, 0, c->st>>>(Pd, (const float*)c->X, c->work);
+            CK(cudaStreamSynchronize(c->st));
+            CK(cudaMemcpy(x, c->work, sizeof(double) * Pd, cudaMemcpyDeviceToHost));
+        } else {
+            CK(cudaMemcpy(x, c->X, sizeof(double) * Pd, cudaMemcpyDeviceToHost));
+        }
+    }
+    if (lp) CK(cudaMemcpy(lp, c->lp, sizeof(double) * c->P, cudaMemcpyDeviceToHost));
+    if (stats) {
+        unsigned long long acc = 0, nonf = 0;
+        CK(cudaMemcpy(&acc, &c->ctl->acc_block, sizeof(acc), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&nonf, &c->ctl->nonfinite, sizeof(nonf), cudaMemcpyDeviceToHost));
+        stats->steps = c->t;
+        stats->n = c->n;
+        stats->accepted = c->acc_all + (c->t % c->nl ? (int64_t)acc : 0);
+        stats->refreshes = c->refreshes;
+        stats->notspd = c->notspd;
+        stats->nonfinite = (int64_t)nonf;
+        stats->beta = c->beta;
+    }
+    return DIAM_OK;
+}
+
+diam_status diam_get_factor(diam_ctx* c, double* L, double* Lq, double* xref, double* beta) {
+    CKS(check_usable(c));
+    CKS(sync_and_check(c));
+    const int d = c->d;
+    if (L) CK(cudaMemcpy(L, c->L, sizeof(double) * d * d, cudaMemcpyDeviceToHost));
+    if (Lq) CK(cudaMemcpy(Lq, c->Lq64, sizeof(double) * d * d, cudaMemcpyDeviceToHost));
+    if (xref) CK(cudaMemcpy(xref, c->xref64, sizeof(double) * d, cudaMemcpyDeviceToHost));
+    if (beta) *beta = c->beta;
+    return DIAM_OK;
+}
+
+diam_status diam_get_trace(diam_ctx* c, double* lp_prop, double* q_prop, double* q_cur, double* loga, int8_t* acc,
+                           int64_t n_steps) {
+    CKS(check_usable(c));
+    CKS(sync_and_check(c));
+    int64_t T = std::min<int64_t>(std::min<int64_t>(c->t, c->tr.steps), n_steps);
+    size_t nt = (size_t)std::max<int64_t>(T, 0) * c->P;
+    if (nt == 0) return DIAM_OK;
+    if (lp_prop) CK(cudaMemcpy(lp_prop, c->tr.lp, nt * 8, cudaMemcpyDeviceToHost));
+    if (q_prop) CK(cudaMemcpy(q_prop, c->tr.q, nt * 8, cudaMemcpyDeviceToHost));
+    if (q_cur) CK(cudaMemcpy(q_cur, c->tr.qc, nt * 8, cudaMemcpyDeviceToHost));
+    if (loga) CK(cudaMemcpy(loga, c->tr.loga, nt * 8, cudaMemcpyDeviceToHost));
+    if (acc) CK(cudaMemcpy(acc, c->tr.acc, nt, cudaMemcpyDeviceToHost));
+    return DIAM_OK;
+}
+
+diam_status diam_get_block_sums(diam_ctx* c, double* xsum, double* lpsum, int64_t* n_blocks) {
+    CKS(check_usable(c));
+    if (!n_blocks) return fail(c, DIAM_EINVAL, "diam_get_block_sums");
+    CKS(sync_and_check(c));
+    int64_t nb = std::min<int64_t>(*n_blocks, std::min<int64_t>(c->bcap, (c->t + c->nl - 1) / c->nl));
+    if (!c->cfg.keep_block_sums) nb = 0;
+    if (nb > 0) {
+        if (xsum) CK(cudaMemcpy(xsum, c->bsum, sizeof(double) * (size_t)nb * c->P * c->d, cudaMemcpyDeviceToHost));
+        if (lpsum) CK(cudaMemcpy(lpsum, c->lpsum, sizeof(double) * (size_t)nb * c->P, cudaMemcpyDeviceToHost));
+    }
+    *n_blocks = nb;
+    return DIAM_OK;
+}
+
+// ---- checkpoint: a flat list of (device buffer, bytes) plus the host schedule
+struct HostState {
+    int64_t t, n, acc_refresh, acc_all, refreshes, notspd, xi_block, begun_block;
+    double beta;
+    int64_t pend_block[9];
+    int64_t bcap;
+};
+
+static std::vector<std::pair<void*, size_t>> state_buffers(diam_ctx* c) {
+    const size_t ts = c->bf ? 4 : 8, Pd = (size_t)c->P * c->d, d = (size_t)c->d;
+    std::vector<std::pair<void*, size_t>> v = {
+        {c->ctl, sizeof(Ctl)}, {c->X, ts * Pd},        {c->Z, ts * Pd},        {c->lp, 8 * (size_t)c->P},
+        {c->q, 8 * (size_t)c->P}, {c->xref, ts * d},   {c->xref64, 8 * d},     {c->cenT, ts * d},
+        {c->cen64, 8 * d},     {c->L, 8 * d * d},      {c->mean, 8 * d},       {c->M2, 8 * d * d}};
+    for (auto& pd : c->pend) {
+        v.push_back({pd.L, 8 * d * d});
+        v.push_back({pd.mean, 8 * d});
+    }
+    if (c->tr.steps) {
+        size_t nt = (size_t)c->tr.steps * c->P;
+        v.push_back({c->tr.lp, nt * 8});
+        v.push_back({c->tr.q, nt * 8});
+        v.push_back({c->tr.qc, nt * 8});
+        v.push_back({c->tr.loga, nt * 8});
+        v.push_back({c->tr.acc, nt});
+    }
+    if (c->bcap) {
+        v.push_back({c->bsum, 8 * (size_t)c->bcap * Pd});
+        v.push_back({c->lpsum, 8 * (size_t)c->bcap * c->P});
+    }
+    return v;
+}
+
+diam_status diam_save(diam_ctx* c, void* buf, size_t* size) {
+    CKS(check_usable(c));
+    if (!size) return fail(c, DIAM_EINVAL, "diam_save");
+    CKS(sync_and_check(c));
+    auto bufs = state_buffers(c);
+    size_t total = sizeof(HostState);
+    for (auto& b : bufs) total += b.second;
+    if (!buf) {
+        *size = total;
+        return DIAM_OK;
+    }
+    if (*size < total) return fail(c, DIAM_EINVAL, "diam_save", "buffer too small");
+    HostState hs{};
+    hs.t = c->t; hs.n = c->n; hs.acc_refresh = c->acc_refresh; hs.acc_all = c->acc_all;
+    hs.refreshes = c->refreshes; hs.notspd = c->notspd; hs.xi_block = -1; hs.begun_block = c->begun_block;
+    hs.beta = c->beta; hs.bcap = c->bcap;
+    for (size_t i = 0; i < c->pend.size(); ++i) hs.pend_block[i] = c->pend[i].block;
+    char* o = (char*)buf;
+    memcpy(o, &hs, sizeof(hs));
+    o += sizeof(hs);
+    for (auto& b : bufs) {
+        CK(cudaMemcpy(o, b.first, b.second, cudaMemcpyDeviceToHost));
+        o += b.second;
+    }
+    *size = total;
+    return DIAM_OK;
+}
+
+diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
+    CKS(check_usable(c));
+    if (!buf || size < sizeof(HostState)) return fail(c, DIAM_EINVAL, "diam_load");
+    HostState hs;
+    memcpy(&hs, buf, sizeof(hs));
+    CKS(sync_and_check(c));
+    if (hs.bcap > c->bcap) {  // grow the interval-sum store to the saved capacity
+        double *nb = nullptr, *nlp = nullptr;
+        CKS(dalloc(c, &nb, sizeof(double) * (size_t)hs.bcap * c->P * c->d));
+        CKS(dalloc(c, &nlp, sizeof(double) * (size_t)hs.bcap * c->P));
+        c->bsum = nb;
+        c->lpsum = nlp;
+        c->bcap = hs.bcap;
+    }
+    if (hs.bcap != c->bcap) return fail(c, DIAM_EINVAL, "diam_load", "checkpoint does not match this context");
+    auto bufs = state_buffers(c);
+    size_t total = sizeof(HostState);
+    for (auto& b : bufs) total += b.second;
+    if (total != size) return fail(c, DIAM_EINVAL, "diam_load", "checkpoint does not match this context");
+    const char* in = (const char*)buf + sizeof(hs);
+    for (auto& b : bufs) {
+        CK(cudaMemcpy(b.first, in, b.second, cudaMemcpyHostToDevice));
+        in += b.second;
+    }
+    c->t = hs.t; c->n = hs.n; c->acc_refresh = hs.acc_refresh; c->acc_all = hs.acc_all;
+    c->refreshes = hs.refreshes; c->notspd = hs.notspd; c->begun_block = hs.begun_block; c->beta = hs.beta;
+    for (size_t i = 0; i < c->pend.size(); ++i) c->pend[i].block = hs.pend_block[i];
+    c->xi_block = -1;  // noise products are regenerated from the counter-based streams
+    CKS(quantise(c));
+    return sync_and_check(c);
+}
+
+void diam_destroy(diam_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    if (c->st) cudaStreamSynchronize(c->st);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+}  // extern "C"

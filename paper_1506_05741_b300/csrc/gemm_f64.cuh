@@ -145,9 +145,9 @@ struct EpiFold {
     int ld;
     const double* s;      // sums of the centred samples of the interval
     const double* delta;  // interval mean - running mean
-    const double* coef;   // [0] = 1/nb, [1] = w = n nb / (n + nb)
+    double inb;           // 1 / nb
+    double w;             // n nb / (n + nb)
     __device__ void apply(double (&acc)[4][4], int m0, int n0, int tx, int ty, int M, int N, int) const {
-        double inb = coef[0], w = coef[1];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             int n = n0 + ty + 16 * j;

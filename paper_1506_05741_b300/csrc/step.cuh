@@ -1,0 +1,365 @@
+// step.cuh -- per-step and per-interval kernels of the DIAM sampler.
+//
+// T is the chain-state type: double (FP64 mode) or float (BF16 mode, where the factor, the noise and the
+// target's linear map are BF16 and the states FP32). One thread block per chain for the O(d) work; the
+// products (noise, linear-map targets, moments) are separate GEMM launches.
+#pragma once
+#include "common.cuh"
+
+namespace diam {
+namespace {  // internal linkage: each translation unit that launches these gets its own copy
+
+// Device-resident scalars of one context.
+struct Ctl {
+    double beta, rho, ba, inv_infl2;   // beta, sqrt(1 - beta^2), beta * alpha, 1 / alpha^2 (in effect)
+    unsigned long long acc_block;      // accepted moves in the current interval
+    unsigned long long nonfinite;      // proposals with a non-finite log-density
+    int status;                        // DEV_* code, first error wins
+    int chol_info;                     // Cholesky failure (pivot + 1)
+    double trace;                      // tr(M2) at the last refresh
+};
+
+enum : int { TK_DIAG = 0, TK_DENSE = 1, TK_TANH = 2, TK_BANANA = 3, TK_REF = 4, TK_CALLBACK = 5 };
+
+struct TargetDev {
+    int kind;
+    int d_y;
+    const double* inv_lam;   // d, 1 / lambda_i
+    double ban_a, ban_b, ban_c;
+};
+
+// O(d) part of log pi at x (terms that need no matrix): the diagonal Gaussian, the tanh-regression prior,
+// the banana tail. Returns this thread's share over i = tid, tid + nthreads, ...
+template <typename T>
+__device__ __forceinline__ double od_term(const TargetDev& tg, int i, T x) {
+    if (tg.kind == TK_DIAG || tg.kind == TK_TANH || (tg.kind == TK_BANANA && i >= 2)) {
+        double xd = (double)x;
+        return -0.5 * xd * xd * tg.inv_lam[i];
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ double banana_head(const TargetDev& tg, double x1, double x2) {
+    double v = x2 + tg.ban_b * x1 * x1 - tg.ban_c;
+    return -x1 * x1 / (2.0 * tg.ban_a) - 0.5 * v * v;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// W for n_steps steps starting at t0 and P chains: row r = s P + p holds W (d entries, zero-padded to ld).
+template <typename OutT>
+__device__ __forceinline__ OutT cvt_w(float v);
+template <>
+__device__ __forceinline__ double cvt_w<double>(float v) { return (double)v; }
+template <>
+__device__ __forceinline__ float cvt_w<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ uint16_t cvt_w<uint16_t>(float v) { return f32_to_bf16_bits(v); }
+
+template <typename OutT>
+__global__ void gen_w_kernel(Key key, int64_t t0, int P, int d, int ld, OutT* __restrict__ out) {
+    const int64_t r = blockIdx.x;
+    const int s = (int)(r / P), p = (int)(r % P);
+    const int64_t t = t0 + s;
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; 4 * j < ld; j += gridDim.y * blockDim.x) {
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * j < d) w = normals4(key, (uint32_t)j, t, (uint32_t)p);
+        OutT* o = out + r * ld + 4 * j;
+        float v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = (4 * j + q < d) ? cvt_w<OutT>(v[q]) : cvt_w<OutT>(0.f);
+    }
+}
+
+template <typename WT>
+__device__ __forceinline__ float w_as_f32(WT v);
+template <>
+__device__ __forceinline__ float w_as_f32<uint16_t>(uint16_t v) { return bf16_bits_to_f32(v); }
+template <>
+__device__ __forceinline__ float w_as_f32<float>(float v) { return v; }
+
+// ---------------------------------------------------------------------------------------------------
+// Proposal of eq. (diamnl) for every chain, with the whitened state carried along:
+//   x* = x_ref + rho (x - x_ref) + xi,   z* = rho z + beta alpha W,   q* = |z*|^2 / (2 alpha^2)
+// (z = A_n^{-1}(x - x_ref) is exact in exact arithmetic: applying A_n^{-1} to the proposal gives the
+// z recursion, so q* needs no triangular solve). The O(d) part of log pi(x*) is summed on the way.
+// BF16 mode also writes x* as a two-term BF16 split (hi + lo) for the tensor-core target product.
+template <typename T, typename WT>
+__global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __restrict__ X, const T* __restrict__ Z,
+                                                      const T* __restrict__ Xi, const WT* __restrict__ W, int ldw,
+                                                      const T* __restrict__ xref, T* __restrict__ Xp, T* __restrict__ Zp,
+                                                      double* __restrict__ qp, double* __restrict__ lpo, const Ctl* ctl,
+                                                      TargetDev tg, uint16_t* __restrict__ op_hi,
+                                                      uint16_t* __restrict__ op_lo, int ldk) {
+    __shared__ double sh[32];
+    const int p = blockIdx.x;
+    const T rho = (T)ctl->rho, ba = (T)ctl->ba;
+    const T* x = X + (size_t)p * d;
+    const T* z = Z + (size_t)p * d;
+    const T* xi = Xi + (size_t)p * d;
+    const WT* w = W + (size_t)p * ldw;
+    T* xp = Xp + (size_t)p * d;
+    T* zp = Zp + (size_t)p * d;
+    double qacc = 0.0, lacc = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        T xr = xref[i];
+        T v = xr + rho * (x[i] - xr) + xi[i];
+        T wz;
+        if constexpr (sizeof(WT) == sizeof(T)) wz = (T)w[i];
+        else wz = (T)w_as_f32<WT>(w[i]);
+        T u = rho * z[i] + ba * wz;
+        xp[i] = v;
+        zp[i] = u;
+        qacc += (double)u * (double)u;
+        lacc += od_term<T>(tg, i, v);
+        if (op_hi) {
+            uint16_t h = f32_to_bf16_bits((float)v);
+            float hv = bf16_bits_to_f32(h);
+            op_hi[(size_t)p * ldk + i] = h;
+            op_lo[(size_t)p * ldk + i] = f32_to_bf16_bits((float)v - hv);
+        }
+    }
+    qacc = block_sum(qacc, sh);
+    lacc = block_sum(lacc, sh);
+    if (threadIdx.x == 0) {
+        if (tg.kind == TK_BANANA) lacc += banana_head(tg, (double)xp[0], d > 1 ? (double)xp[1] : 0.0);
+        qp[p] = 0.5 * qacc * ctl->inv_infl2;
+        lpo[p] = lacc;
+    }
+}
+
+// O(d) part of log pi for any state buffer (initial state, imported state); BF16 operand planes if asked.
+template <typename T>
+__global__ void __launch_bounds__(256) od_terms_kernel(int d, const T* __restrict__ Xs, double* __restrict__ lpo,
+                                                       TargetDev tg, uint16_t* __restrict__ op_hi,
+                                                       uint16_t* __restrict__ op_lo, int ldk) {
+    __shared__ double sh[32];
+    const int p = blockIdx.x;
+    const T* x = Xs + (size_t)p * d;
+    double lacc = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        T v = x[i];
+        lacc += od_term<T>(tg, i, v);
+        if (op_hi) {
+            uint16_t h = f32_to_bf16_bits((float)v);
+            op_hi[(size_t)p * ldk + i] = h;
+            op_lo[(size_t)p * ldk + i] = f32_to_bf16_bits((float)v - bf16_bits_to_f32(h));
+        }
+    }
+    lacc = block_sum(lacc, sh);
+    if (threadIdx.x == 0) {
+        if (tg.kind == TK_BANANA) lacc += banana_head(tg, (double)x[0], d > 1 ? (double)x[1] : 0.0);
+        lpo[p] = lacc;
+    }
+}
+
+// lp[p] = lpo[p] + sum over m-tiles of the linear-map partials (fixed order), or the external value.
+__global__ void sum_lp_kernel(int P, const double* __restrict__ lpo, const double* __restrict__ partial, int nparts,
+                              const double* __restrict__ ext, double* __restrict__ lp) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double v;
+    if (ext) {
+        v = ext[p];
+    } else {
+        v = lpo[p];
+        for (int m = 0; m < nparts; ++m) v += partial[(size_t)m * P + p];
+    }
+    lp[p] = v;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Metropolis-Hastings test of Algorithm 1 and the select / record step.
+//   log a = log pi(x*) + q(x*) - log pi(x) - q(x);  accept iff log u < log a, u = Philox uniform (tag U).
+// Records x_{n+1} - c (c the interval's centring point) for the moment fold, and per-chain interval sums.
+template <typename T, typename HT>
+__device__ __forceinline__ HT to_hist(T v);
+template <>
+__device__ __forceinline__ double to_hist<double, double>(double v) { return v; }
+template <>
+__device__ __forceinline__ uint16_t to_hist<float, uint16_t>(float v) { return f32_to_bf16_bits(v); }
+
+struct TraceDev {
+    double *lp, *q, *qc, *loga;
+    int8_t* acc;
+    int64_t steps;
+};
+
+template <typename T, typename HT>
+__global__ void __launch_bounds__(256) accept_kernel(int d, int P, Key key, int64_t t, T* __restrict__ X, T* __restrict__ Z,
+                                                     const T* __restrict__ Xp, const T* __restrict__ Zp,
+                                                     double* __restrict__ lp, double* __restrict__ q,
+                                                     const double* __restrict__ lpp_in, const double* __restrict__ qp,
+                                                     Ctl* ctl, HT* __restrict__ hist, int ldh, const T* __restrict__ cen,
+                                                     double* __restrict__ bsum, double* __restrict__ lpsum,
+                                                     TraceDev tr) {
+    __shared__ int s_acc;
+    __shared__ double s_lp;
+    const int p = blockIdx.x;
+    if (threadIdx.x == 0) {
+        double lpp = lpp_in[p], qpp = qp[p], lpc = lp[p], qc = q[p];
+        double loga = lpp - lpc + qpp - qc;
+        bool finite = isfinite(lpp) && isfinite(qpp);
+        double u = uniform53(key, t, (uint32_t)p, TAG_U);
+        int a = finite && (log(u) < loga);
+        if (t < tr.steps) {
+            size_t k = (size_t)t * P + p;
+            tr.lp[k] = lpp; tr.q[k] = qpp; tr.qc[k] = qc; tr.loga[k] = loga; tr.acc[k] = (int8_t)a;
+        }
+        if (a) {
+            lp[p] = lpp;
+            q[p] = qpp;
+            atomicAdd(&ctl->acc_block, 1ull);
+        }
+        if (!finite) atomicAdd(&ctl->nonfinite, 1ull);
+        s_acc = a;
+        s_lp = a ? lpp : lpc;
+    }
+    __syncthreads();
+    const int a = s_acc;
+    T* x = X + (size_t)p * d;
+    T* z = Z + (size_t)p * d;
+    const T* xp = Xp + (size_t)p * d;
+    const T* zp = Zp + (size_t)p * d;
+    HT* h = hist ? hist + (size_t)p * ldh : nullptr;
+    double* bs = bsum ? bsum + (size_t)p * d : nullptr;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        T v = a ? xp[i] : x[i];
+        if (a) {
+            x[i] = v;
+            z[i] = zp[i];
+        }
+        if (h) h[i] = to_hist<T, HT>(v - cen[i]);
+        if (bs) bs[i] += (double)v;
+    }
+    if (lpsum && threadIdx.x == 0) lpsum[p] += s_lp;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Interval moment fold: column sums of the centred samples (two-pass, fixed order).
+template <typename HT>
+__device__ __forceinline__ double hist_val(HT v);
+template <>
+__device__ __forceinline__ double hist_val<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ double hist_val<uint16_t>(uint16_t v) { return (double)bf16_bits_to_f32(v); }
+
+template <typename HT>
+__global__ void colsum_partial_kernel(const HT* __restrict__ H, int ldh, int rows, int d, double* __restrict__ part) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    double s = 0.0;
+    for (int r = blockIdx.y; r < rows; r += gridDim.y) s += hist_val<HT>(H[(size_t)r * ldh + i]);
+    part[(size_t)blockIdx.y * d + i] = s;
+}
+
+// s = sum of the partials; delta = (c + s / nb) - mean
+__global__ void fold_prep_kernel(int d, int nparts, const double* __restrict__ part, const double* __restrict__ cen64,
+                                 const double* __restrict__ mean, double inb, double* __restrict__ s,
+                                 double* __restrict__ delta) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    double v = 0.0;
+    for (int c = 0; c < nparts; ++c) v += part[(size_t)c * d + i];
+    s[i] = v;
+    delta[i] = (cen64[i] + v * inb) - mean[i];
+}
+
+// mean += delta nb / (n + nb); the next interval is centred at the new mean (cen64 exact copy of cenT).
+template <typename T>
+__global__ void mean_update_kernel(int d, double frac, const double* __restrict__ delta, double* __restrict__ mean,
+                                   double* __restrict__ cen64, T* __restrict__ cenT) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    double m = mean[i] + delta[i] * frac;
+    mean[i] = m;
+    T c = (T)m;
+    cenT[i] = c;
+    cen64[i] = (double)c;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Refresh helpers.
+__global__ void trace_kernel(int d, const double* __restrict__ M2, int ld, Ctl* ctl) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) s += M2[(size_t)i * ld + i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) ctl->trace = s;
+}
+
+// C = M2 / n + tau I (lower triangle)
+__global__ void build_c_kernel(int d, const double* __restrict__ M2, int ld, double inv_n, double tau,
+                               double* __restrict__ Cm) {
+    int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i; j += gridDim.x * blockDim.x) {
+        double v = M2[(size_t)i * ld + j] * inv_n;
+        if (i == j) v += tau;
+        Cm[(size_t)i * ld + j] = v;
+    }
+}
+
+// Quantised factor: Lq64 = round_bf16(L) and its BF16 bits (row-major, ldk columns, zero padded).
+__global__ void quantise_factor_kernel(int d, const double* __restrict__ L, int ld, double* __restrict__ Lq64,
+                                       uint16_t* __restrict__ Lq16, int ldk) {
+    int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ldk; j += gridDim.x * blockDim.x) {
+        double v = (j < d) ? round_bf16(L[(size_t)i * ld + j]) : 0.0;
+        if (j < d) Lq64[(size_t)i * ld + j] = v;
+        Lq16[(size_t)i * ldk + j] = bf16_bits_of_rounded(v);
+    }
+}
+
+// work = x - x_ref in FP64 (for the whitening solve z = Lq^{-1}(x - x_ref))
+template <typename T>
+__global__ void diff_kernel(int d, const T* __restrict__ Xs, const T* __restrict__ xref, double* __restrict__ work) {
+    int p = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x)
+        work[(size_t)p * d + i] = (double)Xs[(size_t)p * d + i] - (double)xref[i];
+}
+
+// z = work (rounded to T), q = |z|^2 / (2 alpha^2) from the stored z; lp = -q for the reference target.
+template <typename T>
+__global__ void __launch_bounds__(256) set_z_kernel(int d, const double* __restrict__ work, T* __restrict__ Zs,
+                                                    double* __restrict__ qout, double inv_infl2,
+                                                    double* __restrict__ lp_ref) {
+    __shared__ double sh[32];
+    int p = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        T v = (T)work[(size_t)p * d + i];
+        if (Zs) Zs[(size_t)p * d + i] = v;
+        acc += (double)v * (double)v;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        double qq = 0.5 * acc * inv_infl2;
+        if (qout) qout[p] = qq;
+        if (lp_ref) lp_ref[p] = -qq;
+    }
+}
+
+__global__ void set_scalars_kernel(Ctl* ctl, double beta, double rho, double ba, double inv_infl2) {
+    ctl->beta = beta;
+    ctl->rho = rho;
+    ctl->ba = ba;
+    ctl->inv_infl2 = inv_infl2;
+    ctl->acc_block = 0ull;
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(size_t n, const A* __restrict__ in, B* __restrict__ out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (B)in[i];
+}
+
+// Row-major d_y x d FP64 matrix -> BF16 bits (round to nearest even), ldk columns, zero padded.
+__global__ void to_bf16_rows_kernel(int rows, int d, const double* __restrict__ in, uint16_t* __restrict__ out, int ldk) {
+    int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ldk; j += gridDim.x * blockDim.x) {
+        double v = (j < d) ? round_bf16(in[(size_t)i * d + j]) : 0.0;
+        out[(size_t)i * ldk + j] = bf16_bits_of_rounded(v);
+    }
+}
+
+}  // namespace
+}  // namespace diam

@@ -1,0 +1,354 @@
+// tc_gemm.cu -- BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// One CTA per 128 x BN output tile (cta_group::1). K advances in blocks of 64 BF16 (128 bytes): a TMA
+// thread stages the A and B tiles (128-byte swizzle) into a 4-deep shared-memory ring, one elected thread
+// issues tcgen05.mma into an FP32 accumulator in tensor memory and releases each stage with
+// tcgen05.commit, and all four warps read the accumulator back (tcgen05.ld) for the epilogue:
+//   - store (the noise product xi = beta alpha Lq W of Algorithm 1's batch update),
+//   - per-chain reduction of the target's log-likelihood terms (linear-map targets),
+//   - the FP64 moment fold of a lower-triangle SYRK (eq. (sampcov) as a pairwise centred update).
+// Every wait is bounded by the clock; on expiry the kernel records DEV_TIMEOUT, drains what it issued,
+// frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "common.cuh"
+#include "tc_gemm.h"
+
+namespace diam {
+
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr long long TC_WAIT_CYCLES = 1ll << 31;  // about one second at the B300 SM clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity; false if the clock limit passed or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          long long limit = TC_WAIT_CYCLES) {
+    long long start = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - start > limit) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, A and B BF16, both K-major, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                         const __grid_constant__ CUtensorMap tmB,
+                                                         const __grid_constant__ CUtensorMap tmB2, int M, int N, int nkb,
+                                                         int a_lower, int has_b2, TcEpi epi, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
+    const uint32_t stage_bytes = A_BYTES + B_BYTES * (has_b2 ? 2u : 1u);
+    uint64_t* bars = (uint64_t*)(smem + TC_STAGES * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + TC_STAGES;
+    uint64_t* done = bars + 2 * TC_STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int mt = blockIdx.x, nt = blockIdx.y;
+    const int m0 = mt * TC_BM, n0 = nt * BN;
+    if (epi.mode == TC_FOLD && n0 + BN - 1 < m0) return;  // every (n, m) of the tile has n < m
+    int kb_end = nkb;
+    if (a_lower) kb_end = min(nkb, (m0 + TC_BM + TC_BK - 1) / TC_BK);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(done), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int issued = 0;
+        for (int kb = 0; kb < kb_end; ++kb) {
+            const int s = kb % TC_STAGES;
+            if (kb >= TC_STAGES && !mbar_wait(smem_u32(&empty[s]), ((kb / TC_STAGES) & 1) ^ 1, abort_flag)) break;
+            uint8_t* st = smem + s * stage_bytes;
+            const uint32_t fb = smem_u32(&full[s]);
+            mbar_expect_tx(fb, stage_bytes);
+            tma_load_2d(smem_u32(st), &tmA, fb, kb * TC_BK, m0);
+            tma_load_2d(smem_u32(st + A_BYTES), &tmB, fb, kb * TC_BK, n0);
+            if (has_b2) tma_load_2d(smem_u32(st + A_BYTES + B_BYTES), &tmB2, fb, kb * TC_BK, n0);
+            issued = kb + 1;
+        }
+        if (*abort_flag) {
+            // drain: every issued stage must land before the CTA may exit
+            for (int kb = max(0, issued - TC_STAGES); kb < issued; ++kb) {
+                long long t0 = clock64();
+                while (!mbar_try(smem_u32(&full[kb % TC_STAGES]), (kb / TC_STAGES) & 1) && clock64() - t0 < TC_WAIT_CYCLES) {
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(BN);
+        for (int kb = 0; kb < kb_end; ++kb) {
+            const int s = kb % TC_STAGES;
+            if (!mbar_wait(smem_u32(&full[s]), (kb / TC_STAGES) & 1, abort_flag)) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * stage_bytes);
+            const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint64_t ad = sdesc_sw128(sa + kk * 32);
+                umma_bf16(tmem, ad, sdesc_sw128(sb + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+                if (has_b2) umma_bf16(tmem, ad, sdesc_sw128(sb + B_BYTES + kk * 32), idesc, 1u);
+            }
+            umma_commit(smem_u32(&empty[s]));
+        }
+        umma_commit(smem_u32(done));
+    }
+    __syncwarp();
+
+    // epilogue: wait for the accumulator (bounded), then every warp reads its 32 TMEM lanes
+    mbar_wait(smem_u32(done), 0, abort_flag);
+    __syncthreads();
+    const bool ok = (*abort_flag == 0);
+    tc_fence_after();
+    if (ok) {
+        const int row = warp * 32 + lane;
+        const int m = m0 + row;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        if (epi.mode == TC_TARGET) {
+            float* red = (float*)smem;  // the staging ring is free once the accumulator is complete
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld32(trow + c * 32, r);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int n = n0 + c * 32 + j;
+                    float f = 0.f;
+                    if (m < M && n < N) {
+                        float u = __uint_as_float(r[j]);
+                        if (epi.tanh_mode) {
+                            double rr = epi.y[m] - (double)tanhf(u);
+                            f = (float)(-rr * rr * epi.inv2s2);
+                        } else {
+                            f = -0.5f * u * u;
+                        }
+                    }
+                    red[row * (BN + 1) + c * 32 + j] = f;
+                }
+            }
+            __syncthreads();
+            for (int col = threadIdx.x; col < BN; col += blockDim.x) {
+                double s = 0.0;
+                for (int rr = 0; rr < TC_BM; ++rr) s += (double)red[rr * (BN + 1) + col];
+                if (n0 + col < N) epi.partial[(size_t)mt * N + n0 + col] = s;
+            }
+        } else {
+            const float scale = (epi.mode == TC_STORE && epi.scale_dev) ? (float)*epi.scale_dev : 1.0f;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld32(trow + c * 32, r);
+                if (m < M) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int n = n0 + c * 32 + j;
+                        if (n >= N) continue;
+                        const float v = __uint_as_float(r[j]);
+                        if (epi.mode == TC_STORE) {
+                            epi.D[(size_t)n * epi.ldd + m] = scale * v;
+                        } else if (n >= m) {
+                            double add = (double)v - epi.s[n] * epi.s[m] * epi.inb + epi.delta[n] * epi.delta[m] * epi.w;
+                            epi.M2[(size_t)n * epi.ldm + m] += add;
+                        }
+                    }
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        set_status(status, DEV_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+}
+
+// ---------------------------------------------------------------------------------------------------- host
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// 2D BF16 map over rows x ld (ld the padded row length, a multiple of 64), box 64 x box_rows, 128B swizzle.
+static bool make_map(CUtensorMap* map, const void* ptr, int rows, int ld, int box_rows) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, int>, CUtensorMap> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_tuple(ptr, rows, ld, box_rows);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *map = it->second;
+        return true;
+    }
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    if (cache.size() > 4096) cache.clear();
+    cache[key] = *map;
+    return true;
+}
+
+template <int BN>
+static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
+                             int ldb, int a_lower, const TcEpi& epi, int* status, cudaStream_t st) {
+    CUtensorMap mA, mB, mB2;
+    if (!make_map(&mA, A, M, lda, TC_BM) || !make_map(&mB, B, N, ldb, BN) ||
+        !make_map(&mB2, B2 ? B2 : B, N, ldb, BN))
+        return cudaErrorInvalidValue;
+    const int has_b2 = B2 != nullptr;
+    const size_t stage = (size_t)TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2 * (has_b2 ? 2 : 1);
+    size_t smem = 1024 + TC_STAGES * stage + 256;
+    const size_t red = (size_t)TC_BM * (BN + 1) * 4;
+    if (smem < 1024 + red + 256) smem = 1024 + red + 256;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN);
+    tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, M, N, K / TC_BK, a_lower, has_b2, epi, status);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2, int ldb,
+                         int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (K <= 0 || K % TC_BK || lda % TC_BK || ldb % TC_BK || K > lda || K > ldb) return cudaErrorInvalidValue;
+    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)(B2 ? B2 : B)) & 15) return cudaErrorInvalidValue;
+    return launch_bn<128>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status_dev, st);
+}
+
+// ---------------------------------------------------------------------------------------------------- transpose
+__global__ void transpose_bf16_kernel(const uint16_t* __restrict__ in, int ldi, int rows, int cols,
+                                      uint16_t* __restrict__ out, int ldo) {
+    __shared__ uint16_t tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        int r = r0 + k, c = c0 + threadIdx.x;
+        tile[k][threadIdx.x] = (r < rows && c < cols) ? in[(size_t)r * ldi + c] : (uint16_t)0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        int c = c0 + k, r = r0 + threadIdx.x;
+        if (c < cols && r < ldo) out[(size_t)c * ldo + r] = tile[threadIdx.x][k];
+    }
+}
+
+cudaError_t transpose_bf16(const uint16_t* in, int ldi, int rows, int cols, uint16_t* out, int ldo, cudaStream_t st) {
+    dim3 grid((cols + 31) / 32, (ldo + 31) / 32);
+    transpose_bf16_kernel<<<grid, dim3(32, 8), 0, st>>>(in, ldi, rows, cols, out, ldo);
+    return cudaGetLastError();
+}
+
+}  // namespace diam

@@ -1,0 +1,43 @@
+// tc_gemm.h -- BF16 tensor-core (tcgen05, sm_103a) GEMM used by the BF16 mode of the sampler.
+//
+//   acc(n, m) = sum_k A[m*lda + k] * B[n*ldb + k]   (+ B2[n*ldb + k] accumulated into the same acc)
+//
+// A and B are BF16, K-contiguous (row-major with K the fastest index), K a multiple of 64 and the row
+// strides multiples of 8 elements; accumulation is FP32 in tensor memory. Tiles are 128 (m) x BN (n).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace diam {
+
+enum TcMode : int {
+    TC_STORE = 0,   // D[n*ldd + m] = scale * acc (FP32), scale = *scale_dev
+    TC_TARGET = 1,  // partial[m_tile * N + n] = sum_m f(acc(n, m)): -(y_m - tanh acc)^2 inv2s2 or -acc^2/2
+    TC_FOLD = 2     // lower triangle n >= m: M2[n*ldm + m] += acc - s_n s_m inb + delta_n delta_m w
+};
+
+struct TcEpi {
+    int mode;
+    float* D;
+    int ldd;
+    const double* scale_dev;
+    double* partial;
+    const double* y;
+    double inv2s2;
+    int tanh_mode;
+    double* M2;
+    int ldm;
+    const double* s;
+    const double* delta;
+    double inb, w;
+};
+
+// a_lower: A is lower triangular (A[m][k] = 0 for k > m), K blocks past the m-tile are skipped.
+// status_dev: receives a non-zero code if a bounded wait inside the kernel expired.
+cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
+                         int ldb, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st);
+
+// out[c*ldo + r] = in[r*ldi + c] for r < rows, c < cols (BF16 bits), zero-padded rows c in [cols, pad_cols)
+cudaError_t transpose_bf16(const uint16_t* in, int ldi, int rows, int cols, uint16_t* out, int ldo, cudaStream_t st);
+
+}  // namespace diam

@@ -1,0 +1,36 @@
+"""Shared set-up for the parity tests: one run description builds both the CUDA sampler (through the C ABI)
+and the oracle with identical parameters. Inputs come from the seeded workload generators only."""
+import numpy as np
+
+import oracle
+import workloads
+
+CFG_KEYS = ["d", "P", "n_lag", "M", "beta0", "infl", "adapt_beta", "xref_mode", "acc_lo", "acc_hi", "beta_factor",
+            "beta_min", "beta_max", "eps_jitter", "min_samples_refresh", "refresh_delay", "prec", "seed",
+            "problem_id", "burnin"]
+
+
+def oracle_target(ts):
+    return oracle.Target(ts.kind, ts.d, ts.d_y, lam=ts.lam, G=ts.G, A=ts.A, y=ts.y, sigma=ts.sigma,
+                         ban_a=ts.ban_a, ban_b=ts.ban_b, ban_c=ts.ban_c)
+
+
+def make_pair(ts, P, trace_steps=0, threads=4, x0=None, C0=None, xref0=None, **kw):
+    """(gpu_sampler, oracle_sampler) for target spec ts, P chains and config overrides kw."""
+    import paper_1506_05741_b300 as dm
+    d = ts.d
+    cfg = dm.default_config(d, P, **kw)
+    cfg["trace_steps"] = trace_steps
+    ocfg = oracle.default_config(**{k: cfg[k] for k in CFG_KEYS})
+    ocfg.update(threads=threads, trace_steps=trace_steps)
+    g = dm.Sampler(cfg, ts, x0=x0, C0=C0, xref0=xref0)
+    o = oracle.Sampler(ocfg, oracle_target(ts), x0=x0, C0=C0, xref0=xref0)
+    return g, o
+
+
+def rel_err(a, b, scale):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b)) / np.maximum(scale, 1.0))
+
+
+def trace_scale(tr):
+    return np.maximum.reduce([np.abs(tr["lp_prop"]), np.abs(tr["q_prop"]), np.abs(tr["q_cur"])])

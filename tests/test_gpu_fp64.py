@@ -1,0 +1,227 @@
+"""FP64 CUDA path vs the FP64 oracle, through the C ABI.
+
+Bars: the noise draws are bit-exact; proposals' log-densities, proposal-density quadratics and log a agree
+to 1e-12 relative (to max(1, |log pi(x*)|, |q(x*)|, |q(x)|)); every accept decision is identical; states,
+moments and factors agree to the same relative level. Sizes are small enough for the oracle (seconds) but
+span several 64-wide tiles with ragged tails (d = 96, 130, 200), odd chain counts and refreshes."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import make_pair, rel_err, trace_scale
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _lib():
+    import paper_1506_05741_b300 as dm
+    l = dm.lib()
+    P, I32, I64, U32, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+    l.diam_op_normals.argtypes = [U64, U32, I64, I32, I32, I32, I32, I32, P, P]
+    l.diam_op_cholesky_f64.argtypes = [I32, P, I32, P, P]
+    l.diam_op_trsm_lower_f64.argtypes = [I32, I32, P, I32, P, I32, P]
+    for f in (l.diam_op_normals, l.diam_op_cholesky_f64, l.diam_op_trsm_lower_f64):
+        f.restype = ctypes.c_int
+    return l
+
+
+def test_noise_draws_are_bit_exact():
+    torch = _torch()
+    l = _lib()
+    d, P, S, ld = 103, 5, 3, 104
+    out = torch.zeros(S * P * ld, dtype=torch.float32, device="cuda")
+    assert l.diam_op_normals(77, 3, 40, S, P, d, ld, 0, out.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    g = out.cpu().numpy().reshape(S, P, ld)
+    for s in range(S):
+        for p in range(P):
+            want = oracle.normals(77, 3, 40 + s, p, d)
+            assert np.array_equal(g[s, p, :d].view(np.uint32), want.view(np.uint32))
+            assert np.all(g[s, p, d:] == 0)
+    # BF16 kind: the FP32 draw rounded to nearest even
+    outb = torch.zeros(S * P * ld, dtype=torch.int16, device="cuda")
+    assert l.diam_op_normals(77, 3, 40, S, P, d, ld, 2, outb.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    bits = outb.cpu().numpy().view(np.uint16).reshape(S, P, ld).astype(np.uint32) << 16
+    vals = bits.view(np.float32).astype(np.float64)
+    for s in range(S):
+        for p in range(P):
+            assert np.array_equal(vals[s, p, :d], oracle.round_bf16(oracle.normals(77, 3, 40 + s, p, d)))
+
+
+@pytest.mark.parametrize("d", [1, 5, 64, 65, 130, 300])
+def test_cholesky_matches_oracle(d):
+    torch = _torch()
+    l = _lib()
+    Cm = workloads.spd_matrix(d, 500 + d, cond=1e6)
+    A = torch.from_numpy(Cm.copy()).cuda()
+    info = ctypes.c_int32(-1)
+    assert l.diam_op_cholesky_f64(d, A.data_ptr(), d, ctypes.byref(info), None) == 0
+    assert info.value == 0
+    L = A.cpu().numpy()
+    ref = oracle.cholesky(Cm)
+    assert np.max(np.abs(L - ref)) <= 1e-11 * np.max(np.abs(ref))
+    assert np.all(np.triu(L, 1) == 0)
+
+
+def test_cholesky_reports_indefinite_and_large_reconstructs():
+    torch = _torch()
+    l = _lib()
+    bad = np.eye(70)
+    bad[40, 40] = -1.0
+    A = torch.from_numpy(bad).cuda()
+    info = ctypes.c_int32(0)
+    assert l.diam_op_cholesky_f64(70, A.data_ptr(), 70, ctypes.byref(info), None) == 0
+    assert info.value == 41
+    d = 2048
+    Cm = workloads.spd_matrix(d, 9, cond=1e4)
+    A = torch.from_numpy(Cm.copy()).cuda()
+    assert l.diam_op_cholesky_f64(d, A.data_ptr(), d, ctypes.byref(info), None) == 0 and info.value == 0
+    L = A
+    Cg = torch.from_numpy(Cm).cuda()
+    assert (torch.linalg.norm(L @ L.T - Cg) / torch.linalg.norm(Cg)).item() < 1e-14
+
+
+def test_trsm_matches_forward_substitution():
+    torch = _torch()
+    l = _lib()
+    d, rows = 200, 7
+    Lm = np.linalg.cholesky(workloads.spd_matrix(d, 3, cond=1e4))
+    B = np.random.default_rng(0).standard_normal((rows, d))
+    Lg = torch.from_numpy(Lm).cuda()
+    Bg = torch.from_numpy(B.copy()).cuda()
+    assert l.diam_op_trsm_lower_f64(d, rows, Lg.data_ptr(), d, Bg.data_ptr(), d, None) == 0
+    torch.cuda.synchronize()
+    Y = Bg.cpu().numpy()
+    for r in range(rows):
+        want = oracle.forward_sub(Lm, B[r])
+        assert np.max(np.abs(Y[r] - want)) <= 1e-12 * max(1.0, np.max(np.abs(want)))
+
+
+def _compare(g, o, steps, tol=TOL):
+    tg, to = g.trace(steps), o.trace()
+    assert np.array_equal(tg["acc"], to["acc"]), np.argwhere(tg["acc"] != to["acc"])[:5]
+    sc = trace_scale(to)
+    for k in ("lp_prop", "q_prop", "q_cur", "loga"):
+        assert rel_err(tg[k], to[k], sc) <= tol, (k, rel_err(tg[k], to[k], sc))
+    xg, lpg, st = g.state()
+    xo, lpo = o.state()
+    assert np.max(np.abs(xg - xo)) <= tol * max(1.0, np.max(np.abs(xo)))
+    assert rel_err(lpg, lpo, np.abs(lpo)) <= tol
+    co = o.counts()
+    assert st["accepted"] == co["accepted"] and st["refreshes"] == co["refreshes"]
+    assert st["n"] == co["n"]
+    mg, cg, n = g.moments()
+    mo, cmo = o.moments()
+    assert n == co["n"]
+    assert np.max(np.abs(mg - mo)) <= 1e-11 * max(1.0, np.max(np.abs(mo)))
+    assert np.max(np.abs(cg - cmo)) <= 1e-10 * np.max(np.abs(cmo))
+    Lg, Lqg, xrg, bg = g.factor()
+    Lo, Lqo, xro = o.factor()
+    assert np.max(np.abs(Lg - Lo)) <= 1e-9 * np.max(np.abs(Lo))
+    assert abs(bg - o.beta) <= 1e-15 * o.beta
+    return tg
+
+
+def test_diag64_single_chain_matches_oracle():
+    """The diag64 workload (d = 64, lambda_i = i^-2, P = 1, n_lag = 100, x_0 = 0, A_0 = Id, beta = 0.3)."""
+    run = workloads.diag64()
+    steps = 3000
+    g, o = make_pair(run.target, run.P, trace_steps=steps, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed)
+    g.run(steps)
+    o.run(steps)
+    tg = _compare(g, o, steps)
+    assert o.counts()["refreshes"] > 0 and tg["acc"].sum() > 100
+
+
+@pytest.mark.parametrize("kind", ["dense", "tanh", "banana"])
+def test_small_targets_match_oracle(kind):
+    if kind == "dense":
+        ts, P = workloads.dense_gaussian(96, 11), 5
+    elif kind == "tanh":
+        ts, P = workloads.tanh_regression(130, 70, 12), 7
+    else:
+        ts, P = workloads.banana(70), 3
+    steps, nl = 320, 16
+    x0 = workloads.start_state(ts.d, P, 5, scale=0.1)
+    g, o = make_pair(ts, P, trace_steps=steps, n_lag=nl, beta0=0.25, seed=21, min_samples_refresh=40, x0=x0)
+    g.run(100)
+    g.run(steps - 100)      # a run that stops mid-interval and resumes
+    o.run(steps)
+    _compare(g, o, steps)
+    assert o.counts()["refreshes"] >= 5
+
+
+def test_refresh_delay_burnin_and_inflation_match_oracle():
+    ts, P = workloads.dense_gaussian(200, 4), 3
+    steps = 240
+    g, o = make_pair(ts, P, trace_steps=steps, n_lag=20, beta0=0.3, seed=5, min_samples_refresh=30,
+                     refresh_delay=2, burnin=50, infl=1.2, x0=workloads.start_state(200, P, 8, scale=0.05))
+    g.run(steps)
+    o.run(steps)
+    _compare(g, o, steps)
+
+
+def test_reference_gaussian_accepts_every_proposal_on_gpu():
+    d, P = 150, 4
+    ts = workloads.TargetSpec(workloads.TARGET_REF, d)
+    import paper_1506_05741_b300 as dm
+    cfg = dm.default_config(d, P, n_lag=20, beta0=0.4, min_samples_refresh=20, infl=1.3, seed=3)
+    cfg["trace_steps"] = 200
+    g = dm.Sampler(cfg, ts, x0=workloads.start_state(d, P, 1))
+    g.run(200)
+    tr = g.trace(200)
+    assert tr["acc"].all()
+    assert np.abs(tr["loga"]).max() < 1e-9
+    assert g.stats()["refreshes"] >= 5
+
+
+def test_checkpoint_resume_is_bit_identical():
+    ts, P = workloads.tanh_regression(96, 30, 2), 4
+    import paper_1506_05741_b300 as dm
+    cfg = dm.default_config(96, P, n_lag=10, beta0=0.3, seed=9, min_samples_refresh=20)
+    cfg["keep_block_sums"] = 1
+    a = dm.Sampler(cfg, ts)
+    a.run(95)
+    blob = a.save()
+    a.run(105)
+    b = dm.Sampler(cfg, ts)
+    b.load(blob)
+    b.run(105)
+    xa, lpa, sa = a.state()
+    xb, lpb, sb = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(lpa, lpb) and sa == sb
+    ma, ca, na = a.moments()
+    mb, cb, nb = b.moments()
+    assert np.array_equal(ma, mb) and np.array_equal(ca, cb) and na == nb
+    xs_a, _ = a.block_sums(20)
+    xs_b, _ = b.block_sums(20)
+    assert np.array_equal(xs_a, xs_b)
+
+
+def test_moment_merge_equals_pooled_samples():
+    """eq. (mom2g), (mom1g): merging exported moments gives the moments of all samples pooled."""
+    ts, P = workloads.diag_gaussian(40, 1.0), 2
+    kw = dict(n_lag=10, beta0=0.4, min_samples_refresh=10)
+    ga, oa = make_pair(ts, P, seed=1, **kw)
+    gb, ob = make_pair(ts, P, seed=2, **kw)
+    oa.run(100, record=True)
+    ob.run(100, record=True)
+    ga.run(100)
+    gb.run(100)
+    mb, M2b, nb = gb.export_moments()
+    ga.sync_moments(mb, M2b, nb)
+    m, cov, n = ga.moments()
+    X = np.concatenate([oa.trajectory().reshape(-1, 40), ob.trajectory().reshape(-1, 40)])
+    assert n == X.shape[0]
+    assert np.max(np.abs(m - X.mean(0))) < 1e-11
+    assert np.max(np.abs(cov - np.cov(X.T, bias=True))) < 1e-10 * np.max(np.abs(cov))
