@@ -1,0 +1,116 @@
+"""BF16 (mixed-precision) CUDA path: the tcgen05 GEMM against torch's FP32-accumulated BF16 product, and the
+sampler against the oracle run in its BF16 mode (same rounded factor A_q, same rounded noise W_q, same
+rounded linear map). The CUDA side keeps FP32 states and FP32 accumulation, so agreement is to the FP32
+level: log-densities, proposal quadratics and log a within 1e-5 relative (to max(1, |log pi|, |q|)),
+accept decisions identical over the compared steps."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import make_pair, rel_err, trace_scale
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _gemm(M, N, K, A, B, B2=None, a_lower=0, scale=1.0):
+    import torch
+    import paper_1506_05741_b300 as dm
+    l = dm.lib()
+    f = l.diam_op_gemm_bf16
+    P, I32 = ctypes.c_void_p, ctypes.c_int32
+    f.argtypes = [I32, I32, I32, P, I32, P, P, I32, I32, ctypes.c_float, P, I32, P]
+    f.restype = ctypes.c_int
+    D = torch.zeros(N, M, dtype=torch.float32, device="cuda")
+    rc = f(M, N, K, A.data_ptr(), A.shape[1], B.data_ptr(), None if B2 is None else B2.data_ptr(), B.shape[1],
+           a_lower, scale, D.data_ptr(), M, None)
+    assert rc == 0, rc
+    return D
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 192), (130, 257, 128)])
+def test_tc_gemm_matches_torch(M, N, K):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    D = _gemm(M, N, K, A.view(torch.int16), B.view(torch.int16), scale=0.5)
+    ref = 0.5 * (B.float() @ A.float().T)
+    assert (D - ref).abs().max().item() <= 1e-5 * ref.abs().max().item() + 1e-6
+
+
+def test_tc_gemm_second_operand_and_lower_triangle():
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(7)
+    M = K = 320
+    N = 192
+    A = torch.tril(torch.randn(M, K, device="cuda", generator=g)).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    B2 = (torch.randn(N, K, device="cuda", generator=g) * 1e-3).to(torch.bfloat16)
+    D = _gemm(M, N, K, A.view(torch.int16), B.view(torch.int16), B2.view(torch.int16), a_lower=1)
+    ref = (B.float() + B2.float()) @ A.float().T
+    assert (D - ref).abs().max().item() <= 1e-5 * ref.abs().max().item()
+
+
+def _bf16_pair(ts, P, steps, **kw):
+    import oracle as _o
+    return make_pair(ts, P, trace_steps=steps, prec=_o.BF16, **kw)
+
+
+@pytest.mark.parametrize("kind", ["tanh", "dense", "diag"])
+def test_bf16_steps_match_oracle_bf16_mode(kind):
+    if kind == "tanh":
+        ts, P = workloads.tanh_regression(200, 130, 31), 6
+    elif kind == "dense":
+        ts, P = workloads.dense_gaussian(150, 32), 5
+    else:
+        ts, P = workloads.diag_gaussian(100), 3
+    d = ts.d
+    steps = 12
+    C0 = np.diag(np.linspace(0.5, 1.5, d) * (ts.lam if ts.lam is not None else np.full(d, 0.01)))
+    x0 = workloads.start_state(d, P, 4, scale=np.sqrt(np.diag(C0)))
+    g, o = _bf16_pair(ts, P, steps, n_lag=8, beta0=0.3, seed=13, C0=C0, x0=x0, min_samples_refresh=10 ** 9)
+    g.run(steps)
+    o.run(steps)
+    tg, to = g.trace(steps), o.trace()
+    assert np.array_equal(tg["acc"], to["acc"])
+    sc = trace_scale(to)
+    for k in ("lp_prop", "q_prop", "q_cur", "loga"):
+        assert rel_err(tg[k], to[k], sc) <= TOL, (k, rel_err(tg[k], to[k], sc))
+    L, Lq, xr, _ = g.factor()
+    Lo, Lqo, xro = o.factor()
+    assert np.array_equal(Lq, Lqo) and np.array_equal(xr, xro)
+
+
+def test_bf16_refresh_and_moments_track_oracle():
+    ts, P = workloads.dense_gaussian(130, 41), 8
+    steps = 64
+    g, o = _bf16_pair(ts, P, steps, n_lag=16, beta0=0.3, seed=3, min_samples_refresh=30,
+                      x0=workloads.start_state(130, P, 2, scale=0.05))
+    g.run(16)
+    o.run(16)
+    # after one interval: identical decisions, so the moments agree to BF16-sample precision (the CUDA
+    # fold multiplies samples rounded to BF16 about the interval centre)
+    assert np.array_equal(g.trace(16)["acc"], o.trace()["acc"])
+    mg, cg, n = g.moments()
+    mo, co = o.moments()
+    assert n == o.counts()["n"]
+    assert np.max(np.abs(mg - mo)) <= 1e-5 * max(1e-3, np.max(np.abs(mo)))
+    assert np.max(np.abs(cg - co)) <= 2e-2 * np.max(np.abs(co))
+
+
+def test_bf16_reference_gaussian_accepts_almost_every_proposal():
+    d, P = 256, 8
+    import paper_1506_05741_b300 as dm
+    ts = workloads.TargetSpec(workloads.TARGET_REF, d)
+    cfg = dm.default_config(d, P, n_lag=32, beta0=0.5, min_samples_refresh=64, seed=4, prec=2)
+    cfg["trace_steps"] = 256
+    g = dm.Sampler(cfg, ts, x0=workloads.start_state(d, P, 6))
+    g.run(256)
+    tr = g.trace(256)
+    assert tr["acc"].mean() > 0.999
+    assert np.abs(tr["loga"]).max() < 1e-3
+    assert g.stats()["refreshes"] >= 3

@@ -135,7 +135,7 @@ def _compare(g, o, steps, tol=TOL):
 def test_diag64_single_chain_matches_oracle():
     """The diag64 workload (d = 64, lambda_i = i^-2, P = 1, n_lag = 100, x_0 = 0, A_0 = Id, beta = 0.3)."""
     run = workloads.diag64()
-    steps = 3000
+    steps = 8000
     g, o = make_pair(run.target, run.P, trace_steps=steps, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed)
     g.run(steps)
     o.run(steps)
