@@ -107,12 +107,16 @@ def test_trsm_matches_forward_substitution():
         assert np.max(np.abs(Y[r] - want)) <= 1e-12 * max(1.0, np.max(np.abs(want)))
 
 
-def _compare(g, o, steps, tol=TOL):
+def _compare(g, o, steps, tol=TOL, q_tol=TOL):
+    """tol bounds log pi(x*) and the states; q_tol bounds q(x*), q(x), log a. The CUDA path carries
+    z = A_n^{-1}(x - x_ref) by the z recursion while the oracle solves by forward substitution, so their
+    difference is the substitution's forward error, proportional to cond(A_n) eps."""
     tg, to = g.trace(steps), o.trace()
     assert np.array_equal(tg["acc"], to["acc"]), np.argwhere(tg["acc"] != to["acc"])[:5]
     sc = trace_scale(to)
-    for k in ("lp_prop", "q_prop", "q_cur", "loga"):
-        assert rel_err(tg[k], to[k], sc) <= tol, (k, rel_err(tg[k], to[k], sc))
+    assert rel_err(tg["lp_prop"], to["lp_prop"], sc) <= tol, rel_err(tg["lp_prop"], to["lp_prop"], sc)
+    for k in ("q_prop", "q_cur", "loga"):
+        assert rel_err(tg[k], to[k], sc) <= q_tol, (k, rel_err(tg[k], to[k], sc))
     xg, lpg, st = g.state()
     xo, lpo = o.state()
     assert np.max(np.abs(xg - xo)) <= tol * max(1.0, np.max(np.abs(xo)))
@@ -139,7 +143,11 @@ def test_diag64_single_chain_matches_oracle():
     g, o = make_pair(run.target, run.P, trace_steps=steps, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed)
     g.run(steps)
     o.run(steps)
-    tg = _compare(g, o, steps)
+    # starting at A_0 = Id the chain is stuck for thousands of steps and the adapted factor spans several
+    # orders of magnitude on its diagonal: the substitution error of q is cond(A_n) eps, not eps
+    L, _, _ = o.factor()
+    cond = np.max(np.abs(np.diag(L))) / np.min(np.abs(np.diag(L)))
+    tg = _compare(g, o, steps, q_tol=max(TOL, 1e-15 * cond * run.target.d))
     assert o.counts()["refreshes"] > 0 and tg["acc"].sum() > 100
 
 
@@ -152,8 +160,12 @@ def test_small_targets_match_oracle(kind):
     else:
         ts, P = workloads.banana(70), 3
     steps, nl = 320, 16
-    x0 = workloads.start_state(ts.d, P, 5, scale=0.1)
-    g, o = make_pair(ts, P, trace_steps=steps, n_lag=nl, beta0=0.25, seed=21, min_samples_refresh=40, x0=x0)
+    C0 = ts.cov if ts.cov is not None else np.diag(ts.lam)
+    x0 = workloads.start_state(ts.d, P, 5) @ np.linalg.cholesky(C0).T
+    # eps_jitter 1e-3 keeps every refresh well conditioned (few samples per dimension early on), so the
+    # two FP64 factorisations agree to rounding instead of to cond(C_n) * rounding
+    g, o = make_pair(ts, P, trace_steps=steps, n_lag=nl, beta0=0.25, seed=21, min_samples_refresh=40, x0=x0,
+                     C0=C0, eps_jitter=1e-3)
     g.run(100)
     g.run(steps - 100)      # a run that stops mid-interval and resumes
     o.run(steps)
@@ -164,8 +176,9 @@ def test_small_targets_match_oracle(kind):
 def test_refresh_delay_burnin_and_inflation_match_oracle():
     ts, P = workloads.dense_gaussian(200, 4), 3
     steps = 240
+    x0 = workloads.start_state(200, P, 8) @ np.linalg.cholesky(ts.cov).T
     g, o = make_pair(ts, P, trace_steps=steps, n_lag=20, beta0=0.3, seed=5, min_samples_refresh=30,
-                     refresh_delay=2, burnin=50, infl=1.2, x0=workloads.start_state(200, P, 8, scale=0.05))
+                     refresh_delay=2, burnin=50, infl=1.2, x0=x0, C0=ts.cov, eps_jitter=1e-3)
     g.run(steps)
     o.run(steps)
     _compare(g, o, steps)
@@ -175,7 +188,7 @@ def test_reference_gaussian_accepts_every_proposal_on_gpu():
     d, P = 150, 4
     ts = workloads.TargetSpec(workloads.TARGET_REF, d)
     import paper_1506_05741_b300 as dm
-    cfg = dm.default_config(d, P, n_lag=20, beta0=0.4, min_samples_refresh=20, infl=1.3, seed=3)
+    cfg = dm.default_config(d, P, n_lag=20, beta0=0.4, min_samples_refresh=20, infl=1.3, seed=3, eps_jitter=1e-3)
     cfg["trace_steps"] = 200
     g = dm.Sampler(cfg, ts, x0=workloads.start_state(d, P, 1))
     g.run(200)
@@ -211,7 +224,8 @@ def test_checkpoint_resume_is_bit_identical():
 def test_moment_merge_equals_pooled_samples():
     """eq. (mom2g), (mom1g): merging exported moments gives the moments of all samples pooled."""
     ts, P = workloads.diag_gaussian(40, 1.0), 2
-    kw = dict(n_lag=10, beta0=0.4, min_samples_refresh=10)
+    x0 = workloads.start_state(40, P, 3) * np.sqrt(ts.lam)
+    kw = dict(n_lag=10, beta0=0.4, min_samples_refresh=10, eps_jitter=1e-3, x0=x0, C0=ts.cov)
     ga, oa = make_pair(ts, P, seed=1, **kw)
     gb, ob = make_pair(ts, P, seed=2, **kw)
     oa.run(100, record=True)
