@@ -109,7 +109,7 @@ typedef struct {
     double acc_lo, acc_hi;  /* acceptance window; Sec. 3.2 uses [0.3, 0.5] for DIAM */
     double beta_factor;     /* multiplicative beta change (the paper leaves it open; default 1.1) */
     double beta_min, beta_max;
-    double eps_jitter;      /* refresh factors chol(C_n + eps tr(C_n)/d I), eps x100 per retry (3 retries) */
+    double eps_jitter;      /* refresh factors chol(C_n + eps diag(C_n)), eps x100 per retry (3 retries) */
     int64_t min_samples_refresh;  /* refresh only after this many accepted moves (< 0: d + 1) */
     int64_t burnin;         /* n_0: steps kept out of the moments (footnote to Algorithm 1) */
     int32_t refresh_delay;  /* the factor built at the end of interval k is used from interval k+1+delay */
@@ -118,7 +118,8 @@ typedef struct {
     uint32_t problem_id;    /* mixed into the key; distinct problems draw distinct streams */
     int32_t trace_steps;    /* keep a per-step, per-chain trace for the first trace_steps steps (0: off) */
     int32_t keep_block_sums;/* 1: keep per-interval, per-chain sums of x and log pi (for ESS / PSRF) */
-    int32_t reserved[7];
+    int32_t profile;        /* 1: time every phase with CUDA events on the context's stream (diam_get_profile) */
+    int32_t reserved[6];
 } diam_config;
 
 typedef struct {
@@ -129,6 +130,7 @@ typedef struct {
     int64_t notspd;         /* refreshes skipped because C_n was not positive definite */
     int64_t nonfinite;      /* proposals whose log-density was not finite (always rejected) */
     double beta;            /* beta in effect */
+    int64_t chol_attempts;  /* Cholesky factorisations run by refreshes (retries included) */
 } diam_stats;
 
 typedef struct diam_ctx diam_ctx;
@@ -180,9 +182,22 @@ DIAM_API diam_status diam_get_block_sums(diam_ctx* ctx, double* xsum, double* lp
 DIAM_API diam_status diam_save(diam_ctx* ctx, void* buf, size_t* size);
 DIAM_API diam_status diam_load(diam_ctx* ctx, const void* buf, size_t size);
 
+/* Phase timings collected while cfg.profile = 1: for each phase, the number of timed launches of its
+ * kernels and their summed device time in milliseconds (CUDA events on the context's stream). Phases:
+ * 0 noise draw, 1 noise product (batched triangular GEMM), 2 propose, 3 target (linear map + reduction),
+ * 4 accept / select / record, 5 moment fold (column sums + SYRK), 6 Cholesky refresh (with its
+ * retries), 7 re-whitening solve after a factor change. counts and ms hold DIAM_N_PHASES entries each.
+ * reset = 1 clears the accumulators after reading. Synchronises. */
+#define DIAM_N_PHASES 8
+DIAM_API diam_status diam_get_profile(diam_ctx* ctx, int64_t* counts, double* ms, int32_t reset);
+
 DIAM_API void diam_destroy(diam_ctx* ctx);
 DIAM_API const char* diam_last_error(const diam_ctx* ctx);
 DIAM_API const char* diam_status_string(diam_status s);
+
+/* Number of CUDA kernel launches this library has made in the calling process (all contexts and op-level
+ * entry points), for accounting what ran on the GPU. */
+DIAM_API uint64_t diam_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -236,9 +236,10 @@ class Sampler:
         return lib().orc_beta(self._h)
 
     def counts(self):
-        out = np.zeros(4, np.int64)
+        out = np.zeros(5, np.int64)
         lib().orc_counts(self._h, _ptr(out))
-        return dict(n=int(out[0]), accepted=int(out[1]), refreshes=int(out[2]), notspd=int(out[3]))
+        return dict(n=int(out[0]), accepted=int(out[1]), refreshes=int(out[2]), notspd=int(out[3]),
+                    chol_attempts=int(out[4]))
 
     def state(self):
         d, P = self.cfg["d"], self.cfg["P"]

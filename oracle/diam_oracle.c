@@ -18,7 +18,7 @@
  *    the Box-Muller transform computed in IEEE FP32 with series for log / sin / cos written out below, so
  *    that the CUDA path can reproduce each draw bit for bit;
  *  - the refresh is skipped until enough moves were accepted, and the Cholesky factor is taken of
- *    C + eps*(tr C / d) I, retrying with a larger eps.
+ *    C + eps diag(C), retrying with a larger eps.
  *
  * Everything else is the plain definition: forward substitution for the quadratic, a textbook
  * Cholesky-Banachiewicz factorisation, sums over samples for the moments.
@@ -268,7 +268,7 @@ typedef struct {
     int64_t n;
     double *sum, *S;                    /* d, d x d */
     int64_t acc_block, acc_total;       /* accepted moves in this block / since the start */
-    int64_t refreshes, notspd;
+    int64_t refreshes, notspd, chol_attempts;
     /* trace */
     double *tr_lp, *tr_q, *tr_qc, *tr_loga;
     int8_t *tr_acc;
@@ -456,19 +456,20 @@ static void orc_block_end(orc_sampler* s, int64_t blk) {
         double* C = (double*)malloc(sizeof(double) * nn);
         double* L = (double*)malloc(sizeof(double) * nn);
         for (int i = 0; i < d; ++i) m[i] = s->sum[i] / (double)s->n;
-        double tr = 0.0;
         for (int i = 0; i < d; ++i)
             for (int j = 0; j < d; ++j) C[(size_t)i * d + j] = s->S[(size_t)i * d + j] / (double)s->n - m[i] * m[j];
-        for (int i = 0; i < d; ++i) tr += C[(size_t)i * d + i];
-        double tau = c->eps_jitter * tr / d;
+        /* skip / jitter rule (the paper is silent on degenerate C_n): factor C_n + eps diag(C_n), i.e. every
+         * variance loaded by the same relative amount, retrying with eps x 100 up to three times */
+        double eps = c->eps_jitter;
         int ok = -1;
         for (int attempt = 0; attempt < 4 && ok != 0; ++attempt) {
             double* Cj = (double*)malloc(sizeof(double) * nn);
             memcpy(Cj, C, sizeof(double) * nn);
-            for (int i = 0; i < d; ++i) Cj[(size_t)i * d + i] += tau;
+            for (int i = 0; i < d; ++i) Cj[(size_t)i * d + i] *= 1.0 + eps;
             ok = orc_cholesky(d, Cj, L);
             free(Cj);
-            tau *= 100.0;
+            eps *= 100.0;
+            s->chol_attempts++;
         }
         if (ok == 0) {
             free(s->pendL[slot]); free(s->pendX[slot]);
@@ -594,6 +595,7 @@ ORC_EXPORT int64_t orc_steps(const orc_sampler* s) { return s->t; }
 ORC_EXPORT double orc_beta(const orc_sampler* s) { return s->beta; }
 ORC_EXPORT void orc_counts(const orc_sampler* s, int64_t* out) {
     out[0] = s->n; out[1] = s->acc_total + s->acc_block; out[2] = s->refreshes; out[3] = s->notspd;
+    out[4] = s->chol_attempts;
 }
 ORC_EXPORT void orc_get_state(const orc_sampler* s, double* x, double* lp) {
     memcpy(x, s->x, sizeof(double) * (size_t)s->cfg.P * s->cfg.d);

@@ -39,17 +39,24 @@ class DiamConfig(C.Structure):
                 ("beta_min", C.c_double), ("beta_max", C.c_double), ("eps_jitter", C.c_double),
                 ("min_samples_refresh", C.c_int64), ("burnin", C.c_int64), ("refresh_delay", C.c_int32),
                 ("prec", C.c_int32), ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("trace_steps", C.c_int32),
-                ("keep_block_sums", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("keep_block_sums", C.c_int32), ("profile", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class DiamStats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("n", C.c_int64), ("accepted", C.c_int64), ("refreshes", C.c_int64),
-                ("notspd", C.c_int64), ("nonfinite", C.c_int64), ("beta", C.c_double)]
+                ("notspd", C.c_int64), ("nonfinite", C.c_int64), ("beta", C.c_double),
+                ("chol_attempts", C.c_int64)]
 
 
 EXPORTS = ["diam_config_default", "diam_init", "diam_run_batch", "diam_sync_moments", "diam_get_moments",
            "diam_export_moments", "diam_get_state", "diam_get_factor", "diam_get_trace", "diam_get_block_sums",
-           "diam_save", "diam_load", "diam_destroy", "diam_last_error", "diam_status_string"]
+           "diam_save", "diam_load", "diam_get_profile", "diam_destroy", "diam_last_error", "diam_status_string"]
+PHASES = ["noise", "xi_gemm", "propose", "target", "accept", "fold", "refresh", "rewhiten"]
+
+
+def kernel_launches() -> int:
+    """CUDA kernel launches made by libdiam.so in this process so far."""
+    return int(lib().diam_kernel_launches())
 
 
 def lib_path() -> str:
@@ -77,9 +84,11 @@ def lib():
                 "diam_get_block_sums": (C.c_int, [P, P, P, P]),
                 "diam_save": (C.c_int, [P, P, P]),
                 "diam_load": (C.c_int, [P, P, C.c_size_t]),
+                "diam_get_profile": (C.c_int, [P, P, P, I32]),
                 "diam_destroy": (None, [P]),
                 "diam_last_error": (C.c_char_p, [P]),
                 "diam_status_string": (C.c_char_p, [C.c_int]),
+                "diam_kernel_launches": (C.c_uint64, []),
             }
             for name, (res, args) in sig.items():
                 f = getattr(l, name)
@@ -211,6 +220,12 @@ class Sampler:
         self._check(self._l.diam_get_state(self._h, _p(x), _p(lp), C.byref(st)), "diam_get_state")
         return x, lp, {k: getattr(st, k) for k, _ in DiamStats._fields_}
 
+    def log_pi(self):
+        """log pi of every chain's current state (P doubles, copied to the host)."""
+        lp = np.zeros(self.P)
+        self._check(self._l.diam_get_state(self._h, None, _p(lp), None), "diam_get_state")
+        return lp
+
     def stats(self):
         st = DiamStats()
         self._check(self._l.diam_get_state(self._h, None, None, C.byref(st)), "diam_get_state")
@@ -237,6 +252,13 @@ class Sampler:
         nb = C.c_int64(n_blocks)
         self._check(self._l.diam_get_block_sums(self._h, _p(xs), _p(ls), C.byref(nb)), "diam_get_block_sums")
         return xs[: nb.value], ls[: nb.value]
+
+    def profile(self, reset: bool = True) -> dict:
+        """Per-phase timed launch counts and device milliseconds (needs cfg['profile'] = 1)."""
+        counts = np.zeros(len(PHASES), np.int64)
+        ms = np.zeros(len(PHASES))
+        self._check(self._l.diam_get_profile(self._h, _p(counts), _p(ms), int(reset)), "diam_get_profile")
+        return {ph: (int(counts[i]), float(ms[i])) for i, ph in enumerate(PHASES)}
 
     def save(self) -> bytes:
         n = C.c_size_t()

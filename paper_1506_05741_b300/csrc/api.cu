@@ -8,6 +8,7 @@
 // factor C_n by FP64 Cholesky; the factor is used from interval k + 1 + refresh_delay on, when the
 // whitened states z are recomputed by a triangular solve. The noise products of an interval are one
 // batched triangular GEMM (Algorithm 1, "Batch update").
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -22,6 +23,11 @@
 #include "tc_gemm.h"
 
 using namespace diam;
+
+namespace diam {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1ull, std::memory_order_relaxed); }
+}  // namespace diam
 
 namespace {
 
@@ -50,7 +56,7 @@ struct diam_ctx {
     Key key{};
 
     // host mirrors of the schedule
-    int64_t t = 0, n = 0, acc_refresh = 0, acc_all = 0, refreshes = 0, notspd = 0;
+    int64_t t = 0, n = 0, acc_refresh = 0, acc_all = 0, refreshes = 0, notspd = 0, chol_attempts = 0;
     uint64_t nonfinite = 0;
     double beta = 0;
     int64_t xi_block = -1, begun_block = -1;
@@ -74,7 +80,49 @@ struct diam_ctx {
     TraceDev tr{};
     double *bsum = nullptr, *lpsum = nullptr;
     int64_t bcap = 0;
+    // phase profiler (cfg.profile): event pairs recorded on the stream, read back at synchronisation points
+    struct Evt {
+        cudaEvent_t a, b;
+        int phase;
+    };
+    std::vector<Evt> evts;
+    size_t evt_used = 0;
+    int64_t prof_cnt[DIAM_N_PHASES] = {};
+    double prof_ms[DIAM_N_PHASES] = {};
 };
+
+enum : int { PH_NOISE = 0, PH_XI = 1, PH_PROPOSE = 2, PH_TARGET = 3, PH_ACCEPT = 4, PH_FOLD = 5, PH_REFRESH = 6,
+             PH_REWHITEN = 7 };
+
+// Start timing a phase; returns the event slot (or -1 when profiling is off).
+static int ph_begin(diam_ctx* c, int phase) {
+    if (!c->cfg.profile) return -1;
+    if (c->evt_used == c->evts.size()) {
+        diam_ctx::Evt e{};
+        if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return -1;
+        c->evts.push_back(e);
+    }
+    int i = (int)c->evt_used++;
+    c->evts[i].phase = phase;
+    cudaEventRecord(c->evts[i].a, c->st);
+    return i;
+}
+
+static void ph_end(diam_ctx* c, int i) {
+    if (i >= 0) cudaEventRecord(c->evts[i].b, c->st);
+}
+
+// Accumulate the recorded pairs (the stream must be synchronised).
+static void prof_flush(diam_ctx* c) {
+    for (size_t i = 0; i < c->evt_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->evts[i].a, c->evts[i].b) == cudaSuccess) {
+            c->prof_ms[c->evts[i].phase] += ms;
+            c->prof_cnt[c->evts[i].phase] += 1;
+        }
+    }
+    c->evt_used = 0;
+}
 
 // ------------------------------------------------------------------------------------------------ helpers
 #define CK(expr)                                                                  \
@@ -155,9 +203,9 @@ template <typename T>
 static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
     const int d = c->d, P = c->P;
     if (c->kind == TK_REF) {
-        diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, src, (const T*)c->xref, c->work);
+        { diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, src, (const T*)c->xref, c->work); count_launch(); }
         CK(trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st));
-        set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)nullptr, nullptr, inv_infl2(c), out);
+        { set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)nullptr, nullptr, inv_infl2(c), out); count_launch(); }
         return DIAM_OK;
     }
     if (c->kind == TK_CALLBACK) {
@@ -165,11 +213,11 @@ static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
         if (s != DIAM_OK) return fail(c, DIAM_ETARGET, "target callback");
         return DIAM_OK;
     }
-    od_terms_kernel<T><<<P, kThreads, 0, c->st>>>(d, src, c->lpo, c->tg, c->bf ? c->op_hi : nullptr,
-                                                  c->bf ? c->op_lo : nullptr, c->ldk);
+    { od_terms_kernel<T><<<P, kThreads, 0, c->st>>>(d, src, c->lpo, c->tg, c->bf ? c->op_hi : nullptr,
+                                                  c->bf ? c->op_lo : nullptr, c->ldk); count_launch(); }
     CKS(linear_target<T>(c, src));
     int np = (c->kind == TK_DENSE || c->kind == TK_TANH) ? c->nparts : 0;
-    sum_lp_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->lpo, c->partial, np, nullptr, out);
+    { sum_lp_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->lpo, c->partial, np, nullptr, out); count_launch(); }
     CK(cudaGetLastError());
     return DIAM_OK;
 }
@@ -178,18 +226,20 @@ static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
 template <typename T>
 static diam_status rewhiten(diam_ctx* c) {
     const int d = c->d, P = c->P;
-    diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, (const T*)c->X, (const T*)c->xref, c->work);
+    int e0 = ph_begin(c, PH_REWHITEN);
+    { diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, (const T*)c->X, (const T*)c->xref, c->work); count_launch(); }
     CK(trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st));
-    set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)c->Z, c->q, inv_infl2(c),
-                                                c->kind == TK_REF ? c->lp : nullptr);
+    { set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)c->Z, c->q, inv_infl2(c),
+                                                c->kind == TK_REF ? c->lp : nullptr); count_launch(); }
     CK(cudaGetLastError());
+    ph_end(c, e0);
     return DIAM_OK;
 }
 
 static void set_xref_from(diam_ctx* c, const double* src_dev) {
     if (c->bf) {
-        convert_kernel<double, float><<<blocks_for(c->d), kThreads, 0, c->st>>>(c->d, src_dev, (float*)c->xref);
-        convert_kernel<float, double><<<blocks_for(c->d), kThreads, 0, c->st>>>(c->d, (const float*)c->xref, c->xref64);
+        { convert_kernel<double, float><<<blocks_for(c->d), kThreads, 0, c->st>>>(c->d, src_dev, (float*)c->xref); count_launch(); }
+        { convert_kernel<float, double><<<blocks_for(c->d), kThreads, 0, c->st>>>(c->d, (const float*)c->xref, c->xref64); count_launch(); }
     } else {
         cudaMemcpyAsync(c->xref, src_dev, sizeof(double) * c->d, cudaMemcpyDeviceToDevice, c->st);
         cudaMemcpyAsync(c->xref64, src_dev, sizeof(double) * c->d, cudaMemcpyDeviceToDevice, c->st);
@@ -200,8 +250,8 @@ static void set_xref_from(diam_ctx* c, const double* src_dev) {
 // BF16 bits) in BF16 mode.
 static diam_status quantise(diam_ctx* c) {
     if (c->bf) {
-        quantise_factor_kernel<<<dim3(blocks_for(c->ldk), c->d), kThreads, 0, c->st>>>(c->d, c->L, c->d, c->Lq64, c->Lq16,
-                                                                                         c->ldk);
+        { quantise_factor_kernel<<<dim3(blocks_for(c->ldk), c->d), kThreads, 0, c->st>>>(c->d, c->L, c->d, c->Lq64, c->Lq16,
+                                                                                         c->ldk); count_launch(); }
         CK(cudaGetLastError());
     }
     return DIAM_OK;
@@ -227,7 +277,10 @@ static diam_status prepare_block(diam_ctx* c, int64_t blk) {
     const int64_t rows = (int64_t)nl * P;
     dim3 g((unsigned)rows, std::max(1u, std::min(64u, blocks_for(c->ldw / 4, 128))));
     if (c->bf) {
-        gen_w_kernel<uint16_t><<<g, 128, 0, c->st>>>(c->key, blk * nl, P, d, c->ldw, (uint16_t*)c->W);
+        int e0 = ph_begin(c, PH_NOISE);
+        { gen_w_kernel<uint16_t><<<g, 128, 0, c->st>>>(c->key, blk * nl, P, d, c->ldw, (uint16_t*)c->W); count_launch(); }
+        ph_end(c, e0);
+        int e1 = ph_begin(c, PH_XI);
         TcEpi epi{};
         epi.mode = TC_STORE;
         epi.D = (float*)c->Xi;
@@ -235,10 +288,15 @@ static diam_status prepare_block(diam_ctx* c, int64_t blk) {
         epi.scale_dev = &c->ctl->ba;
         CK(tc_gemm_bf16(d, (int)rows, c->ldk, c->Lq16, c->ldk, (const uint16_t*)c->W, nullptr, c->ldw, 1, epi,
                         &c->ctl->status, c->st));
+        ph_end(c, e1);
     } else {
-        gen_w_kernel<double><<<g, 128, 0, c->st>>>(c->key, blk * nl, P, d, c->ldw, (double*)c->W);
+        int e0 = ph_begin(c, PH_NOISE);
+        { gen_w_kernel<double><<<g, 128, 0, c->st>>>(c->key, blk * nl, P, d, c->ldw, (double*)c->W); count_launch(); }
+        ph_end(c, e0);
+        int e1 = ph_begin(c, PH_XI);
         EpiStore epi{(double*)c->Xi, d, 1.0, &c->ctl->ba, 0.0};
         CK((gemm_f64<true, true>(d, (int)rows, d, c->Lq64, d, (const double*)c->W, c->ldw, TileRange{1, 0}, epi, c->st)));
+        ph_end(c, e1);
     }
     c->xi_block = blk;
     return DIAM_OK;
@@ -249,26 +307,30 @@ static diam_status do_step(diam_ctx* c, int s, int64_t t) {
     const int d = c->d, P = c->P;
     const T* Xi = (const T*)c->Xi + (size_t)s * P * d;
     constexpr bool BF = std::is_same<T, float>::value;
+    int e0 = ph_begin(c, PH_PROPOSE);
     if constexpr (BF) {
         const uint16_t* Ws = (const uint16_t*)c->W + (size_t)s * P * c->ldw;
-        propose_kernel<T, uint16_t><<<P, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
+        { propose_kernel<T, uint16_t><<<P, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
                                                                (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qp, c->lpo,
-                                                               c->ctl, c->tg, c->op_hi, c->op_lo, c->ldk);
+                                                               c->ctl, c->tg, c->op_hi, c->op_lo, c->ldk); count_launch(); }
     } else {
         const T* Ws = (const T*)c->W + (size_t)s * P * c->ldw;
-        propose_kernel<T, T><<<P, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
+        { propose_kernel<T, T><<<P, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
                                                         (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qp, c->lpo, c->ctl,
-                                                        c->tg, nullptr, nullptr, c->ldk);
+                                                        c->tg, nullptr, nullptr, c->ldk); count_launch(); }
     }
     CK(cudaGetLastError());
+    ph_end(c, e0);
     const double* lpp = c->lpp;
+    int e1 = ph_begin(c, PH_TARGET);
     if (c->kind == TK_REF || c->kind == TK_CALLBACK) {
         CKS(eval_lp<T>(c, (const T*)c->Xp, c->lpp));
     } else {
         CKS(linear_target<T>(c, (const T*)c->Xp));
         int np = (c->kind == TK_DENSE || c->kind == TK_TANH) ? c->nparts : 0;
-        sum_lp_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->lpo, c->partial, np, nullptr, c->lpp);
+        { sum_lp_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->lpo, c->partial, np, nullptr, c->lpp); count_launch(); }
     }
+    ph_end(c, e1);
     const int64_t blk = t / c->nl;
     double* bs = nullptr;
     double* ls = nullptr;
@@ -289,16 +351,18 @@ static diam_status do_step(diam_ctx* c, int s, int64_t t) {
         bs = c->bsum + (size_t)blk * P * d;
         ls = c->lpsum + (size_t)blk * P;
     }
+    int e2 = ph_begin(c, PH_ACCEPT);
     if constexpr (BF) {
-        accept_kernel<T, uint16_t><<<P, kThreads, 0, c->st>>>(
+        { accept_kernel<T, float><<<P, kThreads, 0, c->st>>>(
             d, P, c->key, t, (T*)c->X, (T*)c->Z, (const T*)c->Xp, (const T*)c->Zp, c->lp, c->q, lpp, c->qp, c->ctl,
-            (uint16_t*)c->hist + (size_t)s * P * c->ldh, c->ldh, (const T*)c->cenT, bs, ls, c->tr);
+            (float*)c->hist + (size_t)s * P * c->ldh, c->ldh, (const T*)c->cenT, bs, ls, c->tr); count_launch(); }
     } else {
-        accept_kernel<T, double><<<P, kThreads, 0, c->st>>>(
+        { accept_kernel<T, double><<<P, kThreads, 0, c->st>>>(
             d, P, c->key, t, (T*)c->X, (T*)c->Z, (const T*)c->Xp, (const T*)c->Zp, c->lp, c->q, lpp, c->qp, c->ctl,
-            (double*)c->hist + (size_t)s * P * c->ldh, c->ldh, (const T*)c->cenT, bs, ls, c->tr);
+            (double*)c->hist + (size_t)s * P * c->ldh, c->ldh, (const T*)c->cenT, bs, ls, c->tr); count_launch(); }
     }
     CK(cudaGetLastError());
+    ph_end(c, e2);
     return DIAM_OK;
 }
 
@@ -312,23 +376,25 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
     if (rows <= 0) return DIAM_OK;
     double nb = (double)rows;
     int R = (int)std::min<int64_t>(64, rows);
+    int e0 = ph_begin(c, PH_FOLD);
     constexpr bool BF = std::is_same<T, float>::value;
     if constexpr (BF) {
-        const uint16_t* H = (const uint16_t*)c->hist + (size_t)s0 * P * c->ldh;
-        colsum_partial_kernel<uint16_t><<<dim3(blocks_for(d), R), kThreads, 0, c->st>>>(H, c->ldh, (int)rows, d, c->colpart);
+        const float* H = (const float*)c->hist + (size_t)s0 * P * c->ldh;
+        { colsum_partial_kernel<float><<<dim3(blocks_for(d), R), kThreads, 0, c->st>>>(H, c->ldh, (int)rows, d, c->colpart); count_launch(); }
     } else {
         const double* H = (const double*)c->hist + (size_t)s0 * P * c->ldh;
-        colsum_partial_kernel<double><<<dim3(blocks_for(d), R), kThreads, 0, c->st>>>(H, c->ldh, (int)rows, d, c->colpart);
+        { colsum_partial_kernel<double><<<dim3(blocks_for(d), R), kThreads, 0, c->st>>>(H, c->ldh, (int)rows, d, c->colpart); count_launch(); }
     }
-    fold_prep_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, R, c->colpart, c->cen64, c->mean, 1.0 / nb, c->svec,
-                                                            c->delta);
+    { fold_prep_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, R, c->colpart, c->cen64, c->mean, 1.0 / nb, c->svec,
+                                                            c->delta); count_launch(); }
     double w = (double)c->n * nb / ((double)c->n + nb);
     if constexpr (BF) {
-        // samples as the K index: transpose the interval's records to d x rows (K-contiguous), then the
-        // lower-triangle SYRK on the tensor cores with the FP64 fold in the epilogue
+        // samples as the K index: transpose the interval's FP32 records to d x rows (K-contiguous), rounded
+        // to BF16, then the lower-triangle SYRK on the tensor cores with the FP64 fold in the epilogue; the
+        // column sums above come from the FP32 records, so the interval mean is not rounded to BF16
         int ldt = ((int)rows + 63) / 64 * 64;
-        const uint16_t* H = (const uint16_t*)c->hist + (size_t)s0 * P * c->ldh;
-        CK(transpose_bf16(H, c->ldh, (int)rows, d, c->histT, ldt, c->st));
+        const float* H = (const float*)c->hist + (size_t)s0 * P * c->ldh;
+        CK(transpose_f32_bf16(H, c->ldh, (int)rows, d, c->histT, ldt, c->st));
         TcEpi epi{};
         epi.mode = TC_FOLD;
         epi.M2 = c->M2;
@@ -343,9 +409,10 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
         EpiFold epi{c->M2, d, c->svec, c->delta, 1.0 / nb, w};
         CK((gemm_f64<false, false>(d, d, (int)rows, H, c->ldh, H, c->ldh, TileRange{0, 1}, epi, c->st)));
     }
-    mean_update_kernel<T><<<blocks_for(d), kThreads, 0, c->st>>>(d, nb / ((double)c->n + nb), c->delta, c->mean,
-                                                                 c->cen64, (T*)c->cenT);
+    { mean_update_kernel<T><<<blocks_for(d), kThreads, 0, c->st>>>(d, nb / ((double)c->n + nb), c->delta, c->mean,
+                                                                 c->cen64, (T*)c->cenT); count_launch(); }
     CK(cudaGetLastError());
+    ph_end(c, e0);
     c->n += rows;
     return DIAM_OK;
 }
@@ -353,23 +420,23 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
 // Cholesky refresh at the end of interval blk (skip / jitter rule, retries with a larger jitter).
 static diam_status refresh(diam_ctx* c, int64_t blk) {
     const int d = c->d;
-    trace_kernel<<<1, kThreads, 0, c->st>>>(d, c->M2, d, c->ctl);
-    CKS(sync_and_check(c));
-    double tr = 0;
-    CK(cudaMemcpy(&tr, &c->ctl->trace, sizeof(double), cudaMemcpyDeviceToHost));
+    int e0 = ph_begin(c, PH_REFRESH);
     double inv_n = 1.0 / (double)c->n;
-    double tau = c->cfg.eps_jitter * tr * inv_n / d;
+    double eps = c->cfg.eps_jitter;
     bool ok = false;
     for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
-        build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, inv_n, tau, c->Cw);
+        // C_n + eps diag(C_n): every variance loaded by the same relative amount (the skip / jitter rule)
+        { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, inv_n, eps, c->Cw); count_launch(); }
         CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
         CK(cholesky_f64(c->Cw, d, d, &c->ctl->chol_info, c->st));
         CKS(sync_and_check(c));
         int info = 0;
         CK(cudaMemcpy(&info, &c->ctl->chol_info, sizeof(int), cudaMemcpyDeviceToHost));
         ok = (info == 0);
-        tau *= 100.0;
+        eps *= 100.0;
+        c->chol_attempts++;
     }
+    ph_end(c, e0);
     if (!ok) {
         c->notspd++;
         c->err = "refresh skipped: C_n + jitter not positive definite (previous factor kept)";
@@ -385,13 +452,14 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
 
 static void push_scalars(diam_ctx* c) {
     double rho = std::sqrt(1.0 - c->beta * c->beta);
-    set_scalars_kernel<<<1, 1, 0, c->st>>>(c->ctl, c->beta, rho, c->beta * c->cfg.infl, inv_infl2(c));
+    { set_scalars_kernel<<<1, 1, 0, c->st>>>(c->ctl, c->beta, rho, c->beta * c->cfg.infl, inv_infl2(c)); count_launch(); }
 }
 
 template <typename T>
 static diam_status block_end(diam_ctx* c, int64_t blk) {
     CKS(fold_block<T>(c, blk));
     CKS(sync_and_check(c));
+    prof_flush(c);
     unsigned long long acc = 0, nonf = 0;
     CK(cudaMemcpy(&acc, &c->ctl->acc_block, sizeof(acc), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&nonf, &c->ctl->nonfinite, sizeof(nonf), cudaMemcpyDeviceToHost));
@@ -438,7 +506,7 @@ static diam_status init_state(diam_ctx* c, const double* x0, const double* C0, c
     CKS(dalloc(c, &tmp, sizeof(double) * (size_t)std::max(P * d, d * d)));
     if (x0) {
         CK(cudaMemcpyAsync(tmp, x0, sizeof(double) * (size_t)P * d, cudaMemcpyHostToDevice, c->st));
-        convert_kernel<double, T><<<blocks_for((size_t)P * d), kThreads, 0, c->st>>>((size_t)P * d, tmp, (T*)c->X);
+        { convert_kernel<double, T><<<blocks_for((size_t)P * d), kThreads, 0, c->st>>>((size_t)P * d, tmp, (T*)c->X); count_launch(); }
     }
     // A_0: Cholesky factor of C0, or the identity (Algorithm 1)
     if (C0) {
@@ -500,7 +568,7 @@ static diam_status alloc_all(diam_ctx* c) {
         c->ldw = c->ldk;
         c->ldh = d;
         CKS(dalloc(c, &c->W, sizeof(uint16_t) * rows * c->ldw));
-        CKS(dalloc(c, &c->hist, sizeof(uint16_t) * rows * c->ldh));
+        CKS(dalloc(c, &c->hist, sizeof(float) * rows * c->ldh));
         CKS(dalloc(c, &c->histT, sizeof(uint16_t) * (size_t)d * ((rows + 63) / 64 * 64)));
     } else {
         c->Lq64 = c->L;
@@ -549,7 +617,7 @@ static diam_status upload_target(diam_ctx* c, const diam_target* tg) {
         CK(cudaMemcpy(c->Gm, M, sizeof(double) * (size_t)dy * d, cudaMemcpyHostToDevice));
         if (c->bf) {
             CKS(dalloc(c, &c->Gq16, sizeof(uint16_t) * (size_t)dy * c->ldk));
-            to_bf16_rows_kernel<<<dim3(blocks_for(c->ldk), dy), kThreads, 0, c->st>>>(dy, d, c->Gm, c->Gq16, c->ldk);
+            { to_bf16_rows_kernel<<<dim3(blocks_for(c->ldk), dy), kThreads, 0, c->st>>>(dy, d, c->Gm, c->Gq16, c->ldk); count_launch(); }
             CK(cudaGetLastError());
         }
         CKS(dalloc(c, &c->y, sizeof(double) * std::max(dy, 1)));
@@ -576,6 +644,8 @@ const char* diam_status_string(diam_status s) {
 }
 
 const char* diam_last_error(const diam_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+uint64_t diam_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 diam_status diam_config_default(diam_config* cfg, int32_t d, int32_t P) {
     if (!cfg || d <= 0 || P <= 0) return DIAM_EINVAL;
@@ -676,8 +746,8 @@ diam_status diam_sync_moments(diam_ctx* c, const double* ext_mean, const double*
         CK(cudaMemcpy(c->Cw, ext_M2, sizeof(double) * d * d, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->work, ext_mean, sizeof(double) * d, cudaMemcpyHostToDevice));
         double nn = (double)c->n, ne = (double)ext_n;
-        merge_mean_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, c->mean, c->work, em, ne / (nn + ne));
-        merge_moments_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, c->Cw, em, nn * ne / (nn + ne));
+        { merge_mean_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, c->mean, c->work, em, ne / (nn + ne)); count_launch(); }
+        { merge_moments_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, c->Cw, em, nn * ne / (nn + ne)); count_launch(); }
         CK(cudaGetLastError());
         c->n += ext_n;
     }
@@ -717,7 +787,7 @@ diam_status diam_get_state(diam_ctx* c, double* x, double* lp, diam_stats* stats
     const size_t Pd = (size_t)c->P * c->d;
     if (x) {
         if (c->bf) {
-            convert_kernel<float, double><<<blocks_for(Pd), kThreads, 0, c->st>>>(Pd, (const float*)c->X, c->work);
+            { convert_kernel<float, double><<<blocks_for(Pd), kThreads, 0, c->st>>>(Pd, (const float*)c->X, c->work); count_launch(); }
             CK(cudaStreamSynchronize(c->st));
             CK(cudaMemcpy(x, c->work, sizeof(double) * Pd, cudaMemcpyDeviceToHost));
         } else {
@@ -736,6 +806,7 @@ diam_status diam_get_state(diam_ctx* c, double* x, double* lp, diam_stats* stats
         stats->notspd = c->notspd;
         stats->nonfinite = (int64_t)nonf;
         stats->beta = c->beta;
+        stats->chol_attempts = c->chol_attempts;
     }
     return DIAM_OK;
 }
@@ -782,7 +853,7 @@ diam_status diam_get_block_sums(diam_ctx* c, double* xsum, double* lpsum, int64_
 
 // ---- checkpoint: a flat list of (device buffer, bytes) plus the host schedule
 struct HostState {
-    int64_t t, n, acc_refresh, acc_all, refreshes, notspd, xi_block, begun_block;
+    int64_t t, n, acc_refresh, acc_all, refreshes, notspd, xi_block, begun_block, chol_attempts;
     double beta;
     int64_t pend_block[9];
     int64_t bcap;
@@ -828,7 +899,7 @@ diam_status diam_save(diam_ctx* c, void* buf, size_t* size) {
     HostState hs{};
     hs.t = c->t; hs.n = c->n; hs.acc_refresh = c->acc_refresh; hs.acc_all = c->acc_all;
     hs.refreshes = c->refreshes; hs.notspd = c->notspd; hs.xi_block = -1; hs.begun_block = c->begun_block;
-    hs.beta = c->beta; hs.bcap = c->bcap;
+    hs.beta = c->beta; hs.bcap = c->bcap; hs.chol_attempts = c->chol_attempts;
     for (size_t i = 0; i < c->pend.size(); ++i) hs.pend_block[i] = c->pend[i].block;
     char* o = (char*)buf;
     memcpy(o, &hs, sizeof(hs));
@@ -867,16 +938,36 @@ diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
     }
     c->t = hs.t; c->n = hs.n; c->acc_refresh = hs.acc_refresh; c->acc_all = hs.acc_all;
     c->refreshes = hs.refreshes; c->notspd = hs.notspd; c->begun_block = hs.begun_block; c->beta = hs.beta;
+    c->chol_attempts = hs.chol_attempts;
     for (size_t i = 0; i < c->pend.size(); ++i) c->pend[i].block = hs.pend_block[i];
     c->xi_block = -1;  // noise products are regenerated from the counter-based streams
     CKS(quantise(c));
     return sync_and_check(c);
 }
 
+diam_status diam_get_profile(diam_ctx* c, int64_t* counts, double* ms, int32_t reset) {
+    CKS(check_usable(c));
+    CKS(sync_and_check(c));
+    prof_flush(c);
+    for (int i = 0; i < DIAM_N_PHASES; ++i) {
+        if (counts) counts[i] = c->prof_cnt[i];
+        if (ms) ms[i] = c->prof_ms[i];
+        if (reset) {
+            c->prof_cnt[i] = 0;
+            c->prof_ms[i] = 0.0;
+        }
+    }
+    return DIAM_OK;
+}
+
 void diam_destroy(diam_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
     if (c->st) cudaStreamSynchronize(c->st);
+    for (auto& e : c->evts) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;

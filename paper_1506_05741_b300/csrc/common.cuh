@@ -12,6 +12,9 @@
 
 namespace diam {
 
+// Host side: every kernel launch of the library is counted (diam_kernel_launches).
+void count_launch();
+
 enum : uint32_t { TAG_W = 0, TAG_U = 1, TAG_X0 = 2, TAG_UDA = 3 };
 
 struct Key {

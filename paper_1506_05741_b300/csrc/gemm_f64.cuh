@@ -168,7 +168,7 @@ inline cudaError_t gemm_f64(int M, int N, int K, const double* A, int lda, const
                             const Epi& epi, cudaStream_t st) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     dim3 grid((M + GF_BM - 1) / GF_BM, (N + GF_BN - 1) / GF_BN);
-    gemm_f64_kernel<A_K, B_K, Epi><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, tr, epi);
+    { gemm_f64_kernel<A_K, B_K, Epi><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, tr, epi); count_launch(); }
     return cudaGetLastError();
 }
 

@@ -82,12 +82,12 @@ static int row_blocks(int nrows) { return max(1, min((nrows + 7) / 8, 148 * 8));
 cudaError_t cholesky_f64(double* A, int n, int lda, int* info_dev, cudaStream_t st) {
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         int nb = min(CH_NB, n - k0);
-        chol_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, nb, info_dev);
+        { chol_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, nb, info_dev); count_launch(); }
         int k1 = k0 + nb, rest = n - k1;
         if (rest <= 0) break;
         // panel rows solve x L_kk^T = a, i.e. L_kk x^T = a^T
-        trsv_rows_kernel<<<row_blocks(rest), 256, 0, st>>>(A + (size_t)k0 * lda + k0, lda, nb,
-                                                             A + (size_t)k1 * lda + k0, lda, rest);
+        { trsv_rows_kernel<<<row_blocks(rest), 256, 0, st>>>(A + (size_t)k0 * lda + k0, lda, nb,
+                                                             A + (size_t)k1 * lda + k0, lda, rest); count_launch(); }
         // trailing lower triangle: A[k1+n][k1+m] -= sum_k L[k1+m][k0+k] L[k1+n][k0+k]
         EpiStore epi{A + (size_t)k1 * lda + k1, lda, -1.0, nullptr, 1.0};
         cudaError_t e = gemm_f64<true, true>(rest, rest, nb, A + (size_t)k1 * lda + k0, lda,
@@ -95,7 +95,7 @@ cudaError_t cholesky_f64(double* A, int n, int lda, int* info_dev, cudaStream_t 
         if (e != cudaSuccess) return e;
     }
     dim3 g(max(1, min(32, (n + 255) / 256)), n);
-    zero_upper_kernel<<<g, 256, 0, st>>>(A, lda, n);
+    { zero_upper_kernel<<<g, 256, 0, st>>>(A, lda, n); count_launch(); }
     return cudaGetLastError();
 }
 
@@ -103,7 +103,7 @@ cudaError_t trsm_lower_f64(const double* L, int ldl, int n, double* B, int ldb, 
     if (nrows <= 0 || n <= 0) return cudaSuccess;
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         int nb = min(CH_NB, n - k0);
-        trsv_rows_kernel<<<row_blocks(nrows), 256, 0, st>>>(L + (size_t)k0 * ldl + k0, ldl, nb, B + k0, ldb, nrows);
+        { trsv_rows_kernel<<<row_blocks(nrows), 256, 0, st>>>(L + (size_t)k0 * ldl + k0, ldl, nb, B + k0, ldb, nrows); count_launch(); }
         int k1 = k0 + nb;
         if (k1 >= n) break;
         // B[r][k1 + i] -= sum_k L[k1 + i][k0 + k] Y[r][k0 + k]

@@ -40,9 +40,9 @@ diam_status diam_op_normals(uint64_t seed, uint32_t problem_id, int64_t t0, int3
     cudaStream_t st = (cudaStream_t)stream;
     Key key = make_key(seed, problem_id);
     dim3 g((unsigned)((int64_t)n_steps * P), std::max(1, std::min(64, (ld / 4 + 127) / 128)));
-    if (kind == 0) gen_w_kernel<float><<<g, 128, 0, st>>>(key, t0, P, d, ld, (float*)out);
-    else if (kind == 1) gen_w_kernel<double><<<g, 128, 0, st>>>(key, t0, P, d, ld, (double*)out);
-    else gen_w_kernel<uint16_t><<<g, 128, 0, st>>>(key, t0, P, d, ld, (uint16_t*)out);
+    if (kind == 0) { gen_w_kernel<float><<<g, 128, 0, st>>>(key, t0, P, d, ld, (float*)out); count_launch(); }
+    else if (kind == 1) { gen_w_kernel<double><<<g, 128, 0, st>>>(key, t0, P, d, ld, (double*)out); count_launch(); }
+    else { gen_w_kernel<uint16_t><<<g, 128, 0, st>>>(key, t0, P, d, ld, (uint16_t*)out); count_launch(); }
     return cudaGetLastError() == cudaSuccess ? DIAM_OK : DIAM_ECUDA;
 }
 
@@ -74,7 +74,7 @@ diam_status diam_op_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A
     if (!sc) return DIAM_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
     cudaMemsetAsync(&sc->status, 0, sizeof(int), st);
-    scale_to_dev_kernel<<<1, 1, 0, st>>>(&sc->scale, (double)scale);
+    { scale_to_dev_kernel<<<1, 1, 0, st>>>(&sc->scale, (double)scale); count_launch(); }
     TcEpi epi{};
     epi.mode = TC_STORE;
     epi.D = D;

@@ -176,7 +176,7 @@ __device__ __forceinline__ HT to_hist(T v);
 template <>
 __device__ __forceinline__ double to_hist<double, double>(double v) { return v; }
 template <>
-__device__ __forceinline__ uint16_t to_hist<float, uint16_t>(float v) { return f32_to_bf16_bits(v); }
+__device__ __forceinline__ float to_hist<float, float>(float v) { return v; }
 
 struct TraceDev {
     double *lp, *q, *qc, *loga;
@@ -241,7 +241,7 @@ __device__ __forceinline__ double hist_val(HT v);
 template <>
 __device__ __forceinline__ double hist_val<double>(double v) { return v; }
 template <>
-__device__ __forceinline__ double hist_val<uint16_t>(uint16_t v) { return (double)bf16_bits_to_f32(v); }
+__device__ __forceinline__ double hist_val<float>(float v) { return (double)v; }
 
 template <typename HT>
 __global__ void colsum_partial_kernel(const HT* __restrict__ H, int ldh, int rows, int d, double* __restrict__ part) {
@@ -287,13 +287,13 @@ __global__ void trace_kernel(int d, const double* __restrict__ M2, int ld, Ctl* 
     if (threadIdx.x == 0) ctl->trace = s;
 }
 
-// C = M2 / n + tau I (lower triangle)
-__global__ void build_c_kernel(int d, const double* __restrict__ M2, int ld, double inv_n, double tau,
+// C = M2 / n with its diagonal loaded by (1 + eps) (lower triangle)
+__global__ void build_c_kernel(int d, const double* __restrict__ M2, int ld, double inv_n, double eps,
                                double* __restrict__ Cm) {
     int i = blockIdx.y;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i; j += gridDim.x * blockDim.x) {
         double v = M2[(size_t)i * ld + j] * inv_n;
-        if (i == j) v += tau;
+        if (i == j) v *= 1.0 + eps;
         Cm[(size_t)i * ld + j] = v;
     }
 }

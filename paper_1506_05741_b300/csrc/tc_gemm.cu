@@ -317,7 +317,7 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
         attr_set = true;
     }
     dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN);
-    tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, M, N, K / TC_BK, a_lower, has_b2, epi, status);
+    { tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, M, N, K / TC_BK, a_lower, has_b2, epi, status); count_launch(); }
     return cudaGetLastError();
 }
 
@@ -330,13 +330,13 @@ cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const 
 }
 
 // ---------------------------------------------------------------------------------------------------- transpose
-__global__ void transpose_bf16_kernel(const uint16_t* __restrict__ in, int ldi, int rows, int cols,
-                                      uint16_t* __restrict__ out, int ldo) {
+__global__ void transpose_f32_bf16_kernel(const float* __restrict__ in, int ldi, int rows, int cols,
+                                          uint16_t* __restrict__ out, int ldo) {
     __shared__ uint16_t tile[32][33];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         int r = r0 + k, c = c0 + threadIdx.x;
-        tile[k][threadIdx.x] = (r < rows && c < cols) ? in[(size_t)r * ldi + c] : (uint16_t)0;
+        tile[k][threadIdx.x] = (r < rows && c < cols) ? f32_to_bf16_bits(in[(size_t)r * ldi + c]) : (uint16_t)0;
     }
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
@@ -345,9 +345,9 @@ __global__ void transpose_bf16_kernel(const uint16_t* __restrict__ in, int ldi, 
     }
 }
 
-cudaError_t transpose_bf16(const uint16_t* in, int ldi, int rows, int cols, uint16_t* out, int ldo, cudaStream_t st) {
+cudaError_t transpose_f32_bf16(const float* in, int ldi, int rows, int cols, uint16_t* out, int ldo, cudaStream_t st) {
     dim3 grid((cols + 31) / 32, (ldo + 31) / 32);
-    transpose_bf16_kernel<<<grid, dim3(32, 8), 0, st>>>(in, ldi, rows, cols, out, ldo);
+    { transpose_f32_bf16_kernel<<<grid, dim3(32, 8), 0, st>>>(in, ldi, rows, cols, out, ldo); count_launch(); }
     return cudaGetLastError();
 }
 

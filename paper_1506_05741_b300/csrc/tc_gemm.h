@@ -37,7 +37,8 @@ struct TcEpi {
 cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
                          int ldb, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st);
 
-// out[c*ldo + r] = in[r*ldi + c] for r < rows, c < cols (BF16 bits), zero-padded rows c in [cols, pad_cols)
-cudaError_t transpose_bf16(const uint16_t* in, int ldi, int rows, int cols, uint16_t* out, int ldo, cudaStream_t st);
+// out[c*ldo + r] = bf16(in[r*ldi + c]) (round to nearest even) for r < rows, c < cols; out[c*ldo + r] = 0 for
+// rows <= r < ldo, so the K padding of the transposed operand is zero
+cudaError_t transpose_f32_bf16(const float* in, int ldi, int rows, int cols, uint16_t* out, int ldo, cudaStream_t st);
 
 }  // namespace diam

@@ -92,8 +92,8 @@ def test_bf16_refresh_and_moments_track_oracle():
                       x0=workloads.start_state(130, P, 2, scale=0.05))
     g.run(16)
     o.run(16)
-    # after one interval: identical decisions, so the moments agree to BF16-sample precision (the CUDA
-    # fold multiplies samples rounded to BF16 about the interval centre)
+    # after one interval: identical decisions. The mean comes from FP32 records (FP32-state precision); the
+    # centred second moment multiplies the records rounded to BF16 (relative 2^-8 per product, averaged)
     assert np.array_equal(g.trace(16)["acc"], o.trace()["acc"])
     mg, cg, n = g.moments()
     mo, co = o.moments()

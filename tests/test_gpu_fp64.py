@@ -120,7 +120,8 @@ def _compare(g, o, steps, tol=TOL, q_tol=TOL):
     xg, lpg, st = g.state()
     xo, lpo = o.state()
     assert np.max(np.abs(xg - xo)) <= tol * max(1.0, np.max(np.abs(xo)))
-    assert rel_err(lpg, lpo, np.abs(lpo)) <= tol
+    # the current log pi is one of the traced values: same scale as the trace (q is its natural size)
+    assert rel_err(lpg, lpo, np.maximum(np.abs(lpo), sc.max(axis=0))) <= tol
     co = o.counts()
     assert st["accepted"] == co["accepted"] and st["refreshes"] == co["refreshes"]
     assert st["n"] == co["n"]
@@ -146,8 +147,7 @@ def test_diag64_single_chain_matches_oracle():
     # starting at A_0 = Id the chain is stuck for thousands of steps and the adapted factor spans several
     # orders of magnitude on its diagonal: the substitution error of q is cond(A_n) eps, not eps
     L, _, _ = o.factor()
-    cond = np.max(np.abs(np.diag(L))) / np.min(np.abs(np.diag(L)))
-    tg = _compare(g, o, steps, q_tol=max(TOL, 1e-15 * cond * run.target.d))
+    tg = _compare(g, o, steps, q_tol=max(TOL, 2e-16 * np.linalg.cond(L) * np.sqrt(run.target.d)))
     assert o.counts()["refreshes"] > 0 and tg["acc"].sum() > 100
 
 
