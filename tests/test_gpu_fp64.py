@@ -1,8 +1,12 @@
 """FP64 CUDA path vs the FP64 oracle, through the C ABI.
 
-Bars: the noise draws are bit-exact; proposals' log-densities, proposal-density quadratics and log a agree
-to 1e-12 relative (to max(1, |log pi(x*)|, |q(x*)|, |q(x)|)); every accept decision is identical; states,
-moments and factors agree to the same relative level. Sizes are small enough for the oracle (seconds) but
+Bars: the noise draws are bit-exact; the proposals' log-densities and the chain states agree to 1e-12
+relative (to max(1, |log pi(x*)|, |q(x*)|, |q(x)|)); every accept decision is identical; moments and
+factors agree to 1e-10 / 1e-9 (they pass through an FP64 Cholesky of C_n). The proposal-density quadratic
+q and log a are compared at Q_TOL = 5e-12 (or 4 d u cond(A_n) if larger): the CUDA path carries
+z = A_n^{-1}(x - x_ref) by its recursion while the oracle solves by forward substitution every step, and
+each side carries the triangular solve's forward error, bounded by about d u cond(A_n) (Higham,
+"Accuracy and Stability of Numerical Algorithms", Thm 8.5). Sizes are small enough for the oracle (seconds) but
 span several 64-wide tiles with ragged tails (d = 96, 130, 200), odd chain counts and refreshes."""
 import ctypes
 
@@ -15,6 +19,8 @@ from helpers import make_pair, rel_err, trace_scale
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
+Q_TOL = 5e-12
+U = 2.0 ** -53
 
 
 def _torch():
@@ -107,10 +113,17 @@ def test_trsm_matches_forward_substitution():
         assert np.max(np.abs(Y[r] - want)) <= 1e-12 * max(1.0, np.max(np.abs(want)))
 
 
-def _compare(g, o, steps, tol=TOL, q_tol=TOL):
+def _q_tol(o):
+    L, _, _ = o.factor()
+    return max(Q_TOL, 4 * L.shape[0] * U * np.linalg.cond(L))
+
+
+def _compare(g, o, steps, tol=TOL, q_tol=None):
     """tol bounds log pi(x*) and the states; q_tol bounds q(x*), q(x), log a. The CUDA path carries
     z = A_n^{-1}(x - x_ref) by the z recursion while the oracle solves by forward substitution, so their
     difference is the substitution's forward error, proportional to cond(A_n) eps."""
+    if q_tol is None:
+        q_tol = _q_tol(o)
     tg, to = g.trace(steps), o.trace()
     assert np.array_equal(tg["acc"], to["acc"]), np.argwhere(tg["acc"] != to["acc"])[:5]
     sc = trace_scale(to)
@@ -144,10 +157,9 @@ def test_diag64_single_chain_matches_oracle():
     g, o = make_pair(run.target, run.P, trace_steps=steps, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed)
     g.run(steps)
     o.run(steps)
-    # starting at A_0 = Id the chain is stuck for thousands of steps and the adapted factor spans several
-    # orders of magnitude on its diagonal: the substitution error of q is cond(A_n) eps, not eps
-    L, _, _ = o.factor()
-    tg = _compare(g, o, steps, q_tol=max(TOL, 2e-16 * np.linalg.cond(L) * np.sqrt(run.target.d)))
+    # starting at A_0 = Id the chain is stuck for thousands of steps and the adapted factor is far worse
+    # conditioned than the target: q's bound grows with cond(A_n) (see the module docstring)
+    tg = _compare(g, o, steps)
     assert o.counts()["refreshes"] > 0 and tg["acc"].sum() > 100
 
 
