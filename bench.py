@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true", help="skip the per-phase profile pass (roofline)")
     return ap.parse_args()
 
 
@@ -234,14 +235,16 @@ def main():
     del s
 
     # ---- profile pass: per-phase device time with CUDA events on the same stream
-    sp = make_sampler(run, ts, x0, C0, dm.BF16, profile=1, stream=stream.cuda_stream)
-    sp.run(args.warmup * run.n_lag)
-    sp.profile(reset=True)
-    sp.run(max(2, args.steps // 2) * run.n_lag)
-    prof = sp.profile()
-    sp.close()
-    del sp
-    roof = roofline(prof, run, ts, args.steps, pk, pk_src)
+    roof = None
+    if not args.no_profile:
+        sp = make_sampler(run, ts, x0, C0, dm.BF16, profile=1, stream=stream.cuda_stream)
+        sp.run(args.warmup * run.n_lag)
+        sp.profile(reset=True)
+        sp.run(max(2, args.steps // 2) * run.n_lag)
+        prof = sp.profile()
+        sp.close()
+        del sp
+        roof = roofline(prof, run, ts, args.steps, pk, pk_src)
 
     # ---- plain FP64 form on the same workload (fewer intervals: FP64 is ~1 TFLOP/s on B300)
     fp64 = None
