@@ -39,6 +39,20 @@ DIAM_API diam_status diam_op_gemm_bf16(int32_t M, int32_t N, int32_t K, const ui
                               const uint16_t* B2, int32_t ldb, int32_t a_lower, float scale, float* D, int32_t ldd,
                               void* stream);
 
+/* The product of diam_op_gemm_bf16 (same arguments, same result within FP32 summation order) for callers
+ * that cannot allocate device memory: code whose device memory belongs to its own pool and forbids outside
+ * allocations, or code running while a stream is captured, where an allocating call is not allowed.
+ * The paper has no counterpart; this is an interface convenience of this library.
+ * It never calls cudaMalloc / cudaFree: its scratch (split-K partial products, a status word) is one fixed
+ * 16 MiB device array inside the library, held by every GPU that loads the library until the process exits.
+ * Limits: M * N at most 4,194,240 (the partials of one split must fit the array); larger products are
+ * rejected with DIAM_EINVAL. The first call on each device looks up the array's device address; make that
+ * call before any stream capture. All calls share the array: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller. Synchronises the stream. */
+DIAM_API diam_status diam_op_gemm_bf16_noalloc(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda,
+                                               const uint16_t* B, const uint16_t* B2, int32_t ldb, int32_t a_lower,
+                                               float scale, float* D, int32_t ldd, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
