@@ -267,7 +267,8 @@ typedef struct {
     /* moments (eq. sampcov, sampmean) as plain sums over all post-step samples of all chains */
     int64_t n;
     double *sum, *S;                    /* d, d x d */
-    int64_t acc_block, acc_total;       /* accepted moves in this block / since the start */
+    int64_t acc_block, acc_total;       /* accepted moves in this block / counted for the refresh rule */
+    int64_t acc_all;                    /* every accepted move, burn-in included */
     int64_t refreshes, notspd, chol_attempts;
     /* trace */
     double *tr_lp, *tr_q, *tr_qc, *tr_loga;
@@ -553,6 +554,7 @@ static void orc_step(orc_sampler* s) {
     for (int p = 0; p < P; ++p) {
         const double* x = s->x + (size_t)p * d;
         s->acc_block += acc[p];
+        s->acc_all += acc[p];
         if (t < c->burnin) continue;
         for (int i = 0; i < d; ++i) {
             s->sum[i] += x[i];
@@ -594,7 +596,7 @@ ORC_EXPORT int orc_run(orc_sampler* s, int64_t n_steps, int record) {
 ORC_EXPORT int64_t orc_steps(const orc_sampler* s) { return s->t; }
 ORC_EXPORT double orc_beta(const orc_sampler* s) { return s->beta; }
 ORC_EXPORT void orc_counts(const orc_sampler* s, int64_t* out) {
-    out[0] = s->n; out[1] = s->acc_total + s->acc_block; out[2] = s->refreshes; out[3] = s->notspd;
+    out[0] = s->n; out[1] = s->acc_all; out[2] = s->refreshes; out[3] = s->notspd;
     out[4] = s->chol_attempts;
 }
 ORC_EXPORT void orc_get_state(const orc_sampler* s, double* x, double* lp) {
