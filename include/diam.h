@@ -109,7 +109,8 @@ typedef struct {
     double acc_lo, acc_hi;  /* acceptance window; Sec. 3.2 uses [0.3, 0.5] for DIAM */
     double beta_factor;     /* multiplicative beta change (the paper leaves it open; default 1.1) */
     double beta_min, beta_max;
-    double eps_jitter;      /* refresh factors chol(C_n + eps diag(C_n)), eps x100 per retry (3 retries) */
+    double eps_jitter;      /* refresh factors chol(C_n + eps diag(C_n)), eps x100 per retry (3 retries);
+                               BF16 mode starts at max(eps_jitter, 1e-6): its C_n is accumulated in FP32 */
     int64_t min_samples_refresh;  /* refresh only after this many accepted moves (< 0: d + 1) */
     int64_t burnin;         /* n_0: steps kept out of the moments (footnote to Algorithm 1) */
     int32_t refresh_delay;  /* the factor built at the end of interval k is used from interval k+1+delay */

@@ -70,6 +70,10 @@ struct diam_ctx {
     double *xref64 = nullptr, *L = nullptr, *Lq64 = nullptr, *mean = nullptr, *M2 = nullptr, *cen64 = nullptr;
     double *colpart = nullptr, *svec = nullptr, *delta = nullptr, *Cw = nullptr, *work = nullptr;
     uint16_t *Lq16 = nullptr, *op_hi = nullptr, *op_lo = nullptr, *histT = nullptr;
+    double *qpart = nullptr, *lpart = nullptr, *s16 = nullptr;   // per-chunk proposal sums; BF16 record sums
+    int8_t* accf = nullptr;                                      // per-chain decision of the current step
+    float* ws = nullptr;                                         // split-K partial target products (BF16 mode)
+    int nchunk = 1, tsplit = 1;
     void *W = nullptr, *hist = nullptr;
     int ldw = 0, ldh = 0, nparts = 0;
     // target
@@ -307,29 +311,53 @@ static diam_status do_step(diam_ctx* c, int s, int64_t t) {
     const int d = c->d, P = c->P;
     const T* Xi = (const T*)c->Xi + (size_t)s * P * d;
     constexpr bool BF = std::is_same<T, float>::value;
+    const dim3 grid2(P, c->nchunk);
     int e0 = ph_begin(c, PH_PROPOSE);
     if constexpr (BF) {
         const uint16_t* Ws = (const uint16_t*)c->W + (size_t)s * P * c->ldw;
-        { propose_kernel<T, uint16_t><<<P, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
-                                                               (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qp, c->lpo,
+        { propose_kernel<T, uint16_t><<<grid2, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
+                                                               (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qpart, c->lpart,
                                                                c->ctl, c->tg, c->op_hi, c->op_lo, c->ldk); count_launch(); }
     } else {
         const T* Ws = (const T*)c->W + (size_t)s * P * c->ldw;
-        { propose_kernel<T, T><<<P, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
-                                                        (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qp, c->lpo, c->ctl,
-                                                        c->tg, nullptr, nullptr, c->ldk); count_launch(); }
+        { propose_kernel<T, T><<<grid2, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
+                                                        (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qpart, c->lpart,
+                                                        c->ctl, c->tg, nullptr, nullptr, c->ldk); count_launch(); }
     }
     CK(cudaGetLastError());
     ph_end(c, e0);
-    const double* lpp = c->lpp;
     int e1 = ph_begin(c, PH_TARGET);
+    const double iw = inv_infl2(c);
     if (c->kind == TK_REF || c->kind == TK_CALLBACK) {
         CKS(eval_lp<T>(c, (const T*)c->Xp, c->lpp));
+        { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, t, c->qpart, c->lpart, nullptr, 0, c->lpp,
+                                                            iw, c->lp, c->q, c->accf, c->ctl, c->tr); count_launch(); }
+    } else if (c->kind == TK_DENSE || c->kind == TK_TANH) {
+        const double inv2s2 = 1.0 / (2.0 * c->sigma * c->sigma);
+        if constexpr (BF) {
+            TcEpi epi{};
+            epi.mode = TC_STORE;
+            epi.D = c->ws;
+            epi.ldd = c->dy;
+            epi.split_stride = (size_t)P * c->dy;
+            int used = 1;
+            CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, c->tsplit, epi,
+                                   &c->ctl->status, c->st, &used));
+            { finish_linear_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y, inv2s2, c->kind == TK_TANH,
+                                                            c->nchunk, c->key, t, c->qpart, c->lpart, iw, c->lp, c->q,
+                                                            c->accf, c->ctl, c->tr); count_launch(); }
+        } else {
+            EpiTargetReduce epi{c->partial, c->y, inv2s2, c->kind == TK_TANH};
+            CK((gemm_f64<true, true>(c->dy, P, d, c->Gm, d, (const double*)c->Xp, d, TileRange{0, 0}, epi, c->st)));
+            { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, t, c->qpart, c->lpart, c->partial,
+                                                                c->nparts, nullptr, iw, c->lp, c->q, c->accf, c->ctl,
+                                                                c->tr); count_launch(); }
+        }
     } else {
-        CKS(linear_target<T>(c, (const T*)c->Xp));
-        int np = (c->kind == TK_DENSE || c->kind == TK_TANH) ? c->nparts : 0;
-        { sum_lp_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->lpo, c->partial, np, nullptr, c->lpp); count_launch(); }
+        { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, t, c->qpart, c->lpart, nullptr, 0, nullptr,
+                                                            iw, c->lp, c->q, c->accf, c->ctl, c->tr); count_launch(); }
     }
+    CK(cudaGetLastError());
     ph_end(c, e1);
     const int64_t blk = t / c->nl;
     double* bs = nullptr;
@@ -353,13 +381,13 @@ static diam_status do_step(diam_ctx* c, int s, int64_t t) {
     }
     int e2 = ph_begin(c, PH_ACCEPT);
     if constexpr (BF) {
-        { accept_kernel<T, float><<<P, kThreads, 0, c->st>>>(
-            d, P, c->key, t, (T*)c->X, (T*)c->Z, (const T*)c->Xp, (const T*)c->Zp, c->lp, c->q, lpp, c->qp, c->ctl,
-            (float*)c->hist + (size_t)s * P * c->ldh, c->ldh, (const T*)c->cenT, bs, ls, c->tr); count_launch(); }
+        { select_kernel<T, float><<<grid2, kThreads, 0, c->st>>>(d, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
+                                                                (const T*)c->Zp, (float*)c->hist + (size_t)s * P * c->ldh,
+                                                                c->ldh, (const T*)c->cenT, bs, ls, c->lp); count_launch(); }
     } else {
-        { accept_kernel<T, double><<<P, kThreads, 0, c->st>>>(
-            d, P, c->key, t, (T*)c->X, (T*)c->Z, (const T*)c->Xp, (const T*)c->Zp, c->lp, c->q, lpp, c->qp, c->ctl,
-            (double*)c->hist + (size_t)s * P * c->ldh, c->ldh, (const T*)c->cenT, bs, ls, c->tr); count_launch(); }
+        { select_kernel<T, double><<<grid2, kThreads, 0, c->st>>>(d, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
+                                                                 (const T*)c->Zp, (double*)c->hist + (size_t)s * P * c->ldh,
+                                                                 c->ldh, (const T*)c->cenT, bs, ls, c->lp); count_launch(); }
     }
     CK(cudaGetLastError());
     ph_end(c, e2);
@@ -395,11 +423,12 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
         int ldt = ((int)rows + 63) / 64 * 64;
         const float* H = (const float*)c->hist + (size_t)s0 * P * c->ldh;
         CK(transpose_f32_bf16(H, c->ldh, (int)rows, d, c->histT, ldt, c->st));
+        { rowsum_bf16_kernel<<<d, kThreads, 0, c->st>>>(c->histT, ldt, (int)rows, c->s16); count_launch(); }
         TcEpi epi{};
         epi.mode = TC_FOLD;
         epi.M2 = c->M2;
         epi.ldm = d;
-        epi.s = c->svec;
+        epi.s = c->s16;   // G - s16 s16^T / nb: the scatter of exactly the values the SYRK multiplies
         epi.delta = c->delta;
         epi.inb = 1.0 / nb;
         epi.w = w;
@@ -423,6 +452,9 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
     int e0 = ph_begin(c, PH_REFRESH);
     double inv_n = 1.0 / (double)c->n;
     double eps = c->cfg.eps_jitter;
+    // BF16 mode: the fold's FP32 tensor-core accumulation leaves C_n off by about 1e-5 in correlation terms,
+    // so the first attempt loads the diagonal by at least 1e-6 (relative) instead of retrying up to it
+    if (c->bf && eps < 1e-6) eps = 1e-6;
     bool ok = false;
     for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
         // C_n + eps diag(C_n): every variance loaded by the same relative amount (the skip / jitter rule)
@@ -549,6 +581,18 @@ static diam_status alloc_all(diam_ctx* c) {
     for (double** p : {&c->lp, &c->q, &c->qp, &c->lpo, &c->lpp}) CKS(dalloc(c, p, sizeof(double) * P));
     c->nparts = c->bf ? (c->dy + 127) / 128 : (c->dy + 63) / 64;  // m-tiles of the target product
     CKS(dalloc(c, &c->partial, sizeof(double) * (size_t)c->nparts * P));
+    c->nchunk = (d + CHUNK - 1) / CHUNK;
+    CKS(dalloc(c, &c->qpart, sizeof(double) * (size_t)c->nchunk * P));
+    CKS(dalloc(c, &c->lpart, sizeof(double) * (size_t)c->nchunk * P));
+    CKS(dalloc(c, &c->accf, (size_t)P));
+    CKS(dalloc(c, &c->s16, sizeof(double) * d));
+    if (c->bf && c->dy > 0) {
+        // split the target product's K so that the tiles times the splits fill the 148 SMs once
+        int tiles = ((c->dy + 127) / 128) * ((P + 127) / 128);
+        c->tsplit = std::max(1, std::min(8, 148 / std::max(tiles, 1)));
+        c->tsplit = std::min(c->tsplit, c->ldk / 64);
+        CKS(dalloc(c, &c->ws, sizeof(float) * (size_t)c->tsplit * P * c->dy));
+    }
     for (double** p : {&c->xref64, &c->mean, &c->cen64, &c->svec, &c->delta}) CKS(dalloc(c, p, sizeof(double) * d));
     CKS(dalloc(c, &c->colpart, sizeof(double) * 64 * d));
     CKS(dalloc(c, &c->L, sizeof(double) * d * d));

@@ -13,43 +13,49 @@ namespace diam {
 constexpr int CH_NB = 64;
 
 // Unblocked Cholesky of the nb x nb diagonal block at (k0, k0); lower part in, L out, upper part zeroed.
+// 256 threads as 8 x 32: the rank-1 update of pivot j touches rows j+1+ty, ... and columns j+1+tx, ...
 __global__ void __launch_bounds__(256) chol_diag_kernel(double* __restrict__ A, int lda, int k0, int nb, int* info) {
     __shared__ double a[CH_NB][CH_NB + 1];
-    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-        int i = idx / nb, j = idx % nb;
-        a[i][j] = (j <= i) ? A[(size_t)(k0 + i) * lda + k0 + j] : 0.0;
-    }
+    __shared__ double s_inv;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < nb; i += 8)
+        for (int j = tx; j < nb; j += 32) a[i][j] = (j <= i) ? A[(size_t)(k0 + i) * lda + k0 + j] : 0.0;
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        double piv = a[j][j];
-        if (!(piv > 0.0) && threadIdx.x == 0 && info) atomicCAS(info, 0, k0 + j + 1);
-        double dj = sqrt(piv);  // NaN on failure: it propagates and the caller discards the result
+        if (threadIdx.x == 0) {
+            double piv = a[j][j];
+            if (!(piv > 0.0) && info) atomicCAS(info, 0, k0 + j + 1);
+            double dj = sqrt(piv);    // NaN on failure: it propagates and the caller discards the result
+            a[j][j] = dj;
+            s_inv = 1.0 / dj;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) a[j][j] = dj;
-        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] = a[i][j] / dj;
+        const double inv = s_inv;
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] *= inv;
         __syncthreads();
-        int m = nb - j - 1;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            int i = j + 1 + idx / m, l = j + 1 + idx % m;
-            if (l <= i) a[i][l] = fma(-a[i][j], a[l][j], a[i][l]);
+        for (int i = j + 1 + ty; i < nb; i += 8) {
+            const double aij = a[i][j];
+            for (int l = j + 1 + tx; l <= i; l += 32) a[i][l] = fma(-aij, a[l][j], a[i][l]);
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-        int i = idx / nb, j = idx % nb;
-        A[(size_t)(k0 + i) * lda + k0 + j] = (j <= i) ? a[i][j] : 0.0;
-    }
+    for (int i = ty; i < nb; i += 8)
+        for (int j = tx; j < nb; j += 32) A[(size_t)(k0 + i) * lda + k0 + j] = (j <= i) ? a[i][j] : 0.0;
 }
 
 // For each of nrows rows r: solve L y = b in place, b = B[r*ldb + 0 .. nb), L the nb x nb lower triangle
-// at Lkk (row stride ldl). One warp per row; lane l holds entries l and l + 32.
+// at Lkk (row stride ldl). One warp per row; lane l holds entries l and l + 32. The diagonal enters as
+// reciprocals computed once per block.
 __global__ void __launch_bounds__(256) trsv_rows_kernel(const double* __restrict__ Lkk, int ldl, int nb,
                                                          double* __restrict__ B, int ldb, int nrows) {
     __shared__ double L[CH_NB][CH_NB + 1];
+    __shared__ double invd[CH_NB];
     for (int idx = threadIdx.x; idx < CH_NB * CH_NB; idx += blockDim.x) {
-        int i = idx / CH_NB, j = idx % CH_NB;
+        int i = idx >> 6, j = idx & 63;
         L[i][j] = (i < nb && j <= i) ? Lkk[(size_t)i * ldl + j] : 0.0;
     }
+    __syncthreads();
+    if (threadIdx.x < nb) invd[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warps = blockDim.x >> 5;
@@ -59,7 +65,7 @@ __global__ void __launch_bounds__(256) trsv_rows_kernel(const double* __restrict
         double v1 = lane + 32 < nb ? b[lane + 32] : 0.0;
         for (int j = 0; j < nb; ++j) {
             double bj = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
-            double yj = bj / L[j][j];
+            double yj = bj * invd[j];
             if (lane == (j & 31)) {
                 if (j < 32) v0 = yj; else v1 = yj;
             }

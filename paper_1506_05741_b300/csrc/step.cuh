@@ -83,15 +83,20 @@ __device__ __forceinline__ float w_as_f32<float>(float v) { return v; }
 // (z = A_n^{-1}(x - x_ref) is exact in exact arithmetic: applying A_n^{-1} to the proposal gives the
 // z recursion, so q* needs no triangular solve). The O(d) part of log pi(x*) is summed on the way.
 // BF16 mode also writes x* as a two-term BF16 split (hi + lo) for the tensor-core target product.
+// Grid (P, chunks): block (p, c) covers entries [c CHUNK, (c+1) CHUNK) of chain p and writes its partial
+// sums of |z*|^2 and of the O(d) log-density terms to qpart[c P + p], lpart[c P + p].
+constexpr int CHUNK = 1024;
+
 template <typename T, typename WT>
 __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __restrict__ X, const T* __restrict__ Z,
                                                       const T* __restrict__ Xi, const WT* __restrict__ W, int ldw,
                                                       const T* __restrict__ xref, T* __restrict__ Xp, T* __restrict__ Zp,
-                                                      double* __restrict__ qp, double* __restrict__ lpo, const Ctl* ctl,
-                                                      TargetDev tg, uint16_t* __restrict__ op_hi,
+                                                      double* __restrict__ qpart, double* __restrict__ lpart,
+                                                      const Ctl* ctl, TargetDev tg, uint16_t* __restrict__ op_hi,
                                                       uint16_t* __restrict__ op_lo, int ldk) {
     __shared__ double sh[32];
-    const int p = blockIdx.x;
+    const int p = blockIdx.x, c = blockIdx.y;
+    const int i0 = c * CHUNK, i1 = min(d, i0 + CHUNK);
     const T rho = (T)ctl->rho, ba = (T)ctl->ba;
     const T* x = X + (size_t)p * d;
     const T* z = Z + (size_t)p * d;
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
     T* xp = Xp + (size_t)p * d;
     T* zp = Zp + (size_t)p * d;
     double qacc = 0.0, lacc = 0.0;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         T xr = xref[i];
         T v = xr + rho * (x[i] - xr) + xi[i];
         T wz;
@@ -121,9 +126,9 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
     qacc = block_sum(qacc, sh);
     lacc = block_sum(lacc, sh);
     if (threadIdx.x == 0) {
-        if (tg.kind == TK_BANANA) lacc += banana_head(tg, (double)xp[0], d > 1 ? (double)xp[1] : 0.0);
-        qp[p] = 0.5 * qacc * ctl->inv_infl2;
-        lpo[p] = lacc;
+        if (tg.kind == TK_BANANA && c == 0) lacc += banana_head(tg, (double)xp[0], d > 1 ? (double)xp[1] : 0.0);
+        qpart[(size_t)c * P + p] = qacc;
+        lpart[(size_t)c * P + p] = lacc;
     }
 }
 
@@ -168,9 +173,92 @@ __global__ void sum_lp_kernel(int P, const double* __restrict__ lpo, const doubl
 }
 
 // ---------------------------------------------------------------------------------------------------
-// Metropolis-Hastings test of Algorithm 1 and the select / record step.
+// Metropolis-Hastings test of Algorithm 1 (finish kernels) and the select / record step.
+struct TraceDev {
+    double *lp, *q, *qc, *loga;
+    int8_t* acc;
+    int64_t steps;
+};
+
+// Metropolis-Hastings test of Algorithm 1 for chain p, given log pi(x*) and q(x*):
 //   log a = log pi(x*) + q(x*) - log pi(x) - q(x);  accept iff log u < log a, u = Philox uniform (tag U).
-// Records x_{n+1} - c (c the interval's centring point) for the moment fold, and per-chain interval sums.
+// Updates lp, q and the counters; records the decision for the select step.
+__device__ __forceinline__ void decide(int p, int P, Key key, int64_t t, double lpp, double qpp, double* lp, double* q,
+                                       int8_t* accf, Ctl* ctl, const TraceDev& tr) {
+    const double lpc = lp[p], qc = q[p];
+    const double loga = lpp - lpc + qpp - qc;
+    const bool finite = isfinite(lpp) && isfinite(qpp);
+    const double u = uniform53(key, t, (uint32_t)p, TAG_U);
+    const int a = finite && (log(u) < loga);
+    if (t < tr.steps) {
+        size_t k = (size_t)t * P + p;
+        tr.lp[k] = lpp; tr.q[k] = qpp; tr.qc[k] = qc; tr.loga[k] = loga; tr.acc[k] = (int8_t)a;
+    }
+    if (a) {
+        lp[p] = lpp;
+        q[p] = qpp;
+        atomicAdd(&ctl->acc_block, 1ull);
+    }
+    if (!finite) atomicAdd(&ctl->nonfinite, 1ull);
+    accf[p] = (int8_t)a;
+}
+
+// One thread per chain: log pi(x*) = O(d) partials + linear-map partials (FP64 GEMM epilogue), or an
+// externally evaluated value; q(x*) from the proposal's partials; then the decision.
+__global__ void finish_kernel(int P, int nchunk, Key key, int64_t t, const double* __restrict__ qpart,
+                              const double* __restrict__ lpart, const double* __restrict__ partial, int nparts,
+                              const double* __restrict__ ext, double inv_infl2, double* lp, double* q, int8_t* accf,
+                              Ctl* ctl, TraceDev tr) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double lpp = 0.0, qs = 0.0;
+    for (int c = 0; c < nchunk; ++c) qs += qpart[(size_t)c * P + p];
+    if (ext) {
+        lpp = ext[p];
+    } else {
+        for (int c = 0; c < nchunk; ++c) lpp += lpart[(size_t)c * P + p];
+        for (int m = 0; m < nparts; ++m) lpp += partial[(size_t)m * P + p];
+    }
+    decide(p, P, key, t, lpp, 0.5 * qs * inv_infl2, lp, q, accf, ctl, tr);
+}
+
+// One block per chain, for a linear-map target computed as split-K FP32 partial products ws[s][p][m]
+// (m < d_y): u_m = sum_s ws (fixed order), log-likelihood -(y_m - tanh u_m)^2 inv2s2 or -u_m^2 / 2, summed
+// in FP64; then the O(d) partials, q(x*) and the decision.
+__global__ void __launch_bounds__(256) finish_linear_kernel(int P, int dy, int nsplit, const float* __restrict__ ws,
+                                                             const double* __restrict__ y, double inv2s2, int tanh_mode,
+                                                             int nchunk, Key key, int64_t t,
+                                                             const double* __restrict__ qpart,
+                                                             const double* __restrict__ lpart, double inv_infl2,
+                                                             double* lp, double* q, int8_t* accf, Ctl* ctl,
+                                                             TraceDev tr) {
+    __shared__ double sh[32];
+    const int p = blockIdx.x;
+    const size_t plane = (size_t)P * dy;
+    double acc = 0.0;
+    for (int m = threadIdx.x; m < dy; m += blockDim.x) {
+        float u = 0.f;
+        for (int s = 0; s < nsplit; ++s) u += ws[s * plane + (size_t)p * dy + m];
+        if (tanh_mode) {
+            double r = y[m] - (double)tanhf(u);
+            acc -= r * r * inv2s2;
+        } else {
+            acc -= 0.5 * (double)u * (double)u;
+        }
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        double qs = 0.0;
+        for (int c = 0; c < nchunk; ++c) {
+            qs += qpart[(size_t)c * P + p];
+            acc += lpart[(size_t)c * P + p];
+        }
+        decide(p, P, key, t, acc, 0.5 * qs * inv_infl2, lp, q, accf, ctl, tr);
+    }
+}
+
+// Select / record, grid (P, chunks): x, z <- x*, z* for accepted chains; the centred post-step state
+// x_{n+1} - c goes to the interval record (moment fold) and to the per-chain interval sums.
 template <typename T, typename HT>
 __device__ __forceinline__ HT to_hist(T v);
 template <>
@@ -178,51 +266,22 @@ __device__ __forceinline__ double to_hist<double, double>(double v) { return v; 
 template <>
 __device__ __forceinline__ float to_hist<float, float>(float v) { return v; }
 
-struct TraceDev {
-    double *lp, *q, *qc, *loga;
-    int8_t* acc;
-    int64_t steps;
-};
-
 template <typename T, typename HT>
-__global__ void __launch_bounds__(256) accept_kernel(int d, int P, Key key, int64_t t, T* __restrict__ X, T* __restrict__ Z,
-                                                     const T* __restrict__ Xp, const T* __restrict__ Zp,
-                                                     double* __restrict__ lp, double* __restrict__ q,
-                                                     const double* __restrict__ lpp_in, const double* __restrict__ qp,
-                                                     Ctl* ctl, HT* __restrict__ hist, int ldh, const T* __restrict__ cen,
-                                                     double* __restrict__ bsum, double* __restrict__ lpsum,
-                                                     TraceDev tr) {
-    __shared__ int s_acc;
-    __shared__ double s_lp;
-    const int p = blockIdx.x;
-    if (threadIdx.x == 0) {
-        double lpp = lpp_in[p], qpp = qp[p], lpc = lp[p], qc = q[p];
-        double loga = lpp - lpc + qpp - qc;
-        bool finite = isfinite(lpp) && isfinite(qpp);
-        double u = uniform53(key, t, (uint32_t)p, TAG_U);
-        int a = finite && (log(u) < loga);
-        if (t < tr.steps) {
-            size_t k = (size_t)t * P + p;
-            tr.lp[k] = lpp; tr.q[k] = qpp; tr.qc[k] = qc; tr.loga[k] = loga; tr.acc[k] = (int8_t)a;
-        }
-        if (a) {
-            lp[p] = lpp;
-            q[p] = qpp;
-            atomicAdd(&ctl->acc_block, 1ull);
-        }
-        if (!finite) atomicAdd(&ctl->nonfinite, 1ull);
-        s_acc = a;
-        s_lp = a ? lpp : lpc;
-    }
-    __syncthreads();
-    const int a = s_acc;
+__global__ void __launch_bounds__(256) select_kernel(int d, const int8_t* __restrict__ accf, T* __restrict__ X,
+                                                     T* __restrict__ Z, const T* __restrict__ Xp,
+                                                     const T* __restrict__ Zp, HT* __restrict__ hist, int ldh,
+                                                     const T* __restrict__ cen, double* __restrict__ bsum,
+                                                     double* __restrict__ lpsum, const double* __restrict__ lp) {
+    const int p = blockIdx.x, c = blockIdx.y;
+    const int i0 = c * CHUNK, i1 = min(d, i0 + CHUNK);
+    const int a = accf[p];
     T* x = X + (size_t)p * d;
     T* z = Z + (size_t)p * d;
     const T* xp = Xp + (size_t)p * d;
     const T* zp = Zp + (size_t)p * d;
     HT* h = hist ? hist + (size_t)p * ldh : nullptr;
     double* bs = bsum ? bsum + (size_t)p * d : nullptr;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         T v = a ? xp[i] : x[i];
         if (a) {
             x[i] = v;
@@ -231,7 +290,7 @@ __global__ void __launch_bounds__(256) accept_kernel(int d, int P, Key key, int6
         if (h) h[i] = to_hist<T, HT>(v - cen[i]);
         if (bs) bs[i] += (double)v;
     }
-    if (lpsum && threadIdx.x == 0) lpsum[p] += s_lp;
+    if (lpsum && c == 0 && threadIdx.x == 0) lpsum[p] += lp[p];
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -262,6 +321,19 @@ __global__ void fold_prep_kernel(int d, int nparts, const double* __restrict__ p
     for (int c = 0; c < nparts; ++c) v += part[(size_t)c * d + i];
     s[i] = v;
     delta[i] = (cen64[i] + v * inb) - mean[i];
+}
+
+// s16[i] = sum over the interval's samples of the BF16-rounded centred records (row i of the transposed
+// record): the sums of exactly the values the tensor-core SYRK multiplies, so that G - s16 s16^T / nb is
+// the scatter matrix of those values (positive semi-definite up to the FP32 accumulation).
+__global__ void __launch_bounds__(256) rowsum_bf16_kernel(const uint16_t* __restrict__ HT_, int ldt, int rows,
+                                                          double* __restrict__ s16) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x;
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) acc += (double)bf16_bits_to_f32(HT_[(size_t)i * ldt + r]);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) s16[i] = acc;
 }
 
 // mean += delta nb / (n + nb); the next interval is centred at the new mean (cen64 exact copy of cenT).

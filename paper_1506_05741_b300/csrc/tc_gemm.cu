@@ -12,6 +12,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -105,7 +106,7 @@ template <int BN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const __grid_constant__ CUtensorMap tmB2, int M, int N, int nkb,
-                                                         int a_lower, int has_b2, TcEpi epi, int* status) {
+                                                         int a_lower, int has_b2, int kb_split, TcEpi epi, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
@@ -122,6 +123,13 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     if (epi.mode == TC_FOLD && n0 + BN - 1 < m0) return;  // every (n, m) of the tile has n < m
     int kb_end = nkb;
     if (a_lower) kb_end = min(nkb, (m0 + TC_BM + TC_BK - 1) / TC_BK);
+    // split K (grid z): this CTA sums K blocks [kb_begin, kb_end) into its own partial plane
+    int kb_begin = 0;
+    if (kb_split > 0) {
+        kb_begin = blockIdx.z * kb_split;
+        kb_end = min(kb_end, kb_begin + kb_split);
+    }
+    const int nk = max(kb_end - kb_begin, 0);   // the launcher guarantees nk >= 1
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -147,16 +155,17 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     if (warp == 0 && lane == 0) {
         // TMA producer
         int issued = 0;
-        for (int kb = 0; kb < kb_end; ++kb) {
-            const int s = kb % TC_STAGES;
-            if (kb >= TC_STAGES && !mbar_wait(smem_u32(&empty[s]), ((kb / TC_STAGES) & 1) ^ 1, abort_flag)) break;
+        for (int it = 0; it < nk; ++it) {
+            const int kb = kb_begin + it;
+            const int s = it % TC_STAGES;
+            if (it >= TC_STAGES && !mbar_wait(smem_u32(&empty[s]), ((it / TC_STAGES) & 1) ^ 1, abort_flag)) break;
             uint8_t* st = smem + s * stage_bytes;
             const uint32_t fb = smem_u32(&full[s]);
             mbar_expect_tx(fb, stage_bytes);
             tma_load_2d(smem_u32(st), &tmA, fb, kb * TC_BK, m0);
             tma_load_2d(smem_u32(st + A_BYTES), &tmB, fb, kb * TC_BK, n0);
             if (has_b2) tma_load_2d(smem_u32(st + A_BYTES + B_BYTES), &tmB2, fb, kb * TC_BK, n0);
-            issued = kb + 1;
+            issued = it + 1;
         }
         if (*abort_flag) {
             // drain: every issued stage must land before the CTA may exit
@@ -169,16 +178,16 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         constexpr uint32_t idesc = idesc_bf16(BN);
-        for (int kb = 0; kb < kb_end; ++kb) {
-            const int s = kb % TC_STAGES;
-            if (!mbar_wait(smem_u32(&full[s]), (kb / TC_STAGES) & 1, abort_flag)) break;
+        for (int it = 0; it < nk; ++it) {
+            const int s = it % TC_STAGES;
+            if (!mbar_wait(smem_u32(&full[s]), (it / TC_STAGES) & 1, abort_flag)) break;
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + s * stage_bytes);
             const uint32_t sb = sa + A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
                 const uint64_t ad = sdesc_sw128(sa + kk * 32);
-                umma_bf16(tmem, ad, sdesc_sw128(sb + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+                umma_bf16(tmem, ad, sdesc_sw128(sb + kk * 32), idesc, (it | kk) ? 1u : 0u);
                 if (has_b2) umma_bf16(tmem, ad, sdesc_sw128(sb + B_BYTES + kk * 32), idesc, 1u);
             }
             umma_commit(smem_u32(&empty[s]));
@@ -237,7 +246,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                         if (n >= N) continue;
                         const float v = __uint_as_float(r[j]);
                         if (epi.mode == TC_STORE) {
-                            epi.D[(size_t)n * epi.ldd + m] = scale * v;
+                            epi.D[(size_t)blockIdx.z * epi.split_stride + (size_t)n * epi.ldd + m] = scale * v;
                         } else if (n >= m) {
                             double add = (double)v - epi.s[n] * epi.s[m] * epi.inb + epi.delta[n] * epi.delta[m] * epi.w;
                             epi.M2[(size_t)n * epi.ldm + m] += add;
@@ -300,7 +309,7 @@ static bool make_map(CUtensorMap* map, const void* ptr, int rows, int ld, int bo
 
 template <int BN>
 static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
-                             int ldb, int a_lower, const TcEpi& epi, int* status, cudaStream_t st) {
+                             int ldb, int a_lower, const TcEpi& epi, int* status, cudaStream_t st, int splits = 1) {
     CUtensorMap mA, mB, mB2;
     if (!make_map(&mA, A, M, lda, TC_BM) || !make_map(&mB, B, N, ldb, BN) ||
         !make_map(&mB2, B2 ? B2 : B, N, ldb, BN))
@@ -316,8 +325,16 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN);
-    { tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, M, N, K / TC_BK, a_lower, has_b2, epi, status); count_launch(); }
+    const int nkb = K / TC_BK;
+    int kb_split = 0;
+    if (splits > 1) {
+        kb_split = (nkb + splits - 1) / splits;
+        splits = (nkb + kb_split - 1) / kb_split;   // every split gets at least one K block
+    } else {
+        splits = 1;
+    }
+    dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN, splits);
+    { tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, M, N, nkb, a_lower, has_b2, kb_split, epi, status); count_launch(); }
     return cudaGetLastError();
 }
 
@@ -327,6 +344,21 @@ cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const 
     if (K <= 0 || K % TC_BK || lda % TC_BK || ldb % TC_BK || K > lda || K > ldb) return cudaErrorInvalidValue;
     if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)(B2 ? B2 : B)) & 15) return cudaErrorInvalidValue;
     return launch_bn<128>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status_dev, st);
+}
+
+// Split-K form: K blocks divided over `splits` CTAs per tile; each writes its FP32 partial product to
+// D + z * split_stride (TC_STORE only, no triangular skip). Returns the number of partial planes in *used.
+cudaError_t tc_gemm_bf16_splitk(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
+                                int ldb, int splits, const TcEpi& epi, int* status_dev, cudaStream_t st, int* used) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (epi.mode != TC_STORE || splits < 1) return cudaErrorInvalidValue;
+    if (K <= 0 || K % TC_BK || lda % TC_BK || ldb % TC_BK || K > lda || K > ldb) return cudaErrorInvalidValue;
+    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)(B2 ? B2 : B)) & 15) return cudaErrorInvalidValue;
+    const int nkb = K / TC_BK;
+    splits = std::min(splits, nkb);
+    const int per = (nkb + splits - 1) / splits;
+    *used = (nkb + per - 1) / per;
+    return launch_bn<128>(M, N, K, A, lda, B, B2, ldb, 0, epi, status_dev, st, *used);
 }
 
 // ---------------------------------------------------------------------------------------------------- transpose

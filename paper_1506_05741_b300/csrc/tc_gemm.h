@@ -30,12 +30,17 @@ struct TcEpi {
     const double* s;
     const double* delta;
     double inb, w;
+    size_t split_stride;   // TC_STORE with split K: distance between partial planes (elements)
 };
 
 // a_lower: A is lower triangular (A[m][k] = 0 for k > m), K blocks past the m-tile are skipped.
 // status_dev: receives a non-zero code if a bounded wait inside the kernel expired.
 cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
                          int ldb, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st);
+
+// Split-K TC_STORE: grid z = splits, K blocks divided evenly; *used receives the number of partial planes.
+cudaError_t tc_gemm_bf16_splitk(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
+                                int ldb, int splits, const TcEpi& epi, int* status_dev, cudaStream_t st, int* used);
 
 // out[c*ldo + r] = bf16(in[r*ldi + c]) (round to nearest even) for r < rows, c < cols; out[c*ldo + r] = 0 for
 // rows <= r < ldo, so the K padding of the transposed operand is zero

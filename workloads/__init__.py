@@ -132,3 +132,11 @@ def spd_matrix(d: int, seed: int, cond: float = 1e3) -> np.ndarray:
     Q, _ = np.linalg.qr(rng.standard_normal((d, d)))
     ev = np.logspace(0, -math.log10(cond), d)
     return (Q * ev) @ Q.T
+
+
+def mlp_init(d: int, h1: int = 512, h2: int = 512, seed: int = 4) -> dict:
+    """Seeded initial weights of the surrogate network (He-scaled normal, zero biases), FP64."""
+    rng = np.random.default_rng(seed)
+    return {"W1": rng.standard_normal((h1, d)) * math.sqrt(2.0 / d), "b1": np.zeros(h1),
+            "W2": rng.standard_normal((h2, h1)) * math.sqrt(2.0 / h1), "b2": np.zeros(h2),
+            "w3": rng.standard_normal(h2) * math.sqrt(1.0 / h2), "b3": np.zeros(())}
