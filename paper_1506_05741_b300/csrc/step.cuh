@@ -4,6 +4,8 @@
 // target's linear map are BF16 and the states FP32). One thread block per chain for the O(d) work; the
 // products (noise, linear-map targets, moments) are separate GEMM launches.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace diam {
@@ -105,7 +107,49 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
     T* xp = Xp + (size_t)p * d;
     T* zp = Zp + (size_t)p * d;
     double qacc = 0.0, lacc = 0.0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    bool vec_done = false;
+    if constexpr (std::is_same<T, float>::value && std::is_same<WT, uint16_t>::value) {
+        // BF16 mode, d a multiple of 4: four entries per thread through 16-byte loads; the per-thread
+        // partial sums of a handful of terms stay in FP32 (B300's FP64 rate is ~1/60 of its FP32 rate)
+        if ((d & 3) == 0) {
+            float qf = 0.f, lf = 0.f;
+            const bool prior = tg.kind == TK_DIAG || tg.kind == TK_TANH || tg.kind == TK_BANANA;
+            for (int i = i0 + 4 * threadIdx.x; i < i1; i += 4 * blockDim.x) {
+                const float4 xr = *reinterpret_cast<const float4*>(xref + i);
+                const float4 xv = *reinterpret_cast<const float4*>(x + i);
+                const float4 zv = *reinterpret_cast<const float4*>(z + i);
+                const float4 xiv = *reinterpret_cast<const float4*>(xi + i);
+                const uint2 wb = *reinterpret_cast<const uint2*>(w + i);
+                const float wv[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
+                                     bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
+                const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ra[4] = {xr.x, xr.y, xr.z, xr.w};
+                const float za[4] = {zv.x, zv.y, zv.z, zv.w}, ia[4] = {xiv.x, xiv.y, xiv.z, xiv.w};
+                float vo[4], uo[4];
+                uint16_t ho[4], lo[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    vo[k] = ra[k] + rho * (xa[k] - ra[k]) + ia[k];
+                    uo[k] = rho * za[k] + ba * wv[k];
+                    qf += uo[k] * uo[k];
+                    if (prior && (tg.kind != TK_BANANA || i + k >= 2)) lf -= 0.5f * vo[k] * vo[k] * (float)tg.inv_lam[i + k];
+                    ho[k] = f32_to_bf16_bits(vo[k]);
+                    lo[k] = f32_to_bf16_bits(vo[k] - bf16_bits_to_f32(ho[k]));
+                }
+                *reinterpret_cast<float4*>(xp + i) = make_float4(vo[0], vo[1], vo[2], vo[3]);
+                *reinterpret_cast<float4*>(zp + i) = make_float4(uo[0], uo[1], uo[2], uo[3]);
+                if (op_hi) {
+                    *reinterpret_cast<uint2*>(op_hi + (size_t)p * ldk + i) =
+                        make_uint2((uint32_t)ho[0] | ((uint32_t)ho[1] << 16), (uint32_t)ho[2] | ((uint32_t)ho[3] << 16));
+                    *reinterpret_cast<uint2*>(op_lo + (size_t)p * ldk + i) =
+                        make_uint2((uint32_t)lo[0] | ((uint32_t)lo[1] << 16), (uint32_t)lo[2] | ((uint32_t)lo[3] << 16));
+                }
+            }
+            qacc = (double)qf;
+            lacc = (double)lf;
+            vec_done = true;
+        }
+    }
+    for (int i = i0 + threadIdx.x; !vec_done && i < i1; i += blockDim.x) {
         T xr = xref[i];
         T v = xr + rho * (x[i] - xr) + xi[i];
         T wz;
@@ -281,6 +325,21 @@ __global__ void __launch_bounds__(256) select_kernel(int d, const int8_t* __rest
     const T* zp = Zp + (size_t)p * d;
     HT* h = hist ? hist + (size_t)p * ldh : nullptr;
     double* bs = bsum ? bsum + (size_t)p * d : nullptr;
+    if constexpr (std::is_same<T, float>::value && std::is_same<HT, float>::value) {
+        if ((d & 3) == 0 && (ldh & 3) == 0 && !bs && h) {
+            for (int i = i0 + 4 * threadIdx.x; i < i1; i += 4 * blockDim.x) {
+                float4 v = a ? *reinterpret_cast<const float4*>(xp + i) : *reinterpret_cast<const float4*>(x + i);
+                if (a) {
+                    *reinterpret_cast<float4*>(x + i) = v;
+                    *reinterpret_cast<float4*>(z + i) = *reinterpret_cast<const float4*>(zp + i);
+                }
+                const float4 cv = *reinterpret_cast<const float4*>(cen + i);
+                *reinterpret_cast<float4*>(h + i) = make_float4(v.x - cv.x, v.y - cv.y, v.z - cv.z, v.w - cv.w);
+            }
+            if (lpsum && c == 0 && threadIdx.x == 0) lpsum[p] += lp[p];
+            return;
+        }
+    }
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         T v = a ? xp[i] : x[i];
         if (a) {
