@@ -183,13 +183,75 @@ DIAM_API diam_status diam_get_block_sums(diam_ctx* ctx, double* xsum, double* lp
 DIAM_API diam_status diam_save(diam_ctx* ctx, void* buf, size_t* size);
 DIAM_API diam_status diam_load(diam_ctx* ctx, const void* buf, size_t size);
 
+/* ---------------------------------------------------------------------------------------------------
+ * Delayed acceptance with a learned surrogate (not in the paper; two-stage Metropolis-Hastings of
+ * Christen & Fox, 2005). A small MLP s(x) ~ log pi(x) (d -> h1 -> h2 -> 1, GELU, BF16 weights, FP32
+ * accumulation on the tensor cores) screens every proposal first:
+ *   stage 1: accept with probability min(1, exp(s(x*) - s(x) + q(x*) - q(x)))       (uniform tag 3)
+ *   stage 2: for the survivors only, log pi(x*) is evaluated and the move is accepted with probability
+ *            min(1, exp(log pi(x*) - log pi(x) - s(x*) + s(x)))                     (uniform tag 1)
+ * so the chain still targets pi exactly. The network is trained on the GPU (own forward, backward and
+ * Adam kernels) on a ring buffer of exactly evaluated pairs (x*, log pi(x*)) from the chains; after each
+ * training its RMSE on held-out pairs decides whether stage 1 is used; when it exceeds rmse_bound (or
+ * before the first training) every proposal goes straight to the exact test (plain DIAM). Needs
+ * prec = BF16 and P <= 1024. */
+typedef struct {
+    int32_t h1, h2;             /* hidden widths (multiples of 128) */
+    int32_t retrain_every;      /* trainings every retrain_every synchronisations (of M intervals) */
+    int32_t ring;               /* ring-buffer capacity in pairs */
+    int32_t train_steps;        /* Adam steps per training */
+    int32_t batch;              /* minibatch size (multiple of 128) */
+    int32_t first_train_min;    /* pairs needed before the first training (at an interval end) */
+    int32_t reserved;
+    double lr, beta1, beta2, adam_eps;
+    double rmse_bound;          /* held-out RMSE (nats) above which stage 1 is switched off */
+    uint64_t seed;              /* minibatch selection stream */
+} diam_da_config;
+
+typedef struct {
+    int64_t trainings;          /* trainings done */
+    int64_t stage1_tested;      /* proposals screened by the surrogate */
+    int64_t stage1_passed;      /* of those, passed to the exact test */
+    int64_t exact_evals;        /* exact log-density evaluations (all proposals when stage 1 is off) */
+    int64_t ring_filled;        /* pairs in the ring */
+    double last_rmse;           /* held-out RMSE of the last training (nats) */
+    int32_t active;             /* 1: stage 1 in use */
+    int32_t pad;
+} diam_da_stats;
+
+/* Defaults: h1 = h2 = 512, retrain_every = 20, ring = 200000, train_steps = 200, batch = 1024,
+ * first_train_min = 20000, lr = 1e-3, beta1 = 0.9, beta2 = 0.999, adam_eps = 1e-8, rmse_bound = 0.5. */
+DIAM_API diam_status diam_da_config_default(diam_da_config* cfg);
+
+/* Enable delayed acceptance with initial weights (host, FP64, row-major): W1 (h1 x d), b1 (h1),
+ * W2 (h2 x h1), b2 (h2), w3 (h2), b3 (1). */
+DIAM_API diam_status diam_da_enable(diam_ctx* ctx, const diam_da_config* cfg, const double* W1, const double* b1,
+                                    const double* W2, const double* b2, const double* w3, const double* b3);
+
+/* Train now (whatever the schedule) on the ring buffer; returns the held-out RMSE in *rmse. Synchronises. */
+DIAM_API diam_status diam_da_train(diam_ctx* ctx, double* rmse);
+
+DIAM_API diam_status diam_da_get_stats(diam_ctx* ctx, diam_da_stats* stats);
+
+/* One forward + backward pass of the network on a given batch (B rows, multiple of 128; U already
+ * normalised, B x d, FP64 host, rounded to BF16 on upload; targets t in network units), without updating
+ * anything: the loss mean((out - t)^2)/2 and its gradients (FP64 host, same shapes as diam_da_enable's
+ * weights). For checking the training kernels. Synchronises. */
+DIAM_API diam_status diam_da_grad(diam_ctx* ctx, int32_t B, const double* U, const double* t, double* loss,
+                                  double* gW1, double* gb1, double* gW2, double* gb2, double* gw3, double* gb3);
+
+/* Current weights (FP32 masters, widened), same shapes as diam_da_enable's. Synchronises. */
+DIAM_API diam_status diam_da_get_weights(diam_ctx* ctx, double* W1, double* b1, double* W2, double* b2, double* w3,
+                                         double* b3);
+
 /* Phase timings collected while cfg.profile = 1: for each phase, the number of timed launches of its
  * kernels and their summed device time in milliseconds (CUDA events on the context's stream). Phases:
  * 0 noise draw, 1 noise product (batched triangular GEMM), 2 propose, 3 target (linear map + reduction),
  * 4 accept / select / record, 5 moment fold (column sums + SYRK), 6 Cholesky refresh (with its
- * retries), 7 re-whitening solve after a factor change. counts and ms hold DIAM_N_PHASES entries each.
+ * retries), 7 re-whitening solve after a factor change, 8 surrogate screening (stage 1), 9 surrogate
+ * training. counts and ms hold DIAM_N_PHASES entries each.
  * reset = 1 clears the accumulators after reading. Synchronises. */
-#define DIAM_N_PHASES 8
+#define DIAM_N_PHASES 10
 DIAM_API diam_status diam_get_profile(diam_ctx* ctx, int64_t* counts, double* ms, int32_t reset);
 
 DIAM_API void diam_destroy(diam_ctx* ctx);

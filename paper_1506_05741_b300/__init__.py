@@ -42,6 +42,19 @@ class DiamConfig(C.Structure):
                 ("keep_block_sums", C.c_int32), ("profile", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
+class DiamDaConfig(C.Structure):
+    _fields_ = [("h1", C.c_int32), ("h2", C.c_int32), ("retrain_every", C.c_int32), ("ring", C.c_int32),
+                ("train_steps", C.c_int32), ("batch", C.c_int32), ("first_train_min", C.c_int32),
+                ("reserved", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("adam_eps", C.c_double), ("rmse_bound", C.c_double), ("seed", C.c_uint64)]
+
+
+class DiamDaStats(C.Structure):
+    _fields_ = [("trainings", C.c_int64), ("stage1_tested", C.c_int64), ("stage1_passed", C.c_int64),
+                ("exact_evals", C.c_int64), ("ring_filled", C.c_int64), ("last_rmse", C.c_double),
+                ("active", C.c_int32), ("pad", C.c_int32)]
+
+
 class DiamStats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("n", C.c_int64), ("accepted", C.c_int64), ("refreshes", C.c_int64),
                 ("notspd", C.c_int64), ("nonfinite", C.c_int64), ("beta", C.c_double),
@@ -51,7 +64,7 @@ class DiamStats(C.Structure):
 EXPORTS = ["diam_config_default", "diam_init", "diam_run_batch", "diam_sync_moments", "diam_get_moments",
            "diam_export_moments", "diam_get_state", "diam_get_factor", "diam_get_trace", "diam_get_block_sums",
            "diam_save", "diam_load", "diam_get_profile", "diam_destroy", "diam_last_error", "diam_status_string"]
-PHASES = ["noise", "xi_gemm", "propose", "target", "accept", "fold", "refresh", "rewhiten"]
+PHASES = ["noise", "xi_gemm", "propose", "target", "accept", "fold", "refresh", "rewhiten", "screen", "train"]
 
 
 def kernel_launches() -> int:
@@ -89,6 +102,12 @@ def lib():
                 "diam_last_error": (C.c_char_p, [P]),
                 "diam_status_string": (C.c_char_p, [C.c_int]),
                 "diam_kernel_launches": (C.c_uint64, []),
+                "diam_da_config_default": (C.c_int, [P]),
+                "diam_da_enable": (C.c_int, [P, P, P, P, P, P, P, P]),
+                "diam_da_train": (C.c_int, [P, P]),
+                "diam_da_get_stats": (C.c_int, [P, P]),
+                "diam_da_grad": (C.c_int, [P, I32, P, P, P, P, P, P, P, P, P]),
+                "diam_da_get_weights": (C.c_int, [P, P, P, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(l, name)
@@ -131,6 +150,17 @@ def _stream_handle(stream):
     except Exception:  # pragma: no cover
         pass
     return None
+
+
+def da_default_config(**kw) -> dict:
+    cs = DiamDaConfig()
+    lib().diam_da_config_default(C.byref(cs))
+    cfg = {k: getattr(cs, k) for k, _ in DiamDaConfig._fields_ if k != "reserved"}
+    for k, v in kw.items():
+        if k not in cfg:
+            raise KeyError(k)
+        cfg[k] = v
+    return cfg
 
 
 class Sampler:
@@ -259,6 +289,46 @@ class Sampler:
         ms = np.zeros(len(PHASES))
         self._check(self._l.diam_get_profile(self._h, _p(counts), _p(ms), int(reset)), "diam_get_profile")
         return {ph: (int(counts[i]), float(ms[i])) for i, ph in enumerate(PHASES)}
+
+    # ---- delayed acceptance (two-stage MH with an MLP surrogate)
+    def da_enable(self, cfg: dict, weights: dict):
+        cs = DiamDaConfig()
+        for k, v in cfg.items():
+            setattr(cs, k, v)
+        self._da_h = (cfg["h1"], cfg["h2"])
+        w = {k: np.ascontiguousarray(weights[k], np.float64) for k in ("W1", "b1", "W2", "b2", "w3", "b3")}
+        self._check(self._l.diam_da_enable(self._h, C.byref(cs), *[_p(w[k]) for k in ("W1", "b1", "W2", "b2", "w3", "b3")]),
+                    "diam_da_enable")
+
+    def da_train(self) -> float:
+        r = C.c_double()
+        self._check(self._l.diam_da_train(self._h, C.byref(r)), "diam_da_train")
+        return r.value
+
+    def da_stats(self) -> dict:
+        s = DiamDaStats()
+        self._check(self._l.diam_da_get_stats(self._h, C.byref(s)), "diam_da_get_stats")
+        return {k: getattr(s, k) for k, _ in DiamDaStats._fields_ if k != "pad"}
+
+    def da_grad(self, U, t):
+        h1, h2 = self._da_h
+        U = np.ascontiguousarray(U, np.float64)
+        t = np.ascontiguousarray(t, np.float64)
+        B = U.shape[0]
+        out = {"W1": np.zeros((h1, self.d)), "b1": np.zeros(h1), "W2": np.zeros((h2, h1)), "b2": np.zeros(h2),
+               "w3": np.zeros(h2), "b3": np.zeros(1)}
+        loss = C.c_double()
+        self._check(self._l.diam_da_grad(self._h, B, _p(U), _p(t), C.byref(loss),
+                                         *[_p(out[k]) for k in ("W1", "b1", "W2", "b2", "w3", "b3")]), "diam_da_grad")
+        return loss.value, out
+
+    def da_weights(self) -> dict:
+        h1, h2 = self._da_h
+        out = {"W1": np.zeros((h1, self.d)), "b1": np.zeros(h1), "W2": np.zeros((h2, h1)), "b2": np.zeros(h2),
+               "w3": np.zeros(h2), "b3": np.zeros(1)}
+        self._check(self._l.diam_da_get_weights(self._h, *[_p(out[k]) for k in ("W1", "b1", "W2", "b2", "w3", "b3")]),
+                    "diam_da_get_weights")
+        return out
 
     def save(self) -> bytes:
         n = C.c_size_t()

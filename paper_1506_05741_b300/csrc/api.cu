@@ -41,8 +41,11 @@ struct Pending {
 
 }  // namespace
 
+struct DaState;
+
 struct diam_ctx {
     diam_config cfg{};
+    DaState* da = nullptr;   // delayed-acceptance surrogate (diam_da_enable)
     int kind = 0, d = 0, P = 0, nl = 0, dy = 0, ldk = 0;
     bool bf = false;
     int dev = 0;
@@ -96,7 +99,7 @@ struct diam_ctx {
 };
 
 enum : int { PH_NOISE = 0, PH_XI = 1, PH_PROPOSE = 2, PH_TARGET = 3, PH_ACCEPT = 4, PH_FOLD = 5, PH_REFRESH = 6,
-             PH_REWHITEN = 7 };
+             PH_REWHITEN = 7, PH_SCREEN = 8, PH_TRAIN = 9 };
 
 // Start timing a phase; returns the event slot (or -1 when profiling is off).
 static int ph_begin(diam_ctx* c, int phase) {
@@ -226,6 +229,8 @@ static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
     return DIAM_OK;
 }
 
+#include "da_host.cuh"
+
 // z = Lq^{-1}(x - x_ref) and q for every chain (after a factor change); lp = -q for the reference target.
 template <typename T>
 static diam_status rewhiten(diam_ctx* c) {
@@ -335,6 +340,9 @@ static diam_status do_step(diam_ctx* c, int s, int64_t t) {
     } else if (c->kind == TK_DENSE || c->kind == TK_TANH) {
         const double inv2s2 = 1.0 / (2.0 * c->sigma * c->sigma);
         if constexpr (BF) {
+          if (c->da) {
+            CKS(da_step(c, t));
+          } else {
             TcEpi epi{};
             epi.mode = TC_STORE;
             epi.D = c->ws;
@@ -346,6 +354,7 @@ static diam_status do_step(diam_ctx* c, int s, int64_t t) {
             { finish_linear_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y, inv2s2, c->kind == TK_TANH,
                                                             c->nchunk, c->key, t, c->qpart, c->lpart, iw, c->lp, c->q,
                                                             c->accf, c->ctl, c->tr); count_launch(); }
+          }
         } else {
             EpiTargetReduce epi{c->partial, c->y, inv2s2, c->kind == TK_TANH};
             CK((gemm_f64<true, true>(c->dy, P, d, c->Gm, d, (const double*)c->Xp, d, TileRange{0, 0}, epi, c->st)));
@@ -509,6 +518,7 @@ static diam_status block_end(diam_ctx* c, int64_t blk) {
     if (c->acc_refresh >= g.min_samples_refresh && c->n > 0) CKS(refresh(c, blk));
     push_scalars(c);
     CK(cudaGetLastError());
+    if (c->da) CKS(da_after_interval(c));
     return DIAM_OK;
 }
 
@@ -1004,6 +1014,131 @@ diam_status diam_get_profile(diam_ctx* c, int64_t* counts, double* ms, int32_t r
     return DIAM_OK;
 }
 
+diam_status diam_da_config_default(diam_da_config* g) {
+    if (!g) return DIAM_EINVAL;
+    memset(g, 0, sizeof(*g));
+    g->h1 = 512;
+    g->h2 = 512;
+    g->retrain_every = 20;
+    g->ring = 200000;
+    g->train_steps = 200;
+    g->batch = 1024;
+    g->first_train_min = 20000;
+    g->lr = 1e-3;
+    g->beta1 = 0.9;
+    g->beta2 = 0.999;
+    g->adam_eps = 1e-8;
+    g->rmse_bound = 0.5;
+    g->seed = 12345;
+    return DIAM_OK;
+}
+
+diam_status diam_da_enable(diam_ctx* c, const diam_da_config* g, const double* W1, const double* b1, const double* W2,
+                           const double* b2, const double* w3, const double* b3) {
+    CKS(check_usable(c));
+    if (!g || !W1 || !b1 || !W2 || !b2 || !w3 || !b3) return fail(c, DIAM_EINVAL, "diam_da_enable");
+    if (!c->bf || (c->kind != TK_DENSE && c->kind != TK_TANH) || c->P > 1024 || c->da)
+        return fail(c, DIAM_EINVAL, "diam_da_enable", "needs BF16 mode, a linear-map target, P <= 1024, once");
+    if (g->h1 <= 0 || g->h2 <= 0 || g->h1 % 128 || g->h2 % 128 || g->batch <= 0 || g->batch % 128 || g->ring < 100 ||
+        g->train_steps < 0 || g->retrain_every <= 0)
+        return fail(c, DIAM_EINVAL, "diam_da_enable", "bad surrogate configuration");
+    return da_alloc(c, g, W1, b1, W2, b2, w3, b3);
+}
+
+diam_status diam_da_train(diam_ctx* c, double* rmse) {
+    CKS(check_usable(c));
+    if (!c->da) return fail(c, DIAM_EINVAL, "diam_da_train", "delayed acceptance not enabled");
+    return da_train_now(c, rmse);
+}
+
+diam_status diam_da_get_stats(diam_ctx* c, diam_da_stats* s) {
+    CKS(check_usable(c));
+    if (!c->da || !s) return fail(c, DIAM_EINVAL, "diam_da_get_stats");
+    CKS(sync_and_check(c));
+    DaCounters hc{};
+    CK(cudaMemcpy(&hc, c->da->cnt, sizeof(hc), cudaMemcpyDeviceToHost));
+    s->trainings = c->da->trainings;
+    s->stage1_tested = (int64_t)hc.tested;
+    s->stage1_passed = (int64_t)hc.passed;
+    s->exact_evals = (int64_t)hc.exact;
+    s->ring_filled = hc.filled;
+    s->last_rmse = c->da->last_rmse;
+    s->active = c->da->active ? 1 : 0;
+    s->pad = 0;
+    return DIAM_OK;
+}
+
+diam_status diam_da_get_weights(diam_ctx* c, double* W1, double* b1, double* W2, double* b2, double* w3, double* b3) {
+    CKS(check_usable(c));
+    if (!c->da) return fail(c, DIAM_EINVAL, "diam_da_get_weights");
+    CKS(sync_and_check(c));
+    DaState* a = c->da;
+    auto down = [&](double* dst, const float* src, size_t n) -> diam_status {
+        if (!dst) return DIAM_OK;
+        std::vector<float> t(n);
+        CK(cudaMemcpy(t.data(), src, sizeof(float) * n, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) dst[i] = t[i];
+        return DIAM_OK;
+    };
+    CKS(down(W1, a->W1, (size_t)a->h1 * c->d)); CKS(down(b1, a->b1, a->h1)); CKS(down(W2, a->W2, (size_t)a->h2 * a->h1));
+    CKS(down(b2, a->b2, a->h2)); CKS(down(w3, a->w3, a->h2)); CKS(down(b3, a->b3, 1));
+    return DIAM_OK;
+}
+
+diam_status diam_da_grad(diam_ctx* c, int32_t B, const double* U, const double* t, double* loss, double* gW1,
+                         double* gb1, double* gW2, double* gb2, double* gw3, double* gb3) {
+    CKS(check_usable(c));
+    if (!c->da || !U || !t || B <= 0 || B % 128 || B > c->da->B) return fail(c, DIAM_EINVAL, "diam_da_grad");
+    DaState* a = c->da;
+    const int d = c->d, ldk = c->ldk, h1 = a->h1, h2 = a->h2;
+    std::vector<uint16_t> xb((size_t)B * ldk, 0);
+    for (int b = 0; b < B; ++b)
+        for (int i = 0; i < d; ++i) {
+            float f = (float)round_bf16(U[(size_t)b * d + i]);
+            uint32_t bits;
+            memcpy(&bits, &f, 4);
+            xb[(size_t)b * ldk + i] = (uint16_t)(bits >> 16);
+        }
+    std::vector<float> tf(t, t + B);
+    CK(cudaMemcpy(a->Xb, xb.data(), sizeof(uint16_t) * xb.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(a->tb, tf.data(), sizeof(float) * B, cudaMemcpyHostToDevice));
+    const int saveB = a->B;
+    a->B = B;
+    diam_status s = da_backward(c);
+    a->B = saveB;
+    CKS(s);
+    CKS(sync_and_check(c));
+    std::vector<double> lpart(B);
+    CK(cudaMemcpy(lpart.data(), a->loss_parts, sizeof(double) * B, cudaMemcpyDeviceToHost));
+    if (loss) {
+        double L = 0.0;
+        for (double v : lpart) L += v;
+        *loss = L;
+    }
+    std::vector<float> g;
+    if (gW1) {
+        g.resize((size_t)ldk * h1);
+        CK(cudaMemcpy(g.data(), a->gW1T, sizeof(float) * g.size(), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < h1; ++i)
+            for (int k = 0; k < d; ++k) gW1[(size_t)i * d + k] = g[(size_t)k * h1 + i];
+    }
+    if (gW2) {
+        g.resize((size_t)h1 * h2);
+        CK(cudaMemcpy(g.data(), a->gW2T, sizeof(float) * g.size(), cudaMemcpyDeviceToHost));
+        for (int o = 0; o < h2; ++o)
+            for (int i = 0; i < h1; ++i) gW2[(size_t)o * h1 + i] = g[(size_t)i * h2 + o];
+    }
+    auto down = [&](double* dst, const float* src, size_t n) -> diam_status {
+        if (!dst) return DIAM_OK;
+        std::vector<float> tt(n);
+        CK(cudaMemcpy(tt.data(), src, sizeof(float) * n, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) dst[i] = tt[i];
+        return DIAM_OK;
+    };
+    CKS(down(gb1, a->gb1, h1)); CKS(down(gb2, a->gb2, h2)); CKS(down(gw3, a->gw3, h2)); CKS(down(gb3, a->gb3, 1));
+    return DIAM_OK;
+}
+
 void diam_destroy(diam_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
@@ -1014,6 +1149,7 @@ void diam_destroy(diam_ctx* c) {
     }
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    delete c->da;
     delete c;
 }
 

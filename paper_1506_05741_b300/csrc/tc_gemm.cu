@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     const int mt = blockIdx.x, nt = blockIdx.y;
     const int m0 = mt * TC_BM, n0 = nt * BN;
     if (epi.mode == TC_FOLD && n0 + BN - 1 < m0) return;  // every (n, m) of the tile has n < m
+    if (epi.n_dev) N = min(N, *epi.n_dev);                // device-side row count of B (compacted rows)
+    if (n0 >= N) return;                                  // uniform per CTA, before any barrier or TMEM use
     int kb_end = nkb;
     if (a_lower) kb_end = min(nkb, (m0 + TC_BM + TC_BK - 1) / TC_BK);
     // split K (grid z): this CTA sums K blocks [kb_begin, kb_end) into its own partial plane
@@ -247,6 +249,11 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                         const float v = __uint_as_float(r[j]);
                         if (epi.mode == TC_STORE) {
                             epi.D[(size_t)blockIdx.z * epi.split_stride + (size_t)n * epi.ldd + m] = scale * v;
+                        } else if (epi.mode == TC_GELU) {
+                            const float zf = v + epi.bias[m];
+                            if (epi.Zout) epi.Zout[(size_t)n * epi.ldz + m] = zf;
+                            const float g = 0.5f * zf * (1.0f + erff(zf * 0.70710678118654752f));
+                            epi.Hout[(size_t)n * epi.ldo + m] = f32_to_bf16_bits(g);
                         } else if (n >= m) {
                             double add = (double)v - epi.s[n] * epi.s[m] * epi.inb + epi.delta[n] * epi.delta[m] * epi.w;
                             epi.M2[(size_t)n * epi.ldm + m] += add;

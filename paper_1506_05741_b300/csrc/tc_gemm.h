@@ -13,7 +13,8 @@ namespace diam {
 enum TcMode : int {
     TC_STORE = 0,   // D[n*ldd + m] = scale * acc (FP32), scale = *scale_dev
     TC_TARGET = 1,  // partial[m_tile * N + n] = sum_m f(acc(n, m)): -(y_m - tanh acc)^2 inv2s2 or -acc^2/2
-    TC_FOLD = 2     // lower triangle n >= m: M2[n*ldm + m] += acc - s_n s_m inb + delta_n delta_m w
+    TC_FOLD = 2,    // lower triangle n >= m: M2[n*ldm + m] += acc - s_n s_m inb + delta_n delta_m w
+    TC_GELU = 3     // z = acc + bias[m]: Zout[n*ldz + m] = z (FP32, optional), Hout[n*ldo + m] = bf16(GELU(z))
 };
 
 struct TcEpi {
@@ -31,6 +32,12 @@ struct TcEpi {
     const double* delta;
     double inb, w;
     size_t split_stride;   // TC_STORE with split K: distance between partial planes (elements)
+    uint16_t* Hout;        // TC_GELU
+    int ldo;
+    float* Zout;
+    int ldz;
+    const float* bias;
+    const int* n_dev;      // optional: the product uses only the first *n_dev rows of B (n-tiles past it exit)
 };
 
 // a_lower: A is lower triangular (A[m][k] = 0 for k > m), K blocks past the m-tile are skipped.
