@@ -213,7 +213,9 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    stream = torch.cuda.current_stream()
+    # one non-default stream for the sampler, its CUDA events and its graph replays
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     pk, pk_src = peaks()
 
     # ---- main timed region: BF16 path

@@ -110,7 +110,7 @@ typedef struct {
     double beta_factor;     /* multiplicative beta change (the paper leaves it open; default 1.1) */
     double beta_min, beta_max;
     double eps_jitter;      /* refresh factors chol(C_n + eps diag(C_n)), eps x100 per retry (3 retries);
-                               BF16 mode starts at max(eps_jitter, 1e-6): its C_n is accumulated in FP32 */
+                               BF16 mode starts at max(eps_jitter, 1e-5): its C_n is accumulated in FP32 */
     int64_t min_samples_refresh;  /* refresh only after this many accepted moves (< 0: d + 1) */
     int64_t burnin;         /* n_0: steps kept out of the moments (footnote to Algorithm 1) */
     int32_t refresh_delay;  /* the factor built at the end of interval k is used from interval k+1+delay */
@@ -120,7 +120,8 @@ typedef struct {
     int32_t trace_steps;    /* keep a per-step, per-chain trace for the first trace_steps steps (0: off) */
     int32_t keep_block_sums;/* 1: keep per-interval, per-chain sums of x and log pi (for ESS / PSRF) */
     int32_t profile;        /* 1: time every phase with CUDA events on the context's stream (diam_get_profile) */
-    int32_t reserved[6];
+    int32_t graphs;         /* 1: each whole interval's n_lag steps replay one captured CUDA graph (default) */
+    int32_t reserved[5];
 } diam_config;
 
 typedef struct {

@@ -463,8 +463,8 @@ static void orc_block_end(orc_sampler* s, int64_t blk) {
          * variance loaded by the same relative amount, retrying with eps x 100 up to three times */
         double eps = c->eps_jitter;
         /* BF16 mode: C_n comes from an FP32-accumulated tensor-core product whose relative error (about 1e-5
-         * in correlation terms) exceeds the FP64 default; its first attempt loads by at least 1e-6 */
-        if (c->prec == 2 && eps < 1e-6) eps = 1e-6;
+         * in correlation terms) exceeds the FP64 default; its first attempt loads by at least 1e-5 */
+        if (c->prec == 2 && eps < 1e-5) eps = 1e-5;
         int ok = -1;
         for (int attempt = 0; attempt < 4 && ok != 0; ++attempt) {
             double* Cj = (double*)malloc(sizeof(double) * nn);

@@ -39,7 +39,8 @@ class DiamConfig(C.Structure):
                 ("beta_min", C.c_double), ("beta_max", C.c_double), ("eps_jitter", C.c_double),
                 ("min_samples_refresh", C.c_int64), ("burnin", C.c_int64), ("refresh_delay", C.c_int32),
                 ("prec", C.c_int32), ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("trace_steps", C.c_int32),
-                ("keep_block_sums", C.c_int32), ("profile", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("keep_block_sums", C.c_int32), ("profile", C.c_int32), ("graphs", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class DiamDaConfig(C.Structure):

@@ -77,6 +77,10 @@ struct diam_ctx {
     int8_t* accf = nullptr;                                      // per-chain decision of the current step
     float* ws = nullptr;                                         // split-K partial target products (BF16 mode)
     int nchunk = 1, tsplit = 1;
+    // CUDA graph of one interval's n_lag steps (captured once; embeds buffer pointers and the DA switch)
+    cudaGraphExec_t graph = nullptr;
+    const void* graph_bsum = nullptr;
+    int graph_da = -1;
     void *W = nullptr, *hist = nullptr;
     int ldw = 0, ldh = 0, nparts = 0;
     // target
@@ -311,20 +315,40 @@ static diam_status prepare_block(diam_ctx* c, int64_t blk) {
     return DIAM_OK;
 }
 
+// Grow the per-interval, per-chain sums to hold interval blk (outside any graph capture).
+static diam_status ensure_bsum(diam_ctx* c, int64_t blk) {
+    if (!c->cfg.keep_block_sums || blk < c->bcap) return DIAM_OK;
+    const int P = c->P, d = c->d;
+    int64_t ncap = std::max<int64_t>(2 * c->bcap, blk + 16);
+    double *nb = nullptr, *nlp = nullptr;
+    CKS(dalloc(c, &nb, sizeof(double) * (size_t)ncap * P * d));
+    CKS(dalloc(c, &nlp, sizeof(double) * (size_t)ncap * P));
+    if (c->bcap) {
+        CK(cudaMemcpyAsync(nb, c->bsum, sizeof(double) * (size_t)c->bcap * P * d, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(nlp, c->lpsum, sizeof(double) * (size_t)c->bcap * P, cudaMemcpyDeviceToDevice, c->st));
+    }
+    c->bsum = nb;
+    c->lpsum = nlp;
+    c->bcap = ncap;
+    return DIAM_OK;
+}
+
+// One step of every chain. The kernels read the step (global t, in-interval s) from the context's device
+// scalars and the last one advances it, so the same launch sequence can be captured once as a graph.
 template <typename T>
-static diam_status do_step(diam_ctx* c, int s, int64_t t) {
+static diam_status do_step(diam_ctx* c) {
     const int d = c->d, P = c->P;
-    const T* Xi = (const T*)c->Xi + (size_t)s * P * d;
+    const T* Xi = (const T*)c->Xi;
     constexpr bool BF = std::is_same<T, float>::value;
     const dim3 grid2(P, c->nchunk);
     int e0 = ph_begin(c, PH_PROPOSE);
     if constexpr (BF) {
-        const uint16_t* Ws = (const uint16_t*)c->W + (size_t)s * P * c->ldw;
+        const uint16_t* Ws = (const uint16_t*)c->W;
         { propose_kernel<T, uint16_t><<<grid2, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
                                                                (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qpart, c->lpart,
                                                                c->ctl, c->tg, c->op_hi, c->op_lo, c->ldk); count_launch(); }
     } else {
-        const T* Ws = (const T*)c->W + (size_t)s * P * c->ldw;
+        const T* Ws = (const T*)c->W;
         { propose_kernel<T, T><<<grid2, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
                                                         (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qpart, c->lpart,
                                                         c->ctl, c->tg, nullptr, nullptr, c->ldk); count_launch(); }
@@ -335,13 +359,13 @@ static diam_status do_step(diam_ctx* c, int s, int64_t t) {
     const double iw = inv_infl2(c);
     if (c->kind == TK_REF || c->kind == TK_CALLBACK) {
         CKS(eval_lp<T>(c, (const T*)c->Xp, c->lpp));
-        { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, t, c->qpart, c->lpart, nullptr, 0, c->lpp,
+        { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, c->qpart, c->lpart, nullptr, 0, c->lpp,
                                                             iw, c->lp, c->q, c->accf, c->ctl, c->tr); count_launch(); }
     } else if (c->kind == TK_DENSE || c->kind == TK_TANH) {
         const double inv2s2 = 1.0 / (2.0 * c->sigma * c->sigma);
         if constexpr (BF) {
           if (c->da) {
-            CKS(da_step(c, t));
+            CKS(da_step(c));
           } else {
             TcEpi epi{};
             epi.mode = TC_STORE;
@@ -352,52 +376,35 @@ static diam_status do_step(diam_ctx* c, int s, int64_t t) {
             CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, c->tsplit, epi,
                                    &c->ctl->status, c->st, &used));
             { finish_linear_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y, inv2s2, c->kind == TK_TANH,
-                                                            c->nchunk, c->key, t, c->qpart, c->lpart, iw, c->lp, c->q,
+                                                            c->nchunk, c->key, c->qpart, c->lpart, iw, c->lp, c->q,
                                                             c->accf, c->ctl, c->tr); count_launch(); }
           }
         } else {
             EpiTargetReduce epi{c->partial, c->y, inv2s2, c->kind == TK_TANH};
             CK((gemm_f64<true, true>(c->dy, P, d, c->Gm, d, (const double*)c->Xp, d, TileRange{0, 0}, epi, c->st)));
-            { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, t, c->qpart, c->lpart, c->partial,
+            { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, c->qpart, c->lpart, c->partial,
                                                                 c->nparts, nullptr, iw, c->lp, c->q, c->accf, c->ctl,
                                                                 c->tr); count_launch(); }
         }
     } else {
-        { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, t, c->qpart, c->lpart, nullptr, 0, nullptr,
+        { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, c->qpart, c->lpart, nullptr, 0, nullptr,
                                                             iw, c->lp, c->q, c->accf, c->ctl, c->tr); count_launch(); }
     }
     CK(cudaGetLastError());
     ph_end(c, e1);
-    const int64_t blk = t / c->nl;
-    double* bs = nullptr;
-    double* ls = nullptr;
-    if (c->cfg.keep_block_sums) {
-        if (blk >= c->bcap) {
-            int64_t ncap = std::max<int64_t>(2 * c->bcap, blk + 16);
-            double *nb = nullptr, *nlp = nullptr;
-            CKS(dalloc(c, &nb, sizeof(double) * (size_t)ncap * P * d));
-            CKS(dalloc(c, &nlp, sizeof(double) * (size_t)ncap * P));
-            if (c->bcap) {
-                CK(cudaMemcpyAsync(nb, c->bsum, sizeof(double) * (size_t)c->bcap * P * d, cudaMemcpyDeviceToDevice, c->st));
-                CK(cudaMemcpyAsync(nlp, c->lpsum, sizeof(double) * (size_t)c->bcap * P, cudaMemcpyDeviceToDevice, c->st));
-            }
-            c->bsum = nb;
-            c->lpsum = nlp;
-            c->bcap = ncap;
-        }
-        bs = c->bsum + (size_t)blk * P * d;
-        ls = c->lpsum + (size_t)blk * P;
-    }
     int e2 = ph_begin(c, PH_ACCEPT);
+    double* bs = c->cfg.keep_block_sums ? c->bsum : nullptr;
+    double* ls = c->cfg.keep_block_sums ? c->lpsum : nullptr;
     if constexpr (BF) {
-        { select_kernel<T, float><<<grid2, kThreads, 0, c->st>>>(d, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
-                                                                (const T*)c->Zp, (float*)c->hist + (size_t)s * P * c->ldh,
-                                                                c->ldh, (const T*)c->cenT, bs, ls, c->lp); count_launch(); }
+        { select_kernel<T, float><<<grid2, kThreads, 0, c->st>>>(d, P, c->nl, c->ctl, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
+                                                                (const T*)c->Zp, (float*)c->hist, c->ldh, (const T*)c->cenT,
+                                                                bs, ls, c->lp); count_launch(); }
     } else {
-        { select_kernel<T, double><<<grid2, kThreads, 0, c->st>>>(d, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
-                                                                 (const T*)c->Zp, (double*)c->hist + (size_t)s * P * c->ldh,
-                                                                 c->ldh, (const T*)c->cenT, bs, ls, c->lp); count_launch(); }
+        { select_kernel<T, double><<<grid2, kThreads, 0, c->st>>>(d, P, c->nl, c->ctl, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
+                                                                 (const T*)c->Zp, (double*)c->hist, c->ldh, (const T*)c->cenT,
+                                                                 bs, ls, c->lp); count_launch(); }
     }
+    { advance_kernel<<<1, 1, 0, c->st>>>(c->ctl); count_launch(); }
     CK(cudaGetLastError());
     ph_end(c, e2);
     return DIAM_OK;
@@ -462,8 +469,8 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
     double inv_n = 1.0 / (double)c->n;
     double eps = c->cfg.eps_jitter;
     // BF16 mode: the fold's FP32 tensor-core accumulation leaves C_n off by about 1e-5 in correlation terms,
-    // so the first attempt loads the diagonal by at least 1e-6 (relative) instead of retrying up to it
-    if (c->bf && eps < 1e-6) eps = 1e-6;
+    // so the first attempt loads the diagonal by at least 1e-5 (relative) instead of retrying up to it
+    if (c->bf && eps < 1e-5) eps = 1e-5;
     bool ok = false;
     for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
         // C_n + eps diag(C_n): every variance loaded by the same relative amount (the skip / jitter rule)
@@ -522,19 +529,58 @@ static diam_status block_end(diam_ctx* c, int64_t blk) {
     return DIAM_OK;
 }
 
+// Replay the captured graph of one interval's steps (capturing it first if needed).
+template <typename T>
+static diam_status interval_graph(diam_ctx* c) {
+    const int da_sig = c->da ? (c->da->active ? 1 : 0) : -1;
+    if (c->graph && (c->graph_bsum != (const void*)c->bsum || c->graph_da != da_sig)) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (!c->graph) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        diam_status s = DIAM_OK;
+        for (int k = 0; k < c->nl && s == DIAM_OK; ++k) s = do_step<T>(c);
+        cudaError_t e = cudaStreamEndCapture(c->st, &g);
+        if (s != DIAM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        CK(e);
+        cudaError_t ei = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        CK(ei);
+        c->graph_bsum = c->bsum;
+        c->graph_da = da_sig;
+    }
+    CK(cudaGraphLaunch(c->graph, c->st));
+    return DIAM_OK;
+}
+
 template <typename T>
 static diam_status run_steps(diam_ctx* c, int64_t n_steps) {
+    { set_step_kernel<<<1, 1, 0, c->st>>>(c->ctl, (long long)c->t, (int)(c->t % c->nl)); count_launch(); }
     while (n_steps > 0) {
         int64_t blk = c->t / c->nl;
         int s = (int)(c->t % c->nl);
         if (s == 0 && c->begun_block != blk) {
             CKS(block_begin<T>(c, blk));
+            { centre_kernel<T><<<blocks_for(c->d), kThreads, 0, c->st>>>(c->d, c->P, (const T*)c->X, (T*)c->cenT, c->cen64); count_launch(); }
             c->begun_block = blk;
         }
         if (c->xi_block != blk) CKS(prepare_block<T>(c, blk));
-        CKS(do_step<T>(c, s, c->t));
-        c->t++;
-        n_steps--;
+        CKS(ensure_bsum(c, blk));
+        const bool whole = s == 0 && n_steps >= c->nl && c->cfg.graphs && c->kind != TK_CALLBACK && !c->cfg.profile;
+        if (whole) {
+            CKS(interval_graph<T>(c));
+            c->t += c->nl;
+            n_steps -= c->nl;
+        } else {
+            CKS(do_step<T>(c));
+            c->t++;
+            n_steps--;
+        }
         if (c->t % c->nl == 0) CKS(block_end<T>(c, blk));
     }
     return DIAM_OK;
@@ -722,6 +768,7 @@ diam_status diam_config_default(diam_config* cfg, int32_t d, int32_t P) {
     cfg->burnin = 0;
     cfg->refresh_delay = 0;
     cfg->prec = DIAM_FP64;
+    cfg->graphs = 1;
     return DIAM_OK;
 }
 
@@ -995,6 +1042,10 @@ diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
     c->chol_attempts = hs.chol_attempts;
     for (size_t i = 0; i < c->pend.size(); ++i) c->pend[i].block = hs.pend_block[i];
     c->xi_block = -1;  // noise products are regenerated from the counter-based streams
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
     CKS(quantise(c));
     return sync_and_check(c);
 }
@@ -1147,6 +1198,7 @@ void diam_destroy(diam_ctx* c) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
     }
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c->da;

@@ -173,7 +173,7 @@ static diam_status da_train_now(diam_ctx* c, double* rmse_out) {
 }
 
 // Per-step DA path (BF16 mode, linear-map target): screen, compact, exact test for the survivors.
-static diam_status da_step(diam_ctx* c, int64_t t) {
+static diam_status da_step(diam_ctx* c) {
     DaState* a = c->da;
     const int P = c->P;
     int e0 = ph_begin(c, PH_SCREEN);
@@ -182,7 +182,7 @@ static diam_status da_step(diam_ctx* c, int64_t t) {
         CKS(da_forward(c, P, a->U, a->H1, a->H2, nullptr, nullptr, a->s_prop));
     }
     const int nthr = (P + 31) / 32 * 32;
-    { stage1_kernel<<<1, nthr, 0, c->st>>>(P, c->nchunk, c->key, t, a->active ? 1 : 0, c->qpart, inv_infl2(c), c->q, a->s_prop,
+    { stage1_kernel<<<1, nthr, 0, c->st>>>(P, c->nchunk, c->key, c->ctl, a->active ? 1 : 0, c->qpart, inv_infl2(c), c->q, a->s_prop,
                                          a->s_cur, a->qsave, a->idx, c->accf, nullptr, a->cnt, c->tr); count_launch(); }
     { gather_rows_kernel<<<P, kThreads, 0, c->st>>>(a->cnt, a->idx, c->op_hi, c->op_lo, a->Chi, a->Clo, c->ldk); count_launch(); }
     CK(cudaGetLastError());
@@ -198,7 +198,7 @@ static diam_status da_step(diam_ctx* c, int64_t t) {
     CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, a->Chi, a->Clo, c->ldk, c->tsplit, epi, &c->ctl->status,
                            c->st, &used));
     { finish_da_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y, 1.0 / (2.0 * c->sigma * c->sigma),
-                                                c->kind == TK_TANH, c->nchunk, c->key, t, c->lpart, a->qsave, a->idx, a->cnt,
+                                                c->kind == TK_TANH, c->nchunk, c->key, c->lpart, a->qsave, a->idx, a->cnt,
                                                 a->s_prop, a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, a->Chi, a->ring_x,
                                                 a->ring_lp, (long long)a->cfg.ring, c->ldk); count_launch(); }
     { ring_advance_kernel<<<1, 1, 0, c->st>>>(a->cnt, (long long)a->cfg.ring); count_launch(); }

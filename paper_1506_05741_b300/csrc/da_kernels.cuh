@@ -49,13 +49,14 @@ struct DaCounters {
 // Stage 1 for every chain (one block, P <= 1024 threads): q(x*) from the proposal's partial sums, then
 // with the surrogate active: log a1 = s(x*) - s(x) + q(x*) - q(x), pass iff log u1 < log a1 (tag 3);
 // inactive: every chain passes. The passing chains are compacted in chain order into idx[0..count).
-__global__ void stage1_kernel(int P, int nchunk, Key key, int64_t t, int active, const double* __restrict__ qpart,
+__global__ void stage1_kernel(int P, int nchunk, Key key, const Ctl* ctl, int active, const double* __restrict__ qpart,
                               double inv_infl2, const double* __restrict__ q, const double* __restrict__ s_prop,
                               const double* __restrict__ s_cur, double* __restrict__ qsave, int* __restrict__ idx,
                               int8_t* __restrict__ accf, double* __restrict__ lp_nan_trace, DaCounters* cnt,
                               TraceDev tr) {
     __shared__ int wsum[32];
     const int p = threadIdx.x;
+    const int64_t t = ctl->t_cur;
     int pass = 0;
     if (p < P) {
         double qs = 0.0;
@@ -121,7 +122,7 @@ __global__ void gather_rows_kernel(const DaCounters* cnt, const int* __restrict_
 // (x*, log pi(x*)) goes to the ring buffer.
 __global__ void __launch_bounds__(256) finish_da_kernel(int P, int dy, int nsplit, const float* __restrict__ ws,
                                                          const double* __restrict__ y, double inv2s2, int tanh_mode,
-                                                         int nchunk, Key key, int64_t t,
+                                                         int nchunk, Key key,
                                                          const double* __restrict__ lpart,
                                                          const double* __restrict__ qsave, const int* __restrict__ idx,
                                                          const DaCounters* cnt, const double* __restrict__ s_prop,
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(256) finish_da_kernel(int P, int dy, int nspli
     const int k = blockIdx.x;
     if (k >= cnt->count) return;
     const int p = idx[k];
+    const int64_t t = ctl->t_cur;
     const size_t plane = (size_t)P * dy;
     double acc = 0.0;
     for (int m = threadIdx.x; m < dy; m += blockDim.x) {

@@ -19,7 +19,22 @@ struct Ctl {
     int status;                        // DEV_* code, first error wins
     int chol_info;                     // Cholesky failure (pivot + 1)
     double trace;                      // tr(M2) at the last refresh
+    long long t_cur;                   // global step the step kernels are working on
+    int s_cur;                         // its index within the interval
+    int pad_;
 };
+
+// End of one step: the step counters move on (the step kernels read them, so a captured graph of the
+// interval's steps replays unchanged).
+__global__ void advance_kernel(Ctl* ctl) {
+    ctl->t_cur += 1;
+    ctl->s_cur += 1;
+}
+
+__global__ void set_step_kernel(Ctl* ctl, long long t, int s) {
+    ctl->t_cur = t;
+    ctl->s_cur = s;
+}
 
 enum : int { TK_DIAG = 0, TK_DENSE = 1, TK_TANH = 2, TK_BANANA = 3, TK_REF = 4, TK_CALLBACK = 5 };
 
@@ -100,10 +115,11 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
     const int p = blockIdx.x, c = blockIdx.y;
     const int i0 = c * CHUNK, i1 = min(d, i0 + CHUNK);
     const T rho = (T)ctl->rho, ba = (T)ctl->ba;
+    const size_t row = (size_t)ctl->s_cur * P + p;   // this step's row of the interval's noise buffers
     const T* x = X + (size_t)p * d;
     const T* z = Z + (size_t)p * d;
-    const T* xi = Xi + (size_t)p * d;
-    const WT* w = W + (size_t)p * ldw;
+    const T* xi = Xi + row * d;
+    const WT* w = W + row * ldw;
     T* xp = Xp + (size_t)p * d;
     T* zp = Zp + (size_t)p * d;
     double qacc = 0.0, lacc = 0.0;
@@ -249,12 +265,13 @@ __device__ __forceinline__ void decide(int p, int P, Key key, int64_t t, double 
 
 // One thread per chain: log pi(x*) = O(d) partials + linear-map partials (FP64 GEMM epilogue), or an
 // externally evaluated value; q(x*) from the proposal's partials; then the decision.
-__global__ void finish_kernel(int P, int nchunk, Key key, int64_t t, const double* __restrict__ qpart,
+__global__ void finish_kernel(int P, int nchunk, Key key, const double* __restrict__ qpart,
                               const double* __restrict__ lpart, const double* __restrict__ partial, int nparts,
                               const double* __restrict__ ext, double inv_infl2, double* lp, double* q, int8_t* accf,
                               Ctl* ctl, TraceDev tr) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
+    const int64_t t = ctl->t_cur;
     double lpp = 0.0, qs = 0.0;
     for (int c = 0; c < nchunk; ++c) qs += qpart[(size_t)c * P + p];
     if (ext) {
@@ -271,13 +288,14 @@ __global__ void finish_kernel(int P, int nchunk, Key key, int64_t t, const doubl
 // in FP64; then the O(d) partials, q(x*) and the decision.
 __global__ void __launch_bounds__(256) finish_linear_kernel(int P, int dy, int nsplit, const float* __restrict__ ws,
                                                              const double* __restrict__ y, double inv2s2, int tanh_mode,
-                                                             int nchunk, Key key, int64_t t,
+                                                             int nchunk, Key key,
                                                              const double* __restrict__ qpart,
                                                              const double* __restrict__ lpart, double inv_infl2,
                                                              double* lp, double* q, int8_t* accf, Ctl* ctl,
                                                              TraceDev tr) {
     __shared__ double sh[32];
     const int p = blockIdx.x;
+    const int64_t t = ctl->t_cur;
     const size_t plane = (size_t)P * dy;
     double acc = 0.0;
     for (int m = threadIdx.x; m < dy; m += blockDim.x) {
@@ -311,12 +329,16 @@ template <>
 __device__ __forceinline__ float to_hist<float, float>(float v) { return v; }
 
 template <typename T, typename HT>
-__global__ void __launch_bounds__(256) select_kernel(int d, const int8_t* __restrict__ accf, T* __restrict__ X,
-                                                     T* __restrict__ Z, const T* __restrict__ Xp,
-                                                     const T* __restrict__ Zp, HT* __restrict__ hist, int ldh,
-                                                     const T* __restrict__ cen, double* __restrict__ bsum,
-                                                     double* __restrict__ lpsum, const double* __restrict__ lp) {
+__global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, const Ctl* ctl, const int8_t* __restrict__ accf,
+                                                     T* __restrict__ X, T* __restrict__ Z, const T* __restrict__ Xp,
+                                                     const T* __restrict__ Zp, HT* __restrict__ hist_base, int ldh,
+                                                     const T* __restrict__ cen, double* __restrict__ bsum_base,
+                                                     double* __restrict__ lpsum_base, const double* __restrict__ lp) {
     const int p = blockIdx.x, c = blockIdx.y;
+    const long long blk = ctl->t_cur / nl;
+    HT* hist = hist_base ? hist_base + (size_t)ctl->s_cur * P * ldh : nullptr;
+    double* bsum = bsum_base ? bsum_base + (size_t)blk * P * d : nullptr;
+    double* lpsum = lpsum_base ? lpsum_base + (size_t)blk * P : nullptr;
     const int i0 = c * CHUNK, i1 = min(d, i0 + CHUNK);
     const int a = accf[p];
     T* x = X + (size_t)p * d;
@@ -408,6 +430,20 @@ __global__ void mean_update_kernel(int d, double frac, const double* __restrict_
     cen64[i] = (double)c;
 }
 
+// Centre of the coming interval's records: the mean of the chains' current states (a close predictor of
+// the interval's mean, so the centred sums stay small and the FP32 tensor-core SYRK loses little to
+// cancellation). cen64 holds exactly the values subtracted (in the state type).
+template <typename T>
+__global__ void centre_kernel(int d, int P, const T* __restrict__ X, T* __restrict__ cenT, double* __restrict__ cen64) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    double s = 0.0;
+    for (int p = 0; p < P; ++p) s += (double)X[(size_t)p * d + i];
+    T c = (T)(s / P);
+    cenT[i] = c;
+    cen64[i] = (double)c;
+}
+
 // ---------------------------------------------------------------------------------------------------
 // Refresh helpers.
 __global__ void trace_kernel(int d, const double* __restrict__ M2, int ld, Ctl* ctl) {
@@ -475,6 +511,7 @@ __global__ void set_scalars_kernel(Ctl* ctl, double beta, double rho, double ba,
     ctl->ba = ba;
     ctl->inv_infl2 = inv_infl2;
     ctl->acc_block = 0ull;
+    ctl->s_cur = 0;
 }
 
 template <typename A, typename B>

@@ -251,3 +251,21 @@ def test_moment_merge_equals_pooled_samples():
     assert n == X.shape[0]
     assert np.max(np.abs(m - X.mean(0))) < 1e-11
     assert np.max(np.abs(cov - np.cov(X.T, bias=True))) < 1e-10 * np.max(np.abs(cov))
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_graph_replay_equals_eager_launches(prec):
+    """Whole intervals replay one captured CUDA graph; the chains are bit-identical to eager launches."""
+    import paper_1506_05741_b300 as dm
+    ts, P = workloads.tanh_regression(128, 64, 3), 6
+    out = []
+    for graphs in (0, 1):
+        cfg = dm.default_config(128, P, n_lag=8, beta0=0.3, seed=4, prec=prec, graphs=graphs, min_samples_refresh=20)
+        s = dm.Sampler(cfg, ts, x0=workloads.start_state(128, P, 1) * np.sqrt(ts.lam), C0=np.diag(ts.lam))
+        s.run(5)      # partial interval (eager), then whole intervals
+        s.run(3 + 8 * 5)
+        out.append((s.state(), s.moments()))
+    (xa, la, sa), (ma, ca, na) = out[0]
+    (xb, lb, sb), (mb, cb, nb) = out[1]
+    assert np.array_equal(xa, xb) and np.array_equal(la, lb) and sa == sb
+    assert np.array_equal(ma, mb) and np.array_equal(ca, cb) and na == nb
