@@ -289,7 +289,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
                 "data": "synthetic", "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk.summary(), "fp64_plain": fp64,
-                "accept_rate": round(st["accepted"] / max(1, st["steps"] * run.P), 4), "refreshes": st["refreshes"]}
+                "accept_rate": round(st["accepted"] / max(1, st["steps"] * run.P), 4), "refreshes": st["refreshes"],
+                "chol_attempts": st["chol_attempts"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -81,6 +81,7 @@ struct diam_ctx {
     cudaGraphExec_t graph = nullptr;
     const void* graph_bsum = nullptr;
     int graph_da = -1;
+    unsigned long long graph_launches = 0;   // kernel launches inside one replay
     void *W = nullptr, *hist = nullptr;
     int ldw = 0, ldh = 0, nparts = 0;
     // target
@@ -539,6 +540,7 @@ static diam_status interval_graph(diam_ctx* c) {
     }
     if (!c->graph) {
         cudaGraph_t g = nullptr;
+        const unsigned long long l0 = g_launches.load();
         CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
         diam_status s = DIAM_OK;
         for (int k = 0; k < c->nl && s == DIAM_OK; ++k) s = do_step<T>(c);
@@ -553,8 +555,11 @@ static diam_status interval_graph(diam_ctx* c) {
         CK(ei);
         c->graph_bsum = c->bsum;
         c->graph_da = da_sig;
+        c->graph_launches = g_launches.load() - l0;
+        g_launches.fetch_sub(c->graph_launches);   // counted when they run, below
     }
     CK(cudaGraphLaunch(c->graph, c->st));
+    g_launches.fetch_add(c->graph_launches);
     return DIAM_OK;
 }
 

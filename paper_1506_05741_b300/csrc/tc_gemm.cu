@@ -345,27 +345,92 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
     return cudaGetLastError();
 }
 
+static cudaError_t launch_any(int bn, int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B,
+                              const uint16_t* B2, int ldb, int a_lower, const TcEpi& epi, int* status, cudaStream_t st,
+                              int splits) {
+    switch (bn) {
+        case 32: return launch_bn<32>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
+        case 64: return launch_bn<64>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
+        default: return launch_bn<128>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
+    }
+}
+
+static bool args_ok(int K, int lda, int ldb, const uint16_t* A, const uint16_t* B, const uint16_t* B2) {
+    if (K <= 0 || K % TC_BK || lda % TC_BK || ldb % TC_BK || K > lda || K > ldb) return false;
+    return ((((uintptr_t)A | (uintptr_t)B | (uintptr_t)(B2 ? B2 : B)) & 15) == 0);
+}
+
 cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2, int ldb,
-                         int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st) {
+                         int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st, int bn) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    if (K <= 0 || K % TC_BK || lda % TC_BK || ldb % TC_BK || K > lda || K > ldb) return cudaErrorInvalidValue;
-    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)(B2 ? B2 : B)) & 15) return cudaErrorInvalidValue;
-    return launch_bn<128>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status_dev, st);
+    if (!args_ok(K, lda, ldb, A, B, B2)) return cudaErrorInvalidValue;
+    return launch_any(bn, M, N, K, A, lda, B, B2, ldb, a_lower, epi, status_dev, st, 1);
 }
 
 // Split-K form: K blocks divided over `splits` CTAs per tile; each writes its FP32 partial product to
 // D + z * split_stride (TC_STORE only, no triangular skip). Returns the number of partial planes in *used.
 cudaError_t tc_gemm_bf16_splitk(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
-                                int ldb, int splits, const TcEpi& epi, int* status_dev, cudaStream_t st, int* used) {
+                                int ldb, int splits, const TcEpi& epi, int* status_dev, cudaStream_t st, int* used, int bn) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (epi.mode != TC_STORE || splits < 1) return cudaErrorInvalidValue;
-    if (K <= 0 || K % TC_BK || lda % TC_BK || ldb % TC_BK || K > lda || K > ldb) return cudaErrorInvalidValue;
-    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)(B2 ? B2 : B)) & 15) return cudaErrorInvalidValue;
+    if (!args_ok(K, lda, ldb, A, B, B2)) return cudaErrorInvalidValue;
     const int nkb = K / TC_BK;
     splits = std::min(splits, nkb);
     const int per = (nkb + splits - 1) / splits;
     *used = (nkb + per - 1) / per;
-    return launch_bn<128>(M, N, K, A, lda, B, B2, ldb, 0, epi, status_dev, st, *used);
+    return launch_any(bn, M, N, K, A, lda, B, B2, ldb, 0, epi, status_dev, st, *used);
+}
+
+// Tile autotuner: times BN = 32, 64, 128 (one warm-up and two timed launches each, CUDA events on st)
+// for this product on the caller's buffers and keeps the fastest per shape.
+int tc_autotune(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2, int ldb,
+                int splits, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st, float* best_ms) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, float>> cache;
+    const auto key = std::make_tuple(M, N, K, B2 ? 1 : 0, splits, a_lower, epi.mode);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            if (best_ms) *best_ms = it->second.second;
+            return it->second.first;
+        }
+    }
+    int best = 128;
+    float best_t = 1e30f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return best;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return best;
+    }
+    for (int bn : {32, 64, 128}) {
+        if (bn > 32 && N <= bn / 2) continue;   // a tile at least twice as wide as N only wastes MMA work
+        int used = 1;
+        auto go = [&]() {
+            return splits > 1 ? tc_gemm_bf16_splitk(M, N, K, A, lda, B, B2, ldb, splits, epi, status_dev, st, &used, bn)
+                              : tc_gemm_bf16(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status_dev, st, bn);
+        };
+        if (go() != cudaSuccess) continue;
+        cudaEventRecord(e0, st);
+        bool ok = go() == cudaSuccess && go() == cudaSuccess;
+        cudaEventRecord(e1, st);
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_t) {
+            best_t = ms;
+            best = bn;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        cache[key] = {best, best_t / 2};
+    }
+    if (best_ms) *best_ms = best_t / 2;
+    return best;
 }
 
 // ---------------------------------------------------------------------------------------------------- transpose

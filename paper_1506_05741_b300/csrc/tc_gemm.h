@@ -42,12 +42,19 @@ struct TcEpi {
 
 // a_lower: A is lower triangular (A[m][k] = 0 for k > m), K blocks past the m-tile are skipped.
 // status_dev: receives a non-zero code if a bounded wait inside the kernel expired.
+// bn: tile width over N (32, 64 or 128; see tc_autotune)
 cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
-                         int ldb, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st);
+                         int ldb, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st, int bn = 128);
 
 // Split-K TC_STORE: grid z = splits, K blocks divided evenly; *used receives the number of partial planes.
 cudaError_t tc_gemm_bf16_splitk(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
-                                int ldb, int splits, const TcEpi& epi, int* status_dev, cudaStream_t st, int* used);
+                                int ldb, int splits, const TcEpi& epi, int* status_dev, cudaStream_t st, int* used,
+                                int bn = 128);
+
+// Tile autotuner: the fastest tile width (32, 64, 128) for this product, timed on the given buffers once
+// per shape (cached); best_ms (optional) receives its launch time. Must not be called during capture.
+int tc_autotune(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2, int ldb,
+                int splits, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st, float* best_ms);
 
 // out[c*ldo + r] = bf16(in[r*ldi + c]) (round to nearest even) for r < rows, c < cols; out[c*ldo + r] = 0 for
 // rows <= r < ldo, so the K padding of the transposed operand is zero
