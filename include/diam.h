@@ -245,6 +245,20 @@ DIAM_API diam_status diam_da_grad(diam_ctx* ctx, int32_t B, const double* U, con
 DIAM_API diam_status diam_da_get_weights(diam_ctx* ctx, double* W1, double* b1, double* W2, double* b2, double* w3,
                                          double* b3);
 
+/* ---------------------------------------------------------------------------------------------------
+ * Many independent samplers run together (uneven dimensions, separate targets): the batched form of the
+ * sampler. Problem j has its own configuration, target and start state, its own context and its own
+ * stream. diam_multi_run advances every problem by n_steps steps; one host thread per problem drives its
+ * context (whole intervals replay that problem's captured interval graph), so the problems' kernels
+ * interleave on the GPU. x0 and C0 may be NULL or hold NULL entries (per-problem defaults). */
+typedef struct diam_multi diam_multi;
+DIAM_API diam_status diam_multi_init(int32_t n, const diam_config* cfgs, const diam_target* targets,
+                                     const double* const* x0, const double* const* C0, diam_multi** out);
+DIAM_API diam_status diam_multi_run(diam_multi* m, int64_t n_steps);
+/* The context of problem j (owned by m; use it with the single-sampler getters). */
+DIAM_API diam_ctx* diam_multi_context(diam_multi* m, int32_t j);
+DIAM_API void diam_multi_destroy(diam_multi* m);
+
 /* Phase timings collected while cfg.profile = 1: for each phase, the number of timed launches of its
  * kernels and their summed device time in milliseconds (CUDA events on the context's stream). Phases:
  * 0 noise draw, 1 noise product (batched triangular GEMM), 2 propose, 3 target (linear map + reduction),

@@ -39,6 +39,12 @@ DIAM_API diam_status diam_op_gemm_bf16(int32_t M, int32_t N, int32_t K, const ui
                               const uint16_t* B2, int32_t ldb, int32_t a_lower, float scale, float* D, int32_t ldd,
                               void* stream);
 
+/* diam_op_gemm_bf16 with an explicit tile width over N (bn = 32, 64 or 128): the candidates the tile
+ * autotuner times for each product shape. Synchronises the stream. */
+DIAM_API diam_status diam_op_gemm_bf16_tile(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda,
+                                            const uint16_t* B, const uint16_t* B2, int32_t ldb, int32_t a_lower,
+                                            float scale, float* D, int32_t ldd, int32_t bn, void* stream);
+
 /* The product of diam_op_gemm_bf16 (same arguments, same result within FP32 summation order) for callers
  * that cannot allocate device memory: code whose device memory belongs to its own pool and forbids outside
  * allocations, or code running while a stream is captured, where an allocating call is not allowed.

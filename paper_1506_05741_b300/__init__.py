@@ -103,6 +103,10 @@ def lib():
                 "diam_last_error": (C.c_char_p, [P]),
                 "diam_status_string": (C.c_char_p, [C.c_int]),
                 "diam_kernel_launches": (C.c_uint64, []),
+                "diam_multi_init": (C.c_int, [I32, P, P, P, P, P]),
+                "diam_multi_run": (C.c_int, [P, I64]),
+                "diam_multi_context": (P, [P, I32]),
+                "diam_multi_destroy": (None, [P]),
                 "diam_da_config_default": (C.c_int, [P]),
                 "diam_da_enable": (C.c_int, [P, P, P, P, P, P, P, P]),
                 "diam_da_train": (C.c_int, [P, P]),
@@ -164,6 +168,93 @@ def da_default_config(**kw) -> dict:
     return cfg
 
 
+def _target_struct(target, keep):
+    def arr(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, np.float64)
+        keep.append(a)
+        return a
+    ts = DiamTarget()
+    ts.kind = int(target.kind)
+    ts.d_y = int(getattr(target, "d_y", 0) or 0)
+    ts.lam = _p(arr(getattr(target, "lam", None)))
+    ts.G = _p(arr(getattr(target, "G", None)))
+    ts.A = _p(arr(getattr(target, "A", None)))
+    ts.y = _p(arr(getattr(target, "y", None)))
+    ts.sigma = float(getattr(target, "sigma", 0.0) or 0.0)
+    ts.ban_a = float(getattr(target, "ban_a", 100.0))
+    ts.ban_b = float(getattr(target, "ban_b", 0.1))
+    ts.ban_c = float(getattr(target, "ban_c", 10.0))
+    return ts
+
+
+class _View:
+    """A problem of a MultiSampler seen through the single-sampler getters (not owning its context)."""
+
+    def __init__(self, l, h, d, P):
+        self._l, self._h, self.d, self.P = l, h, d, P
+
+    def close(self):
+        pass
+
+    __del__ = close
+
+
+class MultiSampler:
+    """Many independent DIAM problems (uneven d, own targets) run together on one GPU (diam_multi_*)."""
+
+    def __init__(self, cfgs, targets, x0s=None, C0s=None):
+        self._l = lib()
+        n = len(cfgs)
+        keep = []
+        carr = (DiamConfig * n)()
+        tarr = (DiamTarget * n)()
+        for j, (cfg, tg) in enumerate(zip(cfgs, targets)):
+            for k, v in cfg.items():
+                setattr(carr[j], k, v)
+            tarr[j] = _target_struct(tg, keep)
+
+        def ptrs(lst):
+            if lst is None:
+                return None
+            out = (C.c_void_p * n)()
+            for j, a in enumerate(lst):
+                if a is not None:
+                    a = np.ascontiguousarray(a, np.float64)
+                    keep.append(a)
+                    out[j] = a.ctypes.data
+            return out
+
+        h = C.c_void_p()
+        rc = self._l.diam_multi_init(n, carr, tarr, ptrs(x0s), ptrs(C0s), C.byref(h))
+        if rc:
+            raise DiamError(rc, "diam_multi_init")
+        self._h = h
+        self.n = n
+        self.views = []
+        for j, cfg in enumerate(cfgs):
+            v = Sampler.__new__(Sampler)
+            v._l, v._h, v.d, v.P, v.cfg = self._l, C.c_void_p(self._l.diam_multi_context(h, j)), cfg["d"], cfg["P"], cfg
+            v._owned = False
+            self.views.append(v)
+
+    def run(self, n_steps: int):
+        rc = self._l.diam_multi_run(self._h, int(n_steps))
+        if rc:
+            raise DiamError(rc, "diam_multi_run")
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            for v in self.views:
+                v._h = None
+            self._l.diam_multi_destroy(h)
+            self._h = None
+
+    __del__ = close
+
+
 class Sampler:
     """P concurrent DIAM chains on one GPU (one context of libdiam.so)."""
 
@@ -216,9 +307,9 @@ class Sampler:
 
     def close(self):
         h = getattr(self, "_h", None)
-        if h:
+        if h and getattr(self, "_owned", True):
             self._l.diam_destroy(h)
-            self._h = None
+        self._h = None
 
     __del__ = close
 

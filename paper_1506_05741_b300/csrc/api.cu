@@ -77,6 +77,7 @@ struct diam_ctx {
     int8_t* accf = nullptr;                                      // per-chain decision of the current step
     float* ws = nullptr;                                         // split-K partial target products (BF16 mode)
     int nchunk = 1, tsplit = 1;
+    int bn_target = 128, bn_xi = 128;        // tile widths picked by the autotuner (BF16 mode)
     // CUDA graph of one interval's n_lag steps (captured once; embeds buffer pointers and the DA switch)
     cudaGraphExec_t graph = nullptr;
     const void* graph_bsum = nullptr;
@@ -301,7 +302,7 @@ static diam_status prepare_block(diam_ctx* c, int64_t blk) {
         epi.ldd = d;
         epi.scale_dev = &c->ctl->ba;
         CK(tc_gemm_bf16(d, (int)rows, c->ldk, c->Lq16, c->ldk, (const uint16_t*)c->W, nullptr, c->ldw, 1, epi,
-                        &c->ctl->status, c->st));
+                        &c->ctl->status, c->st, c->bn_xi));
         ph_end(c, e1);
     } else {
         int e0 = ph_begin(c, PH_NOISE);
@@ -375,7 +376,7 @@ static diam_status do_step(diam_ctx* c) {
             epi.split_stride = (size_t)P * c->dy;
             int used = 1;
             CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, c->tsplit, epi,
-                                   &c->ctl->status, c->st, &used));
+                                   &c->ctl->status, c->st, &used, c->bn_target));
             { finish_linear_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y, inv2s2, c->kind == TK_TANH,
                                                             c->nchunk, c->key, c->qpart, c->lpart, iw, c->lp, c->q,
                                                             c->accf, c->ctl, c->tr); count_launch(); }
@@ -592,6 +593,28 @@ static diam_status run_steps(diam_ctx* c, int64_t n_steps) {
 }
 
 // ------------------------------------------------------------------------------------------------ init
+// Tile widths of the tensor-core products this context launches, timed on its own buffers (the outputs
+// written here are scratch: the split-K planes and the noise-product buffer, both rewritten before use).
+static diam_status autotune(diam_ctx* c) {
+    if (c->ws) {
+        TcEpi epi{};
+        epi.mode = TC_STORE;
+        epi.D = c->ws;
+        epi.ldd = c->dy;
+        epi.split_stride = (size_t)c->P * c->dy;
+        c->bn_target = tc_autotune(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, c->tsplit, 0, epi,
+                                   &c->ctl->status, c->st, nullptr);
+    }
+    TcEpi ex{};
+    ex.mode = TC_STORE;
+    ex.D = (float*)c->Xi;
+    ex.ldd = c->d;
+    ex.scale_dev = &c->ctl->ba;
+    c->bn_xi = tc_autotune(c->d, c->nl * c->P, c->ldk, c->Lq16, c->ldk, (const uint16_t*)c->W, nullptr, c->ldw, 1, 1, ex,
+                           &c->ctl->status, c->st, nullptr);
+    return sync_and_check(c);
+}
+
 template <typename T>
 static diam_status init_state(diam_ctx* c, const double* x0, const double* C0, const double* xref0) {
     const int d = c->d, P = c->P;
@@ -624,6 +647,7 @@ static diam_status init_state(diam_ctx* c, const double* x0, const double* C0, c
     CKS(rewhiten<T>(c));
     if (c->kind != TK_REF) CKS(eval_lp<T>(c, (const T*)c->X, c->lp));
     CKS(sync_and_check(c));
+    if (c->bf) CKS(autotune(c));
     return DIAM_OK;
 }
 

@@ -196,7 +196,7 @@ static diam_status da_step(diam_ctx* c) {
     epi.n_dev = &a->cnt->count;
     int used = 1;
     CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, a->Chi, a->Clo, c->ldk, c->tsplit, epi, &c->ctl->status,
-                           c->st, &used));
+                           c->st, &used, c->bn_target));
     { finish_da_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y, 1.0 / (2.0 * c->sigma * c->sigma),
                                                 c->kind == TK_TANH, c->nchunk, c->key, c->lpart, a->qsave, a->idx, a->cnt,
                                                 a->s_prop, a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, a->Chi, a->ring_x,

@@ -63,9 +63,10 @@ diam_status diam_op_trsm_lower_f64(int32_t n, int32_t nrows, const double* L, in
     return trsm_lower_f64(L, ldl, n, B, ldb, nrows, (cudaStream_t)stream) == cudaSuccess ? DIAM_OK : DIAM_ECUDA;
 }
 
-diam_status diam_op_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda, const uint16_t* B,
-                              const uint16_t* B2, int32_t ldb, int32_t a_lower, float scale, float* D, int32_t ldd,
-                              void* stream) {
+diam_status diam_op_gemm_bf16_tile(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda,
+                                   const uint16_t* B, const uint16_t* B2, int32_t ldb, int32_t a_lower, float scale,
+                                   float* D, int32_t ldd, int32_t bn, void* stream) {
+    if (bn != 32 && bn != 64 && bn != 128) return DIAM_EINVAL;
     if (!A || !B || !D || M <= 0 || N <= 0 || K <= 0 || K % 64 || lda % 64 || ldb % 64 || K > lda || K > ldb ||
         ldd < M)
         return DIAM_EINVAL;
@@ -80,11 +81,17 @@ diam_status diam_op_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A
     epi.D = D;
     epi.ldd = ldd;
     epi.scale_dev = &sc->scale;
-    if (tc_gemm_bf16(M, N, K, A, lda, B, B2, ldb, a_lower, epi, &sc->status, st) != cudaSuccess) return DIAM_ECUDA;
+    if (tc_gemm_bf16(M, N, K, A, lda, B, B2, ldb, a_lower, epi, &sc->status, st, bn) != cudaSuccess) return DIAM_ECUDA;
     int status = 0;
     if (cudaMemcpyAsync(&status, &sc->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return DIAM_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return DIAM_ECUDA;
     return status == DEV_TIMEOUT ? DIAM_ETIMEOUT : DIAM_OK;
+}
+
+diam_status diam_op_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda, const uint16_t* B,
+                              const uint16_t* B2, int32_t ldb, int32_t a_lower, float scale, float* D, int32_t ldd,
+                              void* stream) {
+    return diam_op_gemm_bf16_tile(M, N, K, A, lda, B, B2, ldb, a_lower, scale, D, ldd, 128, stream);
 }
 
 }  // extern "C"

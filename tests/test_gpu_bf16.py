@@ -16,28 +16,29 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def _gemm(M, N, K, A, B, B2=None, a_lower=0, scale=1.0):
+def _gemm(M, N, K, A, B, B2=None, a_lower=0, scale=1.0, bn=128):
     import torch
     import paper_1506_05741_b300 as dm
     l = dm.lib()
-    f = l.diam_op_gemm_bf16
+    f = l.diam_op_gemm_bf16_tile
     P, I32 = ctypes.c_void_p, ctypes.c_int32
-    f.argtypes = [I32, I32, I32, P, I32, P, P, I32, I32, ctypes.c_float, P, I32, P]
+    f.argtypes = [I32, I32, I32, P, I32, P, P, I32, I32, ctypes.c_float, P, I32, I32, P]
     f.restype = ctypes.c_int
     D = torch.zeros(N, M, dtype=torch.float32, device="cuda")
     rc = f(M, N, K, A.data_ptr(), A.shape[1], B.data_ptr(), None if B2 is None else B2.data_ptr(), B.shape[1],
-           a_lower, scale, D.data_ptr(), M, None)
+           a_lower, scale, D.data_ptr(), M, bn, None)
     assert rc == 0, rc
     return D
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 192), (130, 257, 128)])
-def test_tc_gemm_matches_torch(M, N, K):
+@pytest.mark.parametrize("bn", [32, 64, 128])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 192), (130, 257, 128), (256, 32, 4096)])
+def test_tc_gemm_matches_torch(M, N, K, bn):
     import torch
     g = torch.Generator(device="cuda").manual_seed(M + N + K)
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
-    D = _gemm(M, N, K, A.view(torch.int16), B.view(torch.int16), scale=0.5)
+    D = _gemm(M, N, K, A.view(torch.int16), B.view(torch.int16), scale=0.5, bn=bn)
     ref = 0.5 * (B.float() @ A.float().T)
     assert (D - ref).abs().max().item() <= 1e-5 * ref.abs().max().item() + 1e-6
 
@@ -114,3 +115,25 @@ def test_bf16_reference_gaussian_accepts_almost_every_proposal():
     assert tr["acc"].mean() > 0.999
     assert np.abs(tr["loga"]).max() < 1e-3
     assert g.stats()["refreshes"] >= 3
+
+
+def test_multi_problem_run_equals_each_problem_alone():
+    """Problems of uneven d (dense Gaussians and bananas, BF16 mode) run together; each result equals the
+    same problem run alone, bit for bit."""
+    import paper_1506_05741_b300 as dm
+    ds = [72, 200, 131, 64, 256, 97]
+    targets, cfgs = [], []
+    for j, d in enumerate(ds):
+        targets.append(workloads.dense_gaussian(d, 900 + j) if j % 2 == 0 else workloads.banana(d))
+        cfgs.append(dm.default_config(d, 8, n_lag=16, seed=50 + j, problem_id=j, prec=dm.BF16, min_samples_refresh=40))
+    m = dm.MultiSampler(cfgs, targets)
+    m.run(16 * 4 + 5)
+    for j in range(len(ds)):
+        s = dm.Sampler(cfgs[j], targets[j])
+        s.run(16 * 4 + 5)
+        xa, la, sa = m.views[j].state()
+        xb, lb, sb = s.state()
+        assert np.array_equal(xa, xb) and np.array_equal(la, lb) and sa == sb
+        s.close()
+    assert all(v.stats()["refreshes"] > 0 for v in m.views)
+    m.close()
