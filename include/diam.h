@@ -110,7 +110,7 @@ typedef struct {
     double beta_factor;     /* multiplicative beta change (the paper leaves it open; default 1.1) */
     double beta_min, beta_max;
     double eps_jitter;      /* refresh factors chol(C_n + eps diag(C_n)), eps x100 per retry (3 retries);
-                               BF16 mode starts at max(eps_jitter, 1e-5): its C_n is accumulated in FP32 */
+                               BF16 mode starts at max(eps_jitter, 1e-4): its C_n is accumulated in FP32 */
     int64_t min_samples_refresh;  /* refresh only after this many accepted moves (< 0: d + 1) */
     int64_t burnin;         /* n_0: steps kept out of the moments (footnote to Algorithm 1) */
     int32_t refresh_delay;  /* the factor built at the end of interval k is used from interval k+1+delay */
