@@ -25,6 +25,14 @@ DIAM_API diam_status diam_op_normals(uint64_t seed, uint32_t problem_id, int64_t
  * 1-based index of the first non-positive pivot. Synchronises the stream. */
 DIAM_API diam_status diam_op_cholesky_f64(int32_t n, double* A, int32_t lda, int32_t* info_host, void* stream);
 
+/* diam_op_cholesky_f64 with the trailing updates on the BF16 tensor cores, FP64-accurate by the error-free
+ * splitting of Ozaki, Ogita, Oishi and Rump (2012): each 64-wide panel row is cut into 7 BF16 integer
+ * slices under a power-of-two scale, slice products are summed exactly in FP32 tensor memory, grouped by
+ * weight and combined in FP64 (the dropped terms are of the size of an FP64 GEMM's rounding). This is the
+ * factorisation the BF16 sampler mode uses for its refresh. Allocates its workspace (7 x 64 x n BF16).
+ * Synchronises the stream. */
+DIAM_API diam_status diam_op_cholesky_f64_tc(int32_t n, double* A, int32_t lda, int32_t* info_host, void* stream);
+
 /* For nrows right-hand sides stored as rows of B (row r at B + r*ldb, n entries): B_r <- L^{-1} B_r with L
  * lower triangular (n x n, stride ldl, FP64). This is z = A_n^{-1}(x - x_ref) for every chain. */
 DIAM_API diam_status diam_op_trsm_lower_f64(int32_t n, int32_t nrows, const double* L, int32_t ldl, double* B, int32_t ldb,

@@ -78,6 +78,7 @@ struct diam_ctx {
     float* ws = nullptr;                                         // split-K partial target products (BF16 mode)
     int nchunk = 1, tsplit = 1;
     int bn_target = 128, bn_xi = 128;        // tile widths picked by the autotuner (BF16 mode)
+    OzakiWs oz;                              // BF16 mode: the refresh's trailing updates on the tensor cores
     // CUDA graph of one interval's n_lag steps (captured once; embeds buffer pointers and the DA switch)
     cudaGraphExec_t graph = nullptr;
     const void* graph_bsum = nullptr;
@@ -479,7 +480,7 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
         // C_n + eps diag(C_n): every variance loaded by the same relative amount (the skip / jitter rule)
         { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, inv_n, eps, c->Cw); count_launch(); }
         CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
-        CK(cholesky_f64(c->Cw, d, d, &c->ctl->chol_info, c->st));
+        CK(cholesky_f64(c->Cw, d, d, &c->ctl->chol_info, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status));
         CKS(sync_and_check(c));
         int info = 0;
         CK(cudaMemcpy(&info, &c->ctl->chol_info, sizeof(int), cudaMemcpyDeviceToHost));
@@ -691,6 +692,9 @@ static diam_status alloc_all(diam_ctx* c) {
         CKS(dalloc(c, &pd.mean, sizeof(double) * d));
     }
     if (c->bf) {
+        CKS(dalloc(c, &c->oz.SL, sizeof(uint16_t) * (size_t)d * 448));
+        CKS(dalloc(c, &c->oz.ex, sizeof(int) * (size_t)d));
+        c->oz.cap_rows = d;
         CKS(dalloc(c, &c->Lq64, sizeof(double) * d * d));
         CKS(dalloc(c, &c->Lq16, sizeof(uint16_t) * (size_t)d * c->ldk));
         CKS(dalloc(c, &c->op_hi, sizeof(uint16_t) * (size_t)P * c->ldk));

@@ -85,7 +85,7 @@ __global__ void zero_upper_kernel(double* A, int lda, int n) {
 
 static int row_blocks(int nrows) { return max(1, min((nrows + 7) / 8, 148 * 8)); }
 
-cudaError_t cholesky_f64(double* A, int n, int lda, int* info_dev, cudaStream_t st) {
+cudaError_t cholesky_f64(double* A, int n, int lda, int* info_dev, cudaStream_t st, OzakiWs* oz, int* status_dev) {
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         int nb = min(CH_NB, n - k0);
         { chol_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, nb, info_dev); count_launch(); }
@@ -95,9 +95,15 @@ cudaError_t cholesky_f64(double* A, int n, int lda, int* info_dev, cudaStream_t 
         { trsv_rows_kernel<<<row_blocks(rest), 256, 0, st>>>(A + (size_t)k0 * lda + k0, lda, nb,
                                                              A + (size_t)k1 * lda + k0, lda, rest); count_launch(); }
         // trailing lower triangle: A[k1+n][k1+m] -= sum_k L[k1+m][k0+k] L[k1+n][k0+k]
-        EpiStore epi{A + (size_t)k1 * lda + k1, lda, -1.0, nullptr, 1.0};
-        cudaError_t e = gemm_f64<true, true>(rest, rest, nb, A + (size_t)k1 * lda + k0, lda,
-                                             A + (size_t)k1 * lda + k0, lda, TileRange{0, 1}, epi, st);
+        cudaError_t e;
+        if (oz && nb == CH_NB && rest >= 128) {
+            e = ozaki_trailing_update(A + (size_t)k1 * lda + k0, lda, rest, A + (size_t)k1 * lda + k1, lda, *oz,
+                                      status_dev, st);
+        } else {
+            EpiStore epi{A + (size_t)k1 * lda + k1, lda, -1.0, nullptr, 1.0};
+            e = gemm_f64<true, true>(rest, rest, nb, A + (size_t)k1 * lda + k0, lda, A + (size_t)k1 * lda + k0, lda,
+                                     TileRange{0, 1}, epi, st);
+        }
         if (e != cudaSuccess) return e;
     }
     dim3 g(max(1, min(32, (n + 255) / 256)), n);

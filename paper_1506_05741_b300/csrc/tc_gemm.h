@@ -8,7 +8,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct CUtensorMap_st;
+
 namespace diam {
+
+// 2D BF16 tensor map over rows x ld (ld = padded row length, multiple of 64), box 64 x box_rows, 128-byte
+// swizzle; cached per (pointer, rows, ld, box_rows).
+bool make_map(struct CUtensorMap_st* map, const void* ptr, int rows, int ld, int box_rows);
 
 enum TcMode : int {
     TC_STORE = 0,   // D[n*ldd + m] = scale * acc (FP32), scale = *scale_dev

@@ -79,6 +79,40 @@ def test_cholesky_matches_oracle(d):
     assert np.all(np.triu(L, 1) == 0)
 
 
+@pytest.mark.parametrize("d", [130, 300, 1000])
+def test_tensor_core_cholesky_matches_oracle(d):
+    """The Ozaki-split tensor-core trailing update keeps the factorisation FP64-accurate."""
+    torch = _torch()
+    l = _lib()
+    l.diam_op_cholesky_f64_tc.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    l.diam_op_cholesky_f64_tc.restype = ctypes.c_int
+    Cm = workloads.spd_matrix(d, 700 + d, cond=1e6)
+    A = torch.from_numpy(Cm.copy()).cuda()
+    info = ctypes.c_int32(-1)
+    assert l.diam_op_cholesky_f64_tc(d, A.data_ptr(), d, ctypes.byref(info), None) == 0
+    assert info.value == 0
+    L = A.cpu().numpy()
+    ref = oracle.cholesky(Cm)
+    assert np.max(np.abs(L - ref)) <= 1e-11 * np.max(np.abs(ref))
+    assert np.linalg.norm(L @ L.T - Cm) / np.linalg.norm(Cm) < 1e-14
+
+
+def test_tensor_core_cholesky_large_reconstructs():
+    torch = _torch()
+    l = _lib()
+    l.diam_op_cholesky_f64_tc.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    d = 4096
+    Cm = workloads.spd_matrix(d, 11, cond=1e5)
+    A = torch.from_numpy(Cm.copy()).cuda()
+    info = ctypes.c_int32(-1)
+    assert l.diam_op_cholesky_f64_tc(d, A.data_ptr(), d, ctypes.byref(info), None) == 0 and info.value == 0
+    Cg = torch.from_numpy(Cm).cuda()
+    assert (torch.linalg.norm(A @ A.T - Cg) / torch.linalg.norm(Cg)).item() < 1e-14
+    B = torch.from_numpy(Cm.copy()).cuda()
+    assert l.diam_op_cholesky_f64(d, B.data_ptr(), d, ctypes.byref(info), None) == 0 and info.value == 0
+    assert (torch.abs(A - B).max() / torch.abs(B).max()).item() < 1e-12
+
+
 def test_cholesky_reports_indefinite_and_large_reconstructs():
     torch = _torch()
     l = _lib()
