@@ -186,8 +186,9 @@ DIAM_API diam_status diam_load(diam_ctx* ctx, const void* buf, size_t size);
 
 /* ---------------------------------------------------------------------------------------------------
  * Delayed acceptance with a learned surrogate (not in the paper; two-stage Metropolis-Hastings of
- * Christen & Fox, 2005). A small MLP s(x) ~ log pi(x) (d -> h1 -> h2 -> 1, GELU, BF16 weights, FP32
- * accumulation on the tensor cores) screens every proposal first:
+ * Christen & Fox, 2005). The surrogate s(x) ~ log pi(x) is the target's exact O(d) terms plus a small MLP
+ * (d -> h1 -> h2 -> 1, GELU, BF16 weights, FP32 accumulation on the tensor cores) that learns the
+ * linear-map terms (the expensive part). It screens every proposal first:
  *   stage 1: accept with probability min(1, exp(s(x*) - s(x) + q(x*) - q(x)))       (uniform tag 3)
  *   stage 2: for the survivors only, log pi(x*) is evaluated and the move is accepted with probability
  *            min(1, exp(log pi(x*) - log pi(x) - s(x*) + s(x)))                     (uniform tag 1)

@@ -28,15 +28,22 @@ DIAM_API diam_status diam_op_cholesky_f64(int32_t n, double* A, int32_t lda, int
 /* diam_op_cholesky_f64 with the trailing updates on the BF16 tensor cores, FP64-accurate by the error-free
  * splitting of Ozaki, Ogita, Oishi and Rump (2012): each 64-wide panel row is cut into 7 BF16 integer
  * slices under a power-of-two scale, slice products are summed exactly in FP32 tensor memory, grouped by
- * weight and combined in FP64 (the dropped terms are of the size of an FP64 GEMM's rounding). This is the
- * factorisation the BF16 sampler mode uses for its refresh. Allocates its workspace (7 x 64 x n BF16).
- * Synchronises the stream. */
+ * weight and combined as 64-bit integers (the dropped terms are of the size of an FP64 GEMM's rounding).
+ * This is the factorisation the BF16 sampler mode uses for its refresh. Allocates its workspace
+ * (7 x 64 x n BF16). Synchronises the stream; DIAM_ETIMEOUT on a device-side timeout. */
 DIAM_API diam_status diam_op_cholesky_f64_tc(int32_t n, double* A, int32_t lda, int32_t* info_host, void* stream);
 
 /* For nrows right-hand sides stored as rows of B (row r at B + r*ldb, n entries): B_r <- L^{-1} B_r with L
  * lower triangular (n x n, stride ldl, FP64). This is z = A_n^{-1}(x - x_ref) for every chain. */
 DIAM_API diam_status diam_op_trsm_lower_f64(int32_t n, int32_t nrows, const double* L, int32_t ldl, double* B, int32_t ldb,
                                    void* stream);
+
+/* diam_op_trsm_lower_f64 with the block updates B[:, k1:] -= Y L[k1:, block]^T on the BF16 tensor cores,
+ * FP64-accurate by the same Ozaki splitting as diam_op_cholesky_f64_tc (the re-solve of z after a refresh
+ * in the BF16 sampler mode). Allocates its workspace (7 x 64 x (n + nrows) BF16). Synchronises the stream;
+ * DIAM_ETIMEOUT on a device-side timeout. */
+DIAM_API diam_status diam_op_trsm_lower_f64_tc(int32_t n, int32_t nrows, const double* L, int32_t ldl, double* B,
+                                               int32_t ldb, void* stream);
 
 /* D[n*ldd + m] = scale * sum_k A[m*lda + k] (B[n*ldb + k] + B2[n*ldb + k]) on the tensor cores (tcgen05):
  * A (M x K) and B, B2 (N x K) BF16 bits, K-contiguous, K, lda, ldb multiples of 64, 16-byte aligned

@@ -218,7 +218,7 @@ static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
     const int d = c->d, P = c->P;
     if (c->kind == TK_REF) {
         { diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, src, (const T*)c->xref, c->work); count_launch(); }
-        CK(trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st));
+        CK(trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status));
         { set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)nullptr, nullptr, inv_infl2(c), out); count_launch(); }
         return DIAM_OK;
     }
@@ -244,7 +244,7 @@ static diam_status rewhiten(diam_ctx* c) {
     const int d = c->d, P = c->P;
     int e0 = ph_begin(c, PH_REWHITEN);
     { diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, (const T*)c->X, (const T*)c->xref, c->work); count_launch(); }
-    CK(trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st));
+    CK(trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status));
     { set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)c->Z, c->q, inv_infl2(c),
                                                 c->kind == TK_REF ? c->lp : nullptr); count_launch(); }
     CK(cudaGetLastError());
@@ -695,6 +695,9 @@ static diam_status alloc_all(diam_ctx* c) {
         CKS(dalloc(c, &c->oz.SL, sizeof(uint16_t) * (size_t)d * 448));
         CKS(dalloc(c, &c->oz.ex, sizeof(int) * (size_t)d));
         c->oz.cap_rows = d;
+        CKS(dalloc(c, &c->oz.SL2, sizeof(uint16_t) * (size_t)P * 448));
+        CKS(dalloc(c, &c->oz.ex2, sizeof(int) * (size_t)P));
+        c->oz.cap2 = P;
         CKS(dalloc(c, &c->Lq64, sizeof(double) * d * d));
         CKS(dalloc(c, &c->Lq16, sizeof(uint16_t) * (size_t)d * c->ldk));
         CKS(dalloc(c, &c->op_hi, sizeof(uint16_t) * (size_t)P * c->ldk));

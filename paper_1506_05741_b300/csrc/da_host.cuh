@@ -63,7 +63,12 @@ static diam_status da_forward(diam_ctx* c, int rows, const uint16_t* U, uint16_t
 static diam_status da_refresh_s_cur(diam_ctx* c) {
     DaState* a = c->da;
     { mlp_input_kernel<float><<<dim3(c->P, 4), kThreads, 0, c->st>>>(c->d, (const float*)c->X, a->shift, a->scale, a->U, c->ldk); count_launch(); }
-    return da_forward(c, c->P, a->U, a->H1, a->H2, nullptr, nullptr, a->s_cur);
+    CKS(da_forward(c, c->P, a->U, a->H1, a->H2, nullptr, nullptr, a->s_cur));
+    // plus the exact O(d) terms of the current states
+    { od_terms_kernel<float><<<c->P, kThreads, 0, c->st>>>(c->d, (const float*)c->X, c->lpo, c->tg, nullptr, nullptr, c->ldk); count_launch(); }
+    { add_kernel<<<blocks_for(c->P), kThreads, 0, c->st>>>(c->P, c->lpo, a->s_cur); count_launch(); }
+    CK(cudaGetLastError());
+    return DIAM_OK;
 }
 
 // Forward + backward on the minibatch in a->Xb / a->tb (B rows): gradients into a->g*, loss parts.
@@ -172,7 +177,8 @@ static diam_status da_train_now(diam_ctx* c, double* rmse_out) {
     return sync_and_check(c);
 }
 
-// Per-step DA path (BF16 mode, linear-map target): screen, compact, exact test for the survivors.
+// Per-step DA path (BF16 mode, linear-map target): screen, compact, exact test for the survivors. The
+// network estimates the linear-map part of log pi only; the O(d) terms enter the surrogate exactly.
 static diam_status da_step(diam_ctx* c) {
     DaState* a = c->da;
     const int P = c->P;
@@ -182,7 +188,7 @@ static diam_status da_step(diam_ctx* c) {
         CKS(da_forward(c, P, a->U, a->H1, a->H2, nullptr, nullptr, a->s_prop));
     }
     const int nthr = (P + 31) / 32 * 32;
-    { stage1_kernel<<<1, nthr, 0, c->st>>>(P, c->nchunk, c->key, c->ctl, a->active ? 1 : 0, c->qpart, inv_infl2(c), c->q, a->s_prop,
+    { stage1_kernel<<<1, nthr, 0, c->st>>>(P, c->nchunk, c->key, c->ctl, a->active ? 1 : 0, c->qpart, c->lpart, inv_infl2(c), c->q, a->s_prop,
                                          a->s_cur, a->qsave, a->idx, c->accf, nullptr, a->cnt, c->tr); count_launch(); }
     { gather_rows_kernel<<<P, kThreads, 0, c->st>>>(a->cnt, a->idx, c->op_hi, c->op_lo, a->Chi, a->Clo, c->ldk); count_launch(); }
     CK(cudaGetLastError());
@@ -199,7 +205,7 @@ static diam_status da_step(diam_ctx* c) {
                            c->st, &used, c->bn_target));
     { finish_da_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y, 1.0 / (2.0 * c->sigma * c->sigma),
                                                 c->kind == TK_TANH, c->nchunk, c->key, c->lpart, a->qsave, a->idx, a->cnt,
-                                                a->s_prop, a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, a->Chi, a->ring_x,
+                                                a->active ? 1 : 0, a->s_prop, a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, a->Chi, a->ring_x,
                                                 a->ring_lp, (long long)a->cfg.ring, c->ldk); count_launch(); }
     { ring_advance_kernel<<<1, 1, 0, c->st>>>(a->cnt, (long long)a->cfg.ring); count_launch(); }
     CK(cudaGetLastError());

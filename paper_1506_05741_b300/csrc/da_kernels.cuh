@@ -47,10 +47,11 @@ struct DaCounters {
 };
 
 // Stage 1 for every chain (one block, P <= 1024 threads): q(x*) from the proposal's partial sums, then
-// with the surrogate active: log a1 = s(x*) - s(x) + q(x*) - q(x), pass iff log u1 < log a1 (tag 3);
-// inactive: every chain passes. The passing chains are compacted in chain order into idx[0..count).
+// with the surrogate active: s(x*) = the exact O(d) terms + the network's value of the linear-map terms,
+// log a1 = s(x*) - s(x) + q(x*) - q(x), pass iff log u1 < log a1 (tag 3); inactive: every chain passes. The passing chains are compacted in chain order into idx[0..count).
 __global__ void stage1_kernel(int P, int nchunk, Key key, const Ctl* ctl, int active, const double* __restrict__ qpart,
-                              double inv_infl2, const double* __restrict__ q, const double* __restrict__ s_prop,
+                              const double* __restrict__ lpart_, double inv_infl2, const double* __restrict__ q,
+                              double* __restrict__ s_prop,
                               const double* __restrict__ s_cur, double* __restrict__ qsave, int* __restrict__ idx,
                               int8_t* __restrict__ accf, double* __restrict__ lp_nan_trace, DaCounters* cnt,
                               TraceDev tr) {
@@ -64,6 +65,10 @@ __global__ void stage1_kernel(int P, int nchunk, Key key, const Ctl* ctl, int ac
         const double qpp = 0.5 * qs * inv_infl2;
         qsave[p] = qpp;
         if (active) {
+            // s(x*) = exact O(d) terms of log pi + the network's estimate of the linear-map terms
+            double lo = 0.0;
+            for (int c = 0; c < nchunk; ++c) lo += lpart_[(size_t)c * P + p];
+            s_prop[p] += lo;
             const double loga1 = s_prop[p] - s_cur[p] + qpp - q[p];
             const double u1 = uniform53(key, t, (uint32_t)p, TAG_UDA);
             pass = isfinite(loga1) && (log(u1) < loga1);
@@ -125,7 +130,7 @@ __global__ void __launch_bounds__(256) finish_da_kernel(int P, int dy, int nspli
                                                          int nchunk, Key key,
                                                          const double* __restrict__ lpart,
                                                          const double* __restrict__ qsave, const int* __restrict__ idx,
-                                                         const DaCounters* cnt, const double* __restrict__ s_prop,
+                                                         const DaCounters* cnt, int active, const double* __restrict__ s_prop,
                                                          double* s_cur, double* lp, double* q, int8_t* accf, Ctl* ctl,
                                                          TraceDev tr, const uint16_t* __restrict__ chi,
                                                          uint16_t* __restrict__ ring_x, float* __restrict__ ring_lp,
@@ -148,15 +153,18 @@ __global__ void __launch_bounds__(256) finish_da_kernel(int P, int dy, int nspli
         }
     }
     acc = block_sum(acc, sh);
+    const double lmap = acc;   // the linear-map part of log pi(x*): what the network learns
     for (int c = 0; c < nchunk; ++c) acc += lpart[(size_t)c * P + p];
     const long long slot = (cnt->head + k) % ring_cap;
     const uint4* src = reinterpret_cast<const uint4*>(chi + (size_t)k * ldk);
     uint4* dst = reinterpret_cast<uint4*>(ring_x + (size_t)slot * ldk);
     for (int j = threadIdx.x; j < ldk / 8; j += blockDim.x) dst[j] = src[j];
     if (threadIdx.x == 0) {
-        ring_lp[slot] = (float)acc;
+        ring_lp[slot] = (float)lmap;
         const double lpp = acc, qpp = qsave[p];
-        const double loga = lpp - lp[p] - s_prop[p] + s_cur[p];
+        // stage 2 (Christen & Fox): log pi(x*) - log pi(x) - s(x*) + s(x); with stage 1 off this is the plain
+        // Metropolis-Hastings ratio of Algorithm 1, log pi(x*) - log pi(x) + q(x*) - q(x)
+        const double loga = active ? (lpp - lp[p] - s_prop[p] + s_cur[p]) : (lpp - lp[p] + qpp - q[p]);
         const bool finite = isfinite(lpp);
         const double u = uniform53(key, t, (uint32_t)p, TAG_U);
         const int a = finite && (log(u) < loga);
@@ -167,12 +175,17 @@ __global__ void __launch_bounds__(256) finish_da_kernel(int P, int dy, int nspli
         if (a) {
             lp[p] = lpp;
             q[p] = qpp;
-            s_cur[p] = s_prop[p];
+            if (active) s_cur[p] = s_prop[p];
             atomicAdd(&ctl->acc_block, 1ull);
         }
         if (!finite) atomicAdd(&ctl->nonfinite, 1ull);
         accf[p] = (int8_t)a;
     }
+}
+
+__global__ void add_kernel(int n, const double* __restrict__ a, double* __restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] += a[i];
 }
 
 __global__ void ring_advance_kernel(DaCounters* cnt, long long cap) {

@@ -57,30 +57,43 @@ diam_status diam_op_cholesky_f64(int32_t n, double* A, int32_t lda, int32_t* inf
     return cudaStreamSynchronize(st) == cudaSuccess ? DIAM_OK : DIAM_ECUDA;
 }
 
+// Workspace of the tensor-core (Ozaki-split) updates for one op call, freed on scope exit.
+struct OzScope {
+    OzakiWs ws;
+    bool ok = true;
+    OzScope(int rows, int rows2) {
+        ws.cap_rows = rows;
+        ws.cap2 = rows2;
+        ok = cudaMalloc(&ws.SL, sizeof(uint16_t) * (size_t)rows * 448) == cudaSuccess &&
+             cudaMalloc(&ws.ex, sizeof(int) * (size_t)rows) == cudaSuccess &&
+             (rows2 == 0 || (cudaMalloc(&ws.SL2, sizeof(uint16_t) * (size_t)rows2 * 448) == cudaSuccess &&
+                             cudaMalloc(&ws.ex2, sizeof(int) * (size_t)rows2) == cudaSuccess));
+    }
+    ~OzScope() {
+        cudaFree(ws.SL);
+        cudaFree(ws.ex);
+        cudaFree(ws.SL2);
+        cudaFree(ws.ex2);
+    }
+};
+
 diam_status diam_op_cholesky_f64_tc(int32_t n, double* A, int32_t lda, int32_t* info_host, void* stream) {
     if (!A || n <= 0 || lda < n || !info_host) return DIAM_EINVAL;
     OpScratch* sc = op_scratch();
     if (!sc) return DIAM_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    OzakiWs oz;
-    oz.cap_rows = n;
-    if (cudaMalloc(&oz.SL, sizeof(uint16_t) * (size_t)n * 448) != cudaSuccess) return DIAM_ENOMEM;
-    if (cudaMalloc(&oz.ex, sizeof(int) * (size_t)n) != cudaSuccess) {
-        cudaFree(oz.SL);
-        return DIAM_ENOMEM;
-    }
+    OzScope oz(n, 0);
+    if (!oz.ok) return DIAM_ENOMEM;
     diam_status r = DIAM_OK;
     if (cudaMemsetAsync(&sc->info, 0, sizeof(int), st) != cudaSuccess ||
         cudaMemsetAsync(&sc->status, 0, sizeof(int), st) != cudaSuccess ||
-        cholesky_f64(A, n, lda, &sc->info, st, &oz, &sc->status) != cudaSuccess)
+        cholesky_f64(A, n, lda, &sc->info, st, &oz.ws, &sc->status) != cudaSuccess)
         r = DIAM_ECUDA;
     int status = 0;
     if (r == DIAM_OK && (cudaMemcpyAsync(info_host, &sc->info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                          cudaMemcpyAsync(&status, &sc->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess))
         r = DIAM_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) r = DIAM_ECUDA;
-    cudaFree(oz.SL);
-    cudaFree(oz.ex);
     if (r == DIAM_OK && status == DEV_TIMEOUT) r = DIAM_ETIMEOUT;
     return r;
 }
@@ -89,6 +102,26 @@ diam_status diam_op_trsm_lower_f64(int32_t n, int32_t nrows, const double* L, in
                                    void* stream) {
     if (!L || !B || n <= 0 || nrows < 0 || ldl < n || ldb < n) return DIAM_EINVAL;
     return trsm_lower_f64(L, ldl, n, B, ldb, nrows, (cudaStream_t)stream) == cudaSuccess ? DIAM_OK : DIAM_ECUDA;
+}
+
+diam_status diam_op_trsm_lower_f64_tc(int32_t n, int32_t nrows, const double* L, int32_t ldl, double* B, int32_t ldb,
+                                      void* stream) {
+    if (!L || !B || n <= 0 || nrows < 0 || ldl < n || ldb < n) return DIAM_EINVAL;
+    if (nrows == 0) return DIAM_OK;
+    OpScratch* sc = op_scratch();
+    if (!sc) return DIAM_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    OzScope oz(n, nrows);
+    if (!oz.ok) return DIAM_ENOMEM;
+    diam_status r = DIAM_OK;
+    int status = 0;
+    if (cudaMemsetAsync(&sc->status, 0, sizeof(int), st) != cudaSuccess ||
+        trsm_lower_f64(L, ldl, n, B, ldb, nrows, st, &oz.ws, &sc->status) != cudaSuccess ||
+        cudaMemcpyAsync(&status, &sc->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        r = DIAM_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) r = DIAM_ECUDA;
+    if (r == DIAM_OK && status == DEV_TIMEOUT) r = DIAM_ETIMEOUT;
+    return r;
 }
 
 diam_status diam_op_gemm_bf16_tile(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda,

@@ -1,17 +1,21 @@
-// ozaki.cu -- FP64-accurate rank-64 trailing update of the Cholesky refresh on the BF16 tensor cores.
+// ozaki.cu -- FP64-accurate rank-64 updates C -= A B^T on the BF16 tensor cores.
 //
-// The refresh factors C_n = A_n A_n^T in FP64 (Algorithm 1); its trailing updates C[n][m] -= sum_k P_nk P_mk
-// (P the 64-wide panel) hold nearly all of its d^3/3 flops, and B300 runs FP64 at about 1/1500 of its BF16
-// tensor rate. The update is computed here by the error-free splitting of Ozaki, Ogita, Oishi and Rump
-// (Numer. Algorithms 59, 2012), with BF16 slices:
-//   - each panel row i is scaled by 2^-e_i (e_i: max_k |P_ik| < 2^e_i) and cut into 7 slices of integers
-//     |S_a| <= 128, P_ik = 2^e_i sum_a S_a[i][k] 2^(-7-8a) + (a remainder below 2^(e_i-63));
+// The refresh factors C_n = A_n A_n^T in FP64 (Algorithm 1) and then re-solves z = A_n^{-1}(x - x_ref) for
+// every chain; the rank-64 updates of the blocked factorisation and of the blocked triangular solve hold
+// nearly all of their flops, and B300 runs FP64 at about 1/1500 of its BF16 tensor rate. The updates are
+// computed here by the error-free splitting of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms 59, 2012),
+// with BF16 slices:
+//   - each operand row i (64 entries) is scaled by 2^-e_i (e_i: max_k |P_ik| < 2^e_i), rounded to the
+//     integer R_ik = round(P_ik 2^(55 - e_i)) (|R| <= 2^55) and cut into 7 signed base-256 digits
+//     |S_a| <= 128: P_ik = 2^(e_i - 7) sum_a S_a[i][k] 2^(-8a) up to 2^(e_i - 56);
 //   - slice products are grouped by g = a + b: T_g = sum_{a+b=g} sum_k S_a[m][k] S_b[n][k] is an integer
 //     below 7 * 64 * 2^14 < 2^23, so its FP32 accumulation in tensor memory is exact;
-//   - the epilogue forms sum_g 2^(-8g) T_g in FP64 and subtracts 2^(e_m + e_n - 14) times it.
-// Terms with g >= 7 are dropped; their size, about 64 * 2^-56 |P_m| |P_n|, is that of an FP64 GEMM's
-// rounding bound. One CTA per 128 x 64 tile of the lower triangle keeps all 14 slice tiles in shared memory
-// and the 7 group accumulators in tensor memory (448 of its 512 columns).
+//   - the epilogue adds the T_g as 64-bit integers, I = sum_{g<6} T_g 2^(40-8g) + floor(T_6 / 2^8)
+//     (|I| < 2^61), and subtracts I 2^(e_m + e_n - 54) with one FP64 fused multiply-add.
+// Terms with g >= 7 and the low bits of T_6 are dropped; their size, about 64 * 2^-56 |P_m| |P_n|, is that
+// of an FP64 GEMM's own rounding bound. Only one conversion and one FMA per output touch the FP64 pipe.
+// One CTA per 128 x 64 output tile keeps all 14 slice tiles in shared memory and the 7 group accumulators
+// in tensor memory (448 of its 512 columns).
 #include "linalg.h"
 #include "tc_common.cuh"
 #include "tc_gemm.h"
@@ -20,34 +24,45 @@ namespace diam {
 
 constexpr int OZ_S = 7, OZ_K = 64, OZ_LD = OZ_S * OZ_K, OZ_BN = 64;
 
-// One warp per panel row: exponent and the 7 BF16 slices (exact integers) of the row's 64 entries.
+// 2^e as a double (exact for normal exponents).
+__device__ __forceinline__ double pow2(int e) {
+    return (e >= -1022 && e <= 1023) ? __hiloint2double((e + 1023) << 20, 0) : ldexp(1.0, e);
+}
+
+// One warp per operand row: exponent and the 7 BF16 slices (exact integers) of the row's 64 entries.
 __global__ void ozaki_slice_kernel(const double* __restrict__ P, int lda, int rows, uint16_t* __restrict__ SL,
                                    int* __restrict__ ex) {
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= rows) return;
-    double v[2] = {P[(size_t)row * lda + lane], P[(size_t)row * lda + lane + 32]};
+    const double v[2] = {P[(size_t)row * lda + lane], P[(size_t)row * lda + lane + 32]};
     double m = fmax(fabs(v[0]), fabs(v[1]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     const int e = (m > 0.0) ? ilogb(m) + 1 : 0;   // m < 2^e
+    const double sc = pow2(55 - e);
+    uint16_t* out = SL + (size_t)row * OZ_LD + lane;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        double r = ldexp(v[h], 7 - e);            // |r| < 128, exact scaling
+        long long R = __double2ll_rn(v[h] * sc);  // exact scaling, then one rounding: |R| <= 2^55
 #pragma unroll
         for (int a = 0; a < OZ_S; ++a) {
-            const double s = rint(r);             // |s| <= 128: exact in BF16
-            SL[(size_t)row * OZ_LD + a * OZ_K + lane + 32 * h] = (uint16_t)(__float_as_uint((float)s) >> 16);
-            r = (r - s) * 256.0;                  // exact: |r - s| <= 1/2
+            const int s = 48 - 8 * a;
+            const long long S = (s > 0) ? ((R + (1ll << (s - 1))) >> s) : R;   // |S| <= 128
+            R -= S * (1ll << s);                                                 // |R| <= 2^(s-1)
+            out[a * OZ_K + 32 * h] = (uint16_t)(__float_as_uint((float)S) >> 16);   // exact in BF16
         }
     }
     if (lane == 0) ex[row] = e;
 }
 
+// C[n][m] -= sum_k A[m][k] B[n][k] for m < Ma, n < Nb (and n >= m when lower), from the slices of A
+// (tensor map tmA, 128-row boxes) and of B (tmB, 64-row boxes).
 __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                              const __grid_constant__ CUtensorMap tmB, int rows,
-                                                              const int* __restrict__ ex, double* __restrict__ Cm,
-                                                              int ldc, int* status) {
+                                                              const __grid_constant__ CUtensorMap tmB, int Ma, int Nb,
+                                                              const int* __restrict__ exA, const int* __restrict__ exB,
+                                                              double* __restrict__ Cm, int ldc, int lower,
+                                                              int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr uint32_t A_BYTES = 128 * OZ_K * 2, B_BYTES = OZ_BN * OZ_K * 2;
@@ -59,7 +74,7 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * OZ_BN;
-    if (n0 + OZ_BN - 1 < m0 || n0 >= rows) return;    // tile strictly above the diagonal, or past the rows
+    if ((lower && n0 + OZ_BN - 1 < m0) || n0 >= Nb || m0 >= Ma) return;   // nothing of this tile is updated
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(full), 1);
@@ -110,26 +125,35 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
     if (ok) {
         const int row = warp * 32 + lane;
         const int m = m0 + row;
-        const bool vm = m < rows;
-        const int em = vm ? ex[m] : 0;
+        const bool vm = m < Ma;
+        const int em = vm ? exA[m] : 0;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
         for (int c = 0; c < OZ_BN / 32; ++c) {
-            double acc[32];
+            long long acc[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+            for (int j = 0; j < 32; ++j) acc[j] = 0;
 #pragma unroll 1
-            for (int g = OZ_S - 1; g >= 0; --g) {     // small groups first
+            for (int g = 0; g < OZ_S; ++g) {
                 uint32_t r[32];
                 tmem_ld32(trow + (uint32_t)(g * OZ_BN + c * 32), r);
+                if (g < OZ_S - 1) {
+                    const int sh = 40 - 8 * g;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc[j] += ldexp((double)__uint_as_float(r[j]), -8 * g);
+                    for (int j = 0; j < 32; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(r[j])) * (1ll << sh);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[j] += (long long)(__float2int_rn(__uint_as_float(r[j])) >> 8);
+                }
             }
             if (vm) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int n = n0 + c * 32 + j;
-                    if (n < rows && n >= m) Cm[(size_t)n * ldc + m] -= ldexp(acc[j], em + ex[n] - 14);
+                    if (n < Nb && (!lower || n >= m)) {
+                        double* p = Cm + (size_t)n * ldc + m;
+                        *p = fma(-(double)acc[j], pow2(em + exB[n] - 54), *p);
+                    }
                 }
             }
         }
@@ -145,23 +169,44 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
 }
 
+static size_t update_smem() { return 1024 + (size_t)OZ_S * (128 * OZ_K * 2 + OZ_BN * OZ_K * 2) + 256; }
+
+static cudaError_t launch_update(const uint16_t* SA, int Ma, const int* exA, const uint16_t* SB, int Nb,
+                                 const int* exB, double* Cm, int ldc, int lower, int* status, cudaStream_t st) {
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, SA, Ma, OZ_LD, 128) || !make_map(&mB, SB, Nb, OZ_LD, OZ_BN)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(ozaki_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_smem());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((Ma + 127) / 128, (Nb + OZ_BN - 1) / OZ_BN);
+    { ozaki_update_kernel<<<grid, 128, update_smem(), st>>>(mA, mB, Ma, Nb, exA, exB, Cm, ldc, lower, status); count_launch(); }
+    return cudaGetLastError();
+}
+
+static void slice(const double* P, int lda, int rows, uint16_t* SL, int* ex, cudaStream_t st) {
+    ozaki_slice_kernel<<<(rows + 7) / 8, 256, 0, st>>>(P, lda, rows, SL, ex);
+    count_launch();
+}
+
 cudaError_t ozaki_trailing_update(const double* Pnl, int lda, int rows, double* Cm, int ldc, OzakiWs& ws, int* status,
                                   cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
     if (rows > ws.cap_rows) return cudaErrorInvalidValue;
-    { ozaki_slice_kernel<<<(rows + 7) / 8, 256, 0, st>>>(Pnl, lda, rows, ws.SL, ws.ex); count_launch(); }
-    CUtensorMap mA, mB;
-    if (!make_map(&mA, ws.SL, rows, OZ_LD, 128) || !make_map(&mB, ws.SL, rows, OZ_LD, OZ_BN)) return cudaErrorInvalidValue;
-    const size_t smem = 1024 + (size_t)OZ_S * (128 * OZ_K * 2 + OZ_BN * OZ_K * 2) + 256;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(ozaki_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    dim3 grid((rows + 127) / 128, (rows + OZ_BN - 1) / OZ_BN);
-    { ozaki_update_kernel<<<grid, 128, smem, st>>>(mA, mB, rows, ws.ex, Cm, ldc, status); count_launch(); }
-    return cudaGetLastError();
+    slice(Pnl, lda, rows, ws.SL, ws.ex, st);
+    return launch_update(ws.SL, rows, ws.ex, ws.SL, rows, ws.ex, Cm, ldc, 1, status, st);
+}
+
+cudaError_t ozaki_gemm_update(const double* A, int lda, int Ma, const double* B, int ldb, int Nb, double* Cm, int ldc,
+                              OzakiWs& ws, int* status, cudaStream_t st) {
+    if (Ma <= 0 || Nb <= 0) return cudaSuccess;
+    if (Ma > ws.cap_rows || Nb > ws.cap2) return cudaErrorInvalidValue;
+    slice(A, lda, Ma, ws.SL, ws.ex, st);
+    slice(B, ldb, Nb, ws.SL2, ws.ex2, st);
+    return launch_update(ws.SL, Ma, ws.ex, ws.SL2, Nb, ws.ex2, Cm, ldc, 0, status, st);
 }
 
 }  // namespace diam

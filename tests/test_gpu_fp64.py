@@ -147,6 +147,29 @@ def test_trsm_matches_forward_substitution():
         assert np.max(np.abs(Y[r] - want)) <= 1e-12 * max(1.0, np.max(np.abs(want)))
 
 
+@pytest.mark.parametrize("d,rows", [(200, 7), (1000, 300), (4096, 256)])
+def test_tensor_core_trsm_matches_forward_substitution(d, rows):
+    """Block updates on the tensor cores (Ozaki split) keep the re-solve FP64-accurate: ragged row and
+    column tiles, and the 4096 x 256 shape of the refresh's re-solve."""
+    torch = _torch()
+    l = _lib()
+    f = l.diam_op_trsm_lower_f64_tc
+    I32, P = ctypes.c_int32, ctypes.c_void_p
+    f.argtypes = [I32, I32, P, I32, P, I32, P]
+    f.restype = ctypes.c_int
+    Lm = np.linalg.cholesky(workloads.spd_matrix(d, 5 + d, cond=1e4))
+    B = np.random.default_rng(d).standard_normal((rows, d))
+    B[0] *= 1e-6                                   # rows of very different scale
+    Lg = torch.from_numpy(Lm).cuda()
+    Bg = torch.from_numpy(B.copy()).cuda()
+    assert f(d, rows, Lg.data_ptr(), d, Bg.data_ptr(), d, None) == 0
+    Y = Bg.cpu().numpy()
+    check = range(rows) if d <= 1000 else (0, 1, 77, rows - 1)
+    for r in check:
+        want = oracle.forward_sub(Lm, B[r])
+        assert np.max(np.abs(Y[r] - want)) <= 1e-12 * np.max(np.abs(want))
+
+
 def _q_tol(o):
     L, _, _ = o.factor()
     return max(Q_TOL, 4 * L.shape[0] * U * np.linalg.cond(L))
