@@ -1,11 +1,19 @@
 """Benchmark of the DIAM hot path on one B300 (or N replicas under torchrun).
 
 Workload (tanh4096): Bayesian tanh regression, d = 4096, d_y = 2048, prior N(0, diag(i^-2)), A (2048 x 4096)
-N(0, 1/4096) in FP32, y = tanh(A x*) + 0.05 eps; P = 256 chains, n_lag = 128, BF16 factor / noise / map on
-the tensor cores, FP32 chain states, FP64 Cholesky refresh and moment fold. A_0 = Cholesky of the prior
+N(0, 1/4096) in FP32, y = tanh(A x*) + 0.05 eps; P = 512 chains, n_lag = 128. A_0 = Cholesky of the prior
 covariance, x_0 drawn from the prior. One benchmark step = one interval of n_lag steps of all P chains
-(noise product, n_lag x (propose, target, accept), moment fold, beta rule and the Cholesky refresh that is
-due every interval). Metric: chain-steps/s = P n_lag steps / wall time of the interval, refreshes included.
+(noise product, n_lag x (propose, screen, target, accept), moment fold, beta rule and the Cholesky refresh
+that is due every interval). Three arms run the same workload from the same start:
+  mixed_da  (the headline value): BF16 factor / noise / map on the tensor cores, FP32 states, FP64-accurate
+            refresh and moment fold, plus delayed acceptance with the MLP surrogate 4096 -> 512 -> 512 -> 1
+            trained on the GPU (first training once 2e4 exactly evaluated pairs are in the 2e5-pair ring,
+            then every 20 synchronisations; stage 1 off while the held-out RMSE exceeds 0.5 nats);
+  mixed     the same without the surrogate;
+  fp64      the plain FP64 form (every kernel FP64, DFMA Cholesky).
+Metrics: chain-steps/s = P n_lag / device time of an interval (everything above included), and min-ESS/s =
+min over coordinates of the batch-means effective sample size of the timed window (batches = one interval
+of one chain) / the window's device time.
 
 Prints one JSON line (rank 0). --impl reference times the CPU oracle (the reference arm for this build).
 """
@@ -32,12 +40,15 @@ FP64_PEAK_TFLOPS = 1.25   # B300 nominal FP64 (vector and tensor), the profiling
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8, help="timed intervals (of n_lag steps each)")
+    ap.add_argument("--steps", type=int, default=8, help="timed intervals (of n_lag steps each) of the headline arm")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--P", type=int, default=256)
+    ap.add_argument("--P", type=int, default=512)
     ap.add_argument("--n-lag", type=int, default=128)
-    ap.add_argument("--fp64-steps", type=int, default=1, help="timed intervals of the plain FP64 form (0: skip)")
+    ap.add_argument("--no-da", action="store_true", help="headline arm without the surrogate")
+    ap.add_argument("--mixed-steps", type=int, default=-1, help="timed intervals of the mixed arm (-1: --steps, 0: skip)")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed intervals of the plain FP64 arm (0: skip)")
+    ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -109,10 +120,16 @@ def workload(P, n_lag):
     return run, ts, x0, C0
 
 
-def make_sampler(run, ts, x0, C0, prec, profile=0, stream=None):
+def make_sampler(run, ts, x0, C0, prec, da=False, profile=0, stream=None, keep_sums=0):
     import paper_1506_05741_b300 as dm
+    import workloads
     cfg = dm.default_config(ts.d, run.P, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed, prec=prec, profile=profile)
-    return dm.Sampler(cfg, ts, x0=x0, C0=C0, stream=stream)
+    cfg["keep_block_sums"] = keep_sums
+    s = dm.Sampler(cfg, ts, x0=x0, C0=C0, stream=stream)
+    if da:
+        dc = dm.da_default_config()
+        s.da_enable(dc, workloads.mlp_init(ts.d, dc["h1"], dc["h2"], seed=11))
+    return s
 
 
 def time_intervals(s, n_lag, K, torch, stream):
@@ -127,37 +144,96 @@ def time_intervals(s, n_lag, K, torch, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
-def roofline(prof, run, ts, K, pk, pk_src):
-    """Dominant phase of the profiled intervals, with its algorithmic work per launch."""
+def ess_window(xs, n_lag, mom0, mom1):
+    """Batch-means ESS per coordinate over a window of K intervals: xs (K, P, d) per-interval, per-chain sums;
+    mom0 / mom1 the pooled (mean, M2, n) at the window's ends. The window's variance comes from the moment
+    difference (Chan et al.'s pairwise update run backwards), its batch means are the interval means of each
+    chain; ESS_i = N s_i^2 / (b var(batch means)_i), capped at N."""
+    (m0, M20, n0), (m1, M21, n1) = mom0, mom1
+    N = n1 - n0
+    mw = (n1 * m1 - n0 * m0) / N
+    delta = mw - m0
+    m2w = np.diag(M21) - np.diag(M20) - delta * delta * (n0 * N / n1)
+    var = m2w / (N - 1)
+    bm = xs / float(n_lag)
+    nbm = bm.shape[0] * bm.shape[1]
+    vbm = ((bm - mw) ** 2).sum(axis=(0, 1)) / (nbm - 1)
+    ess = np.minimum(float(N), N * var / (n_lag * np.maximum(vbm, 1e-300)))
+    return ess, N
+
+
+def run_arm(name, run, ts, x0, C0, prec, da, W, K, torch, stream, dm, clocks_index=None):
+    """W warm-up intervals, then K timed intervals; chain-steps/s, ESS of the timed window, counters."""
+    s = make_sampler(run, ts, x0, C0, prec, da=da, stream=stream.cuda_stream, keep_sums=1)
+    s.run(W * run.n_lag)
+    mom0 = s.export_moments()
+    l0 = dm.kernel_launches()
+    clk = None
+    if clocks_index is not None:
+        with ClockSampler(clocks_index) as clk:
+            dt = time_intervals(s, run.n_lag, K, torch, stream)
+    else:
+        dt = time_intervals(s, run.n_lag, K, torch, stream)
+    launches = dm.kernel_launches() - l0
+    mom1 = s.export_moments()
+    xs, _ = s.block_sums(W + K)
+    ess, N = ess_window(xs[W:W + K], run.n_lag, mom0, mom1)
+    st = s.stats()
+    out = {"chain_steps_per_s": round(run.P * run.n_lag * K / dt, 1), "ms_per_step": round(dt / K * 1e3, 3),
+           "timed_intervals": K, "warmup_intervals": W, "min_ess": round(float(ess.min()), 1),
+           "min_ess_per_s": round(float(ess.min()) / dt, 2), "median_ess_per_s": round(float(np.median(ess)) / dt, 1),
+           "argmin_coordinate": int(np.argmin(ess)), "window_samples": int(N),
+           "accept_rate": round(st["accepted"] / max(1, st["steps"] * run.P), 4), "beta": round(st["beta"], 5),
+           "refreshes": st["refreshes"], "chol_attempts": st["chol_attempts"]}
+    if da:
+        dst = s.da_stats()
+        out["da"] = {"trainings": dst["trainings"], "active": int(dst["active"]),
+                     "last_rmse_nats": round(dst["last_rmse"], 4),
+                     "stage1_pass_rate": round(dst["stage1_passed"] / max(1, dst["stage1_tested"]), 4),
+                     "exact_evals_per_step": round(dst["exact_evals"] / max(1, st["steps"] * run.P), 4)}
+    s.close()
+    return out, dt, launches, clk
+
+
+def roofline(prof, run, ts, pk, pk_src):
+    """Per-phase achieved rate against its bound, from the profiled intervals; the dominant phase first."""
     d, dy, P, nl = ts.d, ts.d_y, run.P, run.n_lag
     N = P * nl
-    # algorithmic work per launch of each phase
+    sus = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    # algorithmic work per launch of each phase (a launch = one step, or one interval for noise / xi / fold /
+    # refresh / rewhiten / train)
     work = {
-        "refresh": ("alu", d ** 3 / 3.0 + d ** 2, "TFLOP/s", FP64_PEAK_TFLOPS),       # FP64 Cholesky
-        "xi_gemm": ("tensor", float(d) * d * N, "TFLOP/s", pk.get("bf16_tflops_sustained", pk["bf16_tflops"])),
-        "fold": ("tensor", float(d) * d * N, "TFLOP/s", pk.get("bf16_tflops_sustained", pk["bf16_tflops"])),
-        "target": ("tensor", 2.0 * dy * d * P * 2, "TFLOP/s", pk.get("bf16_tflops_sustained", pk["bf16_tflops"])),
-        # bytes per launch: propose reads x, z, xi (FP32), W (BF16), writes x*, z* (FP32) and the BF16 split
-        "propose": ("hbm", P * d * (4 + 4 + 4 + 2 + 4 + 4 + 2 + 2), "GB/s", pk["hbm_gbs"]),
-        # accept reads x*, z* and writes x, z (accepted chains) and the BF16 record; bound at full traffic
-        "accept": ("hbm", P * d * (4 + 4 + 4 + 4 + 2), "GB/s", pk["hbm_gbs"]),
-        "noise": ("hbm", N * d * 2, "GB/s", pk["hbm_gbs"]),
-        "rewhiten": ("alu", float(d) * d * P, "TFLOP/s", FP64_PEAK_TFLOPS),
+        # the FP64 Cholesky d^3/3 flops, computed FP64-accurate on the BF16 tensor cores (Ozaki split: 28
+        # slice products per rank-64 update) around a serial FP64 chain of diagonal blocks
+        "refresh": ("alu", d ** 3 / 3.0, "TFLOP/s", FP64_PEAK_TFLOPS),
+        "xi_gemm": ("tensor", float(d) * d * N, "TFLOP/s", sus),             # lower-triangular A_n W, 2 d^2 N / 2
+        "fold": ("tensor", float(d) * d * N, "TFLOP/s", sus),                # SYRK of the interval, lower half
+        "target": ("tensor", 2.0 * dy * d * P * 2, "TFLOP/s", sus),          # A x* with the hi + lo split
+        # bytes: propose reads x, z, xi (FP32), writes x*, z* (FP32) and the BF16 hi / lo split of x*
+        "propose": ("hbm", P * d * (4 + 4 + 4 + 4 + 4 + 2 + 2), "GB/s", pk["hbm_gbs"]),
+        # accept reads x*, z* and writes x, z and the FP32 record row
+        "accept": ("hbm", P * d * (4 + 4 + 4 + 4 + 4), "GB/s", pk["hbm_gbs"]),
+        "noise": ("hbm", N * d * 2, "GB/s", pk["hbm_gbs"]),                  # BF16 W for the interval
+        "rewhiten": ("alu", float(d) * d * P, "TFLOP/s", FP64_PEAK_TFLOPS),  # the triangular re-solve
+        "screen": ("tensor", 2.0 * P * (d * 512 + 512 * 512), "TFLOP/s", sus),
     }
     total = sum(ms for _, ms in prof.values())
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (cnt, ms) = dom
-    bound, units, unit, peak = work[name]
-    per_launch_s = ms / 1e3 / max(cnt, 1)
-    if unit == "TFLOP/s":
-        achieved = units / per_launch_s / 1e12
-    else:
-        achieved = units / per_launch_s / 1e9
-    shares = {k: round(v[1] / total, 4) for k, v in prof.items() if total > 0}
-    return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": unit,
-            "frac": round(achieved / peak, 4), "traffic": None, "launch_ms": round(per_launch_s * 1e3, 4),
-            "peak_source": ("nominal FP64 of the profiling recipe" if bound == "alu" else pk_src),
-            "phase_share": shares}
+    table = {}
+    for k, (cnt, ms) in prof.items():
+        if cnt == 0 or k not in work:
+            continue
+        bound, units, unit, peak = work[k]
+        per = ms / 1e3 / cnt
+        ach = units / per / (1e12 if unit == "TFLOP/s" else 1e9)
+        table[k] = {"share": round(ms / total, 4), "launch_ms": round(per * 1e3, 4), "bound": bound,
+                    "achieved": round(ach, 3), "unit": unit, "peak": peak, "frac": round(ach / peak, 4)}
+    dom = max(table, key=lambda k: table[k]["share"])
+    t = table[dom]
+    return {"kernel": dom, "bound": t["bound"], "achieved": t["achieved"], "peak": t["peak"], "unit": t["unit"],
+            "frac": t["frac"], "traffic": None, "launch_ms": t["launch_ms"],
+            "peak_source": ("nominal FP64 of the profiling recipe" if t["bound"] == "alu" else pk_src + " (sustained)"
+                            if t["bound"] == "tensor" else pk_src),
+            "phases": table}
 
 
 def cpu_leg(run, ts, x0, C0, seconds, cores):
@@ -173,8 +249,9 @@ def cpu_leg(run, ts, x0, C0, seconds, cores):
         steps += 1
     dt = time.time() - t0
     return {"value": round(Ps * steps / dt, 3), "unit": "chain-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{steps} steps x {Ps} chains of tanh4096 (FP64 oracle, OpenMP over chains; refresh-free "
-                      f"prefix: its amortised Cholesky is ~1.4% of the oracle's per-step work)"}
+            "sample": f"{steps} steps x {Ps} chains of tanh4096 (plain FP64 oracle, OpenMP over chains, no "
+                      f"surrogate; refresh-free prefix: its amortised Cholesky is ~1.4% of the oracle's per-step "
+                      f"work)"}
 
 
 def main():
@@ -185,20 +262,22 @@ def main():
     cores = os.cpu_count() or 1
     run, ts, x0, C0 = workload(args.P, args.n_lag)
     N = run.P * run.n_lag
+    da = not args.no_da
     config = {"workload": f"tanh4096: d={ts.d}, d_y={ts.d_y}, P={run.P}, n_lag={run.n_lag}, BF16 factor/noise/map, "
-                          f"FP32 states, FP64 Cholesky refresh every interval",
-              "d": ts.d, "d_y": ts.d_y, "P": run.P, "n_lag": run.n_lag,
+                          f"FP32 states, FP64-accurate Cholesky refresh every interval"
+                          + (", delayed acceptance with the 4096-512-512-1 MLP surrogate" if da else ""),
+              "d": ts.d, "d_y": ts.d_y, "P": run.P, "n_lag": run.n_lag, "delayed_acceptance": da,
               "step": "one interval: n_lag steps of all chains + moment fold + beta rule + Cholesky refresh",
-              "l2": "working set per interval > L2 (noise product 537 MB, BF16 noise 268 MB)",
+              "l2": "inputs larger than L2 (per interval: BF16 noise 537 MB, noise product 1074 MB FP32)",
               "parallelism": f"replicas x{world} (chains independent; no data-path collective)"}
+    metric = "chain-steps/s and min-ESS/s at d=4096, mixed-prec+DA vs plain FP64, one B300"
 
     if args.impl == "reference":
         if rank != 0:
             return
-        cores_used = cores
         t0 = time.time()
-        leg = cpu_leg(run, ts, x0, C0, args.cpu_seconds, cores_used)
-        line = {"impl": "reference", "metric": "chain-steps/s", "value": leg["value"], "unit": "chain-steps/s",
+        leg = cpu_leg(run, ts, x0, C0, args.cpu_seconds, cores)
+        line = {"impl": "reference", "metric": metric, "value": leg["value"], "unit": "chain-steps/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
                 "cpu_baseline": leg,
@@ -213,86 +292,82 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    # one non-default stream for the sampler, its CUDA events and its graph replays
+    # one non-default stream for the samplers, their CUDA events and their graph replays
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     pk, pk_src = peaks()
 
-    # ---- main timed region: BF16 path
-    s = make_sampler(run, ts, x0, C0, dm.BF16, stream=stream.cuda_stream)
-    s.run(args.warmup * run.n_lag)
+    # ---- headline arm (every rank): mixed precision + delayed acceptance
     if world > 1:
         torch.distributed.barrier()
-    l0 = dm.kernel_launches()
-    with ClockSampler(local) as clk:
-        dt = time_intervals(s, run.n_lag, args.steps, torch, stream)
-    launches = dm.kernel_launches() - l0
-    st = s.stats()
+    head, dt, launches, clk = run_arm("mixed_da" if da else "mixed", run, ts, x0, C0, dm.BF16, da, args.warmup,
+                                      args.steps, torch, stream, dm, clocks_index=local)
     if world > 1:
         t = torch.tensor([dt], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         dt = t.item()
     value = world * N * args.steps / dt
-    s.close()
-    del s
+    arms = {("mixed_da" if da else "mixed"): head}
 
-    # ---- profile pass: per-phase device time with CUDA events on the same stream
-    roof = None
-    if not args.no_profile:
-        sp = make_sampler(run, ts, x0, C0, dm.BF16, profile=1, stream=stream.cuda_stream)
-        sp.run(args.warmup * run.n_lag)
-        sp.profile(reset=True)
-        sp.run(max(2, args.steps // 2) * run.n_lag)
-        prof = sp.profile()
-        sp.close()
-        del sp
-        roof = roofline(prof, run, ts, args.steps, pk, pk_src)
+    roof = fp64 = e2e = cpu = None
+    if rank == 0:
+        # ---- comparison arms on the same workload and start
+        msteps = args.steps if args.mixed_steps < 0 else args.mixed_steps
+        if da and msteps > 0:
+            arms["mixed"], _, _, _ = run_arm("mixed", run, ts, x0, C0, dm.BF16, False, args.warmup, msteps, torch,
+                                             stream, dm)
+        if args.fp64_steps > 0:
+            arms["fp64"], _, _, _ = run_arm("fp64", run, ts, x0, C0, dm.FP64, False, args.fp64_warmup,
+                                            args.fp64_steps, torch, stream, dm)
 
-    # ---- plain FP64 form on the same workload (fewer intervals: FP64 is ~1 TFLOP/s on B300)
-    fp64 = None
-    if args.fp64_steps > 0:
-        s64 = make_sampler(run, ts, x0, C0, dm.FP64, stream=stream.cuda_stream)
-        s64.run(run.n_lag)
-        dt64 = time_intervals(s64, run.n_lag, args.fp64_steps, torch, stream)
-        fp64 = {"value": round(N * args.fp64_steps / dt64, 1), "unit": "chain-steps/s",
-                "ms_per_step": round(dt64 / args.fp64_steps * 1e3, 2), "steps": args.fp64_steps}
-        s64.close()
-        del s64
+        # ---- profile pass: per-phase device time with CUDA events on the same stream
+        if not args.no_profile:
+            sp = make_sampler(run, ts, x0, C0, dm.BF16, da=da, profile=1, stream=stream.cuda_stream)
+            sp.run(args.warmup * run.n_lag)
+            sp.profile(reset=True)
+            sp.run(max(2, args.steps // 2) * run.n_lag)
+            prof = sp.profile()
+            sp.close()
+            roof = roofline(prof, run, ts, pk, pk_src)
 
-    # ---- end to end through the public API with host buffers: init (target + start state uploaded from
-    # host memory), K intervals each followed by a read of log pi, then the pooled moments read back
-    e2e = None
-    if not args.no_e2e:
-        torch.cuda.synchronize()
-        t0 = time.time()
-        se = make_sampler(run, ts, x0, C0, dm.BF16, stream=stream.cuda_stream)
-        for _ in range(args.steps):
-            se.run(run.n_lag)
-            se.log_pi()
-        m, cov, n = se.moments()
-        torch.cuda.synchronize()
-        te = time.time() - t0
-        se.close()
-        h2d = (ts.A.nbytes + ts.y.nbytes + ts.lam.nbytes + x0.nbytes + C0.nbytes)
-        d2h_final = m.nbytes + cov.nbytes
-        e2e = {"value": round(world * N * args.steps / te, 1), "unit": "chain-steps/s",
-               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(run.P * 8 + d2h_final / args.steps),
-               "includes": "diam_init from host arrays, K intervals each with a log-pi read, final moments read"}
+        # ---- end to end through the public API with host buffers: init (target, start state and surrogate
+        # weights uploaded from host memory), K intervals each followed by a read of log pi, then the pooled
+        # moments read back
+        if not args.no_e2e:
+            torch.cuda.synchronize()
+            t0 = time.time()
+            se = make_sampler(run, ts, x0, C0, dm.BF16, da=da, stream=stream.cuda_stream)
+            for _ in range(args.steps):
+                se.run(run.n_lag)
+                se.log_pi()
+            m, cov, n = se.moments()
+            torch.cuda.synchronize()
+            te = time.time() - t0
+            se.close()
+            h2d = ts.A.nbytes + ts.y.nbytes + ts.lam.nbytes + x0.nbytes + C0.nbytes
+            if da:
+                h2d += 8 * (512 * ts.d + 512 + 512 * 512 + 512 + 512 + 1)
+            d2h_final = m.nbytes + cov.nbytes
+            e2e = {"value": round(N * args.steps / te, 1), "unit": "chain-steps/s",
+                   "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(run.P * 8 + d2h_final / args.steps),
+                   "includes": "diam_init from host arrays, K intervals each with a log-pi read, final moments read"}
 
-    cpu = None
-    if rank == 0 and not args.no_cpu:
-        cpu = cpu_leg(run, ts, x0, C0, args.cpu_seconds, cores)
+        if not args.no_cpu:
+            cpu = cpu_leg(run, ts, x0, C0, args.cpu_seconds, cores)
 
     if rank == 0:
-        line = {"metric": "chain-steps/s", "value": round(value, 1), "unit": "chain-steps/s", "n_gpus": world,
+        ess_ratio = None
+        if "fp64" in arms and arms["fp64"]["min_ess_per_s"] > 0:
+            ess_ratio = round(head["min_ess_per_s"] / arms["fp64"]["min_ess_per_s"], 2)
+        line = {"metric": metric, "value": round(value, 1), "unit": "chain-steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
-                "data": "synthetic", "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clk.summary(), "fp64_plain": fp64,
-                "accept_rate": round(st["accepted"] / max(1, st["steps"] * run.P), 4), "refreshes": st["refreshes"],
-                "chol_attempts": st["chol_attempts"]}
+                "data": "synthetic", "config": config, "min_ess_per_s": head["min_ess_per_s"],
+                "min_ess_per_s_vs_fp64": ess_ratio, "arms": arms, "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary() if clk else None}
         print(json.dumps(line), flush=True)
     if world > 1:
+        torch.distributed.barrier()
         torch.distributed.destroy_process_group()
 
 

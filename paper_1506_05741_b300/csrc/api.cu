@@ -692,12 +692,15 @@ static diam_status alloc_all(diam_ctx* c) {
         CKS(dalloc(c, &pd.mean, sizeof(double) * d));
     }
     if (c->bf) {
-        CKS(dalloc(c, &c->oz.SL, sizeof(uint16_t) * (size_t)d * 448));
-        CKS(dalloc(c, &c->oz.ex, sizeof(int) * (size_t)d));
+        CKS(dalloc(c, &c->oz.SL, ozaki_sl_bytes(d)));
+        CKS(dalloc(c, &c->oz.ex, ozaki_ex_bytes(d)));
         c->oz.cap_rows = d;
-        CKS(dalloc(c, &c->oz.SL2, sizeof(uint16_t) * (size_t)P * 448));
-        CKS(dalloc(c, &c->oz.ex2, sizeof(int) * (size_t)P));
+        CKS(dalloc(c, &c->oz.SL2, ozaki_sl_bytes(P)));
+        CKS(dalloc(c, &c->oz.ex2, ozaki_ex_bytes(P)));
         c->oz.cap2 = P;
+        c->oz.capP = ozaki_panel_rows(d);
+        CKS(dalloc(c, &c->oz.SLP, sizeof(uint16_t) * (size_t)std::max<int64_t>(1, c->oz.capP) * 448));
+        CKS(dalloc(c, &c->oz.exP, sizeof(int) * (size_t)std::max<int64_t>(1, c->oz.capP)));
         CKS(dalloc(c, &c->Lq64, sizeof(double) * d * d));
         CKS(dalloc(c, &c->Lq16, sizeof(uint16_t) * (size_t)d * c->ldk));
         CKS(dalloc(c, &c->op_hi, sizeof(uint16_t) * (size_t)P * c->ldk));
@@ -1236,6 +1239,7 @@ void diam_destroy(diam_ctx* c) {
         cudaEventDestroy(e.b);
     }
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    ozaki_ws_release(c->oz);
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c->da;

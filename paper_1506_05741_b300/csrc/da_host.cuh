@@ -30,6 +30,7 @@ struct DaState {
     uint16_t *Xb, *XbT, *H1b, *H2b, *H1T, *dZ2, *dZ2T, *dZ1T;
     float *tb, *raw_lp, *Z1, *Z2, *ds, *dZ2f, *dH1, *dZ1f, *gW1T, *gW2T, *gb1, *gb2, *gw3, *gb3;
     double *loss_parts, *sbatch, *stats;
+    double* musig;   // device copy of (mu, sigma)
     Key key{};
 };
 
@@ -53,7 +54,7 @@ static diam_status da_forward(diam_ctx* c, int rows, const uint16_t* U, uint16_t
     e2.bias = a->b2;
     CK(tc_gemm_bf16(a->h2, rows, a->h1, a->W2q, a->h1, H1, nullptr, a->h1, 0, e2, &c->ctl->status, c->st));
     if (s_out) {
-        { mlp_out_kernel<<<blocks_for(rows), kThreads, 0, c->st>>>(rows, a->h2, H2, a->w3, a->b3, a->mu, a->sigma, s_out); count_launch(); }
+        { mlp_out_kernel<<<blocks_for(rows), kThreads, 0, c->st>>>(rows, a->h2, H2, a->w3, a->b3, a->musig, s_out); count_launch(); }
     }
     CK(cudaGetLastError());
     return DIAM_OK;
@@ -147,6 +148,8 @@ static diam_status da_train_now(diam_ctx* c, double* rmse_out) {
     const double ntr = std::max(1.0, st3[2]);
     a->mu = st3[0] / ntr;
     a->sigma = std::sqrt(std::max(1e-30, st3[1] / ntr - a->mu * a->mu));
+    const double ms[2] = {a->mu, a->sigma};
+    CK(cudaMemcpyAsync(a->musig, ms, sizeof(ms), cudaMemcpyHostToDevice, c->st));
     for (int s = 0; s < a->cfg.train_steps; ++s) {
         { gather_batch_kernel<<<a->B, kThreads, 0, c->st>>>(a->key, a->adam_t, 0, 0, a->ring_x, a->ring_lp, a->cnt, c->d, c->ldk,
                                                           a->shift, a->scale, a->mu, a->sigma, a->Xb, a->tb, nullptr); count_launch(); }
@@ -260,7 +263,12 @@ static diam_status da_alloc(diam_ctx* c, const diam_da_config* g, const double* 
     CKS(F(&a->dZ2f, (size_t)B * h2)); CKS(F(&a->dH1, (size_t)B * h1)); CKS(F(&a->dZ1f, (size_t)B * h1));
     CKS(F(&a->gW1T, (size_t)ldk * h1)); CKS(F(&a->gW2T, (size_t)h1 * h2)); CKS(F(&a->gb1, h1)); CKS(F(&a->gb2, h2));
     CKS(F(&a->gw3, h2)); CKS(F(&a->gb3, 1));
-    CKS(D(&a->loss_parts, B)); CKS(D(&a->sbatch, B)); CKS(D(&a->stats, 4));
+    CKS(D(&a->loss_parts, B)); CKS(D(&a->sbatch, B)); CKS(D(&a->stats, 4)); CKS(D(&a->musig, 2));
+    {
+        const double ms[2] = {a->mu, a->sigma};
+        CK(cudaMemcpyAsync(a->musig, ms, sizeof(ms), cudaMemcpyHostToDevice, c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
     // initial weights (FP64 host -> FP32 masters -> BF16 copies); unit feature scales until the first training
     std::vector<float> tmp;
     auto up = [&](float* dst, const double* src, size_t n) -> diam_status {

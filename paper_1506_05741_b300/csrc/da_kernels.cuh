@@ -30,13 +30,15 @@ __global__ void mlp_input_kernel(int d, const T* __restrict__ Xs, const float* _
 }
 
 // s_r = mu + sigma (w3 . H2_r + b3), one thread per row
+// musig: the output scaling (mu, sigma) of the current training, in device memory so that a captured
+// interval graph sees every retraining
 __global__ void mlp_out_kernel(int rows, int h2, const uint16_t* __restrict__ H2, const float* __restrict__ w3,
-                               const float* __restrict__ b3, double mu, double sigma, double* __restrict__ s_out) {
+                               const float* __restrict__ b3, const double* __restrict__ musig, double* __restrict__ s_out) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
     float acc = 0.f;
     for (int o = 0; o < h2; ++o) acc += w3[o] * bf16_bits_to_f32(H2[(size_t)r * h2 + o]);
-    s_out[r] = mu + sigma * (double)(acc + b3[0]);
+    s_out[r] = musig[0] + musig[1] * (double)(acc + b3[0]);
 }
 
 struct DaCounters {

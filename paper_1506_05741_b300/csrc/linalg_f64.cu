@@ -7,6 +7,7 @@
 // z = A_n^{-1}(x - x_ref) for every chain when the factor changes.
 #include "linalg.h"
 #include "gemm_f64.cuh"
+#include "ozaki_slice.cuh"
 
 namespace diam {
 
@@ -24,106 +25,127 @@ __device__ __forceinline__ double recip_newton(double D) {
     return fma(y, e, y);
 }
 
-// Owner warp of column j of the diagonal block: broadcast D_j, take its reciprocal on one lane, publish the
-// column a_ij (i > j) and its scaled copy a_ij / D_j into buffer j & 1.
-__device__ __forceinline__ void diag_publish(int j, double v0, double v1, int lane, int k0, int* info, double* dpiv,
-                                             double (*colb)[64], double (*scol)[64]) {
-    const double D = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
+// Cholesky of the nb x nb diagonal block at (k0, k0), nb <= 64: lower part in, L out, upper part zeroed.
+// Right-looking LDL^T in shared memory: pivot j subtracts a_ij (a_lj / D_j) from every a_il with
+// j < l <= i, leaving a_ij = L_ij sqrt(D_j); the square roots are taken once at the end. Per pivot j:
+//   - warp 0 (the critical path) updates column j + 1 in registers, takes 1 / D_{j+1} and publishes that
+//     column and its scaled copy into a double-buffered shared column;
+//   - the warps on the other three schedulers update columns j + 2 .. nb - 1, whose elements a packed table
+//     lists column by column from the last one, so the active elements are always a prefix of it and no lane
+//     is masked off; each thread loads up to four of its elements before it updates them;
+// then one barrier.
+constexpr int DIAG_THREADS = 512;
+
+__device__ __forceinline__ void diag_publish(int c, double v0, double v1, int lane, int nb, int k0, int* info,
+                                             double* dpiv, double (*colb)[CH_NB], double (*scol)[CH_NB]) {
+    const double D = __shfl_sync(0xffffffffu, v0, 0);
     double r = 0.0;
     if (lane == 0) {
         if (D > 0.0) {
             r = recip_newton(D);
         } else {   // not positive definite: NaN propagates and the caller discards the factor
             r = __longlong_as_double(0x7ff8000000000000ll);
-            if (info) atomicCAS(info, 0, k0 + j + 1);
+            if (info) atomicCAS(info, 0, k0 + c + 1);
         }
-        dpiv[j] = D;
+        dpiv[c] = D;
     }
     r = __shfl_sync(0xffffffffu, r, 0);
-    const int b = j & 1;
-    if (lane > j) {
-        colb[b][lane] = v0;
-        scol[b][lane] = v0 * r;
+    const int b = c & 1;
+    if (c + lane < nb) {
+        colb[b][c + lane] = v0;
+        scol[b][c + lane] = v0 * r;
     }
-    if (lane + 32 > j) {
-        colb[b][lane + 32] = v1;
-        scol[b][lane + 32] = v1 * r;
+    if (c + lane + 32 < nb) {
+        colb[b][c + lane + 32] = v1;
+        scol[b][c + lane + 32] = v1 * r;
     }
 }
 
-// Cholesky of the nb x nb diagonal block at (k0, k0), nb <= 64: lower part in, L out, upper part zeroed.
-// Right-looking LDL^T in registers: pivot j subtracts a_ij (a_lj / D_j) from every a_il with j < l <= i,
-// leaving a_ij = L_ij sqrt(D_j); the square roots are taken once at the end. Warp w owns the columns
-// l = w, w + 8, ..., w + 56 and lane t the rows t and t + 32. After its own update, the warp that owns
-// column j + 1 publishes it (and its scaled copy a_i,j+1 / D_j+1) into a double-buffered shared column, so
-// each pivot costs one barrier.
-__global__ void __launch_bounds__(256) chol_diag_kernel(double* __restrict__ A, int lda, int k0, int nb, int* info) {
-    __shared__ double colb[2][CH_NB];   // a_ij, i > j (column j of the current pivot)
-    __shared__ double scol[2][CH_NB];   // a_lj / D_j
+__global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(double* __restrict__ A, int lda, int k0, int nb,
+                                                                 int* info) {
+    __shared__ double a[CH_NB][CH_NB + 1];
+    __shared__ double colb[2][CH_NB];   // a_ij, i > j, of the current pivot j
+    __shared__ double scol[2][CH_NB];   // a_ij / D_j
     __shared__ double dpiv[CH_NB];      // D_j
     __shared__ double dsq[CH_NB], dinv[CH_NB];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double a[8][2];
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int l = w + 8 * c, i = lane + 32 * h;
-            a[c][h] = (l <= i && i < nb) ? A[(size_t)(k0 + i) * lda + k0 + l] : 0.0;
-        }
-    if (w == 0) diag_publish(0, a[0][0], a[0][1], lane, k0, info, dpiv, colb, scol);
+    __shared__ uint16_t tab[CH_NB * (CH_NB + 1) / 2];   // (i << 8) | l, columns nb-1 down to 0
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    for (int idx = tid; idx < nb * nb; idx += DIAG_THREADS) {
+        const int i = idx / nb, l = idx - i * nb;
+        a[i][l] = (l <= i) ? A[(size_t)(k0 + i) * lda + k0 + l] : 0.0;
+    }
+    if (tid < nb) {   // column l = tid: its nb - l elements follow those of the columns right of it
+        const int l = tid, off = (nb - l - 1) * (nb - l) / 2;
+        for (int r = 0; r < nb - l; ++r) tab[off + r] = (uint16_t)(((l + r) << 8) | l);
+    }
     __syncthreads();
+    if (w == 0)
+        diag_publish(0, lane < nb ? a[lane][0] : 0.0, lane + 32 < nb ? a[lane + 32][0] : 0.0, lane, nb, k0, info, dpiv,
+                     colb, scol);
+    __syncthreads();
+    // bulk warps: those not on warp 0's scheduler (warp w issues on sub-partition w % 4), so that the
+    // pivot chain never waits behind their FP64 instructions
+    constexpr int NB_T = (DIAG_THREADS / 32) / 4 * 3 * 32;
+    const int bt = (w - (w >> 2) - 1) * 32 + lane;   // index among the bulk threads (w % 4 != 0)
     for (int j = 0; j < nb; ++j) {
         const int b = j & 1, jn = j + 1;
-        const double ci0 = colb[b][lane], ci1 = colb[b][lane + 32];
-        const bool owner = jn < nb && w == (jn & 7);
-        if (owner) {   // the next pivot's column first: it is on the critical path
-            const double s = scol[b][jn];
-            double v0 = 0.0, v1 = 0.0;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {   // register arrays need compile-time indices
-                if (w + 8 * c == jn) {
-                    if (jn < 32 && lane >= jn) a[c][0] = fma(-ci0, s, a[c][0]);
-                    if (lane + 32 >= jn) a[c][1] = fma(-ci1, s, a[c][1]);
-                    v0 = a[c][0];
-                    v1 = a[c][1];
+        if (w == 0) {
+            if (jn < nb) {
+                const double s = scol[b][jn];
+                const int i0 = jn + lane, i1 = jn + lane + 32;
+                double v0 = 0.0, v1 = 0.0;
+                if (i0 < nb) {
+                    v0 = fma(-colb[b][i0], s, a[i0][jn]);
+                    a[i0][jn] = v0;
                 }
+                if (i1 < nb) {
+                    v1 = fma(-colb[b][i1], s, a[i1][jn]);
+                    a[i1][jn] = v1;
+                }
+                diag_publish(jn, v0, v1, lane, nb, k0, info, dpiv, colb, scol);
             }
-            diag_publish(jn, v0, v1, lane, k0, info, dpiv, colb, scol);
-        }
+        } else if (w & 3) {
+            const int T = (nb - j - 2) * (nb - j - 1) / 2;   // elements of columns j + 2 .. nb - 1
+            for (int e0 = bt; e0 < T; e0 += 4 * NB_T) {
+                int ii[4], ll[4];
+                double x[4], c[4], sc[4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int l = w + 8 * c;
-            if (l <= j || l >= nb || (owner && l == jn)) continue;   // warp-uniform
-            const double s = scol[b][l];
-            if (l < 32) {
-                if (lane >= l) a[c][0] = fma(-ci0, s, a[c][0]);
+                for (int q = 0; q < 4; ++q) {
+                    const int e = e0 + q * NB_T;
+                    const int t = (e < T) ? tab[e] : 0;
+                    ii[q] = t >> 8;
+                    ll[q] = t & 255;
+                    x[q] = a[ii[q]][ll[q]];
+                    c[q] = colb[b][ii[q]];
+                    sc[q] = scol[b][ll[q]];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (e0 + q * NB_T < T) a[ii[q]][ll[q]] = fma(-c[q], sc[q], x[q]);
             }
-            if (lane + 32 >= l) a[c][1] = fma(-ci1, s, a[c][1]);
         }
         __syncthreads();
     }
-    if (threadIdx.x < nb) {
-        const double q = sqrt(dpiv[threadIdx.x]);
-        dsq[threadIdx.x] = q;
-        dinv[threadIdx.x] = 1.0 / q;
+    if (tid < nb) {
+        const double q = sqrt(dpiv[tid]);
+        dsq[tid] = q;
+        dinv[tid] = 1.0 / q;
     }
     __syncthreads();
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int l = w + 8 * c, i = lane + 32 * h;
-            if (i < nb && l < nb)
-                A[(size_t)(k0 + i) * lda + k0 + l] = (l < i) ? a[c][h] * dinv[l] : (l == i ? dsq[l] : 0.0);
-        }
+    for (int idx = tid; idx < nb * nb; idx += DIAG_THREADS) {
+        const int i = idx / nb, l = idx - i * nb;
+        A[(size_t)(k0 + i) * lda + k0 + l] = (l < i) ? a[i][l] * dinv[l] : (l == i ? dsq[l] : 0.0);
+    }
 }
 
 // For each of nrows rows r: solve L y = b in place, b = B[r*ldb + 0 .. nb), L the nb x nb lower triangle
 // at Lkk (row stride ldl). With L = U D (U unit lower, D = diag L): U w = b by forward substitution, then
 // y = D^{-1} w. One warp per row; lane l holds entries l and l + 32.
+// With SL != nullptr (nb = 64), each solved row is also cut into its Ozaki slices (row r at SL + r * 448,
+// exponent in ex[r]) for the tensor-core update that follows.
 __global__ void __launch_bounds__(256) trsv_rows_kernel(const double* __restrict__ Lkk, int ldl, int nb,
-                                                         double* __restrict__ B, int ldb, int nrows) {
+                                                         double* __restrict__ B, int ldb, int nrows,
+                                                         uint16_t* __restrict__ SL = nullptr, int* __restrict__ ex = nullptr) {
     __shared__ double U[CH_NB][CH_NB + 1];
     __shared__ double invd[CH_NB];
     if (threadIdx.x < CH_NB) invd[threadIdx.x] = threadIdx.x < nb ? 1.0 / Lkk[(size_t)threadIdx.x * ldl + threadIdx.x] : 0.0;
@@ -150,8 +172,14 @@ __global__ void __launch_bounds__(256) trsv_rows_kernel(const double* __restrict
             const double wj = __shfl_sync(0xffffffffu, v1, j - 32);
             if (lane + 32 > j) v1 = fma(-U[lane + 32][j], wj, v1);
         }
-        if (lane < nb) b[lane] = v0 * id0;
-        if (lane + 32 < nb) b[lane + 32] = v1 * id1;
+        v0 *= id0;
+        v1 *= id1;
+        if (lane < nb) b[lane] = v0;
+        if (lane + 32 < nb) b[lane + 32] = v1;
+        if (SL) {
+            const int e = ozaki_slice_row(v0, v1, lane, SL + (size_t)r * OZ_LD);
+            if (lane == 0) ex[r] = e;
+        }
     }
 }
 
@@ -163,53 +191,168 @@ __global__ void zero_upper_kernel(double* A, int lda, int n) {
 
 static int row_blocks(int nrows) { return max(1, min((nrows + 7) / 8, 148 * 8)); }
 
-cudaError_t cholesky_f64(double* A, int n, int lda, int* info_dev, cudaStream_t st, OzakiWs* oz, int* status_dev) {
+static cudaError_t ensure_streams(OzakiWs& ws) {
+    if (ws.hi) return cudaSuccess;
+    int lo_pri = 0, hi_pri = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ws.hi, cudaStreamNonBlocking, hi_pri);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ws.lo, cudaStreamNonBlocking, lo_pri);
+    for (cudaEvent_t* ev : {&ws.ev_in, &ws.ev_slice, &ws.ev_rest, &ws.ev_lo})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) ozaki_ws_release(ws);
+    return e;
+}
+
+#define LA_CK(x)                          \
+    do {                                  \
+        cudaError_t e_ = (x);             \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+// DFMA form: diagonal block, panel solve, DFMA rank-64 update of the trailing lower triangle, in order.
+static cudaError_t cholesky_dfma(double* A, int n, int lda, int* info_dev, cudaStream_t st) {
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         int nb = min(CH_NB, n - k0);
-        { chol_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, nb, info_dev); count_launch(); }
+        { chol_diag_kernel<<<1, DIAG_THREADS, 0, st>>>(A, lda, k0, nb, info_dev); count_launch(); }
         int k1 = k0 + nb, rest = n - k1;
         if (rest <= 0) break;
         // panel rows solve x L_kk^T = a, i.e. L_kk x^T = a^T
         { trsv_rows_kernel<<<row_blocks(rest), 256, 0, st>>>(A + (size_t)k0 * lda + k0, lda, nb,
                                                              A + (size_t)k1 * lda + k0, lda, rest); count_launch(); }
         // trailing lower triangle: A[k1+n][k1+m] -= sum_k L[k1+m][k0+k] L[k1+n][k0+k]
-        cudaError_t e;
-        if (oz && nb == CH_NB && rest >= 128) {
-            e = ozaki_trailing_update(A + (size_t)k1 * lda + k0, lda, rest, A + (size_t)k1 * lda + k1, lda, *oz,
-                                      status_dev, st);
-        } else {
-            EpiStore epi{A + (size_t)k1 * lda + k1, lda, -1.0, nullptr, 1.0};
-            e = gemm_f64<true, true>(rest, rest, nb, A + (size_t)k1 * lda + k0, lda, A + (size_t)k1 * lda + k0, lda,
-                                     TileRange{0, 1}, epi, st);
-        }
-        if (e != cudaSuccess) return e;
+        EpiStore epi{A + (size_t)k1 * lda + k1, lda, -1.0, nullptr, 1.0};
+        LA_CK((gemm_f64<true, true>(rest, rest, nb, A + (size_t)k1 * lda + k0, lda, A + (size_t)k1 * lda + k0, lda,
+                                    TileRange{0, 1}, epi, st)));
     }
+    return cudaGetLastError();
+}
+
+// Tensor-core form with lookahead. On a high-priority stream: diagonal block, panel solve, slicing of the
+// panel, then the update of the next 64 columns only (what the next diagonal block and panel need). The
+// update of everything right of them runs on a second stream and overlaps the next block's chain; the
+// chain waits for it only before its own next-columns update, which writes inside that region.
+static cudaError_t cholesky_ozaki(double* A, int n, int lda, int* info_dev, cudaStream_t st, OzakiWs& oz,
+                                  int* status_dev) {
+    LA_CK(ensure_streams(oz));
+    cudaStream_t hi = oz.hi, lo = oz.lo;
+    LA_CK(cudaEventRecord(oz.ev_in, st));
+    LA_CK(cudaStreamWaitEvent(hi, oz.ev_in, 0));
+    LA_CK(cudaStreamWaitEvent(lo, oz.ev_in, 0));
+    bool rest_pending = false;
+    for (int k0 = 0; k0 < n; k0 += CH_NB) {
+        int nb = min(CH_NB, n - k0);
+        { chol_diag_kernel<<<1, DIAG_THREADS, 0, hi>>>(A, lda, k0, nb, info_dev); count_launch(); }
+        int k1 = k0 + nb, rest = n - k1;
+        if (rest <= 0) break;
+        double* T = A + (size_t)k1 * lda + k1;   // trailing block
+        const bool tc = nb == CH_NB && rest >= 2 * CH_NB && rest <= oz.cap_rows;
+        const int buf = (k0 / CH_NB) & 1;
+        // panel solve; on the tensor-core path it also writes the panel's Ozaki slices into buffer buf
+        { trsv_rows_kernel<<<row_blocks(rest), 256, 0, hi>>>(A + (size_t)k0 * lda + k0, lda, nb,
+                                                             A + (size_t)k1 * lda + k0, lda, rest,
+                                                             tc ? oz.SL + (size_t)buf * oz.cap_rows * OZ_LD : nullptr,
+                                                             tc ? oz.ex + (size_t)buf * oz.cap_rows : nullptr); count_launch(); }
+        if (tc) {
+            LA_CK(cudaEventRecord(oz.ev_slice, hi));
+            if (rest_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_rest, 0));
+            // next 64 columns: T[n][m] for m < 64, n >= m
+            LA_CK(ozaki_update_sliced(buf, 0, CH_NB, 0, rest, T, lda, 1, oz, status_dev, hi));
+            // the rest: T[n][m] for 64 <= m <= n, on the second stream
+            LA_CK(cudaStreamWaitEvent(lo, oz.ev_slice, 0));
+            LA_CK(ozaki_update_sliced(buf, CH_NB, rest - CH_NB, CH_NB, rest - CH_NB, T + (size_t)CH_NB * lda + CH_NB,
+                                      lda, 1, oz, status_dev, lo));
+            LA_CK(cudaEventRecord(oz.ev_rest, lo));
+            rest_pending = true;
+        } else {
+            if (rest_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_rest, 0));
+            rest_pending = false;
+            EpiStore epi{T, lda, -1.0, nullptr, 1.0};
+            LA_CK((gemm_f64<true, true>(rest, rest, nb, A + (size_t)k1 * lda + k0, lda, A + (size_t)k1 * lda + k0, lda,
+                                        TileRange{0, 1}, epi, hi)));
+        }
+    }
+    if (rest_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_rest, 0));
+    dim3 g(max(1, min(32, (n + 255) / 256)), n);
+    { zero_upper_kernel<<<g, 256, 0, hi>>>(A, lda, n); count_launch(); }
+    LA_CK(cudaEventRecord(oz.ev_lo, hi));
+    LA_CK(cudaStreamWaitEvent(st, oz.ev_lo, 0));
+    return cudaGetLastError();
+}
+
+cudaError_t cholesky_f64(double* A, int n, int lda, int* info_dev, cudaStream_t st, OzakiWs* oz, int* status_dev) {
+    if (oz) return cholesky_ozaki(A, n, lda, info_dev, st, *oz, status_dev);
+    LA_CK(cholesky_dfma(A, n, lda, info_dev, st));
     dim3 g(max(1, min(32, (n + 255) / 256)), n);
     { zero_upper_kernel<<<g, 256, 0, st>>>(A, lda, n); count_launch(); }
     return cudaGetLastError();
 }
 
-cudaError_t trsm_lower_f64(const double* L, int ldl, int n, double* B, int ldb, int nrows, cudaStream_t st,
-                           OzakiWs* oz, int* status_dev) {
-    if (nrows <= 0 || n <= 0) return cudaSuccess;
+// DFMA form of the blocked solve: panel solve of the right-hand sides, DFMA update of the columns right
+// of the block.
+static cudaError_t trsm_dfma(const double* L, int ldl, int n, double* B, int ldb, int nrows, cudaStream_t st) {
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         int nb = min(CH_NB, n - k0);
         { trsv_rows_kernel<<<row_blocks(nrows), 256, 0, st>>>(L + (size_t)k0 * ldl + k0, ldl, nb, B + k0, ldb, nrows); count_launch(); }
         int k1 = k0 + nb;
         if (k1 >= n) break;
         // B[r][k1 + i] -= sum_k L[k1 + i][k0 + k] Y[r][k0 + k]
-        cudaError_t e;
-        if (oz && nb == CH_NB && n - k1 <= oz->cap_rows && nrows <= oz->cap2) {
-            e = ozaki_gemm_update(L + (size_t)k1 * ldl + k0, ldl, n - k1, B + k0, ldb, nrows, B + k1, ldb, *oz,
-                                  status_dev, st);
-        } else {
-            EpiStore epi{B + k1, ldb, -1.0, nullptr, 1.0};
-            e = gemm_f64<true, true>(n - k1, nrows, nb, L + (size_t)k1 * ldl + k0, ldl, B + k0, ldb, TileRange{0, 0},
-                                     epi, st);
-        }
-        if (e != cudaSuccess) return e;
+        EpiStore epi{B + k1, ldb, -1.0, nullptr, 1.0};
+        LA_CK((gemm_f64<true, true>(n - k1, nrows, nb, L + (size_t)k1 * ldl + k0, ldl, B + k0, ldb, TileRange{0, 0},
+                                    epi, st)));
     }
     return cudaGetLastError();
+}
+
+// Tensor-core form with lookahead: the panels of L are sliced once up front; per block, on the
+// high-priority stream, the panel solve of the right-hand sides (which also slices them) and the update of
+// the next 64 columns; the update of the columns right of those runs on the second stream and overlaps the
+// next block's solve.
+static cudaError_t trsm_ozaki(const double* L, int ldl, int n, double* B, int ldb, int nrows, cudaStream_t st,
+                              OzakiWs& oz, int* status_dev) {
+    LA_CK(ensure_streams(oz));
+    cudaStream_t hi = oz.hi, lo = oz.lo;
+    LA_CK(cudaEventRecord(oz.ev_in, st));
+    LA_CK(cudaStreamWaitEvent(hi, oz.ev_in, 0));
+    LA_CK(cudaStreamWaitEvent(lo, oz.ev_in, 0));
+    LA_CK(ozaki_slice_panels(L, ldl, n, oz, hi));
+    bool rest_pending = false;
+    int64_t off = 0;   // first row of panel k in the panel slices
+    for (int k0 = 0; k0 < n; k0 += CH_NB) {
+        const int nb = min(CH_NB, n - k0), k1 = k0 + nb, rows = n - k1;
+        const int buf = (k0 / CH_NB) & 1;
+        const bool tc = nb == CH_NB && rows > 0;
+        uint16_t* SY = oz.SL2 + (size_t)buf * oz.cap2 * OZ_LD;
+        int* eY = oz.ex2 + (size_t)buf * oz.cap2;
+        { trsv_rows_kernel<<<row_blocks(nrows), 256, 0, hi>>>(L + (size_t)k0 * ldl + k0, ldl, nb, B + k0, ldb, nrows,
+                                                              tc ? SY : nullptr, tc ? eY : nullptr); count_launch(); }
+        if (rows <= 0) break;
+        const uint16_t* SA = oz.SLP + (size_t)off * OZ_LD;
+        const int* eA = oz.exP + off;
+        LA_CK(cudaEventRecord(oz.ev_slice, hi));
+        if (rest_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_rest, 0));
+        // next 64 columns: B[r][k1 + i] -= sum_k L[k1 + i][k0 + k] Y[r][k0 + k], i < 64
+        LA_CK(ozaki_update_raw(SA, min(CH_NB, rows), eA, SY, nrows, eY, B + k1, ldb, 0, status_dev, hi));
+        if (rows > CH_NB) {
+            LA_CK(cudaStreamWaitEvent(lo, oz.ev_slice, 0));
+            LA_CK(ozaki_update_raw(SA + (size_t)CH_NB * OZ_LD, rows - CH_NB, eA + CH_NB, SY, nrows, eY, B + k1 + CH_NB,
+                                   ldb, 0, status_dev, lo));
+            LA_CK(cudaEventRecord(oz.ev_rest, lo));
+            rest_pending = true;
+        }
+        off += rows;
+    }
+    if (rest_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_rest, 0));
+    LA_CK(cudaEventRecord(oz.ev_lo, hi));
+    LA_CK(cudaStreamWaitEvent(st, oz.ev_lo, 0));
+    return cudaGetLastError();
+}
+
+cudaError_t trsm_lower_f64(const double* L, int ldl, int n, double* B, int ldb, int nrows, cudaStream_t st,
+                           OzakiWs* oz, int* status_dev) {
+    if (nrows <= 0 || n <= 0) return cudaSuccess;
+    if (oz && nrows <= oz->cap2 && ozaki_panel_rows(n) <= oz->capP && oz->SLP)
+        return trsm_ozaki(L, ldl, n, B, ldb, nrows, st, *oz, status_dev);
+    return trsm_dfma(L, ldl, n, B, ldb, nrows, st);
 }
 
 }  // namespace diam

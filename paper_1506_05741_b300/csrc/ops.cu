@@ -61,19 +61,26 @@ diam_status diam_op_cholesky_f64(int32_t n, double* A, int32_t lda, int32_t* inf
 struct OzScope {
     OzakiWs ws;
     bool ok = true;
+    // rows: the factor's order; rows2 > 0: also the workspace of a triangular solve with rows2 right-hand sides
     OzScope(int rows, int rows2) {
         ws.cap_rows = rows;
         ws.cap2 = rows2;
-        ok = cudaMalloc(&ws.SL, sizeof(uint16_t) * (size_t)rows * 448) == cudaSuccess &&
-             cudaMalloc(&ws.ex, sizeof(int) * (size_t)rows) == cudaSuccess &&
-             (rows2 == 0 || (cudaMalloc(&ws.SL2, sizeof(uint16_t) * (size_t)rows2 * 448) == cudaSuccess &&
-                             cudaMalloc(&ws.ex2, sizeof(int) * (size_t)rows2) == cudaSuccess));
+        ws.capP = rows2 > 0 ? ozaki_panel_rows(rows) : 0;
+        ok = cudaMalloc(&ws.SL, ozaki_sl_bytes(rows)) == cudaSuccess &&
+             cudaMalloc(&ws.ex, ozaki_ex_bytes(rows)) == cudaSuccess &&
+             (rows2 == 0 || (cudaMalloc(&ws.SL2, ozaki_sl_bytes(rows2)) == cudaSuccess &&
+                             cudaMalloc(&ws.ex2, ozaki_ex_bytes(rows2)) == cudaSuccess &&
+                             cudaMalloc(&ws.SLP, sizeof(uint16_t) * (size_t)std::max<int64_t>(1, ws.capP) * 448) == cudaSuccess &&
+                             cudaMalloc(&ws.exP, sizeof(int) * (size_t)std::max<int64_t>(1, ws.capP)) == cudaSuccess));
     }
     ~OzScope() {
+        ozaki_ws_release(ws);
         cudaFree(ws.SL);
         cudaFree(ws.ex);
         cudaFree(ws.SL2);
         cudaFree(ws.ex2);
+        cudaFree(ws.SLP);
+        cudaFree(ws.exP);
     }
 };
 

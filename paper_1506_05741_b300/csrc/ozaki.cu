@@ -17,17 +17,13 @@
 // One CTA per 128 x 64 output tile keeps all 14 slice tiles in shared memory and the 7 group accumulators
 // in tensor memory (448 of its 512 columns).
 #include "linalg.h"
+#include "ozaki_slice.cuh"
 #include "tc_common.cuh"
 #include "tc_gemm.h"
 
 namespace diam {
 
-constexpr int OZ_S = 7, OZ_K = 64, OZ_LD = OZ_S * OZ_K, OZ_BN = 64;
-
-// 2^e as a double (exact for normal exponents).
-__device__ __forceinline__ double pow2(int e) {
-    return (e >= -1022 && e <= 1023) ? __hiloint2double((e + 1023) << 20, 0) : ldexp(1.0, e);
-}
+constexpr int OZ_BN = 64;
 
 // One warp per operand row: exponent and the 7 BF16 slices (exact integers) of the row's 64 entries.
 __global__ void ozaki_slice_kernel(const double* __restrict__ P, int lda, int rows, uint16_t* __restrict__ SL,
@@ -35,24 +31,8 @@ __global__ void ozaki_slice_kernel(const double* __restrict__ P, int lda, int ro
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= rows) return;
-    const double v[2] = {P[(size_t)row * lda + lane], P[(size_t)row * lda + lane + 32]};
-    double m = fmax(fabs(v[0]), fabs(v[1]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const int e = (m > 0.0) ? ilogb(m) + 1 : 0;   // m < 2^e
-    const double sc = pow2(55 - e);
-    uint16_t* out = SL + (size_t)row * OZ_LD + lane;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        long long R = __double2ll_rn(v[h] * sc);  // exact scaling, then one rounding: |R| <= 2^55
-#pragma unroll
-        for (int a = 0; a < OZ_S; ++a) {
-            const int s = 48 - 8 * a;
-            const long long S = (s > 0) ? ((R + (1ll << (s - 1))) >> s) : R;   // |S| <= 128
-            R -= S * (1ll << s);                                                 // |R| <= 2^(s-1)
-            out[a * OZ_K + 32 * h] = (uint16_t)(__float_as_uint((float)S) >> 16);   // exact in BF16
-        }
-    }
+    const int e = ozaki_slice_row(P[(size_t)row * lda + lane], P[(size_t)row * lda + lane + 32], lane,
+                                  SL + (size_t)row * OZ_LD);
     if (lane == 0) ex[row] = e;
 }
 
@@ -76,6 +56,8 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * OZ_BN;
     if ((lower && n0 + OZ_BN - 1 < m0) || n0 >= Nb || m0 >= Ma) return;   // nothing of this tile is updated
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int sex[OZ_BN];   // exponents of this tile's B rows
+    if (threadIdx.x < OZ_BN) sex[threadIdx.x] = (n0 + (int)threadIdx.x < Nb) ? exB[n0 + threadIdx.x] : 0;
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(full), 1);
         mbar_init(smem_u32(done), 1);
@@ -130,6 +112,13 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
         for (int c = 0; c < OZ_BN / 32; ++c) {
+            // issue this chunk's 32 loads of C first: their latency hides behind the tensor-memory reads
+            double cv[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int n = n0 + c * 32 + j;
+                cv[j] = (vm && n < Nb && (!lower || n >= m)) ? Cm[(size_t)n * ldc + m] : 0.0;
+            }
             long long acc[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) acc[j] = 0;
@@ -146,15 +135,11 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
                     for (int j = 0; j < 32; ++j) acc[j] += (long long)(__float2int_rn(__uint_as_float(r[j])) >> 8);
                 }
             }
-            if (vm) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int n = n0 + c * 32 + j;
-                    if (n < Nb && (!lower || n >= m)) {
-                        double* p = Cm + (size_t)n * ldc + m;
-                        *p = fma(-(double)acc[j], pow2(em + exB[n] - 54), *p);
-                    }
-                }
+            for (int j = 0; j < 32; ++j) {
+                const int n = n0 + c * 32 + j;
+                if (vm && n < Nb && (!lower || n >= m))
+                    Cm[(size_t)n * ldc + m] = fma(-(double)acc[j], pow2(em + sex[c * 32 + j] - 54), cv[j]);
             }
         }
     } else if (threadIdx.x == 0) {
@@ -198,6 +183,59 @@ cudaError_t ozaki_trailing_update(const double* Pnl, int lda, int rows, double* 
     if (rows > ws.cap_rows) return cudaErrorInvalidValue;
     slice(Pnl, lda, rows, ws.SL, ws.ex, st);
     return launch_update(ws.SL, rows, ws.ex, ws.SL, rows, ws.ex, Cm, ldc, 1, status, st);
+}
+
+cudaError_t ozaki_slice_panel(const double* Pnl, int lda, int rows, int buf, OzakiWs& ws, cudaStream_t st) {
+    if (rows > ws.cap_rows) return cudaErrorInvalidValue;
+    slice(Pnl, lda, rows, ws.SL + (size_t)buf * ws.cap_rows * OZ_LD, ws.ex + (size_t)buf * ws.cap_rows, st);
+    return cudaGetLastError();
+}
+
+cudaError_t ozaki_update_sliced(int buf, int r0, int Ma, int c0, int Nb, double* Cm, int ldc, int lower, OzakiWs& ws,
+                                int* status, cudaStream_t st) {
+    if (Ma <= 0 || Nb <= 0) return cudaSuccess;
+    const uint16_t* S = ws.SL + (size_t)buf * ws.cap_rows * OZ_LD;
+    const int* e = ws.ex + (size_t)buf * ws.cap_rows;
+    return launch_update(S + (size_t)r0 * OZ_LD, Ma, e + r0, S + (size_t)c0 * OZ_LD, Nb, e + c0, Cm, ldc, lower, status, st);
+}
+
+__global__ void ozaki_slice_panels_kernel(const double* __restrict__ L, int ldl, int n, int64_t total,
+                                          uint16_t* __restrict__ SL, int* __restrict__ ex) {
+    const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= total) return;
+    int k = 0;
+    int64_t off = 0;
+    while (g >= off + (n - OZ_K * (k + 1))) {   // the panel holding row g (warp-uniform)
+        off += n - OZ_K * (k + 1);
+        ++k;
+    }
+    const double* row = L + (size_t)(OZ_K * (k + 1) + (g - off)) * ldl + OZ_K * k;
+    const int e = ozaki_slice_row(row[lane], row[lane + 32], lane, SL + (size_t)g * OZ_LD);
+    if (lane == 0) ex[g] = e;
+}
+
+cudaError_t ozaki_slice_panels(const double* L, int ldl, int n, OzakiWs& ws, cudaStream_t st) {
+    const int64_t total = ozaki_panel_rows(n);
+    if (total > ws.capP) return cudaErrorInvalidValue;
+    if (total == 0) return cudaSuccess;
+    { ozaki_slice_panels_kernel<<<(unsigned)((total + 7) / 8), 256, 0, st>>>(L, ldl, n, total, ws.SLP, ws.exP); count_launch(); }
+    return cudaGetLastError();
+}
+
+cudaError_t ozaki_update_raw(const uint16_t* SA, int Ma, const int* exA, const uint16_t* SB, int Nb, const int* exB,
+                             double* C, int ldc, int lower, int* status, cudaStream_t st) {
+    if (Ma <= 0 || Nb <= 0) return cudaSuccess;
+    return launch_update(SA, Ma, exA, SB, Nb, exB, C, ldc, lower, status, st);
+}
+
+void ozaki_ws_release(OzakiWs& ws) {
+    if (ws.hi) cudaStreamDestroy(ws.hi);
+    if (ws.lo) cudaStreamDestroy(ws.lo);
+    for (cudaEvent_t e : {ws.ev_in, ws.ev_slice, ws.ev_rest, ws.ev_lo})
+        if (e) cudaEventDestroy(e);
+    ws.hi = ws.lo = nullptr;
+    ws.ev_in = ws.ev_slice = ws.ev_rest = ws.ev_lo = nullptr;
 }
 
 cudaError_t ozaki_gemm_update(const double* A, int lda, int Ma, const double* B, int ldb, int Nb, double* Cm, int ldc,

@@ -101,3 +101,43 @@ def test_delayed_acceptance_keeps_the_target():
     m, cov, n = s.moments()
     rel = np.abs(np.diag(cov) - np.diag(ts.cov)) / np.diag(ts.cov)
     assert np.median(rel) < 0.1
+
+
+def test_trained_surrogate_saves_exact_evaluations():
+    """What the network gains: on the same tanh-regression target, seed and start, the two-stage sampler
+    with the trained surrogate spends fewer exact log-density evaluations per accepted move than the plain
+    sampler, and screens out a real share of the proposals, while its acceptance per proposal stays within a
+    factor of two of the plain chain's."""
+    import paper_1506_05741_b300 as dm
+    d, P, nl = 256, 128, 16
+    ts = workloads.tanh_regression(d, 128, 23)
+    x0 = workloads.start_state(d, P, 5) * np.sqrt(ts.lam)
+
+    def sampler():
+        cfg = dm.default_config(d, P, prec=dm.BF16, n_lag=nl, M=2, seed=7, beta0=0.2)
+        return dm.Sampler(cfg, ts, x0=x0, C0=np.diag(ts.lam))
+
+    plain = sampler()
+    plain.run(nl * 60)
+    sp = plain.stats()
+    evals_plain = sp["steps"] * P
+    per_acc_plain = evals_plain / max(1, sp["accepted"])
+
+    two = sampler()
+    two.da_enable(dm.da_default_config(h1=128, h2=128, batch=256, ring=20000, first_train_min=4000, train_steps=300,
+                                       retrain_every=2, rmse_bound=1e9), workloads.mlp_init(d, 128, 128, seed=8))
+    two.run(nl * 20)                 # fill the ring; trainings every 2 synchronisations
+    s0, d0 = two.stats(), two.da_stats()
+    two.run(nl * 40)
+    s1, d1 = two.stats(), two.da_stats()
+    assert d1["active"] == 1 and d1["trainings"] >= 2
+    evals = d1["exact_evals"] - d0["exact_evals"]
+    acc = s1["accepted"] - s0["accepted"]
+    tested = d1["stage1_tested"] - d0["stage1_tested"]
+    passed = d1["stage1_passed"] - d0["stage1_passed"]
+    per_acc_two = evals / max(1, acc)
+    assert passed < 0.9 * tested                       # stage 1 screens out a real share
+    assert per_acc_two < per_acc_plain                 # fewer exact evaluations per accepted move
+    assert acc / (40 * nl * P) > 0.5 * sp["accepted"] / (60 * nl * P)
+    plain.close()
+    two.close()
