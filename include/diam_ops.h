@@ -54,8 +54,9 @@ DIAM_API diam_status diam_op_gemm_bf16(int32_t M, int32_t N, int32_t K, const ui
                               const uint16_t* B2, int32_t ldb, int32_t a_lower, float scale, float* D, int32_t ldd,
                               void* stream);
 
-/* diam_op_gemm_bf16 with an explicit tile width over N (bn = 32, 64 or 128): the candidates the tile
- * autotuner times for each product shape. Synchronises the stream. */
+/* diam_op_gemm_bf16 with an explicit tile width over N (bn = 32, 64, 128, or 256 when B2 is NULL): the
+ * candidates the tile autotuner times for each product shape. DIAM_EINVAL for other widths. Synchronises the
+ * stream. */
 DIAM_API diam_status diam_op_gemm_bf16_tile(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda,
                                             const uint16_t* B, const uint16_t* B2, int32_t ldb, int32_t a_lower,
                                             float scale, float* D, int32_t ldd, int32_t bn, void* stream);

@@ -32,6 +32,7 @@ void count_launch() { g_launches.fetch_add(1ull, std::memory_order_relaxed); }
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int TSPLIT_MAX = 8;   // split planes of the target product's K
 
 struct Pending {
     double* L = nullptr;
@@ -51,6 +52,8 @@ struct diam_ctx {
     int dev = 0;
     cudaStream_t st = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;                 // overlaps the interval's noise product with the re-solve
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     bool bad = false;
     diam_logpi_fn fn = nullptr;
@@ -88,11 +91,13 @@ struct diam_ctx {
     int ldw = 0, ldh = 0, nparts = 0;
     // target
     double *inv_lam = nullptr, *Gm = nullptr, *y = nullptr;
+    float *inv_lam32 = nullptr, *y32 = nullptr;   // FP32 copies for the BF16-mode kernels
     uint16_t* Gq16 = nullptr;
     TargetDev tg{};
     // trace and interval sums
     TraceDev tr{};
-    double *bsum = nullptr, *lpsum = nullptr;
+    void* bsum = nullptr;   // per-interval, per-chain sums of x: FP64 (FP32 in BF16 mode)
+    double* lpsum = nullptr;
     int64_t bcap = 0;
     // phase profiler (cfg.profile): event pairs recorded on the stream, read back at synchronisation points
     struct Evt {
@@ -159,6 +164,17 @@ static diam_status fail(diam_ctx* c, diam_status s, const char* what, const char
     return s;
 }
 
+// Host <-> device copies ordered on the context's stream (which does not synchronise with the legacy default
+// stream). A host-to-device copy from pageable memory is staged before the call returns; a device-to-host
+// copy is waited for.
+static cudaError_t h2d(diam_ctx* c, void* dst, const void* src, size_t n) {
+    return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->st);
+}
+static cudaError_t d2h(diam_ctx* c, void* dst, const void* src, size_t n) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->st);
+    return e == cudaSuccess ? cudaStreamSynchronize(c->st) : e;
+}
+
 template <typename P_>
 static diam_status dalloc(diam_ctx* c, P_** p, size_t bytes) {
     void* v = nullptr;
@@ -186,7 +202,7 @@ static diam_status check_usable(diam_ctx* c) {
 static diam_status sync_and_check(diam_ctx* c) {
     CK(cudaStreamSynchronize(c->st));
     int stt = 0;
-    CK(cudaMemcpy(&stt, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(d2h(c, &stt, &c->ctl->status, sizeof(int)));
     if (stt == DEV_TIMEOUT) return fail(c, DIAM_ETIMEOUT, "device", "a bounded wait inside a kernel expired");
     if (stt != 0) return fail(c, DIAM_ECUDA, "device", "kernel reported a bad argument");
     return DIAM_OK;
@@ -274,27 +290,41 @@ static diam_status quantise(diam_ctx* c) {
 }
 
 template <typename T>
+static diam_status prepare_block(diam_ctx* c, int64_t blk, cudaStream_t st);
+
+template <typename T>
 static diam_status block_begin(diam_ctx* c, int64_t blk) {
     for (auto& pd : c->pend) {
         if (pd.block != blk) continue;
         CK(cudaMemcpyAsync(c->L, pd.L, sizeof(double) * c->d * c->d, cudaMemcpyDeviceToDevice, c->st));
         CKS(quantise(c));
         if (c->cfg.xref_mode == 1) set_xref_from(c, pd.mean);
+        // the interval's noise and noise product need only the new quantised factor, z's re-solve needs the
+        // states: with the side stream they run side by side (the steps wait for both)
+        const bool overlap = c->side && !c->cfg.profile && c->xi_block != blk;
+        if (overlap) {
+            CK(cudaEventRecord(c->ev_fork, c->st));
+            CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+            CKS(prepare_block<T>(c, blk, c->side));
+            CK(cudaEventRecord(c->ev_join, c->side));
+        }
         CKS(rewhiten<T>(c));
+        if (overlap) CK(cudaStreamWaitEvent(c->st, c->ev_join, 0));
         pd.block = -1;
     }
     return DIAM_OK;
 }
 
-// W for the n_lag steps of interval blk and their noise products xi = beta alpha Lq W (one GEMM).
+// W for the n_lag steps of interval blk and their noise products xi = beta alpha Lq W (one GEMM), on
+// stream st (the context's stream, or the side stream that overlaps them with the re-solve of z).
 template <typename T>
-static diam_status prepare_block(diam_ctx* c, int64_t blk) {
+static diam_status prepare_block(diam_ctx* c, int64_t blk, cudaStream_t st) {
     const int d = c->d, P = c->P, nl = c->nl;
     const int64_t rows = (int64_t)nl * P;
     dim3 g((unsigned)rows, std::max(1u, std::min(64u, blocks_for(c->ldw / 4, 128))));
     if (c->bf) {
         int e0 = ph_begin(c, PH_NOISE);
-        { gen_w_kernel<uint16_t><<<g, 128, 0, c->st>>>(c->key, blk * nl, P, d, c->ldw, (uint16_t*)c->W); count_launch(); }
+        { gen_w_kernel<uint16_t><<<g, 128, 0, st>>>(c->key, blk * nl, P, d, c->ldw, (uint16_t*)c->W); count_launch(); }
         ph_end(c, e0);
         int e1 = ph_begin(c, PH_XI);
         TcEpi epi{};
@@ -303,31 +333,34 @@ static diam_status prepare_block(diam_ctx* c, int64_t blk) {
         epi.ldd = d;
         epi.scale_dev = &c->ctl->ba;
         CK(tc_gemm_bf16(d, (int)rows, c->ldk, c->Lq16, c->ldk, (const uint16_t*)c->W, nullptr, c->ldw, 1, epi,
-                        &c->ctl->status, c->st, c->bn_xi));
+                        &c->ctl->status, st, c->bn_xi));
         ph_end(c, e1);
     } else {
         int e0 = ph_begin(c, PH_NOISE);
-        { gen_w_kernel<double><<<g, 128, 0, c->st>>>(c->key, blk * nl, P, d, c->ldw, (double*)c->W); count_launch(); }
+        { gen_w_kernel<double><<<g, 128, 0, st>>>(c->key, blk * nl, P, d, c->ldw, (double*)c->W); count_launch(); }
         ph_end(c, e0);
         int e1 = ph_begin(c, PH_XI);
         EpiStore epi{(double*)c->Xi, d, 1.0, &c->ctl->ba, 0.0};
-        CK((gemm_f64<true, true>(d, (int)rows, d, c->Lq64, d, (const double*)c->W, c->ldw, TileRange{1, 0}, epi, c->st)));
+        CK((gemm_f64<true, true>(d, (int)rows, d, c->Lq64, d, (const double*)c->W, c->ldw, TileRange{1, 0}, epi, st)));
         ph_end(c, e1);
     }
     c->xi_block = blk;
     return DIAM_OK;
 }
 
+static size_t bsum_elt(const diam_ctx* c) { return c->bf ? sizeof(float) : sizeof(double); }
+
 // Grow the per-interval, per-chain sums to hold interval blk (outside any graph capture).
 static diam_status ensure_bsum(diam_ctx* c, int64_t blk) {
     if (!c->cfg.keep_block_sums || blk < c->bcap) return DIAM_OK;
     const int P = c->P, d = c->d;
     int64_t ncap = std::max<int64_t>(2 * c->bcap, blk + 16);
-    double *nb = nullptr, *nlp = nullptr;
-    CKS(dalloc(c, &nb, sizeof(double) * (size_t)ncap * P * d));
+    void* nb = nullptr;
+    double* nlp = nullptr;
+    CKS(dalloc(c, (char**)&nb, bsum_elt(c) * (size_t)ncap * P * d));
     CKS(dalloc(c, &nlp, sizeof(double) * (size_t)ncap * P));
     if (c->bcap) {
-        CK(cudaMemcpyAsync(nb, c->bsum, sizeof(double) * (size_t)c->bcap * P * d, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(nb, c->bsum, bsum_elt(c) * (size_t)c->bcap * P * d, cudaMemcpyDeviceToDevice, c->st));
         CK(cudaMemcpyAsync(nlp, c->lpsum, sizeof(double) * (size_t)c->bcap * P, cudaMemcpyDeviceToDevice, c->st));
     }
     c->bsum = nb;
@@ -378,7 +411,7 @@ static diam_status do_step(diam_ctx* c) {
             int used = 1;
             CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, c->tsplit, epi,
                                    &c->ctl->status, c->st, &used, c->bn_target));
-            { finish_linear_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y, inv2s2, c->kind == TK_TANH,
+            { finish_linear_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y32, (float)inv2s2, c->kind == TK_TANH,
                                                             c->nchunk, c->key, c->qpart, c->lpart, iw, c->lp, c->q,
                                                             c->accf, c->ctl, c->tr); count_launch(); }
           }
@@ -396,16 +429,16 @@ static diam_status do_step(diam_ctx* c) {
     CK(cudaGetLastError());
     ph_end(c, e1);
     int e2 = ph_begin(c, PH_ACCEPT);
-    double* bs = c->cfg.keep_block_sums ? c->bsum : nullptr;
+    void* bs = c->cfg.keep_block_sums ? c->bsum : nullptr;
     double* ls = c->cfg.keep_block_sums ? c->lpsum : nullptr;
     if constexpr (BF) {
         { select_kernel<T, float><<<grid2, kThreads, 0, c->st>>>(d, P, c->nl, c->ctl, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
                                                                 (const T*)c->Zp, (float*)c->hist, c->ldh, (const T*)c->cenT,
-                                                                bs, ls, c->lp); count_launch(); }
+                                                                (float*)bs, ls, c->lp); count_launch(); }
     } else {
         { select_kernel<T, double><<<grid2, kThreads, 0, c->st>>>(d, P, c->nl, c->ctl, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
                                                                  (const T*)c->Zp, (double*)c->hist, c->ldh, (const T*)c->cenT,
-                                                                 bs, ls, c->lp); count_launch(); }
+                                                                 (double*)bs, ls, c->lp); count_launch(); }
     }
     { advance_kernel<<<1, 1, 0, c->st>>>(c->ctl); count_launch(); }
     CK(cudaGetLastError());
@@ -451,7 +484,7 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
         epi.delta = c->delta;
         epi.inb = 1.0 / nb;
         epi.w = w;
-        CK(tc_gemm_bf16(d, d, ldt, c->histT, ldt, c->histT, nullptr, ldt, 0, epi, &c->ctl->status, c->st));
+        CK(tc_gemm_bf16(d, d, ldt, c->histT, ldt, c->histT, nullptr, ldt, 0, epi, &c->ctl->status, c->st, 256));
     } else {
         const double* H = (const double*)c->hist + (size_t)s0 * P * c->ldh;
         EpiFold epi{c->M2, d, c->svec, c->delta, 1.0 / nb, w};
@@ -483,7 +516,7 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
         CK(cholesky_f64(c->Cw, d, d, &c->ctl->chol_info, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status));
         CKS(sync_and_check(c));
         int info = 0;
-        CK(cudaMemcpy(&info, &c->ctl->chol_info, sizeof(int), cudaMemcpyDeviceToHost));
+        CK(d2h(c, &info, &c->ctl->chol_info, sizeof(int)));
         ok = (info == 0);
         eps *= 100.0;
         c->chol_attempts++;
@@ -513,8 +546,8 @@ static diam_status block_end(diam_ctx* c, int64_t blk) {
     CKS(sync_and_check(c));
     prof_flush(c);
     unsigned long long acc = 0, nonf = 0;
-    CK(cudaMemcpy(&acc, &c->ctl->acc_block, sizeof(acc), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&nonf, &c->ctl->nonfinite, sizeof(nonf), cudaMemcpyDeviceToHost));
+    CK(d2h(c, &acc, &c->ctl->acc_block, sizeof(acc)));
+    CK(d2h(c, &nonf, &c->ctl->nonfinite, sizeof(nonf)));
     c->acc_all += (int64_t)acc;
     c->nonfinite = nonf;
     const diam_config& g = c->cfg;
@@ -577,7 +610,7 @@ static diam_status run_steps(diam_ctx* c, int64_t n_steps) {
             { centre_kernel<T><<<blocks_for(c->d), kThreads, 0, c->st>>>(c->d, c->P, (const T*)c->X, (T*)c->cenT, c->cen64); count_launch(); }
             c->begun_block = blk;
         }
-        if (c->xi_block != blk) CKS(prepare_block<T>(c, blk));
+        if (c->xi_block != blk) CKS(prepare_block<T>(c, blk, c->st));
         CKS(ensure_bsum(c, blk));
         const bool whole = s == 0 && n_steps >= c->nl && c->cfg.graphs && c->kind != TK_CALLBACK && !c->cfg.profile;
         if (whole) {
@@ -604,8 +637,18 @@ static diam_status autotune(diam_ctx* c) {
         epi.D = c->ws;
         epi.ldd = c->dy;
         epi.split_stride = (size_t)c->P * c->dy;
-        c->bn_target = tc_autotune(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, c->tsplit, 0, epi,
-                                   &c->ctl->status, c->st, nullptr);
+        // tile width and split of K together: each split count gets its best width, the fastest pair wins
+        float best = 1e30f;
+        for (int sp = 1; sp <= TSPLIT_MAX && sp <= 2 * c->ldk / 64; sp *= 2) {
+            float ms = 1e30f;
+            const int bn = tc_autotune(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, sp, 0, epi,
+                                       &c->ctl->status, c->st, &ms);
+            if (ms < best) {
+                best = ms;
+                c->bn_target = bn;
+                c->tsplit = sp;
+            }
+        }
     }
     TcEpi ex{};
     ex.mode = TC_STORE;
@@ -633,12 +676,12 @@ static diam_status init_state(diam_ctx* c, const double* x0, const double* C0, c
         CK(cholesky_f64(c->L, d, d, &c->ctl->chol_info, c->st));
         CKS(sync_and_check(c));
         int info = 0;
-        CK(cudaMemcpy(&info, &c->ctl->chol_info, sizeof(int), cudaMemcpyDeviceToHost));
+        CK(d2h(c, &info, &c->ctl->chol_info, sizeof(int)));
         if (info) return fail(c, DIAM_EINVAL, "diam_init", "C0 is not positive definite");
     } else {
         std::vector<double> I((size_t)d * d, 0.0);
         for (int i = 0; i < d; ++i) I[(size_t)i * d + i] = 1.0;
-        CK(cudaMemcpy(c->L, I.data(), sizeof(double) * d * d, cudaMemcpyHostToDevice));
+        CK(h2d(c, c->L, I.data(), sizeof(double) * d * d));
     }
     CKS(quantise(c));
     if (xref0) {
@@ -674,11 +717,11 @@ static diam_status alloc_all(diam_ctx* c) {
     CKS(dalloc(c, &c->accf, (size_t)P));
     CKS(dalloc(c, &c->s16, sizeof(double) * d));
     if (c->bf && c->dy > 0) {
-        // split the target product's K so that the tiles times the splits fill the 148 SMs once
+        // split of the target product's K (the autotuner picks it with the tile width): room for 8 planes
         int tiles = ((c->dy + 127) / 128) * ((P + 127) / 128);
         c->tsplit = std::max(1, std::min(8, 148 / std::max(tiles, 1)));
         c->tsplit = std::min(c->tsplit, c->ldk / 64);
-        CKS(dalloc(c, &c->ws, sizeof(float) * (size_t)c->tsplit * P * c->dy));
+        CKS(dalloc(c, &c->ws, sizeof(float) * (size_t)TSPLIT_MAX * P * c->dy));
     }
     for (double** p : {&c->xref64, &c->mean, &c->cen64, &c->svec, &c->delta}) CKS(dalloc(c, p, sizeof(double) * d));
     CKS(dalloc(c, &c->colpart, sizeof(double) * 64 * d));
@@ -746,23 +789,35 @@ static diam_status upload_target(diam_ctx* c, const diam_target* tg) {
         }
     }
     CKS(dalloc(c, &c->inv_lam, sizeof(double) * d));
-    CK(cudaMemcpy(c->inv_lam, il.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
+    CK(h2d(c, c->inv_lam, il.data(), sizeof(double) * d));
     c->tg.inv_lam = c->inv_lam;
+    {
+        std::vector<float> il32(il.begin(), il.end());
+        CKS(dalloc(c, &c->inv_lam32, sizeof(float) * d));
+        CK(h2d(c, c->inv_lam32, il32.data(), sizeof(float) * d));
+        c->tg.inv_lam32 = c->inv_lam32;
+    }
     if (c->kind == TK_DENSE || c->kind == TK_TANH) {
         const double* M = c->kind == TK_DENSE ? tg->G : tg->A;
         if (!M || dy <= 0) return fail(c, DIAM_EINVAL, "diam_init", "target needs its matrix and d_y");
         if (c->kind == TK_TANH && (!tg->y || !(tg->sigma > 0)))
             return fail(c, DIAM_EINVAL, "diam_init", "tanh target needs y and sigma > 0");
         CKS(dalloc(c, &c->Gm, sizeof(double) * (size_t)dy * d));
-        CK(cudaMemcpy(c->Gm, M, sizeof(double) * (size_t)dy * d, cudaMemcpyHostToDevice));
+        CK(h2d(c, c->Gm, M, sizeof(double) * (size_t)dy * d));
         if (c->bf) {
             CKS(dalloc(c, &c->Gq16, sizeof(uint16_t) * (size_t)dy * c->ldk));
             { to_bf16_rows_kernel<<<dim3(blocks_for(c->ldk), dy), kThreads, 0, c->st>>>(dy, d, c->Gm, c->Gq16, c->ldk); count_launch(); }
             CK(cudaGetLastError());
         }
         CKS(dalloc(c, &c->y, sizeof(double) * std::max(dy, 1)));
-        if (tg->y) CK(cudaMemcpy(c->y, tg->y, sizeof(double) * dy, cudaMemcpyHostToDevice));
+        CKS(dalloc(c, &c->y32, sizeof(float) * std::max(dy, 1)));
+        if (tg->y) {
+            CK(h2d(c, c->y, tg->y, sizeof(double) * dy));
+            std::vector<float> y32(tg->y, tg->y + dy);
+            CK(h2d(c, c->y32, y32.data(), sizeof(float) * dy));
+        }
     }
+    CK(cudaStreamSynchronize(c->st));   // the staged host copies are complete before the host arrays go
     return DIAM_OK;
 }
 
@@ -846,6 +901,12 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
         }
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        diam_destroy(c);
+        return DIAM_ECUDA;
+    }
     diam_status s = alloc_all(c);
     if (s == DIAM_OK) s = upload_target(c, tg);
     if (s == DIAM_OK) s = c->bf ? init_state<float>(c, x0, C0, xref0) : init_state<double>(c, x0, C0, xref0);
@@ -884,8 +945,8 @@ diam_status diam_sync_moments(diam_ctx* c, const double* ext_mean, const double*
         const int d = c->d;
         double* em = c->svec;  // interval scratch is free between intervals only: use the refresh buffers
         CKS(sync_and_check(c));
-        CK(cudaMemcpy(c->Cw, ext_M2, sizeof(double) * d * d, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(c->work, ext_mean, sizeof(double) * d, cudaMemcpyHostToDevice));
+        CK(h2d(c, c->Cw, ext_M2, sizeof(double) * d * d));
+        CK(h2d(c, c->work, ext_mean, sizeof(double) * d));
         double nn = (double)c->n, ne = (double)ext_n;
         { merge_mean_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, c->mean, c->work, em, ne / (nn + ne)); count_launch(); }
         { merge_moments_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, c->Cw, em, nn * ne / (nn + ne)); count_launch(); }
@@ -899,9 +960,9 @@ static diam_status read_moments(diam_ctx* c, double* mean, double* M, int64_t* n
     CKS(check_usable(c));
     CKS(sync_and_check(c));
     const int d = c->d;
-    if (mean) CK(cudaMemcpy(mean, c->mean, sizeof(double) * d, cudaMemcpyDeviceToHost));
+    if (mean) CK(d2h(c, mean, c->mean, sizeof(double) * d));
     if (M) {
-        CK(cudaMemcpy(M, c->M2, sizeof(double) * d * d, cudaMemcpyDeviceToHost));
+        CK(d2h(c, M, c->M2, sizeof(double) * d * d));
         double s = (as_cov && c->n > 0) ? 1.0 / (double)c->n : 1.0;
         for (int i = 0; i < d; ++i)
             for (int j = 0; j <= i; ++j) {
@@ -930,16 +991,16 @@ diam_status diam_get_state(diam_ctx* c, double* x, double* lp, diam_stats* stats
         if (c->bf) {
             { convert_kernel<float, double><<<blocks_for(Pd), kThreads, 0, c->st>>>(Pd, (const float*)c->X, c->work); count_launch(); }
             CK(cudaStreamSynchronize(c->st));
-            CK(cudaMemcpy(x, c->work, sizeof(double) * Pd, cudaMemcpyDeviceToHost));
+            CK(d2h(c, x, c->work, sizeof(double) * Pd));
         } else {
-            CK(cudaMemcpy(x, c->X, sizeof(double) * Pd, cudaMemcpyDeviceToHost));
+            CK(d2h(c, x, c->X, sizeof(double) * Pd));
         }
     }
-    if (lp) CK(cudaMemcpy(lp, c->lp, sizeof(double) * c->P, cudaMemcpyDeviceToHost));
+    if (lp) CK(d2h(c, lp, c->lp, sizeof(double) * c->P));
     if (stats) {
         unsigned long long acc = 0, nonf = 0;
-        CK(cudaMemcpy(&acc, &c->ctl->acc_block, sizeof(acc), cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(&nonf, &c->ctl->nonfinite, sizeof(nonf), cudaMemcpyDeviceToHost));
+        CK(d2h(c, &acc, &c->ctl->acc_block, sizeof(acc)));
+        CK(d2h(c, &nonf, &c->ctl->nonfinite, sizeof(nonf)));
         stats->steps = c->t;
         stats->n = c->n;
         stats->accepted = c->acc_all + (c->t % c->nl ? (int64_t)acc : 0);
@@ -956,9 +1017,9 @@ diam_status diam_get_factor(diam_ctx* c, double* L, double* Lq, double* xref, do
     CKS(check_usable(c));
     CKS(sync_and_check(c));
     const int d = c->d;
-    if (L) CK(cudaMemcpy(L, c->L, sizeof(double) * d * d, cudaMemcpyDeviceToHost));
-    if (Lq) CK(cudaMemcpy(Lq, c->Lq64, sizeof(double) * d * d, cudaMemcpyDeviceToHost));
-    if (xref) CK(cudaMemcpy(xref, c->xref64, sizeof(double) * d, cudaMemcpyDeviceToHost));
+    if (L) CK(d2h(c, L, c->L, sizeof(double) * d * d));
+    if (Lq) CK(d2h(c, Lq, c->Lq64, sizeof(double) * d * d));
+    if (xref) CK(d2h(c, xref, c->xref64, sizeof(double) * d));
     if (beta) *beta = c->beta;
     return DIAM_OK;
 }
@@ -970,11 +1031,11 @@ diam_status diam_get_trace(diam_ctx* c, double* lp_prop, double* q_prop, double*
     int64_t T = std::min<int64_t>(std::min<int64_t>(c->t, c->tr.steps), n_steps);
     size_t nt = (size_t)std::max<int64_t>(T, 0) * c->P;
     if (nt == 0) return DIAM_OK;
-    if (lp_prop) CK(cudaMemcpy(lp_prop, c->tr.lp, nt * 8, cudaMemcpyDeviceToHost));
-    if (q_prop) CK(cudaMemcpy(q_prop, c->tr.q, nt * 8, cudaMemcpyDeviceToHost));
-    if (q_cur) CK(cudaMemcpy(q_cur, c->tr.qc, nt * 8, cudaMemcpyDeviceToHost));
-    if (loga) CK(cudaMemcpy(loga, c->tr.loga, nt * 8, cudaMemcpyDeviceToHost));
-    if (acc) CK(cudaMemcpy(acc, c->tr.acc, nt, cudaMemcpyDeviceToHost));
+    if (lp_prop) CK(d2h(c, lp_prop, c->tr.lp, nt * 8));
+    if (q_prop) CK(d2h(c, q_prop, c->tr.q, nt * 8));
+    if (q_cur) CK(d2h(c, q_cur, c->tr.qc, nt * 8));
+    if (loga) CK(d2h(c, loga, c->tr.loga, nt * 8));
+    if (acc) CK(d2h(c, acc, c->tr.acc, nt));
     return DIAM_OK;
 }
 
@@ -985,8 +1046,14 @@ diam_status diam_get_block_sums(diam_ctx* c, double* xsum, double* lpsum, int64_
     int64_t nb = std::min<int64_t>(*n_blocks, std::min<int64_t>(c->bcap, (c->t + c->nl - 1) / c->nl));
     if (!c->cfg.keep_block_sums) nb = 0;
     if (nb > 0) {
-        if (xsum) CK(cudaMemcpy(xsum, c->bsum, sizeof(double) * (size_t)nb * c->P * c->d, cudaMemcpyDeviceToHost));
-        if (lpsum) CK(cudaMemcpy(lpsum, c->lpsum, sizeof(double) * (size_t)nb * c->P, cudaMemcpyDeviceToHost));
+        const size_t n = (size_t)nb * c->P * c->d;
+        if (xsum && !c->bf) CK(d2h(c, xsum, c->bsum, sizeof(double) * n));
+        if (xsum && c->bf) {   // FP32 sums, widened on the host
+            std::vector<float> tmp(n);
+            CK(d2h(c, tmp.data(), c->bsum, sizeof(float) * n));
+            for (size_t k = 0; k < n; ++k) xsum[k] = (double)tmp[k];
+        }
+        if (lpsum) CK(d2h(c, lpsum, c->lpsum, sizeof(double) * (size_t)nb * c->P));
     }
     *n_blocks = nb;
     return DIAM_OK;
@@ -1019,7 +1086,7 @@ static std::vector<std::pair<void*, size_t>> state_buffers(diam_ctx* c) {
         v.push_back({c->tr.acc, nt});
     }
     if (c->bcap) {
-        v.push_back({c->bsum, 8 * (size_t)c->bcap * Pd});
+        v.push_back({c->bsum, bsum_elt(c) * (size_t)c->bcap * Pd});
         v.push_back({c->lpsum, 8 * (size_t)c->bcap * c->P});
     }
     return v;
@@ -1046,7 +1113,7 @@ diam_status diam_save(diam_ctx* c, void* buf, size_t* size) {
     memcpy(o, &hs, sizeof(hs));
     o += sizeof(hs);
     for (auto& b : bufs) {
-        CK(cudaMemcpy(o, b.first, b.second, cudaMemcpyDeviceToHost));
+        CK(d2h(c, o, b.first, b.second));
         o += b.second;
     }
     *size = total;
@@ -1060,8 +1127,9 @@ diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
     memcpy(&hs, buf, sizeof(hs));
     CKS(sync_and_check(c));
     if (hs.bcap > c->bcap) {  // grow the interval-sum store to the saved capacity
-        double *nb = nullptr, *nlp = nullptr;
-        CKS(dalloc(c, &nb, sizeof(double) * (size_t)hs.bcap * c->P * c->d));
+        void* nb = nullptr;
+        double* nlp = nullptr;
+        CKS(dalloc(c, (char**)&nb, bsum_elt(c) * (size_t)hs.bcap * c->P * c->d));
         CKS(dalloc(c, &nlp, sizeof(double) * (size_t)hs.bcap * c->P));
         c->bsum = nb;
         c->lpsum = nlp;
@@ -1074,7 +1142,7 @@ diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
     if (total != size) return fail(c, DIAM_EINVAL, "diam_load", "checkpoint does not match this context");
     const char* in = (const char*)buf + sizeof(hs);
     for (auto& b : bufs) {
-        CK(cudaMemcpy(b.first, in, b.second, cudaMemcpyHostToDevice));
+        CK(h2d(c, b.first, in, b.second));
         in += b.second;
     }
     c->t = hs.t; c->n = hs.n; c->acc_refresh = hs.acc_refresh; c->acc_all = hs.acc_all;
@@ -1147,7 +1215,7 @@ diam_status diam_da_get_stats(diam_ctx* c, diam_da_stats* s) {
     if (!c->da || !s) return fail(c, DIAM_EINVAL, "diam_da_get_stats");
     CKS(sync_and_check(c));
     DaCounters hc{};
-    CK(cudaMemcpy(&hc, c->da->cnt, sizeof(hc), cudaMemcpyDeviceToHost));
+    CK(d2h(c, &hc, c->da->cnt, sizeof(hc)));
     s->trainings = c->da->trainings;
     s->stage1_tested = (int64_t)hc.tested;
     s->stage1_passed = (int64_t)hc.passed;
@@ -1167,7 +1235,7 @@ diam_status diam_da_get_weights(diam_ctx* c, double* W1, double* b1, double* W2,
     auto down = [&](double* dst, const float* src, size_t n) -> diam_status {
         if (!dst) return DIAM_OK;
         std::vector<float> t(n);
-        CK(cudaMemcpy(t.data(), src, sizeof(float) * n, cudaMemcpyDeviceToHost));
+        CK(d2h(c, t.data(), src, sizeof(float) * n));
         for (size_t i = 0; i < n; ++i) dst[i] = t[i];
         return DIAM_OK;
     };
@@ -1191,8 +1259,8 @@ diam_status diam_da_grad(diam_ctx* c, int32_t B, const double* U, const double* 
             xb[(size_t)b * ldk + i] = (uint16_t)(bits >> 16);
         }
     std::vector<float> tf(t, t + B);
-    CK(cudaMemcpy(a->Xb, xb.data(), sizeof(uint16_t) * xb.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(a->tb, tf.data(), sizeof(float) * B, cudaMemcpyHostToDevice));
+    CK(h2d(c, a->Xb, xb.data(), sizeof(uint16_t) * xb.size()));
+    CK(h2d(c, a->tb, tf.data(), sizeof(float) * B));
     const int saveB = a->B;
     a->B = B;
     diam_status s = da_backward(c);
@@ -1200,7 +1268,7 @@ diam_status diam_da_grad(diam_ctx* c, int32_t B, const double* U, const double* 
     CKS(s);
     CKS(sync_and_check(c));
     std::vector<double> lpart(B);
-    CK(cudaMemcpy(lpart.data(), a->loss_parts, sizeof(double) * B, cudaMemcpyDeviceToHost));
+    CK(d2h(c, lpart.data(), a->loss_parts, sizeof(double) * B));
     if (loss) {
         double L = 0.0;
         for (double v : lpart) L += v;
@@ -1209,20 +1277,20 @@ diam_status diam_da_grad(diam_ctx* c, int32_t B, const double* U, const double* 
     std::vector<float> g;
     if (gW1) {
         g.resize((size_t)ldk * h1);
-        CK(cudaMemcpy(g.data(), a->gW1T, sizeof(float) * g.size(), cudaMemcpyDeviceToHost));
+        CK(d2h(c, g.data(), a->gW1T, sizeof(float) * g.size()));
         for (int i = 0; i < h1; ++i)
             for (int k = 0; k < d; ++k) gW1[(size_t)i * d + k] = g[(size_t)k * h1 + i];
     }
     if (gW2) {
         g.resize((size_t)h1 * h2);
-        CK(cudaMemcpy(g.data(), a->gW2T, sizeof(float) * g.size(), cudaMemcpyDeviceToHost));
+        CK(d2h(c, g.data(), a->gW2T, sizeof(float) * g.size()));
         for (int o = 0; o < h2; ++o)
             for (int i = 0; i < h1; ++i) gW2[(size_t)o * h1 + i] = g[(size_t)i * h2 + o];
     }
     auto down = [&](double* dst, const float* src, size_t n) -> diam_status {
         if (!dst) return DIAM_OK;
         std::vector<float> tt(n);
-        CK(cudaMemcpy(tt.data(), src, sizeof(float) * n, cudaMemcpyDeviceToHost));
+        CK(d2h(c, tt.data(), src, sizeof(float) * n));
         for (size_t i = 0; i < n; ++i) dst[i] = tt[i];
         return DIAM_OK;
     };
@@ -1241,6 +1309,12 @@ void diam_destroy(diam_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     ozaki_ws_release(c->oz);
     for (void* p : c->allocs) cudaFree(p);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c->da;
     delete c;

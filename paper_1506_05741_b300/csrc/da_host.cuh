@@ -134,7 +134,7 @@ static diam_status da_train_now(diam_ctx* c, double* rmse_out) {
     int e0 = ph_begin(c, PH_TRAIN);
     CKS(sync_and_check(c));
     DaCounters hc{};
-    CK(cudaMemcpy(&hc, a->cnt, sizeof(hc), cudaMemcpyDeviceToHost));
+    CK(d2h(c, &hc, a->cnt, sizeof(hc)));
     if (hc.filled < 20) return fail(c, DIAM_EINVAL, "diam_da_train", "ring buffer holds too few pairs");
     // normalisation frozen for this surrogate: shift = x_ref, scale = 1/sqrt(C_ii), targets (lp - mu)/sigma
     CK(cudaMemcpyAsync(a->shift, c->xref, sizeof(float) * c->d, cudaMemcpyDeviceToDevice, c->st));
@@ -193,7 +193,14 @@ static diam_status da_step(diam_ctx* c) {
     const int nthr = (P + 31) / 32 * 32;
     { stage1_kernel<<<1, nthr, 0, c->st>>>(P, c->nchunk, c->key, c->ctl, a->active ? 1 : 0, c->qpart, c->lpart, inv_infl2(c), c->q, a->s_prop,
                                          a->s_cur, a->qsave, a->idx, c->accf, nullptr, a->cnt, c->tr); count_launch(); }
-    { gather_rows_kernel<<<P, kThreads, 0, c->st>>>(a->cnt, a->idx, c->op_hi, c->op_lo, a->Chi, a->Clo, c->ldk); count_launch(); }
+    // stage 1 off: every chain passes in chain order, so the exact test reads the proposals' rows in place
+    const uint16_t* bh = c->op_hi;
+    const uint16_t* bl = c->op_lo;
+    if (a->active) {
+        { gather_rows_kernel<<<P, kThreads, 0, c->st>>>(a->cnt, a->idx, c->op_hi, c->op_lo, a->Chi, a->Clo, c->ldk); count_launch(); }
+        bh = a->Chi;
+        bl = a->Clo;
+    }
     CK(cudaGetLastError());
     ph_end(c, e0);
     int e1 = ph_begin(c, PH_TARGET);
@@ -204,11 +211,11 @@ static diam_status da_step(diam_ctx* c) {
     epi.split_stride = (size_t)P * c->dy;
     epi.n_dev = &a->cnt->count;
     int used = 1;
-    CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, a->Chi, a->Clo, c->ldk, c->tsplit, epi, &c->ctl->status,
+    CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, bh, bl, c->ldk, c->tsplit, epi, &c->ctl->status,
                            c->st, &used, c->bn_target));
-    { finish_da_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y, 1.0 / (2.0 * c->sigma * c->sigma),
+    { finish_da_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y32, (float)(1.0 / (2.0 * c->sigma * c->sigma)),
                                                 c->kind == TK_TANH, c->nchunk, c->key, c->lpart, a->qsave, a->idx, a->cnt,
-                                                a->active ? 1 : 0, a->s_prop, a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, a->Chi, a->ring_x,
+                                                a->active ? 1 : 0, a->s_prop, a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, bh, a->ring_x,
                                                 a->ring_lp, (long long)a->cfg.ring, c->ldk); count_launch(); }
     { ring_advance_kernel<<<1, 1, 0, c->st>>>(a->cnt, (long long)a->cfg.ring); count_launch(); }
     CK(cudaGetLastError());
@@ -221,7 +228,7 @@ static diam_status da_after_interval(diam_ctx* c) {
     DaState* a = c->da;
     a->intervals++;
     DaCounters hc{};
-    CK(cudaMemcpy(&hc, a->cnt, sizeof(hc), cudaMemcpyDeviceToHost));
+    CK(d2h(c, &hc, a->cnt, sizeof(hc)));
     const int64_t period = (int64_t)std::max(1, c->cfg.M) * std::max(1, a->cfg.retrain_every);
     const bool first = a->trainings == 0 && hc.filled >= a->cfg.first_train_min;
     const bool due = a->trainings > 0 && a->intervals % period == 0;
@@ -273,13 +280,13 @@ static diam_status da_alloc(diam_ctx* c, const diam_da_config* g, const double* 
     std::vector<float> tmp;
     auto up = [&](float* dst, const double* src, size_t n) -> diam_status {
         tmp.assign(src, src + n);
-        CK(cudaMemcpy(dst, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+        CK(h2d(c, dst, tmp.data(), sizeof(float) * n));
         return DIAM_OK;
     };
     CKS(up(a->W1, W1, (size_t)h1 * d)); CKS(up(a->b1, b1, h1)); CKS(up(a->W2, W2, (size_t)h2 * h1));
     CKS(up(a->b2, b2, h2)); CKS(up(a->w3, w3, h2)); CKS(up(a->b3, b3, 1));
     std::vector<float> ones((size_t)d, 1.0f);
-    CK(cudaMemcpy(a->scale, ones.data(), sizeof(float) * d, cudaMemcpyHostToDevice));
+    CK(h2d(c, a->scale, ones.data(), sizeof(float) * d));
     { quant_weights_kernel<<<std::min<unsigned>(148 * 8, blocks_for((size_t)h1 * d)), kThreads, 0, c->st>>>(h1, d, a->W1, a->W1q, ldk, nullptr, 0); count_launch(); }
     { quant_weights_kernel<<<std::min<unsigned>(148 * 8, blocks_for((size_t)h2 * h1)), kThreads, 0, c->st>>>(h2, h1, a->W2, a->W2q, h1, a->W2Tq, h2); count_launch(); }
     CK(cudaGetLastError());

@@ -128,7 +128,7 @@ __global__ void gather_rows_kernel(const DaCounters* cnt, const int* __restrict_
 // log a2 = log pi(x*) - log pi(x) - s(x*) + s(x), accept iff log u < log a2 (tag 1); the evaluated pair
 // (x*, log pi(x*)) goes to the ring buffer.
 __global__ void __launch_bounds__(256) finish_da_kernel(int P, int dy, int nsplit, const float* __restrict__ ws,
-                                                         const double* __restrict__ y, double inv2s2, int tanh_mode,
+                                                         const float* __restrict__ y32, float inv2s2, int tanh_mode,
                                                          int nchunk, Key key,
                                                          const double* __restrict__ lpart,
                                                          const double* __restrict__ qsave, const int* __restrict__ idx,
@@ -137,24 +137,24 @@ __global__ void __launch_bounds__(256) finish_da_kernel(int P, int dy, int nspli
                                                          TraceDev tr, const uint16_t* __restrict__ chi,
                                                          uint16_t* __restrict__ ring_x, float* __restrict__ ring_lp,
                                                          long long ring_cap, int ldk) {
-    __shared__ double sh[32];
+    __shared__ float shf[32];
     const int k = blockIdx.x;
     if (k >= cnt->count) return;
     const int p = idx[k];
     const int64_t t = ctl->t_cur;
     const size_t plane = (size_t)P * dy;
-    double acc = 0.0;
+    float af = 0.f;   // the linear-map terms in FP32, as in the plain exact test
     for (int m = threadIdx.x; m < dy; m += blockDim.x) {
         float u = 0.f;
         for (int s = 0; s < nsplit; ++s) u += ws[s * plane + (size_t)k * dy + m];
         if (tanh_mode) {
-            double r = y[m] - (double)tanhf(u);
-            acc -= r * r * inv2s2;
+            const float r = y32[m] - tanhf(u);
+            af -= r * r * inv2s2;
         } else {
-            acc -= 0.5 * (double)u * (double)u;
+            af -= 0.5f * u * u;
         }
     }
-    acc = block_sum(acc, sh);
+    double acc = (double)block_sum(af, shf);
     const double lmap = acc;   // the linear-map part of log pi(x*): what the network learns
     for (int c = 0; c < nchunk; ++c) acc += lpart[(size_t)c * P + p];
     const long long slot = (cnt->head + k) % ring_cap;

@@ -13,16 +13,27 @@ namespace diam {
 
 constexpr int CH_NB = 64;
 
-// 1/D by the Newton-Raphson iteration y <- y + y (1 - D y) from an FP32 seed (two steps: relative error
-// below 2^-46 after the first, at rounding level after the second); outside the FP32 range, a division.
-__device__ __forceinline__ double recip_newton(double D) {
-    const double aD = fabs(D);
-    if (!(aD > 1e-30 && aD < 1e30)) return 1.0 / D;
-    double y = (double)__frcp_rn((float)D);
-    double e = fma(-D, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-D, y, 1.0);
-    return fma(y, e, y);
+// 1/D for the pivot chain, with as few FP64 instructions as possible (on B300 each one costs about 64
+// cycles of latency, one lane or thirty-two): the seed y0 ~ 1/D (relative error below 2^-21) comes from an
+// FP32 reciprocal of D's leading 23 mantissa bits, assembled and taken apart with integer operations; one
+// cubic Newton-Raphson step y = y0 (1 + e + e^2), e = 1 - D y0, leaves a relative error of e^3 < 2^-63 plus
+// the rounding of its two fused multiply-adds. Outside the exponents where that holds, a division.
+__device__ __forceinline__ double recip_pivot(double D) {
+    const long long b = __double_as_longlong(D);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 2 || e > 2044) return 1.0 / D;
+    const float m = __uint_as_float(0x3F800000u | (unsigned)((b >> 29) & 0x7FFFFF));   // [1, 2)
+    const unsigned rb = __float_as_uint(__frcp_rn(m));                                 // (0.5, 1]
+    const int er = (int)((rb >> 23) & 0xff) - 127;                                     // -1 or 0
+    const double y0 = __longlong_as_double(((long long)(er + 2046 - e) << 52) | ((long long)(rb & 0x7FFFFF) << 29));
+    const double eps = fma(-D, y0, 1.0);
+    return fma(y0, fma(eps, eps, eps), y0);
+}
+
+// D > 0 and finite, from the bits (no FP64 comparison on the pivot chain).
+__device__ __forceinline__ bool positive_finite(double D) {
+    const long long b = __double_as_longlong(D);
+    return b > 0 && ((b >> 52) & 0x7ff) != 0x7ff;
 }
 
 // Cholesky of the nb x nb diagonal block at (k0, k0), nb <= 64: lower part in, L out, upper part zeroed.
@@ -36,18 +47,18 @@ __device__ __forceinline__ double recip_newton(double D) {
 // then one barrier.
 constexpr int DIAG_THREADS = 512;
 
+// Warp 0 publishes column c: rows c + lane (v0) and c + 32 + lane (v1), D_c = v0 on lane 0.
 __device__ __forceinline__ void diag_publish(int c, double v0, double v1, int lane, int nb, int k0, int* info,
                                              double* dpiv, double (*colb)[CH_NB], double (*scol)[CH_NB]) {
-    const double D = __shfl_sync(0xffffffffu, v0, 0);
     double r = 0.0;
     if (lane == 0) {
-        if (D > 0.0) {
-            r = recip_newton(D);
+        if (positive_finite(v0)) {
+            r = recip_pivot(v0);
         } else {   // not positive definite: NaN propagates and the caller discards the factor
             r = __longlong_as_double(0x7ff8000000000000ll);
             if (info) atomicCAS(info, 0, k0 + c + 1);
         }
-        dpiv[c] = D;
+        dpiv[c] = v0;
     }
     r = __shfl_sync(0xffffffffu, r, 0);
     const int b = c & 1;
@@ -55,9 +66,11 @@ __device__ __forceinline__ void diag_publish(int c, double v0, double v1, int la
         colb[b][c + lane] = v0;
         scol[b][c + lane] = v0 * r;
     }
-    if (c + lane + 32 < nb) {
-        colb[b][c + lane + 32] = v1;
-        scol[b][c + lane + 32] = v1 * r;
+    if (c + 32 < nb) {   // warp-uniform: the second half exists
+        if (c + 32 + lane < nb) {
+            colb[b][c + 32 + lane] = v1;
+            scol[b][c + 32 + lane] = v1 * r;
+        }
     }
 }
 
@@ -98,9 +111,11 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(double* __restr
                     v0 = fma(-colb[b][i0], s, a[i0][jn]);
                     a[i0][jn] = v0;
                 }
-                if (i1 < nb) {
-                    v1 = fma(-colb[b][i1], s, a[i1][jn]);
-                    a[i1][jn] = v1;
+                if (jn + 32 < nb) {   // warp-uniform, so no FP64 instruction is issued for an empty half
+                    if (i1 < nb) {
+                        v1 = fma(-colb[b][i1], s, a[i1][jn]);
+                        a[i1][jn] = v1;
+                    }
                 }
                 diag_publish(jn, v0, v1, lane, nb, k0, info, dpiv, colb, scol);
             }

@@ -134,7 +134,7 @@ diam_status diam_op_trsm_lower_f64_tc(int32_t n, int32_t nrows, const double* L,
 diam_status diam_op_gemm_bf16_tile(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda,
                                    const uint16_t* B, const uint16_t* B2, int32_t ldb, int32_t a_lower, float scale,
                                    float* D, int32_t ldd, int32_t bn, void* stream) {
-    if (bn != 32 && bn != 64 && bn != 128) return DIAM_EINVAL;
+    if (bn != 32 && bn != 64 && bn != 128 && bn != 256) return DIAM_EINVAL;
     if (!A || !B || !D || M <= 0 || N <= 0 || K <= 0 || K % 64 || lda % 64 || ldb % 64 || K > lda || K > ldb ||
         ldd < M)
         return DIAM_EINVAL;

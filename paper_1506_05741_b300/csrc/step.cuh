@@ -41,7 +41,8 @@ enum : int { TK_DIAG = 0, TK_DENSE = 1, TK_TANH = 2, TK_BANANA = 3, TK_REF = 4, 
 struct TargetDev {
     int kind;
     int d_y;
-    const double* inv_lam;   // d, 1 / lambda_i
+    const double* inv_lam;     // d, 1 / lambda_i
+    const float* inv_lam32;    // the same in FP32 (BF16 mode: FP32 states)
     double ban_a, ban_b, ban_c;
 };
 
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
                                                       const Ctl* ctl, TargetDev tg, uint16_t* __restrict__ op_hi,
                                                       uint16_t* __restrict__ op_lo, int ldk) {
     __shared__ double sh[32];
+    __shared__ float shf[32];
     const int p = blockIdx.x, c = blockIdx.y;
     const int i0 = c * CHUNK, i1 = min(d, i0 + CHUNK);
     const T rho = (T)ctl->rho, ba = (T)ctl->ba;
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
                     vo[k] = ra[k] + rho * (xa[k] - ra[k]) + ia[k];
                     uo[k] = rho * za[k] + ba * wv[k];
                     qf += uo[k] * uo[k];
-                    if (prior && (tg.kind != TK_BANANA || i + k >= 2)) lf -= 0.5f * vo[k] * vo[k] * (float)tg.inv_lam[i + k];
+                    if (prior && (tg.kind != TK_BANANA || i + k >= 2)) lf -= 0.5f * vo[k] * vo[k] * tg.inv_lam32[i + k];
                     ho[k] = f32_to_bf16_bits(vo[k]);
                     lo[k] = f32_to_bf16_bits(vo[k] - bf16_bits_to_f32(ho[k]));
                 }
@@ -160,9 +162,17 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
                         make_uint2((uint32_t)lo[0] | ((uint32_t)lo[1] << 16), (uint32_t)lo[2] | ((uint32_t)lo[3] << 16));
                 }
             }
-            qacc = (double)qf;
-            lacc = (double)lf;
-            vec_done = true;
+            // block sums in FP32 too: FP64 adds run at about 1/64 of the FP32 rate on B300, and a tree of
+            // 256 partial sums loses about 8 ulps of FP32 (relative 5e-7), far inside the BF16-mode bounds
+            qf = block_sum(qf, shf);
+            lf = block_sum(lf, shf);
+            if (threadIdx.x == 0) {
+                double la = (double)lf;
+                if (tg.kind == TK_BANANA && c == 0) la += banana_head(tg, (double)xp[0], d > 1 ? (double)xp[1] : 0.0);
+                qpart[(size_t)c * P + p] = (double)qf;
+                lpart[(size_t)c * P + p] = la;
+            }
+            return;
         }
     }
     for (int i = i0 + threadIdx.x; !vec_done && i < i1; i += blockDim.x) {
@@ -286,29 +296,31 @@ __global__ void finish_kernel(int P, int nchunk, Key key, const double* __restri
 // One block per chain, for a linear-map target computed as split-K FP32 partial products ws[s][p][m]
 // (m < d_y): u_m = sum_s ws (fixed order), log-likelihood -(y_m - tanh u_m)^2 inv2s2 or -u_m^2 / 2, summed
 // in FP64; then the O(d) partials, q(x*) and the decision.
+// The linear-map terms in FP32 (FP32 products and sums over d_y; relative error ~1e-6 of the sum, inside
+// the BF16-mode bounds), the O(d) partials and the quadratic in FP64.
 __global__ void __launch_bounds__(256) finish_linear_kernel(int P, int dy, int nsplit, const float* __restrict__ ws,
-                                                             const double* __restrict__ y, double inv2s2, int tanh_mode,
+                                                             const float* __restrict__ y32, float inv2s2, int tanh_mode,
                                                              int nchunk, Key key,
                                                              const double* __restrict__ qpart,
                                                              const double* __restrict__ lpart, double inv_infl2,
                                                              double* lp, double* q, int8_t* accf, Ctl* ctl,
                                                              TraceDev tr) {
-    __shared__ double sh[32];
+    __shared__ float shf[32];
     const int p = blockIdx.x;
     const int64_t t = ctl->t_cur;
     const size_t plane = (size_t)P * dy;
-    double acc = 0.0;
+    float accf32 = 0.f;
     for (int m = threadIdx.x; m < dy; m += blockDim.x) {
         float u = 0.f;
         for (int s = 0; s < nsplit; ++s) u += ws[s * plane + (size_t)p * dy + m];
         if (tanh_mode) {
-            double r = y[m] - (double)tanhf(u);
-            acc -= r * r * inv2s2;
+            const float r = y32[m] - tanhf(u);
+            accf32 -= r * r * inv2s2;
         } else {
-            acc -= 0.5 * (double)u * (double)u;
+            accf32 -= 0.5f * u * u;
         }
     }
-    acc = block_sum(acc, sh);
+    double acc = (double)block_sum(accf32, shf);
     if (threadIdx.x == 0) {
         double qs = 0.0;
         for (int c = 0; c < nchunk; ++c) {
@@ -332,12 +344,12 @@ template <typename T, typename HT>
 __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, const Ctl* ctl, const int8_t* __restrict__ accf,
                                                      T* __restrict__ X, T* __restrict__ Z, const T* __restrict__ Xp,
                                                      const T* __restrict__ Zp, HT* __restrict__ hist_base, int ldh,
-                                                     const T* __restrict__ cen, double* __restrict__ bsum_base,
+                                                     const T* __restrict__ cen, HT* __restrict__ bsum_base,
                                                      double* __restrict__ lpsum_base, const double* __restrict__ lp) {
     const int p = blockIdx.x, c = blockIdx.y;
     const long long blk = ctl->t_cur / nl;
     HT* hist = hist_base ? hist_base + (size_t)ctl->s_cur * P * ldh : nullptr;
-    double* bsum = bsum_base ? bsum_base + (size_t)blk * P * d : nullptr;
+    HT* bsum = bsum_base ? bsum_base + (size_t)blk * P * d : nullptr;
     double* lpsum = lpsum_base ? lpsum_base + (size_t)blk * P : nullptr;
     const int i0 = c * CHUNK, i1 = min(d, i0 + CHUNK);
     const int a = accf[p];
@@ -346,9 +358,9 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, const
     const T* xp = Xp + (size_t)p * d;
     const T* zp = Zp + (size_t)p * d;
     HT* h = hist ? hist + (size_t)p * ldh : nullptr;
-    double* bs = bsum ? bsum + (size_t)p * d : nullptr;
+    HT* bs = bsum ? bsum + (size_t)p * d : nullptr;
     if constexpr (std::is_same<T, float>::value && std::is_same<HT, float>::value) {
-        if ((d & 3) == 0 && (ldh & 3) == 0 && !bs && h) {
+        if ((d & 3) == 0 && (ldh & 3) == 0 && h) {
             for (int i = i0 + 4 * threadIdx.x; i < i1; i += 4 * blockDim.x) {
                 float4 v = a ? *reinterpret_cast<const float4*>(xp + i) : *reinterpret_cast<const float4*>(x + i);
                 if (a) {
@@ -357,6 +369,10 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, const
                 }
                 const float4 cv = *reinterpret_cast<const float4*>(cen + i);
                 *reinterpret_cast<float4*>(h + i) = make_float4(v.x - cv.x, v.y - cv.y, v.z - cv.z, v.w - cv.w);
+                if (bs) {   // BF16 mode keeps the per-chain interval sums in FP32 (128-step sums, ~1e-5 relative)
+                    float4 b = *reinterpret_cast<float4*>(bs + i);
+                    *reinterpret_cast<float4*>(bs + i) = make_float4(b.x + v.x, b.y + v.y, b.z + v.z, b.w + v.w);
+                }
             }
             if (lpsum && c == 0 && threadIdx.x == 0) lpsum[p] += lp[p];
             return;
@@ -369,7 +385,7 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, const
             z[i] = zp[i];
         }
         if (h) h[i] = to_hist<T, HT>(v - cen[i]);
-        if (bs) bs[i] += (double)v;
+        if (bs) bs[i] += (HT)v;
     }
     if (lpsum && c == 0 && threadIdx.x == 0) lpsum[p] += lp[p];
 }
@@ -387,6 +403,19 @@ template <typename HT>
 __global__ void colsum_partial_kernel(const HT* __restrict__ H, int ldh, int rows, int d, double* __restrict__ part) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d) return;
+    if constexpr (std::is_same<HT, float>::value) {
+        // FP32 records: compensated FP32 summation (Kahan 1965), error ~2 ulps of FP32 on the sum whatever the
+        // number of rows, at FP32 rate
+        float s = 0.f, comp = 0.f;
+        for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+            const float yv = H[(size_t)r * ldh + i] - comp;
+            const float tv = s + yv;
+            comp = (tv - s) - yv;
+            s = tv;
+        }
+        part[(size_t)blockIdx.y * d + i] = (double)s - (double)comp;
+        return;
+    }
     double s = 0.0;
     for (int r = blockIdx.y; r < rows; r += gridDim.y) s += hist_val<HT>(H[(size_t)r * ldh + i]);
     part[(size_t)blockIdx.y * d + i] = s;
@@ -411,9 +440,14 @@ __global__ void __launch_bounds__(256) rowsum_bf16_kernel(const uint16_t* __rest
                                                           double* __restrict__ s16) {
     __shared__ double sh[32];
     const int i = blockIdx.x;
-    double acc = 0.0;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) acc += (double)bf16_bits_to_f32(HT_[(size_t)i * ldt + r]);
-    acc = block_sum(acc, sh);
+    float s = 0.f, comp = 0.f;   // compensated FP32 summation per thread (Kahan 1965), FP64 across threads
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const float yv = bf16_bits_to_f32(HT_[(size_t)i * ldt + r]) - comp;
+        const float tv = s + yv;
+        comp = (tv - s) - yv;
+        s = tv;
+    }
+    double acc = block_sum((double)s - (double)comp, sh);
     if (threadIdx.x == 0) s16[i] = acc;
 }
 

@@ -9,7 +9,7 @@
 
 namespace diam {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_BK = 64, TC_MAX_STAGES = 4;
 constexpr long long TC_WAIT_CYCLES = 1ll << 31;  // about one second at the B300 SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }

@@ -1,9 +1,10 @@
 // tc_gemm.cu -- BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // One CTA per 128 x BN output tile (cta_group::1). K advances in blocks of 64 BF16 (128 bytes): a TMA
-// thread stages the A and B tiles (128-byte swizzle) into a 4-deep shared-memory ring, one elected thread
-// issues tcgen05.mma into an FP32 accumulator in tensor memory and releases each stage with
-// tcgen05.commit, and all four warps read the accumulator back (tcgen05.ld) for the epilogue:
+// thread stages the A and B tiles (128-byte swizzle) into a shared-memory ring (4 stages, fewer when they
+// do not fit), one elected thread issues tcgen05.mma into an FP32 accumulator in tensor memory and
+// releases each stage with tcgen05.commit, and all four warps read the accumulator back (tcgen05.ld) for
+// the epilogue:
 //   - store (the noise product xi = beta alpha Lq W of Algorithm 1's batch update),
 //   - per-chain reduction of the target's log-likelihood terms (linear-map targets),
 //   - the FP64 moment fold of a lower-triangle SYRK (eq. (sampcov) as a pairwise centred update).
@@ -27,15 +28,19 @@ template <int BN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const __grid_constant__ CUtensorMap tmB2, int M, int N, int nkb,
-                                                         int a_lower, int has_b2, int kb_split, TcEpi epi, int* status) {
+                                                         int a_lower, int has_b2, int kb_split, int stages, TcEpi epi,
+                                                         int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
-    const uint32_t stage_bytes = A_BYTES + B_BYTES * (has_b2 ? 2u : 1u);
-    uint64_t* bars = (uint64_t*)(smem + TC_STAGES * stage_bytes);
+    // B2 up to 128 wide: both B tiles share a stage with one A tile; 256 wide: a second pass over K (two
+    // 256-row B tiles per stage would leave room for two stages only)
+    constexpr bool kext = BN == 256;
+    const uint32_t stage_bytes = A_BYTES + B_BYTES * ((has_b2 && !kext) ? 2u : 1u);
+    uint64_t* bars = (uint64_t*)(smem + stages * stage_bytes);
     uint64_t* full = bars;
-    uint64_t* empty = bars + TC_STAGES;
-    uint64_t* done = bars + 2 * TC_STAGES;
+    uint64_t* empty = bars + stages;
+    uint64_t* done = bars + 2 * stages;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -44,8 +49,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     if (epi.mode == TC_FOLD && n0 + BN - 1 < m0) return;  // every (n, m) of the tile has n < m
     if (epi.n_dev) N = min(N, *epi.n_dev);                // device-side row count of B (compacted rows)
     if (n0 >= N) return;                                  // uniform per CTA, before any barrier or TMEM use
-    int kb_end = nkb;
-    if (a_lower) kb_end = min(nkb, (m0 + TC_BM + TC_BK - 1) / TC_BK);
+    // K blocks of A this tile needs (a_lower: none past the tile's last row); with B2 the loop runs over them
+    // twice, the second pass pairing A's block with B2's
+    const int cap = a_lower ? min(nkb, (m0 + TC_BM + TC_BK - 1) / TC_BK) : nkb;
+    int kb_end = (has_b2 && kext) ? 2 * cap : cap;
     // split K (grid z): this CTA sums K blocks [kb_begin, kb_end) into its own partial plane
     int kb_begin = 0;
     if (kb_split > 0) {
@@ -56,7 +63,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < stages; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
@@ -80,21 +87,23 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         int issued = 0;
         for (int it = 0; it < nk; ++it) {
             const int kb = kb_begin + it;
-            const int s = it % TC_STAGES;
-            if (it >= TC_STAGES && !mbar_wait(smem_u32(&empty[s]), ((it / TC_STAGES) & 1) ^ 1, abort_flag)) break;
+            const int s = it % stages;
+            if (it >= stages && !mbar_wait(smem_u32(&empty[s]), ((it / stages) & 1) ^ 1, abort_flag)) break;
             uint8_t* st = smem + s * stage_bytes;
             const uint32_t fb = smem_u32(&full[s]);
+            const bool second = kb >= cap;
+            const int ka = second ? kb - cap : kb;
             mbar_expect_tx(fb, stage_bytes);
-            tma_load_2d(smem_u32(st), &tmA, fb, kb * TC_BK, m0);
-            tma_load_2d(smem_u32(st + A_BYTES), &tmB, fb, kb * TC_BK, n0);
-            if (has_b2) tma_load_2d(smem_u32(st + A_BYTES + B_BYTES), &tmB2, fb, kb * TC_BK, n0);
+            tma_load_2d(smem_u32(st), &tmA, fb, ka * TC_BK, m0);
+            tma_load_2d(smem_u32(st + A_BYTES), second ? &tmB2 : &tmB, fb, ka * TC_BK, n0);
+            if (has_b2 && !kext) tma_load_2d(smem_u32(st + A_BYTES + B_BYTES), &tmB2, fb, ka * TC_BK, n0);
             issued = it + 1;
         }
         if (*abort_flag) {
             // drain: every issued stage must land before the CTA may exit
-            for (int kb = max(0, issued - TC_STAGES); kb < issued; ++kb) {
+            for (int kb = max(0, issued - stages); kb < issued; ++kb) {
                 long long t0 = clock64();
-                while (!mbar_try(smem_u32(&full[kb % TC_STAGES]), (kb / TC_STAGES) & 1) && clock64() - t0 < TC_WAIT_CYCLES) {
+                while (!mbar_try(smem_u32(&full[kb % stages]), (kb / stages) & 1) && clock64() - t0 < TC_WAIT_CYCLES) {
                 }
             }
         }
@@ -102,8 +111,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         // MMA issuer
         constexpr uint32_t idesc = idesc_bf16(BN);
         for (int it = 0; it < nk; ++it) {
-            const int s = it % TC_STAGES;
-            if (!mbar_wait(smem_u32(&full[s]), (it / TC_STAGES) & 1, abort_flag)) break;
+            const int s = it % stages;
+            if (!mbar_wait(smem_u32(&full[s]), (it / stages) & 1, abort_flag)) break;
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + s * stage_bytes);
             const uint32_t sb = sa + A_BYTES;
@@ -111,7 +120,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
                 const uint64_t ad = sdesc_sw128(sa + kk * 32);
                 umma_bf16(tmem, ad, sdesc_sw128(sb + kk * 32), idesc, (it | kk) ? 1u : 0u);
-                if (has_b2) umma_bf16(tmem, ad, sdesc_sw128(sb + B_BYTES + kk * 32), idesc, 1u);
+                if (has_b2 && !kext) umma_bf16(tmem, ad, sdesc_sw128(sb + B_BYTES + kk * 32), idesc, 1u);
             }
             umma_commit(smem_u32(&empty[s]));
         }
@@ -243,8 +252,11 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
         !make_map(&mB2, B2 ? B2 : B, N, ldb, BN))
         return cudaErrorInvalidValue;
     const int has_b2 = B2 != nullptr;
-    const size_t stage = (size_t)TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2 * (has_b2 ? 2 : 1);
-    size_t smem = 1024 + TC_STAGES * stage + 256;
+    const bool kext = BN == 256;
+    const size_t stage = (size_t)TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2 * ((has_b2 && !kext) ? 2 : 1);
+    // 4 stages where they fit (measured: deeper rings only add L2 traffic in flight at the same rate)
+    const int stages = (int)std::min<size_t>(TC_MAX_STAGES, (227 * 1024 - 1024 - 256) / stage);
+    size_t smem = 1024 + stages * stage + 256;
     const size_t red = (size_t)TC_BM * (BN + 1) * 4;
     if (smem < 1024 + red + 256) smem = 1024 + red + 256;
     static bool attr_set = false;
@@ -253,16 +265,16 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int nkb = K / TC_BK;
+    const int nkb = K / TC_BK, ktot = (has_b2 && kext) ? 2 * nkb : nkb;
     int kb_split = 0;
     if (splits > 1) {
-        kb_split = (nkb + splits - 1) / splits;
-        splits = (nkb + kb_split - 1) / kb_split;   // every split gets at least one K block
+        kb_split = (ktot + splits - 1) / splits;
+        splits = (ktot + kb_split - 1) / kb_split;   // every split gets at least one K block
     } else {
         splits = 1;
     }
     dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN, splits);
-    { tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, M, N, nkb, a_lower, has_b2, kb_split, epi, status); count_launch(); }
+    { tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, M, N, nkb, a_lower, has_b2, kb_split, stages, epi, status); count_launch(); }
     return cudaGetLastError();
 }
 
@@ -272,6 +284,7 @@ static cudaError_t launch_any(int bn, int M, int N, int K, const uint16_t* A, in
     switch (bn) {
         case 32: return launch_bn<32>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
         case 64: return launch_bn<64>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
+        case 256: return launch_bn<256>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
         default: return launch_bn<128>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
     }
 }
@@ -295,10 +308,10 @@ cudaError_t tc_gemm_bf16_splitk(int M, int N, int K, const uint16_t* A, int lda,
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (epi.mode != TC_STORE || splits < 1) return cudaErrorInvalidValue;
     if (!args_ok(K, lda, ldb, A, B, B2)) return cudaErrorInvalidValue;
-    const int nkb = K / TC_BK;
-    splits = std::min(splits, nkb);
-    const int per = (nkb + splits - 1) / splits;
-    *used = (nkb + per - 1) / per;
+    const int ktot = (K / TC_BK) * ((B2 && bn == 256) ? 2 : 1);
+    splits = std::min(splits, ktot);
+    const int per = (ktot + splits - 1) / splits;
+    *used = (ktot + per - 1) / per;
     return launch_any(bn, M, N, K, A, lda, B, B2, ldb, 0, epi, status_dev, st, *used);
 }
 
@@ -325,7 +338,7 @@ int tc_autotune(int M, int N, int K, const uint16_t* A, int lda, const uint16_t*
         cudaEventDestroy(e0);
         return best;
     }
-    for (int bn : {32, 64, 128}) {
+    for (int bn : {32, 64, 128, 256}) {
         if (bn > 32 && N <= bn / 2) continue;   // a tile at least twice as wide as N only wastes MMA work
         int used = 1;
         auto go = [&]() {

@@ -48,7 +48,7 @@ struct TcEpi {
 
 // a_lower: A is lower triangular (A[m][k] = 0 for k > m), K blocks past the m-tile are skipped.
 // status_dev: receives a non-zero code if a bounded wait inside the kernel expired.
-// bn: tile width over N (32, 64 or 128; see tc_autotune)
+// bn: tile width over N (32, 64, 128 or 256; see tc_autotune).
 cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
                          int ldb, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st, int bn = 128);
 

@@ -31,7 +31,7 @@ def _gemm(M, N, K, A, B, B2=None, a_lower=0, scale=1.0, bn=128):
     return D
 
 
-@pytest.mark.parametrize("bn", [32, 64, 128])
+@pytest.mark.parametrize("bn", [32, 64, 128, 256])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 192), (130, 257, 128), (256, 32, 4096)])
 def test_tc_gemm_matches_torch(M, N, K, bn):
     import torch
@@ -137,3 +137,23 @@ def test_multi_problem_run_equals_each_problem_alone():
         s.close()
     assert all(v.stats()["n"] == 16 * 4 * 8 for v in m.views)   # every problem folded its four intervals
     m.close()
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_initial_log_density_after_upload(prec):
+    """log pi of the starting states, for several samplers created one after another in one process (each
+    reuses freed device memory): the target's arrays reach the device before the first kernel that reads them
+    (every copy is ordered on the sampler's stream)."""
+    import paper_1506_05741_b300 as dm
+    d, dy, P = 2048, 1024, 64
+    ts = workloads.tanh_regression(d, dy, 77)
+    x0 = workloads.start_state(d, P, 3) * np.sqrt(ts.lam)
+    A = oracle.round_bf16(ts.A) if prec == 2 else ts.A
+    X = x0.astype(np.float32).astype(np.float64) if prec == 2 else x0
+    want = -0.5 * np.sum(X * X / ts.lam, axis=1) - np.sum((ts.y - np.tanh(X @ A.T)) ** 2, axis=1) / (2 * ts.sigma ** 2)
+    tol = 1e-5 if prec == 2 else 1e-12
+    for _ in range(3):
+        s = dm.Sampler(dm.default_config(d, P, n_lag=16, prec=prec), ts, x0=x0, C0=np.diag(ts.lam))
+        lp = s.log_pi()
+        s.close()
+        assert np.max(np.abs(lp - want) / np.abs(want)) <= tol
