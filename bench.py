@@ -132,6 +132,17 @@ def make_sampler(run, ts, x0, C0, prec, da=False, profile=0, stream=None, keep_s
     return s
 
 
+def rank_max(x, world, device):
+    """Max of x over the ranks (timings: the slowest replica sets the whole job's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def time_intervals(s, n_lag, K, torch, stream):
     """Device time of K intervals with CUDA events on the sampler's stream (synchronised on both sides)."""
     torch.cuda.synchronize()
@@ -302,10 +313,7 @@ def main():
         torch.distributed.barrier()
     head, dt, launches, clk = run_arm("mixed_da" if da else "mixed", run, ts, x0, C0, dm.BF16, da, args.warmup,
                                       args.steps, torch, stream, dm, clocks_index=local)
-    if world > 1:
-        t = torch.tensor([dt], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = t.item()
+    dt = rank_max(dt, world, "cuda")
     value = world * N * args.steps / dt
     arms = {("mixed_da" if da else "mixed"): head}
 

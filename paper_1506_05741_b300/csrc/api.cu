@@ -20,6 +20,7 @@
 #include "gemm_f64.cuh"
 #include "linalg.h"
 #include "step.cuh"
+#include "rec.cuh"
 #include "tc_gemm.h"
 
 using namespace diam;
@@ -54,6 +55,11 @@ struct diam_ctx {
     bool own_stream = false;
     cudaStream_t side = nullptr;                 // overlaps the interval's noise product with the re-solve
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the refresh's factorisation and the re-solve of z, captured once (fixed buffers) and replayed
+    struct Captured {
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long launches = 0;
+    } chol_graph, trsm_graph;
     std::string err;
     bool bad = false;
     diam_logpi_fn fn = nullptr;
@@ -92,6 +98,12 @@ struct diam_ctx {
     // target
     double *inv_lam = nullptr, *Gm = nullptr, *y = nullptr;
     float *inv_lam32 = nullptr, *y32 = nullptr;   // FP32 copies for the BF16-mode kernels
+    // the linear map carried through the proposal (BF16 mode, linear-map targets): M = A Lq as BF16 hi + lo,
+    // A x of the states and of the proposals, A x_ref, the interval's products M W (scaled by beta alpha)
+    bool rec = false, ax_dirty = true;
+    uint16_t *Lt16 = nullptr, *ALh = nullptr, *ALl = nullptr;
+    float *ALf = nullptr, *AXi = nullptr, *Ax = nullptr, *Axp = nullptr, *axref = nullptr;
+    double* lmap = nullptr;
     uint16_t* Gq16 = nullptr;
     TargetDev tg{};
     // trace and interval sums
@@ -259,11 +271,19 @@ template <typename T>
 static diam_status rewhiten(diam_ctx* c) {
     const int d = c->d, P = c->P;
     int e0 = ph_begin(c, PH_REWHITEN);
-    { diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, (const T*)c->X, (const T*)c->xref, c->work); count_launch(); }
-    CK(trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status));
-    { set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)c->Z, c->q, inv_infl2(c),
-                                                c->kind == TK_REF ? c->lp : nullptr); count_launch(); }
-    CK(cudaGetLastError());
+    auto body = [&]() -> cudaError_t {
+        { diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, (const T*)c->X, (const T*)c->xref, c->work); count_launch(); }
+        cudaError_t e = trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status);
+        if (e != cudaSuccess) return e;
+        { set_z_kernel<T><<<P, kThreads, 0, c->st>>>(d, c->work, (T*)c->Z, c->q, inv_infl2(c),
+                                                    c->kind == TK_REF ? c->lp : nullptr); count_launch(); }
+        return cudaGetLastError();
+    };
+    if (c->bf && c->cfg.graphs && !c->cfg.profile && c->oz.hi) {   // after a first eager re-solve
+        CKS(run_captured(c, c->trsm_graph, body));
+    } else {
+        CK(body());
+    }
     ph_end(c, e0);
     return DIAM_OK;
 }
@@ -289,6 +309,42 @@ static diam_status quantise(diam_ctx* c) {
     return DIAM_OK;
 }
 
+// M = A Lq for a new factor (FP32 on the tensor cores: A Lq[m][j] = sum_k A[m][k] Lq[k][j] through Lq's
+// transpose), kept as BF16 hi + lo; and A x_ref for the current x_ref.
+static diam_status rec_factor(diam_ctx* c) {
+    if (!c->rec) return DIAM_OK;
+    const int ldk = c->ldk;
+    { transpose_bf16_kernel<<<dim3(ldk / 32, ldk / 32), dim3(32, 8), 0, c->st>>>(c->Lq16, ldk, c->d, ldk, c->Lt16, ldk); count_launch(); }
+    TcEpi epi{};
+    epi.mode = TC_STORE;
+    epi.D = c->ALf;
+    epi.ldd = ldk;
+    CK(tc_gemm_bf16(c->d, c->dy, ldk, c->Lt16, ldk, c->Gq16, nullptr, ldk, 0, epi, &c->ctl->status, c->st, 256));
+    { split_hi_lo_kernel<<<dim3(blocks_for(ldk), c->dy), kThreads, 0, c->st>>>(c->dy, ldk, ldk, c->ALf, c->ALh, c->ALl); count_launch(); }
+    CK(cudaGetLastError());
+    return DIAM_OK;
+}
+
+static diam_status rec_xref(diam_ctx* c) {
+    if (!c->rec) return DIAM_OK;
+    { axref_kernel<<<c->dy, kThreads, 0, c->st>>>(c->d, c->ldk, c->Gq16, (const float*)c->xref, c->axref); count_launch(); }
+    CK(cudaGetLastError());
+    return DIAM_OK;
+}
+
+// A x of the current states, exactly (hi + lo split of x, as for log pi), at an interval start.
+static diam_status rec_ax(diam_ctx* c) {
+    if (!c->rec) return DIAM_OK;
+    { od_terms_kernel<float><<<c->P, kThreads, 0, c->st>>>(c->d, (const float*)c->X, c->lpo, c->tg, c->op_hi, c->op_lo, c->ldk); count_launch(); }
+    TcEpi epi{};
+    epi.mode = TC_STORE;
+    epi.D = c->Ax;
+    epi.ldd = c->dy;
+    CK(tc_gemm_bf16(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, 0, epi, &c->ctl->status, c->st));
+    c->ax_dirty = false;
+    return DIAM_OK;
+}
+
 template <typename T>
 static diam_status prepare_block(diam_ctx* c, int64_t blk, cudaStream_t st);
 
@@ -299,6 +355,8 @@ static diam_status block_begin(diam_ctx* c, int64_t blk) {
         CK(cudaMemcpyAsync(c->L, pd.L, sizeof(double) * c->d * c->d, cudaMemcpyDeviceToDevice, c->st));
         CKS(quantise(c));
         if (c->cfg.xref_mode == 1) set_xref_from(c, pd.mean);
+        CKS(rec_factor(c));
+        CKS(rec_xref(c));
         // the interval's noise and noise product need only the new quantised factor, z's re-solve needs the
         // states: with the side stream they run side by side (the steps wait for both)
         const bool overlap = c->side && !c->cfg.profile && c->xi_block != blk;
@@ -334,6 +392,15 @@ static diam_status prepare_block(diam_ctx* c, int64_t blk, cudaStream_t st) {
         epi.scale_dev = &c->ctl->ba;
         CK(tc_gemm_bf16(d, (int)rows, c->ldk, c->Lq16, c->ldk, (const uint16_t*)c->W, nullptr, c->ldw, 1, epi,
                         &c->ctl->status, st, c->bn_xi));
+        if (c->rec) {   // the map of every step's noise product: beta alpha (A Lq) W, in one GEMM
+            TcEpi em{};
+            em.mode = TC_STORE;
+            em.D = c->AXi;
+            em.ldd = c->dy;
+            em.scale_dev = &c->ctl->ba;
+            CK(tc_gemm_bf16_a2(c->dy, (int)rows, c->ldk, c->ALh, c->ALl, c->ldk, (const uint16_t*)c->W, c->ldw, 0, em,
+                               &c->ctl->status, st, 256));
+        }
         ph_end(c, e1);
     } else {
         int e0 = ph_begin(c, PH_NOISE);
@@ -380,9 +447,11 @@ static diam_status do_step(diam_ctx* c) {
     int e0 = ph_begin(c, PH_PROPOSE);
     if constexpr (BF) {
         const uint16_t* Ws = (const uint16_t*)c->W;
+        const bool planes = !c->rec || c->da;   // x* as BF16 hi + lo for a per-step target product or the ring
         { propose_kernel<T, uint16_t><<<grid2, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
                                                                (const T*)c->xref, (T*)c->Xp, (T*)c->Zp, c->qpart, c->lpart,
-                                                               c->ctl, c->tg, c->op_hi, c->op_lo, c->ldk); count_launch(); }
+                                                               c->ctl, c->tg, planes ? c->op_hi : nullptr,
+                                                               planes ? c->op_lo : nullptr, c->ldk); count_launch(); }
     } else {
         const T* Ws = (const T*)c->W;
         { propose_kernel<T, T><<<grid2, kThreads, 0, c->st>>>(d, P, (const T*)c->X, (const T*)c->Z, Xi, Ws, c->ldw,
@@ -402,6 +471,12 @@ static diam_status do_step(diam_ctx* c) {
         if constexpr (BF) {
           if (c->da) {
             CKS(da_step(c));
+          } else if (c->rec) {
+            { rec_map_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, c->ctl, c->Ax, c->axref, c->AXi, c->Axp, c->y32,
+                                                       (float)inv2s2, c->kind == TK_TANH, c->lmap); count_launch(); }
+            { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, c->qpart, c->lpart, c->lmap, 1,
+                                                                nullptr, iw, c->lp, c->q, c->accf, c->ctl, c->tr); count_launch(); }
+            { select_ax_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, c->accf, c->Ax, c->Axp); count_launch(); }
           } else {
             TcEpi epi{};
             epi.mode = TC_STORE;
@@ -498,6 +573,31 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
     return DIAM_OK;
 }
 
+// Replay of a captured launch sequence (captured on first use, on the context's stream, with the work it
+// forks onto other streams joined back); the library's launch counter counts the kernels of every replay.
+template <typename F>
+static diam_status run_captured(diam_ctx* c, diam_ctx::Captured& g, F body) {
+    if (!g.exec) {
+        cudaGraph_t gr = nullptr;
+        const unsigned long long l0 = g_launches.load();
+        CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t eb = body();
+        cudaError_t e = cudaStreamEndCapture(c->st, &gr);
+        if (eb != cudaSuccess || e != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            return fail(c, DIAM_ECUDA, "graph capture", cudaGetErrorString(eb != cudaSuccess ? eb : e));
+        }
+        cudaError_t ei = cudaGraphInstantiate(&g.exec, gr, 0);
+        cudaGraphDestroy(gr);
+        CK(ei);
+        g.launches = g_launches.load() - l0;
+        g_launches.fetch_sub(g.launches);
+    }
+    CK(cudaGraphLaunch(g.exec, c->st));
+    g_launches.fetch_add(g.launches);
+    return DIAM_OK;
+}
+
 // Cholesky refresh at the end of interval blk (skip / jitter rule, retries with a larger jitter).
 static diam_status refresh(diam_ctx* c, int64_t blk) {
     const int d = c->d;
@@ -513,7 +613,13 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
         // C_n + eps diag(C_n): every variance loaded by the same relative amount (the skip / jitter rule)
         { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, inv_n, eps, c->Cw); count_launch(); }
         CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
-        CK(cholesky_f64(c->Cw, d, d, &c->ctl->chol_info, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status));
+        if (c->bf && c->cfg.graphs && !c->cfg.profile && c->oz.hi) {   // after a first eager factorisation
+            CKS(run_captured(c, c->chol_graph, [&]() {
+                return cholesky_f64(c->Cw, d, d, &c->ctl->chol_info, c->st, &c->oz, &c->ctl->status);
+            }));
+        } else {
+            CK(cholesky_f64(c->Cw, d, d, &c->ctl->chol_info, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status));
+        }
         CKS(sync_and_check(c));
         int info = 0;
         CK(d2h(c, &info, &c->ctl->chol_info, sizeof(int)));
@@ -609,7 +715,9 @@ static diam_status run_steps(diam_ctx* c, int64_t n_steps) {
             CKS(block_begin<T>(c, blk));
             { centre_kernel<T><<<blocks_for(c->d), kThreads, 0, c->st>>>(c->d, c->P, (const T*)c->X, (T*)c->cenT, c->cen64); count_launch(); }
             c->begun_block = blk;
+            c->ax_dirty = true;   // A x recomputed exactly at every interval start
         }
+        if (c->rec && c->ax_dirty) CKS(rec_ax(c));
         if (c->xi_block != blk) CKS(prepare_block<T>(c, blk, c->st));
         CKS(ensure_bsum(c, blk));
         const bool whole = s == 0 && n_steps >= c->nl && c->cfg.graphs && c->kind != TK_CALLBACK && !c->cfg.profile;
@@ -688,6 +796,8 @@ static diam_status init_state(diam_ctx* c, const double* x0, const double* C0, c
         CK(cudaMemcpyAsync(tmp, xref0, sizeof(double) * d, cudaMemcpyHostToDevice, c->st));
         set_xref_from(c, tmp);
     }
+    CKS(rec_factor(c));
+    CKS(rec_xref(c));
     push_scalars(c);
     CKS(rewhiten<T>(c));
     if (c->kind != TK_REF) CKS(eval_lp<T>(c, (const T*)c->X, c->lp));
@@ -753,6 +863,20 @@ static diam_status alloc_all(diam_ctx* c) {
         CKS(dalloc(c, &c->W, sizeof(uint16_t) * rows * c->ldw));
         CKS(dalloc(c, &c->hist, sizeof(float) * rows * c->ldh));
         CKS(dalloc(c, &c->histT, sizeof(uint16_t) * (size_t)d * ((rows + 63) / 64 * 64)));
+        if (c->kind == TK_TANH || c->kind == TK_DENSE) {
+            c->rec = true;
+            const size_t dy = (size_t)std::max(c->dy, 1);
+            CKS(dalloc(c, &c->Lt16, sizeof(uint16_t) * (size_t)c->ldk * c->ldk));
+            CKS(dalloc(c, &c->ALf, sizeof(float) * dy * c->ldk));
+            CK(cudaMemsetAsync(c->ALf, 0, sizeof(float) * dy * c->ldk, c->st));   // padding columns stay zero
+            CKS(dalloc(c, &c->ALh, sizeof(uint16_t) * dy * c->ldk));
+            CKS(dalloc(c, &c->ALl, sizeof(uint16_t) * dy * c->ldk));
+            CKS(dalloc(c, &c->AXi, sizeof(float) * rows * dy));
+            CKS(dalloc(c, &c->Ax, sizeof(float) * (size_t)P * dy));
+            CKS(dalloc(c, &c->Axp, sizeof(float) * (size_t)P * dy));
+            CKS(dalloc(c, &c->axref, sizeof(float) * dy));
+            CKS(dalloc(c, &c->lmap, sizeof(double) * (size_t)P));
+        }
     } else {
         c->Lq64 = c->L;
         c->ldw = (d + 3) / 4 * 4;
@@ -1155,6 +1279,9 @@ diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
         c->graph = nullptr;
     }
     CKS(quantise(c));
+    CKS(rec_factor(c));
+    CKS(rec_xref(c));
+    c->ax_dirty = true;
     return sync_and_check(c);
 }
 
@@ -1307,6 +1434,8 @@ void diam_destroy(diam_ctx* c) {
         cudaEventDestroy(e.b);
     }
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->chol_graph.exec) cudaGraphExecDestroy(c->chol_graph.exec);
+    if (c->trsm_graph.exec) cudaGraphExecDestroy(c->trsm_graph.exec);
     ozaki_ws_release(c->oz);
     for (void* p : c->allocs) cudaFree(p);
     if (c->side) {

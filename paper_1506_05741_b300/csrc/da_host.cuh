@@ -196,7 +196,7 @@ static diam_status da_step(diam_ctx* c) {
     // stage 1 off: every chain passes in chain order, so the exact test reads the proposals' rows in place
     const uint16_t* bh = c->op_hi;
     const uint16_t* bl = c->op_lo;
-    if (a->active) {
+    if (a->active && !c->rec) {
         { gather_rows_kernel<<<P, kThreads, 0, c->st>>>(a->cnt, a->idx, c->op_hi, c->op_lo, a->Chi, a->Clo, c->ldk); count_launch(); }
         bh = a->Chi;
         bl = a->Clo;
@@ -204,19 +204,30 @@ static diam_status da_step(diam_ctx* c) {
     CK(cudaGetLastError());
     ph_end(c, e0);
     int e1 = ph_begin(c, PH_TARGET);
-    TcEpi epi{};
-    epi.mode = TC_STORE;
-    epi.D = c->ws;
-    epi.ldd = c->dy;
-    epi.split_stride = (size_t)P * c->dy;
-    epi.n_dev = &a->cnt->count;
-    int used = 1;
-    CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, bh, bl, c->ldk, c->tsplit, epi, &c->ctl->status,
-                           c->st, &used, c->bn_target));
-    { finish_da_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y32, (float)(1.0 / (2.0 * c->sigma * c->sigma)),
-                                                c->kind == TK_TANH, c->nchunk, c->key, c->lpart, a->qsave, a->idx, a->cnt,
-                                                a->active ? 1 : 0, a->s_prop, a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, bh, a->ring_x,
-                                                a->ring_lp, (long long)a->cfg.ring, c->ldk); count_launch(); }
+    const float inv2s2 = (float)(1.0 / (2.0 * c->sigma * c->sigma));
+    if (c->rec) {   // the map carried through the proposal: every chain's map terms at O(d_y) cost
+        { rec_map_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, c->ctl, c->Ax, c->axref, c->AXi, c->Axp, c->y32, inv2s2,
+                                                   c->kind == TK_TANH, c->lmap); count_launch(); }
+        { finish_da_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, 0, nullptr, c->y32, inv2s2, c->kind == TK_TANH, c->nchunk,
+                                                    c->key, c->lpart, a->qsave, a->idx, a->cnt, a->active ? 1 : 0, a->s_prop,
+                                                    a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, c->op_hi, a->ring_x,
+                                                    a->ring_lp, (long long)a->cfg.ring, c->ldk, c->lmap); count_launch(); }
+        { select_ax_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, c->accf, c->Ax, c->Axp); count_launch(); }
+    } else {
+        TcEpi epi{};
+        epi.mode = TC_STORE;
+        epi.D = c->ws;
+        epi.ldd = c->dy;
+        epi.split_stride = (size_t)P * c->dy;
+        epi.n_dev = &a->cnt->count;
+        int used = 1;
+        CK(tc_gemm_bf16_splitk(c->dy, P, c->ldk, c->Gq16, c->ldk, bh, bl, c->ldk, c->tsplit, epi, &c->ctl->status,
+                               c->st, &used, c->bn_target));
+        { finish_da_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, used, c->ws, c->y32, inv2s2, c->kind == TK_TANH, c->nchunk,
+                                                    c->key, c->lpart, a->qsave, a->idx, a->cnt, a->active ? 1 : 0, a->s_prop,
+                                                    a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, bh, a->ring_x,
+                                                    a->ring_lp, (long long)a->cfg.ring, c->ldk); count_launch(); }
+    }
     { ring_advance_kernel<<<1, 1, 0, c->st>>>(a->cnt, (long long)a->cfg.ring); count_launch(); }
     CK(cudaGetLastError());
     ph_end(c, e1);

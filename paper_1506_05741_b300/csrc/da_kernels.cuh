@@ -136,29 +136,36 @@ __global__ void __launch_bounds__(256) finish_da_kernel(int P, int dy, int nspli
                                                          double* s_cur, double* lp, double* q, int8_t* accf, Ctl* ctl,
                                                          TraceDev tr, const uint16_t* __restrict__ chi,
                                                          uint16_t* __restrict__ ring_x, float* __restrict__ ring_lp,
-                                                         long long ring_cap, int ldk) {
+                                                         long long ring_cap, int ldk,
+                                                         const double* __restrict__ lmap_in = nullptr) {
     __shared__ float shf[32];
     const int k = blockIdx.x;
     if (k >= cnt->count) return;
     const int p = idx[k];
     const int64_t t = ctl->t_cur;
     const size_t plane = (size_t)P * dy;
-    float af = 0.f;   // the linear-map terms in FP32, as in the plain exact test
-    for (int m = threadIdx.x; m < dy; m += blockDim.x) {
-        float u = 0.f;
-        for (int s = 0; s < nsplit; ++s) u += ws[s * plane + (size_t)k * dy + m];
-        if (tanh_mode) {
-            const float r = y32[m] - tanhf(u);
-            af -= r * r * inv2s2;
-        } else {
-            af -= 0.5f * u * u;
+    double acc;
+    if (lmap_in) {   // the map terms already computed for every chain (map carried through the proposal)
+        acc = lmap_in[p];
+    } else {
+        float af = 0.f;   // the linear-map terms in FP32, as in the plain exact test
+        for (int m = threadIdx.x; m < dy; m += blockDim.x) {
+            float u = 0.f;
+            for (int s = 0; s < nsplit; ++s) u += ws[s * plane + (size_t)k * dy + m];
+            if (tanh_mode) {
+                const float r = y32[m] - tanhf(u);
+                af -= r * r * inv2s2;
+            } else {
+                af -= 0.5f * u * u;
+            }
         }
+        acc = (double)block_sum(af, shf);
     }
-    double acc = (double)block_sum(af, shf);
     const double lmap = acc;   // the linear-map part of log pi(x*): what the network learns
     for (int c = 0; c < nchunk; ++c) acc += lpart[(size_t)c * P + p];
     const long long slot = (cnt->head + k) % ring_cap;
-    const uint4* src = reinterpret_cast<const uint4*>(chi + (size_t)k * ldk);
+    // chi: the survivors' rows in compacted order, or (lmap_in given) every proposal's row in chain order
+    const uint4* src = reinterpret_cast<const uint4*>(chi + (size_t)(lmap_in ? p : k) * ldk);
     uint4* dst = reinterpret_cast<uint4*>(ring_x + (size_t)slot * ldk);
     for (int j = threadIdx.x; j < ldk / 8; j += blockDim.x) dst[j] = src[j];
     if (threadIdx.x == 0) {

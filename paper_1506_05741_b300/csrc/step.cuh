@@ -295,9 +295,8 @@ __global__ void finish_kernel(int P, int nchunk, Key key, const double* __restri
 
 // One block per chain, for a linear-map target computed as split-K FP32 partial products ws[s][p][m]
 // (m < d_y): u_m = sum_s ws (fixed order), log-likelihood -(y_m - tanh u_m)^2 inv2s2 or -u_m^2 / 2, summed
-// in FP64; then the O(d) partials, q(x*) and the decision.
-// The linear-map terms in FP32 (FP32 products and sums over d_y; relative error ~1e-6 of the sum, inside
-// the BF16-mode bounds), the O(d) partials and the quadratic in FP64.
+// in FP32 (relative error ~1e-6 of the sum, inside the BF16-mode bounds); then the O(d) partials and q(x*)
+// in FP64, and the decision.
 __global__ void __launch_bounds__(256) finish_linear_kernel(int P, int dy, int nsplit, const float* __restrict__ ws,
                                                              const float* __restrict__ y32, float inv2s2, int tanh_mode,
                                                              int nchunk, Key key,

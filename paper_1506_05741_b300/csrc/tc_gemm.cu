@@ -27,16 +27,19 @@ namespace diam {
 template <int BN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
-                                                         const __grid_constant__ CUtensorMap tmB2, int M, int N, int nkb,
-                                                         int a_lower, int has_b2, int kb_split, int stages, TcEpi epi,
-                                                         int* status) {
+                                                         const __grid_constant__ CUtensorMap tmB2,
+                                                         const __grid_constant__ CUtensorMap tmA2, int M, int N, int nkb,
+                                                         int a_lower, int has_b2, int has_a2, int kb_split, int stages,
+                                                         TcEpi epi, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
     // B2 up to 128 wide: both B tiles share a stage with one A tile; 256 wide: a second pass over K (two
-    // 256-row B tiles per stage would leave room for two stages only)
+    // 256-row B tiles per stage would leave room for two stages only). A2: always a second pass (A2 with B).
     constexpr bool kext = BN == 256;
-    const uint32_t stage_bytes = A_BYTES + B_BYTES * ((has_b2 && !kext) ? 2u : 1u);
+    const bool inst_b2 = has_b2 && !kext && !has_a2;
+    const bool two_pass = (has_b2 && !inst_b2) || has_a2;
+    const uint32_t stage_bytes = A_BYTES + B_BYTES * (inst_b2 ? 2u : 1u);
     uint64_t* bars = (uint64_t*)(smem + stages * stage_bytes);
     uint64_t* full = bars;
     uint64_t* empty = bars + stages;
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     // K blocks of A this tile needs (a_lower: none past the tile's last row); with B2 the loop runs over them
     // twice, the second pass pairing A's block with B2's
     const int cap = a_lower ? min(nkb, (m0 + TC_BM + TC_BK - 1) / TC_BK) : nkb;
-    int kb_end = (has_b2 && kext) ? 2 * cap : cap;
+    int kb_end = two_pass ? 2 * cap : cap;
     // split K (grid z): this CTA sums K blocks [kb_begin, kb_end) into its own partial plane
     int kb_begin = 0;
     if (kb_split > 0) {
@@ -94,9 +97,9 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
             const bool second = kb >= cap;
             const int ka = second ? kb - cap : kb;
             mbar_expect_tx(fb, stage_bytes);
-            tma_load_2d(smem_u32(st), &tmA, fb, ka * TC_BK, m0);
-            tma_load_2d(smem_u32(st + A_BYTES), second ? &tmB2 : &tmB, fb, ka * TC_BK, n0);
-            if (has_b2 && !kext) tma_load_2d(smem_u32(st + A_BYTES + B_BYTES), &tmB2, fb, ka * TC_BK, n0);
+            tma_load_2d(smem_u32(st), (second && has_a2) ? &tmA2 : &tmA, fb, ka * TC_BK, m0);
+            tma_load_2d(smem_u32(st + A_BYTES), (second && has_b2) ? &tmB2 : &tmB, fb, ka * TC_BK, n0);
+            if (inst_b2) tma_load_2d(smem_u32(st + A_BYTES + B_BYTES), &tmB2, fb, ka * TC_BK, n0);
             issued = it + 1;
         }
         if (*abort_flag) {
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
                 const uint64_t ad = sdesc_sw128(sa + kk * 32);
                 umma_bf16(tmem, ad, sdesc_sw128(sb + kk * 32), idesc, (it | kk) ? 1u : 0u);
-                if (has_b2 && !kext) umma_bf16(tmem, ad, sdesc_sw128(sb + B_BYTES + kk * 32), idesc, 1u);
+                if (inst_b2) umma_bf16(tmem, ad, sdesc_sw128(sb + B_BYTES + kk * 32), idesc, 1u);
             }
             umma_commit(smem_u32(&empty[s]));
         }
@@ -246,14 +249,17 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int ld, int box_rows)
 
 template <int BN>
 static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
-                             int ldb, int a_lower, const TcEpi& epi, int* status, cudaStream_t st, int splits = 1) {
-    CUtensorMap mA, mB, mB2;
+                             int ldb, int a_lower, const TcEpi& epi, int* status, cudaStream_t st, int splits = 1,
+                             const uint16_t* A2 = nullptr) {
+    CUtensorMap mA, mB, mB2, mA2;
+    if (B2 && A2) return cudaErrorInvalidValue;
     if (!make_map(&mA, A, M, lda, TC_BM) || !make_map(&mB, B, N, ldb, BN) ||
-        !make_map(&mB2, B2 ? B2 : B, N, ldb, BN))
+        !make_map(&mB2, B2 ? B2 : B, N, ldb, BN) || !make_map(&mA2, A2 ? A2 : A, M, lda, TC_BM))
         return cudaErrorInvalidValue;
-    const int has_b2 = B2 != nullptr;
+    const int has_b2 = B2 != nullptr, has_a2 = A2 != nullptr;
     const bool kext = BN == 256;
-    const size_t stage = (size_t)TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2 * ((has_b2 && !kext) ? 2 : 1);
+    const bool inst_b2 = has_b2 && !kext && !has_a2, two_pass = (has_b2 && !inst_b2) || has_a2;
+    const size_t stage = (size_t)TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2 * (inst_b2 ? 2 : 1);
     // 4 stages where they fit (measured: deeper rings only add L2 traffic in flight at the same rate)
     const int stages = (int)std::min<size_t>(TC_MAX_STAGES, (227 * 1024 - 1024 - 256) / stage);
     size_t smem = 1024 + stages * stage + 256;
@@ -265,7 +271,7 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int nkb = K / TC_BK, ktot = (has_b2 && kext) ? 2 * nkb : nkb;
+    const int nkb = K / TC_BK, ktot = two_pass ? 2 * nkb : nkb;
     int kb_split = 0;
     if (splits > 1) {
         kb_split = (ktot + splits - 1) / splits;
@@ -274,18 +280,19 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
         splits = 1;
     }
     dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN, splits);
-    { tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, M, N, nkb, a_lower, has_b2, kb_split, stages, epi, status); count_launch(); }
+    { tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, mA2, M, N, nkb, a_lower, has_b2, has_a2, kb_split, stages,
+                                                  epi, status); count_launch(); }
     return cudaGetLastError();
 }
 
 static cudaError_t launch_any(int bn, int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B,
                               const uint16_t* B2, int ldb, int a_lower, const TcEpi& epi, int* status, cudaStream_t st,
-                              int splits) {
+                              int splits, const uint16_t* A2 = nullptr) {
     switch (bn) {
-        case 32: return launch_bn<32>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
-        case 64: return launch_bn<64>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
-        case 256: return launch_bn<256>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
-        default: return launch_bn<128>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits);
+        case 32: return launch_bn<32>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits, A2);
+        case 64: return launch_bn<64>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits, A2);
+        case 256: return launch_bn<256>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits, A2);
+        default: return launch_bn<128>(M, N, K, A, lda, B, B2, ldb, a_lower, epi, status, st, splits, A2);
     }
 }
 
@@ -299,6 +306,13 @@ cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const 
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (!args_ok(K, lda, ldb, A, B, B2)) return cudaErrorInvalidValue;
     return launch_any(bn, M, N, K, A, lda, B, B2, ldb, a_lower, epi, status_dev, st, 1);
+}
+
+cudaError_t tc_gemm_bf16_a2(int M, int N, int K, const uint16_t* A, const uint16_t* A2, int lda, const uint16_t* B,
+                            int ldb, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st, int bn) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (!A2 || (((uintptr_t)A2) & 15) || !args_ok(K, lda, ldb, A, B, nullptr)) return cudaErrorInvalidValue;
+    return launch_any(bn, M, N, K, A, lda, B, nullptr, ldb, a_lower, epi, status_dev, st, 1, A2);
 }
 
 // Split-K form: K blocks divided over `splits` CTAs per tile; each writes its FP32 partial product to

@@ -52,6 +52,11 @@ struct TcEpi {
 cudaError_t tc_gemm_bf16(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
                          int ldb, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st, int bn = 128);
 
+// D = op(A + A2, B): the product with a second A operand (same layout as A) summed in, as a second pass over
+// K (A2 with B). No B2.
+cudaError_t tc_gemm_bf16_a2(int M, int N, int K, const uint16_t* A, const uint16_t* A2, int lda, const uint16_t* B,
+                            int ldb, int a_lower, const TcEpi& epi, int* status_dev, cudaStream_t st, int bn = 128);
+
 // Split-K TC_STORE: grid z = splits, K blocks divided evenly; *used receives the number of partial planes.
 cudaError_t tc_gemm_bf16_splitk(int M, int N, int K, const uint16_t* A, int lda, const uint16_t* B, const uint16_t* B2,
                                 int ldb, int splits, const TcEpi& epi, int* status_dev, cudaStream_t st, int* used,
