@@ -476,7 +476,6 @@ static diam_status do_step(diam_ctx* c) {
                                                        (float)inv2s2, c->kind == TK_TANH, c->lmap); count_launch(); }
             { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, c->qpart, c->lpart, c->lmap, 1,
                                                                 nullptr, iw, c->lp, c->q, c->accf, c->ctl, c->tr); count_launch(); }
-            { select_ax_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, c->accf, c->Ax, c->Axp); count_launch(); }
           } else {
             TcEpi epi{};
             epi.mode = TC_STORE;
@@ -506,16 +505,21 @@ static diam_status do_step(diam_ctx* c) {
     int e2 = ph_begin(c, PH_ACCEPT);
     void* bs = c->cfg.keep_block_sums ? c->bsum : nullptr;
     double* ls = c->cfg.keep_block_sums ? c->lpsum : nullptr;
+    // the select kernel also copies A x* for accepted chains (carried map), moves the surrogate's ring head
+    // past this step's pairs and, in its last block, the step counters
+    DaCounters* dac = c->da ? c->da->cnt : nullptr;
+    const long long rcap = c->da ? (long long)c->da->cfg.ring : 1;
     if constexpr (BF) {
         { select_kernel<T, float><<<grid2, kThreads, 0, c->st>>>(d, P, c->nl, c->ctl, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
                                                                 (const T*)c->Zp, (float*)c->hist, c->ldh, (const T*)c->cenT,
-                                                                (float*)bs, ls, c->lp); count_launch(); }
+                                                                (float*)bs, ls, c->lp, c->rec ? c->Ax : nullptr, c->Axp,
+                                                                c->dy, dac, rcap); count_launch(); }
     } else {
         { select_kernel<T, double><<<grid2, kThreads, 0, c->st>>>(d, P, c->nl, c->ctl, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
                                                                  (const T*)c->Zp, (double*)c->hist, c->ldh, (const T*)c->cenT,
-                                                                 (double*)bs, ls, c->lp); count_launch(); }
+                                                                 (double*)bs, ls, c->lp, nullptr, nullptr, 0, dac,
+                                                                 rcap); count_launch(); }
     }
-    { advance_kernel<<<1, 1, 0, c->st>>>(c->ctl); count_launch(); }
     CK(cudaGetLastError());
     ph_end(c, e2);
     return DIAM_OK;
@@ -781,7 +785,7 @@ static diam_status init_state(diam_ctx* c, const double* x0, const double* C0, c
     if (C0) {
         CK(cudaMemcpyAsync(c->L, C0, sizeof(double) * d * d, cudaMemcpyHostToDevice, c->st));
         CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
-        CK(cholesky_f64(c->L, d, d, &c->ctl->chol_info, c->st));
+        CK(cholesky_f64(c->L, d, d, &c->ctl->chol_info, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status));
         CKS(sync_and_check(c));
         int info = 0;
         CK(d2h(c, &info, &c->ctl->chol_info, sizeof(int)));

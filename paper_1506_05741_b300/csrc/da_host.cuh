@@ -212,7 +212,6 @@ static diam_status da_step(diam_ctx* c) {
                                                     c->key, c->lpart, a->qsave, a->idx, a->cnt, a->active ? 1 : 0, a->s_prop,
                                                     a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, c->op_hi, a->ring_x,
                                                     a->ring_lp, (long long)a->cfg.ring, c->ldk, c->lmap); count_launch(); }
-        { select_ax_kernel<<<P, kThreads, 0, c->st>>>(P, c->dy, c->accf, c->Ax, c->Axp); count_launch(); }
     } else {
         TcEpi epi{};
         epi.mode = TC_STORE;
@@ -228,7 +227,6 @@ static diam_status da_step(diam_ctx* c) {
                                                     a->s_cur, c->lp, c->q, c->accf, c->ctl, c->tr, bh, a->ring_x,
                                                     a->ring_lp, (long long)a->cfg.ring, c->ldk); count_launch(); }
     }
-    { ring_advance_kernel<<<1, 1, 0, c->st>>>(a->cnt, (long long)a->cfg.ring); count_launch(); }
     CK(cudaGetLastError());
     ph_end(c, e1);
     return DIAM_OK;

@@ -41,12 +41,6 @@ __global__ void mlp_out_kernel(int rows, int h2, const uint16_t* __restrict__ H2
     s_out[r] = musig[0] + musig[1] * (double)(acc + b3[0]);
 }
 
-struct DaCounters {
-    unsigned long long tested, passed, exact;
-    int count;           // survivors of the current step
-    int pad;
-    long long head, filled;   // ring buffer
-};
 
 // Stage 1 for every chain (one block, P <= 1024 threads): q(x*) from the proposal's partial sums, then
 // with the surrogate active: s(x*) = the exact O(d) terms + the network's value of the linear-map terms,
@@ -197,10 +191,7 @@ __global__ void add_kernel(int n, const double* __restrict__ a, double* __restri
     if (i < n) b[i] += a[i];
 }
 
-__global__ void ring_advance_kernel(DaCounters* cnt, long long cap) {
-    cnt->head = (cnt->head + cnt->count) % cap;
-    cnt->filled = min(cap, cnt->filled + (long long)cnt->count);
-}
+
 
 // ---------------------------------------------------------------------------------------------------- training
 // Training slot j (of the non-held-out slots, those with slot % 10 != 9) -> ring slot.

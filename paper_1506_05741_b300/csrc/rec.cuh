@@ -64,13 +64,5 @@ __global__ void __launch_bounds__(256) rec_map_kernel(int P, int dy, const Ctl* 
     if (threadIdx.x == 0) lmap[p] = (double)acc;
 }
 
-// Accepted chains take the proposal's map values.
-__global__ void select_ax_kernel(int P, int dy, const int8_t* __restrict__ accf, float* __restrict__ Ax,
-                                 const float* __restrict__ Axp) {
-    const int p = blockIdx.x;
-    if (!accf[p]) return;
-    for (int m = threadIdx.x; m < dy; m += blockDim.x) Ax[(size_t)p * dy + m] = Axp[(size_t)p * dy + m];
-}
-
 }  // namespace
 }  // namespace diam

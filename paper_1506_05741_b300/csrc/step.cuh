@@ -21,7 +21,7 @@ struct Ctl {
     double trace;                      // tr(M2) at the last refresh
     long long t_cur;                   // global step the step kernels are working on
     int s_cur;                         // its index within the interval
-    int pad_;
+    unsigned done_blocks;              // blocks of the step's last kernel that have finished (0 between steps)
 };
 
 // End of one step: the step counters move on (the step kernels read them, so a captured graph of the
@@ -339,12 +339,28 @@ __device__ __forceinline__ double to_hist<double, double>(double v) { return v; 
 template <>
 __device__ __forceinline__ float to_hist<float, float>(float v) { return v; }
 
+// Counters of the delayed-acceptance screen and of its ring buffer of exactly evaluated pairs.
+struct DaCounters {
+    unsigned long long tested, passed, exact;
+    int count;           // survivors of the current step
+    int pad;
+    long long head, filled;   // ring buffer
+};
+
+// The ring head moves past this step's exactly evaluated pairs.
+__device__ __forceinline__ void ring_advance_step(DaCounters* cnt, long long cap) {
+    cnt->head = (cnt->head + cnt->count) % cap;
+    cnt->filled = min(cap, cnt->filled + (long long)cnt->count);
+}
+
 template <typename T, typename HT>
-__global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, const Ctl* ctl, const int8_t* __restrict__ accf,
+__global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* ctl, const int8_t* __restrict__ accf,
                                                      T* __restrict__ X, T* __restrict__ Z, const T* __restrict__ Xp,
                                                      const T* __restrict__ Zp, HT* __restrict__ hist_base, int ldh,
                                                      const T* __restrict__ cen, HT* __restrict__ bsum_base,
-                                                     double* __restrict__ lpsum_base, const double* __restrict__ lp) {
+                                                     double* __restrict__ lpsum_base, const double* __restrict__ lp,
+                                                     float* __restrict__ Ax, const float* __restrict__ Axp, int dy,
+                                                     DaCounters* dacnt, long long ring_cap) {
     const int p = blockIdx.x, c = blockIdx.y;
     const long long blk = ctl->t_cur / nl;
     HT* hist = hist_base ? hist_base + (size_t)ctl->s_cur * P * ldh : nullptr;
@@ -358,6 +374,7 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, const
     const T* zp = Zp + (size_t)p * d;
     HT* h = hist ? hist + (size_t)p * ldh : nullptr;
     HT* bs = bsum ? bsum + (size_t)p * d : nullptr;
+    bool vec_done = false;
     if constexpr (std::is_same<T, float>::value && std::is_same<HT, float>::value) {
         if ((d & 3) == 0 && (ldh & 3) == 0 && h) {
             for (int i = i0 + 4 * threadIdx.x; i < i1; i += 4 * blockDim.x) {
@@ -373,11 +390,10 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, const
                     *reinterpret_cast<float4*>(bs + i) = make_float4(b.x + v.x, b.y + v.y, b.z + v.z, b.w + v.w);
                 }
             }
-            if (lpsum && c == 0 && threadIdx.x == 0) lpsum[p] += lp[p];
-            return;
+            vec_done = true;
         }
     }
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    for (int i = i0 + threadIdx.x; !vec_done && i < i1; i += blockDim.x) {
         T v = a ? xp[i] : x[i];
         if (a) {
             x[i] = v;
@@ -386,7 +402,23 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, const
         if (h) h[i] = to_hist<T, HT>(v - cen[i]);
         if (bs) bs[i] += (HT)v;
     }
+    if (Ax && a) {   // the carried map: accepted chains take A x*, block c its share of the row
+        const int per = (dy + gridDim.y - 1) / gridDim.y;
+        for (int m = c * per + threadIdx.x; m < min(dy, (c + 1) * per); m += blockDim.x)
+            Ax[(size_t)p * dy + m] = Axp[(size_t)p * dy + m];
+    }
     if (lpsum && c == 0 && threadIdx.x == 0) lpsum[p] += lp[p];
+    // the last block of the step moves the step counters (and the ring head) on
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->done_blocks, 1u) == gridDim.x * gridDim.y - 1) {
+            if (dacnt) ring_advance_step(dacnt, ring_cap);
+            ctl->t_cur += 1;
+            ctl->s_cur += 1;
+            ctl->done_blocks = 0;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------------
