@@ -98,6 +98,7 @@ struct diam_ctx {
     // target
     double *inv_lam = nullptr, *Gm = nullptr, *y = nullptr;
     float *inv_lam32 = nullptr, *y32 = nullptr;   // FP32 copies for the BF16-mode kernels
+    float* psum = nullptr;   // per-tile sums of the interval's records (BF16 mode fold): 2 x tiles x d
     // the linear map carried through the proposal (BF16 mode, linear-map targets): M = A Lq as BF16 hi + lo,
     // A x of the states and of the proposals, A x_ref, the interval's products M W (scaled by beta alpha)
     bool rec = false, ax_dirty = true;
@@ -538,23 +539,25 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
     int e0 = ph_begin(c, PH_FOLD);
     constexpr bool BF = std::is_same<T, float>::value;
     if constexpr (BF) {
+        // samples as the K index: one pass over the interval's FP32 records writes their BF16 transpose
+        // (d x rows, K-contiguous) and the per-tile sums of the records and of their BF16 values; the totals give
+        // the centring terms (the interval mean from the FP32 records, not rounded to BF16) and s16 for the
+        // lower-triangle SYRK on the tensor cores, whose epilogue does the FP64 fold
+        const int ldt = ((int)rows + 63) / 64 * 64, ntile = ldt / 32;
         const float* H = (const float*)c->hist + (size_t)s0 * P * c->ldh;
-        { colsum_partial_kernel<float><<<dim3(blocks_for(d), R), kThreads, 0, c->st>>>(H, c->ldh, (int)rows, d, c->colpart); count_launch(); }
+        { fold_transpose_kernel<<<dim3((d + 31) / 32, ntile), dim3(32, 8), 0, c->st>>>(H, c->ldh, (int)rows, d, c->histT, ldt,
+                                                                                    c->psum, c->psum + (size_t)ntile * d); count_launch(); }
+        { fold_sums_kernel<<<(d + 31) / 32, kThreads, 0, c->st>>>(d, ntile, c->psum, c->psum + (size_t)ntile * d, c->cen64,
+                                                                c->mean, 1.0 / nb, c->svec, c->delta, c->s16); count_launch(); }
     } else {
         const double* H = (const double*)c->hist + (size_t)s0 * P * c->ldh;
         { colsum_partial_kernel<double><<<dim3(blocks_for(d), R), kThreads, 0, c->st>>>(H, c->ldh, (int)rows, d, c->colpart); count_launch(); }
+        { fold_prep_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, R, c->colpart, c->cen64, c->mean, 1.0 / nb, c->svec,
+                                                                c->delta); count_launch(); }
     }
-    { fold_prep_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, R, c->colpart, c->cen64, c->mean, 1.0 / nb, c->svec,
-                                                            c->delta); count_launch(); }
     double w = (double)c->n * nb / ((double)c->n + nb);
     if constexpr (BF) {
-        // samples as the K index: transpose the interval's FP32 records to d x rows (K-contiguous), rounded
-        // to BF16, then the lower-triangle SYRK on the tensor cores with the FP64 fold in the epilogue; the
-        // column sums above come from the FP32 records, so the interval mean is not rounded to BF16
-        int ldt = ((int)rows + 63) / 64 * 64;
-        const float* H = (const float*)c->hist + (size_t)s0 * P * c->ldh;
-        CK(transpose_f32_bf16(H, c->ldh, (int)rows, d, c->histT, ldt, c->st));
-        { rowsum_bf16_kernel<<<d, kThreads, 0, c->st>>>(c->histT, ldt, (int)rows, c->s16); count_launch(); }
+        const int ldt = ((int)rows + 63) / 64 * 64;
         TcEpi epi{};
         epi.mode = TC_FOLD;
         epi.M2 = c->M2;
@@ -867,6 +870,7 @@ static diam_status alloc_all(diam_ctx* c) {
         CKS(dalloc(c, &c->W, sizeof(uint16_t) * rows * c->ldw));
         CKS(dalloc(c, &c->hist, sizeof(float) * rows * c->ldh));
         CKS(dalloc(c, &c->histT, sizeof(uint16_t) * (size_t)d * ((rows + 63) / 64 * 64)));
+        CKS(dalloc(c, &c->psum, sizeof(float) * 2 * (size_t)d * (((rows + 63) / 64 * 64) / 32)));
         if (c->kind == TK_TANH || c->kind == TK_DENSE) {
             c->rec = true;
             const size_t dy = (size_t)std::max(c->dy, 1);

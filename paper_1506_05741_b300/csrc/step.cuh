@@ -464,6 +464,82 @@ __global__ void fold_prep_kernel(int d, int nparts, const double* __restrict__ p
     delta[i] = (cen64[i] + v * inb) - mean[i];
 }
 
+// The interval's FP32 records (rows samples x d coordinates, stride ldh) in one pass: their BF16 transpose
+// (d x ldt, K-contiguous, zero past the last sample: the SYRK operand) and, per 32-sample tile and
+// coordinate, the FP32 sums of the records and of their BF16-rounded values (psum, pbf: ntile x d).
+__global__ void __launch_bounds__(256) fold_transpose_kernel(const float* __restrict__ H, int ldh, int rows, int d,
+                                                             uint16_t* __restrict__ HT_, int ldt,
+                                                             float* __restrict__ psum, float* __restrict__ pbf) {
+    __shared__ uint16_t tile[32][33];
+    __shared__ float sx[8][33], sb[8][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    float ax = 0.f, ab = 0.f;
+    for (int k = ty; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + tx;
+        const float v = (r < rows && c < d) ? H[(size_t)r * ldh + c] : 0.f;
+        const uint16_t b = f32_to_bf16_bits(v);
+        tile[k][tx] = b;
+        ax += v;
+        ab += bf16_bits_to_f32(b);
+    }
+    sx[ty][tx] = ax;
+    sb[ty][tx] = ab;
+    __syncthreads();
+    if (ty == 0 && c0 + tx < d) {
+        float tx_sum = 0.f, tb_sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            tx_sum += sx[k][tx];
+            tb_sum += sb[k][tx];
+        }
+        psum[(size_t)blockIdx.y * d + c0 + tx] = tx_sum;
+        pbf[(size_t)blockIdx.y * d + c0 + tx] = tb_sum;
+    }
+    for (int k = ty; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + tx;
+        if (c < d && r < ldt) HT_[(size_t)c * ldt + r] = tile[tx][k];
+    }
+}
+
+// Column totals of the tile sums (compensated FP32 per thread, Kahan 1965; FP64 across threads), then the
+// interval's centring terms: s = sum of the records, delta = (c + s / nb) - mean, s16 = sum of their BF16
+// values. One block per 32 coordinates, 8 threads per coordinate.
+__global__ void __launch_bounds__(256) fold_sums_kernel(int d, int ntile, const float* __restrict__ psum,
+                                                        const float* __restrict__ pbf, const double* __restrict__ cen64,
+                                                        const double* __restrict__ mean, double inb,
+                                                        double* __restrict__ s, double* __restrict__ delta,
+                                                        double* __restrict__ s16) {
+    __shared__ double rx[8][32], rb[8][32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    float sx = 0.f, cx = 0.f, sb = 0.f, cb = 0.f;
+    if (i < d) {
+        for (int t = g; t < ntile; t += 8) {
+            const float yx = psum[(size_t)t * d + i] - cx, yb = pbf[(size_t)t * d + i] - cb;
+            const float tx = sx + yx, tb = sb + yb;
+            cx = (tx - sx) - yx;
+            cb = (tb - sb) - yb;
+            sx = tx;
+            sb = tb;
+        }
+    }
+    rx[g][lane] = (double)sx - (double)cx;
+    rb[g][lane] = (double)sb - (double)cb;
+    __syncthreads();
+    if (g == 0 && i < d) {
+        double vx = 0.0, vb = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            vx += rx[k][lane];
+            vb += rb[k][lane];
+        }
+        s[i] = vx;
+        delta[i] = (cen64[i] + vx * inb) - mean[i];
+        s16[i] = vb;
+    }
+}
+
 // s16[i] = sum over the interval's samples of the BF16-rounded centred records (row i of the transposed
 // record): the sums of exactly the values the tensor-core SYRK multiplies, so that G - s16 s16^T / nb is
 // the scatter matrix of those values (positive semi-definite up to the FP32 accumulation).
