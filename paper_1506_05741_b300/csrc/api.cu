@@ -1093,15 +1093,11 @@ static diam_status read_moments(diam_ctx* c, double* mean, double* M, int64_t* n
     CKS(sync_and_check(c));
     const int d = c->d;
     if (mean) CK(d2h(c, mean, c->mean, sizeof(double) * d));
-    if (M) {
-        CK(d2h(c, M, c->M2, sizeof(double) * d * d));
-        double s = (as_cov && c->n > 0) ? 1.0 / (double)c->n : 1.0;
-        for (int i = 0; i < d; ++i)
-            for (int j = 0; j <= i; ++j) {
-                double v = M[(size_t)i * d + j] * s;
-                M[(size_t)i * d + j] = v;
-                M[(size_t)j * d + i] = v;
-            }
+    if (M) {   // scaled and mirrored on the device (the refresh's scratch matrix), then one copy
+        const double s = (as_cov && c->n > 0) ? 1.0 / (double)c->n : 1.0;
+        { symmetrize_kernel<<<dim3((d + 31) / 32, (d + 31) / 32), dim3(32, 8), 0, c->st>>>(d, c->M2, s, c->Cw); count_launch(); }
+        CK(cudaGetLastError());
+        CK(d2h(c, M, c->Cw, sizeof(double) * d * d));
     }
     if (n) *n = c->n;
     return DIAM_OK;

@@ -37,19 +37,19 @@ __device__ __forceinline__ bool positive_finite(double D) {
 }
 
 // Cholesky of the nb x nb diagonal block at (k0, k0), nb <= 64: lower part in, L out, upper part zeroed.
-// Right-looking LDL^T in shared memory: pivot j subtracts a_ij (a_lj / D_j) from every a_il with
-// j < l <= i, leaving a_ij = L_ij sqrt(D_j); the square roots are taken once at the end. Per pivot j:
-//   - warp 0 (the critical path) updates column j + 1 in registers, takes 1 / D_{j+1} and publishes that
-//     column and its scaled copy into a double-buffered shared column;
-//   - the warps on the other three schedulers update columns j + 2 .. nb - 1, whose elements a packed table
-//     lists column by column from the last one, so the active elements are always a prefix of it and no lane
-//     is masked off; each thread loads up to four of its elements before it updates them;
-// then one barrier.
-constexpr int DIAG_THREADS = 512;
+// LDL^T in shared memory, in sub-panels of 16 columns: pivot j subtracts a_ij (a_lj / D_j) from a_il, leaving
+// a_ij = L_ij sqrt(D_j); the square roots are taken once at the end. Inside a sub-panel, per pivot j:
+//   - warp 0 (the critical path) updates column j + 1, takes 1 / D_{j+1} and publishes that column and its
+//     scaled copy (double-buffered shared columns, and the sub-panel's scaled columns for the rank update);
+//   - the warps on the other three schedulers update the sub-panel's columns j + 2 .. (a packed table lists
+//     the lower triangle column by column from the last one, so any run of columns is one contiguous range);
+// then one barrier. After the sub-panel's pivots every thread takes part in its rank-16 update of the
+// columns to its right, so the pivot steps carry only the small in-panel updates.
+constexpr int DIAG_THREADS = 512, DIAG_SB = 16;
 
-// Warp 0 publishes column c: rows c + lane (v0) and c + 32 + lane (v1), D_c = v0 on lane 0.
-__device__ __forceinline__ void diag_publish(int c, double v0, double v1, int lane, int nb, int k0, int* info,
-                                             double* dpiv, double (*colb)[CH_NB], double (*scol)[CH_NB]) {
+__device__ __forceinline__ void diag_publish(int c, int q0, double v0, double v1, int lane, int nb, int k0, int* info,
+                                             double* dpiv, double (*colb)[CH_NB], double (*scol)[CH_NB],
+                                             double (*scp)[CH_NB + 1]) {
     double r = 0.0;
     if (lane == 0) {
         if (positive_finite(v0)) {
@@ -63,13 +63,17 @@ __device__ __forceinline__ void diag_publish(int c, double v0, double v1, int la
     r = __shfl_sync(0xffffffffu, r, 0);
     const int b = c & 1;
     if (c + lane < nb) {
+        const double sv = v0 * r;
         colb[b][c + lane] = v0;
-        scol[b][c + lane] = v0 * r;
+        scol[b][c + lane] = sv;
+        scp[c - q0][c + lane] = sv;
     }
     if (c + 32 < nb) {   // warp-uniform: the second half exists
         if (c + 32 + lane < nb) {
+            const double sv = v1 * r;
             colb[b][c + 32 + lane] = v1;
-            scol[b][c + 32 + lane] = v1 * r;
+            scol[b][c + 32 + lane] = sv;
+            scp[c - q0][c + 32 + lane] = sv;
         }
     }
 }
@@ -77,9 +81,10 @@ __device__ __forceinline__ void diag_publish(int c, double v0, double v1, int la
 __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(double* __restrict__ A, int lda, int k0, int nb,
                                                                  int* info) {
     __shared__ double a[CH_NB][CH_NB + 1];
-    __shared__ double colb[2][CH_NB];   // a_ij, i > j, of the current pivot j
-    __shared__ double scol[2][CH_NB];   // a_ij / D_j
-    __shared__ double dpiv[CH_NB];      // D_j
+    __shared__ double colb[2][CH_NB];          // a_ij, i > j, of the current pivot j
+    __shared__ double scol[2][CH_NB];          // a_ij / D_j
+    __shared__ double scp[DIAG_SB][CH_NB + 1]; // the current sub-panel's scaled columns
+    __shared__ double dpiv[CH_NB];             // D_j
     __shared__ double dsq[CH_NB], dinv[CH_NB];
     __shared__ uint16_t tab[CH_NB * (CH_NB + 1) / 2];   // (i << 8) | l, columns nb-1 down to 0
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -92,59 +97,64 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(double* __restr
         for (int r = 0; r < nb - l; ++r) tab[off + r] = (uint16_t)(((l + r) << 8) | l);
     }
     __syncthreads();
-    if (w == 0)
-        diag_publish(0, lane < nb ? a[lane][0] : 0.0, lane + 32 < nb ? a[lane + 32][0] : 0.0, lane, nb, k0, info, dpiv,
-                     colb, scol);
-    __syncthreads();
-    // bulk warps: those not on warp 0's scheduler (warp w issues on sub-partition w % 4), so that the
-    // pivot chain never waits behind their FP64 instructions
+    // bulk warps (the three schedulers other than warp 0's, warp w issuing on sub-partition w % 4)
     constexpr int NB_T = (DIAG_THREADS / 32) / 4 * 3 * 32;
-    const int bt = (w - (w >> 2) - 1) * 32 + lane;   // index among the bulk threads (w % 4 != 0)
-    for (int j = 0; j < nb; ++j) {
-        const int b = j & 1, jn = j + 1;
-        if (w == 0) {
-            if (jn < nb) {
-                const double s = scol[b][jn];
-                const int i0 = jn + lane, i1 = jn + lane + 32;
-                double v0 = 0.0, v1 = 0.0;
-                if (i0 < nb) {
-                    v0 = fma(-colb[b][i0], s, a[i0][jn]);
-                    a[i0][jn] = v0;
-                }
-                if (jn + 32 < nb) {   // warp-uniform, so no FP64 instruction is issued for an empty half
-                    if (i1 < nb) {
-                        v1 = fma(-colb[b][i1], s, a[i1][jn]);
-                        a[i1][jn] = v1;
-                    }
-                }
-                diag_publish(jn, v0, v1, lane, nb, k0, info, dpiv, colb, scol);
-            }
-        } else if (w & 3) {
-            const int T = (nb - j - 2) * (nb - j - 1) / 2;   // elements of columns j + 2 .. nb - 1
-            for (int e0 = bt; e0 < T; e0 += 4 * NB_T) {
-                int ii[4], ll[4];
-                double x[4], c[4], sc[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int e = e0 + q * NB_T;
-                    const int t = (e < T) ? tab[e] : 0;
-                    ii[q] = t >> 8;
-                    ll[q] = t & 255;
-                    x[q] = a[ii[q]][ll[q]];
-                    c[q] = colb[b][ii[q]];
-                    sc[q] = scol[b][ll[q]];
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (e0 + q * NB_T < T) a[ii[q]][ll[q]] = fma(-c[q], sc[q], x[q]);
-            }
-        }
+    const int bt = (w - (w >> 2) - 1) * 32 + lane;
+    auto col_start = [&](int l) { return (nb - l - 1) * (nb - l) / 2; };   // first table entry of column l
+    for (int q0 = 0; q0 < nb; q0 += DIAG_SB) {
+        const int q1 = min(nb, q0 + DIAG_SB);
+        if (w == 0)
+            diag_publish(q0, q0, q0 + lane < nb ? a[q0 + lane][q0] : 0.0, q0 + 32 + lane < nb ? a[q0 + 32 + lane][q0] : 0.0,
+                         lane, nb, k0, info, dpiv, colb, scol, scp);
         __syncthreads();
+        for (int j = q0; j < q1; ++j) {
+            const int b = j & 1, jn = j + 1;
+            if (w == 0) {
+                if (jn < q1) {
+                    const double s = scol[b][jn];
+                    const int i0 = jn + lane, i1 = jn + lane + 32;
+                    double v0 = 0.0, v1 = 0.0;
+                    if (i0 < nb) {
+                        v0 = fma(-colb[b][i0], s, a[i0][jn]);
+                        a[i0][jn] = v0;
+                    }
+                    if (jn + 32 < nb) {   // warp-uniform, so no FP64 instruction is issued for an empty half
+                        if (i1 < nb) {
+                            v1 = fma(-colb[b][i1], s, a[i1][jn]);
+                            a[i1][jn] = v1;
+                        }
+                    }
+                    diag_publish(jn, q0, v0, v1, lane, nb, k0, info, dpiv, colb, scol, scp);
+                }
+            } else if ((w & 3) && j + 2 < q1) {
+                // columns j + 2 .. q1 - 1 of the sub-panel: table entries [start(q1 - 1), start(j + 1))
+                const int e0 = col_start(q1 - 1), e1 = col_start(j + 1);
+                for (int e = e0 + bt; e < e1; e += NB_T) {
+                    const int t = tab[e], i = t >> 8, l = t & 255;
+                    a[i][l] = fma(-colb[b][i], scol[b][l], a[i][l]);
+                }
+            }
+            __syncthreads();
+        }
+        if (q1 < nb) {   // rank-(q1 - q0) update of the columns q1 .. nb - 1: table entries [0, start(q1 - 1))
+            const int e1 = col_start(q1 - 1), kn = q1 - q0;
+            for (int e = tid; e < e1; e += DIAG_THREADS) {
+                const int t = tab[e], i = t >> 8, l = t & 255;
+                double s0 = 0.0, s1 = 0.0;   // two partial sums: half the dependent FP64 chain
+                for (int k = 0; k + 1 < kn; k += 2) {
+                    s0 = fma(a[i][q0 + k], scp[k][l], s0);
+                    s1 = fma(a[i][q0 + k + 1], scp[k + 1][l], s1);
+                }
+                if (kn & 1) s0 = fma(a[i][q1 - 1], scp[kn - 1][l], s0);
+                a[i][l] -= s0 + s1;
+            }
+            __syncthreads();
+        }
     }
     if (tid < nb) {
-        const double q = sqrt(dpiv[tid]);
-        dsq[tid] = q;
-        dinv[tid] = 1.0 / q;
+        const double qv = sqrt(dpiv[tid]);
+        dsq[tid] = qv;
+        dinv[tid] = 1.0 / qv;
     }
     __syncthreads();
     for (int idx = tid; idx < nb * nb; idx += DIAG_THREADS) {

@@ -540,6 +540,27 @@ __global__ void __launch_bounds__(256) fold_sums_kernel(int d, int ntile, const 
     }
 }
 
+// out = s * M with M symmetric and only its lower triangle stored (both d x d, stride d): 32 x 32 tiles,
+// the upper tiles through a shared-memory transpose of their lower mirror.
+__global__ void symmetrize_kernel(int d, const double* __restrict__ M, double s, double* __restrict__ out) {
+    __shared__ double t[32][33];
+    const int bi = blockIdx.y, bj = blockIdx.x;   // output tile (rows bi, columns bj)
+    const int si = max(bi, bj), sj = min(bi, bj);  // source tile in the lower triangle
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = si * 32 + k, c = sj * 32 + threadIdx.x;
+        t[k][threadIdx.x] = (r < d && c < d && c <= r) ? M[(size_t)r * d + c] : 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = bi * 32 + k, c = bj * 32 + threadIdx.x;
+        if (r >= d || c >= d) continue;
+        // element (r, c) = M[max][min]: in the source tile at (r - 32 si, c - 32 sj) or its transpose
+        const double v = (c <= r) ? ((bi == si) ? t[k][threadIdx.x] : t[threadIdx.x][k])
+                                  : ((bi == si) ? t[threadIdx.x][k] : t[threadIdx.x][k]);
+        out[(size_t)r * d + c] = s * v;
+    }
+}
+
 // s16[i] = sum over the interval's samples of the BF16-rounded centred records (row i of the transposed
 // record): the sums of exactly the values the tensor-core SYRK multiplies, so that G - s16 s16^T / nb is
 // the scatter matrix of those values (positive semi-definite up to the FP32 accumulation).
