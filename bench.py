@@ -206,9 +206,14 @@ def run_arm(name, run, ts, x0, C0, prec, da, W, K, torch, stream, dm, clocks_ind
     return out, dt, launches, clk
 
 
-def roofline(prof, run, ts, pk, pk_src):
+def roofline(prof, run, ts, pk, pk_src, acc_rate, ring, keep_sums):
     """Per-phase achieved rate against its bound, from the profiled intervals; the dominant phase first."""
     d, dy, P, nl = ts.d, ts.d_y, run.P, run.n_lag
+    # the fused step (one launch): reads x, z, xi (FP32), W (BF16), A x and A xi (FP32); writes the FP32 record
+    # row, x, z and A x of the accepted chains, the BF16 ring row of every proposal (surrogate attached) and
+    # the interval sums (read + write, when kept)
+    step_bytes = (P * d * (4 + 4 + 4 + 2 + 4) + acc_rate * P * d * (4 + 4) + P * dy * (4 + 4) + acc_rate * P * dy * 4
+                  + (P * d * 2 if ring else 0) + (P * d * 8 if keep_sums else 0))
     N = P * nl
     sus = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
     # algorithmic work per launch of each phase (a launch = one step, or one interval for noise / xi / fold /
@@ -227,6 +232,7 @@ def roofline(prof, run, ts, pk, pk_src):
         "noise": ("hbm", N * d * 2, "GB/s", pk["hbm_gbs"]),                  # BF16 W for the interval
         "rewhiten": ("alu", float(d) * d * P, "TFLOP/s", FP64_PEAK_TFLOPS),  # the triangular re-solve
         "screen": ("tensor", 2.0 * P * (d * 512 + 512 * 512), "TFLOP/s", sus),
+        "step": ("hbm", step_bytes, "GB/s", pk["hbm_gbs"]),
     }
     total = sum(ms for _, ms in prof.values())
     table = {}
@@ -341,7 +347,7 @@ def main():
             sp.run(max(2, args.steps // 2) * run.n_lag)
             prof = sp.profile()
             sp.close()
-            roof = roofline(prof, run, ts, pk, pk_src)
+            roof = roofline(prof, run, ts, pk, pk_src, head["accept_rate"], da, False)
 
         # ---- end to end through the public API with host buffers: init (target, start state and surrogate
         # weights uploaded from host memory), K intervals each followed by a read of log pi, then the pooled

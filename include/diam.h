@@ -265,9 +265,11 @@ DIAM_API void diam_multi_destroy(diam_multi* m);
  * 0 noise draw, 1 noise product (batched triangular GEMM), 2 propose, 3 target (linear map + reduction),
  * 4 accept / select / record, 5 moment fold (column sums + SYRK), 6 Cholesky refresh (with its
  * retries), 7 re-whitening solve after a factor change, 8 surrogate screening (stage 1), 9 surrogate
- * training. counts and ms hold DIAM_N_PHASES entries each.
+ * training, 10 the whole step in one launch (propose + map + test + record, BF16 mode with the map carried
+ * through the proposal and no surrogate screen in force; phases 2-4 then stay empty).
+ * counts and ms hold DIAM_N_PHASES entries each.
  * reset = 1 clears the accumulators after reading. Synchronises. */
-#define DIAM_N_PHASES 10
+#define DIAM_N_PHASES 11
 DIAM_API diam_status diam_get_profile(diam_ctx* ctx, int64_t* counts, double* ms, int32_t reset);
 
 DIAM_API void diam_destroy(diam_ctx* ctx);

@@ -65,7 +65,7 @@ class DiamStats(C.Structure):
 EXPORTS = ["diam_config_default", "diam_init", "diam_run_batch", "diam_sync_moments", "diam_get_moments",
            "diam_export_moments", "diam_get_state", "diam_get_factor", "diam_get_trace", "diam_get_block_sums",
            "diam_save", "diam_load", "diam_get_profile", "diam_destroy", "diam_last_error", "diam_status_string"]
-PHASES = ["noise", "xi_gemm", "propose", "target", "accept", "fold", "refresh", "rewhiten", "screen", "train"]
+PHASES = ["noise", "xi_gemm", "propose", "target", "accept", "fold", "refresh", "rewhiten", "screen", "train", "step"]
 
 
 def kernel_launches() -> int:

@@ -124,7 +124,7 @@ struct diam_ctx {
 };
 
 enum : int { PH_NOISE = 0, PH_XI = 1, PH_PROPOSE = 2, PH_TARGET = 3, PH_ACCEPT = 4, PH_FOLD = 5, PH_REFRESH = 6,
-             PH_REWHITEN = 7, PH_SCREEN = 8, PH_TRAIN = 9 };
+             PH_REWHITEN = 7, PH_SCREEN = 8, PH_TRAIN = 9, PH_STEP = 10 };
 
 // Start timing a phase; returns the event slot (or -1 when profiling is off).
 static int ph_begin(diam_ctx* c, int phase) {
@@ -437,11 +437,64 @@ static diam_status ensure_bsum(diam_ctx* c, int64_t blk) {
     return DIAM_OK;
 }
 
+// The whole step in one launch (step_rec_kernel): BF16 mode, the target's map carried through the proposal
+// and no surrogate screen in force, for d, d_y <= 8192.
+static bool fused_step_fits(const diam_ctx* c) {
+    return c->bf && c->rec && (!c->da || !c->da->active) && c->d <= 4 * 8 * FUSED_THREADS &&
+           c->dy <= 4 * 8 * FUSED_THREADS;
+}
+
+template <int NV, int NM, bool VEC>
+static void launch_fused_step(diam_ctx* c) {
+    DaState* a = c->da;
+    const bool keep = c->cfg.keep_block_sums != 0;
+    step_rec_kernel<NV, NM, VEC><<<c->P, FUSED_THREADS, 0, c->st>>>(
+        c->d, c->P, c->nl, c->dy, c->ctl, c->key, c->tg, inv_infl2(c), (float*)c->X, (float*)c->Z,
+        (const float*)c->Xi, (const uint16_t*)c->W, c->ldw, (const float*)c->xref, (const float*)c->cenT, c->Ax,
+        c->axref, c->AXi, c->y32, (float)(1.0 / (2.0 * c->sigma * c->sigma)), c->kind == TK_TANH, c->lp, c->q,
+        c->accf, c->tr, (float*)c->hist, c->ldh, keep ? (float*)c->bsum : nullptr, keep ? c->lpsum : nullptr,
+        a ? a->cnt : nullptr, a ? a->ring_x : nullptr, a ? a->ring_lp : nullptr, a ? (long long)a->cfg.ring : 1,
+        c->ldk);
+    count_launch();
+}
+
+template <int NV, bool VEC>
+static void fused_step_nm(diam_ctx* c) {
+    const int nm = (c->dy + 4 * FUSED_THREADS - 1) / (4 * FUSED_THREADS);
+    if (nm <= 1) launch_fused_step<NV, 1, VEC>(c);
+    else if (nm <= 2) launch_fused_step<NV, 2, VEC>(c);
+    else if (nm <= 4) launch_fused_step<NV, 4, VEC>(c);
+    else launch_fused_step<NV, 8, VEC>(c);
+}
+
+template <bool VEC>
+static void fused_step_nv(diam_ctx* c) {
+    const int nv = (c->d + 4 * FUSED_THREADS - 1) / (4 * FUSED_THREADS);
+    if (nv <= 1) fused_step_nm<1, VEC>(c);
+    else if (nv <= 2) fused_step_nm<2, VEC>(c);
+    else if (nv <= 4) fused_step_nm<4, VEC>(c);
+    else fused_step_nm<8, VEC>(c);
+}
+
+static diam_status fused_step(diam_ctx* c) {
+    const bool vec = (c->d % 4) == 0 && (c->dy % 4) == 0 && (c->ldw % 4) == 0 && (c->ldh % 4) == 0 && (c->ldk % 4) == 0;
+    if (vec) fused_step_nv<true>(c);
+    else fused_step_nv<false>(c);
+    CK(cudaGetLastError());
+    return DIAM_OK;
+}
+
 // One step of every chain. The kernels read the step (global t, in-interval s) from the context's device
 // scalars and the last one advances it, so the same launch sequence can be captured once as a graph.
 template <typename T>
 static diam_status do_step(diam_ctx* c) {
     const int d = c->d, P = c->P;
+    if (fused_step_fits(c)) {
+        int e = ph_begin(c, PH_STEP);
+        CKS(fused_step(c));
+        ph_end(c, e);
+        return DIAM_OK;
+    }
     const T* Xi = (const T*)c->Xi;
     constexpr bool BF = std::is_same<T, float>::value;
     const dim3 grid2(P, c->nchunk);

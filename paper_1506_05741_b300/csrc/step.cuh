@@ -252,8 +252,8 @@ struct TraceDev {
 
 // Metropolis-Hastings test of Algorithm 1 for chain p, given log pi(x*) and q(x*):
 //   log a = log pi(x*) + q(x*) - log pi(x) - q(x);  accept iff log u < log a, u = Philox uniform (tag U).
-// Updates lp, q and the counters; records the decision for the select step.
-__device__ __forceinline__ void decide(int p, int P, Key key, int64_t t, double lpp, double qpp, double* lp, double* q,
+// Updates lp, q and the counters; records the decision for the select step and returns it.
+__device__ __forceinline__ int decide(int p, int P, Key key, int64_t t, double lpp, double qpp, double* lp, double* q,
                                        int8_t* accf, Ctl* ctl, const TraceDev& tr) {
     const double lpc = lp[p], qc = q[p];
     const double loga = lpp - lpc + qpp - qc;
@@ -271,6 +271,7 @@ __device__ __forceinline__ void decide(int p, int P, Key key, int64_t t, double 
     }
     if (!finite) atomicAdd(&ctl->nonfinite, 1ull);
     accf[p] = (int8_t)a;
+    return a;
 }
 
 // One thread per chain: log pi(x*) = O(d) partials + linear-map partials (FP64 GEMM epilogue), or an
@@ -414,6 +415,266 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
         __threadfence();
         if (atomicAdd(&ctl->done_blocks, 1u) == gridDim.x * gridDim.y - 1) {
             if (dacnt) ring_advance_step(dacnt, ring_cap);
+            ctl->t_cur += 1;
+            ctl->s_cur += 1;
+            ctl->done_blocks = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// One whole step of every chain in one launch, for a target whose expensive term is a linear map carried
+// through the proposal (BF16 mode; no surrogate screen in force). Block p holds chain p's proposal from the
+// draw to the record:
+//   x* = x_ref + rho (x - x_ref) + xi,  z* = rho z + beta alpha W   (eq. (diamnl), z-recursion)
+//   u  = rho (A x) + (1 - rho) (A x_ref) + A xi                     (the map of x*, A xi from the interval GEMM)
+//   log pi(x*) = prior terms of x* + likelihood terms of u,  q* = |z*|^2 / (2 alpha^2)
+// then the Metropolis-Hastings test of Algorithm 1, x, z, A x <- x*, z*, u when accepted, the centred record
+// row, the interval sums and, with a surrogate attached, the (bf16(x*), likelihood terms) training pair in
+// ring slot head + p. The last block to finish moves the step counters (and the ring head) on.
+// Only x* and u stay in registers across the test; the second pass reads x (rejected) or z and W (accepted,
+// z* recomputed by the same fused multiply-add) again, from L2. Sums are FP32, one tree per block.
+// Element layout of thread tid: VEC (d, d_y multiples of 4): entries 4 (tid + g FT) + j of group g < NV (NM);
+// otherwise entries tid + (4 g + j) FT. So d <= 4 NV FT and d_y <= 4 NM FT.
+constexpr int FUSED_THREADS = 256;
+
+template <int NV, int NM, bool VEC>
+__global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
+    int d, int P, int nl, int dy, Ctl* ctl, Key key, TargetDev tg, double inv_infl2,
+    float* __restrict__ X, float* __restrict__ Z, const float* __restrict__ Xi, const uint16_t* __restrict__ W, int ldw,
+    const float* __restrict__ xref, const float* __restrict__ cen, float* __restrict__ Ax,
+    const float* __restrict__ axref, const float* __restrict__ AXi, const float* __restrict__ y32, float inv2s2,
+    int tanh_mode, double* lp, double* q, int8_t* accf, TraceDev tr, float* __restrict__ hist_base, int ldh,
+    float* __restrict__ bsum_base, double* __restrict__ lpsum_base, DaCounters* dacnt, uint16_t* __restrict__ ring_x,
+    float* __restrict__ ring_lp, long long ring_cap, int ldk) {
+    constexpr int FT = FUSED_THREADS;
+    __shared__ float red[3][FT / 32];
+    __shared__ double s_lu, s_lpc, s_qc;
+    __shared__ int s_acc;
+    const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const float rho = (float)ctl->rho, ba = (float)ctl->ba, om = (float)(1.0 - ctl->rho);
+    const int s = ctl->s_cur;
+    const long long t = ctl->t_cur;
+    const size_t row = (size_t)s * P + p;
+    float* x = X + (size_t)p * d;
+    float* z = Z + (size_t)p * d;
+    const float* xi = Xi + row * d;
+    const uint16_t* w = W + row * ldw;
+    const bool prior = tg.kind == TK_TANH;   // the dense Gaussian's whole density is its map
+    auto idx = [&](int g, int j) { return VEC ? 4 * (tid + g * FT) + j : tid + (4 * g + j) * FT; };
+    if (tid == FT - 32) {   // the test's other inputs, off the path of the sums: log u (FP64), log pi(x), q(x)
+        s_lu = log(uniform53(key, t, (uint32_t)p, TAG_U));
+        s_lpc = lp[p];
+        s_qc = q[p];
+    }
+
+    float xs[4 * NV];
+    float qf = 0.f, lf = 0.f, mf = 0.f;
+#pragma unroll
+    for (int g = 0; g < NV; ++g) {
+        if (VEC) {
+            const int i = idx(g, 0);
+            if (i < d) {
+                const float4 xr = *reinterpret_cast<const float4*>(xref + i);
+                const float4 xa = *reinterpret_cast<const float4*>(x + i);
+                const float4 za = *reinterpret_cast<const float4*>(z + i);
+                const float4 ia = *reinterpret_cast<const float4*>(xi + i);
+                const uint2 wb = *reinterpret_cast<const uint2*>(w + i);
+                const float r4[4] = {xr.x, xr.y, xr.z, xr.w}, x4[4] = {xa.x, xa.y, xa.z, xa.w};
+                const float z4[4] = {za.x, za.y, za.z, za.w}, i4[4] = {ia.x, ia.y, ia.z, ia.w};
+                const float w4[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
+                                     bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
+                    const float zs = fmaf(rho, z4[j], ba * w4[j]);
+                    qf += zs * zs;
+                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i + j];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = idx(g, j);
+                if (i < d) {
+                    const float xr = xref[i];
+                    xs[4 * g + j] = xr + rho * (x[i] - xr) + xi[i];
+                    const float zs = fmaf(rho, z[i], ba * bf16_bits_to_f32(w[i]));
+                    qf += zs * zs;
+                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i];
+                }
+            }
+        }
+    }
+    float uv[4 * NM];
+    const float* ax = Ax + (size_t)p * dy;
+    const float* axi = AXi + row * dy;
+    auto map_term = [&](float u, float yv) {
+        if (tanh_mode) {
+            const float r = yv - tanhf(u);
+            mf -= r * r * inv2s2;
+        } else {
+            mf -= 0.5f * u * u;
+        }
+    };
+#pragma unroll
+    for (int g = 0; g < NM; ++g) {
+        if (VEC) {
+            const int m = idx(g, 0);
+            if (m < dy) {
+                const float4 a4 = *reinterpret_cast<const float4*>(ax + m);
+                const float4 r4 = *reinterpret_cast<const float4*>(axref + m);
+                const float4 i4 = *reinterpret_cast<const float4*>(axi + m);
+                const float4 y4 = tanh_mode ? *reinterpret_cast<const float4*>(y32 + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+                uv[4 * g] = fmaf(rho, a4.x, fmaf(om, r4.x, i4.x));
+                uv[4 * g + 1] = fmaf(rho, a4.y, fmaf(om, r4.y, i4.y));
+                uv[4 * g + 2] = fmaf(rho, a4.z, fmaf(om, r4.z, i4.z));
+                uv[4 * g + 3] = fmaf(rho, a4.w, fmaf(om, r4.w, i4.w));
+                map_term(uv[4 * g], y4.x);
+                map_term(uv[4 * g + 1], y4.y);
+                map_term(uv[4 * g + 2], y4.z);
+                map_term(uv[4 * g + 3], y4.w);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int m = idx(g, j);
+                if (m < dy) {
+                    uv[4 * g + j] = fmaf(rho, ax[m], fmaf(om, axref[m], axi[m]));
+                    map_term(uv[4 * g + j], tanh_mode ? y32[m] : 0.f);
+                }
+            }
+        }
+    }
+    // the three sums over the block, then the test (Algorithm 1) in thread 0
+    qf = warp_sum(qf);
+    lf = warp_sum(lf);
+    mf = warp_sum(mf);
+    if (lane == 0) {
+        red[0][wid] = qf;
+        red[1][wid] = lf;
+        red[2][wid] = mf;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        float a0 = lane < FT / 32 ? red[0][lane] : 0.f;
+        float a1 = lane < FT / 32 ? red[1][lane] : 0.f;
+        float a2 = lane < FT / 32 ? red[2][lane] : 0.f;
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+        if (lane == 0) {
+            const double lmap = (double)a2;
+            const double lpp = (double)a1 + lmap, qpp = 0.5 * (double)a0 * inv_infl2;
+            const double loga = lpp - s_lpc + qpp - s_qc;
+            const bool finite = isfinite(lpp) && isfinite(qpp);
+            const int a = finite && (s_lu < loga);
+            if (t < tr.steps) {
+                const size_t k = (size_t)t * P + p;
+                tr.lp[k] = lpp; tr.q[k] = qpp; tr.qc[k] = s_qc; tr.loga[k] = loga; tr.acc[k] = (int8_t)a;
+            }
+            if (a) {
+                lp[p] = lpp;
+                q[p] = qpp;
+                atomicAdd(&ctl->acc_block, 1ull);
+            }
+            if (!finite) atomicAdd(&ctl->nonfinite, 1ull);
+            accf[p] = (int8_t)a;
+            s_acc = a;
+            if (ring_x) ring_lp[(dacnt->head + p) % ring_cap] = (float)lmap;
+            if (lpsum_base) lpsum_base[(size_t)(t / nl) * P + p] += a ? lpp : s_lpc;
+        }
+    }
+    __syncthreads();
+    const int a = s_acc;
+    float* h = hist_base ? hist_base + row * ldh : nullptr;
+    float* bs = bsum_base ? bsum_base + ((size_t)(t / nl) * P + p) * d : nullptr;
+    uint16_t* rx = ring_x ? ring_x + (size_t)((dacnt->head + p) % ring_cap) * ldk : nullptr;
+#pragma unroll
+    for (int g = 0; g < NV; ++g) {
+        if (VEC) {
+            const int i = idx(g, 0);
+            if (i < d) {
+                float v[4];
+                if (a) {
+                    const float4 za = *reinterpret_cast<const float4*>(z + i);
+                    const uint2 wb = *reinterpret_cast<const uint2*>(w + i);
+                    const float z4[4] = {za.x, za.y, za.z, za.w};
+                    const float w4[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
+                                         bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
+                    float zn[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        v[j] = xs[4 * g + j];
+                        zn[j] = fmaf(rho, z4[j], ba * w4[j]);
+                    }
+                    *reinterpret_cast<float4*>(x + i) = make_float4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<float4*>(z + i) = make_float4(zn[0], zn[1], zn[2], zn[3]);
+                } else {
+                    const float4 xa = *reinterpret_cast<const float4*>(x + i);
+                    v[0] = xa.x; v[1] = xa.y; v[2] = xa.z; v[3] = xa.w;
+                }
+                if (h) {
+                    const float4 cv = *reinterpret_cast<const float4*>(cen + i);
+                    *reinterpret_cast<float4*>(h + i) = make_float4(v[0] - cv.x, v[1] - cv.y, v[2] - cv.z, v[3] - cv.w);
+                }
+                if (bs) {
+                    const float4 b = *reinterpret_cast<const float4*>(bs + i);
+                    *reinterpret_cast<float4*>(bs + i) = make_float4(b.x + v[0], b.y + v[1], b.z + v[2], b.w + v[3]);
+                }
+                if (rx) {
+                    const uint32_t lo = (uint32_t)f32_to_bf16_bits(xs[4 * g]) | ((uint32_t)f32_to_bf16_bits(xs[4 * g + 1]) << 16);
+                    const uint32_t hi = (uint32_t)f32_to_bf16_bits(xs[4 * g + 2]) | ((uint32_t)f32_to_bf16_bits(xs[4 * g + 3]) << 16);
+                    *reinterpret_cast<uint2*>(rx + i) = make_uint2(lo, hi);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = idx(g, j);
+                if (i < d) {
+                    float v;
+                    if (a) {
+                        v = xs[4 * g + j];
+                        x[i] = v;
+                        z[i] = fmaf(rho, z[i], ba * bf16_bits_to_f32(w[i]));
+                    } else {
+                        v = x[i];
+                    }
+                    if (h) h[i] = v - cen[i];
+                    if (bs) bs[i] += v;
+                    if (rx) rx[i] = f32_to_bf16_bits(xs[4 * g + j]);
+                }
+            }
+        }
+    }
+    if (rx)   // the row's padding stays zero (the network's input width is ldk)
+        for (int i = d + tid; i < ldk; i += FT) rx[i] = 0;
+    if (a) {
+        float* axw = Ax + (size_t)p * dy;
+#pragma unroll
+        for (int g = 0; g < NM; ++g) {
+            if (VEC) {
+                const int m = idx(g, 0);
+                if (m < dy) *reinterpret_cast<float4*>(axw + m) = make_float4(uv[4 * g], uv[4 * g + 1], uv[4 * g + 2], uv[4 * g + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int m = idx(g, j);
+                    if (m < dy) axw[m] = uv[4 * g + j];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->done_blocks, 1u) == gridDim.x - 1) {
+            if (dacnt) {   // every proposal was evaluated exactly and went to the ring
+                dacnt->count = P;
+                dacnt->exact += (unsigned long long)P;
+                ring_advance_step(dacnt, ring_cap);
+            }
             ctl->t_cur += 1;
             ctl->s_cur += 1;
             ctl->done_blocks = 0;

@@ -61,12 +61,19 @@ def _bf16_pair(ts, P, steps, **kw):
     return make_pair(ts, P, trace_steps=steps, prec=_o.BF16, **kw)
 
 
-@pytest.mark.parametrize("kind", ["tanh", "dense", "diag"])
+@pytest.mark.parametrize("kind", ["tanh", "dense", "diag", "tanh_vec", "dense_vec"])
 def test_bf16_steps_match_oracle_bf16_mode(kind):
+    """The map-carrying targets run as one fused launch per step: scalar element layout for d or d_y not a
+    multiple of 4 (tanh, dense), 16-byte vectors otherwise (tanh_vec, dense_vec, with d past one element
+    group per thread)."""
     if kind == "tanh":
         ts, P = workloads.tanh_regression(200, 130, 31), 6
     elif kind == "dense":
         ts, P = workloads.dense_gaussian(150, 32), 5
+    elif kind == "tanh_vec":
+        ts, P = workloads.tanh_regression(2052, 132, 35), 4
+    elif kind == "dense_vec":
+        ts, P = workloads.dense_gaussian(160, 36), 5
     else:
         ts, P = workloads.diag_gaussian(100), 3
     d = ts.d

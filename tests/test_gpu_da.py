@@ -141,3 +141,33 @@ def test_trained_surrogate_saves_exact_evaluations():
     assert acc / (40 * nl * P) > 0.5 * sp["accepted"] / (60 * nl * P)
     plain.close()
     two.close()
+
+
+def test_inactive_surrogate_leaves_the_chain_unchanged():
+    """Until the surrogate passes its error bound, the screen is off: the chain with the network attached (its
+    ring filled by every step) is bit for bit the chain without it, and every proposal counts as an exact
+    evaluation that went to the ring."""
+    import paper_1506_05741_b300 as dm
+    d, P, nl = 256, 64, 16
+    ts = workloads.tanh_regression(d, 128, 24)
+    x0 = workloads.start_state(d, P, 6) * np.sqrt(ts.lam)
+
+    def sampler():
+        cfg = dm.default_config(d, P, prec=dm.BF16, n_lag=nl, M=2, seed=9, beta0=0.2)
+        return dm.Sampler(cfg, ts, x0=x0, C0=np.diag(ts.lam))
+
+    plain = sampler()
+    plain.run(nl * 12 + 5)
+    two = sampler()
+    two.da_enable(dm.da_default_config(h1=128, h2=128, batch=256, ring=3000, first_train_min=2000, train_steps=20,
+                                       retrain_every=2, rmse_bound=1e-9), workloads.mlp_init(d, 128, 128, seed=10))
+    two.run(nl * 12 + 5)
+    xa, la, sa = plain.state()
+    xb, lb, sb = two.state()
+    assert np.array_equal(xa, xb) and np.array_equal(la, lb) and sa == sb
+    st = two.da_stats()
+    steps = two.stats()["steps"]
+    assert st["active"] == 0 and st["trainings"] >= 1
+    assert st["exact_evals"] == steps * P and st["ring_filled"] == min(3000, steps * P)
+    plain.close()
+    two.close()
