@@ -4,12 +4,15 @@ Workload (tanh4096): Bayesian tanh regression, d = 4096, d_y = 2048, prior N(0, 
 N(0, 1/4096) in FP32, y = tanh(A x*) + 0.05 eps; P = 512 chains, n_lag = 128. A_0 = Cholesky of the prior
 covariance, x_0 drawn from the prior. One benchmark step = one interval of n_lag steps of all P chains
 (noise product, n_lag x (propose, screen, target, accept), moment fold, beta rule and the Cholesky refresh
-that is due every interval). Three arms run the same workload from the same start:
+that is due every interval). With --refresh-delay 1 (default; the paper's lag-time between a refresh and its
+use) the factor built from interval k's moments drives interval k + 2 and its Cholesky runs on its own stream
+beside interval k + 1; the timed region still holds the K intervals' K refreshes. Arms, same workload and start:
   mixed_da  (the headline value): BF16 factor / noise / map on the tensor cores, FP32 states, FP64-accurate
             refresh and moment fold, plus delayed acceptance with the MLP surrogate 4096 -> 512 -> 512 -> 1
             trained on the GPU (first training once 2e4 exactly evaluated pairs are in the 2e5-pair ring,
             then every 20 synchronisations; stage 1 off while the held-out RMSE exceeds 0.5 nats);
   mixed     the same without the surrogate;
+  mixed_da_in_order  the headline arm with refresh_delay 0 (each factor used right after its refresh);
   fp64      the plain FP64 form (every kernel FP64, DFMA Cholesky).
 Metrics: chain-steps/s = P n_lag / device time of an interval (everything above included), and min-ESS/s =
 min over coordinates of the batch-means effective sample size of the timed window (batches = one interval
@@ -40,12 +43,16 @@ FP64_PEAK_TFLOPS = 1.25   # B300 nominal FP64 (vector and tensor), the profiling
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8, help="timed intervals (of n_lag steps each) of the headline arm")
+    ap.add_argument("--steps", type=int, default=16, help="timed intervals (of n_lag steps each) of the headline arm")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--P", type=int, default=512)
     ap.add_argument("--n-lag", type=int, default=128)
     ap.add_argument("--no-da", action="store_true", help="headline arm without the surrogate")
+    ap.add_argument("--refresh-delay", type=int, default=1,
+                    help="interval k's factor drives interval k+1+delay (>= 1: its Cholesky runs beside interval k+1)")
+    ap.add_argument("--in-order-steps", type=int, default=-1,
+                    help="timed intervals of the headline arm with refresh_delay 0 (-1: --steps, 0: skip)")
     ap.add_argument("--mixed-steps", type=int, default=-1, help="timed intervals of the mixed arm (-1: --steps, 0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed intervals of the plain FP64 arm (0: skip)")
     ap.add_argument("--fp64-warmup", type=int, default=1)
@@ -120,10 +127,11 @@ def workload(P, n_lag):
     return run, ts, x0, C0
 
 
-def make_sampler(run, ts, x0, C0, prec, da=False, profile=0, stream=None, keep_sums=0):
+def make_sampler(run, ts, x0, C0, prec, da=False, profile=0, stream=None, keep_sums=0, delay=0):
     import paper_1506_05741_b300 as dm
     import workloads
-    cfg = dm.default_config(ts.d, run.P, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed, prec=prec, profile=profile)
+    cfg = dm.default_config(ts.d, run.P, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed, prec=prec, profile=profile,
+                            refresh_delay=delay)
     cfg["keep_block_sums"] = keep_sums
     s = dm.Sampler(cfg, ts, x0=x0, C0=C0, stream=stream)
     if da:
@@ -144,12 +152,15 @@ def rank_max(x, world, device):
 
 
 def time_intervals(s, n_lag, K, torch, stream):
-    """Device time of K intervals with CUDA events on the sampler's stream (synchronised on both sides)."""
+    """Device time of K intervals with CUDA events on the sampler's stream (synchronised on both sides). The
+    region opens with every stream idle and closes after the last interval's refresh has finished (flush), so
+    it holds exactly the K intervals' refreshes even when they run beside the following interval."""
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     s.run(K * n_lag)
+    s.flush()
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1e3
@@ -173,10 +184,11 @@ def ess_window(xs, n_lag, mom0, mom1):
     return ess, N
 
 
-def run_arm(name, run, ts, x0, C0, prec, da, W, K, torch, stream, dm, clocks_index=None):
+def run_arm(name, run, ts, x0, C0, prec, da, W, K, torch, stream, dm, clocks_index=None, delay=0):
     """W warm-up intervals, then K timed intervals; chain-steps/s, ESS of the timed window, counters."""
-    s = make_sampler(run, ts, x0, C0, prec, da=da, stream=stream.cuda_stream, keep_sums=1)
+    s = make_sampler(run, ts, x0, C0, prec, da=da, stream=stream.cuda_stream, keep_sums=1, delay=delay)
     s.run(W * run.n_lag)
+    s.profile(reset=True)
     mom0 = s.export_moments()
     l0 = dm.kernel_launches()
     clk = None
@@ -190,12 +202,15 @@ def run_arm(name, run, ts, x0, C0, prec, da, W, K, torch, stream, dm, clocks_ind
     xs, _ = s.block_sums(W + K)
     ess, N = ess_window(xs[W:W + K], run.n_lag, mom0, mom1)
     st = s.stats()
+    rf_cnt, rf_ms = s.profile()["refresh"]
     out = {"chain_steps_per_s": round(run.P * run.n_lag * K / dt, 1), "ms_per_step": round(dt / K * 1e3, 3),
            "timed_intervals": K, "warmup_intervals": W, "min_ess": round(float(ess.min()), 1),
            "min_ess_per_s": round(float(ess.min()) / dt, 2), "median_ess_per_s": round(float(np.median(ess)) / dt, 1),
            "argmin_coordinate": int(np.argmin(ess)), "window_samples": int(N),
            "accept_rate": round(st["accepted"] / max(1, st["steps"] * run.P), 4), "beta": round(st["beta"], 5),
            "refreshes": st["refreshes"], "chol_attempts": st["chol_attempts"]}
+    if rf_cnt:   # refreshes factorised beside the following interval: their device time there
+        out["refresh_beside_ms"] = round(rf_ms / rf_cnt, 3)
     if da:
         dst = s.da_stats()
         out["da"] = {"trainings": dst["trainings"], "active": int(dst["active"]),
@@ -287,8 +302,11 @@ def main():
     da = not args.no_da
     config = {"workload": f"tanh4096: d={ts.d}, d_y={ts.d_y}, P={run.P}, n_lag={run.n_lag}, BF16 factor/noise/map, "
                           f"FP32 states, FP64-accurate Cholesky refresh every interval"
+                          + (f" (used from the interval {1 + args.refresh_delay} after; factorised beside the next one)"
+                             if args.refresh_delay > 0 else "")
                           + (", delayed acceptance with the 4096-512-512-1 MLP surrogate" if da else ""),
               "d": ts.d, "d_y": ts.d_y, "P": run.P, "n_lag": run.n_lag, "delayed_acceptance": da,
+              "refresh_delay": args.refresh_delay,
               "step": "one interval: n_lag steps of all chains + moment fold + beta rule + Cholesky refresh",
               "l2": "inputs larger than L2 (per interval: BF16 noise 537 MB, noise product 1074 MB FP32)",
               "parallelism": f"replicas x{world} (chains independent; no data-path collective)"}
@@ -323,7 +341,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     head, dt, launches, clk = run_arm("mixed_da" if da else "mixed", run, ts, x0, C0, dm.BF16, da, args.warmup,
-                                      args.steps, torch, stream, dm, clocks_index=local)
+                                      args.steps, torch, stream, dm, clocks_index=local, delay=args.refresh_delay)
     dt = rank_max(dt, world, "cuda")
     value = world * N * args.steps / dt
     arms = {("mixed_da" if da else "mixed"): head}
@@ -334,10 +352,15 @@ def main():
         msteps = args.steps if args.mixed_steps < 0 else args.mixed_steps
         if da and msteps > 0:
             arms["mixed"], _, _, _ = run_arm("mixed", run, ts, x0, C0, dm.BF16, False, args.warmup, msteps, torch,
-                                             stream, dm)
+                                             stream, dm, delay=args.refresh_delay)
+        isteps = args.steps if args.in_order_steps < 0 else args.in_order_steps
+        if args.refresh_delay > 0 and isteps > 0:   # the same arm with each factor used right after its refresh
+            name = ("mixed_da" if da else "mixed") + "_in_order"
+            arms[name], _, _, _ = run_arm(name, run, ts, x0, C0, dm.BF16, da, args.warmup, isteps, torch, stream, dm,
+                                          delay=0)
         if args.fp64_steps > 0:
             arms["fp64"], _, _, _ = run_arm("fp64", run, ts, x0, C0, dm.FP64, False, args.fp64_warmup,
-                                            args.fp64_steps, torch, stream, dm)
+                                            args.fp64_steps, torch, stream, dm, delay=args.refresh_delay)
 
         # ---- profile pass: per-phase device time with CUDA events on the same stream
         if not args.no_profile:

@@ -113,7 +113,9 @@ typedef struct {
                                BF16 mode starts at max(eps_jitter, 1e-4): its C_n is accumulated in FP32 */
     int64_t min_samples_refresh;  /* refresh only after this many accepted moves (< 0: d + 1) */
     int64_t burnin;         /* n_0: steps kept out of the moments (footnote to Algorithm 1) */
-    int32_t refresh_delay;  /* the factor built at the end of interval k is used from interval k+1+delay */
+    int32_t refresh_delay;  /* the factor built at the end of interval k is used from interval k+1+delay;
+                               with delay >= 1, BF16 mode and graphs on, its Cholesky runs on a stream of
+                               its own beside interval k+1's steps and is resolved at that interval's end */
     int32_t prec;           /* diam_prec */
     uint64_t seed;          /* Philox4x32-10 key */
     uint32_t problem_id;    /* mixed into the key; distinct problems draw distinct streams */
@@ -148,6 +150,11 @@ DIAM_API diam_status diam_init(const diam_config* cfg, const diam_target* target
 
 /* Advance every chain n_steps steps (any n_steps >= 0; refreshes happen at multiples of n_lag). */
 DIAM_API diam_status diam_run_batch(diam_ctx* ctx, int64_t n_steps);
+
+/* Wait for the work the context runs beside its stream (a refresh factorisation in flight, see
+ * refresh_delay) and apply its outcome; afterwards the context's stream is ordered after that work.
+ * State queries and checkpoints do this themselves. Synchronises. */
+DIAM_API diam_status diam_flush(diam_ctx* ctx);
 
 /* Synchronisation point of Sec. 2.3.1 (eq. (mom2g), (mom1g)). With the pooled reading used here the
  * local moments already are the global ones; this call merges moments exported by other samplers (other
@@ -267,7 +274,8 @@ DIAM_API void diam_multi_destroy(diam_multi* m);
  * retries), 7 re-whitening solve after a factor change, 8 surrogate screening (stage 1), 9 surrogate
  * training, 10 the whole step in one launch (propose + map + test + record, BF16 mode with the map carried
  * through the proposal and no surrogate screen in force; phases 2-4 then stay empty).
- * counts and ms hold DIAM_N_PHASES entries each.
+ * counts and ms hold DIAM_N_PHASES entries each. A refresh factorised beside the next interval (refresh_delay
+ * >= 1) is timed on its own stream whether or not cfg.profile is set, and counted in phase 6.
  * reset = 1 clears the accumulators after reading. Synchronises. */
 #define DIAM_N_PHASES 11
 DIAM_API diam_status diam_get_profile(diam_ctx* ctx, int64_t* counts, double* ms, int32_t reset);

@@ -62,7 +62,7 @@ class DiamStats(C.Structure):
                 ("chol_attempts", C.c_int64)]
 
 
-EXPORTS = ["diam_config_default", "diam_init", "diam_run_batch", "diam_sync_moments", "diam_get_moments",
+EXPORTS = ["diam_config_default", "diam_init", "diam_run_batch", "diam_flush", "diam_sync_moments", "diam_get_moments",
            "diam_export_moments", "diam_get_state", "diam_get_factor", "diam_get_trace", "diam_get_block_sums",
            "diam_save", "diam_load", "diam_get_profile", "diam_destroy", "diam_last_error", "diam_status_string"]
 PHASES = ["noise", "xi_gemm", "propose", "target", "accept", "fold", "refresh", "rewhiten", "screen", "train", "step"]
@@ -89,6 +89,7 @@ def lib():
                 "diam_config_default": (C.c_int, [P, I32, I32]),
                 "diam_init": (C.c_int, [P, P, P, P, P, P, P]),
                 "diam_run_batch": (C.c_int, [P, I64]),
+                "diam_flush": (C.c_int, [P]),
                 "diam_sync_moments": (C.c_int, [P, P, P, I64]),
                 "diam_get_moments": (C.c_int, [P, P, P, P]),
                 "diam_export_moments": (C.c_int, [P, P, P, P]),
@@ -315,6 +316,10 @@ class Sampler:
 
     def run(self, n_steps: int):
         self._check(self._l.diam_run_batch(self._h, int(n_steps)), "diam_run_batch")
+
+    def flush(self):
+        """Wait for a refresh still running beside the chains (refresh_delay >= 1) and apply its outcome."""
+        self._check(self._l.diam_flush(self._h), "diam_flush")
 
     def moments(self):
         m = np.zeros(self.d)

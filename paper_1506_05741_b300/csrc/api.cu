@@ -59,7 +59,18 @@ struct diam_ctx {
     struct Captured {
         cudaGraphExec_t exec = nullptr;
         unsigned long long launches = 0;
-    } chol_graph, trsm_graph;
+    } chol_graph, trsm_graph, chol_graph_r;
+    // refresh beside the next interval (BF16 mode, graphs, refresh_delay >= 1): the factorisation of interval
+    // k's C_n runs on its own stream and workspaces while interval k + 1 steps; resolved at k + 1's end
+    cudaStream_t rs = nullptr;
+    cudaEvent_t rs_fork = nullptr, rs_start = nullptr, rs_done = nullptr;   // start / done: timed
+    OzakiWs ozr;
+    double *Cr = nullptr, *M2s = nullptr;   // its matrix; the moments it was built from (for retries)
+    struct {
+        bool active = false;
+        int64_t blk = 0, n = 0;
+        double eps = 0;
+    } rf;
     std::string err;
     bool bad = false;
     diam_logpi_fn fn = nullptr;
@@ -636,13 +647,14 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
 // Replay of a captured launch sequence (captured on first use, on the context's stream, with the work it
 // forks onto other streams joined back); the library's launch counter counts the kernels of every replay.
 template <typename F>
-static diam_status run_captured(diam_ctx* c, diam_ctx::Captured& g, F body) {
+static diam_status run_captured(diam_ctx* c, diam_ctx::Captured& g, F body, cudaStream_t st = nullptr) {
+    if (!st) st = c->st;
     if (!g.exec) {
         cudaGraph_t gr = nullptr;
         const unsigned long long l0 = g_launches.load();
-        CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         cudaError_t eb = body();
-        cudaError_t e = cudaStreamEndCapture(c->st, &gr);
+        cudaError_t e = cudaStreamEndCapture(st, &gr);
         if (eb != cudaSuccess || e != cudaSuccess) {
             if (gr) cudaGraphDestroy(gr);
             return fail(c, DIAM_ECUDA, "graph capture", cudaGetErrorString(eb != cudaSuccess ? eb : e));
@@ -653,7 +665,7 @@ static diam_status run_captured(diam_ctx* c, diam_ctx::Captured& g, F body) {
         g.launches = g_launches.load() - l0;
         g_launches.fetch_sub(g.launches);
     }
-    CK(cudaGraphLaunch(g.exec, c->st));
+    CK(cudaGraphLaunch(g.exec, st));
     g_launches.fetch_add(g.launches);
     return DIAM_OK;
 }
@@ -701,6 +713,81 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
     return DIAM_OK;
 }
 
+// The refresh of interval blk beside interval blk + 1 (its factor is due at interval blk + 1 + delay >= blk + 2):
+// C_n with the first jitter built and the moments kept on the context's stream, then the factorisation, on
+// the refresh stream with its own workspaces, into pending slot blk. refresh_finish resolves it.
+static bool refresh_async_ok(const diam_ctx* c) {
+    return c->bf && c->cfg.graphs && !c->cfg.profile && c->cfg.refresh_delay >= 1 && c->rs && c->Cr;
+}
+
+static diam_status refresh_launch(diam_ctx* c, int64_t blk) {
+    const int d = c->d;
+    double eps = c->cfg.eps_jitter;
+    if (eps < 1e-4) eps = 1e-4;   // the BF16-mode floor of the refresh rule
+    { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, 1.0 / (double)c->n, eps, c->Cr); count_launch(); }
+    CK(cudaMemcpyAsync(c->M2s, c->M2, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
+    Pending& pd = c->pend[(size_t)(blk % (int64_t)c->pend.size())];
+    CK(cudaMemcpyAsync(pd.mean, c->mean, sizeof(double) * d, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
+    CK(cudaEventRecord(c->rs_fork, c->st));
+    CK(cudaStreamWaitEvent(c->rs, c->rs_fork, 0));
+    CK(cudaEventRecord(c->rs_start, c->rs));
+    auto body = [&]() { return cholesky_f64(c->Cr, d, d, &c->ctl->chol_info, c->rs, &c->ozr, &c->ctl->status); };
+    if (c->ozr.hi) {   // after a first eager factorisation (which creates the workspace's streams)
+        CKS(run_captured(c, c->chol_graph_r, body, c->rs));
+    } else {
+        CK(body());
+    }
+    CK(cudaMemcpyAsync(pd.L, c->Cr, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->rs));
+    CK(cudaEventRecord(c->rs_done, c->rs));
+    c->rf.active = true;
+    c->rf.blk = blk;
+    c->rf.n = c->n;
+    c->rf.eps = eps;
+    return DIAM_OK;
+}
+
+// Wait for the refresh in flight and apply the refresh rule's outcome: its pending factor, or the retries
+// with a larger jitter (from the kept moments, in order on the context's stream), or the skip.
+static diam_status refresh_finish(diam_ctx* c) {
+    if (!c->rf.active) return DIAM_OK;
+    c->rf.active = false;
+    const int d = c->d;
+    CK(cudaStreamWaitEvent(c->st, c->rs_done, 0));   // later work on the stream is ordered after it
+    CK(cudaEventSynchronize(c->rs_done));
+    CKS(sync_and_check(c));
+    float ms = 0.f;   // its device time beside the interval, in the refresh phase's accumulators
+    if (cudaEventElapsedTime(&ms, c->rs_start, c->rs_done) == cudaSuccess) {
+        c->prof_ms[PH_REFRESH] += ms;
+        c->prof_cnt[PH_REFRESH] += 1;
+    }
+    int info = 0;
+    CK(d2h(c, &info, &c->ctl->chol_info, sizeof(int)));
+    c->chol_attempts++;
+    Pending& pd = c->pend[(size_t)(c->rf.blk % (int64_t)c->pend.size())];
+    bool ok = info == 0;
+    double eps = c->rf.eps * 100.0;
+    for (int attempt = 1; attempt < 4 && !ok; ++attempt) {
+        { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2s, d, 1.0 / (double)c->rf.n, eps, c->Cr); count_launch(); }
+        CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
+        CK(cholesky_f64(c->Cr, d, d, &c->ctl->chol_info, c->st, &c->oz, &c->ctl->status));
+        CKS(sync_and_check(c));
+        CK(d2h(c, &info, &c->ctl->chol_info, sizeof(int)));
+        ok = info == 0;
+        eps *= 100.0;
+        c->chol_attempts++;
+        if (ok) CK(cudaMemcpyAsync(pd.L, c->Cr, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
+    }
+    if (!ok) {
+        c->notspd++;
+        c->err = "refresh skipped: C_n + jitter not positive definite (previous factor kept)";
+        return DIAM_OK;
+    }
+    pd.block = c->rf.blk + 1 + c->cfg.refresh_delay;
+    c->refreshes++;
+    return DIAM_OK;
+}
+
 static void push_scalars(diam_ctx* c) {
     double rho = std::sqrt(1.0 - c->beta * c->beta);
     { set_scalars_kernel<<<1, 1, 0, c->st>>>(c->ctl, c->beta, rho, c->beta * c->cfg.infl, inv_infl2(c)); count_launch(); }
@@ -725,7 +812,11 @@ static diam_status block_end(diam_ctx* c, int64_t blk) {
         if (c->beta > g.beta_max) c->beta = g.beta_max;
     }
     if ((blk + 1) * (int64_t)c->nl > g.burnin) c->acc_refresh += (int64_t)acc;
-    if (c->acc_refresh >= g.min_samples_refresh && c->n > 0) CKS(refresh(c, blk));
+    CKS(refresh_finish(c));
+    if (c->acc_refresh >= g.min_samples_refresh && c->n > 0) {
+        if (refresh_async_ok(c)) CKS(refresh_launch(c, blk));
+        else CKS(refresh(c, blk));
+    }
     push_scalars(c);
     CK(cudaGetLastError());
     if (c->da) CKS(da_after_interval(c));
@@ -914,6 +1005,18 @@ static diam_status alloc_all(diam_ctx* c) {
         c->oz.capP = ozaki_panel_rows(d);
         CKS(dalloc(c, &c->oz.SLP, sizeof(uint16_t) * (size_t)std::max<int64_t>(1, c->oz.capP) * 448));
         CKS(dalloc(c, &c->oz.exP, sizeof(int) * (size_t)std::max<int64_t>(1, c->oz.capP)));
+        if (c->cfg.refresh_delay >= 1 && c->cfg.graphs) {   // the refresh beside the next interval
+            CKS(dalloc(c, &c->Cr, sizeof(double) * d * d));
+            CKS(dalloc(c, &c->M2s, sizeof(double) * d * d));
+            CKS(dalloc(c, &c->ozr.SL, ozaki_sl_bytes(d)));
+            CKS(dalloc(c, &c->ozr.ex, ozaki_ex_bytes(d)));
+            c->ozr.cap_rows = d;
+            c->ozr.lo_high = true;   // ahead of the interval's work: the chain waits on these updates
+            CK(cudaStreamCreateWithFlags(&c->rs, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&c->rs_fork, cudaEventDisableTiming));
+            CK(cudaEventCreate(&c->rs_start));
+            CK(cudaEventCreate(&c->rs_done));
+        }
         CKS(dalloc(c, &c->Lq64, sizeof(double) * d * d));
         CKS(dalloc(c, &c->Lq16, sizeof(uint16_t) * (size_t)d * c->ldk));
         CKS(dalloc(c, &c->op_hi, sizeof(uint16_t) * (size_t)P * c->ldk));
@@ -1123,6 +1226,12 @@ __global__ void merge_mean_kernel(int d, double* mean, const double* extm, doubl
     mean[i] += dl * frac;
 }
 
+diam_status diam_flush(diam_ctx* c) {
+    CKS(check_usable(c));
+    CKS(refresh_finish(c));
+    return sync_and_check(c);
+}
+
 diam_status diam_sync_moments(diam_ctx* c, const double* ext_mean, const double* ext_M2, int64_t ext_n) {
     CKS(check_usable(c));
     if (ext_n < 0 || (ext_n > 0 && (!ext_mean || !ext_M2))) return fail(c, DIAM_EINVAL, "diam_sync_moments");
@@ -1167,6 +1276,7 @@ diam_status diam_export_moments(diam_ctx* c, double* mean, double* M2, int64_t* 
 diam_status diam_get_state(diam_ctx* c, double* x, double* lp, diam_stats* stats) {
     CKS(check_usable(c));
     CKS(sync_and_check(c));
+    CKS(refresh_finish(c));   // the refresh in flight counts (and its factor is saved) as in order
     const size_t Pd = (size_t)c->P * c->d;
     if (x) {
         if (c->bf) {
@@ -1277,6 +1387,7 @@ diam_status diam_save(diam_ctx* c, void* buf, size_t* size) {
     CKS(check_usable(c));
     if (!size) return fail(c, DIAM_EINVAL, "diam_save");
     CKS(sync_and_check(c));
+    CKS(refresh_finish(c));   // the refresh in flight counts (and its factor is saved) as in order
     auto bufs = state_buffers(c);
     size_t total = sizeof(HostState);
     for (auto& b : bufs) total += b.second;
@@ -1307,6 +1418,7 @@ diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
     HostState hs;
     memcpy(&hs, buf, sizeof(hs));
     CKS(sync_and_check(c));
+    CKS(refresh_finish(c));   // nothing may still write the pending factors
     if (hs.bcap > c->bcap) {  // grow the interval-sum store to the saved capacity
         void* nb = nullptr;
         double* nlp = nullptr;
@@ -1485,6 +1597,7 @@ diam_status diam_da_grad(diam_ctx* c, int32_t B, const double* U, const double* 
 void diam_destroy(diam_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
+    if (c->rs) cudaStreamSynchronize(c->rs);   // a refresh still in flight
     if (c->st) cudaStreamSynchronize(c->st);
     for (auto& e : c->evts) {
         cudaEventDestroy(e.a);
@@ -1493,7 +1606,9 @@ void diam_destroy(diam_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->chol_graph.exec) cudaGraphExecDestroy(c->chol_graph.exec);
     if (c->trsm_graph.exec) cudaGraphExecDestroy(c->trsm_graph.exec);
+    if (c->chol_graph_r.exec) cudaGraphExecDestroy(c->chol_graph_r.exec);
     ozaki_ws_release(c->oz);
+    ozaki_ws_release(c->ozr);
     for (void* p : c->allocs) cudaFree(p);
     if (c->side) {
         cudaStreamSynchronize(c->side);
@@ -1501,6 +1616,10 @@ void diam_destroy(diam_ctx* c) {
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->rs) cudaStreamDestroy(c->rs);
+    if (c->rs_fork) cudaEventDestroy(c->rs_fork);
+    if (c->rs_done) cudaEventDestroy(c->rs_done);
+    if (c->rs_start) cudaEventDestroy(c->rs_start);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c->da;
     delete c;

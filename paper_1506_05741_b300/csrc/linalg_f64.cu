@@ -221,7 +221,8 @@ static cudaError_t ensure_streams(OzakiWs& ws) {
     int lo_pri = 0, hi_pri = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ws.hi, cudaStreamNonBlocking, hi_pri);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ws.lo, cudaStreamNonBlocking, lo_pri);
+    const int lo_use = ws.lo_high ? (hi_pri < lo_pri ? hi_pri + 1 : hi_pri) : lo_pri;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ws.lo, cudaStreamNonBlocking, lo_use);
     for (cudaEvent_t* ev : {&ws.ev_in, &ws.ev_slice, &ws.ev_rest, &ws.ev_lo})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) ozaki_ws_release(ws);

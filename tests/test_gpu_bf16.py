@@ -110,6 +110,52 @@ def test_bf16_refresh_and_moments_track_oracle():
     assert np.max(np.abs(cg - co)) <= 2e-2 * np.max(np.abs(co))
 
 
+def test_refresh_delay_applies_the_factor_where_the_oracle_does():
+    """refresh_delay = 1 in BF16 mode (graphs on, so each factorisation runs on its own stream beside the next
+    interval). The factor built from interval 0's moments drives the chains from interval 2 on: up to there
+    decisions and log-densities follow the oracle, and both re-whiten exactly at step 2 n_lag (q of the
+    current states stops being carried from the accepted proposals). Past that step the two factors come from
+    differently rounded moments (BF16 records with FP32 accumulation against FP64), so the trajectories are
+    not compared further."""
+    ts, P, nl = workloads.tanh_regression(256, 128, 37), 8, 16
+    steps = 3 * nl
+    x0 = workloads.start_state(256, P, 5) * np.sqrt(ts.lam)
+    g, o = _bf16_pair(ts, P, steps, n_lag=nl, beta0=0.3, seed=21, min_samples_refresh=30, refresh_delay=1,
+                      x0=x0, C0=np.diag(ts.lam))
+    g.run(steps)
+    o.run(steps)
+    tg, to = g.trace(steps), o.trace()
+    k = 2 * nl
+    assert np.array_equal(tg["acc"][:k], to["acc"][:k])
+    sc = trace_scale(to)[:k]
+    for key in ("lp_prop", "q_prop", "q_cur", "loga"):
+        assert rel_err(tg[key][:k], to[key][:k], sc) <= TOL, (key, rel_err(tg[key][:k], to[key][:k], sc))
+    for tr in (tg, to):
+        carried = np.where(tr["acc"], tr["q_prop"], tr["q_cur"])   # q of each step's outcome
+        assert np.array_equal(tr["q_cur"][1:k], carried[:k - 1])   # no factor change before step 2 n_lag
+        assert np.all(np.abs(tr["q_cur"][k] - carried[k - 1]) > 1e-6 * np.abs(carried[k - 1]))   # re-whitened
+    assert g.stats()["refreshes"] == o.counts()["refreshes"] == 3
+
+
+def test_refresh_beside_the_next_interval_equals_refresh_in_order():
+    """The overlapped refresh (graphs on) and the in-order one (graphs off) give bit-identical chains."""
+    import paper_1506_05741_b300 as dm
+    ts, P = workloads.tanh_regression(192, 64, 38), 6
+    out = []
+    for graphs in (0, 1):
+        cfg = dm.default_config(192, P, n_lag=8, beta0=0.3, seed=6, prec=dm.BF16, graphs=graphs,
+                                min_samples_refresh=20, refresh_delay=1)
+        s = dm.Sampler(cfg, ts, x0=workloads.start_state(192, P, 2) * np.sqrt(ts.lam), C0=np.diag(ts.lam))
+        s.run(8 * 12 + 3)
+        out.append((s.state(), s.moments(), s.stats()["refreshes"]))
+        s.close()
+    (xa, la, sa), (ma, ca, na), ra = out[0]
+    (xb, lb, sb), (mb, cb, nb), rb = out[1]
+    assert np.array_equal(xa, xb) and np.array_equal(la, lb) and sa == sb
+    assert np.array_equal(ma, mb) and np.array_equal(ca, cb) and na == nb
+    assert ra == rb >= 8
+
+
 def test_bf16_reference_gaussian_accepts_almost_every_proposal():
     d, P = 256, 8
     import paper_1506_05741_b300 as dm
