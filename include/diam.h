@@ -182,7 +182,9 @@ DIAM_API diam_status diam_get_trace(diam_ctx* ctx, double* lp_prop, double* q_pr
                            int8_t* acc, int64_t n_steps);
 
 /* Per-interval, per-chain sums (needs keep_block_sums): xsum (n_blocks x P x d), lpsum (n_blocks x P).
- * *n_blocks is the capacity on input and the count on output. Synchronises. */
+ * *n_blocks is the capacity on input and the count on output: in FP64 mode every interval begun (the
+ * current one partial), in BF16 mode the completed intervals (their x sums are formed from the interval's
+ * records when it completes). Synchronises. */
 DIAM_API diam_status diam_get_block_sums(diam_ctx* ctx, double* xsum, double* lpsum, int64_t* n_blocks);
 
 /* Checkpoint: the full sampler state (chains, factor, moments, beta, counters, pending factors). Philox

@@ -463,7 +463,7 @@ static void launch_fused_step(diam_ctx* c) {
         c->d, c->P, c->nl, c->dy, c->ctl, c->key, c->tg, inv_infl2(c), (float*)c->X, (float*)c->Z,
         (const float*)c->Xi, (const uint16_t*)c->W, c->ldw, (const float*)c->xref, (const float*)c->cenT, c->Ax,
         c->axref, c->AXi, c->y32, (float)(1.0 / (2.0 * c->sigma * c->sigma)), c->kind == TK_TANH, c->lp, c->q,
-        c->accf, c->tr, (float*)c->hist, c->ldh, keep ? (float*)c->bsum : nullptr, keep ? c->lpsum : nullptr,
+        c->accf, c->tr, (float*)c->hist, c->ldh, nullptr, keep ? c->lpsum : nullptr,
         a ? a->cnt : nullptr, a ? a->ring_x : nullptr, a ? a->ring_lp : nullptr, a ? (long long)a->cfg.ring : 1,
         c->ldk);
     count_launch();
@@ -568,7 +568,7 @@ static diam_status do_step(diam_ctx* c) {
     CK(cudaGetLastError());
     ph_end(c, e1);
     int e2 = ph_begin(c, PH_ACCEPT);
-    void* bs = c->cfg.keep_block_sums ? c->bsum : nullptr;
+    void* bs = (c->cfg.keep_block_sums && !BF) ? c->bsum : nullptr;   // BF16 mode: formed in the fold
     double* ls = c->cfg.keep_block_sums ? c->lpsum : nullptr;
     // the select kernel also copies A x* for accepted chains (carried map), moves the surrogate's ring head
     // past this step's pairs and, in its last block, the step counters
@@ -597,20 +597,30 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
     int64_t tstart = blk * nl;
     int64_t s0 = std::max<int64_t>(0, std::min<int64_t>(nl, c->cfg.burnin - tstart));
     int64_t rows = (nl - s0) * P;
-    if (rows <= 0) return DIAM_OK;
+    constexpr bool BF = std::is_same<T, float>::value;
+    // BF16 mode: the per-chain interval sums of x come from the records (in the fold's pass over them)
+    float* xs = (BF && c->cfg.keep_block_sums) ? (float*)c->bsum + (size_t)blk * P * d : nullptr;
+    const int npb = (P + 31) / 32;
+    if (rows <= 0) {
+        if (xs) { fold_records_kernel<<<dim3((d + 31) / 32, npb), dim3(32, 8), 0, c->st>>>((const float*)c->hist, c->ldh, P, nl, nl, d,
+                                                                                     (const float*)c->cenT, nullptr, 0, nullptr,
+                                                                                     nullptr, xs); count_launch(); }
+        return DIAM_OK;
+    }
     double nb = (double)rows;
     int R = (int)std::min<int64_t>(64, rows);
     int e0 = ph_begin(c, PH_FOLD);
-    constexpr bool BF = std::is_same<T, float>::value;
     if constexpr (BF) {
         // samples as the K index: one pass over the interval's FP32 records writes their BF16 transpose
-        // (d x rows, K-contiguous) and the per-tile sums of the records and of their BF16 values; the totals give
-        // the centring terms (the interval mean from the FP32 records, not rounded to BF16) and s16 for the
-        // lower-triangle SYRK on the tensor cores, whose epilogue does the FP64 fold
-        const int ldt = ((int)rows + 63) / 64 * 64, ntile = ldt / 32;
-        const float* H = (const float*)c->hist + (size_t)s0 * P * c->ldh;
-        { fold_transpose_kernel<<<dim3((d + 31) / 32, ntile), dim3(32, 8), 0, c->st>>>(H, c->ldh, (int)rows, d, c->histT, ldt,
-                                                                                    c->psum, c->psum + (size_t)ntile * d); count_launch(); }
+        // (d x rows, K-contiguous), the per-tile sums of the records and of their BF16 values (the totals give
+        // the centring terms, the interval mean from the FP32 records, and s16 for the lower-triangle SYRK on
+        // the tensor cores, whose epilogue does the FP64 fold) and the per-chain interval sums
+        const int ldt = ((int)rows + 63) / 64 * 64, ntile = (int)(nl - s0) * npb;
+        { fold_records_kernel<<<dim3((d + 31) / 32, npb), dim3(32, 8), 0, c->st>>>((const float*)c->hist, c->ldh, P, nl, (int)s0, d,
+                                                                                (const float*)c->cenT, c->histT, ldt, c->psum,
+                                                                                c->psum + (size_t)ntile * d, xs); count_launch(); }
+        if (ldt > rows)   // the K padding of the SYRK operand
+            CK(cudaMemset2DAsync(c->histT + rows, sizeof(uint16_t) * ldt, 0, sizeof(uint16_t) * (ldt - rows), d, c->st));
         { fold_sums_kernel<<<(d + 31) / 32, kThreads, 0, c->st>>>(d, ntile, c->psum, c->psum + (size_t)ntile * d, c->cen64,
                                                                 c->mean, 1.0 / nb, c->svec, c->delta, c->s16); count_launch(); }
     } else {
@@ -1026,7 +1036,8 @@ static diam_status alloc_all(diam_ctx* c) {
         CKS(dalloc(c, &c->W, sizeof(uint16_t) * rows * c->ldw));
         CKS(dalloc(c, &c->hist, sizeof(float) * rows * c->ldh));
         CKS(dalloc(c, &c->histT, sizeof(uint16_t) * (size_t)d * ((rows + 63) / 64 * 64)));
-        CKS(dalloc(c, &c->psum, sizeof(float) * 2 * (size_t)d * (((rows + 63) / 64 * 64) / 32)));
+        // the fold's tile sums: one per (step, 32-chain block)
+        CKS(dalloc(c, &c->psum, sizeof(float) * 2 * (size_t)d * ((size_t)nl * ((P + 31) / 32))));
         if (c->kind == TK_TANH || c->kind == TK_DENSE) {
             c->rec = true;
             const size_t dy = (size_t)std::max(c->dy, 1);
@@ -1334,7 +1345,9 @@ diam_status diam_get_block_sums(diam_ctx* c, double* xsum, double* lpsum, int64_
     CKS(check_usable(c));
     if (!n_blocks) return fail(c, DIAM_EINVAL, "diam_get_block_sums");
     CKS(sync_and_check(c));
-    int64_t nb = std::min<int64_t>(*n_blocks, std::min<int64_t>(c->bcap, (c->t + c->nl - 1) / c->nl));
+    // BF16 mode forms an interval's sums when the interval completes (FP64 mode: step by step)
+    const int64_t have = c->bf ? c->t / c->nl : (c->t + c->nl - 1) / c->nl;
+    int64_t nb = std::min<int64_t>(*n_blocks, std::min<int64_t>(c->bcap, have));
     if (!c->cfg.keep_block_sums) nb = 0;
     if (nb > 0) {
         const size_t n = (size_t)nb * c->P * c->d;

@@ -725,41 +725,75 @@ __global__ void fold_prep_kernel(int d, int nparts, const double* __restrict__ p
     delta[i] = (cen64[i] + v * inb) - mean[i];
 }
 
-// The interval's FP32 records (rows samples x d coordinates, stride ldh) in one pass: their BF16 transpose
-// (d x ldt, K-contiguous, zero past the last sample: the SYRK operand) and, per 32-sample tile and
-// coordinate, the FP32 sums of the records and of their BF16-rounded values (psum, pbf: ntile x d).
-__global__ void __launch_bounds__(256) fold_transpose_kernel(const float* __restrict__ H, int ldh, int rows, int d,
-                                                             uint16_t* __restrict__ HT_, int ldt,
-                                                             float* __restrict__ psum, float* __restrict__ pbf) {
+// The interval's FP32 records (row s P + p: step s < n_lag, chain p < P; stride ldh), read once by blocks of
+// 32 chains x 32 coordinates that walk the interval's steps (the next step's records loaded ahead):
+//   - rows of the steps s >= s0 (past the burn-in): their BF16 transpose HT[c][(s - s0) P + p] (the SYRK
+//     operand) and, per (step, chain block) tile, the FP32 sums of the records and of their BF16 values
+//     (psum, pbf: tile (s - s0) gridDim.y + blockIdx.y, d entries each); HT == nullptr skips this part;
+//   - xs != nullptr: every chain's sum over all n_lag steps, xs[p][c] = sum_s H + n_lag cen[c] (the records
+//     are x - cen), the per-interval, per-chain sums of x.
+__global__ void __launch_bounds__(256) fold_records_kernel(const float* __restrict__ H, int ldh, int P, int nl, int s0,
+                                                           int d, const float* __restrict__ cen,
+                                                           uint16_t* __restrict__ HT, int ldt, float* __restrict__ psum,
+                                                           float* __restrict__ pbf, float* __restrict__ xs) {
     __shared__ uint16_t tile[32][33];
     __shared__ float sx[8][33], sb[8][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int c0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    float ax = 0.f, ab = 0.f;
-    for (int k = ty; k < 32; k += 8) {
-        const int r = r0 + k, c = c0 + tx;
-        const float v = (r < rows && c < d) ? H[(size_t)r * ldh + c] : 0.f;
-        const uint16_t b = f32_to_bf16_bits(v);
-        tile[k][tx] = b;
-        ax += v;
-        ab += bf16_bits_to_f32(b);
-    }
-    sx[ty][tx] = ax;
-    sb[ty][tx] = ab;
-    __syncthreads();
-    if (ty == 0 && c0 + tx < d) {
-        float tx_sum = 0.f, tb_sum = 0.f;
+    const int c = c0 + tx;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, cur[4], nxt[4];
+    auto load = [&](int st, float* v) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            tx_sum += sx[k][tx];
-            tb_sum += sb[k][tx];
+        for (int k = 0; k < 4; ++k) {
+            const int p = p0 + ty + 8 * k;
+            v[k] = (p < P && c < d) ? H[((size_t)st * P + p) * ldh + c] : 0.f;
         }
-        psum[(size_t)blockIdx.y * d + c0 + tx] = tx_sum;
-        pbf[(size_t)blockIdx.y * d + c0 + tx] = tb_sum;
+    };
+    load(0, cur);
+    for (int st = 0; st < nl; ++st) {
+        if (st + 1 < nl) load(st + 1, nxt);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += cur[k];
+        if (HT && st >= s0) {
+            float ax = 0.f, ab = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint16_t b = f32_to_bf16_bits(cur[k]);
+                tile[ty + 8 * k][tx] = b;
+                ax += cur[k];
+                ab += bf16_bits_to_f32(b);
+            }
+            sx[ty][tx] = ax;
+            sb[ty][tx] = ab;
+            __syncthreads();
+            if (ty == 0 && c < d) {
+                float tsx = 0.f, tsb = 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    tsx += sx[k][tx];
+                    tsb += sb[k][tx];
+                }
+                const size_t tl = (size_t)(st - s0) * gridDim.y + blockIdx.y;
+                psum[tl * d + c] = tsx;
+                pbf[tl * d + c] = tsb;
+            }
+            const size_t r0 = (size_t)(st - s0) * P + p0;
+            for (int k = ty; k < 32; k += 8) {
+                const int cc = c0 + k;
+                if (cc < d && p0 + tx < P) HT[(size_t)cc * ldt + r0 + tx] = tile[tx][k];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
     }
-    for (int k = ty; k < 32; k += 8) {
-        const int c = c0 + k, r = r0 + tx;
-        if (c < d && r < ldt) HT_[(size_t)c * ldt + r] = tile[tx][k];
+    if (xs && c < d) {
+        const float cn = (float)nl * cen[c];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int p = p0 + ty + 8 * k;
+            if (p < P) xs[(size_t)p * d + c] = acc[k] + cn;
+        }
     }
 }
 

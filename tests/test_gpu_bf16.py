@@ -156,6 +156,29 @@ def test_refresh_beside_the_next_interval_equals_refresh_in_order():
     assert ra == rb >= 8
 
 
+def test_bf16_interval_sums_equal_the_states_summed():
+    """BF16 mode forms each interval's per-chain sums of x from the interval's records in the fold's pass
+    (blocks of 32 chains: P = 40 leaves a partial block); they equal the states read back after every step
+    and summed on the host, FP32-close, for intervals inside, across and past the burn-in."""
+    import paper_1506_05741_b300 as dm
+    d, P, nl = 96, 40, 8
+    ts = workloads.tanh_regression(d, 48, 39)
+    cfg = dm.default_config(d, P, n_lag=nl, beta0=0.4, seed=8, prec=dm.BF16, burnin=nl + 3, min_samples_refresh=30)
+    cfg["keep_block_sums"] = 1
+    s = dm.Sampler(cfg, ts, x0=workloads.start_state(d, P, 3) * np.sqrt(ts.lam), C0=np.diag(ts.lam))
+    want = np.zeros((4, P, d))
+    for t in range(4 * nl):
+        s.run(1)
+        x, _, _ = s.state()
+        want[t // nl] += x
+    s.run(3)   # a partial interval is not reported
+    xs, _ = s.block_sums(10)
+    assert xs.shape[0] == 4
+    scale = np.abs(want).max()
+    assert np.max(np.abs(xs - want)) <= 1e-5 * scale
+    s.close()
+
+
 def test_bf16_reference_gaussian_accepts_almost_every_proposal():
     d, P = 256, 8
     import paper_1506_05741_b300 as dm
