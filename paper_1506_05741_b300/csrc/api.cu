@@ -455,11 +455,18 @@ static bool fused_step_fits(const diam_ctx* c) {
            c->dy <= 4 * 8 * FUSED_THREADS;
 }
 
-template <int NV, int NM, bool VEC>
-static void launch_fused_step(diam_ctx* c) {
+template <int NV, int NM, bool VEC, bool STAGE>
+static void launch_fused_step(diam_ctx* c, bool setup) {
     DaState* a = c->da;
     const bool keep = c->cfg.keep_block_sums != 0;
-    step_rec_kernel<NV, NM, VEC><<<c->P, FUSED_THREADS, 0, c->st>>>(
+    const size_t smem = STAGE ? sizeof(float) * 3 * (size_t)c->d : 0;
+    if (setup) {   // outside any capture: the staged rows may take all 48 KB of dynamic shared memory
+        if (STAGE)
+            cudaFuncSetAttribute(step_rec_kernel<NV, NM, VEC, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 48 * 1024);
+        return;
+    }
+    step_rec_kernel<NV, NM, VEC, STAGE><<<c->P, FUSED_THREADS, smem, c->st>>>(
         c->d, c->P, c->nl, c->dy, c->ctl, c->key, c->tg, inv_infl2(c), (float*)c->X, (float*)c->Z,
         (const float*)c->Xi, (const uint16_t*)c->W, c->ldw, (const float*)c->xref, (const float*)c->cenT, c->Ax,
         c->axref, c->AXi, c->y32, (float)(1.0 / (2.0 * c->sigma * c->sigma)), c->kind == TK_TANH, c->lp, c->q,
@@ -469,28 +476,32 @@ static void launch_fused_step(diam_ctx* c) {
     count_launch();
 }
 
-template <int NV, bool VEC>
-static void fused_step_nm(diam_ctx* c) {
+template <int NV, bool VEC, bool STAGE>
+static void fused_step_nm(diam_ctx* c, bool setup) {
     const int nm = (c->dy + 4 * FUSED_THREADS - 1) / (4 * FUSED_THREADS);
-    if (nm <= 1) launch_fused_step<NV, 1, VEC>(c);
-    else if (nm <= 2) launch_fused_step<NV, 2, VEC>(c);
-    else if (nm <= 4) launch_fused_step<NV, 4, VEC>(c);
-    else launch_fused_step<NV, 8, VEC>(c);
+    if (nm <= 1) launch_fused_step<NV, 1, VEC, STAGE>(c, setup);
+    else if (nm <= 2) launch_fused_step<NV, 2, VEC, STAGE>(c, setup);
+    else if (nm <= 4) launch_fused_step<NV, 4, VEC, STAGE>(c, setup);
+    else launch_fused_step<NV, 8, VEC, STAGE>(c, setup);
 }
 
-template <bool VEC>
-static void fused_step_nv(diam_ctx* c) {
+template <bool VEC, bool STAGE>
+static void fused_step_nv(diam_ctx* c, bool setup) {
     const int nv = (c->d + 4 * FUSED_THREADS - 1) / (4 * FUSED_THREADS);
-    if (nv <= 1) fused_step_nm<1, VEC>(c);
-    else if (nv <= 2) fused_step_nm<2, VEC>(c);
-    else if (nv <= 4) fused_step_nm<4, VEC>(c);
-    else fused_step_nm<8, VEC>(c);
+    if (nv <= 1) fused_step_nm<1, VEC, STAGE>(c, setup);
+    else if (nv <= 2) fused_step_nm<2, VEC, STAGE>(c, setup);
+    else if (nv <= 4) fused_step_nm<4, VEC, STAGE>(c, setup);
+    else if (!STAGE) fused_step_nm<8, VEC, false>(c, setup);
 }
 
-static diam_status fused_step(diam_ctx* c) {
+// setup: only prepare the kernel this context will launch (at init, outside any graph capture).
+static diam_status fused_step(diam_ctx* c, bool setup = false) {
     const bool vec = (c->d % 4) == 0 && (c->dy % 4) == 0 && (c->ldw % 4) == 0 && (c->ldh % 4) == 0 && (c->ldk % 4) == 0;
-    if (vec) fused_step_nv<true>(c);
-    else fused_step_nv<false>(c);
+    // the chain's x, z, xi rows staged by bulk copies while they fit the default 48 KB of dynamic shared memory
+    const bool stage = vec && (size_t)c->d * 12 <= 48 * 1024;
+    if (stage) fused_step_nv<true, true>(c, setup);
+    else if (vec) fused_step_nv<true, false>(c, setup);
+    else fused_step_nv<false, false>(c, setup);
     CK(cudaGetLastError());
     return DIAM_OK;
 }
@@ -1207,6 +1218,7 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
         return DIAM_ECUDA;
     }
     diam_status s = alloc_all(c);
+    if (s == DIAM_OK && c->bf && c->rec) s = fused_step(c, true);
     if (s == DIAM_OK) s = upload_target(c, tg);
     if (s == DIAM_OK) s = c->bf ? init_state<float>(c, x0, C0, xref0) : init_state<double>(c, x0, C0, xref0);
     if (s != DIAM_OK) {

@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace diam {
 namespace {  // internal linkage: each translation unit that launches these gets its own copy
@@ -433,12 +434,16 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
 // row, the interval sums and, with a surrogate attached, the (bf16(x*), likelihood terms) training pair in
 // ring slot head + p. The last block to finish moves the step counters (and the ring head) on.
 // Only x* and u stay in registers across the test; the second pass reads x (rejected) or z and W (accepted,
-// z* recomputed by the same fused multiply-add) again, from L2. Sums are FP32, one tree per block.
+// z* recomputed by the same fused multiply-add) again, from L2 (or the staged rows). Sums are FP32, one tree
+// per block.
 // Element layout of thread tid: VEC (d, d_y multiples of 4): entries 4 (tid + g FT) + j of group g < NV (NM);
 // otherwise entries tid + (4 g + j) FT. So d <= 4 NV FT and d_y <= 4 NM FT.
+// STAGE (with VEC): the chain's x, z and xi rows (12 d bytes of dynamic shared memory) arrive by three bulk
+// copies issued at the start, so the whole row is requested at once; the map terms are computed while they
+// are in flight, and the second pass reads x or z from shared memory. The copy wait is clock-bounded.
 constexpr int FUSED_THREADS = 256;
 
-template <int NV, int NM, bool VEC>
+template <int NV, int NM, bool VEC, bool STAGE = false>
 __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     int d, int P, int nl, int dy, Ctl* ctl, Key key, TargetDev tg, double inv_infl2,
     float* __restrict__ X, float* __restrict__ Z, const float* __restrict__ Xi, const uint16_t* __restrict__ W, int ldw,
@@ -447,10 +452,14 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     int tanh_mode, double* lp, double* q, int8_t* accf, TraceDev tr, float* __restrict__ hist_base, int ldh,
     float* __restrict__ bsum_base, double* __restrict__ lpsum_base, DaCounters* dacnt, uint16_t* __restrict__ ring_x,
     float* __restrict__ ring_lp, long long ring_cap, int ldk) {
+    static_assert(!STAGE || VEC, "staging reads 16-byte vectors");
     constexpr int FT = FUSED_THREADS;
+    extern __shared__ float4 stage_smem[];   // STAGE: x, z, xi of the chain (d floats each)
     __shared__ float red[3][FT / 32];
-    __shared__ double s_lu, s_lpc, s_qc;
+    __shared__ double s_u, s_lpc, s_qc;
+    __shared__ float s_lu32;
     __shared__ int s_acc;
+    __shared__ uint64_t s_bar;
     const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const float rho = (float)ctl->rho, ba = (float)ctl->ba, om = (float)(1.0 - ctl->rho);
     const int s = ctl->s_cur;
@@ -460,52 +469,38 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     float* z = Z + (size_t)p * d;
     const float* xi = Xi + row * d;
     const uint16_t* w = W + row * ldw;
+    float* sx = reinterpret_cast<float*>(stage_smem);
+    float* sz = sx + d;
+    float* sxi = sz + d;
+    if (STAGE) {
+        if (tid == 0) {
+            mbar_init(smem_u32(&s_bar), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t bar = smem_u32(&s_bar), bytes = (uint32_t)d * 4u;
+            mbar_expect_tx(bar, 3u * bytes);
+            bulk_load_1d(smem_u32(sx), x, bytes, bar);
+            bulk_load_1d(smem_u32(sz), z, bytes, bar);
+            bulk_load_1d(smem_u32(sxi), xi, bytes, bar);
+        }
+    }
+    const float* xsrc = STAGE ? sx : x;
+    const float* zsrc = STAGE ? sz : z;
+    const float* isrc = STAGE ? sxi : xi;
     const bool prior = tg.kind == TK_TANH;   // the dense Gaussian's whole density is its map
     auto idx = [&](int g, int j) { return VEC ? 4 * (tid + g * FT) + j : tid + (4 * g + j) * FT; };
-    if (tid == FT - 32) {   // the test's other inputs, off the path of the sums: log u (FP64), log pi(x), q(x)
-        s_lu = log(uniform53(key, t, (uint32_t)p, TAG_U));
+    if (tid == FT - 32) {   // the test's other inputs, off the path of the sums: u, its FP32 log, log pi(x), q(x)
+        const double u = uniform53(key, t, (uint32_t)p, TAG_U);
+        s_u = u;
+        s_lu32 = logf((float)u);
         s_lpc = lp[p];
         s_qc = q[p];
     }
-
-    float xs[4 * NV];
     float qf = 0.f, lf = 0.f, mf = 0.f;
-#pragma unroll
-    for (int g = 0; g < NV; ++g) {
-        if (VEC) {
-            const int i = idx(g, 0);
-            if (i < d) {
-                const float4 xr = *reinterpret_cast<const float4*>(xref + i);
-                const float4 xa = *reinterpret_cast<const float4*>(x + i);
-                const float4 za = *reinterpret_cast<const float4*>(z + i);
-                const float4 ia = *reinterpret_cast<const float4*>(xi + i);
-                const uint2 wb = *reinterpret_cast<const uint2*>(w + i);
-                const float r4[4] = {xr.x, xr.y, xr.z, xr.w}, x4[4] = {xa.x, xa.y, xa.z, xa.w};
-                const float z4[4] = {za.x, za.y, za.z, za.w}, i4[4] = {ia.x, ia.y, ia.z, ia.w};
-                const float w4[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
-                                     bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
-                    const float zs = fmaf(rho, z4[j], ba * w4[j]);
-                    qf += zs * zs;
-                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i + j];
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int i = idx(g, j);
-                if (i < d) {
-                    const float xr = xref[i];
-                    xs[4 * g + j] = xr + rho * (x[i] - xr) + xi[i];
-                    const float zs = fmaf(rho, z[i], ba * bf16_bits_to_f32(w[i]));
-                    qf += zs * zs;
-                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i];
-                }
-            }
-        }
-    }
+    // the map of x* and its likelihood terms first (they need none of the chain's d-vectors)
     float uv[4 * NM];
     const float* ax = Ax + (size_t)p * dy;
     const float* axi = AXi + row * dy;
@@ -546,6 +541,62 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
             }
         }
     }
+    if (STAGE) {   // every thread waits for the staged rows (bounded; on expiry the step is abandoned)
+        const uint32_t bar = smem_u32(&s_bar);
+        long long t0 = clock64();
+        bool ok = true;
+        while (!mbar_try(bar, 0)) {
+            if (clock64() - t0 > TC_WAIT_CYCLES) {
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) {
+            if (tid == 0) set_status(&ctl->status, DEV_TIMEOUT);
+            t0 = clock64();   // the copies still in flight target this CTA's shared memory: wait for them
+            while (!mbar_try(bar, 0) && clock64() - t0 < TC_WAIT_CYCLES) {
+            }
+            return;
+        }
+    }
+
+    float xs[4 * NV];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) {
+        if (VEC) {
+            const int i = idx(g, 0);
+            if (i < d) {
+                const float4 xr = *reinterpret_cast<const float4*>(xref + i);
+                const float4 xa = *reinterpret_cast<const float4*>(xsrc + i);
+                const float4 za = *reinterpret_cast<const float4*>(zsrc + i);
+                const float4 ia = *reinterpret_cast<const float4*>(isrc + i);
+                const uint2 wb = *reinterpret_cast<const uint2*>(w + i);
+                const float r4[4] = {xr.x, xr.y, xr.z, xr.w}, x4[4] = {xa.x, xa.y, xa.z, xa.w};
+                const float z4[4] = {za.x, za.y, za.z, za.w}, i4[4] = {ia.x, ia.y, ia.z, ia.w};
+                const float w4[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
+                                     bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
+                    const float zs = fmaf(rho, z4[j], ba * w4[j]);
+                    qf += zs * zs;
+                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i + j];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = idx(g, j);
+                if (i < d) {
+                    const float xr = xref[i];
+                    xs[4 * g + j] = xr + rho * (x[i] - xr) + xi[i];
+                    const float zs = fmaf(rho, z[i], ba * bf16_bits_to_f32(w[i]));
+                    qf += zs * zs;
+                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i];
+                }
+            }
+        }
+    }
     // the three sums over the block, then the test (Algorithm 1) in thread 0
     qf = warp_sum(qf);
     lf = warp_sum(lf);
@@ -568,7 +619,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
             const double lpp = (double)a1 + lmap, qpp = 0.5 * (double)a0 * inv_infl2;
             const double loga = lpp - s_lpc + qpp - s_qc;
             const bool finite = isfinite(lpp) && isfinite(qpp);
-            const int a = finite && (s_lu < loga);
+            // log u < log a as in FP64: the FP32 log of u (within 1e-5 of log u: u's rounding to FP32 and a few
+            // ulps of logf, |log u| <= 37) decides unless log a is within 1e-4 of it; then the FP64 log does
+            const double l32 = (double)s_lu32;
+            int a = 0;
+            if (finite) a = loga > l32 + 1e-4 ? 1 : loga < l32 - 1e-4 ? 0 : (log(s_u) < loga);
             if (t < tr.steps) {
                 const size_t k = (size_t)t * P + p;
                 tr.lp[k] = lpp; tr.q[k] = qpp; tr.qc[k] = s_qc; tr.loga[k] = loga; tr.acc[k] = (int8_t)a;
@@ -597,7 +652,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
             if (i < d) {
                 float v[4];
                 if (a) {
-                    const float4 za = *reinterpret_cast<const float4*>(z + i);
+                    const float4 za = *reinterpret_cast<const float4*>(zsrc + i);
                     const uint2 wb = *reinterpret_cast<const uint2*>(w + i);
                     const float z4[4] = {za.x, za.y, za.z, za.w};
                     const float w4[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
@@ -611,7 +666,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                     *reinterpret_cast<float4*>(x + i) = make_float4(v[0], v[1], v[2], v[3]);
                     *reinterpret_cast<float4*>(z + i) = make_float4(zn[0], zn[1], zn[2], zn[3]);
                 } else {
-                    const float4 xa = *reinterpret_cast<const float4*>(x + i);
+                    const float4 xa = *reinterpret_cast<const float4*>(xsrc + i);
                     v[0] = xa.x; v[1] = xa.y; v[2] = xa.z; v[3] = xa.w;
                 }
                 if (h) {

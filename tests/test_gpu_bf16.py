@@ -61,11 +61,12 @@ def _bf16_pair(ts, P, steps, **kw):
     return make_pair(ts, P, trace_steps=steps, prec=_o.BF16, **kw)
 
 
-@pytest.mark.parametrize("kind", ["tanh", "dense", "diag", "tanh_vec", "dense_vec"])
+@pytest.mark.parametrize("kind", ["tanh", "dense", "diag", "tanh_vec", "dense_vec", "tanh4096"])
 def test_bf16_steps_match_oracle_bf16_mode(kind):
     """The map-carrying targets run as one fused launch per step: scalar element layout for d or d_y not a
     multiple of 4 (tanh, dense), 16-byte vectors otherwise (tanh_vec, dense_vec, with d past one element
-    group per thread)."""
+    group per thread), and the chain's rows staged in shared memory by bulk copies (the vector cases; at
+    d = 4096 they fill the 48 KB the kernel is set up for)."""
     if kind == "tanh":
         ts, P = workloads.tanh_regression(200, 130, 31), 6
     elif kind == "dense":
@@ -74,10 +75,12 @@ def test_bf16_steps_match_oracle_bf16_mode(kind):
         ts, P = workloads.tanh_regression(2052, 132, 35), 4
     elif kind == "dense_vec":
         ts, P = workloads.dense_gaussian(160, 36), 5
+    elif kind == "tanh4096":
+        ts, P = workloads.tanh_regression(4096, 2048, 40), 3
     else:
         ts, P = workloads.diag_gaussian(100), 3
     d = ts.d
-    steps = 12
+    steps = 6 if d > 2048 else 12
     C0 = np.diag(np.linspace(0.5, 1.5, d) * (ts.lam if ts.lam is not None else np.full(d, 0.01)))
     x0 = workloads.start_state(d, P, 4, scale=np.sqrt(np.diag(C0)))
     g, o = _bf16_pair(ts, P, steps, n_lag=8, beta0=0.3, seed=13, C0=C0, x0=x0, min_samples_refresh=10 ** 9)
