@@ -18,7 +18,7 @@ Metrics: chain-steps/s = P n_lag / device time of an interval (everything above 
 min over coordinates of the batch-means effective sample size of the timed window (batches = one interval
 of one chain) / the window's device time.
 
-Prints one JSON line (rank 0). --impl reference times the CPU oracle (the reference arm for this build).
+Prints one JSON line (rank 0). --impl reference times the CPU oracle (the reference arm: a plain FP64 CPU program).
 """
 from __future__ import annotations
 

@@ -10,7 +10,7 @@
  *   - the Metropolis-Hastings test of eq. (accept), written as in Algorithm 1:
  *     log a = log pi(x*) + q(x*) - log pi(x_n) - q(x_n),  q(v) = |A_n^{-1}(v - x_ref)|^2 / (2 alpha^2);
  *   - every n_lag steps: the beta rule of Algorithm 1, the moments of eq. (sampmean) / eq. (sampcov) pooled
- *     over all chains (Sec. 2.3.1), and A_n = Cholesky(C_n).
+ *     over all chains (Sec. 2.4.1), and A_n = Cholesky(C_n).
  *
  * Conventions (every entry point):
  *   - Host pointers are owned by the caller and only read/written during the call. Target arrays are
@@ -68,7 +68,7 @@ typedef enum { DIAM_FP64 = 0, DIAM_BF16 = 2 } diam_prec;
  *  TANH_REG   : -sum_i x_i^2 / (2 lam_i) - sum_k (y_k - tanh((A x)_k))^2 / (2 sigma^2), A is d_y x d
  *  BANANA     : -x1^2/(2a) - (x2 + b x1^2 - c)^2 / 2 - sum_{i>=3} x_i^2 / (2 lam_i)
  *  REF_GAUSS  : the current reference Gaussian N(x_ref, alpha^2 A_n A_n^T), evaluated from x by a
- *               triangular solve; every proposal is accepted (a test target, Sec. 2.2.2)
+ *               triangular solve; every proposal is accepted (a test target, Sec. 2.3.2)
  *  CALLBACK   : user function on device memory (see diam_logpi_fn) */
 typedef enum {
     DIAM_T_DIAG_GAUSS = 0,
@@ -101,7 +101,7 @@ typedef struct {
 typedef struct {
     int32_t d, P;           /* dimension, number of concurrent chains */
     int32_t n_lag;          /* steps between factor refreshes (Algorithm 1) */
-    int32_t M;              /* intervals per batch between synchronisations (Sec. 2.3.1) */
+    int32_t M;              /* intervals per batch between synchronisations (Sec. 2.4.1) */
     double beta0;           /* initial beta; Algorithm 1 uses min(2.4/sqrt(d), 0.5) */
     double infl;            /* inflation alpha of eq. (diamnl); 1 = eq. (diam) */
     int32_t adapt_beta;     /* 1: Algorithm 1's beta rule, pooled over chains */
@@ -156,7 +156,7 @@ DIAM_API diam_status diam_run_batch(diam_ctx* ctx, int64_t n_steps);
  * State queries and checkpoints do this themselves. Synchronises. */
 DIAM_API diam_status diam_flush(diam_ctx* ctx);
 
-/* Synchronisation point of Sec. 2.3.1 (eq. (mom2g), (mom1g)). With the pooled reading used here the
+/* Synchronisation point of Sec. 2.4.1 (eq. (mom2g), (mom1g)). With the pooled reading used here the
  * local moments already are the global ones; this call merges moments exported by other samplers (other
  * processes, other GPUs) into them: ext_mean (d), ext_M2 (d x d, the centred sum
  * sum_i (x_i - ext_mean)(x_i - ext_mean)^T) and ext_n samples. ext_* may be NULL / 0 (no import).

@@ -7,8 +7,8 @@
  *
  * Paper: "Accelerated dimension-independent adaptive Metropolis" (arXiv 1506.05741).
  * Every routine cites the passage it follows. The sampler is Algorithm 1 with the proposal of eq. (diam) /
- * eq. (diamnl) (Sec. 2.2.4), the MH acceptance of eq. (accept) (Sec. 2.1), the moments of eq. (sampcov) /
- * eq. (sampmean) (Sec. 2.2.3) pooled over the P concurrent chains of Sec. 2.3.1.
+ * eq. (diamnl) (Sec. 2.3.4), the MH acceptance of eq. (accept) (Sec. 2.2), the moments of eq. (sampcov) /
+ * eq. (sampmean) (Sec. 2.3.3) pooled over the P concurrent chains of Sec. 2.4.1.
  *
  * Readings where the paper is silent (listed in full in the design notes):
  *  - one proposal factor shared by all chains, built from the moments pooled over every chain;
@@ -314,7 +314,7 @@ static double orc_logpi(const orc_sampler* s, const double* x, double* work) {
         }
         case ORC_T_REF: {
             /* the current reference Gaussian N(x_ref, infl^2 Lq Lq^T): a target for which every proposal
-             * of eq. (diamnl) is accepted (Sec. 2.2.2: the pCN move preserves N(0, A A^T)). */
+             * of eq. (diamnl) is accepted (Sec. 2.3.2: the pCN move preserves N(0, A A^T)). */
             double* dv = work;
             double* z = work + d;
             for (int i = 0; i < d; ++i) dv[i] = x[i] - s->xref[i];

@@ -1,4 +1,4 @@
-"""Diagnostics for the oracle's chains: batch-means ESS and the PSRF of Sec. 2.3.2.
+"""Diagnostics for the oracle's chains: batch-means ESS and the PSRF of Sec. 2.4.2.
 
 TEST INFRASTRUCTURE (see ``oracle/__init__.py``). Plain numpy, written from the definitions.
 """

@@ -168,7 +168,7 @@ def test_target_banana_is_a_volume_preserving_transform_of_a_gaussian():
 
 # ------------------------------------------------------------------ S2-S7: proposal + accept invariants
 def test_reference_gaussian_target_accepts_every_proposal():
-    """Sec. 2.2.2 / 2.2.4: the move of eq. (diam) preserves N(x_ref, A A^T), so with that Gaussian as the
+    """Sec. 2.3.2 / 2.3.4: the move of eq. (diam) preserves N(x_ref, A A^T), so with that Gaussian as the
     target every proposal is accepted - also across factor refreshes (x_ref and A_n both change)."""
     d, P = 9, 3
     ts = workloads.diag_gaussian(d)

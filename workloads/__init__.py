@@ -4,7 +4,7 @@ This module only builds inputs: target data (the arrays that define log pi) and 
 none of the sampler's arithmetic and draws with numpy's PCG64 generator, never with the sampler's Philox
 streams, so both the CUDA path and the CPU oracle can take their inputs from here.
 
-Workloads (sizes from the paper's kind of targets, Sec. 3.1, scaled to the runs defined for this build):
+Workloads (the kinds of target of the paper's experiments, Sec. 3.1, at the sizes of the runs below):
   diag64     Gaussian N(0, diag(i^-2)), d = 64, one chain.
   dense1024  Gaussian with covariance Q diag(i^-1) Q^T, Q from the QR factorisation of a seeded
              N(0, 1) matrix; log pi = -|G x|^2 / 2 with G = diag(sqrt(i)) Q^T. d = 1024, P = 128.
