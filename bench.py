@@ -201,6 +201,7 @@ def run_arm(name, run, ts, x0, C0, prec, da, W, K, torch, stream, dm, clocks_ind
     mom1 = s.export_moments()
     xs, _ = s.block_sums(W + K)
     ess, N = ess_window(xs[W:W + K], run.n_lag, mom0, mom1)
+    rhat = s.psrf(W, K) if run.P > 1 else None   # Sec. 2.4.2 over the timed window
     st = s.stats()
     rf_cnt, rf_ms = s.profile()["refresh"]
     out = {"chain_steps_per_s": round(run.P * run.n_lag * K / dt, 1), "ms_per_step": round(dt / K * 1e3, 3),
@@ -209,6 +210,9 @@ def run_arm(name, run, ts, x0, C0, prec, da, W, K, torch, stream, dm, clocks_ind
            "argmin_coordinate": int(np.argmin(ess)), "window_samples": int(N),
            "accept_rate": round(st["accepted"] / max(1, st["steps"] * run.P), 4), "beta": round(st["beta"], 5),
            "refreshes": st["refreshes"], "chol_attempts": st["chol_attempts"]}
+    if rhat is not None:
+        out["psrf_max"] = round(float(rhat.max()), 4)
+        out["psrf_frac_within_0.2"] = round(float(np.mean(rhat - 1.0 <= 0.2)), 4)
     if rf_cnt:   # refreshes factorised beside the following interval: their device time there
         out["refresh_beside_ms"] = round(rf_ms / rf_cnt, 3)
     if da:

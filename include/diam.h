@@ -120,7 +120,8 @@ typedef struct {
     uint64_t seed;          /* Philox4x32-10 key */
     uint32_t problem_id;    /* mixed into the key; distinct problems draw distinct streams */
     int32_t trace_steps;    /* keep a per-step, per-chain trace for the first trace_steps steps (0: off) */
-    int32_t keep_block_sums;/* 1: keep per-interval, per-chain sums of x and log pi (for ESS / PSRF) */
+    int32_t keep_block_sums;/* 1: keep per-interval, per-chain sums of x, of x^2 (as the scatter about the
+                               interval mean in BF16 mode) and of log pi (for ESS and the PSRF) */
     int32_t profile;        /* 1: time every phase with CUDA events on the context's stream (diam_get_profile) */
     int32_t graphs;         /* 1: each whole interval's n_lag steps replay one captured CUDA graph (default) */
     int32_t reserved[5];
@@ -186,6 +187,15 @@ DIAM_API diam_status diam_get_trace(diam_ctx* ctx, double* lp_prop, double* q_pr
  * current one partial), in BF16 mode the completed intervals (their x sums are formed from the interval's
  * records when it completes). Synchronises. */
 DIAM_API diam_status diam_get_block_sums(diam_ctx* ctx, double* xsum, double* lpsum, int64_t* n_blocks);
+
+/* Potential scale reduction factor sqrt(R_i) of Sec. 2.4.2 (eq. (winco), (btwco), (psrf)) for every
+ * coordinate i, over the completed intervals first_block .. first_block + n_blocks - 1: each chain's mean
+ * and variance (1/n normalisation of eq. (sampcov), n = n_blocks n_lag samples per chain) from its interval
+ * sums, then the between-chain variance B_i and the mean within-chain variance W_i across the P chains.
+ * psrf (host, d entries) receives sqrt(R_i). Needs keep_block_sums and P >= 2; computed on the device in
+ * FP64 from the interval sums (FP32 sums in BF16 mode). DIAM_EINVAL if the window is not available.
+ * Synchronises. */
+DIAM_API diam_status diam_get_psrf(diam_ctx* ctx, int64_t first_block, int64_t n_blocks, double* psrf);
 
 /* Checkpoint: the full sampler state (chains, factor, moments, beta, counters, pending factors). Philox
  * is counter-based, so save + load + run N reproduces run N bit for bit. diam_save with buf = NULL

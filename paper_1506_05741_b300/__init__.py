@@ -63,7 +63,7 @@ class DiamStats(C.Structure):
 
 
 EXPORTS = ["diam_config_default", "diam_init", "diam_run_batch", "diam_flush", "diam_sync_moments", "diam_get_moments",
-           "diam_export_moments", "diam_get_state", "diam_get_factor", "diam_get_trace", "diam_get_block_sums",
+           "diam_export_moments", "diam_get_state", "diam_get_factor", "diam_get_trace", "diam_get_block_sums", "diam_get_psrf",
            "diam_save", "diam_load", "diam_get_profile", "diam_destroy", "diam_last_error", "diam_status_string"]
 PHASES = ["noise", "xi_gemm", "propose", "target", "accept", "fold", "refresh", "rewhiten", "screen", "train", "step"]
 
@@ -90,6 +90,7 @@ def lib():
                 "diam_init": (C.c_int, [P, P, P, P, P, P, P]),
                 "diam_run_batch": (C.c_int, [P, I64]),
                 "diam_flush": (C.c_int, [P]),
+                "diam_get_psrf": (C.c_int, [P, I64, I64, P]),
                 "diam_sync_moments": (C.c_int, [P, P, P, I64]),
                 "diam_get_moments": (C.c_int, [P, P, P, P]),
                 "diam_export_moments": (C.c_int, [P, P, P, P]),
@@ -379,6 +380,12 @@ class Sampler:
         nb = C.c_int64(n_blocks)
         self._check(self._l.diam_get_block_sums(self._h, _p(xs), _p(ls), C.byref(nb)), "diam_get_block_sums")
         return xs[: nb.value], ls[: nb.value]
+
+    def psrf(self, first_block: int, n_blocks: int) -> np.ndarray:
+        """sqrt(R_i) of Sec. 2.4.2 for every coordinate over the given completed intervals (keep_block_sums)."""
+        out = np.zeros(self.d)
+        self._check(self._l.diam_get_psrf(self._h, int(first_block), int(n_blocks), _p(out)), "diam_get_psrf")
+        return out
 
     def profile(self, reset: bool = True) -> dict:
         """Per-phase timed launch counts and device milliseconds (needs cfg['profile'] = 1)."""

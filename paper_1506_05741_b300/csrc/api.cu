@@ -59,18 +59,22 @@ struct diam_ctx {
     struct Captured {
         cudaGraphExec_t exec = nullptr;
         unsigned long long launches = 0;
-    } chol_graph, trsm_graph, chol_graph_r;
-    // refresh beside the next interval (BF16 mode, graphs, refresh_delay >= 1): the factorisation of interval
-    // k's C_n runs on its own stream and workspaces while interval k + 1 steps; resolved at k + 1's end
-    cudaStream_t rs = nullptr;
-    cudaEvent_t rs_fork = nullptr, rs_start = nullptr, rs_done = nullptr;   // start / done: timed
-    OzakiWs ozr;
-    double *Cr = nullptr, *M2s = nullptr;   // its matrix; the moments it was built from (for retries)
-    struct {
+    } chol_graph, trsm_graph;
+    // refreshes beside the following intervals (BF16 mode, graphs, refresh_delay >= 1): the factorisation of
+    // interval k's C_n runs on a stream and workspaces of its own while the next intervals step, and is
+    // resolved at the end of interval k + min(delay, 2); with delay >= 2 two of them can be in flight
+    struct AsyncRefresh {
+        cudaStream_t rs = nullptr;
+        cudaEvent_t fork = nullptr, start = nullptr, done = nullptr;   // start / done: timed
+        OzakiWs oz;
+        double *Cr = nullptr, *M2s = nullptr;   // its matrix; the moments it was built from (for retries)
+        int* info = nullptr;                    // its failing pivot + 1 (device)
+        Captured graph;
         bool active = false;
         int64_t blk = 0, n = 0;
         double eps = 0;
-    } rf;
+    } ar[2];
+    int n_ar = 0;   // slots in use (0: refreshes run between the intervals)
     std::string err;
     bool bad = false;
     diam_logpi_fn fn = nullptr;
@@ -121,8 +125,10 @@ struct diam_ctx {
     // trace and interval sums
     TraceDev tr{};
     void* bsum = nullptr;   // per-interval, per-chain sums of x: FP64 (FP32 in BF16 mode)
+    void* bm2 = nullptr;    // and of x^2 (FP64 mode) / the scatter about the interval mean (BF16 mode)
     double* lpsum = nullptr;
     int64_t bcap = 0;
+    double* psrf_ws = nullptr;   // 2 x P x d: per-chain means and variances of a PSRF window
     // phase profiler (cfg.profile): event pairs recorded on the stream, read back at synchronisation points
     struct Evt {
         cudaEvent_t a, b;
@@ -434,15 +440,18 @@ static diam_status ensure_bsum(diam_ctx* c, int64_t blk) {
     if (!c->cfg.keep_block_sums || blk < c->bcap) return DIAM_OK;
     const int P = c->P, d = c->d;
     int64_t ncap = std::max<int64_t>(2 * c->bcap, blk + 16);
-    void* nb = nullptr;
+    void *nb = nullptr, *nq = nullptr;
     double* nlp = nullptr;
     CKS(dalloc(c, (char**)&nb, bsum_elt(c) * (size_t)ncap * P * d));
+    CKS(dalloc(c, (char**)&nq, bsum_elt(c) * (size_t)ncap * P * d));
     CKS(dalloc(c, &nlp, sizeof(double) * (size_t)ncap * P));
     if (c->bcap) {
         CK(cudaMemcpyAsync(nb, c->bsum, bsum_elt(c) * (size_t)c->bcap * P * d, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(nq, c->bm2, bsum_elt(c) * (size_t)c->bcap * P * d, cudaMemcpyDeviceToDevice, c->st));
         CK(cudaMemcpyAsync(nlp, c->lpsum, sizeof(double) * (size_t)c->bcap * P, cudaMemcpyDeviceToDevice, c->st));
     }
     c->bsum = nb;
+    c->bm2 = nq;
     c->lpsum = nlp;
     c->bcap = ncap;
     return DIAM_OK;
@@ -588,12 +597,13 @@ static diam_status do_step(diam_ctx* c) {
     if constexpr (BF) {
         { select_kernel<T, float><<<grid2, kThreads, 0, c->st>>>(d, P, c->nl, c->ctl, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
                                                                 (const T*)c->Zp, (float*)c->hist, c->ldh, (const T*)c->cenT,
-                                                                (float*)bs, ls, c->lp, c->rec ? c->Ax : nullptr, c->Axp,
+                                                                (float*)bs, nullptr, ls, c->lp, c->rec ? c->Ax : nullptr, c->Axp,
                                                                 c->dy, dac, rcap); count_launch(); }
     } else {
         { select_kernel<T, double><<<grid2, kThreads, 0, c->st>>>(d, P, c->nl, c->ctl, c->accf, (T*)c->X, (T*)c->Z, (const T*)c->Xp,
                                                                  (const T*)c->Zp, (double*)c->hist, c->ldh, (const T*)c->cenT,
-                                                                 (double*)bs, ls, c->lp, nullptr, nullptr, 0, dac,
+                                                                 (double*)bs, bs ? (double*)c->bm2 : nullptr, ls, c->lp, nullptr,
+                                                                 nullptr, 0, dac,
                                                                  rcap); count_launch(); }
     }
     CK(cudaGetLastError());
@@ -611,11 +621,12 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
     constexpr bool BF = std::is_same<T, float>::value;
     // BF16 mode: the per-chain interval sums of x come from the records (in the fold's pass over them)
     float* xs = (BF && c->cfg.keep_block_sums) ? (float*)c->bsum + (size_t)blk * P * d : nullptr;
+    float* xq = xs ? (float*)c->bm2 + (size_t)blk * P * d : nullptr;
     const int npb = (P + 31) / 32;
     if (rows <= 0) {
         if (xs) { fold_records_kernel<<<dim3((d + 31) / 32, npb), dim3(32, 8), 0, c->st>>>((const float*)c->hist, c->ldh, P, nl, nl, d,
                                                                                      (const float*)c->cenT, nullptr, 0, nullptr,
-                                                                                     nullptr, xs); count_launch(); }
+                                                                                     nullptr, xs, xq); count_launch(); }
         return DIAM_OK;
     }
     double nb = (double)rows;
@@ -629,7 +640,7 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
         const int ldt = ((int)rows + 63) / 64 * 64, ntile = (int)(nl - s0) * npb;
         { fold_records_kernel<<<dim3((d + 31) / 32, npb), dim3(32, 8), 0, c->st>>>((const float*)c->hist, c->ldh, P, nl, (int)s0, d,
                                                                                 (const float*)c->cenT, c->histT, ldt, c->psum,
-                                                                                c->psum + (size_t)ntile * d, xs); count_launch(); }
+                                                                                c->psum + (size_t)ntile * d, xs, xq); count_launch(); }
         if (ldt > rows)   // the K padding of the SYRK operand
             CK(cudaMemset2DAsync(c->histT + rows, sizeof(uint16_t) * ldt, 0, sizeof(uint16_t) * (ldt - rows), d, c->st));
         { fold_sums_kernel<<<(d + 31) / 32, kThreads, 0, c->st>>>(d, ntile, c->psum, c->psum + (size_t)ntile * d, c->cen64,
@@ -734,80 +745,95 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
     return DIAM_OK;
 }
 
-// The refresh of interval blk beside interval blk + 1 (its factor is due at interval blk + 1 + delay >= blk + 2):
+// The refresh of interval blk beside the following intervals (its factor is due at interval blk + 1 + delay):
 // C_n with the first jitter built and the moments kept on the context's stream, then the factorisation, on
-// the refresh stream with its own workspaces, into pending slot blk. refresh_finish resolves it.
+// the slot's stream with its own workspaces, into pending slot blk. refresh_finish_due resolves it.
 static bool refresh_async_ok(const diam_ctx* c) {
-    return c->bf && c->cfg.graphs && !c->cfg.profile && c->cfg.refresh_delay >= 1 && c->rs && c->Cr;
+    return c->bf && c->cfg.graphs && !c->cfg.profile && c->cfg.refresh_delay >= 1 && c->n_ar > 0;
 }
 
 static diam_status refresh_launch(diam_ctx* c, int64_t blk) {
     const int d = c->d;
+    diam_ctx::AsyncRefresh& r = c->ar[blk % c->n_ar];
+    if (r.active) return fail(c, DIAM_ESTATE, "refresh", "slot still in flight");
     double eps = c->cfg.eps_jitter;
     if (eps < 1e-4) eps = 1e-4;   // the BF16-mode floor of the refresh rule
-    { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, 1.0 / (double)c->n, eps, c->Cr); count_launch(); }
-    CK(cudaMemcpyAsync(c->M2s, c->M2, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
+    { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, 1.0 / (double)c->n, eps, r.Cr); count_launch(); }
+    CK(cudaMemcpyAsync(r.M2s, c->M2, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
     Pending& pd = c->pend[(size_t)(blk % (int64_t)c->pend.size())];
     CK(cudaMemcpyAsync(pd.mean, c->mean, sizeof(double) * d, cudaMemcpyDeviceToDevice, c->st));
-    CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
-    CK(cudaEventRecord(c->rs_fork, c->st));
-    CK(cudaStreamWaitEvent(c->rs, c->rs_fork, 0));
-    CK(cudaEventRecord(c->rs_start, c->rs));
-    auto body = [&]() { return cholesky_f64(c->Cr, d, d, &c->ctl->chol_info, c->rs, &c->ozr, &c->ctl->status); };
-    if (c->ozr.hi) {   // after a first eager factorisation (which creates the workspace's streams)
-        CKS(run_captured(c, c->chol_graph_r, body, c->rs));
+    CK(cudaMemsetAsync(r.info, 0, sizeof(int), c->st));
+    CK(cudaEventRecord(r.fork, c->st));
+    CK(cudaStreamWaitEvent(r.rs, r.fork, 0));
+    CK(cudaEventRecord(r.start, r.rs));
+    auto body = [&]() { return cholesky_f64(r.Cr, d, d, r.info, r.rs, &r.oz, &c->ctl->status); };
+    if (r.oz.hi) {   // after a first eager factorisation (which creates the workspace's streams)
+        CKS(run_captured(c, r.graph, body, r.rs));
     } else {
         CK(body());
     }
-    CK(cudaMemcpyAsync(pd.L, c->Cr, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->rs));
-    CK(cudaEventRecord(c->rs_done, c->rs));
-    c->rf.active = true;
-    c->rf.blk = blk;
-    c->rf.n = c->n;
-    c->rf.eps = eps;
+    CK(cudaMemcpyAsync(pd.L, r.Cr, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, r.rs));
+    CK(cudaEventRecord(r.done, r.rs));
+    r.active = true;
+    r.blk = blk;
+    r.n = c->n;
+    r.eps = eps;
     return DIAM_OK;
 }
 
-// Wait for the refresh in flight and apply the refresh rule's outcome: its pending factor, or the retries
+// Wait for a refresh in flight and apply the refresh rule's outcome: its pending factor, or the retries
 // with a larger jitter (from the kept moments, in order on the context's stream), or the skip.
-static diam_status refresh_finish(diam_ctx* c) {
-    if (!c->rf.active) return DIAM_OK;
-    c->rf.active = false;
+static diam_status refresh_finish_slot(diam_ctx* c, diam_ctx::AsyncRefresh& r) {
+    if (!r.active) return DIAM_OK;
+    r.active = false;
     const int d = c->d;
-    CK(cudaStreamWaitEvent(c->st, c->rs_done, 0));   // later work on the stream is ordered after it
-    CK(cudaEventSynchronize(c->rs_done));
+    CK(cudaStreamWaitEvent(c->st, r.done, 0));   // later work on the stream is ordered after it
+    CK(cudaEventSynchronize(r.done));
     CKS(sync_and_check(c));
-    float ms = 0.f;   // its device time beside the interval, in the refresh phase's accumulators
-    if (cudaEventElapsedTime(&ms, c->rs_start, c->rs_done) == cudaSuccess) {
+    float ms = 0.f;   // its device time beside the intervals, in the refresh phase's accumulators
+    if (cudaEventElapsedTime(&ms, r.start, r.done) == cudaSuccess) {
         c->prof_ms[PH_REFRESH] += ms;
         c->prof_cnt[PH_REFRESH] += 1;
     }
     int info = 0;
-    CK(d2h(c, &info, &c->ctl->chol_info, sizeof(int)));
+    CK(d2h(c, &info, r.info, sizeof(int)));
     c->chol_attempts++;
-    Pending& pd = c->pend[(size_t)(c->rf.blk % (int64_t)c->pend.size())];
+    Pending& pd = c->pend[(size_t)(r.blk % (int64_t)c->pend.size())];
     bool ok = info == 0;
-    double eps = c->rf.eps * 100.0;
+    double eps = r.eps * 100.0;
     for (int attempt = 1; attempt < 4 && !ok; ++attempt) {
-        { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2s, d, 1.0 / (double)c->rf.n, eps, c->Cr); count_launch(); }
-        CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
-        CK(cholesky_f64(c->Cr, d, d, &c->ctl->chol_info, c->st, &c->oz, &c->ctl->status));
+        { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, r.M2s, d, 1.0 / (double)r.n, eps, r.Cr); count_launch(); }
+        CK(cudaMemsetAsync(r.info, 0, sizeof(int), c->st));
+        CK(cholesky_f64(r.Cr, d, d, r.info, c->st, &c->oz, &c->ctl->status));
         CKS(sync_and_check(c));
-        CK(d2h(c, &info, &c->ctl->chol_info, sizeof(int)));
+        CK(d2h(c, &info, r.info, sizeof(int)));
         ok = info == 0;
         eps *= 100.0;
         c->chol_attempts++;
-        if (ok) CK(cudaMemcpyAsync(pd.L, c->Cr, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
+        if (ok) CK(cudaMemcpyAsync(pd.L, r.Cr, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
     }
     if (!ok) {
         c->notspd++;
         c->err = "refresh skipped: C_n + jitter not positive definite (previous factor kept)";
         return DIAM_OK;
     }
-    pd.block = c->rf.blk + 1 + c->cfg.refresh_delay;
+    pd.block = r.blk + 1 + c->cfg.refresh_delay;
     c->refreshes++;
     return DIAM_OK;
 }
+
+// Resolve the refreshes in flight built at or before interval last (all of them: last < 0), oldest first.
+static diam_status refresh_finish_due(diam_ctx* c, int64_t last) {
+    for (;;) {
+        diam_ctx::AsyncRefresh* o = nullptr;
+        for (int i = 0; i < c->n_ar; ++i)
+            if (c->ar[i].active && (last < 0 || c->ar[i].blk <= last) && (!o || c->ar[i].blk < o->blk)) o = &c->ar[i];
+        if (!o) return DIAM_OK;
+        CKS(refresh_finish_slot(c, *o));
+    }
+}
+
+static diam_status refresh_finish(diam_ctx* c) { return refresh_finish_due(c, -1); }
 
 static void push_scalars(diam_ctx* c) {
     double rho = std::sqrt(1.0 - c->beta * c->beta);
@@ -833,7 +859,9 @@ static diam_status block_end(diam_ctx* c, int64_t blk) {
         if (c->beta > g.beta_max) c->beta = g.beta_max;
     }
     if ((blk + 1) * (int64_t)c->nl > g.burnin) c->acc_refresh += (int64_t)acc;
-    CKS(refresh_finish(c));
+    // the refreshes in flight whose factors may be due at the next interval: built at or before
+    // blk - min(delay, 2) (at most two run beside the intervals)
+    CKS(refresh_finish_due(c, blk - std::max(1, c->n_ar)));
     if (c->acc_refresh >= g.min_samples_refresh && c->n > 0) {
         if (refresh_async_ok(c)) CKS(refresh_launch(c, blk));
         else CKS(refresh(c, blk));
@@ -1026,17 +1054,22 @@ static diam_status alloc_all(diam_ctx* c) {
         c->oz.capP = ozaki_panel_rows(d);
         CKS(dalloc(c, &c->oz.SLP, sizeof(uint16_t) * (size_t)std::max<int64_t>(1, c->oz.capP) * 448));
         CKS(dalloc(c, &c->oz.exP, sizeof(int) * (size_t)std::max<int64_t>(1, c->oz.capP)));
-        if (c->cfg.refresh_delay >= 1 && c->cfg.graphs) {   // the refresh beside the next interval
-            CKS(dalloc(c, &c->Cr, sizeof(double) * d * d));
-            CKS(dalloc(c, &c->M2s, sizeof(double) * d * d));
-            CKS(dalloc(c, &c->ozr.SL, ozaki_sl_bytes(d)));
-            CKS(dalloc(c, &c->ozr.ex, ozaki_ex_bytes(d)));
-            c->ozr.cap_rows = d;
-            c->ozr.lo_high = true;   // ahead of the interval's work: the chain waits on these updates
-            CK(cudaStreamCreateWithFlags(&c->rs, cudaStreamNonBlocking));
-            CK(cudaEventCreateWithFlags(&c->rs_fork, cudaEventDisableTiming));
-            CK(cudaEventCreate(&c->rs_start));
-            CK(cudaEventCreate(&c->rs_done));
+        if (c->cfg.refresh_delay >= 1 && c->cfg.graphs) {   // refreshes beside the following intervals
+            c->n_ar = c->cfg.refresh_delay >= 2 ? 2 : 1;
+            for (int i = 0; i < c->n_ar; ++i) {
+                diam_ctx::AsyncRefresh& r = c->ar[i];
+                CKS(dalloc(c, &r.Cr, sizeof(double) * d * d));
+                CKS(dalloc(c, &r.M2s, sizeof(double) * d * d));
+                CKS(dalloc(c, &r.info, sizeof(int)));
+                CKS(dalloc(c, &r.oz.SL, ozaki_sl_bytes(d)));
+                CKS(dalloc(c, &r.oz.ex, ozaki_ex_bytes(d)));
+                r.oz.cap_rows = d;
+                r.oz.lo_high = true;   // ahead of the intervals' work: the chain waits on these updates
+                CK(cudaStreamCreateWithFlags(&r.rs, cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming));
+                CK(cudaEventCreate(&r.start));
+                CK(cudaEventCreate(&r.done));
+            }
         }
         CKS(dalloc(c, &c->Lq64, sizeof(double) * d * d));
         CKS(dalloc(c, &c->Lq16, sizeof(uint16_t) * (size_t)d * c->ldk));
@@ -1375,6 +1408,31 @@ diam_status diam_get_block_sums(diam_ctx* c, double* xsum, double* lpsum, int64_
     return DIAM_OK;
 }
 
+diam_status diam_get_psrf(diam_ctx* c, int64_t first_block, int64_t n_blocks, double* psrf) {
+    CKS(check_usable(c));
+    CKS(sync_and_check(c));
+    const int64_t have = std::min<int64_t>(c->bcap, c->t / c->nl);   // completed intervals
+    if (!psrf || !c->cfg.keep_block_sums || c->P < 2 || first_block < 0 || n_blocks < 1 || first_block + n_blocks > have)
+        return fail(c, DIAM_EINVAL, "diam_get_psrf", "needs keep_block_sums, P >= 2 and completed intervals");
+    const int d = c->d, P = c->P;
+    if (!c->psrf_ws) CKS(dalloc(c, &c->psrf_ws, sizeof(double) * 2 * (size_t)P * d + sizeof(double) * d));
+    double* cm = c->psrf_ws;
+    double* cv = cm + (size_t)P * d;
+    double* out = cv + (size_t)P * d;
+    const dim3 g((d + 255) / 256, P);
+    if (c->bf) {
+        { psrf_chain_kernel<float><<<g, 256, 0, c->st>>>(d, P, c->nl, (long long)first_block, (int)n_blocks, (const float*)c->bsum,
+                                                      (const float*)c->bm2, 0, cm, cv); count_launch(); }
+    } else {
+        { psrf_chain_kernel<double><<<g, 256, 0, c->st>>>(d, P, c->nl, (long long)first_block, (int)n_blocks, (const double*)c->bsum,
+                                                       (const double*)c->bm2, 1, cm, cv); count_launch(); }
+    }
+    { psrf_final_kernel<<<(d + 255) / 256, 256, 0, c->st>>>(d, P, (double)n_blocks * c->nl, cm, cv, out); count_launch(); }
+    CK(cudaGetLastError());
+    CK(d2h(c, psrf, out, sizeof(double) * d));
+    return DIAM_OK;
+}
+
 // ---- checkpoint: a flat list of (device buffer, bytes) plus the host schedule
 struct HostState {
     int64_t t, n, acc_refresh, acc_all, refreshes, notspd, xi_block, begun_block, chol_attempts;
@@ -1403,6 +1461,7 @@ static std::vector<std::pair<void*, size_t>> state_buffers(diam_ctx* c) {
     }
     if (c->bcap) {
         v.push_back({c->bsum, bsum_elt(c) * (size_t)c->bcap * Pd});
+        v.push_back({c->bm2, bsum_elt(c) * (size_t)c->bcap * Pd});
         v.push_back({c->lpsum, 8 * (size_t)c->bcap * c->P});
     }
     return v;
@@ -1447,9 +1506,12 @@ diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
     if (hs.bcap > c->bcap) {  // grow the interval-sum store to the saved capacity
         void* nb = nullptr;
         double* nlp = nullptr;
+        void* nq = nullptr;
         CKS(dalloc(c, (char**)&nb, bsum_elt(c) * (size_t)hs.bcap * c->P * c->d));
+        CKS(dalloc(c, (char**)&nq, bsum_elt(c) * (size_t)hs.bcap * c->P * c->d));
         CKS(dalloc(c, &nlp, sizeof(double) * (size_t)hs.bcap * c->P));
         c->bsum = nb;
+        c->bm2 = nq;
         c->lpsum = nlp;
         c->bcap = hs.bcap;
     }
@@ -1622,7 +1684,8 @@ diam_status diam_da_grad(diam_ctx* c, int32_t B, const double* U, const double* 
 void diam_destroy(diam_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
-    if (c->rs) cudaStreamSynchronize(c->rs);   // a refresh still in flight
+    for (auto& r : c->ar)
+        if (r.rs) cudaStreamSynchronize(r.rs);   // a refresh still in flight
     if (c->st) cudaStreamSynchronize(c->st);
     for (auto& e : c->evts) {
         cudaEventDestroy(e.a);
@@ -1631,9 +1694,11 @@ void diam_destroy(diam_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->chol_graph.exec) cudaGraphExecDestroy(c->chol_graph.exec);
     if (c->trsm_graph.exec) cudaGraphExecDestroy(c->trsm_graph.exec);
-    if (c->chol_graph_r.exec) cudaGraphExecDestroy(c->chol_graph_r.exec);
     ozaki_ws_release(c->oz);
-    ozaki_ws_release(c->ozr);
+    for (auto& r : c->ar) {
+        if (r.graph.exec) cudaGraphExecDestroy(r.graph.exec);
+        ozaki_ws_release(r.oz);
+    }
     for (void* p : c->allocs) cudaFree(p);
     if (c->side) {
         cudaStreamSynchronize(c->side);
@@ -1641,10 +1706,11 @@ void diam_destroy(diam_ctx* c) {
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
-    if (c->rs) cudaStreamDestroy(c->rs);
-    if (c->rs_fork) cudaEventDestroy(c->rs_fork);
-    if (c->rs_done) cudaEventDestroy(c->rs_done);
-    if (c->rs_start) cudaEventDestroy(c->rs_start);
+    for (auto& r : c->ar) {
+        if (r.rs) cudaStreamDestroy(r.rs);
+        for (cudaEvent_t e : {r.fork, r.start, r.done})
+            if (e) cudaEventDestroy(e);
+    }
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c->da;
     delete c;

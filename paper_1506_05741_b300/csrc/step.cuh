@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
                                                      T* __restrict__ X, T* __restrict__ Z, const T* __restrict__ Xp,
                                                      const T* __restrict__ Zp, HT* __restrict__ hist_base, int ldh,
                                                      const T* __restrict__ cen, HT* __restrict__ bsum_base,
+                                                     HT* __restrict__ bsq_base,
                                                      double* __restrict__ lpsum_base, const double* __restrict__ lp,
                                                      float* __restrict__ Ax, const float* __restrict__ Axp, int dy,
                                                      DaCounters* dacnt, long long ring_cap) {
@@ -367,6 +368,7 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
     const long long blk = ctl->t_cur / nl;
     HT* hist = hist_base ? hist_base + (size_t)ctl->s_cur * P * ldh : nullptr;
     HT* bsum = bsum_base ? bsum_base + (size_t)blk * P * d : nullptr;
+    HT* bsq = bsq_base ? bsq_base + (size_t)blk * P * d : nullptr;   // per-chain interval sums of x^2
     double* lpsum = lpsum_base ? lpsum_base + (size_t)blk * P : nullptr;
     const int i0 = c * CHUNK, i1 = min(d, i0 + CHUNK);
     const int a = accf[p];
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
     const T* zp = Zp + (size_t)p * d;
     HT* h = hist ? hist + (size_t)p * ldh : nullptr;
     HT* bs = bsum ? bsum + (size_t)p * d : nullptr;
+    HT* bq = bsq ? bsq + (size_t)p * d : nullptr;
     bool vec_done = false;
     if constexpr (std::is_same<T, float>::value && std::is_same<HT, float>::value) {
         if ((d & 3) == 0 && (ldh & 3) == 0 && h) {
@@ -403,6 +406,7 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
         }
         if (h) h[i] = to_hist<T, HT>(v - cen[i]);
         if (bs) bs[i] += (HT)v;
+        if (bq) bq[i] += (HT)v * (HT)v;
     }
     if (Ax && a) {   // the carried map: accepted chains take A x*, block c its share of the row
         const int per = (dy + gridDim.y - 1) / gridDim.y;
@@ -786,17 +790,19 @@ __global__ void fold_prep_kernel(int d, int nparts, const double* __restrict__ p
 //     operand) and, per (step, chain block) tile, the FP32 sums of the records and of their BF16 values
 //     (psum, pbf: tile (s - s0) gridDim.y + blockIdx.y, d entries each); HT == nullptr skips this part;
 //   - xs != nullptr: every chain's sum over all n_lag steps, xs[p][c] = sum_s H + n_lag cen[c] (the records
-//     are x - cen), the per-interval, per-chain sums of x.
+//     are x - cen), the per-interval, per-chain sums of x, and its scatter about its interval mean,
+//     xm2[p][c] = sum_s H^2 - (sum_s H)^2 / n_lag (the PSRF's within-chain terms).
 __global__ void __launch_bounds__(256) fold_records_kernel(const float* __restrict__ H, int ldh, int P, int nl, int s0,
                                                            int d, const float* __restrict__ cen,
                                                            uint16_t* __restrict__ HT, int ldt, float* __restrict__ psum,
-                                                           float* __restrict__ pbf, float* __restrict__ xs) {
+                                                           float* __restrict__ pbf, float* __restrict__ xs,
+                                                           float* __restrict__ xm2) {
     __shared__ uint16_t tile[32][33];
     __shared__ float sx[8][33], sb[8][33];
     const int c0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c = c0 + tx;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f}, cur[4], nxt[4];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, acc2[4] = {0.f, 0.f, 0.f, 0.f}, cur[4], nxt[4];
     auto load = [&](int st, float* v) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -808,7 +814,10 @@ __global__ void __launch_bounds__(256) fold_records_kernel(const float* __restri
     for (int st = 0; st < nl; ++st) {
         if (st + 1 < nl) load(st + 1, nxt);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] += cur[k];
+        for (int k = 0; k < 4; ++k) {
+            acc[k] += cur[k];
+            acc2[k] = fmaf(cur[k], cur[k], acc2[k]);
+        }
         if (HT && st >= s0) {
             float ax = 0.f, ab = 0.f;
 #pragma unroll
@@ -847,9 +856,55 @@ __global__ void __launch_bounds__(256) fold_records_kernel(const float* __restri
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int p = p0 + ty + 8 * k;
-            if (p < P) xs[(size_t)p * d + c] = acc[k] + cn;
+            if (p < P) {
+                xs[(size_t)p * d + c] = acc[k] + cn;
+                if (xm2) xm2[(size_t)p * d + c] = fmaxf(0.f, acc2[k] - acc[k] * acc[k] / (float)nl);
+            }
         }
     }
+}
+
+// Potential scale reduction factor of eq. (winco), (btwco), (psrf) over the intervals [b0, b0 + nb) of the
+// per-chain interval sums (n = nb n_lag samples per chain). Stage 1, thread (p, i): the window's mean of
+// chain p and its scatter, the intervals combined pairwise (Chan, Golub & LeVeque 1979); q holds per interval
+// the scatter about the interval mean (raw = 0) or the raw sum of squares (raw = 1).
+template <typename HT>
+__global__ void psrf_chain_kernel(int d, int P, int nl, long long b0, int nb, const HT* __restrict__ bsum,
+                                  const HT* __restrict__ bq, int raw, double* __restrict__ cmean,
+                                  double* __restrict__ cvar) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+    if (i >= d) return;
+    double m = 0.0, M2 = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        const size_t o = ((size_t)(b0 + k) * P + p) * d + i;
+        const double s = (double)bsum[o], q = (double)bq[o];
+        const double mk = s / nl, m2k = raw ? fmax(0.0, q - s * mk) : q;
+        const double delta = mk - m;
+        m += delta / (k + 1);
+        M2 += m2k + delta * delta * ((double)k * nl / (k + 1));
+    }
+    cmean[(size_t)p * d + i] = m;
+    cvar[(size_t)p * d + i] = M2 / ((double)nb * nl);   // (C^p)_ii with the 1/n of eq. (sampcov)
+}
+
+// Stage 2, thread i: B_i, W_i of eq. (btwco) over the P chains and sqrt(R_i) of eq. (psrf).
+__global__ void psrf_final_kernel(int d, int P, double n, const double* __restrict__ cmean,
+                                  const double* __restrict__ cvar, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    double mg = 0.0, w = 0.0;
+    for (int p = 0; p < P; ++p) {
+        mg += cmean[(size_t)p * d + i];
+        w += cvar[(size_t)p * d + i];
+    }
+    mg /= P;
+    double b = 0.0;
+    for (int p = 0; p < P; ++p) {
+        const double e = cmean[(size_t)p * d + i] - mg;
+        b += e * e;
+    }
+    const double B = n / (P - 1) * b, W = n / ((n - 1.0) * P) * w;
+    out[i] = sqrt((n - 1.0) / n + (P + 1.0) / (P * n) * B / W);
 }
 
 // Column totals of the tile sums (compensated FP32 per thread, Kahan 1965; FP64 across threads), then the

@@ -140,14 +140,16 @@ def test_refresh_delay_applies_the_factor_where_the_oracle_does():
     assert g.stats()["refreshes"] == o.counts()["refreshes"] == 3
 
 
-def test_refresh_beside_the_next_interval_equals_refresh_in_order():
-    """The overlapped refresh (graphs on) and the in-order one (graphs off) give bit-identical chains."""
+@pytest.mark.parametrize("delay", [1, 2])
+def test_refresh_beside_the_next_interval_equals_refresh_in_order(delay):
+    """The overlapped refreshes (graphs on; with delay 2 two are in flight) and the in-order ones (graphs off)
+    give bit-identical chains."""
     import paper_1506_05741_b300 as dm
     ts, P = workloads.tanh_regression(192, 64, 38), 6
     out = []
     for graphs in (0, 1):
         cfg = dm.default_config(192, P, n_lag=8, beta0=0.3, seed=6, prec=dm.BF16, graphs=graphs,
-                                min_samples_refresh=20, refresh_delay=1)
+                                min_samples_refresh=20, refresh_delay=delay)
         s = dm.Sampler(cfg, ts, x0=workloads.start_state(192, P, 2) * np.sqrt(ts.lam), C0=np.diag(ts.lam))
         s.run(8 * 12 + 3)
         out.append((s.state(), s.moments(), s.stats()["refreshes"]))
@@ -236,3 +238,29 @@ def test_initial_log_density_after_upload(prec):
         lp = s.log_pi()
         s.close()
         assert np.max(np.abs(lp - want) / np.abs(want)) <= tol
+
+
+def test_bf16_psrf_matches_the_states_read_back():
+    """BF16 mode forms the PSRF's per-chain terms in the fold's pass over the records (sum and scatter about the
+    interval mean, FP32); the device PSRF over a window equals eq. (winco)-(psrf) evaluated on the states read
+    back after every step, to FP32 accuracy."""
+    from oracle import stats
+    import paper_1506_05741_b300 as dm
+    d, P, nl = 64, 40, 8
+    ts = workloads.tanh_regression(d, 32, 41)
+    cfg = dm.default_config(d, P, n_lag=nl, beta0=0.4, seed=10, prec=dm.BF16, min_samples_refresh=30)
+    cfg["keep_block_sums"] = 1
+    s = dm.Sampler(cfg, ts, x0=workloads.start_state(d, P, 4) * 2.0 * np.sqrt(ts.lam), C0=np.diag(ts.lam))
+    states = []
+    for _ in range(6 * nl):
+        s.run(1)
+        states.append(s.state()[0])
+    traj = np.array(states)
+    for first, count in [(1, 5), (0, 6)]:
+        win = traj[first * nl:(first + count) * nl]
+        mean = win.mean(axis=0)
+        var = ((win - mean) ** 2).mean(axis=0)
+        want = stats.psrf(mean, var, count * nl)
+        got = s.psrf(first, count)
+        assert np.max(np.abs(got - want) / want) <= 1e-4, (first, count, np.max(np.abs(got - want) / want))
+    s.close()

@@ -326,3 +326,24 @@ def test_graph_replay_equals_eager_launches(prec):
     (xb, lb, sb), (mb, cb, nb) = out[1]
     assert np.array_equal(xa, xb) and np.array_equal(la, lb) and sa == sb
     assert np.array_equal(ma, mb) and np.array_equal(ca, cb) and na == nb
+
+
+def test_psrf_matches_oracle_chains():
+    """The device PSRF (Sec. 2.4.2) over a window of completed intervals equals eq. (winco)-(psrf) evaluated
+    by the oracle's statistics on the oracle's own recorded trajectory (FP64 mode: the same chains)."""
+    from oracle import stats
+    d, P, nl = 48, 6, 16
+    ts = workloads.dense_gaussian(d, 12)
+    x0 = workloads.start_state(d, P, 2) * 3.0   # over-dispersed starts
+    g, o = make_pair(ts, P, n_lag=nl, beta0=0.4, seed=9, min_samples_refresh=40, x0=x0, C0=ts.cov,
+                     keep_block_sums=1)
+    g.run(8 * nl)
+    o.run(8 * nl, record=True)
+    traj = o.trajectory()            # post-step states, (steps, P, d)
+    for first, count in [(2, 6), (0, 8), (7, 1)]:
+        win = traj[first * nl:(first + count) * nl]
+        mean = win.mean(axis=0)
+        var = ((win - mean) ** 2).mean(axis=0)
+        want = stats.psrf(mean, var, count * nl)
+        got = g.psrf(first, count)
+        assert np.max(np.abs(got - want) / want) <= 1e-10, (first, count)
