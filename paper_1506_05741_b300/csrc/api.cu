@@ -285,10 +285,26 @@ static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
 #include "da_host.cuh"
 
 // z = Lq^{-1}(x - x_ref) and q for every chain (after a factor change); lp = -q for the reference target.
+// BF16 mode: chains per CTA of the FP32 re-whitening (its right-hand sides in shared memory).
+static int rewhiten32_group(int d) {
+    for (int g = RW_G; g > 1; g /= 2)
+        if (rewhiten32_smem(d, g) <= 220 * 1024) return g;
+    return 1;
+}
+
 template <typename T>
 static diam_status rewhiten(diam_ctx* c) {
     const int d = c->d, P = c->P;
     int e0 = ph_begin(c, PH_REWHITEN);
+    if (c->bf && rewhiten32_smem(d, 1) <= 220 * 1024) {   // FP32 forward substitution (reading G20)
+        const int G = rewhiten32_group(d);
+        { rewhiten32_kernel<<<(P + G - 1) / G, RW_THREADS, rewhiten32_smem(d, G), c->st>>>(
+              d, P, G, c->Lq16, c->ldk, (const float*)c->X, (const float*)c->xref, (float*)c->Z, c->q, inv_infl2(c),
+              c->kind == TK_REF ? c->lp : nullptr); count_launch(); }
+        CK(cudaGetLastError());
+        ph_end(c, e0);
+        return DIAM_OK;
+    }
     auto body = [&]() -> cudaError_t {
         { diff_kernel<T><<<dim3(blocks_for(d), P), kThreads, 0, c->st>>>(d, (const T*)c->X, (const T*)c->xref, c->work); count_launch(); }
         cudaError_t e = trsm_lower_f64(c->Lq64, d, d, c->work, d, P, c->st, c->bf ? &c->oz : nullptr, &c->ctl->status);
@@ -1252,6 +1268,10 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
     }
     diam_status s = alloc_all(c);
     if (s == DIAM_OK && c->bf && c->rec) s = fused_step(c, true);
+    if (s == DIAM_OK && c->bf && rewhiten32_smem(c->d, 1) <= 220 * 1024 &&
+        cudaFuncSetAttribute(rewhiten32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rewhiten32_smem(c->d, rewhiten32_group(c->d))) != cudaSuccess)
+        s = fail(c, DIAM_ECUDA, "cudaFuncSetAttribute");
     if (s == DIAM_OK) s = upload_target(c, tg);
     if (s == DIAM_OK) s = c->bf ? init_state<float>(c, x0, C0, xref0) : init_state<double>(c, x0, C0, xref0);
     if (s != DIAM_OK) {

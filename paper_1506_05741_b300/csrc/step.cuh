@@ -1051,6 +1051,164 @@ __global__ void diff_kernel(int d, const T* __restrict__ Xs, const T* __restrict
         work[(size_t)p * d + i] = (double)Xs[(size_t)p * d + i] - (double)xref[i];
 }
 
+// Re-whitening after a factor change in BF16 mode: z = Lq^{-1}(x - x_ref) for every chain in FP32, the
+// precision of the states (Lq is BF16, exact in FP32), by blocked forward substitution with a lookahead of
+// one block. One CTA per G chains keeps their right-hand sides in shared memory. Per 64-column block k (its
+// unknowns already solved): all threads first update the next block's 64 rows by block k; then warps 0 .. G-1
+// stage nothing new but solve the next block's diagonal system (warp g: chain g, the 64-step chain on lane
+// shuffles, the diagonal factor staged in shared memory) while the other warps update every row below it by
+// block k (G dot products of length 64 per row, the factor's row segment read as eight 16-byte loads, two
+// rows per iteration). Finally z and q = |z|^2 / (2 alpha^2) (and log pi = -q for the reference target).
+// Dynamic shared memory: rewhiten32_smem(d, G) bytes.
+constexpr int RW_G = 4, RW_THREADS = 512;
+
+__host__ __device__ inline size_t rewhiten32_smem(int d, int g) {
+    return sizeof(float) * ((size_t)g * d + 2 * 64 * 65 + 2 * 64 + 2 * 64 * 4);
+}
+
+// rows [r0, r1) of the G right-hand sides -= L[rows][k0 .. k0 + 64) y, y in shared memory as 64 float4
+// (column c: the G chains' values, zero past G); the threads t0, t0 + nt, ... each take four rows per
+// iteration, so one broadcast 16-byte load of y feeds 16 fused multiply-adds. Every CTA reads the same factor
+// rows, so each starts at its own rotation of the row quads.
+__device__ __forceinline__ void rw_update_rows(const uint16_t* __restrict__ Lq, int ldk, int d, int k0, int r0, int r1,
+                                               int G, const float4* __restrict__ y, float* __restrict__ rw, int t,
+                                               int nt) {
+    const int nq = (r1 - r0 + 3) / 4;
+    const int rot = nq > 0 ? (int)((blockIdx.x * 97u) % (unsigned)nq) : 0;
+    for (int qq = t; qq < nq; qq += nt) {
+        const int q = qq + rot < nq ? qq + rot : qq + rot - nq;
+        const int i0 = r0 + 4 * q;
+        const uint4* lr[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            lr[r] = reinterpret_cast<const uint4*>(Lq + (size_t)min(i0 + r, r1 - 1) * ldk + k0);
+        float4 acc[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+        for (int c8 = 0; c8 < 8; ++c8) {
+            uint4 u[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) u[r] = lr[r][c8];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const float4 yc = y[c8 * 8 + 2 * h + e];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const uint32_t w = h == 0 ? u[r].x : h == 1 ? u[r].y : h == 2 ? u[r].z : u[r].w;
+                        const float l = __uint_as_float(e ? (w & 0xFFFF0000u) : (w << 16));
+                        acc[r].x = fmaf(l, yc.x, acc[r].x);
+                        acc[r].y = fmaf(l, yc.y, acc[r].y);
+                        acc[r].z = fmaf(l, yc.z, acc[r].z);
+                        acc[r].w = fmaf(l, yc.w, acc[r].w);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = i0 + r;
+            if (i < r1) {
+                const float a[4] = {acc[r].x, acc[r].y, acc[r].z, acc[r].w};
+#pragma unroll
+                for (int g = 0; g < RW_G; ++g)
+                    if (g < G) rw[(size_t)g * d + i] -= a[g];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RW_THREADS) rewhiten32_kernel(int d, int P, int G, const uint16_t* __restrict__ Lq,
+                                                                int ldk, const float* __restrict__ X,
+                                                                const float* __restrict__ xref, float* __restrict__ Zs,
+                                                                double* __restrict__ qout, double inv_infl2,
+                                                                double* __restrict__ lp_ref) {
+    extern __shared__ float4 rw_smem4[];
+    float* yb = reinterpret_cast<float*>(rw_smem4);   // 2 x 64 x 4: a block's solution ([column][chain]), 16-byte aligned
+    float* rdiag = yb + 2 * 64 * 4;                   // 2 x 64: reciprocals of the diagonal blocks' diagonals
+    float* Ld = rdiag + 2 * 64;                       // 2 x 64 x 65: diagonal blocks (two buffers)
+    float* rw = Ld + 2 * 64 * 65;                     // G x d: right-hand sides, overwritten by z
+    __shared__ double sh[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int p0 = blockIdx.x * G, ng = min(G, P - p0);
+    const int nblk = (d + 63) / 64;
+    for (int g = 0; g < ng; ++g)
+        for (int i = tid; i < d; i += RW_THREADS) rw[(size_t)g * d + i] = X[(size_t)(p0 + g) * d + i] - xref[i];
+    // diagonal block kb into buffer kb & 1 (all threads)
+    auto stage = [&](int kb) {
+        const int k0 = kb * 64, nb = min(64, d - k0);
+        float* L = Ld + (kb & 1) * 64 * 65;
+        for (int e = tid; e < nb * nb; e += RW_THREADS) {
+            const int r = e / nb, cc = e - r * nb;
+            L[r * 65 + cc] = (cc <= r) ? bf16_bits_to_f32(Lq[(size_t)(k0 + r) * ldk + k0 + cc]) : 0.f;
+        }
+    };
+    // warp g < ng: solve block kb's unknowns of chain g (rows already updated by every earlier block)
+    auto solve = [&](int kb) {
+        const int k0 = kb * 64, nb = min(64, d - k0);
+        const float* L = Ld + (kb & 1) * 64 * 65;
+        const float* rd = rdiag + (kb & 1) * 64;
+        float* y = yb + (kb & 1) * 64 * 4;
+        float* rg = rw + (size_t)warp * d + k0;
+        float v0 = lane < nb ? rg[lane] : 0.f, v1 = lane + 32 < nb ? rg[lane + 32] : 0.f;
+        for (int j = 0; j < nb; ++j) {
+            const float vj = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
+            const float yj = vj * rd[j];
+            if (lane > j && lane < nb) v0 = fmaf(-L[lane * 65 + j], yj, v0);
+            if (lane + 32 > j && lane + 32 < nb) v1 = fmaf(-L[(lane + 32) * 65 + j], yj, v1);
+            if (lane == (j & 31)) {
+                if (j < 32) v0 = yj;
+                else v1 = yj;
+            }
+        }
+        if (lane < nb) rg[lane] = v0;
+        if (lane + 32 < nb) rg[lane + 32] = v1;
+        y[lane * 4 + warp] = lane < nb ? v0 : 0.f;   // zero past a short last block
+        y[(lane + 32) * 4 + warp] = lane + 32 < nb ? v1 : 0.f;
+    };
+    stage(0);
+    __syncthreads();
+    if (tid < min(64, d)) rdiag[tid] = 1.0f / Ld[tid * 65 + tid];
+    for (int e = tid; e < 2 * 64 * 4; e += RW_THREADS) yb[e] = 0.f;   // columns of chains past G stay zero
+    __syncthreads();
+    if (warp < ng) solve(0);
+    __syncthreads();
+    for (int kb = 0; kb < nblk; ++kb) {
+        const int k0 = kb * 64, k1 = k0 + 64;
+        const float4* y = reinterpret_cast<const float4*>(yb + (kb & 1) * 64 * 4);
+        if (k1 >= d) break;
+        const int n1 = min(64, d - k1);
+        // the next block's rows by block k, and its diagonal factor staged
+        rw_update_rows(Lq, ldk, d, k0, k1, k1 + n1, ng, y, rw, tid, RW_THREADS);
+        stage(kb + 1);
+        __syncthreads();
+        if (tid < n1) rdiag[((kb + 1) & 1) * 64 + tid] = 1.0f / Ld[((kb + 1) & 1) * 64 * 65 + tid * 65 + tid];
+        __syncthreads();
+        if (warp < ng) {
+            solve(kb + 1);   // the next block's unknowns ...
+        } else {             // ... while the other warps update the rows below it by block k
+            rw_update_rows(Lq, ldk, d, k0, k1 + n1, d, ng, y, rw, tid - 32 * ng, RW_THREADS - 32 * ng);
+        }
+        __syncthreads();
+    }
+    for (int g = 0; g < ng; ++g) {
+        double acc = 0.0;
+        for (int i = tid; i < d; i += RW_THREADS) {
+            const float v = rw[(size_t)g * d + i];
+            Zs[(size_t)(p0 + g) * d + i] = v;
+            acc += (double)v * (double)v;
+        }
+        acc = block_sum(acc, sh);
+        if (tid == 0) {
+            const double qq = 0.5 * acc * inv_infl2;
+            qout[p0 + g] = qq;
+            if (lp_ref) lp_ref[p0 + g] = -qq;
+        }
+    }
+}
+
 // z = work (rounded to T), q = |z|^2 / (2 alpha^2) from the stored z; lp = -q for the reference target.
 template <typename T>
 __global__ void __launch_bounds__(256) set_z_kernel(int d, const double* __restrict__ work, T* __restrict__ Zs,

@@ -264,3 +264,26 @@ def test_bf16_psrf_matches_the_states_read_back():
         got = s.psrf(first, count)
         assert np.max(np.abs(got - want) / want) <= 1e-4, (first, count, np.max(np.abs(got - want) / want))
     s.close()
+
+
+def test_bf16_rewhitening_matches_fp64_solve():
+    """After a refresh, BF16 mode re-solves z = Lq^{-1}(x - x_ref) in FP32 (the states' precision): q of every
+    chain at the interval start agrees with the FP64 forward substitution on the same factor and states to
+    1e-5 relative (it is ~1e-6; the states themselves are FP32)."""
+    import scipy.linalg as sl
+    import paper_1506_05741_b300 as dm
+    d, P, nl = 512, 8, 16
+    ts = workloads.tanh_regression(d, 256, 42)
+    cfg = dm.default_config(d, P, n_lag=nl, beta0=0.3, seed=12, prec=dm.BF16, min_samples_refresh=30)
+    cfg["trace_steps"] = 5 * nl + 1
+    s = dm.Sampler(cfg, ts, x0=workloads.start_state(d, P, 5) * np.sqrt(ts.lam), C0=np.diag(ts.lam))
+    s.run(4 * nl)
+    x, _, _ = s.state()
+    s.run(1)                               # the interval start applies the new factor and re-whitens
+    _, Lq, xr, _ = s.factor()
+    assert s.stats()["refreshes"] >= 3
+    z = sl.solve_triangular(Lq, (x - xr).T, lower=True)
+    q64 = 0.5 * np.sum(z * z, axis=0)
+    qg = s.trace(4 * nl + 1)["q_cur"][4 * nl]
+    assert np.max(np.abs(qg - q64) / q64) <= 1e-5
+    s.close()
