@@ -14,8 +14,8 @@
 //     (|I| < 2^61), and subtracts I 2^(e_m + e_n - 54) with one FP64 fused multiply-add.
 // Terms with g >= 7 and the low bits of T_6 are dropped; their size, about 64 * 2^-56 |P_m| |P_n|, is that
 // of an FP64 GEMM's own rounding bound. Only one conversion and one FMA per output touch the FP64 pipe.
-// One CTA per 128 x 64 output tile keeps all 14 slice tiles in shared memory and the 7 group accumulators
-// in tensor memory (448 of its 512 columns).
+// One CTA per 128 x 32 output tile keeps the 7 B slices in shared memory, streams the 7 A slices through
+// two stages and holds the 7 group accumulators in tensor memory (224 of 256 columns); two CTAs share an SM.
 #include "linalg.h"
 #include "ozaki_slice.cuh"
 #include "tc_common.cuh"
@@ -23,7 +23,7 @@
 
 namespace diam {
 
-constexpr int OZ_BN = 64;
+constexpr int OZ_BN = 32;
 
 // One warp per operand row: exponent and the 7 BF16 slices (exact integers) of the row's 64 entries.
 __global__ void ozaki_slice_kernel(const double* __restrict__ P, int lda, int rows, uint16_t* __restrict__ SL,
@@ -37,8 +37,11 @@ __global__ void ozaki_slice_kernel(const double* __restrict__ P, int lda, int ro
 }
 
 // C[n][m] -= sum_k A[m][k] B[n][k] for m < Ma, n < Nb (and n >= m when lower), from the slices of A
-// (tensor map tmA, 128-row boxes) and of B (tmB, 64-row boxes).
-__global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_constant__ CUtensorMap tmA,
+// (tensor map tmA, 128-row boxes) and of B (tmB, 32-row boxes). A 128 x 32 tile per CTA: the 7 B slices stay
+// in shared memory, the A slices stream through a two-stage ring in slice order (slice a meets B slices
+// 0 .. 6 - a, so each group's first product comes with a = 0), the 7 groups take 224 tensor-memory columns.
+// With 60 KB of shared memory and 256 columns two CTAs share an SM, one's epilogue beside the other's loads.
+__global__ void __launch_bounds__(128, 2) ozaki_update_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB, int Ma, int Nb,
                                                               const int* __restrict__ exA, const int* __restrict__ exB,
                                                               double* __restrict__ Cm, int ldc, int lower,
@@ -46,10 +49,12 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr uint32_t A_BYTES = 128 * OZ_K * 2, B_BYTES = OZ_BN * OZ_K * 2;
-    uint8_t* sA = smem;                                 // 7 x 16 KB
-    uint8_t* sB = smem + OZ_S * A_BYTES;                // 7 x 8 KB
-    uint64_t* full = (uint64_t*)(smem + OZ_S * (A_BYTES + B_BYTES));
-    uint64_t* done = full + 1;
+    uint8_t* sB = smem;                                 // 7 x 4 KB
+    uint8_t* sA = smem + OZ_S * B_BYTES;                // 2 x 16 KB ring
+    uint64_t* fullB = (uint64_t*)(sA + 2 * A_BYTES);
+    uint64_t* fullA = fullB + 1;                        // 2
+    uint64_t* emptyA = fullA + 2;                       // 2
+    uint64_t* done = emptyA + 2;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -59,7 +64,11 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
     __shared__ int sex[OZ_BN];   // exponents of this tile's B rows
     if (threadIdx.x < OZ_BN) sex[threadIdx.x] = (n0 + (int)threadIdx.x < Nb) ? exB[n0 + threadIdx.x] : 0;
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(full), 1);
+        mbar_init(smem_u32(fullB), 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&fullA[s]), 1);
+            mbar_init(smem_u32(&emptyA[s]), 1);
+        }
         mbar_init(smem_u32(done), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -67,7 +76,7 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(512u));
+                     "r"(256u));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -76,26 +85,44 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        const uint32_t fb = smem_u32(full);
-        mbar_expect_tx(fb, OZ_S * (A_BYTES + B_BYTES));
+        // producer: the B slices, then the A slices through the ring
+        mbar_expect_tx(smem_u32(fullB), OZ_S * B_BYTES);
+        for (int b = 0; b < OZ_S; ++b) tma_load_2d(smem_u32(sB + b * B_BYTES), &tmB, smem_u32(fullB), b * OZ_K, n0);
+        int issued = 0;
         for (int a = 0; a < OZ_S; ++a) {
-            tma_load_2d(smem_u32(sA + a * A_BYTES), &tmA, fb, a * OZ_K, m0);
-            tma_load_2d(smem_u32(sB + a * B_BYTES), &tmB, fb, a * OZ_K, n0);
+            const int st = a & 1;
+            if (a >= 2 && !mbar_wait(smem_u32(&emptyA[st]), ((a >> 1) - 1) & 1, abort_flag)) break;
+            mbar_expect_tx(smem_u32(&fullA[st]), A_BYTES);
+            tma_load_2d(smem_u32(sA + st * A_BYTES), &tmA, smem_u32(&fullA[st]), a * OZ_K, m0);
+            issued = a + 1;
         }
-    } else if (warp == 1 && lane == 0) {
-        constexpr uint32_t idesc = idesc_bf16(OZ_BN);
-        if (mbar_wait(smem_u32(full), 0, abort_flag)) {
-            tc_fence_after();
-            for (int g = 0; g < OZ_S; ++g) {
-                for (int a = 0; a <= g; ++a) {
-                    const int b = g - a;
-                    const uint32_t pa = smem_u32(sA + a * A_BYTES), pb = smem_u32(sB + b * B_BYTES);
-#pragma unroll
-                    for (int kk = 0; kk < OZ_K / 16; ++kk)
-                        umma_bf16(tmem + (uint32_t)(g * OZ_BN), sdesc_sw128(pa + kk * 32), sdesc_sw128(pb + kk * 32),
-                                  idesc, (a | kk) ? 1u : 0u);
+        if (*abort_flag) {   // every issued copy lands before the CTA may exit (bounded)
+            for (int a = (issued > 2 ? issued - 2 : 0); a < issued; ++a) {
+                const long long t0 = clock64();
+                while (!mbar_try(smem_u32(&fullA[a & 1]), (a >> 1) & 1) && clock64() - t0 < TC_WAIT_CYCLES) {
                 }
             }
+            const long long t0 = clock64();
+            while (!mbar_try(smem_u32(fullB), 0) && clock64() - t0 < TC_WAIT_CYCLES) {
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: slice a of A against B slices 0 .. 6 - a, product (a, b) into group a + b
+        constexpr uint32_t idesc = idesc_bf16(OZ_BN);
+        bool ok = mbar_wait(smem_u32(fullB), 0, abort_flag);
+        for (int a = 0; ok && a < OZ_S; ++a) {
+            const int st = a & 1;
+            if (!mbar_wait(smem_u32(&fullA[st]), (a >> 1) & 1, abort_flag)) break;
+            tc_fence_after();
+            const uint32_t pa = smem_u32(sA + st * A_BYTES);
+            for (int b = 0; a + b < OZ_S; ++b) {
+                const uint32_t pb = smem_u32(sB + b * B_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < OZ_K / 16; ++kk)
+                    umma_bf16(tmem + (uint32_t)((a + b) * OZ_BN), sdesc_sw128(pa + kk * 32), sdesc_sw128(pb + kk * 32),
+                              idesc, (a | kk) ? 1u : 0u);
+            }
+            umma_commit(smem_u32(&emptyA[st]));   // the stage is free once these products are done
         }
         umma_commit(smem_u32(done));
     }
@@ -143,18 +170,14 @@ __global__ void __launch_bounds__(128, 1) ozaki_update_kernel(const __grid_const
             }
         }
     } else if (threadIdx.x == 0) {
-        set_status(status, DEV_TIMEOUT);
-        // the loads were issued on one barrier: let them land before the CTA exits (bounded)
-        long long t0 = clock64();
-        while (!mbar_try(smem_u32(full), 0) && clock64() - t0 < TC_WAIT_CYCLES) {
-        }
+        set_status(status, DEV_TIMEOUT);   // the producer has waited for its copies in flight
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u));
 }
 
-static size_t update_smem() { return 1024 + (size_t)OZ_S * (128 * OZ_K * 2 + OZ_BN * OZ_K * 2) + 256; }
+static size_t update_smem() { return 1024 + (size_t)OZ_S * OZ_BN * OZ_K * 2 + 2 * (size_t)128 * OZ_K * 2 + 256; }
 
 static cudaError_t launch_update(const uint16_t* SA, int Ma, const int* exA, const uint16_t* SB, int Nb,
                                  const int* exB, double* Cm, int ldc, int lower, int* status, cudaStream_t st) {
