@@ -4,14 +4,17 @@ Workload (tanh4096): Bayesian tanh regression, d = 4096, d_y = 2048, prior N(0, 
 N(0, 1/4096) in FP32, y = tanh(A x*) + 0.05 eps; P = 512 chains, n_lag = 128. A_0 = Cholesky of the prior
 covariance, x_0 drawn from the prior. One benchmark step = one interval of n_lag steps of all P chains
 (noise product, n_lag x (propose, screen, target, accept), moment fold, beta rule and the Cholesky refresh
-that is due every interval). With --refresh-delay 1 (default; the paper's lag-time between a refresh and its
-use) the factor built from interval k's moments drives interval k + 2 and its Cholesky runs on its own stream
-beside interval k + 1; the timed region still holds the K intervals' K refreshes. Arms, same workload and start:
+that is due every interval). With --refresh-delay D >= 1 (the paper's lag-time between a refresh and its use,
+Sec. "Computational introduction"; default D = 2, a lag of 2 n_lag = 256 steps at d = 4096) the factor built
+from interval k's moments drives interval k + 1 + D and its Cholesky runs on its own streams beside the
+following intervals (two at a time for D >= 2); the timed region still holds the K intervals' K refreshes.
+Arms, same workload and start:
   mixed_da  (the headline value): BF16 factor / noise / map on the tensor cores, FP32 states, FP64-accurate
             refresh and moment fold, plus delayed acceptance with the MLP surrogate 4096 -> 512 -> 512 -> 1
             trained on the GPU (first training once 2e4 exactly evaluated pairs are in the 2e5-pair ring,
             then every 20 synchronisations; stage 1 off while the held-out RMSE exceeds 0.5 nats);
   mixed     the same without the surrogate;
+  mixed_da_delay1    the headline arm with refresh_delay 1 (one factorisation beside the next interval);
   mixed_da_in_order  the headline arm with refresh_delay 0 (each factor used right after its refresh);
   fp64      the plain FP64 form (every kernel FP64, DFMA Cholesky).
 Metrics: chain-steps/s = P n_lag / device time of an interval (everything above included), and min-ESS/s =
@@ -49,10 +52,10 @@ def parse():
     ap.add_argument("--P", type=int, default=512)
     ap.add_argument("--n-lag", type=int, default=128)
     ap.add_argument("--no-da", action="store_true", help="headline arm without the surrogate")
-    ap.add_argument("--refresh-delay", type=int, default=1,
+    ap.add_argument("--refresh-delay", type=int, default=2,
                     help="interval k's factor drives interval k+1+delay (>= 1: its Cholesky runs beside interval k+1)")
     ap.add_argument("--in-order-steps", type=int, default=-1,
-                    help="timed intervals of the headline arm with refresh_delay 0 (-1: --steps, 0: skip)")
+                    help="timed intervals of the headline arm with refresh_delay 0 and 1 (-1: --steps, 0: skip)")
     ap.add_argument("--mixed-steps", type=int, default=-1, help="timed intervals of the mixed arm (-1: --steps, 0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed intervals of the plain FP64 arm (0: skip)")
     ap.add_argument("--fp64-warmup", type=int, default=1)
@@ -241,7 +244,9 @@ def roofline(prof, run, ts, pk, pk_src, acc_rate, ring, keep_sums):
         # the FP64 Cholesky d^3/3 flops, computed FP64-accurate on the BF16 tensor cores (Ozaki split: 28
         # slice products per rank-64 update) around a serial FP64 chain of diagonal blocks
         "refresh": ("alu", d ** 3 / 3.0, "TFLOP/s", FP64_PEAK_TFLOPS),
-        "xi_gemm": ("tensor", float(d) * d * N, "TFLOP/s", sus),             # lower-triangular A_n W, 2 d^2 N / 2
+        # lower-triangular A_n W (2 d^2 N / 2) and the map of the noise, (A A_n) W (2 d_y d N; its lo pass, a
+        # precision overhead, is not counted)
+        "xi_gemm": ("tensor", float(d) * d * N + 2.0 * dy * d * N, "TFLOP/s", sus),
         "fold": ("tensor", float(d) * d * N, "TFLOP/s", sus),                # SYRK of the interval, lower half
         "target": ("tensor", 2.0 * dy * d * P * 2, "TFLOP/s", sus),          # A x* with the hi + lo split
         # bytes: propose reads x, z, xi (FP32), writes x*, z* (FP32) and the BF16 hi / lo split of x*
@@ -306,7 +311,7 @@ def main():
     da = not args.no_da
     config = {"workload": f"tanh4096: d={ts.d}, d_y={ts.d_y}, P={run.P}, n_lag={run.n_lag}, BF16 factor/noise/map, "
                           f"FP32 states, FP64-accurate Cholesky refresh every interval"
-                          + (f" (used from the interval {1 + args.refresh_delay} after; factorised beside the next one)"
+                          + (f" (used from the interval {1 + args.refresh_delay} after; factorised beside the following ones)"
                              if args.refresh_delay > 0 else "")
                           + (", delayed acceptance with the 4096-512-512-1 MLP surrogate" if da else ""),
               "d": ts.d, "d_y": ts.d_y, "P": run.P, "n_lag": run.n_lag, "delayed_acceptance": da,
@@ -358,10 +363,11 @@ def main():
             arms["mixed"], _, _, _ = run_arm("mixed", run, ts, x0, C0, dm.BF16, False, args.warmup, msteps, torch,
                                              stream, dm, delay=args.refresh_delay)
         isteps = args.steps if args.in_order_steps < 0 else args.in_order_steps
-        if args.refresh_delay > 0 and isteps > 0:   # the same arm with each factor used right after its refresh
-            name = ("mixed_da" if da else "mixed") + "_in_order"
-            arms[name], _, _, _ = run_arm(name, run, ts, x0, C0, dm.BF16, da, args.warmup, isteps, torch, stream, dm,
-                                          delay=0)
+        for dly, suffix in ((1, "_delay1"), (0, "_in_order")):   # the same arm with shorter lags
+            if dly < args.refresh_delay and isteps > 0:
+                name = ("mixed_da" if da else "mixed") + suffix
+                arms[name], _, _, _ = run_arm(name, run, ts, x0, C0, dm.BF16, da, args.warmup, isteps, torch, stream,
+                                              dm, delay=dly)
         if args.fp64_steps > 0:
             arms["fp64"], _, _, _ = run_arm("fp64", run, ts, x0, C0, dm.FP64, False, args.fp64_warmup,
                                             args.fp64_steps, torch, stream, dm, delay=args.refresh_delay)

@@ -113,22 +113,23 @@ def test_bf16_refresh_and_moments_track_oracle():
     assert np.max(np.abs(cg - co)) <= 2e-2 * np.max(np.abs(co))
 
 
-def test_refresh_delay_applies_the_factor_where_the_oracle_does():
-    """refresh_delay = 1 in BF16 mode (graphs on, so each factorisation runs on its own stream beside the next
-    interval). The factor built from interval 0's moments drives the chains from interval 2 on: up to there
-    decisions and log-densities follow the oracle, and both re-whiten exactly at step 2 n_lag (q of the
-    current states stops being carried from the accepted proposals). Past that step the two factors come from
-    differently rounded moments (BF16 records with FP32 accumulation against FP64), so the trajectories are
-    not compared further."""
+@pytest.mark.parametrize("delay", [1, 2])
+def test_refresh_delay_applies_the_factor_where_the_oracle_does(delay):
+    """refresh_delay = 1 or 2 in BF16 mode (graphs on, so each factorisation runs on its own streams beside the
+    following intervals). The factor built from interval 0's moments drives the chains from interval 1 + delay
+    on: up to there decisions and log-densities follow the oracle, and both re-whiten exactly at step
+    (1 + delay) n_lag (q of the current states stops being carried from the accepted proposals). Past that step
+    the two factors come from differently rounded moments (BF16 records with FP32 accumulation against FP64),
+    so the trajectories are not compared further."""
     ts, P, nl = workloads.tanh_regression(256, 128, 37), 8, 16
-    steps = 3 * nl
+    steps = (2 + delay) * nl
     x0 = workloads.start_state(256, P, 5) * np.sqrt(ts.lam)
-    g, o = _bf16_pair(ts, P, steps, n_lag=nl, beta0=0.3, seed=21, min_samples_refresh=30, refresh_delay=1,
+    g, o = _bf16_pair(ts, P, steps, n_lag=nl, beta0=0.3, seed=21, min_samples_refresh=30, refresh_delay=delay,
                       x0=x0, C0=np.diag(ts.lam))
     g.run(steps)
     o.run(steps)
     tg, to = g.trace(steps), o.trace()
-    k = 2 * nl
+    k = (1 + delay) * nl
     assert np.array_equal(tg["acc"][:k], to["acc"][:k])
     sc = trace_scale(to)[:k]
     for key in ("lp_prop", "q_prop", "q_cur", "loga"):
@@ -137,7 +138,7 @@ def test_refresh_delay_applies_the_factor_where_the_oracle_does():
         carried = np.where(tr["acc"], tr["q_prop"], tr["q_cur"])   # q of each step's outcome
         assert np.array_equal(tr["q_cur"][1:k], carried[:k - 1])   # no factor change before step 2 n_lag
         assert np.all(np.abs(tr["q_cur"][k] - carried[k - 1]) > 1e-6 * np.abs(carried[k - 1]))   # re-whitened
-    assert g.stats()["refreshes"] == o.counts()["refreshes"] == 3
+    assert g.stats()["refreshes"] == o.counts()["refreshes"] == 2 + delay
 
 
 @pytest.mark.parametrize("delay", [1, 2])
