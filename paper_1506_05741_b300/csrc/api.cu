@@ -21,6 +21,7 @@
 #include "linalg.h"
 #include "step.cuh"
 #include "rec.cuh"
+#include "rewhiten.h"
 #include "tc_gemm.h"
 
 using namespace diam;
@@ -296,6 +297,12 @@ template <typename T>
 static diam_status rewhiten(diam_ctx* c) {
     const int d = c->d, P = c->P;
     int e0 = ph_begin(c, PH_REWHITEN);
+    if (c->bf && rewhiten_tc_fits(d, c->ldk)) {   // FP32 forward substitution, panel updates on the tensor cores
+        CK(rewhiten_tc(d, P, c->Lq16, c->ldk, (const float*)c->X, (const float*)c->xref, (float*)c->Z, c->q, inv_infl2(c),
+                       c->kind == TK_REF ? c->lp : nullptr, &c->ctl->status, c->st));
+        ph_end(c, e0);
+        return DIAM_OK;
+    }
     if (c->bf && rewhiten32_smem(d, 1) <= 220 * 1024) {   // FP32 forward substitution (reading G20)
         const int G = rewhiten32_group(d);
         { rewhiten32_kernel<<<(P + G - 1) / G, RW_THREADS, rewhiten32_smem(d, G), c->st>>>(
@@ -1268,6 +1275,8 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
     }
     diam_status s = alloc_all(c);
     if (s == DIAM_OK && c->bf && c->rec) s = fused_step(c, true);
+    if (s == DIAM_OK && c->bf && rewhiten_tc_fits(c->d, c->ldk) && rewhiten_tc_setup(c->d) != cudaSuccess)
+        s = fail(c, DIAM_ECUDA, "cudaFuncSetAttribute");
     if (s == DIAM_OK && c->bf && rewhiten32_smem(c->d, 1) <= 220 * 1024 &&
         cudaFuncSetAttribute(rewhiten32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rewhiten32_smem(c->d, rewhiten32_group(c->d))) != cudaSuccess)
