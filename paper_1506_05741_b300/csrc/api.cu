@@ -634,6 +634,22 @@ static diam_status do_step(diam_ctx* c) {
     return DIAM_OK;
 }
 
+// The fold's pass over the interval's FP32 records (BF16 mode): the 16-byte form where the sizes allow it.
+static diam_status fold_records(diam_ctx* c, int s0, uint16_t* HT, int ldt, int ntile, float* xs, float* xq) {
+    const int d = c->d, P = c->P, nl = c->nl, npb = (P + 31) / 32;
+    float* pb = HT ? c->psum + (size_t)ntile * d : nullptr;
+    float* ps = HT ? c->psum : nullptr;
+    if (d % 4 == 0 && c->ldh % 4 == 0 && P % 8 == 0) {
+        { fold_records4_kernel<<<dim3((d + 127) / 128, npb), 256, 0, c->st>>>((const float*)c->hist, c->ldh, P, nl, s0, d,
+                                                                           (const float*)c->cenT, HT, ldt, ps, pb, xs, xq); count_launch(); }
+    } else {
+        { fold_records_kernel<<<dim3((d + 31) / 32, npb), dim3(32, 8), 0, c->st>>>((const float*)c->hist, c->ldh, P, nl, s0, d,
+                                                                                (const float*)c->cenT, HT, ldt, ps, pb, xs, xq); count_launch(); }
+    }
+    CK(cudaGetLastError());
+    return DIAM_OK;
+}
+
 // Fold the samples of interval blk (those past the burn-in) into the pooled moments.
 template <typename T>
 static diam_status fold_block(diam_ctx* c, int64_t blk) {
@@ -647,9 +663,7 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
     float* xq = xs ? (float*)c->bm2 + (size_t)blk * P * d : nullptr;
     const int npb = (P + 31) / 32;
     if (rows <= 0) {
-        if (xs) { fold_records_kernel<<<dim3((d + 31) / 32, npb), dim3(32, 8), 0, c->st>>>((const float*)c->hist, c->ldh, P, nl, nl, d,
-                                                                                     (const float*)c->cenT, nullptr, 0, nullptr,
-                                                                                     nullptr, xs, xq); count_launch(); }
+        if (xs) CKS(fold_records(c, nl, nullptr, 0, 0, xs, xq));
         return DIAM_OK;
     }
     double nb = (double)rows;
@@ -661,9 +675,7 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
         // the centring terms, the interval mean from the FP32 records, and s16 for the lower-triangle SYRK on
         // the tensor cores, whose epilogue does the FP64 fold) and the per-chain interval sums
         const int ldt = ((int)rows + 63) / 64 * 64, ntile = (int)(nl - s0) * npb;
-        { fold_records_kernel<<<dim3((d + 31) / 32, npb), dim3(32, 8), 0, c->st>>>((const float*)c->hist, c->ldh, P, nl, (int)s0, d,
-                                                                                (const float*)c->cenT, c->histT, ldt, c->psum,
-                                                                                c->psum + (size_t)ntile * d, xs, xq); count_launch(); }
+        CKS(fold_records(c, (int)s0, c->histT, ldt, ntile, xs, xq));
         if (ldt > rows)   // the K padding of the SYRK operand
             CK(cudaMemset2DAsync(c->histT + rows, sizeof(uint16_t) * ldt, 0, sizeof(uint16_t) * (ldt - rows), d, c->st));
         { fold_sums_kernel<<<(d + 31) / 32, kThreads, 0, c->st>>>(d, ntile, c->psum, c->psum + (size_t)ntile * d, c->cen64,

@@ -864,6 +864,121 @@ __global__ void __launch_bounds__(256) fold_records_kernel(const float* __restri
     }
 }
 
+// fold_records_kernel with 16-byte loads: blocks of 32 chains x 128 coordinates (d, ldh multiples of 4, P a
+// multiple of 8, so every 8 chains' BF16 values of one coordinate are one 16-byte store of the transpose).
+// Thread (ty, tx) loads coordinates 4 tx .. 4 tx + 3 of chains ty + 8 k; the tile is kept chain-major in shared
+// memory and read across chains for the transposed stores. Same outputs as fold_records_kernel.
+__global__ void __launch_bounds__(256) fold_records4_kernel(const float* __restrict__ H, int ldh, int P, int nl, int s0,
+                                                            int d, const float* __restrict__ cen,
+                                                            uint16_t* __restrict__ HT, int ldt, float* __restrict__ psum,
+                                                            float* __restrict__ pbf, float* __restrict__ xs,
+                                                            float* __restrict__ xm2) {
+    __shared__ __align__(16) uint16_t tile[32][136];   // [chain][coordinate], 272-byte rows
+    __shared__ float sx[8][132], sb[8][132];
+    const int c0 = blockIdx.x * 128, p0 = blockIdx.y * 32;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int c = c0 + 4 * tx;
+    const bool cv = c < d;
+    float4 acc[4], acc2[4], cur[4], nxt[4];
+    auto load = [&](int st, float4* v) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int p = p0 + ty + 8 * k;
+            v[k] = (p < P && cv) ? *reinterpret_cast<const float4*>(H + ((size_t)st * P + p) * ldh + c)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        acc2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    load(0, cur);
+    for (int st = 0; st < nl; ++st) {
+        if (st + 1 < nl) load(st + 1, nxt);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[k].x += cur[k].x; acc[k].y += cur[k].y; acc[k].z += cur[k].z; acc[k].w += cur[k].w;
+            acc2[k].x = fmaf(cur[k].x, cur[k].x, acc2[k].x);
+            acc2[k].y = fmaf(cur[k].y, cur[k].y, acc2[k].y);
+            acc2[k].z = fmaf(cur[k].z, cur[k].z, acc2[k].z);
+            acc2[k].w = fmaf(cur[k].w, cur[k].w, acc2[k].w);
+        }
+        if (HT && st >= s0) {
+            float ax[4] = {0.f, 0.f, 0.f, 0.f}, ab[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float v[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
+                uint16_t b[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    b[j] = f32_to_bf16_bits(v[j]);
+                    ax[j] += v[j];
+                    ab[j] += bf16_bits_to_f32(b[j]);
+                }
+                *reinterpret_cast<uint2*>(&tile[ty + 8 * k][4 * tx]) =
+                    make_uint2((uint32_t)b[0] | ((uint32_t)b[1] << 16), (uint32_t)b[2] | ((uint32_t)b[3] << 16));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                sx[ty][4 * tx + j] = ax[j];
+                sb[ty][4 * tx + j] = ab[j];
+            }
+            __syncthreads();
+            const size_t tl = (size_t)(st - s0) * gridDim.y + blockIdx.y;
+            if (tid < 128 && c0 + tid < d) {
+                float tsx = 0.f, tsb = 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    tsx += sx[k][tid];
+                    tsb += sb[k][tid];
+                }
+                psum[tl * d + c0 + tid] = tsx;
+                pbf[tl * d + c0 + tid] = tsb;
+            }
+            {   // transposed stores: coordinate cc, chains 16 h .. 16 h + 15 as two 16-byte stores
+                const int cc = tid >> 1, h = tid & 1;
+                const size_t r0 = (size_t)(st - s0) * P + p0 + 16 * h;
+                if (c0 + cc < d) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (p0 + 16 * h + 8 * q < P) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                w[i] = (uint32_t)tile[16 * h + 8 * q + 2 * i][cc] |
+                                       ((uint32_t)tile[16 * h + 8 * q + 2 * i + 1][cc] << 16);
+                            *reinterpret_cast<uint4*>(HT + (size_t)(c0 + cc) * ldt + r0 + 8 * q) =
+                                make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+    }
+    if (xs && cv) {
+        const float4 cn = *reinterpret_cast<const float4*>(cen + c);
+        const float fn = (float)nl;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int p = p0 + ty + 8 * k;
+            if (p < P) {
+                *reinterpret_cast<float4*>(xs + (size_t)p * d + c) =
+                    make_float4(acc[k].x + fn * cn.x, acc[k].y + fn * cn.y, acc[k].z + fn * cn.z, acc[k].w + fn * cn.w);
+                if (xm2)
+                    *reinterpret_cast<float4*>(xm2 + (size_t)p * d + c) =
+                        make_float4(fmaxf(0.f, acc2[k].x - acc[k].x * acc[k].x / (float)nl),
+                                    fmaxf(0.f, acc2[k].y - acc[k].y * acc[k].y / (float)nl),
+                                    fmaxf(0.f, acc2[k].z - acc[k].z * acc[k].z / (float)nl),
+                                    fmaxf(0.f, acc2[k].w - acc[k].w * acc[k].w / (float)nl));
+            }
+        }
+    }
+}
+
 // Potential scale reduction factor of eq. (winco), (btwco), (psrf) over the intervals [b0, b0 + nb) of the
 // per-chain interval sums (n = nb n_lag samples per chain). Stage 1, thread (p, i): the window's mean of
 // chain p and its scatter, the intervals combined pairwise (Chan, Golub & LeVeque 1979); q holds per interval
