@@ -14,8 +14,8 @@
 //     (|I| < 2^61), and subtracts I 2^(e_m + e_n - 54) with one FP64 fused multiply-add.
 // Terms with g >= 7 and the low bits of T_6 are dropped; their size, about 64 * 2^-56 |P_m| |P_n|, is that
 // of an FP64 GEMM's own rounding bound. Only one conversion and one FMA per output touch the FP64 pipe.
-// One CTA per 128 x 32 output tile keeps the 7 B slices in shared memory, streams the 7 A slices through
-// two stages and holds the 7 group accumulators in tensor memory (224 of 256 columns); two CTAs share an SM.
+// One CTA per 128 x 16 output tile keeps the 7 B slices in shared memory, streams the 7 A slices through
+// two stages and holds the 7 group accumulators in tensor memory (112 of 128 columns); four CTAs share an SM.
 #include "linalg.h"
 #include "ozaki_slice.cuh"
 #include "tc_common.cuh"
@@ -23,7 +23,7 @@
 
 namespace diam {
 
-constexpr int OZ_BN = 32;
+constexpr int OZ_BN = 16, OZ_TMEM = 128;   // tile width; tensor-memory columns (7 x 16 used)
 
 // One warp per operand row: exponent and the 7 BF16 slices (exact integers) of the row's 64 entries.
 __global__ void ozaki_slice_kernel(const double* __restrict__ P, int lda, int rows, uint16_t* __restrict__ SL,
@@ -37,11 +37,11 @@ __global__ void ozaki_slice_kernel(const double* __restrict__ P, int lda, int ro
 }
 
 // C[n][m] -= sum_k A[m][k] B[n][k] for m < Ma, n < Nb (and n >= m when lower), from the slices of A
-// (tensor map tmA, 128-row boxes) and of B (tmB, 32-row boxes). A 128 x 32 tile per CTA: the 7 B slices stay
+// (tensor map tmA, 128-row boxes) and of B (tmB, 16-row boxes). A 128 x 16 tile per CTA: the 7 B slices stay
 // in shared memory, the A slices stream through a two-stage ring in slice order (slice a meets B slices
-// 0 .. 6 - a, so each group's first product comes with a = 0), the 7 groups take 224 tensor-memory columns.
-// With 60 KB of shared memory and 256 columns two CTAs share an SM, one's epilogue beside the other's loads.
-__global__ void __launch_bounds__(128, 2) ozaki_update_kernel(const __grid_constant__ CUtensorMap tmA,
+// 0 .. 6 - a, so each group's first product comes with a = 0), the 7 groups take 112 tensor-memory columns.
+// With 47 KB of shared memory and 128 columns four CTAs share an SM, their epilogues beside others' loads.
+__global__ void __launch_bounds__(128, 4) ozaki_update_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB, int Ma, int Nb,
                                                               const int* __restrict__ exA, const int* __restrict__ exB,
                                                               double* __restrict__ Cm, int ldc, int lower,
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(const __grid_const
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(256u));
+                     "r"((uint32_t)OZ_TMEM));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -137,36 +137,35 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(const __grid_const
         const bool vm = m < Ma;
         const int em = vm ? exA[m] : 0;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int c = 0; c < OZ_BN / 32; ++c) {
-            // issue this chunk's 32 loads of C first: their latency hides behind the tensor-memory reads
-            double cv[32];
+        {
+            // issue the tile's 16 loads of C first: their latency hides behind the tensor-memory reads
+            double cv[OZ_BN];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int n = n0 + c * 32 + j;
+            for (int j = 0; j < OZ_BN; ++j) {
+                const int n = n0 + j;
                 cv[j] = (vm && n < Nb && (!lower || n >= m)) ? Cm[(size_t)n * ldc + m] : 0.0;
             }
-            long long acc[32];
+            long long acc[OZ_BN];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] = 0;
+            for (int j = 0; j < OZ_BN; ++j) acc[j] = 0;
 #pragma unroll 1
             for (int g = 0; g < OZ_S; ++g) {
-                uint32_t r[32];
-                tmem_ld32(trow + (uint32_t)(g * OZ_BN + c * 32), r);
+                uint32_t r[OZ_BN];
+                tmem_ld16(trow + (uint32_t)(g * OZ_BN), r);
                 if (g < OZ_S - 1) {
                     const int sh = 40 - 8 * g;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(r[j])) * (1ll << sh);
+                    for (int j = 0; j < OZ_BN; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(r[j])) * (1ll << sh);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[j] += (long long)(__float2int_rn(__uint_as_float(r[j])) >> 8);
+                    for (int j = 0; j < OZ_BN; ++j) acc[j] += (long long)(__float2int_rn(__uint_as_float(r[j])) >> 8);
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int n = n0 + c * 32 + j;
+            for (int j = 0; j < OZ_BN; ++j) {
+                const int n = n0 + j;
                 if (vm && n < Nb && (!lower || n >= m))
-                    Cm[(size_t)n * ldc + m] = fma(-(double)acc[j], pow2(em + sex[c * 32 + j] - 54), cv[j]);
+                    Cm[(size_t)n * ldc + m] = fma(-(double)acc[j], pow2(em + sex[j] - 54), cv[j]);
             }
         }
     } else if (threadIdx.x == 0) {
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(const __grid_const
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)OZ_TMEM));
 }
 
 static size_t update_smem() { return 1024 + (size_t)OZ_S * OZ_BN * OZ_K * 2 + 2 * (size_t)128 * OZ_K * 2 + 256; }
