@@ -500,7 +500,7 @@ static void launch_fused_step(diam_ctx* c, bool setup) {
     }
     step_rec_kernel<NV, NM, VEC, STAGE><<<c->P, FUSED_THREADS, smem, c->st>>>(
         c->d, c->P, c->nl, c->dy, c->ctl, c->key, c->tg, inv_infl2(c), (float*)c->X, (float*)c->Z,
-        (const float*)c->Xi, (const uint16_t*)c->W, c->ldw, (const float*)c->xref, (const float*)c->cenT, c->Ax,
+        (const float*)c->Xi, (const uint16_t*)c->W, c->ldw, (const float*)c->xref, c->Ax,
         c->axref, c->AXi, c->y32, (float)(1.0 / (2.0 * c->sigma * c->sigma)), c->kind == TK_TANH, c->lp, c->q,
         c->accf, c->tr, (float*)c->hist, c->ldh, nullptr, keep ? c->lpsum : nullptr,
         a ? a->cnt : nullptr, a ? a->ring_x : nullptr, a ? a->ring_lp : nullptr, a ? (long long)a->cfg.ring : 1,

@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(256) finish_linear_kernel(int P, int dy, int n
     }
 }
 
-// Select / record, grid (P, chunks): x, z <- x*, z* for accepted chains; the centred post-step state
+// Select / record, grid (P, chunks): x, z <- x*, z* for accepted chains; the post-step state (centred in FP64
+// mode)
 // x_{n+1} - c goes to the interval record (moment fold) and to the per-chain interval sums.
 template <typename T, typename HT>
 __device__ __forceinline__ HT to_hist(T v);
@@ -388,8 +389,7 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
                     *reinterpret_cast<float4*>(x + i) = v;
                     *reinterpret_cast<float4*>(z + i) = *reinterpret_cast<const float4*>(zp + i);
                 }
-                const float4 cv = *reinterpret_cast<const float4*>(cen + i);
-                *reinterpret_cast<float4*>(h + i) = make_float4(v.x - cv.x, v.y - cv.y, v.z - cv.z, v.w - cv.w);
+                *reinterpret_cast<float4*>(h + i) = v;   // BF16 mode: the fold subtracts the centre
                 if (bs) {   // BF16 mode keeps the per-chain interval sums in FP32 (128-step sums, ~1e-5 relative)
                     float4 b = *reinterpret_cast<float4*>(bs + i);
                     *reinterpret_cast<float4*>(bs + i) = make_float4(b.x + v.x, b.y + v.y, b.z + v.z, b.w + v.w);
@@ -404,7 +404,10 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
             x[i] = v;
             z[i] = zp[i];
         }
-        if (h) h[i] = to_hist<T, HT>(v - cen[i]);
+        if (h) {   // FP64 mode records x - c; BF16 mode records x (its fold subtracts c in FP32)
+            if constexpr (std::is_same<HT, float>::value) h[i] = (float)v;
+            else h[i] = to_hist<T, HT>(v - cen[i]);
+        }
         if (bs) bs[i] += (HT)v;
         if (bq) bq[i] += (HT)v * (HT)v;
     }
@@ -434,12 +437,13 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
 //   x* = x_ref + rho (x - x_ref) + xi,  z* = rho z + beta alpha W   (eq. (diamnl), z-recursion)
 //   u  = rho (A x) + (1 - rho) (A x_ref) + A xi                     (the map of x*, A xi from the interval GEMM)
 //   log pi(x*) = prior terms of x* + likelihood terms of u,  q* = |z*|^2 / (2 alpha^2)
-// then the Metropolis-Hastings test of Algorithm 1, x, z, A x <- x*, z*, u when accepted, the centred record
-// row, the interval sums and, with a surrogate attached, the (bf16(x*), likelihood terms) training pair in
+// then the Metropolis-Hastings test of Algorithm 1, x, z, A x <- x*, z*, u when accepted, the record row (the
+// post-step state; the fold centres it), the log pi sums and, with a surrogate attached, the (bf16(x*),
+// likelihood terms) training pair in
 // ring slot head + p. The last block to finish moves the step counters (and the ring head) on.
-// Only x* and u stay in registers across the test; the second pass reads x (rejected) or z and W (accepted,
-// z* recomputed by the same fused multiply-add) again, from L2 (or the staged rows). Sums are FP32, one tree
-// per block.
+// Only x*, u and W stay in registers across the test; the second pass reads x (rejected) or z (accepted, z*
+// recomputed by the same fused multiply-add) again, from the staged rows (or L2), and issues no other load.
+// Sums are FP32, one tree per block.
 // Element layout of thread tid: VEC (d, d_y multiples of 4): entries 4 (tid + g FT) + j of group g < NV (NM);
 // otherwise entries tid + (4 g + j) FT. So d <= 4 NV FT and d_y <= 4 NM FT.
 // STAGE (with VEC): the chain's x, z and xi rows (12 d bytes of dynamic shared memory) arrive by three bulk
@@ -451,7 +455,7 @@ template <int NV, int NM, bool VEC, bool STAGE = false>
 __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     int d, int P, int nl, int dy, Ctl* ctl, Key key, TargetDev tg, double inv_infl2,
     float* __restrict__ X, float* __restrict__ Z, const float* __restrict__ Xi, const uint16_t* __restrict__ W, int ldw,
-    const float* __restrict__ xref, const float* __restrict__ cen, float* __restrict__ Ax,
+    const float* __restrict__ xref, float* __restrict__ Ax,
     const float* __restrict__ axref, const float* __restrict__ AXi, const float* __restrict__ y32, float inv2s2,
     int tanh_mode, double* lp, double* q, int8_t* accf, TraceDev tr, float* __restrict__ hist_base, int ldh,
     float* __restrict__ bsum_base, double* __restrict__ lpsum_base, DaCounters* dacnt, uint16_t* __restrict__ ring_x,
@@ -565,16 +569,19 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     }
 
     float xs[4 * NV];
+    uint2 wreg[NV];   // VEC: this thread's W, kept for z* of an accepted chain
 #pragma unroll
     for (int g = 0; g < NV; ++g) {
         if (VEC) {
             const int i = idx(g, 0);
+            wreg[g] = make_uint2(0u, 0u);
             if (i < d) {
                 const float4 xr = *reinterpret_cast<const float4*>(xref + i);
                 const float4 xa = *reinterpret_cast<const float4*>(xsrc + i);
                 const float4 za = *reinterpret_cast<const float4*>(zsrc + i);
                 const float4 ia = *reinterpret_cast<const float4*>(isrc + i);
                 const uint2 wb = *reinterpret_cast<const uint2*>(w + i);
+                wreg[g] = wb;
                 const float r4[4] = {xr.x, xr.y, xr.z, xr.w}, x4[4] = {xa.x, xa.y, xa.z, xa.w};
                 const float z4[4] = {za.x, za.y, za.z, za.w}, i4[4] = {ia.x, ia.y, ia.z, ia.w};
                 const float w4[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
@@ -657,7 +664,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                 float v[4];
                 if (a) {
                     const float4 za = *reinterpret_cast<const float4*>(zsrc + i);
-                    const uint2 wb = *reinterpret_cast<const uint2*>(w + i);
+                    const uint2 wb = wreg[g];
                     const float z4[4] = {za.x, za.y, za.z, za.w};
                     const float w4[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
                                          bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
@@ -673,10 +680,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                     const float4 xa = *reinterpret_cast<const float4*>(xsrc + i);
                     v[0] = xa.x; v[1] = xa.y; v[2] = xa.z; v[3] = xa.w;
                 }
-                if (h) {
-                    const float4 cv = *reinterpret_cast<const float4*>(cen + i);
-                    *reinterpret_cast<float4*>(h + i) = make_float4(v[0] - cv.x, v[1] - cv.y, v[2] - cv.z, v[3] - cv.w);
-                }
+                if (h) *reinterpret_cast<float4*>(h + i) = make_float4(v[0], v[1], v[2], v[3]);
                 if (bs) {
                     const float4 b = *reinterpret_cast<const float4*>(bs + i);
                     *reinterpret_cast<float4*>(bs + i) = make_float4(b.x + v[0], b.y + v[1], b.z + v[2], b.w + v[3]);
@@ -700,7 +704,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                     } else {
                         v = x[i];
                     }
-                    if (h) h[i] = v - cen[i];
+                    if (h) h[i] = v;
                     if (bs) bs[i] += v;
                     if (rx) rx[i] = f32_to_bf16_bits(xs[4 * g + j]);
                 }
@@ -784,13 +788,14 @@ __global__ void fold_prep_kernel(int d, int nparts, const double* __restrict__ p
     delta[i] = (cen64[i] + v * inb) - mean[i];
 }
 
-// The interval's FP32 records (row s P + p: step s < n_lag, chain p < P; stride ldh), read once by blocks of
+// The interval's FP32 records of x (row s P + p: step s < n_lag, chain p < P; stride ldh), centred here by
+// c (cen) as they are read, once, by blocks of
 // 32 chains x 32 coordinates that walk the interval's steps (the next step's records loaded ahead):
 //   - rows of the steps s >= s0 (past the burn-in): their BF16 transpose HT[c][(s - s0) P + p] (the SYRK
 //     operand) and, per (step, chain block) tile, the FP32 sums of the records and of their BF16 values
 //     (psum, pbf: tile (s - s0) gridDim.y + blockIdx.y, d entries each); HT == nullptr skips this part;
-//   - xs != nullptr: every chain's sum over all n_lag steps, xs[p][c] = sum_s H + n_lag cen[c] (the records
-//     are x - cen), the per-interval, per-chain sums of x, and its scatter about its interval mean,
+//   - xs != nullptr: every chain's sum over all n_lag steps, xs[p][c] = sum_s (H - cen[c]) + n_lag cen[c],
+//     the per-interval, per-chain sums of x, and its scatter about its interval mean,
 //     xm2[p][c] = sum_s H^2 - (sum_s H)^2 / n_lag (the PSRF's within-chain terms).
 __global__ void __launch_bounds__(256) fold_records_kernel(const float* __restrict__ H, int ldh, int P, int nl, int s0,
                                                            int d, const float* __restrict__ cen,
@@ -803,11 +808,12 @@ __global__ void __launch_bounds__(256) fold_records_kernel(const float* __restri
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c = c0 + tx;
     float acc[4] = {0.f, 0.f, 0.f, 0.f}, acc2[4] = {0.f, 0.f, 0.f, 0.f}, cur[4], nxt[4];
-    auto load = [&](int st, float* v) {
+    const float cc0 = c < d ? cen[c] : 0.f;
+    auto load = [&](int st, float* v) {   // the centred record x - c
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int p = p0 + ty + 8 * k;
-            v[k] = (p < P && c < d) ? H[((size_t)st * P + p) * ldh + c] : 0.f;
+            v[k] = (p < P && c < d) ? H[((size_t)st * P + p) * ldh + c] - cc0 : 0.f;
         }
     };
     load(0, cur);
@@ -880,12 +886,17 @@ __global__ void __launch_bounds__(256) fold_records4_kernel(const float* __restr
     const int c = c0 + 4 * tx;
     const bool cv = c < d;
     float4 acc[4], acc2[4], cur[4], nxt[4];
-    auto load = [&](int st, float4* v) {
+    const float4 cc4 = cv ? *reinterpret_cast<const float4*>(cen + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    auto load = [&](int st, float4* v) {   // the centred records x - c
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int p = p0 + ty + 8 * k;
-            v[k] = (p < P && cv) ? *reinterpret_cast<const float4*>(H + ((size_t)st * P + p) * ldh + c)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p < P && cv) {
+                const float4 r = *reinterpret_cast<const float4*>(H + ((size_t)st * P + p) * ldh + c);
+                v[k] = make_float4(r.x - cc4.x, r.y - cc4.y, r.z - cc4.z, r.w - cc4.w);
+            } else {
+                v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
     };
 #pragma unroll
