@@ -63,7 +63,68 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-phase profile pass (roofline)")
+    ap.add_argument("--convergence", action="store_true",
+                    help="instead of the throughput bench: samples and device time to convergence on a dense Gaussian "
+                         "of known covariance, over n_lag (Sec. 3.3)")
+    ap.add_argument("--conv-d", type=int, default=128)
+    ap.add_argument("--conv-P", type=int, default=256)
+    ap.add_argument("--conv-tol-mean", type=float, default=0.02, help="|m_n - mu|_2 (the n_lag tuning criterion)")
+    ap.add_argument("--conv-tol-cov", type=float, default=0.05, help="|C_n - Sigma|_F / |Sigma|_F")
+    ap.add_argument("--conv-max-steps", type=int, default=100000)
     return ap.parse_args()
+
+
+def convergence(args):
+    """Sec. 3.3's experiment on the GPU sampler: dense Gaussian N(0, Sigma), Sigma = Q diag(1/i) Q^T, chains
+    started over-dispersed; for n_lag in {d/100, d/10, d/4, d/2, d, 2d, 4d}, the chain-steps (P x steps) and the
+    device time until the pooled mean is within tol_mean of the truth (Euclidean norm: the paper's criterion for
+    tuning n_lag) and until the pooled covariance is within tol_cov of Sigma (relative Frobenius norm: the paper's
+    stopping criterion, there with TOL = 1e-3). BF16 mode, refresh in order (refresh_delay 0). One JSON line."""
+    import torch
+    import paper_1506_05741_b300 as dm
+    import workloads
+    d, P = args.conv_d, args.conv_P
+    ts = workloads.dense_gaussian(d, 1000 + d)
+    nS = float(np.linalg.norm(ts.cov))
+    x0 = workloads.start_state(d, P, 3) @ np.linalg.cholesky(ts.cov).T * 3.0
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rows = []
+    for frac in (0.01, 0.1, 0.25, 0.5, 1.0, 2.0, 4.0):
+        nl = max(1, int(round(frac * d)))
+        cfg = dm.default_config(d, P, n_lag=nl, seed=17, prec=dm.BF16, refresh_delay=0)
+        s = dm.Sampler(cfg, ts, x0=x0, stream=stream.cuda_stream)
+        chunk = max(nl, (2048 // nl) * nl)   # whole intervals, about 2048 steps a check
+        steps, dev_s = 0, 0.0
+        hit = {"mean": None, "cov": None}
+        while steps < args.conv_max_steps and (hit["mean"] is None or hit["cov"] is None):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.run(chunk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dev_s += e0.elapsed_time(e1) / 1e3
+            steps += chunk
+            m, C, n = s.moments()
+            em = float(np.linalg.norm(m - ts.mean))
+            ec = float(np.linalg.norm(C - ts.cov)) / nS
+            for key, err, tol in (("mean", em, args.conv_tol_mean), ("cov", ec, args.conv_tol_cov)):
+                if hit[key] is None and err <= tol:
+                    hit[key] = {"chain_steps": steps * P, "device_s": round(dev_s, 4), "error": round(err, 5)}
+        st = s.stats()
+        s.close()
+        rows.append({"n_lag": nl, "n_lag_over_d": frac, "to_mean_tol": hit["mean"], "to_cov_tol": hit["cov"],
+                     "steps_run": steps, "final_mean_error": round(em, 5), "final_cov_error": round(ec, 5),
+                     "device_s": round(dev_s, 3), "accept_rate": round(st["accepted"] / max(1, st["steps"] * P), 4),
+                     "beta": round(st["beta"], 4), "refreshes": st["refreshes"]})
+        print(json.dumps({"n_lag": nl, "done": rows[-1]}), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "chain-steps and device seconds to convergence (Sec. 3.3), dense Gaussian",
+                      "config": {"workload": f"dense Gaussian d={d}, Sigma = Q diag(1/i) Q^T, P={P}, BF16 mode, "
+                                             f"refresh in order, starts 3x over-dispersed",
+                                 "tol_mean": args.conv_tol_mean, "tol_cov_rel_frobenius": args.conv_tol_cov,
+                                 "max_steps": args.conv_max_steps},
+                      "rows": rows}), flush=True)
 
 
 def peaks():
@@ -302,6 +363,9 @@ def cpu_leg(run, ts, x0, C0, seconds, cores):
 
 def main():
     args = parse()
+    if args.convergence:
+        convergence(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
