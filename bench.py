@@ -41,6 +41,7 @@ sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.25   # B300 nominal FP64 (vector and tensor), the profiling recipe's figure
+OZ_PRODUCTS = 28          # BF16 slice products per FP64 product in the Ozaki-split updates (7 slices, a + b <= 6)
 
 
 def parse():
@@ -289,22 +290,22 @@ def run_arm(name, run, ts, x0, C0, prec, da, W, K, torch, stream, dm, clocks_ind
     return out, dt, launches, clk
 
 
-def roofline(prof, run, ts, pk, pk_src, acc_rate, ring, keep_sums):
+def roofline(prof, run, ts, pk, pk_src, ring):
     """Per-phase achieved rate against its bound, from the profiled intervals; the dominant phase first."""
     d, dy, P, nl = ts.d, ts.d_y, run.P, run.n_lag
-    # the fused step (one launch): reads x, z, xi (FP32), W (BF16), A x and A xi (FP32); writes the FP32 record
-    # row, x, z and A x of the accepted chains, the BF16 ring row of every proposal (surrogate attached) and
-    # the interval sums (read + write, when kept)
-    step_bytes = (P * d * (4 + 4 + 4 + 2 + 4) + acc_rate * P * d * (4 + 4) + P * dy * (4 + 4) + acc_rate * P * dy * 4
-                  + (P * d * 2 if ring else 0) + (P * d * 8 if keep_sums else 0))
+    # the interval kernel (one launch walks every chain through the interval's n_lag steps): per step it reads
+    # the chain's xi (FP32), W (BF16) and A xi (FP32) rows and writes the FP32 record row and, with the
+    # surrogate attached, the BF16 ring row; x, z and A x are read and written once per interval
+    step_bytes = (nl * P * (d * (4 + 2 + 4) + dy * 4 + (d * 2 if ring else 0)) + 2 * P * (d * (4 + 4) + dy * 4))
     N = P * nl
     sus = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
     # algorithmic work per launch of each phase (a launch = one step, or one interval for noise / xi / fold /
     # refresh / rewhiten / train)
     work = {
-        # the FP64 Cholesky d^3/3 flops, computed FP64-accurate on the BF16 tensor cores (Ozaki split: 28
-        # slice products per rank-64 update) around a serial FP64 chain of diagonal blocks
-        "refresh": ("alu", d ** 3 / 3.0, "TFLOP/s", FP64_PEAK_TFLOPS),
+        # the FP64 Cholesky (d^3/3 flops) is computed FP64-accurate on the BF16 tensor cores: its rank-64
+        # updates issue 28 BF16 slice products per FP64 product (Ozaki split), around a serial FP64 chain of
+        # diagonal blocks; the work counted is the tensor work issued
+        "refresh": ("tensor", OZ_PRODUCTS * d ** 3 / 3.0, "TFLOP/s", sus),
         # lower-triangular A_n W (2 d^2 N / 2) and the map of the noise, (A A_n) W (2 d_y d N; its lo pass, a
         # precision overhead, is not counted)
         "xi_gemm": ("tensor", float(d) * d * N + 2.0 * dy * d * N, "TFLOP/s", sus),
@@ -315,7 +316,9 @@ def roofline(prof, run, ts, pk, pk_src, acc_rate, ring, keep_sums):
         # accept reads x*, z* and writes x, z and the FP32 record row
         "accept": ("hbm", P * d * (4 + 4 + 4 + 4 + 4), "GB/s", pk["hbm_gbs"]),
         "noise": ("hbm", N * d * 2, "GB/s", pk["hbm_gbs"]),                  # BF16 W for the interval
-        "rewhiten": ("alu", float(d) * d * P, "TFLOP/s", FP64_PEAK_TFLOPS),  # the triangular re-solve
+        # the triangular re-solve: its panel products issue 16 tensor-core columns per 4 chains (each chain's
+        # solution split into 3 BF16 terms), 2 (d^2 / 2) 16 (P / 4) flops
+        "rewhiten": ("tensor", 4.0 * d * d * P, "TFLOP/s", sus),
         "screen": ("tensor", 2.0 * P * (d * 512 + 512 * 512), "TFLOP/s", sus),
         "step": ("hbm", step_bytes, "GB/s", pk["hbm_gbs"]),
     }
@@ -336,10 +339,14 @@ def roofline(prof, run, ts, pk, pk_src, acc_rate, ring, keep_sums):
            "peak_source": ("nominal FP64 of the profiling recipe" if t["bound"] == "alu" else pk_src + " (sustained)"
                            if t["bound"] == "tensor" else pk_src),
            "phases": table}
-    if t["bound"] == "alu":
-        out["note"] = ("FP64-equivalent work (d^3/3 for the factorisation, d^2 P for the re-solve) of an FP64-accurate "
-                       "computation whose rank-64 updates run on the BF16 tensor cores (Ozaki split); what remains is a "
-                       "latency-bound chain of 64 diagonal blocks, so the fraction of the FP64 pipe exceeds 1")
+    if "refresh" in table:   # the same factorisation counted as FP64 work against the FP64 figure
+        r = table["refresh"]
+        r["fp64_equivalent_tflops"] = round(r["achieved"] / OZ_PRODUCTS, 3)
+        r["fp64_nominal_tflops"] = FP64_PEAK_TFLOPS
+    if dom == "refresh":
+        out["note"] = ("BF16 tensor work issued by the FP64-accurate factorisation (28 slice products per FP64 product "
+                       "of its rank-64 updates); the factorisation is a latency-bound chain of 64 diagonal blocks and "
+                       "runs beside the next intervals (refresh_delay 2), so the tensor pipe is mostly idle")
     return out
 
 
@@ -444,7 +451,7 @@ def main():
             sp.run(max(2, args.steps // 2) * run.n_lag)
             prof = sp.profile()
             sp.close()
-            roof = roofline(prof, run, ts, pk, pk_src, head["accept_rate"], da, False)
+            roof = roofline(prof, run, ts, pk, pk_src, da)
 
         # ---- end to end through the public API with host buffers: init (target, start state and surrogate
         # weights uploaded from host memory), K intervals each followed by a read of log pi, then the pooled

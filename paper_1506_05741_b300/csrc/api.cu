@@ -526,6 +526,51 @@ static void fused_step_nv(diam_ctx* c, bool setup) {
     else if (!STAGE) fused_step_nm<8, VEC, false>(c, setup);
 }
 
+// A whole interval of every chain in one launch (interval_rec_kernel): the fused step's conditions, the
+// 16-byte layout, and x, z, A x of one chain in shared memory.
+static bool interval_kernel_fits(const diam_ctx* c) {
+    const bool vec = (c->d % 4) == 0 && (c->dy % 4) == 0 && (c->ldw % 4) == 0 && (c->ldh % 4) == 0 && (c->ldk % 4) == 0;
+    return fused_step_fits(c) && vec && sizeof(float) * (2 * (size_t)c->d + c->dy) <= 128 * 1024;
+}
+
+template <int NV, int NM>
+static void launch_interval(diam_ctx* c, int ns, bool setup) {
+    DaState* a = c->da;
+    const bool keep = c->cfg.keep_block_sums != 0;
+    const size_t smem = sizeof(float) * (2 * (size_t)c->d + c->dy);
+    if (setup) {   // outside any capture
+        cudaFuncSetAttribute(interval_rec_kernel<NV, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return;
+    }
+    interval_rec_kernel<NV, NM><<<c->P, FUSED_THREADS, smem, c->st>>>(
+        c->d, c->P, c->nl, c->dy, ns, c->ctl, c->key, c->tg, inv_infl2(c), (float*)c->X, (float*)c->Z,
+        (const float*)c->Xi, (const uint16_t*)c->W, c->ldw, (const float*)c->xref, c->Ax, c->axref, c->AXi, c->y32,
+        (float)(1.0 / (2.0 * c->sigma * c->sigma)), c->kind == TK_TANH, c->lp, c->q, c->accf, c->tr, (float*)c->hist,
+        c->ldh, keep ? c->lpsum : nullptr, a ? a->cnt : nullptr, a ? a->ring_x : nullptr, a ? a->ring_lp : nullptr,
+        a ? (long long)a->cfg.ring : 1, c->ldk);
+    count_launch();
+}
+
+template <int NV>
+static void interval_nm(diam_ctx* c, int ns, bool setup) {
+    const int nm = (c->dy + 4 * FUSED_THREADS - 1) / (4 * FUSED_THREADS);
+    if (nm <= 1) launch_interval<NV, 1>(c, ns, setup);
+    else if (nm <= 2) launch_interval<NV, 2>(c, ns, setup);
+    else if (nm <= 4) launch_interval<NV, 4>(c, ns, setup);
+    else launch_interval<NV, 8>(c, ns, setup);
+}
+
+// ns steps of every chain, from the current step, all inside one interval (setup: prepare the kernel only).
+static diam_status interval_steps(diam_ctx* c, int ns, bool setup = false) {
+    const int nv = (c->d + 4 * FUSED_THREADS - 1) / (4 * FUSED_THREADS);
+    if (nv <= 1) interval_nm<1>(c, ns, setup);
+    else if (nv <= 2) interval_nm<2>(c, ns, setup);
+    else if (nv <= 4) interval_nm<4>(c, ns, setup);
+    else interval_nm<8>(c, ns, setup);
+    CK(cudaGetLastError());
+    return DIAM_OK;
+}
+
 // setup: only prepare the kernel this context will launch (at init, outside any graph capture).
 static diam_status fused_step(diam_ctx* c, bool setup = false) {
     const bool vec = (c->d % 4) == 0 && (c->dy % 4) == 0 && (c->ldw % 4) == 0 && (c->ldh % 4) == 0 && (c->ldk % 4) == 0;
@@ -956,7 +1001,13 @@ static diam_status run_steps(diam_ctx* c, int64_t n_steps) {
         if (c->xi_block != blk) CKS(prepare_block<T>(c, blk, c->st));
         CKS(ensure_bsum(c, blk));
         const bool whole = s == 0 && n_steps >= c->nl && c->cfg.graphs && c->kind != TK_CALLBACK && !c->cfg.profile;
-        if (whole) {
+        if (s == 0 && n_steps >= c->nl && c->cfg.graphs && interval_kernel_fits(c)) {
+            int e = ph_begin(c, PH_STEP);
+            CKS(interval_steps(c, c->nl));
+            ph_end(c, e);
+            c->t += c->nl;
+            n_steps -= c->nl;
+        } else if (whole) {
             CKS(interval_graph<T>(c));
             c->t += c->nl;
             n_steps -= c->nl;
@@ -1287,6 +1338,7 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
     }
     diam_status s = alloc_all(c);
     if (s == DIAM_OK && c->bf && c->rec) s = fused_step(c, true);
+    if (s == DIAM_OK && interval_kernel_fits(c)) s = interval_steps(c, 0, true);
     if (s == DIAM_OK && c->bf && rewhiten_tc_fits(c->d, c->ldk) && rewhiten_tc_setup(c->d) != cudaSuccess)
         s = fail(c, DIAM_ECUDA, "cudaFuncSetAttribute");
     if (s == DIAM_OK && c->bf && rewhiten32_smem(c->d, 1) <= 220 * 1024 &&

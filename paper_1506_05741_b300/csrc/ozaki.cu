@@ -14,8 +14,9 @@
 //     (|I| < 2^61), and subtracts I 2^(e_m + e_n - 54) with one FP64 fused multiply-add.
 // Terms with g >= 7 and the low bits of T_6 are dropped; their size, about 64 * 2^-56 |P_m| |P_n|, is that
 // of an FP64 GEMM's own rounding bound. Only one conversion and one FMA per output touch the FP64 pipe.
-// One CTA per 128 x 16 output tile keeps the 7 B slices in shared memory, streams the 7 A slices through
-// two stages and holds the 7 group accumulators in tensor memory (112 of 128 columns); four CTAs share an SM.
+// A CTA keeps the 7 B slices of a 16-row tile in shared memory and walks a run of 128-row tiles of A, whose
+// slices stream through a four-stage ring; slice a of A meets B slices 0 .. 6 - a in one product of width
+// 16 (7 - a), and the 7 group accumulators of a tile fill one of two tensor-memory buffers.
 #include "linalg.h"
 #include "ozaki_slice.cuh"
 #include "tc_common.cuh"
@@ -23,7 +24,7 @@
 
 namespace diam {
 
-constexpr int OZ_BN = 16, OZ_TMEM = 128;   // tile width; tensor-memory columns (7 x 16 used)
+constexpr int OZ_BN = 16, OZ_TMEM = 256;   // tile width; tensor-memory columns (two buffers of 7 x 16)
 
 // One warp per operand row: exponent and the 7 BF16 slices (exact integers) of the row's 64 entries.
 __global__ void ozaki_slice_kernel(const double* __restrict__ P, int lda, int rows, uint16_t* __restrict__ SL,
@@ -36,45 +37,105 @@ __global__ void ozaki_slice_kernel(const double* __restrict__ P, int lda, int ro
     if (lane == 0) ex[row] = e;
 }
 
+// Work units of the update: one 16-row tile of B (n0 .. n0 + 15) with a run of 128-row tiles of A
+// (mt0 .. mt1 - 1), at most ch of them. With lower, A tile mt takes part only if 128 mt <= n0 + 15; the
+// n-tiles come in groups of eight with the same number of A tiles (g + 1 for group g, up to the last A tile).
+// Unit u counts from the largest units down, so the longest-running CTAs start first.
+struct OzUnit {
+    int n0, mt0, mt1;
+};
+
+__host__ __device__ inline int oz_units(int Ma, int Nb, int lower, int ch, int u, OzUnit* w) {
+    const int NT = (Nb + OZ_BN - 1) / OZ_BN, MT = (Ma + 127) / 128;
+    int total = 0;
+    if (!lower) {
+        const int nch = (MT + ch - 1) / ch;
+        total = NT * nch;
+        if (w && u < total) {
+            const int v = total - 1 - u, nt = v / nch, c = v % nch;
+            *w = OzUnit{nt * OZ_BN, c * ch, min(MT, c * ch + ch)};
+        }
+        return total;
+    }
+    for (int g = 0; 8 * g < NT; ++g) total += min(8, NT - 8 * g) * ((min(MT, g + 1) + ch - 1) / ch);
+    if (w && u < total) {
+        int v = total - 1 - u;
+        for (int g = 0; 8 * g < NT; ++g) {
+            const int cnt = min(MT, g + 1), nch = (cnt + ch - 1) / ch, units = min(8, NT - 8 * g) * nch;
+            if (v < units) {
+                const int nt = 8 * g + v / nch, c = v % nch;
+                *w = OzUnit{nt * OZ_BN, c * ch, min(cnt, c * ch + ch)};
+                break;
+            }
+            v -= units;
+        }
+    }
+    return total;
+}
+
+constexpr int OZ_STAGES = 4;            // A slices in flight
+constexpr int OZ_THREADS = 192;         // warp 0: TMA, warp 1: MMA issue, warps 2-5: epilogue
+constexpr uint32_t OZ_ABYTES = 128 * OZ_K * 2, OZ_BBYTES = OZ_BN * OZ_K * 2;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // C[n][m] -= sum_k A[m][k] B[n][k] for m < Ma, n < Nb (and n >= m when lower), from the slices of A
-// (tensor map tmA, 128-row boxes) and of B (tmB, 16-row boxes). A 128 x 16 tile per CTA: the 7 B slices stay
-// in shared memory, the A slices stream through a two-stage ring in slice order (slice a meets B slices
-// 0 .. 6 - a, so each group's first product comes with a = 0), the 7 groups take 112 tensor-memory columns.
-// With 47 KB of shared memory and 128 columns four CTAs share an SM, their epilogues beside others' loads.
-__global__ void __launch_bounds__(128, 4) ozaki_update_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                              const __grid_constant__ CUtensorMap tmB, int Ma, int Nb,
-                                                              const int* __restrict__ exA, const int* __restrict__ exB,
-                                                              double* __restrict__ Cm, int ldc, int lower,
-                                                              int* status) {
+// (tensor map tmA, 128-row boxes) and of B (tmB, 16-row boxes). One CTA per work unit: the 7 B slices of
+// its n-tile stay in shared memory; the A slices of its m-tiles stream through a four-stage ring in slice
+// order (slice a meets B slices 0 .. 6 - a in one product, so each group's first product comes with a = 0);
+// each tile's 7 group accumulators take 112 columns of one of two tensor-memory buffers (128 columns apart),
+// so the epilogue of one tile overlaps the products of the next. The epilogue warps read a tile's groups, release
+// its buffer, then combine and subtract. With 78 KB of shared memory and 256 columns two CTAs share an SM.
+__global__ void __launch_bounds__(OZ_THREADS, 2) ozaki_update_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                     const __grid_constant__ CUtensorMap tmB, int Ma,
+                                                                     int Nb, const int* __restrict__ exA,
+                                                                     const int* __restrict__ exB,
+                                                                     double* __restrict__ Cm, int ldc, int lower,
+                                                                     int ch, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr uint32_t A_BYTES = 128 * OZ_K * 2, B_BYTES = OZ_BN * OZ_K * 2;
-    uint8_t* sB = smem;                                 // 7 x 4 KB
-    uint8_t* sA = smem + OZ_S * B_BYTES;                // 2 x 16 KB ring
-    uint64_t* fullB = (uint64_t*)(sA + 2 * A_BYTES);
-    uint64_t* fullA = fullB + 1;                        // 2
-    uint64_t* emptyA = fullA + 2;                       // 2
-    uint64_t* done = emptyA + 2;
+    uint8_t* sB = smem;                                  // 7 x 2 KB
+    uint8_t* sA = smem + OZ_S * OZ_BBYTES;               // OZ_STAGES x 16 KB
+    uint64_t* fullB = (uint64_t*)(sA + OZ_STAGES * OZ_ABYTES);
+    uint64_t* fullA = fullB + 1;                         // OZ_STAGES
+    uint64_t* emptyA = fullA + OZ_STAGES;                // OZ_STAGES
+    uint64_t* tfull = emptyA + OZ_STAGES;                // 2: a tile's accumulators are complete
+    uint64_t* tempty = tfull + 2;                        // 2: the epilogue has read them
+    uint64_t* done = tempty + 2;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-
-    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * OZ_BN;
-    if ((lower && n0 + OZ_BN - 1 < m0) || n0 >= Nb || m0 >= Ma) return;   // nothing of this tile is updated
+    __shared__ OzUnit su;
+    __shared__ int sex[OZ_BN];   // exponents of the n-tile's B rows
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ int sex[OZ_BN];   // exponents of this tile's B rows
+    if (threadIdx.x == 0) {
+        OzUnit w{0, 0, 0};
+        oz_units(Ma, Nb, lower, ch, blockIdx.x, &w);
+        su = w;
+    }
+    __syncthreads();
+    const OzUnit w = su;
+    const int ntiles = w.mt1 - w.mt0;
+    if (ntiles <= 0) return;
+    const int n0 = w.n0;
     if (threadIdx.x < OZ_BN) sex[threadIdx.x] = (n0 + (int)threadIdx.x < Nb) ? exB[n0 + threadIdx.x] : 0;
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(fullB), 1);
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < OZ_STAGES; ++s) {
             mbar_init(smem_u32(&fullA[s]), 1);
             mbar_init(smem_u32(&emptyA[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull[b]), 1);
+            mbar_init(smem_u32(&tempty[b]), 4);   // one arrival per epilogue warp
         }
         mbar_init(smem_u32(done), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"((uint32_t)OZ_TMEM));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -83,23 +144,25 @@ __global__ void __launch_bounds__(128, 4) ozaki_update_kernel(const __grid_const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const int nq = ntiles * OZ_S;   // A slices of the unit, in order (tile i, slice a) -> q = 7 i + a
 
     if (warp == 0 && lane == 0) {
-        // producer: the B slices, then the A slices through the ring
-        mbar_expect_tx(smem_u32(fullB), OZ_S * B_BYTES);
-        for (int b = 0; b < OZ_S; ++b) tma_load_2d(smem_u32(sB + b * B_BYTES), &tmB, smem_u32(fullB), b * OZ_K, n0);
+        // producer: the B slices, then every A slice of the unit through the ring
+        mbar_expect_tx(smem_u32(fullB), OZ_S * OZ_BBYTES);
+        for (int b = 0; b < OZ_S; ++b) tma_load_2d(smem_u32(sB + b * OZ_BBYTES), &tmB, smem_u32(fullB), b * OZ_K, n0);
         int issued = 0;
-        for (int a = 0; a < OZ_S; ++a) {
-            const int st = a & 1;
-            if (a >= 2 && !mbar_wait(smem_u32(&emptyA[st]), ((a >> 1) - 1) & 1, abort_flag)) break;
-            mbar_expect_tx(smem_u32(&fullA[st]), A_BYTES);
-            tma_load_2d(smem_u32(sA + st * A_BYTES), &tmA, smem_u32(&fullA[st]), a * OZ_K, m0);
-            issued = a + 1;
+        for (int q = 0; q < nq; ++q) {
+            const int st = q % OZ_STAGES;
+            if (q >= OZ_STAGES && !mbar_wait(smem_u32(&emptyA[st]), ((q / OZ_STAGES) - 1) & 1, abort_flag)) break;
+            mbar_expect_tx(smem_u32(&fullA[st]), OZ_ABYTES);
+            tma_load_2d(smem_u32(sA + st * OZ_ABYTES), &tmA, smem_u32(&fullA[st]), (q % OZ_S) * OZ_K,
+                        (w.mt0 + q / OZ_S) * 128);
+            issued = q + 1;
         }
         if (*abort_flag) {   // every issued copy lands before the CTA may exit (bounded)
-            for (int a = (issued > 2 ? issued - 2 : 0); a < issued; ++a) {
+            for (int q = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); q < issued; ++q) {
                 const long long t0 = clock64();
-                while (!mbar_try(smem_u32(&fullA[a & 1]), (a >> 1) & 1) && clock64() - t0 < TC_WAIT_CYCLES) {
+                while (!mbar_try(smem_u32(&fullA[q % OZ_STAGES]), (q / OZ_STAGES) & 1) && clock64() - t0 < TC_WAIT_CYCLES) {
                 }
             }
             const long long t0 = clock64();
@@ -107,44 +170,51 @@ __global__ void __launch_bounds__(128, 4) ozaki_update_kernel(const __grid_const
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: slice a of A against B slices 0 .. 6 - a, product (a, b) into group a + b
-        constexpr uint32_t idesc = idesc_bf16(OZ_BN);
+        // MMA issuer: tile i into buffer i & 1; slice a of A against B slices 0 .. 6 - a as one product of
+        // width 16 (7 - a): the B slices lie one after another with the same 1024-byte group stride, and block b
+        // of the result lands in columns 16 (a + b) of the buffer, the accumulator of group a + b
         bool ok = mbar_wait(smem_u32(fullB), 0, abort_flag);
-        for (int a = 0; ok && a < OZ_S; ++a) {
-            const int st = a & 1;
-            if (!mbar_wait(smem_u32(&fullA[st]), (a >> 1) & 1, abort_flag)) break;
+        for (int i = 0; ok && i < ntiles; ++i) {
+            const int buf = i & 1;
+            if (i >= 2 && !mbar_wait(smem_u32(&tempty[buf]), ((i >> 1) - 1) & 1, abort_flag)) break;
             tc_fence_after();
-            const uint32_t pa = smem_u32(sA + st * A_BYTES);
-            for (int b = 0; a + b < OZ_S; ++b) {
-                const uint32_t pb = smem_u32(sB + b * B_BYTES);
+            const uint32_t tb = tmem + (uint32_t)(buf * 128);
+            for (int a = 0; a < OZ_S; ++a) {
+                const int q = i * OZ_S + a, st = q % OZ_STAGES;
+                if (!mbar_wait(smem_u32(&fullA[st]), (q / OZ_STAGES) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t pa = smem_u32(sA + st * OZ_ABYTES), pb = smem_u32(sB);
+                const uint32_t idesc = idesc_bf16(OZ_BN * (OZ_S - a));
 #pragma unroll
                 for (int kk = 0; kk < OZ_K / 16; ++kk)
-                    umma_bf16(tmem + (uint32_t)((a + b) * OZ_BN), sdesc_sw128(pa + kk * 32), sdesc_sw128(pb + kk * 32),
-                              idesc, (a | kk) ? 1u : 0u);
+                    umma_bf16(tb + (uint32_t)(a * OZ_BN), sdesc_sw128(pa + kk * 32), sdesc_sw128(pb + kk * 32), idesc,
+                              (a | kk) ? 1u : 0u);
+                umma_commit(smem_u32(&emptyA[st]));   // the stage is free once these products are done
             }
-            umma_commit(smem_u32(&emptyA[st]));   // the stage is free once these products are done
+            if (ok) umma_commit(smem_u32(&tfull[buf]));
         }
-        umma_commit(smem_u32(done));
-    }
-    __syncwarp();
-    mbar_wait(smem_u32(done), 0, abort_flag);
-    __syncthreads();
-    const bool ok = (*abort_flag == 0);
-    tc_fence_after();
-    if (ok) {
-        const int row = warp * 32 + lane;
-        const int m = m0 + row;
-        const bool vm = m < Ma;
-        const int em = vm ? exA[m] : 0;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        {
-            // issue the tile's 16 loads of C first: their latency hides behind the tensor-memory reads
+        umma_commit(smem_u32(done));   // arrives once every product issued here has completed
+    } else if (warp >= 2) {
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31, i.e. rows of the A tile
+        const int rq = warp & 3, row = rq * 32 + lane;
+        for (int i = 0; i < ntiles; ++i) {
+            const int m = (w.mt0 + i) * 128 + row;
+            const bool vm = m < Ma;
+            const int em = vm ? exA[m] : 0;
+            // the tile's 16 loads of C first: their latency hides behind the wait and the tensor-memory reads
             double cv[OZ_BN];
 #pragma unroll
             for (int j = 0; j < OZ_BN; ++j) {
                 const int n = n0 + j;
                 cv[j] = (vm && n < Nb && (!lower || n >= m)) ? Cm[(size_t)n * ldc + m] : 0.0;
             }
+            const int buf = i & 1;
+            if (!mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1, abort_flag)) break;
+            tc_fence_after();
+            const uint32_t trow = tmem + (uint32_t)(buf * 128) + ((uint32_t)(rq * 32) << 16);
             long long acc[OZ_BN];
 #pragma unroll
             for (int j = 0; j < OZ_BN; ++j) acc[j] = 0;
@@ -161,6 +231,9 @@ __global__ void __launch_bounds__(128, 4) ozaki_update_kernel(const __grid_const
                     for (int j = 0; j < OZ_BN; ++j) acc[j] += (long long)(__float2int_rn(__uint_as_float(r[j])) >> 8);
                 }
             }
+            tc_fence_before();   // the buffer goes back to the MMA issuer
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
 #pragma unroll
             for (int j = 0; j < OZ_BN; ++j) {
                 const int n = n0 + j;
@@ -168,15 +241,24 @@ __global__ void __launch_bounds__(128, 4) ozaki_update_kernel(const __grid_const
                     Cm[(size_t)n * ldc + m] = fma(-(double)acc[j], pow2(em + sex[j] - 54), cv[j]);
             }
         }
-    } else if (threadIdx.x == 0) {
-        set_status(status, DEV_TIMEOUT);   // the producer has waited for its copies in flight
     }
+    __syncwarp();
+    {   // no thread leaves before the products it depends on are complete (bounded)
+        const long long t0 = clock64();
+        while (!mbar_try(smem_u32(done), 0) && clock64() - t0 < TC_WAIT_CYCLES) {
+        }
+    }
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) set_status(status, DEV_TIMEOUT);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)OZ_TMEM));
+    tc_fence_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)OZ_TMEM));
 }
 
-static size_t update_smem() { return 1024 + (size_t)OZ_S * OZ_BN * OZ_K * 2 + 2 * (size_t)128 * OZ_K * 2 + 256; }
+static size_t update_smem() {
+    return 1024 + (size_t)OZ_S * OZ_BBYTES + (size_t)OZ_STAGES * OZ_ABYTES + (OZ_STAGES * 2 + 6) * 8 + 16;
+}
 
 static cudaError_t launch_update(const uint16_t* SA, int Ma, const int* exA, const uint16_t* SB, int Nb,
                                  const int* exB, double* Cm, int ldc, int lower, int* status, cudaStream_t st) {
@@ -189,8 +271,11 @@ static cudaError_t launch_update(const uint16_t* SA, int Ma, const int* exA, con
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid((Ma + 127) / 128, (Nb + OZ_BN - 1) / OZ_BN);
-    { ozaki_update_kernel<<<grid, 128, update_smem(), st>>>(mA, mB, Ma, Nb, exA, exB, Cm, ldc, lower, status); count_launch(); }
+    // A tiles per unit: about four units per SM over the whole update (two resident at a time), at most 8
+    const int tiles = oz_units(Ma, Nb, lower, 1, 0, nullptr);
+    const int ch = std::max(1, std::min(8, tiles / (4 * 148)));
+    const int units = oz_units(Ma, Nb, lower, ch, 0, nullptr);
+    { ozaki_update_kernel<<<units, OZ_THREADS, update_smem(), st>>>(mA, mB, Ma, Nb, exA, exB, Cm, ldc, lower, ch, status); count_launch(); }
     return cudaGetLastError();
 }
 

@@ -430,6 +430,29 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
     }
 }
 
+// The test of Algorithm 1 in the fused kernels, from the block's three FP32 sums (|z*|^2, the prior terms,
+// the likelihood terms of the map): log pi(x*) = prior + likelihood, q* = |z*|^2 / (2 alpha^2),
+// log a = log pi(x*) + q* - log pi(x) - q(x). log u < log a is decided as in FP64: the FP32 log of u (within
+// 1e-5 of log u: u's rounding to FP32 and a few ulps of logf, |log u| <= 37) decides unless log a lies within
+// 1e-4 of it; then the FP64 log does. Writes the trace entry of (t, p) when it is kept.
+__device__ __forceinline__ int rec_test(float sq, float sl, float sm, double inv_infl2, double lpc, double qc, double u,
+                                        float lu32, long long t, int p, int P, const TraceDev& tr, double& lmap,
+                                        double& lpp, double& qpp, bool& finite) {
+    lmap = (double)sm;
+    lpp = (double)sl + lmap;
+    qpp = 0.5 * (double)sq * inv_infl2;
+    const double loga = lpp - lpc + qpp - qc;
+    finite = isfinite(lpp) && isfinite(qpp);
+    const double l32 = (double)lu32;
+    int a = 0;
+    if (finite) a = loga > l32 + 1e-4 ? 1 : loga < l32 - 1e-4 ? 0 : (log(u) < loga);
+    if (t < tr.steps) {
+        const size_t k = (size_t)t * P + p;
+        tr.lp[k] = lpp; tr.q[k] = qpp; tr.qc[k] = qc; tr.loga[k] = loga; tr.acc[k] = (int8_t)a;
+    }
+    return a;
+}
+
 // ---------------------------------------------------------------------------------------------------
 // One whole step of every chain in one launch, for a target whose expensive term is a linear map carried
 // through the proposal (BF16 mode; no surrogate screen in force). Block p holds chain p's proposal from the
@@ -626,19 +649,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
         a1 = warp_sum(a1);
         a2 = warp_sum(a2);
         if (lane == 0) {
-            const double lmap = (double)a2;
-            const double lpp = (double)a1 + lmap, qpp = 0.5 * (double)a0 * inv_infl2;
-            const double loga = lpp - s_lpc + qpp - s_qc;
-            const bool finite = isfinite(lpp) && isfinite(qpp);
-            // log u < log a as in FP64: the FP32 log of u (within 1e-5 of log u: u's rounding to FP32 and a few
-            // ulps of logf, |log u| <= 37) decides unless log a is within 1e-4 of it; then the FP64 log does
-            const double l32 = (double)s_lu32;
-            int a = 0;
-            if (finite) a = loga > l32 + 1e-4 ? 1 : loga < l32 - 1e-4 ? 0 : (log(s_u) < loga);
-            if (t < tr.steps) {
-                const size_t k = (size_t)t * P + p;
-                tr.lp[k] = lpp; tr.q[k] = qpp; tr.qc[k] = s_qc; tr.loga[k] = loga; tr.acc[k] = (int8_t)a;
-            }
+            double lmap, lpp, qpp;
+            bool finite;
+            const int a = rec_test(a0, a1, a2, inv_infl2, s_lpc, s_qc, s_u, s_lu32, t, p, P, tr, lmap, lpp, qpp, finite);
             if (a) {
                 lp[p] = lpp;
                 q[p] = qpp;
@@ -740,6 +753,247 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
             }
             ctl->t_cur += 1;
             ctl->s_cur += 1;
+            ctl->done_blocks = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// ns consecutive steps of chain p in one block (the steps of step_rec_kernel, in the same arithmetic). Within
+// an interval the chains share nothing that changes: the factor, x_ref, rho, beta alpha and the interval's
+// noise W, its product xi and the map of xi are fixed before the first step (Algorithm 1 changes the factor
+// only between intervals). So each block walks its chain through the steps on its own, x, z and A x held in
+// shared memory throughout: per step it reads the chain's xi, W and A xi rows and writes the record row (and
+// the ring row); the state, log pi and q go back to memory after the last step, and the last block to finish
+// moves the counters on by ns. No block waits on another, so the blocks drift apart and the loads of some
+// overlap the reductions and tests of others. The caller keeps steps s0 .. s0 + ns - 1 inside one interval.
+// VEC layout (entries 4 (tid + g FT) + j); dynamic shared memory (2 d + d_y) floats: x, z, A x.
+template <int NV, int NM>
+__global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
+    int d, int P, int nl, int dy, int ns, Ctl* ctl, Key key, TargetDev tg, double inv_infl2,
+    float* __restrict__ X, float* __restrict__ Z, const float* __restrict__ Xi, const uint16_t* __restrict__ W, int ldw,
+    const float* __restrict__ xref, float* __restrict__ Ax, const float* __restrict__ axref,
+    const float* __restrict__ AXi, const float* __restrict__ y32, float inv2s2, int tanh_mode, double* lp, double* q,
+    int8_t* accf, TraceDev tr, float* __restrict__ hist_base, int ldh, double* __restrict__ lpsum_base,
+    DaCounters* dacnt, uint16_t* __restrict__ ring_x, float* __restrict__ ring_lp, long long ring_cap, int ldk) {
+    constexpr int FT = FUSED_THREADS;
+    extern __shared__ float4 ival_smem[];
+    __shared__ float red[3][FT / 32];
+    __shared__ double s_u;
+    __shared__ float s_lu32;
+    __shared__ int s_acc;
+    const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const float rho = (float)ctl->rho, ba = (float)ctl->ba, om = (float)(1.0 - ctl->rho);
+    const int s0 = ctl->s_cur;
+    const long long t0 = ctl->t_cur;
+    const long long head0 = dacnt ? dacnt->head : 0;
+    float* sx = reinterpret_cast<float*>(ival_smem);
+    float* sz = sx + d;
+    float* su = sz + d;
+    const bool prior = tg.kind == TK_TANH;
+    auto idx = [&](int g) { return 4 * (tid + g * FT); };
+    // the chain's state: every thread loads (and later stores) only its own entries, so no barrier is needed
+#pragma unroll
+    for (int g = 0; g < NV; ++g) {
+        const int i = idx(g);
+        if (i < d) {
+            *reinterpret_cast<float4*>(sx + i) = *reinterpret_cast<const float4*>(X + (size_t)p * d + i);
+            *reinterpret_cast<float4*>(sz + i) = *reinterpret_cast<const float4*>(Z + (size_t)p * d + i);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NM; ++g) {
+        const int m = idx(g);
+        if (m < dy) *reinterpret_cast<float4*>(su + m) = *reinterpret_cast<const float4*>(Ax + (size_t)p * dy + m);
+    }
+    // thread 0 carries log pi(x), q(x), the interval's log pi sum and the counts from step to step (in shared
+    // memory: registers of every thread would hold them otherwise)
+    __shared__ double lpc, qc, lps;
+    __shared__ unsigned long long nacc, nnf;
+    __shared__ int a_last;
+    const size_t lps_at = (size_t)(t0 / nl) * P + p;
+    if (tid == 0) {
+        lpc = lp[p];
+        qc = q[p];
+        lps = lpsum_base ? lpsum_base[lps_at] : 0.0;
+        nacc = 0;
+        nnf = 0;
+        a_last = 0;
+    }
+    auto map_term = [&](float u, float yv, float& mf) {
+        if (tanh_mode) {
+            const float r = yv - tanhf(u);
+            mf -= r * r * inv2s2;
+        } else {
+            mf -= 0.5f * u * u;
+        }
+    };
+    for (int k = 0; k < ns; ++k) {
+        const int s = s0 + k;
+        const long long t = t0 + k;
+        const size_t row = (size_t)s * P + p;
+        const float* xi = Xi + row * d;
+        const uint16_t* w = W + row * ldw;
+        const float* axi = AXi + row * dy;
+        if (tid == FT - 32) {   // u and its FP32 log, off the path of the sums
+            const double u = uniform53(key, t, (uint32_t)p, TAG_U);
+            s_u = u;
+            s_lu32 = logf((float)u);
+        }
+        float qf = 0.f, lf = 0.f, mf = 0.f;
+        float uv[4 * NM];
+#pragma unroll
+        for (int g = 0; g < NM; ++g) {
+            const int m = idx(g);
+            if (m < dy) {
+                const float4 a4 = *reinterpret_cast<const float4*>(su + m);
+                const float4 r4 = *reinterpret_cast<const float4*>(axref + m);
+                const float4 i4 = *reinterpret_cast<const float4*>(axi + m);
+                const float4 y4 = tanh_mode ? *reinterpret_cast<const float4*>(y32 + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+                uv[4 * g] = fmaf(rho, a4.x, fmaf(om, r4.x, i4.x));
+                uv[4 * g + 1] = fmaf(rho, a4.y, fmaf(om, r4.y, i4.y));
+                uv[4 * g + 2] = fmaf(rho, a4.z, fmaf(om, r4.z, i4.z));
+                uv[4 * g + 3] = fmaf(rho, a4.w, fmaf(om, r4.w, i4.w));
+                map_term(uv[4 * g], y4.x, mf);
+                map_term(uv[4 * g + 1], y4.y, mf);
+                map_term(uv[4 * g + 2], y4.z, mf);
+                map_term(uv[4 * g + 3], y4.w, mf);
+            }
+        }
+        float xs[4 * NV];
+        uint2 wreg[NV];
+#pragma unroll
+        for (int g = 0; g < NV; ++g) {
+            const int i = idx(g);
+            wreg[g] = make_uint2(0u, 0u);
+            if (i < d) {
+                const float4 xr = *reinterpret_cast<const float4*>(xref + i);
+                const float4 xa = *reinterpret_cast<const float4*>(sx + i);
+                const float4 za = *reinterpret_cast<const float4*>(sz + i);
+                const float4 ia = *reinterpret_cast<const float4*>(xi + i);
+                const uint2 wb = *reinterpret_cast<const uint2*>(w + i);
+                wreg[g] = wb;
+                const float r4[4] = {xr.x, xr.y, xr.z, xr.w}, x4[4] = {xa.x, xa.y, xa.z, xa.w};
+                const float z4[4] = {za.x, za.y, za.z, za.w}, i4[4] = {ia.x, ia.y, ia.z, ia.w};
+                const float w4[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
+                                     bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
+                    const float zs = fmaf(rho, z4[j], ba * w4[j]);
+                    qf += zs * zs;
+                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i + j];
+                }
+            }
+        }
+        qf = warp_sum(qf);
+        lf = warp_sum(lf);
+        mf = warp_sum(mf);
+        if (lane == 0) {
+            red[0][wid] = qf;
+            red[1][wid] = lf;
+            red[2][wid] = mf;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            float a0 = lane < FT / 32 ? red[0][lane] : 0.f;
+            float a1 = lane < FT / 32 ? red[1][lane] : 0.f;
+            float a2 = lane < FT / 32 ? red[2][lane] : 0.f;
+            a0 = warp_sum(a0);
+            a1 = warp_sum(a1);
+            a2 = warp_sum(a2);
+            if (lane == 0) {
+                double lmap, lpp, qpp;
+                bool finite;
+                const int a = rec_test(a0, a1, a2, inv_infl2, lpc, qc, s_u, s_lu32, t, p, P, tr, lmap, lpp, qpp, finite);
+                if (a) {
+                    lpc = lpp;
+                    qc = qpp;
+                    ++nacc;
+                }
+                if (!finite) ++nnf;
+                if (ring_x) ring_lp[(head0 + (long long)k * P + p) % ring_cap] = (float)lmap;
+                lps += lpc;   // log pi after the step: log pi(x*) if accepted, else log pi(x)
+                s_acc = a;
+                a_last = a;
+            }
+        }
+        __syncthreads();
+        const int a = s_acc;
+        float* h = hist_base ? hist_base + row * ldh : nullptr;
+        uint16_t* rx = ring_x ? ring_x + (size_t)((head0 + (long long)k * P + p) % ring_cap) * ldk : nullptr;
+#pragma unroll
+        for (int g = 0; g < NV; ++g) {
+            const int i = idx(g);
+            if (i < d) {
+                float v[4];
+                if (a) {
+                    const float4 za = *reinterpret_cast<const float4*>(sz + i);
+                    const uint2 wb = wreg[g];
+                    const float z4[4] = {za.x, za.y, za.z, za.w};
+                    const float w4[4] = {bf16_bits_to_f32((uint16_t)(wb.x & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.x >> 16)),
+                                         bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
+                    float zn[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        v[j] = xs[4 * g + j];
+                        zn[j] = fmaf(rho, z4[j], ba * w4[j]);
+                    }
+                    *reinterpret_cast<float4*>(sx + i) = make_float4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<float4*>(sz + i) = make_float4(zn[0], zn[1], zn[2], zn[3]);
+                } else {
+                    const float4 xa = *reinterpret_cast<const float4*>(sx + i);
+                    v[0] = xa.x; v[1] = xa.y; v[2] = xa.z; v[3] = xa.w;
+                }
+                if (h) *reinterpret_cast<float4*>(h + i) = make_float4(v[0], v[1], v[2], v[3]);
+                if (rx) {
+                    const uint32_t lo = (uint32_t)f32_to_bf16_bits(xs[4 * g]) | ((uint32_t)f32_to_bf16_bits(xs[4 * g + 1]) << 16);
+                    const uint32_t hi = (uint32_t)f32_to_bf16_bits(xs[4 * g + 2]) | ((uint32_t)f32_to_bf16_bits(xs[4 * g + 3]) << 16);
+                    *reinterpret_cast<uint2*>(rx + i) = make_uint2(lo, hi);
+                }
+            }
+        }
+        if (rx)   // the row's padding stays zero (the network's input width is ldk)
+            for (int i = d + tid; i < ldk; i += FT) rx[i] = 0;
+        if (a) {
+#pragma unroll
+            for (int g = 0; g < NM; ++g) {
+                const int m = idx(g);
+                if (m < dy) *reinterpret_cast<float4*>(su + m) = make_float4(uv[4 * g], uv[4 * g + 1], uv[4 * g + 2], uv[4 * g + 3]);
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NV; ++g) {
+        const int i = idx(g);
+        if (i < d) {
+            *reinterpret_cast<float4*>(X + (size_t)p * d + i) = *reinterpret_cast<const float4*>(sx + i);
+            *reinterpret_cast<float4*>(Z + (size_t)p * d + i) = *reinterpret_cast<const float4*>(sz + i);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NM; ++g) {
+        const int m = idx(g);
+        if (m < dy) *reinterpret_cast<float4*>(Ax + (size_t)p * dy + m) = *reinterpret_cast<const float4*>(su + m);
+    }
+    if (tid == 0) {
+        lp[p] = lpc;
+        q[p] = qc;
+        accf[p] = (int8_t)a_last;
+        if (lpsum_base) lpsum_base[lps_at] = lps;
+        if (nacc) atomicAdd(&ctl->acc_block, nacc);
+        if (nnf) atomicAdd(&ctl->nonfinite, nnf);
+        __threadfence();
+        if (atomicAdd(&ctl->done_blocks, 1u) == gridDim.x - 1) {
+            if (dacnt) {   // every proposal was evaluated exactly and went to the ring, P per step
+                const long long n = (long long)ns * P;
+                dacnt->count = P;
+                dacnt->exact += (unsigned long long)n;
+                dacnt->head = (head0 + n) % ring_cap;
+                dacnt->filled = min(ring_cap, dacnt->filled + n);
+            }
+            ctl->t_cur += ns;
+            ctl->s_cur += ns;
             ctl->done_blocks = 0;
         }
     }
