@@ -123,7 +123,10 @@ typedef struct {
     int32_t keep_block_sums;/* 1: keep per-interval, per-chain sums of x, of x^2 (as the scatter about the
                                interval mean in BF16 mode) and of log pi (for ESS and the PSRF) */
     int32_t profile;        /* 1: time every phase with CUDA events on the context's stream (diam_get_profile) */
-    int32_t graphs;         /* 1: each whole interval's n_lag steps replay one captured CUDA graph (default) */
+    int32_t graphs;         /* 1 (default): each whole interval's n_lag steps run as one launch (BF16 mode with a
+                               linear-map target and no surrogate screen in force: one block walks each chain
+                               through the interval) or replay one captured CUDA graph; 0: launches step by
+                               step (the same results, bit for bit) */
     int32_t reserved[5];
 } diam_config;
 

@@ -74,7 +74,8 @@ __host__ __device__ inline int oz_units(int Ma, int Nb, int lower, int ch, int u
 }
 
 constexpr int OZ_STAGES = 4;            // A slices in flight
-constexpr int OZ_THREADS = 192;         // warp 0: TMA, warp 1: MMA issue, warps 2-5: epilogue
+constexpr int OZ_THREADS = 320;         // warp 0: TMA, warp 1: MMA issue, warps 2-9: epilogue
+constexpr int OZ_EPI_WARPS = 8;         // two per tensor-memory lane quarter, 8 of the 16 columns each
 constexpr uint32_t OZ_ABYTES = 128 * OZ_K * 2, OZ_BBYTES = OZ_BN * OZ_K * 2;
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -87,7 +88,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // order (slice a meets B slices 0 .. 6 - a in one product, so each group's first product comes with a = 0);
 // each tile's 7 group accumulators take 112 columns of one of two tensor-memory buffers (128 columns apart),
 // so the epilogue of one tile overlaps the products of the next. The epilogue warps read a tile's groups, release
-// its buffer, then combine and subtract. With 78 KB of shared memory and 256 columns two CTAs share an SM.
+// its buffer, then combine and subtract (eight epilogue warps, two per lane quarter, split the 16 columns).
+// With 78 KB of shared memory and 256 columns two CTAs share an SM.
 __global__ void __launch_bounds__(OZ_THREADS, 2) ozaki_update_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                      const __grid_constant__ CUtensorMap tmB, int Ma,
                                                                      int Nb, const int* __restrict__ exA,
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) ozaki_update_kernel(const __gri
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&tfull[b]), 1);
-            mbar_init(smem_u32(&tempty[b]), 4);   // one arrival per epilogue warp
+            mbar_init(smem_u32(&tempty[b]), OZ_EPI_WARPS);   // one arrival per epilogue warp
         }
         mbar_init(smem_u32(done), 1);
         *abort_flag = 0;
@@ -198,47 +200,50 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) ozaki_update_kernel(const __gri
         }
         umma_commit(smem_u32(done));   // arrives once every product issued here has completed
     } else if (warp >= 2) {
-        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31, i.e. rows of the A tile
-        const int rq = warp & 3, row = rq * 32 + lane;
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31, i.e. rows of the A tile, and columns
+        // 8 h .. 8 h + 7 of every group (h = 0 for warps 2-5, 1 for warps 6-9)
+        constexpr int NJ = OZ_BN / 2;
+        const int rq = warp & 3, row = rq * 32 + lane, j0 = (warp - 2) / 4 * NJ;
+        int sx[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) sx[j] = sex[j0 + j];
         for (int i = 0; i < ntiles; ++i) {
             const int m = (w.mt0 + i) * 128 + row;
             const bool vm = m < Ma;
             const int em = vm ? exA[m] : 0;
-            // the tile's 16 loads of C first: their latency hides behind the wait and the tensor-memory reads
-            double cv[OZ_BN];
+            // the loads of C first: their latency hides behind the wait and the tensor-memory reads
+            double cv[NJ];
 #pragma unroll
-            for (int j = 0; j < OZ_BN; ++j) {
-                const int n = n0 + j;
+            for (int j = 0; j < NJ; ++j) {
+                const int n = n0 + j0 + j;
                 cv[j] = (vm && n < Nb && (!lower || n >= m)) ? Cm[(size_t)n * ldc + m] : 0.0;
             }
             const int buf = i & 1;
             if (!mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1, abort_flag)) break;
             tc_fence_after();
-            const uint32_t trow = tmem + (uint32_t)(buf * 128) + ((uint32_t)(rq * 32) << 16);
-            long long acc[OZ_BN];
+            const uint32_t trow = tmem + (uint32_t)(buf * 128 + j0) + ((uint32_t)(rq * 32) << 16);
+            long long acc[NJ];
 #pragma unroll
-            for (int j = 0; j < OZ_BN; ++j) acc[j] = 0;
-#pragma unroll 1
-            for (int g = 0; g < OZ_S; ++g) {
-                uint32_t r[OZ_BN];
-                tmem_ld16(trow + (uint32_t)(g * OZ_BN), r);
-                if (g < OZ_S - 1) {
-                    const int sh = 40 - 8 * g;
+            for (int j = 0; j < NJ; ++j) acc[j] = 0;
 #pragma unroll
-                    for (int j = 0; j < OZ_BN; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(r[j])) * (1ll << sh);
-                } else {
+            for (int g = 0; g < OZ_S; ++g) {   // constant shifts: one or two integer operations per term
+                uint32_t r[NJ];
+                tmem_ld8(trow + (uint32_t)(g * OZ_BN), r);
 #pragma unroll
-                    for (int j = 0; j < OZ_BN; ++j) acc[j] += (long long)(__float2int_rn(__uint_as_float(r[j])) >> 8);
+                for (int j = 0; j < NJ; ++j) {
+                    const int v = __float2int_rn(__uint_as_float(r[j]));
+                    if (g < OZ_S - 1) acc[j] += (long long)v * (1ll << (40 - 8 * g));
+                    else acc[j] += (long long)(v >> 8);
                 }
             }
             tc_fence_before();   // the buffer goes back to the MMA issuer
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
 #pragma unroll
-            for (int j = 0; j < OZ_BN; ++j) {
-                const int n = n0 + j;
+            for (int j = 0; j < NJ; ++j) {
+                const int n = n0 + j0 + j;
                 if (vm && n < Nb && (!lower || n >= m))
-                    Cm[(size_t)n * ldc + m] = fma(-(double)acc[j], pow2(em + sex[j] - 54), cv[j]);
+                    Cm[(size_t)n * ldc + m] = fma(-(double)acc[j], pow2(em + sx[j] - 54), cv[j]);
             }
         }
     }
