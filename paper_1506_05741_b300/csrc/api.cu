@@ -547,7 +547,7 @@ static void launch_interval(diam_ctx* c, int ns, bool setup) {
         (const float*)c->Xi, (const uint16_t*)c->W, c->ldw, (const float*)c->xref, c->Ax, c->axref, c->AXi, c->y32,
         (float)(1.0 / (2.0 * c->sigma * c->sigma)), c->kind == TK_TANH, c->lp, c->q, c->accf, c->tr, (float*)c->hist,
         c->ldh, keep ? c->lpsum : nullptr, a ? a->cnt : nullptr, a ? a->ring_x : nullptr, a ? a->ring_lp : nullptr,
-        a ? (long long)a->cfg.ring : 1, c->ldk);
+        a ? (long long)a->cfg.ring : 1, c->ldk, (c->d % 4) == 0 && (c->dy % 4) == 0 && (c->ldw % 8) == 0);
     count_launch();
 }
 

@@ -767,7 +767,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
 // the ring row); the state, log pi and q go back to memory after the last step, and the last block to finish
 // moves the counters on by ns. No block waits on another, so the blocks drift apart and the loads of some
 // overlap the reductions and tests of others. The caller keeps steps s0 .. s0 + ns - 1 inside one interval.
-// VEC layout (entries 4 (tid + g FT) + j); dynamic shared memory (2 d + d_y) floats: x, z, A x.
+// VEC layout (entries 4 (tid + g FT) + j); dynamic shared memory (2 d + d_y) floats: x, z, A x. pf_l2 (rows
+// 16-byte aligned): thread 0 asks for the next step's xi, W and A xi rows to be brought into L2 at the start
+// of each step, so the HBM reads of a step overlap the previous step's reductions, test and stores.
 template <int NV, int NM>
 __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
     int d, int P, int nl, int dy, int ns, Ctl* ctl, Key key, TargetDev tg, double inv_infl2,
@@ -775,7 +777,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
     const float* __restrict__ xref, float* __restrict__ Ax, const float* __restrict__ axref,
     const float* __restrict__ AXi, const float* __restrict__ y32, float inv2s2, int tanh_mode, double* lp, double* q,
     int8_t* accf, TraceDev tr, float* __restrict__ hist_base, int ldh, double* __restrict__ lpsum_base,
-    DaCounters* dacnt, uint16_t* __restrict__ ring_x, float* __restrict__ ring_lp, long long ring_cap, int ldk) {
+    DaCounters* dacnt, uint16_t* __restrict__ ring_x, float* __restrict__ ring_lp, long long ring_cap, int ldk,
+    int pf_l2) {
     constexpr int FT = FUSED_THREADS;
     extern __shared__ float4 ival_smem[];
     __shared__ float red[3][FT / 32];
@@ -839,6 +842,12 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
             const double u = uniform53(key, t, (uint32_t)p, TAG_U);
             s_u = u;
             s_lu32 = logf((float)u);
+        }
+        if (pf_l2 && tid == 0 && k + 1 < ns) {   // the next step's rows into L2 while this step runs
+            const size_t rn = row + (size_t)P;
+            l2_prefetch(Xi + rn * d, (uint32_t)d * 4u);
+            l2_prefetch(W + rn * ldw, (uint32_t)ldw * 2u);
+            l2_prefetch(AXi + rn * dy, (uint32_t)dy * 4u);
         }
         float qf = 0.f, lf = 0.f, mf = 0.f;
         float uv[4 * NM];
