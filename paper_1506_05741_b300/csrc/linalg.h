@@ -16,12 +16,14 @@ struct OzakiWs {
     uint16_t* SLP = nullptr;   // capP x 448: every 64-column panel below the diagonal of the solve's factor
     int* exP = nullptr;        // capP
     int64_t capP = 0;
-    // streams and events of the factorisation's lookahead, created on first use (ozaki_ws_release frees them);
-    // the chain runs at the highest stream priority, the wide updates at the lowest unless lo_high is set
-    // (a factorisation running beside other work, whose chain waits on those updates)
+    // streams and events of the factorisation's lookahead, created on first use (ozaki_ws_release frees them):
+    // hi carries the chain of diagonal blocks, mid the rest of each panel, lo the trailing updates. The chain
+    // runs at the highest stream priority, mid just below it, the trailing updates at the lowest unless
+    // lo_high is set (a factorisation running beside other work, whose chain waits on those updates)
     bool lo_high = false;
-    cudaStream_t hi = nullptr, lo = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_slice = nullptr, ev_rest = nullptr, ev_lo = nullptr;
+    cudaStream_t hi = nullptr, mid = nullptr, lo = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_slice = nullptr, ev_rest = nullptr, ev_lo = nullptr, ev_diag = nullptr,
+                ev_mid = nullptr;
 };
 
 // Bytes of the slice buffers a workspace for rows / rows2 needs (SL: both buffers).

@@ -219,11 +219,13 @@ static int row_blocks(int nrows) { return max(1, min((nrows + 7) / 8, 148 * 8));
 static cudaError_t ensure_streams(OzakiWs& ws) {
     if (ws.hi) return cudaSuccess;
     int lo_pri = 0, hi_pri = 0;
-    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);   // numerically lower = higher priority
+    const int next = hi_pri < lo_pri ? hi_pri + 1 : hi_pri;
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ws.hi, cudaStreamNonBlocking, hi_pri);
-    const int lo_use = ws.lo_high ? (hi_pri < lo_pri ? hi_pri + 1 : hi_pri) : lo_pri;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ws.mid, cudaStreamNonBlocking, next);
+    const int lo_use = ws.lo_high ? next : lo_pri;
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ws.lo, cudaStreamNonBlocking, lo_use);
-    for (cudaEvent_t* ev : {&ws.ev_in, &ws.ev_slice, &ws.ev_rest, &ws.ev_lo})
+    for (cudaEvent_t* ev : {&ws.ev_in, &ws.ev_slice, &ws.ev_rest, &ws.ev_lo, &ws.ev_diag, &ws.ev_mid})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) ozaki_ws_release(ws);
     return e;
@@ -253,50 +255,70 @@ static cudaError_t cholesky_dfma(double* A, int n, int lda, int* info_dev, cudaS
     return cudaGetLastError();
 }
 
-// Tensor-core form with lookahead. On a high-priority stream: diagonal block, panel solve, slicing of the
-// panel, then the update of the next 64 columns only (what the next diagonal block and panel need). The
-// update of everything right of them runs on a second stream and overlaps the next block's chain; the
-// chain waits for it only before its own next-columns update, which writes inside that region.
+// Tensor-core form with lookahead, on three streams. Per 64-column block k (panel P = the rows below the
+// diagonal block, T = the trailing triangle):
+//   hi:  diagonal block k; solve of P's top 64 rows (the rows of block k + 1, with their Ozaki slices); the
+//        update of diagonal block k + 1 by those rows -- all that diagonal block k + 1 needs from block k;
+//   mid: solve of the rest of P (with slices); the update of the rest of T's first 64 columns, the panel
+//        of block k + 1 (it runs while diagonal block k + 1 is factored; block k + 1's top solve waits on it);
+//   lo:  the update of T right of its first 64 columns.
+// A region written by the trailing update of block k - 1 is updated for block k only after it (hi and mid
+// wait for that update first); a slice buffer (two, alternating by block) is rewritten only after every
+// update that reads it.
 static cudaError_t cholesky_ozaki(double* A, int n, int lda, int* info_dev, cudaStream_t st, OzakiWs& oz,
                                   int* status_dev) {
     LA_CK(ensure_streams(oz));
-    cudaStream_t hi = oz.hi, lo = oz.lo;
+    cudaStream_t hi = oz.hi, mid = oz.mid, lo = oz.lo;
     LA_CK(cudaEventRecord(oz.ev_in, st));
     LA_CK(cudaStreamWaitEvent(hi, oz.ev_in, 0));
+    LA_CK(cudaStreamWaitEvent(mid, oz.ev_in, 0));
     LA_CK(cudaStreamWaitEvent(lo, oz.ev_in, 0));
-    bool rest_pending = false;
+    bool rest_pending = false, mid_pending = false;
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         int nb = min(CH_NB, n - k0);
         { chol_diag_kernel<<<1, DIAG_THREADS, 0, hi>>>(A, lda, k0, nb, info_dev); count_launch(); }
         int k1 = k0 + nb, rest = n - k1;
         if (rest <= 0) break;
-        double* T = A + (size_t)k1 * lda + k1;   // trailing block
+        double* T = A + (size_t)k1 * lda + k1;          // trailing block
+        const double* Lkk = A + (size_t)k0 * lda + k0;
+        double* Pn = A + (size_t)k1 * lda + k0;         // the panel
         const bool tc = nb == CH_NB && rest >= 2 * CH_NB && rest <= oz.cap_rows;
-        const int buf = (k0 / CH_NB) & 1;
-        // panel solve; on the tensor-core path it also writes the panel's Ozaki slices into buffer buf
-        { trsv_rows_kernel<<<row_blocks(rest), 256, 0, hi>>>(A + (size_t)k0 * lda + k0, lda, nb,
-                                                             A + (size_t)k1 * lda + k0, lda, rest,
-                                                             tc ? oz.SL + (size_t)buf * oz.cap_rows * OZ_LD : nullptr,
-                                                             tc ? oz.ex + (size_t)buf * oz.cap_rows : nullptr); count_launch(); }
         if (tc) {
-            LA_CK(cudaEventRecord(oz.ev_slice, hi));
+            const int buf = (k0 / CH_NB) & 1, rr = rest - CH_NB;
+            uint16_t* SLb = oz.SL + (size_t)buf * oz.cap_rows * OZ_LD;
+            int* exb = oz.ex + (size_t)buf * oz.cap_rows;
+            // hi: the top rows of the panel (updated for this block by the previous block's mid work)
+            if (mid_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_mid, 0));
+            { trsv_rows_kernel<<<row_blocks(CH_NB), 256, 0, hi>>>(Lkk, lda, nb, Pn, lda, CH_NB, SLb, exb); count_launch(); }
+            LA_CK(cudaEventRecord(oz.ev_diag, hi));
+            // mid: the rest of the panel, then the rest of the next 64 columns
+            LA_CK(cudaStreamWaitEvent(mid, oz.ev_diag, 0));
+            { trsv_rows_kernel<<<row_blocks(rr), 256, 0, mid>>>(Lkk, lda, nb, Pn + (size_t)CH_NB * lda, lda, rr,
+                                                                SLb + (size_t)CH_NB * OZ_LD, exb + CH_NB); count_launch(); }
+            LA_CK(cudaEventRecord(oz.ev_slice, mid));
+            if (rest_pending) LA_CK(cudaStreamWaitEvent(mid, oz.ev_rest, 0));
+            LA_CK(ozaki_update_sliced(buf, 0, CH_NB, CH_NB, rr, T + (size_t)CH_NB * lda, lda, 0, oz, status_dev, mid));
+            LA_CK(cudaEventRecord(oz.ev_mid, mid));
+            mid_pending = true;
+            // hi: the next diagonal block
             if (rest_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_rest, 0));
-            // next 64 columns: T[n][m] for m < 64, n >= m
-            LA_CK(ozaki_update_sliced(buf, 0, CH_NB, 0, rest, T, lda, 1, oz, status_dev, hi));
-            // the rest: T[n][m] for 64 <= m <= n, on the second stream
+            LA_CK(ozaki_update_sliced(buf, 0, CH_NB, 0, CH_NB, T, lda, 1, oz, status_dev, hi));
+            // lo: the rest of the trailing triangle
             LA_CK(cudaStreamWaitEvent(lo, oz.ev_slice, 0));
-            LA_CK(ozaki_update_sliced(buf, CH_NB, rest - CH_NB, CH_NB, rest - CH_NB, T + (size_t)CH_NB * lda + CH_NB,
-                                      lda, 1, oz, status_dev, lo));
+            LA_CK(ozaki_update_sliced(buf, CH_NB, rr, CH_NB, rr, T + (size_t)CH_NB * lda + CH_NB, lda, 1, oz, status_dev,
+                                      lo));
             LA_CK(cudaEventRecord(oz.ev_rest, lo));
             rest_pending = true;
-        } else {
+        } else {   // the last blocks, in order on hi
+            if (mid_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_mid, 0));
             if (rest_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_rest, 0));
-            rest_pending = false;
+            mid_pending = rest_pending = false;
+            { trsv_rows_kernel<<<row_blocks(rest), 256, 0, hi>>>(Lkk, lda, nb, Pn, lda, rest); count_launch(); }
             EpiStore epi{T, lda, -1.0, nullptr, 1.0};
-            LA_CK((gemm_f64<true, true>(rest, rest, nb, A + (size_t)k1 * lda + k0, lda, A + (size_t)k1 * lda + k0, lda,
-                                        TileRange{0, 1}, epi, hi)));
+            LA_CK((gemm_f64<true, true>(rest, rest, nb, Pn, lda, Pn, lda, TileRange{0, 1}, epi, hi)));
         }
     }
+    if (mid_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_mid, 0));
     if (rest_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_rest, 0));
     dim3 g(max(1, min(32, (n + 255) / 256)), n);
     { zero_upper_kernel<<<g, 256, 0, hi>>>(A, lda, n); count_launch(); }

@@ -342,12 +342,12 @@ cudaError_t ozaki_update_raw(const uint16_t* SA, int Ma, const int* exA, const u
 }
 
 void ozaki_ws_release(OzakiWs& ws) {
-    if (ws.hi) cudaStreamDestroy(ws.hi);
-    if (ws.lo) cudaStreamDestroy(ws.lo);
-    for (cudaEvent_t e : {ws.ev_in, ws.ev_slice, ws.ev_rest, ws.ev_lo})
+    for (cudaStream_t s : {ws.hi, ws.mid, ws.lo})
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : {ws.ev_in, ws.ev_slice, ws.ev_rest, ws.ev_lo, ws.ev_diag, ws.ev_mid})
         if (e) cudaEventDestroy(e);
-    ws.hi = ws.lo = nullptr;
-    ws.ev_in = ws.ev_slice = ws.ev_rest = ws.ev_lo = nullptr;
+    ws.hi = ws.mid = ws.lo = nullptr;
+    ws.ev_in = ws.ev_slice = ws.ev_rest = ws.ev_lo = ws.ev_diag = ws.ev_mid = nullptr;
 }
 
 cudaError_t ozaki_gemm_update(const double* A, int lda, int Ma, const double* B, int ldb, int Nb, double* Cm, int ldc,
