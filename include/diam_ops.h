@@ -63,7 +63,8 @@ DIAM_API diam_status diam_op_gemm_bf16_tile(int32_t M, int32_t N, int32_t K, con
 
 /* The product of diam_op_gemm_bf16 (same arguments, same result within FP32 summation order) for callers
  * that cannot allocate device memory: code whose device memory belongs to its own pool and forbids outside
- * allocations, or code running while a stream is captured, where an allocating call is not allowed.
+ * allocations, or code on a latency-critical path that cannot afford the device-wide synchronisation that
+ * cudaMalloc and cudaFree may cause.
  * The paper has no counterpart; this is an interface convenience of this library.
  * It never calls cudaMalloc / cudaFree: its scratch (split-K partial products, a status word) is one fixed
  * 16 MiB device array inside the library, held by every GPU that loads the library until the process exits.

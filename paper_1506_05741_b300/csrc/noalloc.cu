@@ -2,9 +2,9 @@
 // cannot allocate device memory.
 //
 // Who needs it: code that must not call cudaMalloc at all -- for example a host runtime whose device
-// memory is owned by its own pool and forbids outside allocations, or code that runs while a stream is
-// being captured (where an allocating call is illegal or would synchronise). diam_op_gemm_bf16 allocates
-// a small per-device scratch block on its first call; this variant never allocates.
+// memory is owned by its own pool and forbids outside allocations, or code on a latency-critical path that
+// cannot afford the device-wide synchronisation cudaMalloc and cudaFree may cause. diam_op_gemm_bf16
+// allocates a small per-device scratch block on its first call; this variant never allocates.
 //
 // Scratch: one file-scope device array (kScratchBytes, 16 MiB, per GPU that loads the library, held until
 // the process exits) holds the FP32 split-K partial products, the status word and the scale. In host code
