@@ -797,7 +797,9 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
         // C_n + eps diag(C_n): every variance loaded by the same relative amount (the skip / jitter rule)
         { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, inv_n, eps, c->Cw); count_launch(); }
         CK(cudaMemsetAsync(&c->ctl->chol_info, 0, sizeof(int), c->st));
-        if (c->bf && c->cfg.graphs && !c->cfg.profile && c->oz.hi) {   // after a first eager factorisation
+        // after a first eager factorisation, replayed as a captured graph (profiled too: the phase's events
+        // lie outside the capture)
+        if (c->bf && c->cfg.graphs && c->oz.hi) {
             CKS(run_captured(c, c->chol_graph, [&]() {
                 return cholesky_f64(c->Cw, d, d, &c->ctl->chol_info, c->st, &c->oz, &c->ctl->status);
             }));
