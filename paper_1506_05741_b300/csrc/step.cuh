@@ -74,18 +74,47 @@ __device__ __forceinline__ float cvt_w<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ uint16_t cvt_w<uint16_t>(float v) { return f32_to_bf16_bits(v); }
 
+// Four entries of a W row, one vector store where the row allows it (BF16: 8 bytes, FP32: 16 bytes).
+template <typename OutT>
+__device__ __forceinline__ void store_w4(OutT* o, float4 w, int left, bool vec) {
+    const float v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = (q < left) ? cvt_w<OutT>(v[q]) : cvt_w<OutT>(0.f);
+}
+template <>
+__device__ __forceinline__ void store_w4<uint16_t>(uint16_t* o, float4 w, int left, bool vec) {
+    if (vec && left >= 4) {
+        *reinterpret_cast<uint2*>(o) = make_uint2((uint32_t)f32_to_bf16_bits(w.x) | ((uint32_t)f32_to_bf16_bits(w.y) << 16),
+                                                  (uint32_t)f32_to_bf16_bits(w.z) | ((uint32_t)f32_to_bf16_bits(w.w) << 16));
+        return;
+    }
+    const float v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = (q < left) ? f32_to_bf16_bits(v[q]) : (uint16_t)0;
+}
+template <>
+__device__ __forceinline__ void store_w4<float>(float* o, float4 w, int left, bool vec) {
+    if (vec && left >= 4) {
+        *reinterpret_cast<float4*>(o) = w;
+        return;
+    }
+    const float v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = (q < left) ? v[q] : 0.f;
+}
+
+// W rows r = s P + p (step s of the interval, chain p), entries 0 .. ld - 1 (zero from d on): grid (rows,
+// column blocks), every thread draws four entries per Philox call and loops over the row.
 template <typename OutT>
 __global__ void gen_w_kernel(Key key, int64_t t0, int P, int d, int ld, OutT* __restrict__ out) {
     const int64_t r = blockIdx.x;
     const int s = (int)(r / P), p = (int)(r % P);
     const int64_t t = t0 + s;
+    const bool vec = (ld % 4) == 0 && ((uintptr_t)out % 16) == 0;
     for (int j = blockIdx.y * blockDim.x + threadIdx.x; 4 * j < ld; j += gridDim.y * blockDim.x) {
         float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
         if (4 * j < d) w = normals4(key, (uint32_t)j, t, (uint32_t)p);
-        OutT* o = out + r * ld + 4 * j;
-        float v[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) o[q] = (4 * j + q < d) ? cvt_w<OutT>(v[q]) : cvt_w<OutT>(0.f);
+        store_w4<OutT>(out + r * ld + 4 * j, w, d - 4 * j, vec);
     }
 }
 
