@@ -420,8 +420,8 @@ template <typename T>
 static diam_status prepare_block(diam_ctx* c, int64_t blk, cudaStream_t st) {
     const int d = c->d, P = c->P, nl = c->nl;
     const int64_t rows = (int64_t)nl * P;
-    // a quarter of the row's four-entry groups per thread block pass: each thread draws four times
-    dim3 g((unsigned)rows, std::max(1u, std::min(64u, blocks_for(c->ldw / 16, 128))));
+    // an eighth of the row's four-entry groups per thread block pass: each thread draws eight times
+    dim3 g((unsigned)rows, std::max(1u, std::min(64u, blocks_for(c->ldw / 32, 128))));
     if (c->bf) {
         int e0 = ph_begin(c, PH_NOISE);
         { gen_w_kernel<uint16_t><<<g, 128, 0, st>>>(c->key, blk * nl, P, d, c->ldw, (uint16_t*)c->W); count_launch(); }
