@@ -459,7 +459,7 @@ def main():
         if not args.no_e2e:
             torch.cuda.synchronize()
             t0 = time.time()
-            se = make_sampler(run, ts, x0, C0, dm.BF16, da=da, stream=stream.cuda_stream)
+            se = make_sampler(run, ts, x0, C0, dm.BF16, da=da, stream=stream.cuda_stream, delay=args.refresh_delay)
             for _ in range(args.steps):
                 se.run(run.n_lag)
                 se.log_pi()
@@ -473,7 +473,7 @@ def main():
             d2h_final = m.nbytes + cov.nbytes
             e2e = {"value": round(N * args.steps / te, 1), "unit": "chain-steps/s",
                    "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(run.P * 8 + d2h_final / args.steps),
-                   "includes": "diam_init from host arrays, K intervals each with a log-pi read, final moments read"}
+                   "includes": "diam_init from host arrays, K intervals each with a log-pi read, final moments read; refresh delay as the headline arm"}
 
         if not args.no_cpu:
             cpu = cpu_leg(run, ts, x0, C0, args.cpu_seconds, cores)

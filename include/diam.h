@@ -173,7 +173,9 @@ DIAM_API diam_status diam_get_moments(diam_ctx* ctx, double* mean, double* cov, 
 /* The same moments in mergeable form: mean (d), M2 (d x d centred sum), n. Synchronises. */
 DIAM_API diam_status diam_export_moments(diam_ctx* ctx, double* mean, double* M2, int64_t* n);
 
-/* Chain states (P x d) and log pi (P); any output may be NULL. Synchronises. */
+/* Chain states (P x d) and log pi (P); any output may be NULL. Synchronises the context's stream. With stats,
+ * the Cholesky refreshes still running beside the intervals (refresh_delay >= 1) are waited for and counted;
+ * x and lp alone are read without waiting for them. */
 DIAM_API diam_status diam_get_state(diam_ctx* ctx, double* x, double* lp, diam_stats* stats);
 
 /* Factor in effect: L (d x d, FP64 master, lower), Lq (the rounded factor actually used; equals L for

@@ -1428,7 +1428,11 @@ diam_status diam_export_moments(diam_ctx* c, double* mean, double* M2, int64_t* 
 diam_status diam_get_state(diam_ctx* c, double* x, double* lp, diam_stats* stats) {
     CKS(check_usable(c));
     CKS(sync_and_check(c));
-    CKS(refresh_finish(c));   // the refresh in flight counts (and its factor is saved) as in order
+    // with stats, the refreshes in flight are resolved first (they count, and their factors are kept, as in
+    // order); the states and log pi do not depend on them (those refreshes use workspaces of their own and
+    // are resolved, with the same outcome, at the interval their factor is due), so reading only x or lp
+    // leaves them running beside the next intervals
+    if (stats) CKS(refresh_finish(c));
     const size_t Pd = (size_t)c->P * c->d;
     if (x) {
         if (c->bf) {
