@@ -162,6 +162,33 @@ def test_refresh_beside_the_next_interval_equals_refresh_in_order(delay):
     assert ra == rb >= 8
 
 
+def test_reading_log_pi_between_intervals_leaves_refreshes_beside_them():
+    """With refresh_delay 2 two factorisations run beside the intervals; reading log pi after every interval
+    (diam_get_state with lp only) neither waits for them nor changes anything: the chains, log pi and the
+    moments are bit-identical to a run that reads nothing in between, and the same refreshes happen."""
+    import paper_1506_05741_b300 as dm
+    ts, P, nl = workloads.tanh_regression(192, 64, 38), 6, 8
+    out = []
+    for read in (False, True):
+        cfg = dm.default_config(192, P, n_lag=nl, beta0=0.3, seed=6, prec=dm.BF16, min_samples_refresh=20,
+                                refresh_delay=2)
+        s = dm.Sampler(cfg, ts, x0=workloads.start_state(192, P, 2) * np.sqrt(ts.lam), C0=np.diag(ts.lam))
+        lps = []
+        for _ in range(12):
+            s.run(nl)
+            if read:
+                lps.append(s.log_pi())
+        s.flush()
+        out.append((s.state(), s.moments(), s.stats()["refreshes"], lps))
+        s.close()
+    (xa, la, sa), (ma, ca, na), ra, _ = out[0]
+    (xb, lb, sb), (mb, cb, nb), rb, lps = out[1]
+    assert np.array_equal(xa, xb) and np.array_equal(la, lb) and sa == sb
+    assert np.array_equal(ma, mb) and np.array_equal(ca, cb) and na == nb
+    assert ra == rb >= 8
+    assert np.array_equal(lps[-1], lb)   # the last read is the final state's log pi
+
+
 def test_bf16_interval_sums_equal_the_states_summed():
     """BF16 mode forms each interval's per-chain sums of x from the interval's records in the fold's pass
     (blocks of 32 chains: P = 40 leaves a partial block); they equal the states read back after every step
