@@ -56,6 +56,10 @@ struct diam_ctx {
     bool own_stream = false;
     cudaStream_t side = nullptr;                 // overlaps the interval's noise product with the re-solve
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // pinned staging of large host <-> device copies (two halves, allocated on the first large copy)
+    char* stage = nullptr;
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    bool stage_failed = false;
     // the refresh's factorisation and the re-solve of z, captured once (fixed buffers) and replayed
     struct Captured {
         cudaGraphExec_t exec = nullptr;
@@ -198,12 +202,74 @@ static diam_status fail(diam_ctx* c, diam_status s, const char* what, const char
 // Host <-> device copies ordered on the context's stream (which does not synchronise with the legacy default
 // stream). A host-to-device copy from pageable memory is staged before the call returns; a device-to-host
 // copy is waited for.
-static cudaError_t h2d(diam_ctx* c, void* dst, const void* src, size_t n) {
-    return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->st);
+// Host <-> device copies on the context's stream. Copies of at least one stage half go through a pinned
+// staging buffer of two halves, so the DMA of one chunk overlaps the host copy of the next (a copy from or
+// to pageable memory runs at a fraction of the link's rate); smaller ones, or all of them if the pinned
+// buffer cannot be had, are plain copies. h2d returns once the caller's buffer has been read.
+constexpr size_t kStageHalf = (size_t)4 << 20;
+
+static bool ensure_stage(diam_ctx* c) {
+    if (c->stage) return true;
+    if (c->stage_failed) return false;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, 2 * kStageHalf, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->stage_failed = true;
+        return false;
+    }
+    if (cudaEventCreateWithFlags(&c->stage_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->stage_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        for (cudaEvent_t& e : c->stage_ev)
+            if (e) cudaEventDestroy(e), e = nullptr;
+        cudaFreeHost(p);
+        c->stage_failed = true;
+        return false;
+    }
+    c->stage = (char*)p;
+    return true;
 }
+
+static cudaError_t h2d(diam_ctx* c, void* dst, const void* src, size_t n) {
+    if (n < kStageHalf || !ensure_stage(c)) return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->st);
+    char* d = (char*)dst;
+    const char* s = (const char*)src;
+    for (size_t i = 0, o = 0; o < n; ++i, o += kStageHalf) {
+        const int b = (int)(i & 1);
+        const size_t l = std::min(kStageHalf, n - o);
+        cudaError_t e = cudaEventSynchronize(c->stage_ev[b]);   // the last copy out of this half has finished
+        if (e != cudaSuccess) return e;
+        memcpy(c->stage + b * kStageHalf, s + o, l);
+        if ((e = cudaMemcpyAsync(d + o, c->stage + b * kStageHalf, l, cudaMemcpyHostToDevice, c->st)) != cudaSuccess ||
+            (e = cudaEventRecord(c->stage_ev[b], c->st)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t d2h(diam_ctx* c, void* dst, const void* src, size_t n) {
-    cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->st);
-    return e == cudaSuccess ? cudaStreamSynchronize(c->st) : e;
+    if (n < kStageHalf || !ensure_stage(c)) {
+        cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->st);
+        return e == cudaSuccess ? cudaStreamSynchronize(c->st) : e;
+    }
+    char* d = (char*)dst;
+    const char* s = (const char*)src;
+    const size_t chunks = (n + kStageHalf - 1) / kStageHalf;
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaEventSynchronize(c->stage_ev[b]);   // earlier uploads
+    for (size_t i = 0; i <= chunks && e == cudaSuccess; ++i) {
+        if (i < chunks) {   // chunk i into half i % 2 (chunk i - 2, its last contents, was copied out already)
+            const size_t o = i * kStageHalf, l = std::min(kStageHalf, n - o);
+            e = cudaMemcpyAsync(c->stage + (i & 1) * kStageHalf, s + o, l, cudaMemcpyDeviceToHost, c->st);
+            if (e == cudaSuccess) e = cudaEventRecord(c->stage_ev[i & 1], c->st);
+        }
+        if (i > 0 && e == cudaSuccess) {   // chunk i - 1 has landed: out of the stage while chunk i is in flight
+            const size_t o = (i - 1) * kStageHalf, l = std::min(kStageHalf, n - o);
+            e = cudaEventSynchronize(c->stage_ev[(i - 1) & 1]);
+            if (e == cudaSuccess) memcpy(d + o, c->stage + ((i - 1) & 1) * kStageHalf, l);
+        }
+    }
+    return e;
 }
 
 template <typename P_>
@@ -1803,6 +1869,10 @@ void diam_destroy(diam_ctx* c) {
     if (c->side) {
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
+    }
+    if (c->stage) {
+        for (cudaEvent_t e : c->stage_ev) cudaEventSynchronize(e), cudaEventDestroy(e);
+        cudaFreeHost(c->stage);
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
