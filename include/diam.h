@@ -114,8 +114,9 @@ typedef struct {
     int64_t min_samples_refresh;  /* refresh only after this many accepted moves (< 0: d + 1) */
     int64_t burnin;         /* n_0: steps kept out of the moments (footnote to Algorithm 1) */
     int32_t refresh_delay;  /* the factor built at the end of interval k is used from interval k+1+delay;
-                               with delay >= 1, BF16 mode and graphs on, its Cholesky runs on a stream of
-                               its own beside interval k+1's steps and is resolved at that interval's end */
+                               with delay >= 1, BF16 mode and graphs on, its Cholesky runs on streams of
+                               its own beside the following intervals' steps (at most two factorisations
+                               in flight) and is resolved, retries included, before its factor is due */
     int32_t prec;           /* diam_prec */
     uint64_t seed;          /* Philox4x32-10 key */
     uint32_t problem_id;    /* mixed into the key; distinct problems draw distinct streams */
@@ -274,7 +275,7 @@ DIAM_API diam_status diam_da_get_weights(diam_ctx* ctx, double* W1, double* b1, 
  * Many independent samplers run together (uneven dimensions, separate targets): the batched form of the
  * sampler. Problem j has its own configuration, target and start state, its own context and its own
  * stream. diam_multi_run advances every problem by n_steps steps; one host thread per problem drives its
- * context (whole intervals replay that problem's captured interval graph), so the problems' kernels
+ * context (whole intervals run as one launch or replay that problem's captured interval graph), so the problems' kernels
  * interleave on the GPU. x0 and C0 may be NULL or hold NULL entries (per-problem defaults). */
 typedef struct diam_multi diam_multi;
 DIAM_API diam_status diam_multi_init(int32_t n, const diam_config* cfgs, const diam_target* targets,
@@ -289,8 +290,9 @@ DIAM_API void diam_multi_destroy(diam_multi* m);
  * 0 noise draw, 1 noise product (batched triangular GEMM), 2 propose, 3 target (linear map + reduction),
  * 4 accept / select / record, 5 moment fold (column sums + SYRK), 6 Cholesky refresh (with its
  * retries), 7 re-whitening solve after a factor change, 8 surrogate screening (stage 1), 9 surrogate
- * training, 10 the whole step in one launch (propose + map + test + record, BF16 mode with the map carried
- * through the proposal and no surrogate screen in force; phases 2-4 then stay empty).
+ * training, 10 the fused steps (propose + map + test + record in one launch per step, or one launch per whole
+ * interval; BF16 mode with the map carried through the proposal and no surrogate screen in force; phases
+ * 2-4 then stay empty).
  * counts and ms hold DIAM_N_PHASES entries each. A refresh factorised beside the next interval (refresh_delay
  * >= 1) is timed on its own stream whether or not cfg.profile is set, and counted in phase 6.
  * reset = 1 clears the accumulators after reading. Synchronises. */

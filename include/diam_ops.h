@@ -29,8 +29,10 @@ DIAM_API diam_status diam_op_cholesky_f64(int32_t n, double* A, int32_t lda, int
  * splitting of Ozaki, Ogita, Oishi and Rump (2012): each 64-wide panel row is cut into 7 BF16 integer
  * slices under a power-of-two scale, slice products are summed exactly in FP32 tensor memory, grouped by
  * weight and combined as 64-bit integers (the dropped terms are of the size of an FP64 GEMM's rounding).
- * This is the factorisation the BF16 sampler mode uses for its refresh. Allocates its workspace
- * (7 x 64 x n BF16). Synchronises the stream; DIAM_ETIMEOUT on a device-side timeout. */
+ * This is the factorisation the BF16 sampler mode uses for its refresh: the chain of 64 x 64 diagonal
+ * blocks, the rest of each panel and the trailing updates run on three streams of its own, ordered after
+ * the work already on `stream` and joined back to it. Allocates its workspace (the panels' slices, about
+ * 2 x 448 x n BF16). Synchronises the stream; DIAM_ETIMEOUT on a device-side timeout. */
 DIAM_API diam_status diam_op_cholesky_f64_tc(int32_t n, double* A, int32_t lda, int32_t* info_host, void* stream);
 
 /* For nrows right-hand sides stored as rows of B (row r at B + r*ldb, n entries): B_r <- L^{-1} B_r with L
