@@ -78,8 +78,12 @@ __device__ __forceinline__ void diag_publish(int c, int q0, double v0, double v1
     }
 }
 
+// pre (a panel follows, so column k0 + nb exists): the panel solve's operands are left in places the
+// factorisation does not read and clears at its end -- U = L D^{-1} (the unit factor, U_ij = L_ij / L_jj)
+// transposed in the block's strict upper triangle, 1 / L_jj in row k0 + j, column k0 + nb -- computed with
+// the operations the panel solve would use, so every CTA of it loads them instead of recomputing them.
 __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(double* __restrict__ A, int lda, int k0, int nb,
-                                                                 int* info) {
+                                                                 int* info, int pre) {
     __shared__ double a[CH_NB][CH_NB + 1];
     __shared__ double colb[2][CH_NB];          // a_ij, i > j, of the current pivot j
     __shared__ double scol[2][CH_NB];          // a_ij / D_j
@@ -159,8 +163,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(double* __restr
     __syncthreads();
     for (int idx = tid; idx < nb * nb; idx += DIAG_THREADS) {
         const int i = idx / nb, l = idx - i * nb;
-        A[(size_t)(k0 + i) * lda + k0 + l] = (l < i) ? a[i][l] * dinv[l] : (l == i ? dsq[l] : 0.0);
+        double v = 0.0;
+        if (l < i) v = a[i][l] * dinv[l];
+        else if (l == i) v = dsq[l];
+        else if (pre) v = (a[l][i] * dinv[i]) * dinv[i];   // U_li = L_li (1 / L_ii), at (i, l)
+        A[(size_t)(k0 + i) * lda + k0 + l] = v;
     }
+    if (pre && tid < nb) A[(size_t)(k0 + tid) * lda + k0 + nb] = dinv[tid];
 }
 
 // For each of nrows rows r: solve L y = b in place, b = B[r*ldb + 0 .. nb), L the nb x nb lower triangle
@@ -168,18 +177,30 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(double* __restr
 // y = D^{-1} w. One warp per row; lane l holds entries l and l + 32.
 // With SL != nullptr (nb = 64), each solved row is also cut into its Ozaki slices (row r at SL + r * 448,
 // exponent in ex[r]) for the tensor-core update that follows.
+// pre: U and 1 / L_jj were left by chol_diag_kernel (U transposed above the block, the reciprocals in the
+// column right of it) and are loaded; otherwise they are computed here.
 __global__ void __launch_bounds__(256) trsv_rows_kernel(const double* __restrict__ Lkk, int ldl, int nb,
                                                          double* __restrict__ B, int ldb, int nrows,
-                                                         uint16_t* __restrict__ SL = nullptr, int* __restrict__ ex = nullptr) {
+                                                         uint16_t* __restrict__ SL = nullptr, int* __restrict__ ex = nullptr,
+                                                         int pre = 0) {
     __shared__ double U[CH_NB][CH_NB + 1];
     __shared__ double invd[CH_NB];
-    if (threadIdx.x < CH_NB) invd[threadIdx.x] = threadIdx.x < nb ? 1.0 / Lkk[(size_t)threadIdx.x * ldl + threadIdx.x] : 0.0;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < CH_NB * CH_NB; idx += blockDim.x) {
-        int i = idx >> 6, j = idx & 63;
-        U[i][j] = (i < nb && j < i) ? Lkk[(size_t)i * ldl + j] * invd[j] : 0.0;
+    if (pre) {
+        if (threadIdx.x < CH_NB) invd[threadIdx.x] = threadIdx.x < nb ? Lkk[(size_t)threadIdx.x * ldl + nb] : 0.0;
+        for (int idx = threadIdx.x; idx < CH_NB * CH_NB; idx += blockDim.x) {   // row j of the stored U^T
+            const int j = idx >> 6, i = idx & 63;
+            U[i][j] = (i < nb && j < i) ? Lkk[(size_t)j * ldl + i] : 0.0;
+        }
+        __syncthreads();
+    } else {
+        if (threadIdx.x < CH_NB) invd[threadIdx.x] = threadIdx.x < nb ? 1.0 / Lkk[(size_t)threadIdx.x * ldl + threadIdx.x] : 0.0;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < CH_NB * CH_NB; idx += blockDim.x) {
+            int i = idx >> 6, j = idx & 63;
+            U[i][j] = (i < nb && j < i) ? Lkk[(size_t)i * ldl + j] * invd[j] : 0.0;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warps = blockDim.x >> 5;
     const double id0 = invd[lane], id1 = invd[lane + 32];
@@ -241,12 +262,12 @@ static cudaError_t ensure_streams(OzakiWs& ws) {
 static cudaError_t cholesky_dfma(double* A, int n, int lda, int* info_dev, cudaStream_t st) {
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         int nb = min(CH_NB, n - k0);
-        { chol_diag_kernel<<<1, DIAG_THREADS, 0, st>>>(A, lda, k0, nb, info_dev); count_launch(); }
+        { chol_diag_kernel<<<1, DIAG_THREADS, 0, st>>>(A, lda, k0, nb, info_dev, k0 + nb < n); count_launch(); }
         int k1 = k0 + nb, rest = n - k1;
         if (rest <= 0) break;
         // panel rows solve x L_kk^T = a, i.e. L_kk x^T = a^T
         { trsv_rows_kernel<<<row_blocks(rest), 256, 0, st>>>(A + (size_t)k0 * lda + k0, lda, nb,
-                                                             A + (size_t)k1 * lda + k0, lda, rest); count_launch(); }
+                                                             A + (size_t)k1 * lda + k0, lda, rest, nullptr, nullptr, 1); count_launch(); }
         // trailing lower triangle: A[k1+n][k1+m] -= sum_k L[k1+m][k0+k] L[k1+n][k0+k]
         EpiStore epi{A + (size_t)k1 * lda + k1, lda, -1.0, nullptr, 1.0};
         LA_CK((gemm_f64<true, true>(rest, rest, nb, A + (size_t)k1 * lda + k0, lda, A + (size_t)k1 * lda + k0, lda,
@@ -276,7 +297,7 @@ static cudaError_t cholesky_ozaki(double* A, int n, int lda, int* info_dev, cuda
     bool rest_pending = false, mid_pending = false;
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         int nb = min(CH_NB, n - k0);
-        { chol_diag_kernel<<<1, DIAG_THREADS, 0, hi>>>(A, lda, k0, nb, info_dev); count_launch(); }
+        { chol_diag_kernel<<<1, DIAG_THREADS, 0, hi>>>(A, lda, k0, nb, info_dev, k0 + nb < n); count_launch(); }
         int k1 = k0 + nb, rest = n - k1;
         if (rest <= 0) break;
         double* T = A + (size_t)k1 * lda + k1;          // trailing block
@@ -289,12 +310,12 @@ static cudaError_t cholesky_ozaki(double* A, int n, int lda, int* info_dev, cuda
             int* exb = oz.ex + (size_t)buf * oz.cap_rows;
             // hi: the top rows of the panel (updated for this block by the previous block's mid work)
             if (mid_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_mid, 0));
-            { trsv_rows_kernel<<<row_blocks(CH_NB), 256, 0, hi>>>(Lkk, lda, nb, Pn, lda, CH_NB, SLb, exb); count_launch(); }
+            { trsv_rows_kernel<<<row_blocks(CH_NB), 256, 0, hi>>>(Lkk, lda, nb, Pn, lda, CH_NB, SLb, exb, 1); count_launch(); }
             LA_CK(cudaEventRecord(oz.ev_diag, hi));
             // mid: the rest of the panel, then the rest of the next 64 columns
             LA_CK(cudaStreamWaitEvent(mid, oz.ev_diag, 0));
             { trsv_rows_kernel<<<row_blocks(rr), 256, 0, mid>>>(Lkk, lda, nb, Pn + (size_t)CH_NB * lda, lda, rr,
-                                                                SLb + (size_t)CH_NB * OZ_LD, exb + CH_NB); count_launch(); }
+                                                                SLb + (size_t)CH_NB * OZ_LD, exb + CH_NB, 1); count_launch(); }
             LA_CK(cudaEventRecord(oz.ev_slice, mid));
             if (rest_pending) LA_CK(cudaStreamWaitEvent(mid, oz.ev_rest, 0));
             LA_CK(ozaki_update_sliced(buf, 0, CH_NB, CH_NB, rr, T + (size_t)CH_NB * lda, lda, 0, oz, status_dev, mid));
@@ -313,7 +334,7 @@ static cudaError_t cholesky_ozaki(double* A, int n, int lda, int* info_dev, cuda
             if (mid_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_mid, 0));
             if (rest_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_rest, 0));
             mid_pending = rest_pending = false;
-            { trsv_rows_kernel<<<row_blocks(rest), 256, 0, hi>>>(Lkk, lda, nb, Pn, lda, rest); count_launch(); }
+            { trsv_rows_kernel<<<row_blocks(rest), 256, 0, hi>>>(Lkk, lda, nb, Pn, lda, rest, nullptr, nullptr, 1); count_launch(); }
             EpiStore epi{T, lda, -1.0, nullptr, 1.0};
             LA_CK((gemm_f64<true, true>(rest, rest, nb, Pn, lda, Pn, lda, TileRange{0, 1}, epi, hi)));
         }
