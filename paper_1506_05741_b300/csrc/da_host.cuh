@@ -29,6 +29,7 @@ struct DaState {
     // training
     uint16_t *Xb, *XbT, *H1b, *H2b, *H1T, *dZ2, *dZ2T, *dZ1T;
     float *tb, *raw_lp, *Z1, *Z2, *ds, *dZ2f, *dH1, *dZ1f, *gW1T, *gW2T, *gb1, *gb2, *gw3, *gb3;
+    float* cs_part;   // COLSUM_CHUNKS x max(h1, h2): the column sums' partial sums
     double *loss_parts, *sbatch, *stats;
     double* musig;   // device copy of (mu, sigma)
     Key key{};
@@ -44,7 +45,8 @@ static diam_status da_forward(diam_ctx* c, int rows, const uint16_t* U, uint16_t
     e1.Zout = Z1;
     e1.ldz = a->h1;
     e1.bias = a->b1;
-    CK(tc_gemm_bf16(a->h1, rows, c->ldk, a->W1q, c->ldk, U, nullptr, c->ldk, 0, e1, &c->ctl->status, c->st));
+    // the network's products are small (a few hundred by a minibatch): 32-column tiles give four times the CTAs
+    CK(tc_gemm_bf16(a->h1, rows, c->ldk, a->W1q, c->ldk, U, nullptr, c->ldk, 0, e1, &c->ctl->status, c->st, 32));
     TcEpi e2{};
     e2.mode = TC_GELU;
     e2.Hout = H2;
@@ -52,7 +54,7 @@ static diam_status da_forward(diam_ctx* c, int rows, const uint16_t* U, uint16_t
     e2.Zout = Z2;
     e2.ldz = a->h2;
     e2.bias = a->b2;
-    CK(tc_gemm_bf16(a->h2, rows, a->h1, a->W2q, a->h1, H1, nullptr, a->h1, 0, e2, &c->ctl->status, c->st));
+    CK(tc_gemm_bf16(a->h2, rows, a->h1, a->W2q, a->h1, H1, nullptr, a->h1, 0, e2, &c->ctl->status, c->st, 32));
     if (s_out) {
         { mlp_out_kernel<<<blocks_for(rows), kThreads, 0, c->st>>>(rows, a->h2, H2, a->w3, a->b3, a->musig, s_out); count_launch(); }
     }
@@ -73,30 +75,38 @@ static diam_status da_refresh_s_cur(diam_ctx* c) {
 }
 
 // Forward + backward on the minibatch in a->Xb / a->tb (B rows): gradients into a->g*, loss parts.
+// out = the column sums of the B x cols matrix M (rows weighted by wrow when given), two fixed-order passes
+template <typename MT>
+static void da_colsum(diam_ctx* c, int B, int cols, const MT* M, const float* wrow, float* out) {
+    DaState* a = c->da;
+    { colsum_part_kernel<MT><<<dim3((cols + 31) / 32, COLSUM_CHUNKS), 256, 0, c->st>>>(B, cols, M, wrow, a->cs_part); count_launch(); }
+    { colsum_final_kernel<<<blocks_for(cols), kThreads, 0, c->st>>>(cols, COLSUM_CHUNKS, a->cs_part, out); count_launch(); }
+}
+
 static diam_status da_backward(diam_ctx* c) {
     DaState* a = c->da;
     const int B = a->B, h1 = a->h1, h2 = a->h2;
     CKS(da_forward(c, B, a->Xb, a->H1b, a->H2b, a->Z1, a->Z2, nullptr));
     { loss_grad_kernel<<<(B + 7) / 8, 256, 0, c->st>>>(B, h2, a->H2b, a->Z2, a->w3, a->b3, a->tb, a->ds, a->dZ2f, a->dZ2, a->dZ2T,
                                                      a->loss_parts); count_launch(); }
-    { colsum_rows_kernel<uint16_t><<<blocks_for(h2), kThreads, 0, c->st>>>(B, h2, a->H2b, a->ds, a->gw3); count_launch(); }
-    { colsum_rows_kernel<float><<<1, kThreads, 0, c->st>>>(B, 1, a->ds, nullptr, a->gb3); count_launch(); }
-    { colsum_rows_kernel<float><<<blocks_for(h2), kThreads, 0, c->st>>>(B, h2, a->dZ2f, nullptr, a->gb2); count_launch(); }
+    da_colsum<uint16_t>(c, B, h2, a->H2b, a->ds, a->gw3);
+    da_colsum<float>(c, B, 1, a->ds, nullptr, a->gb3);
+    da_colsum<float>(c, B, h2, a->dZ2f, nullptr, a->gb2);
     // dW2 (as [h1][h2]) = sum_b H1[b][i] dZ2[b][o]
     { transpose_bf16_kernel<<<dim3((h1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, c->st>>>(a->H1b, h1, B, h1, a->H1T, B); count_launch(); }
     TcEpi ew{};
     ew.mode = TC_STORE;
     ew.D = a->gW2T;
     ew.ldd = h2;
-    CK(tc_gemm_bf16(h2, h1, B, a->dZ2T, B, a->H1T, nullptr, B, 0, ew, &c->ctl->status, c->st));
+    CK(tc_gemm_bf16(h2, h1, B, a->dZ2T, B, a->H1T, nullptr, B, 0, ew, &c->ctl->status, c->st, 32));
     // dH1 = dZ2 W2, then dZ1 = dH1 * GELU'(Z1)
     TcEpi eh{};
     eh.mode = TC_STORE;
     eh.D = a->dH1;
     eh.ldd = h1;
-    CK(tc_gemm_bf16(h1, B, h2, a->W2Tq, h2, a->dZ2, nullptr, h2, 0, eh, &c->ctl->status, c->st));
+    CK(tc_gemm_bf16(h1, B, h2, a->W2Tq, h2, a->dZ2, nullptr, h2, 0, eh, &c->ctl->status, c->st, 32));
     { dz1_kernel<<<blocks_for((size_t)B * h1), kThreads, 0, c->st>>>(B, h1, a->dH1, a->Z1, a->dZ1f, a->dZ1T); count_launch(); }
-    { colsum_rows_kernel<float><<<blocks_for(h1), kThreads, 0, c->st>>>(B, h1, a->dZ1f, nullptr, a->gb1); count_launch(); }
+    da_colsum<float>(c, B, h1, a->dZ1f, nullptr, a->gb1);
     // dW1 (as [d][h1]) = sum_b U[b][k] dZ1[b][i]
     { transpose_bf16_kernel<<<dim3((c->ldk + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, c->st>>>(a->Xb, c->ldk, B, c->ldk, a->XbT, B); count_launch(); }
     TcEpi e1{};
@@ -278,7 +288,7 @@ static diam_status da_alloc(diam_ctx* c, const diam_da_config* g, const double* 
     CKS(F(&a->tb, B)); CKS(F(&a->raw_lp, B)); CKS(F(&a->Z1, (size_t)B * h1)); CKS(F(&a->Z2, (size_t)B * h2)); CKS(F(&a->ds, B));
     CKS(F(&a->dZ2f, (size_t)B * h2)); CKS(F(&a->dH1, (size_t)B * h1)); CKS(F(&a->dZ1f, (size_t)B * h1));
     CKS(F(&a->gW1T, (size_t)ldk * h1)); CKS(F(&a->gW2T, (size_t)h1 * h2)); CKS(F(&a->gb1, h1)); CKS(F(&a->gb2, h2));
-    CKS(F(&a->gw3, h2)); CKS(F(&a->gb3, 1));
+    CKS(F(&a->gw3, h2)); CKS(F(&a->gb3, 1)); CKS(F(&a->cs_part, (size_t)COLSUM_CHUNKS * std::max(h1, h2)));
     CKS(D(&a->loss_parts, B)); CKS(D(&a->sbatch, B)); CKS(D(&a->stats, 4)); CKS(D(&a->musig, 2));
     {
         const double ms[2] = {a->mu, a->sigma};

@@ -273,20 +273,43 @@ __global__ void dz1_kernel(int B, int h1, const float* __restrict__ dH1, const f
     }
 }
 
-// out[c] = sum_b M[b][c] * (wrow ? wrow[b] : 1) for c < cols (fixed order over b), FP32 in, FP32 out
+// Column sums out[c] = sum_b M[b][c] * (wrow ? wrow[b] : 1), c < cols, FP32, in two passes of fixed order.
+// Pass 1: grid (ceil(cols / 32), COLSUM_CHUNKS), block 32 x 8: chunk y of the rows, warp w takes its rows
+// w, w + 8, ... (lane = column, so every row is read coalesced); the 8 warp sums in warp order go to
+// part[y cols + c]. Pass 2 adds the chunks' sums in chunk order.
+constexpr int COLSUM_CHUNKS = 16;
+
 template <typename MT>
-__global__ void colsum_rows_kernel(int B, int cols, const MT* __restrict__ M, const float* __restrict__ wrow,
-                                   float* __restrict__ out) {
+__global__ void __launch_bounds__(256) colsum_part_kernel(int B, int cols, const MT* __restrict__ M,
+                                                          const float* __restrict__ wrow, float* __restrict__ part) {
+    __shared__ float red[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, c = blockIdx.x * 32 + lane, y = blockIdx.y;
+    const int b0 = (int)((long long)B * y / gridDim.y), b1 = (int)((long long)B * (y + 1) / gridDim.y);
+    float acc = 0.f;
+    if (c < cols) {
+        for (int b = b0 + w; b < b1; b += 8) {
+            float v;
+            if constexpr (sizeof(MT) == 2) v = bf16_bits_to_f32(M[(size_t)b * cols + c]);
+            else v = M[(size_t)b * cols + c];
+            acc += wrow ? v * wrow[b] : v;
+        }
+    }
+    red[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && c < cols) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += red[k][lane];
+        part[(size_t)y * cols + c] = s;
+    }
+}
+
+__global__ void colsum_final_kernel(int cols, int chunks, const float* __restrict__ part, float* __restrict__ out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cols) return;
-    float acc = 0.f;
-    for (int b = 0; b < B; ++b) {
-        float v;
-        if constexpr (sizeof(MT) == 2) v = bf16_bits_to_f32(M[(size_t)b * cols + c]);
-        else v = M[(size_t)b * cols + c];
-        acc += wrow ? v * wrow[b] : v;
-    }
-    out[c] = acc;
+    float s = 0.f;
+    for (int y = 0; y < chunks; ++y) s += part[(size_t)y * cols + c];
+    out[c] = s;
 }
 
 // One Adam step (Kingma & Ba) on a parameter tensor of rows x cols with FP32 master weights; the gradient
