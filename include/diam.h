@@ -69,29 +69,36 @@ typedef enum { DIAM_FP64 = 0, DIAM_BF16 = 2 } diam_prec;
  *  BANANA     : -x1^2/(2a) - (x2 + b x1^2 - c)^2 / 2 - sum_{i>=3} x_i^2 / (2 lam_i)
  *  REF_GAUSS  : the current reference Gaussian N(x_ref, alpha^2 A_n A_n^T), evaluated from x by a
  *               triangular solve; every proposal is accepted (a test target, Sec. 2.3.2)
- *  CALLBACK   : user function on device memory (see diam_logpi_fn) */
+ *  CALLBACK   : user function on device memory (see diam_logpi_fn)
+ *  TWISTED    : -sum_j (u_j + c_j u_{j-1}^2)^2 / (2 lam_j), u = G x (G is d_y x d, lam and c = y hold d_y
+ *               entries, c_0 unused): the twisted Gaussians pi_5, pi_6 of Sec. 3.1 (G = V^T, lam the eigenvalues
+ *               of pi_1's covariance, c the twist coefficients), a unit-Jacobian transform of N(0, diag(lam)) */
 typedef enum {
     DIAM_T_DIAG_GAUSS = 0,
     DIAM_T_DENSE_GAUSS = 1,
     DIAM_T_TANH_REG = 2,
     DIAM_T_BANANA = 3,
     DIAM_T_REF_GAUSS = 4,
-    DIAM_T_CALLBACK = 5
+    DIAM_T_CALLBACK = 5,
+    DIAM_T_TWISTED = 6
 } diam_target_kind;
 
 /* User log-density: X is P x d on the device (FP64 when prec = FP64, FP32 when prec = BF16), lp_out is
- * P doubles on the device, stream is the cudaStream_t the call must use. Return DIAM_OK or
- * DIAM_ETARGET. The function must not synchronise the device. */
+ * P doubles on the device, stream is the cudaStream_t the call must use (work on it is ordered with the
+ * sampler's; the call may synchronise that stream: callback targets never run inside a captured graph, but it
+ * must not synchronise the whole device). A non-finite value rejects that proposal and is counted in
+ * diam_stats.nonfinite. Return DIAM_OK, or DIAM_ETARGET to stop diam_run_batch (the context is then left in
+ * DIAM_ESTATE). */
 typedef diam_status (*diam_logpi_fn)(void* user, const void* X, int32_t d, int32_t P, int32_t prec,
                                      double* lp_out, void* stream);
 
 typedef struct {
     int32_t kind;           /* diam_target_kind */
     int32_t d_y;            /* rows of G or A */
-    const double* lam;      /* d (host): lambda_i; unused for DENSE_GAUSS / REF_GAUSS / CALLBACK */
-    const double* G;        /* d_y x d (host), DENSE_GAUSS */
+    const double* lam;      /* d (host): lambda_i (d_y for TWISTED); unused for DENSE_GAUSS / REF_GAUSS / CALLBACK */
+    const double* G;        /* d_y x d (host), DENSE_GAUSS and TWISTED */
     const double* A;        /* d_y x d (host), TANH_REG */
-    const double* y;        /* d_y (host), TANH_REG */
+    const double* y;        /* d_y (host): TANH_REG observations; TWISTED twist coefficients */
     double sigma;           /* TANH_REG noise std */
     double ban_a, ban_b, ban_c;
     diam_logpi_fn fn;       /* CALLBACK */
@@ -109,8 +116,8 @@ typedef struct {
     double acc_lo, acc_hi;  /* acceptance window; Sec. 3.2 uses [0.3, 0.5] for DIAM */
     double beta_factor;     /* multiplicative beta change (the paper leaves it open; default 1.1) */
     double beta_min, beta_max;
-    double eps_jitter;      /* refresh factors chol(C_n + eps diag(C_n)), eps x100 per retry (3 retries);
-                               BF16 mode starts at max(eps_jitter, 1e-4): its C_n is accumulated in FP32 */
+    double eps_jitter;      /* refresh factors chol(C_n + eps diag(C_n)), eps = max(eps_jitter, eps_jitter_min) at
+                               the first attempt, x100 per retry (3 retries) */
     int64_t min_samples_refresh;  /* refresh only after this many accepted moves (< 0: d + 1) */
     int64_t burnin;         /* n_0: steps kept out of the moments (footnote to Algorithm 1) */
     int32_t refresh_delay;  /* the factor built at the end of interval k is used from interval k+1+delay;
@@ -128,8 +135,24 @@ typedef struct {
                                linear-map target and no surrogate screen in force: one block walks each chain
                                through the interval) or replay one captured CUDA graph; 0: launches step by
                                step (the same results, bit for bit) */
-    int32_t reserved[5];
+    int32_t proposal;       /* diam_proposal: DIAM_PROP_DIAM (default) or DIAM_PROP_RW */
+    int32_t carry_map;      /* BF16 mode, linear-map targets: 1 (default) carries A x through the proposal (the
+                               map of an interval's noise is one product at the interval start, O(d_y) per step);
+                               0 evaluates A x* for every proposal (a tensor-core product per step) */
+    double eps_jitter_min;  /* floor of the refresh rule's first jitter (0: none). The library's default is 0;
+                               BF16-mode callers set it (the tests and the benchmark use 1e-4, reading G8) */
+    int32_t reserved[2];
 } diam_config;
+
+/* Proposal of the chain update (config field proposal).
+ * DIAM: x* = x_ref + sqrt(1 - beta^2)(x - x_ref) + beta alpha A_n W (eq. (diam), (diamnl)), with the quadratic q of
+ *       the reference Gaussian in the test. With A_n fixed (no refresh) and x_ref = 0 this is the
+ *       preconditioned Crank-Nicolson proposal of eq. (pcn) (Sec. 2.3.2).
+ * RW:   x* = x + beta alpha A_n W (eq. (rw), Sec. 2.3.1), a symmetric proposal: log a = log pi(x*) - log pi(x)
+ *       (q = 0). x_ref is not used. With the factor refreshed from the pooled moments this is the adaptive
+ *       Metropolis sampler of Sec. 2.3.3 (eq. (sampcov), (sampmean)). FP64 and BF16 modes; not with delayed
+ *       acceptance. */
+typedef enum { DIAM_PROP_DIAM = 0, DIAM_PROP_RW = 1 } diam_proposal;
 
 typedef struct {
     int64_t steps;          /* steps done by every chain */
@@ -164,9 +187,30 @@ DIAM_API diam_status diam_flush(diam_ctx* ctx);
 /* Synchronisation point of Sec. 2.4.1 (eq. (mom2g), (mom1g)). With the pooled reading used here the
  * local moments already are the global ones; this call merges moments exported by other samplers (other
  * processes, other GPUs) into them: ext_mean (d), ext_M2 (d x d, the centred sum
- * sum_i (x_i - ext_mean)(x_i - ext_mean)^T) and ext_n samples. ext_* may be NULL / 0 (no import).
+ * sum_i (x_i - ext_mean)(x_i - ext_mean)^T) and ext_n samples. ext_* may be NULL / 0 (no import). Every call
+ * marks a synchronisation: diam_export_increment counts from the moments as they stand after it.
  * Synchronises the stream. */
 DIAM_API diam_status diam_sync_moments(diam_ctx* ctx, const double* ext_mean, const double* ext_M2, int64_t ext_n);
+
+/* The moments of the samples this context folded since its last diam_sync_moments (since diam_init if there
+ * was none; after diam_load every sample the context holds counts as new), in the mergeable form of diam_export_moments: mean (d), M2 (d x d centred sum)
+ * and n (0: no new samples; mean and M2 are then zero). This is what a sampler adds to a pool of samplers
+ * between two synchronisations: each member exports its increment, imports every other member's with
+ * diam_sync_moments, and all members then hold the moments of every member's samples, each counted once
+ * (eq. (mom2g), (mom1g) with sample counts as weights). Computed from the current and the last synchronised
+ * moments (the pairwise update of Chan, Golub and LeVeque run backwards, FP64). Synchronises. */
+DIAM_API diam_status diam_export_increment(diam_ctx* ctx, double* mean, double* M2, int64_t* n);
+
+/* Interval-end hook: fn(user, ctx, interval) is called by diam_run_batch on the calling host thread at the end
+ * of every interval of n_lag steps, after the interval's samples are folded into the moments and before the
+ * beta rule and the refresh that uses those moments: the synchronisation point of Sec. 2.4.1 for a pool of
+ * samplers (processes, GPUs) sharing one factor. Inside the hook the caller may use diam_export_increment,
+ * diam_export_moments, diam_get_moments, diam_sync_moments and the other getters on ctx (each synchronises);
+ * diam_run_batch, diam_save, diam_load and diam_destroy on ctx return DIAM_EINVAL there. A status other than
+ * DIAM_OK from fn stops diam_run_batch, which returns that status (DIAM_ETARGET for DIAM_ENOTSPD) with the
+ * context left in DIAM_ESTATE. fn = NULL removes the hook. */
+typedef diam_status (*diam_interval_fn)(void* user, diam_ctx* ctx, int64_t interval);
+DIAM_API diam_status diam_set_interval_hook(diam_ctx* ctx, diam_interval_fn fn, void* user);
 
 /* Pooled moments of eq. (sampmean), (sampcov): mean (d), cov (d x d, may be NULL), n. Synchronises. */
 DIAM_API diam_status diam_get_moments(diam_ctx* ctx, double* mean, double* cov, int64_t* n);

@@ -25,7 +25,7 @@ _lib = None
 # prec codes shared with the C side of the oracle
 FP64, BF16 = 0, 2
 # target kinds
-T_DIAG, T_DENSE, T_TANH, T_BANANA, T_REF = 0, 1, 2, 3, 4
+T_DIAG, T_DENSE, T_TANH, T_BANANA, T_REF, T_TWIST = 0, 1, 2, 3, 4, 6
 
 
 def build(force: bool = False) -> str:
@@ -54,8 +54,8 @@ class OrcConfig(C.Structure):
                 ("eps_jitter", C.c_double), ("min_samples_refresh", C.c_int64),
                 ("refresh_delay", C.c_int32), ("prec", C.c_int32),
                 ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("threads", C.c_int32),
-                ("trace_steps", C.c_int64), ("record_traj", C.c_int32), ("pad_", C.c_int32),
-                ("burnin", C.c_int64)]
+                ("trace_steps", C.c_int64), ("record_traj", C.c_int32), ("chain0", C.c_uint32),
+                ("burnin", C.c_int64), ("proposal", C.c_int32), ("pad2_", C.c_int32), ("eps_jitter_min", C.c_double)]
 
 
 def lib():
@@ -193,7 +193,8 @@ def default_config(**kw):
     c = dict(d=0, P=1, n_lag=100, M=10, beta0=0.3, infl=1.0, adapt_beta=1, xref_mode=1,
              acc_lo=0.3, acc_hi=0.5, beta_factor=1.1, beta_min=1e-4, beta_max=0.999,
              eps_jitter=1e-10, min_samples_refresh=-1, refresh_delay=0, prec=FP64,
-             seed=0, problem_id=0, threads=1, trace_steps=0, record_traj=0, burnin=0)
+             seed=0, problem_id=0, threads=1, trace_steps=0, record_traj=0, burnin=0, chain0=0, proposal=0,
+             eps_jitter_min=0.0)
     c.update(kw)
     if c["min_samples_refresh"] < 0:
         c["min_samples_refresh"] = c["d"] + 1
@@ -206,7 +207,7 @@ class Sampler:
     def __init__(self, cfg: dict, target: Target, x0=None, C0=None, xref0=None):
         self.cfg = dict(cfg)
         self.target = target
-        self._cs = OrcConfig(**{k: self.cfg[k] for k, _ in OrcConfig._fields_ if k != "pad_"})
+        self._cs = OrcConfig(**{k: self.cfg[k] for k, _ in OrcConfig._fields_ if k not in ("pad_", "pad2_")})
         self._ts = target.struct()
         d, P = self.cfg["d"], self.cfg["P"]
         self._x0 = None if x0 is None else np.ascontiguousarray(np.broadcast_to(x0, (P, d)), np.float64)

@@ -219,7 +219,7 @@ ORC_EXPORT void orc_forward_sub(int n, const double* L, const double* b, double*
 /* ------------------------------------------------------------------------------------------------ */
 /* Targets: log pi up to an additive constant (eq. (bayes), Sec. 2.1).                               */
 /* ------------------------------------------------------------------------------------------------ */
-enum { ORC_T_DIAG = 0, ORC_T_DENSE = 1, ORC_T_TANH = 2, ORC_T_BANANA = 3, ORC_T_REF = 4 };
+enum { ORC_T_DIAG = 0, ORC_T_DENSE = 1, ORC_T_TANH = 2, ORC_T_BANANA = 3, ORC_T_REF = 4, ORC_T_TWIST = 6 };
 
 typedef struct {
     int32_t kind;
@@ -227,9 +227,10 @@ typedef struct {
     int32_t d_y;
     int32_t pad_;
     const double* lam;     /* d: prior / diagonal variances lambda_i */
-    const double* G;       /* d_y x d row-major: dense Gaussian, log pi = -|G x|^2 / 2 */
+    const double* G;       /* d_y x d row-major: dense Gaussian, log pi = -|G x|^2 / 2; the map u = G x of the
+                              twisted target */
     const double* A;       /* d_y x d row-major: forward map of the tanh regression */
-    const double* y;       /* d_y observations */
+    const double* y;       /* d_y observations (tanh regression); twist coefficients c_j (twisted target) */
     double sigma;          /* observation noise std */
     double ban_a, ban_b, ban_c;  /* banana: -x1^2/(2a) - (x2 + b x1^2 - c)^2 / 2 */
 } orc_target;
@@ -246,8 +247,16 @@ typedef struct {
     uint32_t problem_id;
     int32_t threads;
     int64_t trace_steps;                /* per-step trace kept for the first trace_steps steps */
-    int32_t record_traj, pad_;          /* keep every post-step state x_{n+1} */
+    int32_t record_traj;                /* keep every post-step state x_{n+1} */
+    uint32_t chain0;                    /* chain p draws the Philox streams of chain chain0 + p (a sample of a
+                                           larger run's chains; chains are independent while beta is fixed
+                                           and no refresh happens) */
     int64_t burnin;                     /* n_0 of Algorithm 1's footnote: steps before any moment is kept */
+    int32_t proposal;                   /* 0: DIAM, eq. (diam) / (diamnl); 1: random walk, eq. (rw) (Sec. 2.3.1):
+                                           x* = x + beta infl A_n W, a symmetric move, so q drops out of the test;
+                                           adaptive Metropolis (Sec. 2.3.3) when A_n is refreshed */
+    int32_t pad2_;
+    double eps_jitter_min;              /* floor of the first jitter of the refresh rule */
 } orc_config;
 
 typedef struct {
@@ -312,6 +321,19 @@ static double orc_logpi(const orc_sampler* s, const double* x, double* work) {
             for (int i = 2; i < d; ++i) lp -= 0.5 * x[i] * x[i] / s->lam[i];
             return lp;
         }
+        case ORC_T_TWIST: {
+            /* the twisted Gaussians of Sec. 3.1 (pi_5, pi_6): u = G x (G = V^T), the twist
+             * phi(u)_j = u_j + c_j u_{j-1}^2 (c_0 = 0; a unit Jacobian), and phi(u) ~ N(0, diag(lambda)) */
+            double prev = 0.0;
+            for (int k = 0; k < T->d_y; ++k) {
+                double u = 0.0;
+                for (int i = 0; i < d; ++i) u += s->G[(size_t)k * d + i] * x[i];
+                double ph = k > 0 ? u + s->y[k] * prev * prev : u;
+                lp -= 0.5 * ph * ph / s->lam[k];
+                prev = u;
+            }
+            return lp;
+        }
         case ORC_T_REF: {
             /* the current reference Gaussian N(x_ref, infl^2 Lq Lq^T): a target for which every proposal
              * of eq. (diamnl) is accepted (Sec. 2.3.2: the pCN move preserves N(0, A A^T)). */
@@ -373,8 +395,9 @@ ORC_EXPORT orc_sampler* orc_new(const orc_config* cfg, const orc_target* tgt, co
     s->tgt = *tgt;
     int d = cfg->d, P = cfg->P, dy = tgt->d_y;
     size_t nn = (size_t)d * d;
-    s->lam = (double*)calloc((size_t)d, sizeof(double));
-    if (tgt->lam) memcpy(s->lam, tgt->lam, sizeof(double) * d);
+    const int nlam = tgt->kind == ORC_T_TWIST ? dy : d;   /* the twisted target's variances are per row of G */
+    s->lam = (double*)calloc((size_t)(nlam > d ? nlam : d), sizeof(double));
+    if (tgt->lam) memcpy(s->lam, tgt->lam, sizeof(double) * nlam);
     if (tgt->G) {
         s->G = (double*)malloc(sizeof(double) * (size_t)dy * d);
         for (size_t i = 0; i < (size_t)dy * d; ++i) s->G[i] = cfg->prec == 2 ? orc_round_bf16(tgt->G[i]) : tgt->G[i];
@@ -461,10 +484,7 @@ static void orc_block_end(orc_sampler* s, int64_t blk) {
             for (int j = 0; j < d; ++j) C[(size_t)i * d + j] = s->S[(size_t)i * d + j] / (double)s->n - m[i] * m[j];
         /* skip / jitter rule (the paper is silent on degenerate C_n): factor C_n + eps diag(C_n), i.e. every
          * variance loaded by the same relative amount, retrying with eps x 100 up to three times */
-        double eps = c->eps_jitter;
-        /* BF16 mode: C_n comes from an FP32-accumulated tensor-core product whose noise (1e-5 to 1e-4 of the
-         * diagonal along near-null directions) exceeds the FP64 default; its first attempt loads by 1e-4 */
-        if (c->prec == 2 && eps < 1e-4) eps = 1e-4;
+        double eps = c->eps_jitter > c->eps_jitter_min ? c->eps_jitter : c->eps_jitter_min;
         int ok = -1;
         for (int attempt = 0; attempt < 4 && ok != 0; ++attempt) {
             double* Cj = (double*)malloc(sizeof(double) * nn);
@@ -495,7 +515,7 @@ static void orc_block_begin(orc_sampler* s, int64_t blk) {
         if (s->pend_block[i] == blk && s->pendL[i]) {
             memcpy(s->L, s->pendL[i], sizeof(double) * (size_t)s->cfg.d * s->cfg.d);
             orc_set_quantised_factor(s);
-            if (s->cfg.xref_mode == 1) orc_set_xref(s, s->pendX[i]);
+            if (s->cfg.xref_mode == 1 && s->cfg.proposal == 0) orc_set_xref(s, s->pendX[i]);
             free(s->pendL[i]); free(s->pendX[i]);
             s->pendL[i] = NULL; s->pendX[i] = NULL;
             s->pend_block[i] = -1;
@@ -511,6 +531,7 @@ static void orc_step(orc_sampler* s) {
     int64_t t = s->t;
     if (t % c->n_lag == 0) orc_block_begin(s, t / c->n_lag);
     double beta = s->beta;
+    const int rw = c->proposal == 1;
     double rho = sqrt(1.0 - beta * beta);
     double ba = beta * c->infl;
     int8_t* acc = (int8_t*)calloc((size_t)P, 1);
@@ -526,21 +547,23 @@ static void orc_step(orc_sampler* s) {
         double* xp = work + 2 * d;
         double* Wd = work + 3 * d;
         float* Wf = (float*)malloc(sizeof(float) * d);
-        orc_normals(c->seed, c->problem_id, t, (uint32_t)p, d, Wf);
+        orc_normals(c->seed, c->problem_id, t, c->chain0 + (uint32_t)p, d, Wf);
         for (int i = 0; i < d; ++i) Wd[i] = c->prec == 2 ? orc_round_bf16((double)Wf[i]) : (double)Wf[i];
         free(Wf);
         const double* x = s->x + (size_t)p * d;
-        /* x* = x_ref + sqrt(1 - beta^2)(x_n - x_ref) + beta * infl * A_n W_n */
+        /* DIAM: x* = x_ref + sqrt(1 - beta^2)(x_n - x_ref) + beta * infl * A_n W_n;  RW: x* = x_n + beta * infl * A_n W_n */
         for (int i = 0; i < d; ++i) {
             double xi = 0.0;
             for (int k = 0; k <= i; ++k) xi += s->Lq[(size_t)i * d + k] * Wd[k];
-            xp[i] = s->xref[i] + rho * (x[i] - s->xref[i]) + ba * xi;
+            xp[i] = rw ? x[i] + ba * xi : s->xref[i] + rho * (x[i] - s->xref[i]) + ba * xi;
         }
         double lpp = orc_logpi(s, xp, work);
-        double qp = orc_quad(s, xp, work);
-        double qc = orc_quad(s, x, work);
+        /* q: minus the log density of the Gaussian the DIAM move preserves; the random walk's density is
+         * symmetric and cancels (eq. (rw)) */
+        double qp = rw ? 0.0 : orc_quad(s, xp, work);
+        double qc = rw ? 0.0 : orc_quad(s, x, work);
         double loga = lpp + qp - (s->lp[p] + qc);
-        double u = orc_uniform(c->seed, c->problem_id, ORC_TAG_U, t, (uint32_t)p);
+        double u = orc_uniform(c->seed, c->problem_id, ORC_TAG_U, t, c->chain0 + (uint32_t)p);
         int a = log(u) < loga;
         if (t < c->trace_steps) {
             size_t k = (size_t)t * P + p;

@@ -15,7 +15,8 @@ import numpy as np
 from . import build as _build
 
 FP64, BF16 = 0, 2
-T_DIAG, T_DENSE, T_TANH, T_BANANA, T_REF, T_CALLBACK = 0, 1, 2, 3, 4, 5
+PROP_DIAM, PROP_RW = 0, 1
+T_DIAG, T_DENSE, T_TANH, T_BANANA, T_REF, T_CALLBACK, T_TWIST = 0, 1, 2, 3, 4, 5, 6
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
           4: "covariance not positive definite", 5: "device wait timed out", 6: "target callback failed",
           7: "context in error state"}
@@ -24,6 +25,7 @@ _lib = None
 _lock = threading.Lock()
 
 LOGPI_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p)
+INTERVAL_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int64)
 
 
 class DiamTarget(C.Structure):
@@ -40,7 +42,8 @@ class DiamConfig(C.Structure):
                 ("min_samples_refresh", C.c_int64), ("burnin", C.c_int64), ("refresh_delay", C.c_int32),
                 ("prec", C.c_int32), ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("trace_steps", C.c_int32),
                 ("keep_block_sums", C.c_int32), ("profile", C.c_int32), ("graphs", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("proposal", C.c_int32), ("carry_map", C.c_int32), ("eps_jitter_min", C.c_double),
+                ("reserved", C.c_int32 * 2)]
 
 
 class DiamDaConfig(C.Structure):
@@ -94,6 +97,8 @@ def lib():
                 "diam_sync_moments": (C.c_int, [P, P, P, I64]),
                 "diam_get_moments": (C.c_int, [P, P, P, P]),
                 "diam_export_moments": (C.c_int, [P, P, P, P]),
+                "diam_export_increment": (C.c_int, [P, P, P, P]),
+                "diam_set_interval_hook": (C.c_int, [P, INTERVAL_FN, P]),
                 "diam_get_state": (C.c_int, [P, P, P, P]),
                 "diam_get_factor": (C.c_int, [P, P, P, P, P]),
                 "diam_get_trace": (C.c_int, [P, P, P, P, P, P, I64]),
@@ -134,6 +139,13 @@ def _p(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
+# First jitter of the refresh rule in BF16 mode (reading G8): its C_n comes from the FP32-accumulated
+# tensor-core fold, whose noise along near-null directions early in a run is 1e-5 to 1e-4 of the diagonal, so
+# smaller loadings fail and only cost retries. A config value (eps_jitter_min), read by the library and the
+# oracle alike; default_config applies it to BF16 configurations unless the caller gives eps_jitter_min.
+BF16_JITTER_MIN = 1e-4
+
+
 def default_config(d: int, P: int, **kw) -> dict:
     cs = DiamConfig()
     rc = lib().diam_config_default(C.byref(cs), d, P)
@@ -144,6 +156,8 @@ def default_config(d: int, P: int, **kw) -> dict:
         if k not in cfg:
             raise KeyError(k)
         cfg[k] = v
+    if cfg["prec"] == BF16 and "eps_jitter_min" not in kw:
+        cfg["eps_jitter_min"] = BF16_JITTER_MIN
     return cfg
 
 
@@ -316,7 +330,39 @@ class Sampler:
     __del__ = close
 
     def run(self, n_steps: int):
-        self._check(self._l.diam_run_batch(self._h, int(n_steps)), "diam_run_batch")
+        self._hook_exc = None
+        rc = self._l.diam_run_batch(self._h, int(n_steps))
+        if rc and getattr(self, "_hook_exc", None) is not None:
+            exc, self._hook_exc = self._hook_exc, None
+            raise exc
+        self._check(rc, "diam_run_batch")
+
+    def set_interval_hook(self, fn):
+        """fn(interval) runs at the end of every interval, after the fold and before the beta rule and the refresh
+        (diam_set_interval_hook); an exception in fn stops run() and is raised from it. None removes the hook."""
+        if fn is None:
+            self._hook = None
+            self._check(self._l.diam_set_interval_hook(self._h, INTERVAL_FN(), None), "diam_set_interval_hook")
+            return
+
+        def tramp(user, ctx, k):
+            try:
+                fn(int(k))
+                return 0
+            except BaseException as e:   # re-raised by run()
+                self._hook_exc = e
+                return 6
+
+        self._hook = INTERVAL_FN(tramp)
+        self._check(self._l.diam_set_interval_hook(self._h, self._hook, None), "diam_set_interval_hook")
+
+    def export_increment(self):
+        """Moments (mean, M2, n) of the samples folded since the last sync_moments (diam_export_increment)."""
+        m = np.zeros(self.d)
+        M2 = np.zeros((self.d, self.d))
+        n = C.c_int64()
+        self._check(self._l.diam_export_increment(self._h, _p(m), _p(M2), C.byref(n)), "diam_export_increment")
+        return m, M2, n.value
 
     def flush(self):
         """Wait for a refresh still running beside the chains (refresh_delay >= 1) and apply its outcome."""

@@ -84,6 +84,12 @@ struct diam_ctx {
     bool bad = false;
     diam_logpi_fn fn = nullptr;
     void* user = nullptr;
+    // interval-end hook (diam_set_interval_hook) and the moments at the last synchronisation (increments)
+    diam_interval_fn hook = nullptr;
+    void* hook_user = nullptr;
+    bool in_hook = false;
+    double *snap_mean = nullptr, *snap_M2 = nullptr;
+    int64_t snap_n = 0;
     double sigma = 0, ban_a = 0, ban_b = 0, ban_c = 0;
     Key key{};
 
@@ -117,6 +123,7 @@ struct diam_ctx {
     int ldw = 0, ldh = 0, nparts = 0;
     // target
     double *inv_lam = nullptr, *Gm = nullptr, *y = nullptr;
+    double *tw_ilam = nullptr, *tw_c = nullptr, *ubuf = nullptr;   // twisted target: 1 / lambda_j, c_j; u = G x (FP64)
     float *inv_lam32 = nullptr, *y32 = nullptr;   // FP32 copies for the BF16-mode kernels
     float* psum = nullptr;   // per-tile sums of the interval's records (BF16 mode fold): 2 x tiles x d
     // the linear map carried through the proposal (BF16 mode, linear-map targets): M = A Lq as BF16 hi + lo,
@@ -287,7 +294,12 @@ static diam_status dalloc(diam_ctx* c, P_** p, size_t bytes) {
 }
 
 static inline unsigned blocks_for(size_t n, int th = kThreads) { return (unsigned)((n + th - 1) / th); }
-static inline double inv_infl2(const diam_ctx* c) { return 1.0 / (c->cfg.infl * c->cfg.infl); }
+// Weight 1 / alpha^2 of the proposal-density quadratic q in the test; 0 for the random-walk proposal of eq. (rw),
+// whose density is symmetric (q drops out of log a).
+static inline double inv_infl2(const diam_ctx* c) {
+    return c->cfg.proposal == DIAM_PROP_RW ? 0.0 : 1.0 / (c->cfg.infl * c->cfg.infl);
+}
+static inline bool is_rw(const diam_ctx* c) { return c->cfg.proposal == DIAM_PROP_RW; }
 
 static diam_status check_usable(diam_ctx* c) {
     if (!c) return DIAM_ESTATE;
@@ -338,6 +350,23 @@ static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
     if (c->kind == TK_CALLBACK) {
         diam_status s = c->fn(c->user, src, d, P, c->cfg.prec, out, (void*)c->st);
         if (s != DIAM_OK) return fail(c, DIAM_ETARGET, "target callback");
+        return DIAM_OK;
+    }
+    if (c->kind == TK_TWIST) {   // u = G x (every chain), then the twisted terms
+        if (!c->bf) {
+            EpiStore epi{c->ubuf, c->dy, 1.0, nullptr, 0.0};
+            CK((gemm_f64<true, true>(c->dy, P, d, c->Gm, d, (const double*)src, d, TileRange{0, 0}, epi, c->st)));
+            { twisted_lp_kernel<double><<<P, kThreads, 0, c->st>>>(c->dy, c->ubuf, c->dy, c->tw_ilam, c->tw_c, out); count_launch(); }
+        } else {   // x as BF16 hi + lo planes against the BF16 map, FP32 accumulation
+            { od_terms_kernel<T><<<P, kThreads, 0, c->st>>>(d, src, c->lpo, c->tg, c->op_hi, c->op_lo, c->ldk); count_launch(); }
+            TcEpi epi{};
+            epi.mode = TC_STORE;
+            epi.D = c->ws;
+            epi.ldd = c->dy;
+            CK(tc_gemm_bf16(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, 0, epi, &c->ctl->status, c->st));
+            { twisted_lp_kernel<float><<<P, kThreads, 0, c->st>>>(c->dy, c->ws, c->dy, c->tw_ilam, c->tw_c, out); count_launch(); }
+        }
+        CK(cudaGetLastError());
         return DIAM_OK;
     }
     { od_terms_kernel<T><<<P, kThreads, 0, c->st>>>(d, src, c->lpo, c->tg, c->bf ? c->op_hi : nullptr,
@@ -461,7 +490,7 @@ static diam_status block_begin(diam_ctx* c, int64_t blk) {
         if (pd.block != blk) continue;
         CK(cudaMemcpyAsync(c->L, pd.L, sizeof(double) * c->d * c->d, cudaMemcpyDeviceToDevice, c->st));
         CKS(quantise(c));
-        if (c->cfg.xref_mode == 1) set_xref_from(c, pd.mean);
+        if (c->cfg.xref_mode == 1 && !is_rw(c)) set_xref_from(c, pd.mean);   // the random walk keeps x_ref = 0
         CKS(rec_factor(c));
         CKS(rec_xref(c));
         // the interval's noise and noise product need only the new quantised factor, z's re-solve needs the
@@ -597,14 +626,14 @@ static void fused_step_nv(diam_ctx* c, bool setup) {
 // 16-byte layout, and x, z, A x of one chain in shared memory.
 static bool interval_kernel_fits(const diam_ctx* c) {
     const bool vec = (c->d % 4) == 0 && (c->dy % 4) == 0 && (c->ldw % 4) == 0 && (c->ldh % 4) == 0 && (c->ldk % 4) == 0;
-    return fused_step_fits(c) && vec && sizeof(float) * (2 * (size_t)c->d + c->dy) <= 128 * 1024;
+    return fused_step_fits(c) && vec && sizeof(float) * (2 * (size_t)c->d + 2 * (size_t)c->dy) <= 128 * 1024;
 }
 
 template <int NV, int NM>
 static void launch_interval(diam_ctx* c, int ns, bool setup) {
     DaState* a = c->da;
     const bool keep = c->cfg.keep_block_sums != 0;
-    const size_t smem = sizeof(float) * (2 * (size_t)c->d + c->dy);
+    const size_t smem = sizeof(float) * (2 * (size_t)c->d + 2 * (size_t)c->dy);
     if (setup) {   // outside any capture
         cudaFuncSetAttribute(interval_rec_kernel<NV, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         return;
@@ -682,7 +711,7 @@ static diam_status do_step(diam_ctx* c) {
     ph_end(c, e0);
     int e1 = ph_begin(c, PH_TARGET);
     const double iw = inv_infl2(c);
-    if (c->kind == TK_REF || c->kind == TK_CALLBACK) {
+    if (c->kind == TK_REF || c->kind == TK_CALLBACK || c->kind == TK_TWIST) {
         CKS(eval_lp<T>(c, (const T*)c->Xp, c->lpp));
         { finish_kernel<<<blocks_for(P), kThreads, 0, c->st>>>(P, c->nchunk, c->key, c->qpart, c->lpart, nullptr, 0, c->lpp,
                                                             iw, c->lp, c->q, c->accf, c->ctl, c->tr); count_launch(); }
@@ -854,11 +883,8 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
     const int d = c->d;
     int e0 = ph_begin(c, PH_REFRESH);
     double inv_n = 1.0 / (double)c->n;
-    double eps = c->cfg.eps_jitter;
-    // BF16 mode: C_n from the FP32-accumulated tensor-core fold; early in a run (fewer effective samples
-    // than dimensions) its near-null directions carry that accumulation noise, about 1e-5 to 1e-4 of the
-    // diagonal, so the first attempt loads by at least 1e-4 (relative) instead of retrying up to it
-    if (c->bf && eps < 1e-4) eps = 1e-4;
+    // the first attempt loads by max(eps_jitter, eps_jitter_min) (relative); the caller's floor (reading G8)
+    double eps = std::max(c->cfg.eps_jitter, c->cfg.eps_jitter_min);
     bool ok = false;
     for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
         // C_n + eps diag(C_n): every variance loaded by the same relative amount (the skip / jitter rule)
@@ -905,8 +931,7 @@ static diam_status refresh_launch(diam_ctx* c, int64_t blk) {
     const int d = c->d;
     diam_ctx::AsyncRefresh& r = c->ar[blk % c->n_ar];
     if (r.active) return fail(c, DIAM_ESTATE, "refresh", "slot still in flight");
-    double eps = c->cfg.eps_jitter;
-    if (eps < 1e-4) eps = 1e-4;   // the BF16-mode floor of the refresh rule
+    const double eps = std::max(c->cfg.eps_jitter, c->cfg.eps_jitter_min);
     { build_c_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, d, 1.0 / (double)c->n, eps, r.Cr); count_launch(); }
     CK(cudaMemcpyAsync(r.M2s, c->M2, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
     Pending& pd = c->pend[(size_t)(blk % (int64_t)c->pend.size())];
@@ -985,7 +1010,8 @@ static diam_status refresh_finish_due(diam_ctx* c, int64_t last) {
 static diam_status refresh_finish(diam_ctx* c) { return refresh_finish_due(c, -1); }
 
 static void push_scalars(diam_ctx* c) {
-    double rho = std::sqrt(1.0 - c->beta * c->beta);
+    // the random walk of eq. (rw) moves from x itself: rho = 1 (with x_ref = 0, x* = x + xi exactly)
+    double rho = is_rw(c) ? 1.0 : std::sqrt(1.0 - c->beta * c->beta);
     { set_scalars_kernel<<<1, 1, 0, c->st>>>(c->ctl, c->beta, rho, c->beta * c->cfg.infl, inv_infl2(c)); count_launch(); }
 }
 
@@ -999,6 +1025,13 @@ static diam_status block_end(diam_ctx* c, int64_t blk) {
     CK(d2h(c, &nonf, &c->ctl->nonfinite, sizeof(nonf)));
     c->acc_all += (int64_t)acc;
     c->nonfinite = nonf;
+    if (c->hook) {   // the synchronisation point: the interval's samples are in the moments, the refresh is next
+        c->in_hook = true;
+        const diam_status hs = c->hook(c->hook_user, c, blk);
+        c->in_hook = false;
+        if (c->bad) return DIAM_ESTATE;
+        if (hs != DIAM_OK) return fail(c, hs == DIAM_ENOTSPD ? DIAM_ETARGET : hs, "interval hook", "returned an error");
+    }
     const diam_config& g = c->cfg;
     if (g.adapt_beta) {  // Algorithm 1: raise beta above the window, lower it below
         double ahat = (double)acc / ((double)c->P * c->nl);
@@ -1147,7 +1180,7 @@ static diam_status init_state(diam_ctx* c, const double* x0, const double* C0, c
         CK(h2d(c, c->L, I.data(), sizeof(double) * d * d));
     }
     CKS(quantise(c));
-    if (xref0) {
+    if (xref0 && !is_rw(c)) {   // the random walk keeps x_ref = 0 (unused by its proposal)
         CK(cudaMemcpyAsync(tmp, xref0, sizeof(double) * d, cudaMemcpyHostToDevice, c->st));
         set_xref_from(c, tmp);
     }
@@ -1237,7 +1270,7 @@ static diam_status alloc_all(diam_ctx* c) {
         CKS(dalloc(c, &c->histT, sizeof(uint16_t) * (size_t)d * ((rows + 63) / 64 * 64)));
         // the fold's tile sums: one per (step, 32-chain block)
         CKS(dalloc(c, &c->psum, sizeof(float) * 2 * (size_t)d * ((size_t)nl * ((P + 31) / 32))));
-        if (c->kind == TK_TANH || c->kind == TK_DENSE) {
+        if ((c->kind == TK_TANH || c->kind == TK_DENSE) && c->cfg.carry_map) {
             c->rec = true;
             const size_t dy = (size_t)std::max(c->dy, 1);
             CKS(dalloc(c, &c->Lt16, sizeof(uint16_t) * (size_t)c->ldk * c->ldk));
@@ -1294,6 +1327,27 @@ static diam_status upload_target(diam_ctx* c, const diam_target* tg) {
         CKS(dalloc(c, &c->inv_lam32, sizeof(float) * d));
         CK(h2d(c, c->inv_lam32, il32.data(), sizeof(float) * d));
         c->tg.inv_lam32 = c->inv_lam32;
+    }
+    if (c->kind == TK_TWIST) {
+        if (!tg->G || !tg->lam || !tg->y || dy <= 0) return fail(c, DIAM_EINVAL, "diam_init", "twisted target needs G, lam, y");
+        std::vector<double> ilam((size_t)dy);
+        for (int j = 0; j < dy; ++j) {
+            if (!(tg->lam[j] > 0)) return fail(c, DIAM_EINVAL, "diam_init", "lam must be positive");
+            ilam[j] = 1.0 / tg->lam[j];
+        }
+        CKS(dalloc(c, &c->tw_ilam, sizeof(double) * dy));
+        CKS(dalloc(c, &c->tw_c, sizeof(double) * dy));
+        CK(h2d(c, c->tw_ilam, ilam.data(), sizeof(double) * dy));
+        CK(h2d(c, c->tw_c, tg->y, sizeof(double) * dy));
+        CKS(dalloc(c, &c->Gm, sizeof(double) * (size_t)dy * d));
+        CK(h2d(c, c->Gm, tg->G, sizeof(double) * (size_t)dy * d));
+        if (c->bf) {
+            CKS(dalloc(c, &c->Gq16, sizeof(uint16_t) * (size_t)dy * c->ldk));
+            { to_bf16_rows_kernel<<<dim3(blocks_for(c->ldk), dy), kThreads, 0, c->st>>>(dy, d, c->Gm, c->Gq16, c->ldk); count_launch(); }
+            CK(cudaGetLastError());
+        } else {
+            CKS(dalloc(c, &c->ubuf, sizeof(double) * (size_t)c->P * dy));
+        }
     }
     if (c->kind == TK_DENSE || c->kind == TK_TANH) {
         const double* M = c->kind == TK_DENSE ? tg->G : tg->A;
@@ -1362,6 +1416,9 @@ diam_status diam_config_default(diam_config* cfg, int32_t d, int32_t P) {
     cfg->refresh_delay = 0;
     cfg->prec = DIAM_FP64;
     cfg->graphs = 1;
+    cfg->proposal = DIAM_PROP_DIAM;
+    cfg->carry_map = 1;
+    cfg->eps_jitter_min = 0.0;
     return DIAM_OK;
 }
 
@@ -1371,8 +1428,10 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
     *out = nullptr;
     if (cfg->d <= 0 || cfg->P <= 0 || cfg->n_lag <= 0 || !(cfg->infl > 0) || !(cfg->beta0 > 0 && cfg->beta0 < 1) ||
         cfg->refresh_delay < 0 || cfg->refresh_delay > 8 || (cfg->prec != DIAM_FP64 && cfg->prec != DIAM_BF16) ||
-        tg->kind < 0 || tg->kind > DIAM_T_CALLBACK || (tg->kind == DIAM_T_CALLBACK && !tg->fn) ||
-        (int64_t)cfg->n_lag * cfg->P > (1 << 24) || cfg->trace_steps < 0)
+        tg->kind < 0 || tg->kind > DIAM_T_TWISTED || (tg->kind == DIAM_T_CALLBACK && !tg->fn) ||
+        (int64_t)cfg->n_lag * cfg->P > (1 << 24) || cfg->trace_steps < 0 ||
+        (cfg->proposal != DIAM_PROP_DIAM && cfg->proposal != DIAM_PROP_RW) ||
+        (cfg->proposal == DIAM_PROP_RW && tg->kind == DIAM_T_REF_GAUSS) || !(cfg->eps_jitter_min >= 0))
         return DIAM_EINVAL;
     diam_ctx* c = new diam_ctx();
     c->cfg = *cfg;
@@ -1381,7 +1440,7 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
     c->d = cfg->d;
     c->P = cfg->P;
     c->nl = cfg->n_lag;
-    c->dy = (tg->kind == DIAM_T_DENSE_GAUSS || tg->kind == DIAM_T_TANH_REG) ? tg->d_y : 0;
+    c->dy = (tg->kind == DIAM_T_DENSE_GAUSS || tg->kind == DIAM_T_TANH_REG || tg->kind == DIAM_T_TWISTED) ? tg->d_y : 0;
     c->ldk = (cfg->d + 63) / 64 * 64;
     c->bf = cfg->prec == DIAM_BF16;
     c->fn = tg->fn;
@@ -1426,6 +1485,7 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
 
 diam_status diam_run_batch(diam_ctx* c, int64_t n_steps) {
     CKS(check_usable(c));
+    if (c->in_hook) return fail(c, DIAM_EINVAL, "diam_run_batch", "called from the interval hook");
     if (n_steps < 0) return fail(c, DIAM_EINVAL, "diam_run_batch", "n_steps < 0");
     return c->bf ? run_steps<float>(c, n_steps) : run_steps<double>(c, n_steps);
 }
@@ -1442,6 +1502,48 @@ __global__ void merge_mean_kernel(int d, double* mean, const double* extm, doubl
     double dl = extm[i] - mean[i];
     delta[i] = dl;
     mean[i] += dl * frac;
+}
+
+// The increment since the last synchronisation: mi = (n m - n0 m0) / ni, delta = m0 - mi (the pairwise
+// update of Chan, Golub and LeVeque, M2 = M2_0 + M2_i + delta delta^T n0 ni / n, run backwards).
+__global__ void increment_mean_kernel(int d, const double* mean, const double* m0, double n, double n0, double* mi,
+                                      double* delta) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    const double v = (n * mean[i] - n0 * m0[i]) / (n - n0);
+    mi[i] = v;
+    delta[i] = m0[i] - v;
+}
+
+// out (d x d, full) = M2 - M2_0 - delta delta^T w, from the lower triangles of M2 and M2_0
+__global__ void increment_m2_kernel(int d, const double* M2, const double* M20, const double* delta, double w,
+                                    double* out) {
+    const int r = blockIdx.y;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d; c += gridDim.x * blockDim.x) {
+        const size_t k = (size_t)max(r, c) * d + min(r, c);
+        out[(size_t)r * d + c] = M2[k] - M20[k] - delta[r] * delta[c] * w;
+    }
+}
+
+// The moments as they stand become the reference of the next increment.
+static diam_status take_snapshot(diam_ctx* c) {
+    const int d = c->d;
+    if (!c->snap_mean) {
+        CKS(dalloc(c, &c->snap_mean, sizeof(double) * d));
+        CKS(dalloc(c, &c->snap_M2, sizeof(double) * d * d));
+    }
+    CK(cudaMemcpyAsync(c->snap_mean, c->mean, sizeof(double) * d, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(c->snap_M2, c->M2, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
+    c->snap_n = c->n;
+    return DIAM_OK;
+}
+
+diam_status diam_set_interval_hook(diam_ctx* c, diam_interval_fn fn, void* user) {
+    CKS(check_usable(c));
+    if (c->in_hook) return fail(c, DIAM_EINVAL, "diam_set_interval_hook", "inside the hook");
+    c->hook = fn;
+    c->hook_user = user;
+    return DIAM_OK;
 }
 
 diam_status diam_flush(diam_ctx* c) {
@@ -1465,6 +1567,7 @@ diam_status diam_sync_moments(diam_ctx* c, const double* ext_mean, const double*
         CK(cudaGetLastError());
         c->n += ext_n;
     }
+    CKS(take_snapshot(c));
     return sync_and_check(c);
 }
 
@@ -1489,6 +1592,32 @@ diam_status diam_get_moments(diam_ctx* c, double* mean, double* cov, int64_t* n)
 
 diam_status diam_export_moments(diam_ctx* c, double* mean, double* M2, int64_t* n) {
     return read_moments(c, mean, M2, n, false);
+}
+
+diam_status diam_export_increment(diam_ctx* c, double* mean, double* M2, int64_t* n) {
+    CKS(check_usable(c));
+    if (!c->snap_mean || c->snap_n == 0) return read_moments(c, mean, M2, n, false);   // everything is new
+    CKS(sync_and_check(c));
+    const int d = c->d;
+    const int64_t ni = c->n - c->snap_n;
+    if (ni <= 0) {
+        if (mean) memset(mean, 0, sizeof(double) * d);
+        if (M2) memset(M2, 0, sizeof(double) * d * d);
+        if (n) *n = 0;
+        return DIAM_OK;
+    }
+    // the fold's scratch vectors are free between intervals
+    const double nn = (double)c->n, n0 = (double)c->snap_n;
+    { increment_mean_kernel<<<blocks_for(d), kThreads, 0, c->st>>>(d, c->mean, c->snap_mean, nn, n0, c->svec, c->delta); count_launch(); }
+    if (M2) {
+        { increment_m2_kernel<<<dim3(blocks_for(d), d), kThreads, 0, c->st>>>(d, c->M2, c->snap_M2, c->delta,
+                                                                               n0 * (double)ni / nn, c->Cw); count_launch(); }
+    }
+    CK(cudaGetLastError());
+    if (mean) CK(d2h(c, mean, c->svec, sizeof(double) * d));
+    if (M2) CK(d2h(c, M2, c->Cw, sizeof(double) * d * d));
+    if (n) *n = ni;
+    return DIAM_OK;
 }
 
 diam_status diam_get_state(diam_ctx* c, double* x, double* lp, diam_stats* stats) {
@@ -1635,6 +1764,7 @@ static std::vector<std::pair<void*, size_t>> state_buffers(diam_ctx* c) {
 
 diam_status diam_save(diam_ctx* c, void* buf, size_t* size) {
     CKS(check_usable(c));
+    if (c->in_hook) return fail(c, DIAM_EINVAL, "diam_save", "called from the interval hook");
     if (!size) return fail(c, DIAM_EINVAL, "diam_save");
     CKS(sync_and_check(c));
     CKS(refresh_finish(c));   // the refresh in flight counts (and its factor is saved) as in order
@@ -1664,6 +1794,7 @@ diam_status diam_save(diam_ctx* c, void* buf, size_t* size) {
 
 diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
     CKS(check_usable(c));
+    if (c->in_hook) return fail(c, DIAM_EINVAL, "diam_load", "called from the interval hook");
     if (!buf || size < sizeof(HostState)) return fail(c, DIAM_EINVAL, "diam_load");
     HostState hs;
     memcpy(&hs, buf, sizeof(hs));
@@ -1696,6 +1827,7 @@ diam_status diam_load(diam_ctx* c, const void* buf, size_t size) {
     c->chol_attempts = hs.chol_attempts;
     for (size_t i = 0; i < c->pend.size(); ++i) c->pend[i].block = hs.pend_block[i];
     c->xi_block = -1;  // noise products are regenerated from the counter-based streams
+    c->snap_n = 0;     // the next increment counts from here: every loaded sample is new
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -1745,8 +1877,9 @@ diam_status diam_da_enable(diam_ctx* c, const diam_da_config* g, const double* W
                            const double* b2, const double* w3, const double* b3) {
     CKS(check_usable(c));
     if (!g || !W1 || !b1 || !W2 || !b2 || !w3 || !b3) return fail(c, DIAM_EINVAL, "diam_da_enable");
-    if (!c->bf || (c->kind != TK_DENSE && c->kind != TK_TANH) || c->P > 1024 || c->da)
-        return fail(c, DIAM_EINVAL, "diam_da_enable", "needs BF16 mode, a linear-map target, P <= 1024, once");
+    if (!c->bf || (c->kind != TK_DENSE && c->kind != TK_TANH) || c->P > 1024 || c->da || is_rw(c))
+        return fail(c, DIAM_EINVAL, "diam_da_enable",
+                    "needs BF16 mode, a linear-map target, the DIAM proposal, P <= 1024, once");
     if (g->h1 <= 0 || g->h2 <= 0 || g->h1 % 128 || g->h2 % 128 || g->batch <= 0 || g->batch % 128 || g->ring < 100 ||
         g->train_steps < 0 || g->retrain_every <= 0)
         return fail(c, DIAM_EINVAL, "diam_da_enable", "bad surrogate configuration");
@@ -1848,7 +1981,7 @@ diam_status diam_da_grad(diam_ctx* c, int32_t B, const double* U, const double* 
 }
 
 void diam_destroy(diam_ctx* c) {
-    if (!c) return;
+    if (!c || c->in_hook) return;
     cudaSetDevice(c->dev);
     for (auto& r : c->ar)
         if (r.rs) cudaStreamSynchronize(r.rs);   // a refresh still in flight

@@ -37,7 +37,7 @@ __global__ void set_step_kernel(Ctl* ctl, long long t, int s) {
     ctl->s_cur = s;
 }
 
-enum : int { TK_DIAG = 0, TK_DENSE = 1, TK_TANH = 2, TK_BANANA = 3, TK_REF = 4, TK_CALLBACK = 5 };
+enum : int { TK_DIAG = 0, TK_DENSE = 1, TK_TANH = 2, TK_BANANA = 3, TK_REF = 4, TK_CALLBACK = 5, TK_TWIST = 6 };
 
 struct TargetDev {
     int kind;
@@ -257,6 +257,26 @@ __global__ void __launch_bounds__(256) od_terms_kernel(int d, const T* __restric
     }
 }
 
+// The twisted Gaussians of Sec. 3.1 (pi_5, pi_6): from u = G x of chain p (row p of U, d_y entries),
+// log pi = -1/2 sum_j (u_j + c_j u_{j-1}^2)^2 / lambda_j (c_0 = 0), summed in FP64 in a fixed order (per thread,
+// then the block tree). One block per chain.
+template <typename UT>
+__global__ void __launch_bounds__(256) twisted_lp_kernel(int dy, const UT* __restrict__ U, int ldu,
+                                                         const double* __restrict__ inv_lam, const double* __restrict__ cw,
+                                                         double* __restrict__ out) {
+    __shared__ double sh[32];
+    const int p = blockIdx.x;
+    const UT* u = U + (size_t)p * ldu;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < dy; j += blockDim.x) {
+        const double uj = (double)u[j];
+        const double ph = j > 0 ? uj + cw[j] * (double)u[j - 1] * (double)u[j - 1] : uj;
+        acc += ph * ph * inv_lam[j];
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[p] = -0.5 * acc;
+}
+
 // lp[p] = lpo[p] + sum over m-tiles of the linear-map partials (fixed order), or the external value.
 __global__ void sum_lp_kernel(int P, const double* __restrict__ lpo, const double* __restrict__ partial, int nparts,
                               const double* __restrict__ ext, double* __restrict__ lp) {
@@ -459,19 +479,23 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
     }
 }
 
-// The test of Algorithm 1 in the fused kernels, from the block's three FP32 sums (|z*|^2, the prior terms,
-// the likelihood terms of the map): log pi(x*) = prior + likelihood, q* = |z*|^2 / (2 alpha^2),
-// log a = log pi(x*) + q* - log pi(x) - q(x). log u < log a is decided as in FP64: the FP32 log of u (within
-// 1e-5 of log u: u's rounding to FP32 and a few ulps of logf, |log u| <= 37) decides unless log a lies within
-// 1e-4 of it; then the FP64 log does. Writes the trace entry of (t, p) when it is kept.
-__device__ __forceinline__ int rec_test(float sq, float sl, float sm, double inv_infl2, double lpc, double qc, double u,
-                                        float lu32, long long t, int p, int P, const TraceDev& tr, double& lmap,
-                                        double& lpp, double& qpp, bool& finite) {
+// The test of Algorithm 1 in the fused kernels, from the block's FP32 sums. Absolute sums (|z*|^2, the prior
+// terms, the likelihood terms of the map) give log pi(x*) = prior + likelihood and q* = |z*|^2 / (2 alpha^2), the
+// values kept for x* when it is accepted. log a = (log pi(x*) - log pi(x)) + (q* - q(x)) is formed from the sums
+// of the per-coordinate differences instead (dq = sum (z*_i - z_i)(z*_i + z_i), the prior's and the likelihood's
+// differences likewise): each difference term is of the size of the move, so the FP32 sums carry rounding of
+// the size of log a's terms rather than of |log pi| (about 3e3 at d = 4096, where absolute FP32 sums lose
+// 1e-3 nats). The same quantity in exact arithmetic. log u < log a is decided as in FP64: the FP32 log of u
+// (within 1e-5 of log u: u's rounding to FP32 and a few ulps of logf, |log u| <= 37) decides unless log a lies
+// within 1e-4 of it; then the FP64 log does. Writes the trace entry of (t, p) when it is kept.
+__device__ __forceinline__ int rec_test(float sq, float sl, float sm, float dsq, float dsl, float dsm, double inv_infl2,
+                                        double qc, double u, float lu32, long long t, int p, int P, const TraceDev& tr,
+                                        double& lmap, double& lpp, double& qpp, bool& finite) {
     lmap = (double)sm;
     lpp = (double)sl + lmap;
     qpp = 0.5 * (double)sq * inv_infl2;
-    const double loga = lpp - lpc + qpp - qc;
-    finite = isfinite(lpp) && isfinite(qpp);
+    const double loga = ((double)dsl + (double)dsm) + 0.5 * (double)dsq * inv_infl2;
+    finite = isfinite(lpp) && isfinite(qpp) && isfinite(loga);
     const double l32 = (double)lu32;
     int a = 0;
     if (finite) a = loga > l32 + 1e-4 ? 1 : loga < l32 - 1e-4 ? 0 : (log(u) < loga);
@@ -515,7 +539,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     static_assert(!STAGE || VEC, "staging reads 16-byte vectors");
     constexpr int FT = FUSED_THREADS;
     extern __shared__ float4 stage_smem[];   // STAGE: x, z, xi of the chain (d floats each)
-    __shared__ float red[3][FT / 32];
+    __shared__ float red[6][FT / 32];
     __shared__ double s_u, s_lpc, s_qc;
     __shared__ float s_lu32;
     __shared__ int s_acc;
@@ -559,17 +583,21 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
         s_lpc = lp[p];
         s_qc = q[p];
     }
-    float qf = 0.f, lf = 0.f, mf = 0.f;
+    float qf = 0.f, lf = 0.f, mf = 0.f, dqf = 0.f, dlf = 0.f, dmf = 0.f;   // absolute sums; differences (rec_test)
     // the map of x* and its likelihood terms first (they need none of the chain's d-vectors)
     float uv[4 * NM];
     const float* ax = Ax + (size_t)p * dy;
     const float* axi = AXi + row * dy;
-    auto map_term = [&](float u, float yv) {
+    // u = (A x*)_m, uc = (A x)_m: the term of x* and its difference from x's
+    auto map_term = [&](float u, float uc, float yv) {
         if (tanh_mode) {
-            const float r = yv - tanhf(u);
+            const float tn = tanhf(u), tc = tanhf(uc);
+            const float r = yv - tn;
             mf -= r * r * inv2s2;
+            dmf -= (tc - tn) * (2.f * yv - tn - tc) * inv2s2;
         } else {
             mf -= 0.5f * u * u;
+            dmf -= 0.5f * (u - uc) * (u + uc);
         }
     };
 #pragma unroll
@@ -585,10 +613,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                 uv[4 * g + 1] = fmaf(rho, a4.y, fmaf(om, r4.y, i4.y));
                 uv[4 * g + 2] = fmaf(rho, a4.z, fmaf(om, r4.z, i4.z));
                 uv[4 * g + 3] = fmaf(rho, a4.w, fmaf(om, r4.w, i4.w));
-                map_term(uv[4 * g], y4.x);
-                map_term(uv[4 * g + 1], y4.y);
-                map_term(uv[4 * g + 2], y4.z);
-                map_term(uv[4 * g + 3], y4.w);
+                map_term(uv[4 * g], a4.x, y4.x);
+                map_term(uv[4 * g + 1], a4.y, y4.y);
+                map_term(uv[4 * g + 2], a4.z, y4.z);
+                map_term(uv[4 * g + 3], a4.w, y4.w);
             }
         } else {
 #pragma unroll
@@ -596,7 +624,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                 const int m = idx(g, j);
                 if (m < dy) {
                     uv[4 * g + j] = fmaf(rho, ax[m], fmaf(om, axref[m], axi[m]));
-                    map_term(uv[4 * g + j], tanh_mode ? y32[m] : 0.f);
+                    map_term(uv[4 * g + j], ax[m], tanh_mode ? y32[m] : 0.f);
                 }
             }
         }
@@ -640,10 +668,14 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                                      bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
+                    const float xv = xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
                     const float zs = fmaf(rho, z4[j], ba * w4[j]);
                     qf += zs * zs;
-                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i + j];
+                    dqf += (zs - z4[j]) * (zs + z4[j]);
+                    if (prior) {
+                        lf -= 0.5f * xv * xv * tg.inv_lam32[i + j];
+                        dlf -= 0.5f * (xv - x4[j]) * (xv + x4[j]) * tg.inv_lam32[i + j];
+                    }
                 }
             }
         } else {
@@ -651,36 +683,44 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
             for (int j = 0; j < 4; ++j) {
                 const int i = idx(g, j);
                 if (i < d) {
-                    const float xr = xref[i];
-                    xs[4 * g + j] = xr + rho * (x[i] - xr) + xi[i];
-                    const float zs = fmaf(rho, z[i], ba * bf16_bits_to_f32(w[i]));
+                    const float xr = xref[i], xc = x[i], zc = z[i];
+                    const float xv = xs[4 * g + j] = xr + rho * (xc - xr) + xi[i];
+                    const float zs = fmaf(rho, zc, ba * bf16_bits_to_f32(w[i]));
                     qf += zs * zs;
-                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i];
+                    dqf += (zs - zc) * (zs + zc);
+                    if (prior) {
+                        lf -= 0.5f * xv * xv * tg.inv_lam32[i];
+                        dlf -= 0.5f * (xv - xc) * (xv + xc) * tg.inv_lam32[i];
+                    }
                 }
             }
         }
     }
-    // the three sums over the block, then the test (Algorithm 1) in thread 0
+    // the six sums over the block, then the test (Algorithm 1) in thread 0
     qf = warp_sum(qf);
     lf = warp_sum(lf);
     mf = warp_sum(mf);
+    dqf = warp_sum(dqf);
+    dlf = warp_sum(dlf);
+    dmf = warp_sum(dmf);
     if (lane == 0) {
         red[0][wid] = qf;
         red[1][wid] = lf;
         red[2][wid] = mf;
+        red[3][wid] = dqf;
+        red[4][wid] = dlf;
+        red[5][wid] = dmf;
     }
     __syncthreads();
     if (wid == 0) {
-        float a0 = lane < FT / 32 ? red[0][lane] : 0.f;
-        float a1 = lane < FT / 32 ? red[1][lane] : 0.f;
-        float a2 = lane < FT / 32 ? red[2][lane] : 0.f;
-        a0 = warp_sum(a0);
-        a1 = warp_sum(a1);
-        a2 = warp_sum(a2);
+        float sum6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sum6[k] = warp_sum(lane < FT / 32 ? red[k][lane] : 0.f);
         if (lane == 0) {
             double lmap, lpp, qpp;
             bool finite;
-            const int a = rec_test(a0, a1, a2, inv_infl2, s_lpc, s_qc, s_u, s_lu32, t, p, P, tr, lmap, lpp, qpp, finite);
+            const int a = rec_test(sum6[0], sum6[1], sum6[2], sum6[3], sum6[4], sum6[5], inv_infl2, s_qc, s_u, s_lu32, t, p,
+                                   P, tr, lmap, lpp, qpp, finite);
             if (a) {
                 lp[p] = lpp;
                 q[p] = qpp;
@@ -796,7 +836,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
 // the ring row); the state, log pi and q go back to memory after the last step, and the last block to finish
 // moves the counters on by ns. No block waits on another, so the blocks drift apart and the loads of some
 // overlap the reductions and tests of others. The caller keeps steps s0 .. s0 + ns - 1 inside one interval.
-// VEC layout (entries 4 (tid + g FT) + j); dynamic shared memory (2 d + d_y) floats: x, z, A x. pf_l2 (rows
+// VEC layout (entries 4 (tid + g FT) + j); dynamic shared memory (2 d + 2 d_y) floats: x, z, A x and, for the tanh
+// regression, tanh(A x) (the current state's terms in log a's likelihood difference). pf_l2 (rows
 // 16-byte aligned): thread 0 asks for the next step's xi, W and A xi rows to be brought into L2 at the start
 // of each step, so the HBM reads of a step overlap the previous step's reductions, test and stores.
 template <int NV, int NM>
@@ -810,7 +851,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
     int pf_l2) {
     constexpr int FT = FUSED_THREADS;
     extern __shared__ float4 ival_smem[];
-    __shared__ float red[3][FT / 32];
+    __shared__ float red[6][FT / 32];
     __shared__ double s_u;
     __shared__ float s_lu32;
     __shared__ int s_acc;
@@ -822,6 +863,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
     float* sx = reinterpret_cast<float*>(ival_smem);
     float* sz = sx + d;
     float* su = sz + d;
+    float* st = su + dy;   // tanh of su (tanh mode)
     const bool prior = tg.kind == TK_TANH;
     auto idx = [&](int g) { return 4 * (tid + g * FT); };
     // the chain's state: every thread loads (and later stores) only its own entries, so no barrier is needed
@@ -836,7 +878,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
 #pragma unroll
     for (int g = 0; g < NM; ++g) {
         const int m = idx(g);
-        if (m < dy) *reinterpret_cast<float4*>(su + m) = *reinterpret_cast<const float4*>(Ax + (size_t)p * dy + m);
+        if (m < dy) {
+            const float4 a4 = *reinterpret_cast<const float4*>(Ax + (size_t)p * dy + m);
+            *reinterpret_cast<float4*>(su + m) = a4;
+            if (tanh_mode) *reinterpret_cast<float4*>(st + m) = make_float4(tanhf(a4.x), tanhf(a4.y), tanhf(a4.z), tanhf(a4.w));
+        }
     }
     // thread 0 carries log pi(x), q(x), the interval's log pi sum and the counts from step to step (in shared
     // memory: registers of every thread would hold them otherwise)
@@ -852,12 +898,16 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
         nnf = 0;
         a_last = 0;
     }
-    auto map_term = [&](float u, float yv, float& mf) {
+    // u = (A x*)_m; uc = (A x)_m and tc = tanh(uc) of the current state: the term of x* and its difference
+    auto map_term = [&](float u, float uc, float tc, float yv, float& mf, float& dmf) {
         if (tanh_mode) {
-            const float r = yv - tanhf(u);
+            const float tn = tanhf(u);
+            const float r = yv - tn;
             mf -= r * r * inv2s2;
+            dmf -= (tc - tn) * (2.f * yv - tn - tc) * inv2s2;
         } else {
             mf -= 0.5f * u * u;
+            dmf -= 0.5f * (u - uc) * (u + uc);
         }
     };
     for (int k = 0; k < ns; ++k) {
@@ -878,7 +928,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
             l2_prefetch(W + rn * ldw, (uint32_t)ldw * 2u);
             l2_prefetch(AXi + rn * dy, (uint32_t)dy * 4u);
         }
-        float qf = 0.f, lf = 0.f, mf = 0.f;
+        float qf = 0.f, lf = 0.f, mf = 0.f, dqf = 0.f, dlf = 0.f, dmf = 0.f;   // absolute sums; differences
         float uv[4 * NM];
 #pragma unroll
         for (int g = 0; g < NM; ++g) {
@@ -888,14 +938,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
                 const float4 r4 = *reinterpret_cast<const float4*>(axref + m);
                 const float4 i4 = *reinterpret_cast<const float4*>(axi + m);
                 const float4 y4 = tanh_mode ? *reinterpret_cast<const float4*>(y32 + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 t4 = tanh_mode ? *reinterpret_cast<const float4*>(st + m) : make_float4(0.f, 0.f, 0.f, 0.f);
                 uv[4 * g] = fmaf(rho, a4.x, fmaf(om, r4.x, i4.x));
                 uv[4 * g + 1] = fmaf(rho, a4.y, fmaf(om, r4.y, i4.y));
                 uv[4 * g + 2] = fmaf(rho, a4.z, fmaf(om, r4.z, i4.z));
                 uv[4 * g + 3] = fmaf(rho, a4.w, fmaf(om, r4.w, i4.w));
-                map_term(uv[4 * g], y4.x, mf);
-                map_term(uv[4 * g + 1], y4.y, mf);
-                map_term(uv[4 * g + 2], y4.z, mf);
-                map_term(uv[4 * g + 3], y4.w, mf);
+                map_term(uv[4 * g], a4.x, t4.x, y4.x, mf, dmf);
+                map_term(uv[4 * g + 1], a4.y, t4.y, y4.y, mf, dmf);
+                map_term(uv[4 * g + 2], a4.z, t4.z, y4.z, mf, dmf);
+                map_term(uv[4 * g + 3], a4.w, t4.w, y4.w, mf, dmf);
             }
         }
         float xs[4 * NV];
@@ -917,33 +968,41 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
                                      bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
+                    const float xv = xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
                     const float zs = fmaf(rho, z4[j], ba * w4[j]);
                     qf += zs * zs;
-                    if (prior) lf -= 0.5f * xs[4 * g + j] * xs[4 * g + j] * tg.inv_lam32[i + j];
+                    dqf += (zs - z4[j]) * (zs + z4[j]);
+                    if (prior) {
+                        lf -= 0.5f * xv * xv * tg.inv_lam32[i + j];
+                        dlf -= 0.5f * (xv - x4[j]) * (xv + x4[j]) * tg.inv_lam32[i + j];
+                    }
                 }
             }
         }
         qf = warp_sum(qf);
         lf = warp_sum(lf);
         mf = warp_sum(mf);
+        dqf = warp_sum(dqf);
+        dlf = warp_sum(dlf);
+        dmf = warp_sum(dmf);
         if (lane == 0) {
             red[0][wid] = qf;
             red[1][wid] = lf;
             red[2][wid] = mf;
+            red[3][wid] = dqf;
+            red[4][wid] = dlf;
+            red[5][wid] = dmf;
         }
         __syncthreads();
         if (wid == 0) {
-            float a0 = lane < FT / 32 ? red[0][lane] : 0.f;
-            float a1 = lane < FT / 32 ? red[1][lane] : 0.f;
-            float a2 = lane < FT / 32 ? red[2][lane] : 0.f;
-            a0 = warp_sum(a0);
-            a1 = warp_sum(a1);
-            a2 = warp_sum(a2);
+            float sum6[6];
+#pragma unroll
+            for (int k2 = 0; k2 < 6; ++k2) sum6[k2] = warp_sum(lane < FT / 32 ? red[k2][lane] : 0.f);
             if (lane == 0) {
                 double lmap, lpp, qpp;
                 bool finite;
-                const int a = rec_test(a0, a1, a2, inv_infl2, lpc, qc, s_u, s_lu32, t, p, P, tr, lmap, lpp, qpp, finite);
+                const int a = rec_test(sum6[0], sum6[1], sum6[2], sum6[3], sum6[4], sum6[5], inv_infl2, qc, s_u, s_lu32, t,
+                                       p, P, tr, lmap, lpp, qpp, finite);
                 if (a) {
                     lpc = lpp;
                     qc = qpp;
@@ -997,7 +1056,12 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
 #pragma unroll
             for (int g = 0; g < NM; ++g) {
                 const int m = idx(g);
-                if (m < dy) *reinterpret_cast<float4*>(su + m) = make_float4(uv[4 * g], uv[4 * g + 1], uv[4 * g + 2], uv[4 * g + 3]);
+                if (m < dy) {
+                    *reinterpret_cast<float4*>(su + m) = make_float4(uv[4 * g], uv[4 * g + 1], uv[4 * g + 2], uv[4 * g + 3]);
+                    if (tanh_mode)
+                        *reinterpret_cast<float4*>(st + m) = make_float4(tanhf(uv[4 * g]), tanhf(uv[4 * g + 1]),
+                                                                         tanhf(uv[4 * g + 2]), tanhf(uv[4 * g + 3]));
+                }
             }
         }
     }

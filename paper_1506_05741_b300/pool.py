@@ -1,40 +1,26 @@
-"""Pooling of moments across processes (the one exchange step of a pooled multi-GPU sampler).
+"""Pooling of moments across processes: the one exchange step of a pooled multi-GPU sampler.
 
-Each process exports its sampler's moments in mergeable form (mean, centred sum M2, sample count n; see
-``Sampler.export_moments``); ``allgather_moments`` collects them from every rank of a torch.distributed group
-and ``merge_moments`` combines them with the pairwise update of Chan, Golub and LeVeque (1979), the same
-combination the library applies inside ``diam_sync_moments`` (the merge of eq. (mom2g)/(mom1g) with sample
-counts as weights). Host-side numpy/torch only: the merged moments are handed back to a sampler through
-``Sampler.sync_moments``.
+A pool of samplers (one per process or GPU) shares one proposal factor built from the moments of every
+member's samples (eq. (mom2g), (mom1g) of Sec. 2.4.1, with sample counts as weights). At every synchronisation
+each member exports the moments of the samples it folded since the last one (``Sampler.export_increment``,
+``diam_export_increment``), the members gather them over a torch.distributed group, and each member imports every
+other member's increment into its own moments (``Sampler.sync_moments``, ``diam_sync_moments``). Each sample is
+then counted once in every member's moments, and the merge arithmetic is the library's: this module only moves
+arrays between processes.
+
+``attach`` makes the synchronisation run at every interval end, after the interval's fold and before the refresh
+that uses the moments (``Sampler.set_interval_hook``), so every member refreshes from the pooled moments.
 """
 from __future__ import annotations
 
 import numpy as np
 
 
-def merge_moments(parts):
-    """Combine [(mean, M2, n), ...] into one (mean, M2, n); parts with n = 0 are skipped."""
-    mean, M2, n = None, None, 0
-    for m_b, M2_b, n_b in parts:
-        if n_b <= 0:
-            continue
-        m_b = np.asarray(m_b, np.float64)
-        M2_b = np.asarray(M2_b, np.float64)
-        if n == 0:
-            mean, M2, n = m_b.copy(), M2_b.copy(), int(n_b)
-            continue
-        tot = n + n_b
-        delta = m_b - mean
-        M2 = M2 + M2_b + np.outer(delta, delta) * (n * n_b / tot)
-        mean = mean + delta * (n_b / tot)
-        n = tot
-    return mean, M2, n
-
-
-def allgather_moments(mean, M2, n, group=None):
-    """Every rank's (mean, M2, n), in rank order, gathered over the default (or given) process group."""
+def allgather_increments(sampler, group=None):
+    """Every member's (mean, M2, n) increment, in rank order, gathered over the default (or given) group."""
     import torch
     import torch.distributed as dist
+    mean, M2, n = sampler.export_increment()
     world = dist.get_world_size(group)
     d = int(np.asarray(mean).shape[0])
     flat = torch.from_numpy(np.concatenate([np.asarray(mean, np.float64).ravel(),
@@ -48,6 +34,20 @@ def allgather_moments(mean, M2, n, group=None):
     return parts
 
 
-def pooled_moments(mean, M2, n, group=None):
-    """The moments of the samples of every rank together (the same on every rank)."""
-    return merge_moments(allgather_moments(mean, M2, n, group))
+def synchronise(sampler, group=None):
+    """One synchronisation of the pool: import every other member's increment (the local one is already in)."""
+    import torch.distributed as dist
+    rank = dist.get_rank(group)
+    parts = allgather_increments(sampler, group)
+    imported = False
+    for r, (m, M2, n) in enumerate(parts):
+        if r != rank and n > 0:
+            sampler.sync_moments(m, M2, n)
+            imported = True
+    if not imported:
+        sampler.sync_moments()   # still a synchronisation point: the next increment counts from here
+
+
+def attach(sampler, group=None):
+    """Synchronise the pool at every interval end, before the refresh (all members must run the same steps)."""
+    sampler.set_interval_hook(lambda interval: synchronise(sampler, group))

@@ -7,7 +7,7 @@ import workloads
 
 CFG_KEYS = ["d", "P", "n_lag", "M", "beta0", "infl", "adapt_beta", "xref_mode", "acc_lo", "acc_hi", "beta_factor",
             "beta_min", "beta_max", "eps_jitter", "min_samples_refresh", "refresh_delay", "prec", "seed",
-            "problem_id", "burnin"]
+            "problem_id", "burnin", "proposal", "eps_jitter_min"]
 
 
 def oracle_target(ts):
@@ -34,3 +34,17 @@ def rel_err(a, b, scale):
 
 def trace_scale(tr):
     return np.maximum.reduce([np.abs(tr["lp_prop"]), np.abs(tr["q_prop"]), np.abs(tr["q_cur"])])
+
+
+def diff_scale(to):
+    """Scale of the log-density differences of each traced step (oracle trace): max(1, |log pi(x*) - log pi(x)|,
+    |q(x*) - q(x)|). log a = (log pi(x*) - log pi(x)) + (q(x*) - q(x)), so its error is measured against the size
+    of its two terms, not against |log pi| itself."""
+    dq = to["q_prop"] - to["q_cur"]
+    dlp = to["loga"] - dq
+    return np.maximum(1.0, np.maximum(np.abs(dlp), np.abs(dq)))
+
+
+def loga_err(tg, to):
+    """Largest error of log a, relative to the difference scale above."""
+    return float(np.max(np.abs(np.asarray(tg["loga"]) - np.asarray(to["loga"])) / diff_scale(to)))

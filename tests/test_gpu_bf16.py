@@ -61,7 +61,7 @@ def _bf16_pair(ts, P, steps, **kw):
     return make_pair(ts, P, trace_steps=steps, prec=_o.BF16, **kw)
 
 
-@pytest.mark.parametrize("kind", ["tanh", "dense", "diag", "tanh_vec", "dense_vec", "tanh4096"])
+@pytest.mark.parametrize("kind", ["tanh", "dense", "diag", "tanh_vec", "dense_vec", "tanh4096", "twisted"])
 def test_bf16_steps_match_oracle_bf16_mode(kind):
     """The map-carrying targets run as one fused launch per step: scalar element layout for d or d_y not a
     multiple of 4 (tanh, dense), 16-byte vectors otherwise (tanh_vec, dense_vec, with d past one element
@@ -77,6 +77,8 @@ def test_bf16_steps_match_oracle_bf16_mode(kind):
         ts, P = workloads.dense_gaussian(160, 36), 5
     elif kind == "tanh4096":
         ts, P = workloads.tanh_regression(4096, 2048, 40), 3
+    elif kind == "twisted":    # pi_6 of Sec. 3.1: the map through the tensor-core product, the twist in FP64
+        ts, P = workloads.paper_targets(128)[6], 5
     else:
         ts, P = workloads.diag_gaussian(100), 3
     d = ts.d
@@ -315,3 +317,44 @@ def test_bf16_rewhitening_matches_fp64_solve():
     qg = s.trace(4 * nl + 1)["q_cur"][4 * nl]
     assert np.max(np.abs(qg - q64) / q64) <= 1e-5
     s.close()
+
+
+def test_bf16_dense1024_chain_matches_closed_form_moments():
+    """The dense1024 target (d = 1024, Sigma = Q diag(1/i) Q^T) in BF16 mode, P = 128, n_lag = 64, from exact
+    draws of the target, with a fixed factor near Sigma (its eigenvalues scaled by seeded factors in [0.7, 1.4],
+    so the quantised proposal is not reversible for the target and the test of eq. (accept) does the work), beta
+    0.4, 400 intervals. The chains' states at the interval ends (second half, 25600 draws), rotated to Sigma's
+    eigenbasis y = Q^T x: the coordinates of v_1 and v_d, their squares and |x|^2 within 4 batch-means standard
+    errors of the closed forms (mean 0, variance lambda_i, E|x|^2 = tr Sigma), and the chi^2 aggregates of all
+    1024 standardised means and second moments below their 99.9% quantile. (The adaptive run from A_0 = Id is
+    far from Sigma after 2e4 steps, see the design notes: its first refreshes come from stuck, degenerate
+    samples.)"""
+    import scipy.stats
+    from oracle import stats
+    import paper_1506_05741_b300 as dm
+    run = workloads.dense1024()
+    ts = run.target
+    d, P, nl, K = ts.d, run.P, run.n_lag, 400
+    lam, Q = np.linalg.eigh(ts.cov)
+    sfac = np.exp(np.random.default_rng(5).uniform(np.log(0.7), np.log(1.4), d))
+    C0 = (Q * (lam * sfac)) @ Q.T
+    x0 = workloads.start_state(d, P, 3) @ np.linalg.cholesky(ts.cov).T
+    cfg = dm.default_config(d, P, n_lag=nl, beta0=0.4, seed=run.seed, prec=dm.BF16, adapt_beta=0, xref_mode=0,
+                            min_samples_refresh=10 ** 12)
+    s = dm.Sampler(cfg, ts, x0=x0, C0=C0)
+    Y = np.zeros((K, P, d), np.float32)
+    for k in range(K):
+        s.run(nl)
+        Y[k] = s.state()[0] @ Q
+    s.close()
+    h = Y[K // 2:].astype(np.float64)
+    zm = np.array([stats.mean_and_se(h[:, :, i]) for i in range(d)])
+    zv = np.array([stats.mean_and_se(h[:, :, i] ** 2) for i in range(d)])
+    for i in (0, d - 1):
+        assert abs(zm[i, 0]) <= 4 * zm[i, 1]
+        assert abs(zv[i, 0] - lam[i]) <= 4 * zv[i, 1]
+    m2, se2 = stats.mean_and_se((h ** 2).sum(axis=2))
+    assert abs(m2 - lam.sum()) <= 4 * se2
+    q = scipy.stats.chi2.ppf(0.999, d)
+    assert np.sum((zm[:, 0] / zm[:, 1]) ** 2) < q
+    assert np.sum(((zv[:, 0] - lam) / zv[:, 1]) ** 2) < q

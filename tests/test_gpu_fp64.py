@@ -1,7 +1,9 @@
 """FP64 CUDA path vs the FP64 oracle, through the C ABI.
 
 Bars: the noise draws are bit-exact; the proposals' log-densities and the chain states agree to 1e-12
-relative (to max(1, |log pi(x*)|, |q(x*)|, |q(x)|)); every accept decision is identical; moments and
+relative (to max(1, |log pi(x*)|, |q(x*)|, |q(x)|)) while both sides run on the starting factor, and past the
+first refresh to the forward error of the FP64 Cholesky factorisation, d u cond(C_n) (two factorisations of
+the same C_n in different orders); every accept decision is identical; moments and
 factors agree to 1e-10 / 1e-9 (they pass through an FP64 Cholesky of C_n). The proposal-density quadratic
 q and log a are compared at Q_TOL = 5e-12 (or 4 d u cond(A_n) if larger): the CUDA path carries
 z = A_n^{-1}(x - x_ref) by its recursion while the oracle solves by forward substitution every step, and
@@ -175,23 +177,41 @@ def _q_tol(o):
     return max(Q_TOL, 4 * L.shape[0] * U * np.linalg.cond(L))
 
 
-def _compare(g, o, steps, tol=TOL, q_tol=None):
-    """tol bounds log pi(x*) and the states; q_tol bounds q(x*), q(x), log a. The CUDA path carries
-    z = A_n^{-1}(x - x_ref) by the z recursion while the oracle solves by forward substitution, so their
-    difference is the substitution's forward error, proportional to cond(A_n) eps."""
+def _refresh_tol(o):
+    """After a refresh the two sides run on factors from two FP64 Cholesky factorisations of the same C_n in
+    different orders; they agree to the factorisation's forward error, about d u cond(C_n) = d u cond(A_n)^2
+    (Higham, "Accuracy and Stability of Numerical Algorithms", Sec. 10.1), and the proposals, states and
+    log-densities from then on agree to that level."""
+    L, _, _ = o.factor()
+    return max(TOL, 4 * L.shape[0] * U * np.linalg.cond(L) ** 2)
+
+
+def _compare(g, o, steps, tol=TOL, q_tol=None, first_factor_steps=None):
+    """tol bounds log pi(x*) and the states while both sides run on the starting factor (the first
+    first_factor_steps steps: n_lag (1 + refresh_delay), before any refreshed factor is in use); past them the
+    bound is _refresh_tol. q_tol bounds q(x*), q(x), log a. The CUDA path carries z = A_n^{-1}(x - x_ref) by the
+    z recursion while the oracle solves by forward substitution, so their difference is the substitution's
+    forward error, proportional to cond(A_n) eps."""
     if q_tol is None:
         q_tol = _q_tol(o)
+    k0 = steps if first_factor_steps is None else min(steps, first_factor_steps)
+    late = max(tol, _refresh_tol(o)) if k0 < steps else tol
+    q_tol = max(q_tol, late)
     tg, to = g.trace(steps), o.trace()
     assert np.array_equal(tg["acc"], to["acc"]), np.argwhere(tg["acc"] != to["acc"])[:5]
     sc = trace_scale(to)
-    assert rel_err(tg["lp_prop"], to["lp_prop"], sc) <= tol, rel_err(tg["lp_prop"], to["lp_prop"], sc)
+    assert rel_err(tg["lp_prop"][:k0], to["lp_prop"][:k0], sc[:k0]) <= tol, \
+        rel_err(tg["lp_prop"][:k0], to["lp_prop"][:k0], sc[:k0])
+    if k0 < steps:
+        assert rel_err(tg["lp_prop"][k0:], to["lp_prop"][k0:], sc[k0:]) <= late, \
+            (rel_err(tg["lp_prop"][k0:], to["lp_prop"][k0:], sc[k0:]), late)
     for k in ("q_prop", "q_cur", "loga"):
         assert rel_err(tg[k], to[k], sc) <= q_tol, (k, rel_err(tg[k], to[k], sc))
     xg, lpg, st = g.state()
     xo, lpo = o.state()
-    assert np.max(np.abs(xg - xo)) <= tol * max(1.0, np.max(np.abs(xo)))
+    assert np.max(np.abs(xg - xo)) <= late * max(1.0, np.max(np.abs(xo)))
     # the current log pi is one of the traced values: same scale as the trace (q is its natural size)
-    assert rel_err(lpg, lpo, np.maximum(np.abs(lpo), sc.max(axis=0))) <= tol
+    assert rel_err(lpg, lpo, np.maximum(np.abs(lpo), sc.max(axis=0))) <= late
     co = o.counts()
     assert st["accepted"] == co["accepted"] and st["refreshes"] == co["refreshes"]
     assert st["n"] == co["n"]
@@ -208,28 +228,55 @@ def _compare(g, o, steps, tol=TOL, q_tol=None):
 
 
 def test_diag64_single_chain_matches_oracle():
-    """The diag64 workload (d = 64, lambda_i = i^-2, P = 1, n_lag = 100, x_0 = 0, A_0 = Id, beta = 0.3)."""
+    """The diag64 workload (d = 64, lambda_i = i^-2, P = 1, n_lag = 100, x_0 = 0, A_0 = Id, beta = 0.3), all of its
+    2e4 steps."""
     run = workloads.diag64()
-    steps = 8000
+    steps = 20000
     g, o = make_pair(run.target, run.P, trace_steps=steps, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed)
     g.run(steps)
     o.run(steps)
     # starting at A_0 = Id the chain is stuck for thousands of steps and the adapted factor is far worse
     # conditioned than the target: q's bound grows with cond(A_n) (see the module docstring)
-    tg = _compare(g, o, steps)
+    tg = _compare(g, o, steps, first_factor_steps=run.n_lag)
     assert o.counts()["refreshes"] > 0 and tg["acc"].sum() > 100
 
 
-@pytest.mark.parametrize("kind", ["dense", "tanh", "banana"])
+@pytest.mark.parametrize("P,steps", [(128, 128), (4, 157 * 64)])
+def test_dense1024_prefix_matches_oracle(P, steps):
+    """The dense1024 workload (d = 1024, Sigma = Q diag(1/i) Q^T, n_lag = 64, seed 2): all 128 chains over two
+    intervals (a refresh between them), and four chains over the first 1e4 steps (157 whole intervals, a refresh
+    at each; the moments fold whole intervals)."""
+    run = workloads.dense1024(P=P)
+    ts = run.target
+    x0 = workloads.start_state(ts.d, P, 3) @ np.linalg.cholesky(ts.cov).T
+    g, o = make_pair(ts, P, trace_steps=steps, threads=8, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed, x0=x0,
+                     C0=ts.cov)
+    g.run(steps)
+    o.run(steps)
+    tg = _compare(g, o, steps, first_factor_steps=run.n_lag)
+    assert o.counts()["refreshes"] >= (1 if steps == 128 else 100) and 0 < tg["acc"].mean() < 1
+
+
+@pytest.mark.parametrize("kind", ["dense", "tanh", "banana", "twisted5", "twisted6", "pi4"])
 def test_small_targets_match_oracle(kind):
+    """Small cases of every target kind, including the test targets of Sec. 3.1: pi_4 (a dense target of
+    condition number d^2) and the twisted pi_5, pi_6 (u = V^T x through the FP64 product, then the twisted
+    terms)."""
     if kind == "dense":
         ts, P = workloads.dense_gaussian(96, 11), 5
     elif kind == "tanh":
         ts, P = workloads.tanh_regression(130, 70, 12), 7
+    elif kind.startswith("twisted"):
+        ts, P = workloads.paper_targets(100)[int(kind[-1])], 5
+    elif kind == "pi4":
+        ts, P = workloads.paper_targets(100)[4], 5
     else:
         ts, P = workloads.banana(70), 3
     steps, nl = 320, 16
-    C0 = ts.cov if ts.cov is not None else np.diag(ts.lam)
+    if ts.uvar is not None:      # the Gaussian with the twisted target's exact first two moments
+        C0 = (ts.G.T * ts.uvar) @ ts.G
+    else:
+        C0 = ts.cov if ts.cov is not None else np.diag(ts.lam)
     x0 = workloads.start_state(ts.d, P, 5) @ np.linalg.cholesky(C0).T
     # eps_jitter 1e-3 keeps every refresh well conditioned (few samples per dimension early on), so the
     # two FP64 factorisations agree to rounding instead of to cond(C_n) * rounding

@@ -74,3 +74,28 @@ def test_adam_without_moment_memory_is_sign_descent():
     before = params["a"].copy()
     mlp.adam_step(params, grads, m, v, t=1, lr=0.01, beta1=0.0, beta2=0.0, eps=0.0)
     assert np.allclose(params["a"], before - 0.01 * np.sign(grads["a"]), rtol=0, atol=1e-15)
+
+
+def test_adam_matches_torch_optim_adam_over_several_steps():
+    """oracle.mlp.adam_step against the library routine torch.optim.Adam (Kingma & Ba 2015, bias-corrected
+    moments), FP64, over five steps with different gradients, beta1 != beta2 and a non-negligible eps, so that
+    swapping beta1 and beta2, an off-by-one in the bias-correction exponent t or eps inside the square root all
+    fail."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    shapes = {"W1": (4, 6), "b1": (4,), "w3": (4,)}
+    params = {k: rng.standard_normal(s) for k, s in shapes.items()}
+    tparams = {k: torch.tensor(v.copy(), dtype=torch.float64, requires_grad=True) for k, v in params.items()}
+    lr, b1, b2, eps = 3e-2, 0.8, 0.95, 1e-3
+    opt = torch.optim.Adam(list(tparams.values()), lr=lr, betas=(b1, b2), eps=eps)
+    m = {k: np.zeros(s) for k, s in shapes.items()}
+    v = {k: np.zeros(s) for k, s in shapes.items()}
+    for t in range(1, 6):
+        grads = {k: rng.standard_normal(s) * (0.1 * t) for k, s in shapes.items()}
+        mlp.adam_step(params, grads, m, v, t, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        opt.zero_grad()
+        for k in shapes:
+            tparams[k].grad = torch.tensor(grads[k], dtype=torch.float64)
+        opt.step()
+        for k in shapes:
+            assert np.allclose(params[k], tparams[k].detach().numpy(), rtol=1e-13, atol=1e-15), (t, k)

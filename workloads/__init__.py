@@ -12,6 +12,8 @@ Workloads (the kinds of target of the paper's experiments, Sec. 3.1, at the size
              N(0, 1/4096) in FP32, x* from the prior. P = 256, n_lag = 128.
   banana     pi ~ exp(-x1^2/200 - (x2 + 0.1 x1^2 - 10)^2 / 2 - sum_{i>=3} x_i^2 / (2 lambda_i)), lambda_i = 1/i.
   multi64    64 problems, d log-uniform in [256, 8192]: even ones dense Gaussians, odd ones bananas.
+  paper_targets  the six test targets pi_1 .. pi_6 of Sec. 3.1 at any d (Gaussians built from a standard normal
+             matrix, and the two twisted Gaussians with their closed-form moments).
 """
 from __future__ import annotations
 
@@ -20,7 +22,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-TARGET_DIAG, TARGET_DENSE, TARGET_TANH, TARGET_BANANA, TARGET_REF = 0, 1, 2, 3, 4
+TARGET_DIAG, TARGET_DENSE, TARGET_TANH, TARGET_BANANA, TARGET_REF, TARGET_TWIST = 0, 1, 2, 3, 4, 6
 
 
 @dataclass
@@ -38,6 +40,8 @@ class TargetSpec:
     ban_c: float = 10.0
     cov: np.ndarray | None = None      # exact covariance when known (for checks)
     mean: np.ndarray | None = None
+    umean: np.ndarray | None = None    # twisted target: exact mean and variance of each u_j = (G x)_j
+    uvar: np.ndarray | None = None
 
 
 @dataclass
@@ -88,6 +92,50 @@ def banana(d: int, a: float = 100.0, b: float = 0.1, c: float = 10.0) -> TargetS
         var[1] = 1.0 + b * b * 2.0 * a * a
     return TargetSpec(TARGET_BANANA, d, lam=lam, ban_a=a, ban_b=b, ban_c=c, mean=np.zeros(d),
                       cov=np.diag(var))
+
+
+def paper_targets(d: int, seed: int = 31, b5: float = 0.3, b6: float = 2.0, sigma2_4: float | None = None) -> dict:
+    """pi_1 .. pi_6 of Sec. 3.1 (keys 1 .. 6). A (d x r) standard normal, B = A A^T:
+    pi_1 = N(0, (B + I)^-1), r = d;  pi_2 = N(0, (B / d + I)^-1), r = d;  pi_3 = N(0, (B + I)^-1), r = d / 10;
+    pi_4 = N(0, V diag[(sigma^-2 n^-4 + 1)^-1] V^T), V the eigenvectors of pi_1's covariance ordered from its
+    smallest eigenvalue (sigma^2 = sigma2_4, default 1 / d^2, a condition number O(d^2));
+    pi_5, pi_6 = pi_1 o V o phi o V^T with phi(w)_j = w_j + b_{j-1} w_{j-1}^2 for the even (1-based) j <= d / 10,
+    b_i = b sigma_i^-2 / sqrt(d), b = b5 (mildly twisted) or b6 (strongly twisted).
+    The Gaussians are dense targets, log pi = -|G x|^2 / 2 with G^T G their precision (G from its Cholesky
+    factor); the twisted ones are TARGET_TWIST: u = G x with G = V^T, log pi = -sum_j (u_j + c_j u_{j-1}^2)^2
+    / (2 lam_j), lam = the eigenvalues sigma_j^2 of pi_1's covariance and c_j the twist coefficients (in y).
+    Their exact moments: E u_j = -c_j sigma_{j-1}^2, var u_j = sigma_j^2 + 2 c_j^2 sigma_{j-1}^4 (mean 0, variance
+    sigma_j^2 where c_j = 0)."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((d, d))
+    A3 = rng.standard_normal((d, max(1, d // 10)))
+    eye = np.eye(d)
+
+    def gauss(prec):
+        cov = np.linalg.inv(prec)
+        return TargetSpec(TARGET_DENSE, d, d_y=d, G=np.ascontiguousarray(np.linalg.cholesky(prec).T),
+                          cov=0.5 * (cov + cov.T), mean=np.zeros(d))
+
+    B = A @ A.T
+    out = {1: gauss(B + eye), 2: gauss(B / d + eye), 3: gauss(A3 @ A3.T + eye)}
+    sig2, V = np.linalg.eigh(out[1].cov)              # ascending: v_1 belongs to the smallest eigenvalue
+    n = np.arange(1, d + 1, dtype=np.float64)
+    s2 = sigma2_4 if sigma2_4 is not None else 1.0 / d ** 2
+    prec4 = n ** -4.0 / s2 + 1.0
+    out[4] = TargetSpec(TARGET_DENSE, d, d_y=d, G=np.ascontiguousarray(np.sqrt(prec4)[:, None] * V.T),
+                        cov=(V / prec4) @ V.T, mean=np.zeros(d))
+    for key, b in ((5, b5), (6, b6)):
+        c = np.zeros(d)
+        for j in range(1, d // 10, 2):                # 0-based j = 1, 3, ...: the 1-based even indices <= d / 10
+            c[j] = b / sig2[j - 1] / math.sqrt(d)
+        umean = np.zeros(d)
+        uvar = sig2.copy()
+        tw = c != 0
+        umean[1:][tw[1:]] = -c[1:][tw[1:]] * sig2[:-1][tw[1:]]
+        uvar[1:][tw[1:]] += 2.0 * c[1:][tw[1:]] ** 2 * sig2[:-1][tw[1:]] ** 2
+        out[key] = TargetSpec(TARGET_TWIST, d, d_y=d, G=np.ascontiguousarray(V.T), lam=sig2.copy(), y=c,
+                              umean=umean, uvar=uvar)
+    return out
 
 
 def diag64() -> RunSpec:
