@@ -273,7 +273,9 @@ typedef struct {
     int32_t train_steps;        /* Adam steps per training */
     int32_t batch;              /* minibatch size (multiple of 128) */
     int32_t first_train_min;    /* pairs needed before the first training (at an interval end) */
-    int32_t reserved;
+    int32_t screen_from_start;  /* 1: stage 1 runs from diam_da_enable on, with the given weights and unit input
+                                   and output scaling (s = the O(d) terms + the network's output), until a training
+                                   decides otherwise; 0 (default): only after a training within rmse_bound */
     double lr, beta1, beta2, adam_eps;
     double rmse_bound;          /* held-out RMSE (nats) above which stage 1 is switched off */
     uint64_t seed;              /* minibatch selection stream */
@@ -310,6 +312,13 @@ DIAM_API diam_status diam_da_get_stats(diam_ctx* ctx, diam_da_stats* stats);
  * weights). For checking the training kernels. Synchronises. */
 DIAM_API diam_status diam_da_grad(diam_ctx* ctx, int32_t B, const double* U, const double* t, double* loss,
                                   double* gW1, double* gb1, double* gW2, double* gb2, double* gw3, double* gb3);
+
+/* One Adam step (Kingma & Ba 2015: bias-corrected first and second moments, the configured lr, beta1, beta2,
+ * adam_eps; the step count continues the context's) on the FP32 master weights with the given gradients (FP64
+ * host, rounded to FP32 on upload; same shapes as diam_da_enable's weights), through the kernel the training
+ * uses; the BF16 copies the network runs on are rewritten. For checking the training's update. Synchronises. */
+DIAM_API diam_status diam_da_adam_step(diam_ctx* ctx, const double* gW1, const double* gb1, const double* gW2,
+                                       const double* gb2, const double* gw3, const double* gb3);
 
 /* Current weights (FP32 masters, widened), same shapes as diam_da_enable's. Synchronises. */
 DIAM_API diam_status diam_da_get_weights(diam_ctx* ctx, double* W1, double* b1, double* W2, double* b2, double* w3,

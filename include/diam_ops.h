@@ -20,6 +20,13 @@ extern "C" {
 DIAM_API diam_status diam_op_normals(uint64_t seed, uint32_t problem_id, int64_t t0, int32_t n_steps, int32_t P, int32_t d,
                             int32_t ld, int32_t kind, void* out, void* stream);
 
+/* The library's bounded device wait as an op: one GPU thread waits until the device int *flag equals expected,
+ * or until limit_cycles SM clock cycles (at most 2^33, about four seconds) have passed, whichever comes first;
+ * DIAM_ETIMEOUT in the second case. The library's kernels bound every wait of theirs this way (a clock limit,
+ * then a recorded timeout instead of a hang); callers that order GPU work on a flag in device memory get the
+ * same guarantee. Nothing is left running when it returns; the device stays usable. Synchronises the stream. */
+DIAM_API diam_status diam_op_wait_flag(const int32_t* flag, int32_t expected, int64_t limit_cycles, void* stream);
+
 /* In-place lower Cholesky factor (Algorithm 1, "A_n = Cholesky(C_n)") of the n x n lower triangle of A
  * (row-major, stride lda, FP64); the strict upper triangle is zeroed. *info_host receives 0, or the
  * 1-based index of the first non-positive pivot. Synchronises the stream. */
@@ -50,7 +57,8 @@ DIAM_API diam_status diam_op_trsm_lower_f64_tc(int32_t n, int32_t nrows, const d
 /* D[n*ldd + m] = scale * sum_k A[m*lda + k] (B[n*ldb + k] + B2[n*ldb + k]) on the tensor cores (tcgen05):
  * A (M x K) and B, B2 (N x K) BF16 bits, K-contiguous, K, lda, ldb multiples of 64, 16-byte aligned
  * pointers; B2 may be NULL; FP32 accumulation; D FP32. a_lower: A is lower triangular and K blocks past
- * each 128-row tile are skipped (the batched noise product xi = beta alpha A_n W of Algorithm 1).
+ * each 128-row tile are skipped (the batched noise product xi = beta alpha A_n W of Algorithm 1); A's strict
+ * upper triangle must then be zero (which of its blocks are read depends on the tiling).
  * Synchronises the stream and reports a device-side timeout as DIAM_ETIMEOUT. */
 DIAM_API diam_status diam_op_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, int32_t lda, const uint16_t* B,
                               const uint16_t* B2, int32_t ldb, int32_t a_lower, float scale, float* D, int32_t ldd,
@@ -63,7 +71,8 @@ DIAM_API diam_status diam_op_gemm_bf16_tile(int32_t M, int32_t N, int32_t K, con
                                             const uint16_t* B, const uint16_t* B2, int32_t ldb, int32_t a_lower,
                                             float scale, float* D, int32_t ldd, int32_t bn, void* stream);
 
-/* The product of diam_op_gemm_bf16 (same arguments, same result within FP32 summation order) for callers
+/* The product of diam_op_gemm_bf16 (same arguments, same result within FP32 summation order; with a_lower, A's
+ * strict upper triangle must be zero, as there) for callers
  * that cannot allocate device memory: code whose device memory belongs to its own pool and forbids outside
  * allocations, or code on a latency-critical path that cannot afford the device-wide synchronisation that
  * cudaMalloc and cudaFree may cause.

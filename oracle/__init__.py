@@ -55,7 +55,8 @@ class OrcConfig(C.Structure):
                 ("refresh_delay", C.c_int32), ("prec", C.c_int32),
                 ("seed", C.c_uint64), ("problem_id", C.c_uint32), ("threads", C.c_int32),
                 ("trace_steps", C.c_int64), ("record_traj", C.c_int32), ("chain0", C.c_uint32),
-                ("burnin", C.c_int64), ("proposal", C.c_int32), ("pad2_", C.c_int32), ("eps_jitter_min", C.c_double)]
+                ("burnin", C.c_int64), ("proposal", C.c_int32), ("pad2_", C.c_int32), ("eps_jitter_min", C.c_double),
+                ("moments_mode", C.c_int32), ("pad3_", C.c_int32)]
 
 
 def lib():
@@ -89,6 +90,7 @@ def lib():
                 "orc_get_trace": (None, [P, P, P, P, P, P]),
                 "orc_get_traj": (None, [P, P]),
                 "orc_get_block_beta": (None, [P, P, I64]),
+                "orc_get_chain_factor": (None, [P, I32, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(l, name)
@@ -194,7 +196,7 @@ def default_config(**kw):
              acc_lo=0.3, acc_hi=0.5, beta_factor=1.1, beta_min=1e-4, beta_max=0.999,
              eps_jitter=1e-10, min_samples_refresh=-1, refresh_delay=0, prec=FP64,
              seed=0, problem_id=0, threads=1, trace_steps=0, record_traj=0, burnin=0, chain0=0, proposal=0,
-             eps_jitter_min=0.0)
+             eps_jitter_min=0.0, moments_mode=0)
     c.update(kw)
     if c["min_samples_refresh"] < 0:
         c["min_samples_refresh"] = c["d"] + 1
@@ -207,7 +209,7 @@ class Sampler:
     def __init__(self, cfg: dict, target: Target, x0=None, C0=None, xref0=None):
         self.cfg = dict(cfg)
         self.target = target
-        self._cs = OrcConfig(**{k: self.cfg[k] for k, _ in OrcConfig._fields_ if k not in ("pad_", "pad2_")})
+        self._cs = OrcConfig(**{k: self.cfg[k] for k, _ in OrcConfig._fields_ if k not in ("pad_", "pad2_", "pad3_")})
         self._ts = target.struct()
         d, P = self.cfg["d"], self.cfg["P"]
         self._x0 = None if x0 is None else np.ascontiguousarray(np.broadcast_to(x0, (P, d)), np.float64)
@@ -273,6 +275,13 @@ class Sampler:
         out = np.zeros((self.steps, P, d))
         lib().orc_get_traj(self._h, _ptr(out))
         return out
+
+    def chain_factor(self, p):
+        """Reading R2: chain p's factor, its quantised form, x_ref and beta."""
+        d = self.cfg["d"]
+        L = np.zeros((d, d)); Lq = np.zeros((d, d)); xr = np.zeros(d); b = C.c_double()
+        lib().orc_get_chain_factor(self._h, int(p), _ptr(L), _ptr(Lq), _ptr(xr), C.byref(b))
+        return L, Lq, xr, b.value
 
     def block_betas(self):
         n = self.steps // self.cfg["n_lag"]

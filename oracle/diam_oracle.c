@@ -257,6 +257,9 @@ typedef struct {
                                            adaptive Metropolis (Sec. 2.3.3) when A_n is refreshed */
     int32_t pad2_;
     double eps_jitter_min;              /* floor of the first jitter of the refresh rule */
+    int32_t moments_mode;               /* 0: reading R1, one factor from the moments pooled over all chains;
+                                           1: reading R2, the per-chain factors of Sec. 2.4.1 (refresh_delay 0) */
+    int32_t pad3_;
 } orc_config;
 
 typedef struct {
@@ -286,6 +289,15 @@ typedef struct {
     double *blk_beta;
     int64_t nblk_rec;
     double *scratch;                    /* threads x (4 d) */
+    /* reading R2: chain p proposes with its own factor A_n^p, x_ref^p and beta^p, refreshed every interval from
+     * its local view of the global moments, eq. (mom2pg), (mom1pg), (cov2pg): the raw sums of the batches merged
+     * so far (every chain's samples, eq. (mom2g), (mom1g)) plus chain p's own samples of the current batch */
+    double *Lp, *Lqp, *xrefp, *betap;   /* P x d x d, P x d x d, P x d, P */
+    int64_t *accp;                      /* accepted moves of each chain in the current interval */
+    double *Sloc, *sumloc;              /* P x d x d, P x d: sums of x x^T and x over the current batch */
+    int64_t nloc;                       /* samples of each chain in the current batch */
+    double *Sglob, *sumglob;            /* d x d, d: the same sums over the merged batches */
+    int64_t nglob;
 } orc_sampler;
 
 static double orc_logpi(const orc_sampler* s, const double* x, double* work) {
@@ -362,12 +374,12 @@ ORC_EXPORT double orc_target_logpi(const orc_target* T, const double* x) {
 
 /* q(v) = |Lq^{-1}(v - x_ref)|^2 / (2 infl^2): minus the log density of the reference Gaussian that the
  * proposal preserves (Algorithm 1's weighted quadratic, with the x_ref shift of eq. (diam)). */
-static double orc_quad(const orc_sampler* s, const double* v, double* work) {
+static double orc_quad(const orc_sampler* s, const double* Lq, const double* xref, const double* v, double* work) {
     int d = s->cfg.d;
     double* dv = work;
     double* z = work + d;
-    for (int i = 0; i < d; ++i) dv[i] = v[i] - s->xref[i];
-    orc_forward_sub(d, s->Lq, dv, z);
+    for (int i = 0; i < d; ++i) dv[i] = v[i] - xref[i];
+    orc_forward_sub(d, Lq, dv, z);
     double q = 0.0;
     for (int i = 0; i < d; ++i) q += z[i] * z[i];
     return 0.5 * q / (s->cfg.infl * s->cfg.infl);
@@ -429,6 +441,24 @@ ORC_EXPORT orc_sampler* orc_new(const orc_config* cfg, const orc_target* tgt, co
     orc_set_quantised_factor(s);
     if (xref0) orc_set_xref(s, xref0);
     s->beta = cfg->beta0;
+    if (cfg->moments_mode == 1) {   /* R2: every chain starts from A_0 and x_ref of the pooled start */
+        size_t pd = (size_t)P * d;
+        s->Lp = (double*)malloc(sizeof(double) * pd * d);
+        s->Lqp = (double*)malloc(sizeof(double) * pd * d);
+        s->xrefp = (double*)malloc(sizeof(double) * pd);
+        s->betap = (double*)malloc(sizeof(double) * P);
+        s->accp = (int64_t*)calloc((size_t)P, sizeof(int64_t));
+        s->Sloc = (double*)calloc(pd * d, sizeof(double));
+        s->sumloc = (double*)calloc(pd, sizeof(double));
+        s->Sglob = (double*)calloc(nn, sizeof(double));
+        s->sumglob = (double*)calloc((size_t)d, sizeof(double));
+        for (int p = 0; p < P; ++p) {
+            memcpy(s->Lp + (size_t)p * nn, s->L, sizeof(double) * nn);
+            memcpy(s->Lqp + (size_t)p * nn, s->Lq, sizeof(double) * nn);
+            memcpy(s->xrefp + (size_t)p * d, s->xref, sizeof(double) * d);
+            s->betap[p] = cfg->beta0;
+        }
+    }
     s->npend = cfg->refresh_delay + 1;
     s->pendL = (double**)calloc((size_t)s->npend, sizeof(double*));
     s->pendX = (double**)calloc((size_t)s->npend, sizeof(double*));
@@ -454,15 +484,105 @@ ORC_EXPORT void orc_free(orc_sampler* s) {
     free(s->pendL); free(s->pendX); free(s->pend_block);
     free(s->tr_lp); free(s->tr_q); free(s->tr_qc); free(s->tr_loga); free(s->tr_acc);
     free(s->traj); free(s->blk_beta); free(s->scratch);
+    free(s->Lp); free(s->Lqp); free(s->xrefp); free(s->betap); free(s->accp);
+    free(s->Sloc); free(s->sumloc); free(s->Sglob); free(s->sumglob);
     free(s);
 }
 
 /* End of an interval of n_lag steps (Algorithm 1, "if n = k n_lag"): beta update from the acceptance
  * ratio, moments, Cholesky of C_n; the new factor takes effect refresh_delay + 1 blocks later. */
+/* Factor of C + eps diag(C) with the refresh rule's retries (eps x100, four attempts in all): 0 on success. */
+static int orc_jittered_cholesky(orc_sampler* s, const double* C, double* L) {
+    const orc_config* c = &s->cfg;
+    int d = c->d;
+    size_t nn = (size_t)d * d;
+    double eps = c->eps_jitter > c->eps_jitter_min ? c->eps_jitter : c->eps_jitter_min;
+    int ok = -1;
+    double* Cj = (double*)malloc(sizeof(double) * nn);
+    for (int attempt = 0; attempt < 4 && ok != 0; ++attempt) {
+        memcpy(Cj, C, sizeof(double) * nn);
+        for (int i = 0; i < d; ++i) Cj[(size_t)i * d + i] *= 1.0 + eps;
+        ok = orc_cholesky(d, Cj, L);
+        eps *= 100.0;
+        s->chol_attempts++;
+    }
+    free(Cj);
+    return ok;
+}
+
+/* Interval end under reading R2 (Sec. 2.4.1): each chain's beta rule on its own acceptance; each chain's factor from
+ * its local view of the global moments, C^{p,glob} = S^{p,glob} - m^{p,glob} (m^{p,glob})^T, with
+ * S^{p,glob} = (sum over the merged batches + chain p's sum over this batch) / (their sample count) -- the
+ * weights k M P n_lag and m n_lag of eq. (mom2pg) as counts; after M intervals the batch's samples of every
+ * chain are merged into the global sums (eq. (mom2g), (mom1g)). */
+static void orc_block_end_r2(orc_sampler* s, int64_t blk) {
+    const orc_config* c = &s->cfg;
+    int d = c->d, P = c->P;
+    size_t nn = (size_t)d * d;
+    int64_t acc_blk = 0;
+    for (int p = 0; p < P; ++p) {
+        acc_blk += s->accp[p];
+        if (c->adapt_beta) {
+            double ahat = (double)s->accp[p] / (double)c->n_lag;
+            double b = s->betap[p];
+            if (ahat > c->acc_hi) b *= c->beta_factor;
+            else if (ahat < c->acc_lo) b /= c->beta_factor;
+            if (b < c->beta_min) b = c->beta_min;
+            if (b > c->beta_max) b = c->beta_max;
+            s->betap[p] = b;
+        }
+        s->accp[p] = 0;
+    }
+    if ((blk + 1) * (int64_t)c->n_lag > c->burnin) s->acc_total += acc_blk;
+    s->acc_block = 0;
+    const int64_t n = s->nglob + s->nloc;
+    if (s->acc_total >= c->min_samples_refresh && n > 0) {
+        double* m = (double*)malloc(sizeof(double) * d);
+        double* C = (double*)malloc(sizeof(double) * nn);
+        double* L = (double*)malloc(sizeof(double) * nn);
+        int any = 0;
+        for (int p = 0; p < P; ++p) {
+            const double* Sl = s->Sloc + (size_t)p * nn;
+            const double* sl = s->sumloc + (size_t)p * d;
+            for (int i = 0; i < d; ++i) m[i] = (s->sumglob[i] + sl[i]) / (double)n;
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j)
+                    C[(size_t)i * d + j] = (s->Sglob[(size_t)i * d + j] + Sl[(size_t)i * d + j]) / (double)n - m[i] * m[j];
+            if (orc_jittered_cholesky(s, C, L) == 0) {
+                double* Lp = s->Lp + (size_t)p * nn;
+                double* Lqp = s->Lqp + (size_t)p * nn;
+                memcpy(Lp, L, sizeof(double) * nn);
+                for (size_t k = 0; k < nn; ++k) Lqp[k] = c->prec == 2 ? orc_round_bf16(L[k]) : L[k];
+                if (c->xref_mode == 1 && c->proposal == 0)
+                    for (int i = 0; i < d; ++i) s->xrefp[(size_t)p * d + i] = c->prec == 2 ? orc_round_f32(m[i]) : m[i];
+                any = 1;
+            } else {
+                s->notspd++;
+            }
+        }
+        if (any) s->refreshes++;
+        free(m); free(C); free(L);
+    }
+    if ((blk + 1) % (c->M > 0 ? c->M : 1) == 0) {   /* the batch's samples of every chain join the global sums */
+        for (int p = 0; p < P; ++p) {
+            for (size_t k = 0; k < nn; ++k) s->Sglob[k] += s->Sloc[(size_t)p * nn + k];
+            for (int i = 0; i < d; ++i) s->sumglob[i] += s->sumloc[(size_t)p * d + i];
+        }
+        s->nglob += (int64_t)P * s->nloc;
+        memset(s->Sloc, 0, sizeof(double) * (size_t)P * nn);
+        memset(s->sumloc, 0, sizeof(double) * (size_t)P * d);
+        s->nloc = 0;
+    }
+}
+
 static void orc_block_end(orc_sampler* s, int64_t blk) {
     const orc_config* c = &s->cfg;
     int d = c->d;
     size_t nn = (size_t)d * d;
+    if (c->moments_mode == 1) {
+        orc_block_end_r2(s, blk);
+        return;
+    }
     /* beta adaptation: raise above the window, lower below it (Algorithm 1; window of Sec. 3.2) */
     if (c->adapt_beta) {
         double ahat = (double)s->acc_block / ((double)c->P * c->n_lag);
@@ -530,10 +650,7 @@ static void orc_step(orc_sampler* s) {
     int d = c->d, P = c->P;
     int64_t t = s->t;
     if (t % c->n_lag == 0) orc_block_begin(s, t / c->n_lag);
-    double beta = s->beta;
-    const int rw = c->proposal == 1;
-    double rho = sqrt(1.0 - beta * beta);
-    double ba = beta * c->infl;
+    const int rw = c->proposal == 1, r2 = c->moments_mode == 1;
     int8_t* acc = (int8_t*)calloc((size_t)P, 1);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(c->threads > 0 ? c->threads : 1)
@@ -546,6 +663,11 @@ static void orc_step(orc_sampler* s) {
         double* work = s->scratch + (size_t)tid * 4 * d;
         double* xp = work + 2 * d;
         double* Wd = work + 3 * d;
+        /* the proposal's factor, x_ref and beta: the pooled ones (R1) or chain p's own (R2) */
+        const double* Lq = r2 ? s->Lqp + (size_t)p * d * d : s->Lq;
+        const double* xref = r2 ? s->xrefp + (size_t)p * d : s->xref;
+        const double beta = r2 ? s->betap[p] : s->beta;
+        const double rho = sqrt(1.0 - beta * beta), ba = beta * c->infl;
         float* Wf = (float*)malloc(sizeof(float) * d);
         orc_normals(c->seed, c->problem_id, t, c->chain0 + (uint32_t)p, d, Wf);
         for (int i = 0; i < d; ++i) Wd[i] = c->prec == 2 ? orc_round_bf16((double)Wf[i]) : (double)Wf[i];
@@ -554,14 +676,14 @@ static void orc_step(orc_sampler* s) {
         /* DIAM: x* = x_ref + sqrt(1 - beta^2)(x_n - x_ref) + beta * infl * A_n W_n;  RW: x* = x_n + beta * infl * A_n W_n */
         for (int i = 0; i < d; ++i) {
             double xi = 0.0;
-            for (int k = 0; k <= i; ++k) xi += s->Lq[(size_t)i * d + k] * Wd[k];
-            xp[i] = rw ? x[i] + ba * xi : s->xref[i] + rho * (x[i] - s->xref[i]) + ba * xi;
+            for (int k = 0; k <= i; ++k) xi += Lq[(size_t)i * d + k] * Wd[k];
+            xp[i] = rw ? x[i] + ba * xi : xref[i] + rho * (x[i] - xref[i]) + ba * xi;
         }
         double lpp = orc_logpi(s, xp, work);
         /* q: minus the log density of the Gaussian the DIAM move preserves; the random walk's density is
          * symmetric and cancels (eq. (rw)) */
-        double qp = rw ? 0.0 : orc_quad(s, xp, work);
-        double qc = rw ? 0.0 : orc_quad(s, x, work);
+        double qp = rw ? 0.0 : orc_quad(s, Lq, xref, xp, work);
+        double qc = rw ? 0.0 : orc_quad(s, Lq, xref, x, work);
         double loga = lpp + qp - (s->lp[p] + qc);
         double u = orc_uniform(c->seed, c->problem_id, ORC_TAG_U, t, c->chain0 + (uint32_t)p);
         int a = log(u) < loga;
@@ -581,13 +703,23 @@ static void orc_step(orc_sampler* s) {
         const double* x = s->x + (size_t)p * d;
         s->acc_block += acc[p];
         s->acc_all += acc[p];
+        if (r2) s->accp[p] += acc[p];
         if (t < c->burnin) continue;
         for (int i = 0; i < d; ++i) {
             s->sum[i] += x[i];
             for (int j = 0; j < d; ++j) s->S[(size_t)i * d + j] += x[i] * x[j];
         }
         s->n += 1;
+        if (r2) {   /* chain p's own sums over the current batch */
+            double* Sl = s->Sloc + (size_t)p * d * d;
+            double* sl = s->sumloc + (size_t)p * d;
+            for (int i = 0; i < d; ++i) {
+                sl[i] += x[i];
+                for (int j = 0; j < d; ++j) Sl[(size_t)i * d + j] += x[i] * x[j];
+            }
+        }
     }
+    if (r2 && t >= c->burnin) s->nloc += 1;
     free(acc);
     if (s->traj) memcpy(s->traj + (size_t)t * P * d, s->x, sizeof(double) * (size_t)P * d);
     s->t = t + 1;
@@ -635,6 +767,16 @@ ORC_EXPORT void orc_get_factor(const orc_sampler* s, double* L, double* Lq, doub
     if (Lq) memcpy(Lq, s->Lq, sizeof(double) * nn);
     if (xref) memcpy(xref, s->xref, sizeof(double) * s->cfg.d);
 }
+/* Reading R2: chain p's factor in use, its quantised form and x_ref, and its beta. */
+ORC_EXPORT void orc_get_chain_factor(const orc_sampler* s, int p, double* L, double* Lq, double* xref, double* beta) {
+    size_t nn = (size_t)s->cfg.d * s->cfg.d;
+    if (!s->Lp || p < 0 || p >= s->cfg.P) return;
+    if (L) memcpy(L, s->Lp + (size_t)p * nn, sizeof(double) * nn);
+    if (Lq) memcpy(Lq, s->Lqp + (size_t)p * nn, sizeof(double) * nn);
+    if (xref) memcpy(xref, s->xrefp + (size_t)p * s->cfg.d, sizeof(double) * s->cfg.d);
+    if (beta) *beta = s->betap[p];
+}
+
 /* mean m_n and covariance C_n of eq. (sampmean) / eq. (sampcov) */
 ORC_EXPORT void orc_get_moments(const orc_sampler* s, double* mean, double* cov) {
     int d = s->cfg.d;

@@ -49,7 +49,7 @@ class DiamConfig(C.Structure):
 class DiamDaConfig(C.Structure):
     _fields_ = [("h1", C.c_int32), ("h2", C.c_int32), ("retrain_every", C.c_int32), ("ring", C.c_int32),
                 ("train_steps", C.c_int32), ("batch", C.c_int32), ("first_train_min", C.c_int32),
-                ("reserved", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("screen_from_start", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
                 ("adam_eps", C.c_double), ("rmse_bound", C.c_double), ("seed", C.c_uint64)]
 
 
@@ -120,6 +120,7 @@ def lib():
                 "diam_da_get_stats": (C.c_int, [P, P]),
                 "diam_da_grad": (C.c_int, [P, I32, P, P, P, P, P, P, P, P, P]),
                 "diam_da_get_weights": (C.c_int, [P, P, P, P, P, P, P]),
+                "diam_da_adam_step": (C.c_int, [P, P, P, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(l, name)
@@ -471,6 +472,12 @@ class Sampler:
         self._check(self._l.diam_da_grad(self._h, B, _p(U), _p(t), C.byref(loss),
                                          *[_p(out[k]) for k in ("W1", "b1", "W2", "b2", "w3", "b3")]), "diam_da_grad")
         return loss.value, out
+
+    def da_adam_step(self, grads: dict):
+        """One Adam update of the network with the given gradients (diam_da_adam_step)."""
+        g = {k: np.ascontiguousarray(grads[k], np.float64) for k in ("W1", "b1", "W2", "b2", "w3", "b3")}
+        self._check(self._l.diam_da_adam_step(self._h, *[_p(g[k]) for k in ("W1", "b1", "W2", "b2", "w3", "b3")]),
+                    "diam_da_adam_step")
 
     def da_weights(self) -> dict:
         h1, h2 = self._da_h

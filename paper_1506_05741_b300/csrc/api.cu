@@ -73,7 +73,8 @@ struct diam_ctx {
         cudaEvent_t fork = nullptr, start = nullptr, done = nullptr;   // start / done: timed
         OzakiWs oz;
         double *Cr = nullptr, *M2s = nullptr;   // its matrix; the moments it was built from (for retries)
-        int* info = nullptr;                    // its failing pivot + 1 (device)
+        int* info = nullptr;                    // its failing pivot + 1, then its own status word (device, 2 ints):
+                                                // a device-side timeout in it is reported when it is resolved
         Captured graph;
         bool active = false;
         int64_t blk = 0, n = 0;
@@ -107,7 +108,7 @@ struct diam_ctx {
     double *lp = nullptr, *q = nullptr, *qp = nullptr, *lpo = nullptr, *lpp = nullptr, *partial = nullptr;
     double *xref64 = nullptr, *L = nullptr, *Lq64 = nullptr, *mean = nullptr, *M2 = nullptr, *cen64 = nullptr;
     double *colpart = nullptr, *svec = nullptr, *delta = nullptr, *Cw = nullptr, *work = nullptr;
-    uint16_t *Lq16 = nullptr, *op_hi = nullptr, *op_lo = nullptr, *histT = nullptr;
+    uint16_t *Lq16 = nullptr, *op_hi = nullptr, *op_lo = nullptr, *op_lo2 = nullptr, *histT = nullptr;
     double *qpart = nullptr, *lpart = nullptr, *s16 = nullptr;   // per-chunk proposal sums; BF16 record sums
     int8_t* accf = nullptr;                                      // per-chain decision of the current step
     float* ws = nullptr;                                         // split-K partial target products (BF16 mode)
@@ -357,13 +358,19 @@ static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
             EpiStore epi{c->ubuf, c->dy, 1.0, nullptr, 0.0};
             CK((gemm_f64<true, true>(c->dy, P, d, c->Gm, d, (const double*)src, d, TileRange{0, 0}, epi, c->st)));
             { twisted_lp_kernel<double><<<P, kThreads, 0, c->st>>>(c->dy, c->ubuf, c->dy, c->tw_ilam, c->tw_c, out); count_launch(); }
-        } else {   // x as BF16 hi + lo planes against the BF16 map, FP32 accumulation
-            { od_terms_kernel<T><<<P, kThreads, 0, c->st>>>(d, src, c->lpo, c->tg, c->op_hi, c->op_lo, c->ldk); count_launch(); }
+        } else {   // x as three BF16 terms (hi + lo + lo2 = x) against the BF16 map, FP32 accumulation: the
+                   // twist's coefficients (up to 1 / (sqrt(d) lambda)) amplify any error in u
+            { od_terms_kernel<T><<<P, kThreads, 0, c->st>>>(d, src, c->lpo, c->tg, c->op_hi, c->op_lo, c->ldk, c->op_lo2); count_launch(); }
             TcEpi epi{};
             epi.mode = TC_STORE;
             epi.D = c->ws;
             epi.ldd = c->dy;
             CK(tc_gemm_bf16(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, 0, epi, &c->ctl->status, c->st));
+            float* w2 = c->ws + (size_t)P * c->dy;   // the second plane of the split-K workspace
+            epi.D = w2;
+            CK(tc_gemm_bf16(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_lo2, nullptr, c->ldk, 0, epi, &c->ctl->status, c->st));
+            const size_t n = (size_t)P * c->dy;
+            { add_f32_kernel<<<(unsigned)std::min<size_t>(148 * 8, blocks_for(n)), kThreads, 0, c->st>>>(n, c->ws, w2); count_launch(); }
             { twisted_lp_kernel<float><<<P, kThreads, 0, c->st>>>(c->dy, c->ws, c->dy, c->tw_ilam, c->tw_c, out); count_launch(); }
         }
         CK(cudaGetLastError());
@@ -468,15 +475,23 @@ static diam_status rec_xref(diam_ctx* c) {
     return DIAM_OK;
 }
 
-// A x of the current states, exactly (hi + lo split of x, as for log pi), at an interval start.
+// A x of the current states at an interval start: x split into three BF16 terms (hi + lo + lo2 = x exactly), the
+// products of A (BF16) with them accumulated in FP32 (two passes: hi + lo, then lo2, added). Every step's map
+// A x* = rho (A x) + ... carries this value through the interval, so its error stays in the chain's map terms.
 static diam_status rec_ax(diam_ctx* c) {
     if (!c->rec) return DIAM_OK;
-    { od_terms_kernel<float><<<c->P, kThreads, 0, c->st>>>(c->d, (const float*)c->X, c->lpo, c->tg, c->op_hi, c->op_lo, c->ldk); count_launch(); }
+    { od_terms_kernel<float><<<c->P, kThreads, 0, c->st>>>(c->d, (const float*)c->X, c->lpo, c->tg, c->op_hi, c->op_lo,
+                                                          c->ldk, c->op_lo2); count_launch(); }
     TcEpi epi{};
     epi.mode = TC_STORE;
     epi.D = c->Ax;
     epi.ldd = c->dy;
     CK(tc_gemm_bf16(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, 0, epi, &c->ctl->status, c->st));
+    epi.D = c->ws;
+    CK(tc_gemm_bf16(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_lo2, nullptr, c->ldk, 0, epi, &c->ctl->status, c->st));
+    const size_t n = (size_t)c->P * c->dy;
+    { add_f32_kernel<<<(unsigned)std::min<size_t>(148 * 8, blocks_for(n)), kThreads, 0, c->st>>>(n, c->Ax, c->ws); count_launch(); }
+    CK(cudaGetLastError());
     c->ax_dirty = false;
     return DIAM_OK;
 }
@@ -936,11 +951,11 @@ static diam_status refresh_launch(diam_ctx* c, int64_t blk) {
     CK(cudaMemcpyAsync(r.M2s, c->M2, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, c->st));
     Pending& pd = c->pend[(size_t)(blk % (int64_t)c->pend.size())];
     CK(cudaMemcpyAsync(pd.mean, c->mean, sizeof(double) * d, cudaMemcpyDeviceToDevice, c->st));
-    CK(cudaMemsetAsync(r.info, 0, sizeof(int), c->st));
+    CK(cudaMemsetAsync(r.info, 0, 2 * sizeof(int), c->st));
     CK(cudaEventRecord(r.fork, c->st));
     CK(cudaStreamWaitEvent(r.rs, r.fork, 0));
     CK(cudaEventRecord(r.start, r.rs));
-    auto body = [&]() { return cholesky_f64(r.Cr, d, d, r.info, r.rs, &r.oz, &c->ctl->status); };
+    auto body = [&]() { return cholesky_f64(r.Cr, d, d, r.info, r.rs, &r.oz, r.info + 1); };
     if (r.oz.hi) {   // after a first eager factorisation (which creates the workspace's streams)
         CKS(run_captured(c, r.graph, body, r.rs));
     } else {
@@ -969,8 +984,11 @@ static diam_status refresh_finish_slot(diam_ctx* c, diam_ctx::AsyncRefresh& r) {
         c->prof_ms[PH_REFRESH] += ms;
         c->prof_cnt[PH_REFRESH] += 1;
     }
-    int info = 0;
-    CK(d2h(c, &info, r.info, sizeof(int)));
+    int iv[2] = {0, 0};
+    CK(d2h(c, iv, r.info, sizeof(iv)));
+    if (iv[1] == DEV_TIMEOUT) return fail(c, DIAM_ETIMEOUT, "refresh", "a bounded wait inside the factorisation expired");
+    if (iv[1] != 0) return fail(c, DIAM_ECUDA, "refresh", "a factorisation kernel reported a bad argument");
+    int info = iv[0];
     c->chol_attempts++;
     Pending& pd = c->pend[(size_t)(r.blk % (int64_t)c->pend.size())];
     bool ok = info == 0;
@@ -1248,7 +1266,7 @@ static diam_status alloc_all(diam_ctx* c) {
                 diam_ctx::AsyncRefresh& r = c->ar[i];
                 CKS(dalloc(c, &r.Cr, sizeof(double) * d * d));
                 CKS(dalloc(c, &r.M2s, sizeof(double) * d * d));
-                CKS(dalloc(c, &r.info, sizeof(int)));
+                CKS(dalloc(c, &r.info, 2 * sizeof(int)));
                 CKS(dalloc(c, &r.oz.SL, ozaki_sl_bytes(d)));
                 CKS(dalloc(c, &r.oz.ex, ozaki_ex_bytes(d)));
                 r.oz.cap_rows = d;
@@ -1263,6 +1281,7 @@ static diam_status alloc_all(diam_ctx* c) {
         CKS(dalloc(c, &c->Lq16, sizeof(uint16_t) * (size_t)d * c->ldk));
         CKS(dalloc(c, &c->op_hi, sizeof(uint16_t) * (size_t)P * c->ldk));
         CKS(dalloc(c, &c->op_lo, sizeof(uint16_t) * (size_t)P * c->ldk));
+        CKS(dalloc(c, &c->op_lo2, sizeof(uint16_t) * (size_t)P * c->ldk));
         c->ldw = c->ldk;
         c->ldh = d;
         CKS(dalloc(c, &c->W, sizeof(uint16_t) * rows * c->ldw));
@@ -1907,6 +1926,33 @@ diam_status diam_da_get_stats(diam_ctx* c, diam_da_stats* s) {
     s->active = c->da->active ? 1 : 0;
     s->pad = 0;
     return DIAM_OK;
+}
+
+diam_status diam_da_adam_step(diam_ctx* c, const double* gW1, const double* gb1, const double* gW2, const double* gb2,
+                              const double* gw3, const double* gb3) {
+    CKS(check_usable(c));
+    if (!c->da || !gW1 || !gb1 || !gW2 || !gb2 || !gw3 || !gb3) return fail(c, DIAM_EINVAL, "diam_da_adam_step");
+    DaState* a = c->da;
+    const int d = c->d, h1 = a->h1, h2 = a->h2;
+    CKS(sync_and_check(c));
+    // the gradient buffers in the layouts the training writes: dW1 as [d][h1], dW2 as [h1][h2]
+    std::vector<float> t((size_t)c->ldk * h1, 0.f);
+    for (int i = 0; i < h1; ++i)
+        for (int k = 0; k < d; ++k) t[(size_t)k * h1 + i] = (float)gW1[(size_t)i * d + k];
+    CK(h2d(c, a->gW1T, t.data(), sizeof(float) * t.size()));
+    t.assign((size_t)h1 * h2, 0.f);
+    for (int o = 0; o < h2; ++o)
+        for (int i = 0; i < h1; ++i) t[(size_t)i * h2 + o] = (float)gW2[(size_t)o * h1 + i];
+    CK(h2d(c, a->gW2T, t.data(), sizeof(float) * t.size()));
+    auto up = [&](float* dst, const double* src, size_t n) -> diam_status {
+        std::vector<float> v(src, src + n);
+        CK(h2d(c, dst, v.data(), sizeof(float) * n));
+        return DIAM_OK;
+    };
+    CKS(up(a->gb1, gb1, h1)); CKS(up(a->gb2, gb2, h2)); CKS(up(a->gw3, gw3, h2)); CKS(up(a->gb3, gb3, 1));
+    da_adam(c);
+    CK(cudaGetLastError());
+    return sync_and_check(c);
 }
 
 diam_status diam_da_get_weights(diam_ctx* c, double* W1, double* b1, double* W2, double* b2, double* w3, double* b3) {

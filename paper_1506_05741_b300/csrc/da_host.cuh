@@ -309,5 +309,9 @@ static diam_status da_alloc(diam_ctx* c, const diam_da_config* g, const double* 
     { quant_weights_kernel<<<std::min<unsigned>(148 * 8, blocks_for((size_t)h1 * d)), kThreads, 0, c->st>>>(h1, d, a->W1, a->W1q, ldk, nullptr, 0); count_launch(); }
     { quant_weights_kernel<<<std::min<unsigned>(148 * 8, blocks_for((size_t)h2 * h1)), kThreads, 0, c->st>>>(h2, h1, a->W2, a->W2q, h1, a->W2Tq, h2); count_launch(); }
     CK(cudaGetLastError());
+    if (g->screen_from_start) {   // stage 1 from now on with the given network, unit scalings (shift 0, scale 1)
+        a->active = true;
+        CKS(da_refresh_s_cur(c));
+    }
     return sync_and_check(c);
 }

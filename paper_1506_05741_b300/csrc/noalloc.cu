@@ -45,14 +45,20 @@ __global__ void prep_kernel(Head* h) {
     h->scale_one = 1.0;
 }
 
-// D[n*ldd + m] = scale * sum_s part[s][n][m], the splits summed in a fixed order
-__global__ void reduce_kernel(int M, int N, int S, const float* __restrict__ part, float scale, float* __restrict__ D,
-                              int ldd) {
+constexpr int kMaxSplits = 4;
+struct SplitRows {
+    int m0[kMaxSplits];   // split s wrote rows m >= m0[s] of its plane (a lower-triangular A: rows above get nothing)
+};
+
+// D[n*ldd + m] = scale * sum_s part[s][n][m] over the splits that wrote row m, summed in a fixed order
+__global__ void reduce_kernel(int M, int N, int S, const float* __restrict__ part, SplitRows rows, float scale,
+                              float* __restrict__ D, int ldd) {
     const size_t plane = (size_t)M * N;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane; idx += (size_t)gridDim.x * blockDim.x) {
-        float acc = 0.f;
-        for (int s = 0; s < S; ++s) acc += part[s * plane + idx];
         const size_t n = idx / M, m = idx % M;
+        float acc = 0.f;
+        for (int s = 0; s < S; ++s)
+            if ((int)m >= rows.m0[s]) acc += part[s * plane + idx];
         D[n * ldd + m] = scale * acc;
     }
 }
@@ -89,29 +95,34 @@ extern "C" diam_status diam_op_gemm_bf16_noalloc(int32_t M, int32_t N, int32_t K
     cudaStream_t st = (cudaStream_t)stream;
     Head* head = (Head*)base;
     float* part = (float*)(base + kHeadBytes);
-    // as many K splits (of whole 64-wide blocks) as the scratch holds, at most 4
+    // as many K splits (of whole 64-wide blocks) as the scratch holds, at most kMaxSplits
     const int kblocks = K / 64;
-    int S = (int)std::min<size_t>(std::min<size_t>(4, (size_t)kblocks), kPartialFloats / plane);
+    int S = (int)std::min<size_t>(std::min<size_t>(kMaxSplits, (size_t)kblocks), kPartialFloats / plane);
     const int per = (kblocks + S - 1) / S;
     { prep_kernel<<<1, 1, 0, st>>>(head); count_launch(); }
     int used = 0;
+    SplitRows rows{};
     for (int s = 0; s < S; ++s) {
         const int kb0 = s * per, kb1 = std::min(kblocks, kb0 + per);
         if (kb0 >= kb1) break;
+        // split s reads K columns [64 kb0, 64 kb1) through offset operands. With a lower-triangular A (zero
+        // strict upper part), rows m < 64 kb0 get nothing from these columns and the rows from 64 kb0 on form a
+        // lower-triangular block again in the split's own frame: the split covers those rows only, with the
+        // triangular K skip, and the reduction leaves its plane's upper rows out
+        const int m0 = a_lower ? 64 * kb0 : 0;
+        if (m0 >= M) break;
         TcEpi epi{};
         epi.mode = TC_STORE;
-        epi.D = part + (size_t)s * plane;
+        epi.D = part + (size_t)used * plane + m0;
         epi.ldd = M;
         epi.scale_dev = &head->scale_one;
-        // split s reads K columns [64 kb0, 64 kb1) through offset operands; a lower-triangular A needs no
-        // special case (its zero upper part contributes nothing), so the split runs as a full product
-        (void)a_lower;
-        if (tc_gemm_bf16(M, N, (kb1 - kb0) * 64, A + (size_t)kb0 * 64, lda, B + (size_t)kb0 * 64,
-                         B2 ? B2 + (size_t)kb0 * 64 : nullptr, ldb, 0, epi, &head->status, st) != cudaSuccess)
+        if (tc_gemm_bf16(M - m0, N, (kb1 - kb0) * 64, A + (size_t)m0 * lda + (size_t)kb0 * 64, lda, B + (size_t)kb0 * 64,
+                         B2 ? B2 + (size_t)kb0 * 64 : nullptr, ldb, a_lower ? 1 : 0, epi, &head->status, st) != cudaSuccess)
             return DIAM_ECUDA;
+        rows.m0[used] = m0;
         ++used;
     }
-    { reduce_kernel<<<(unsigned)std::min<size_t>(148 * 16, (plane + 255) / 256), 256, 0, st>>>(M, N, used, part, scale, D, ldd); count_launch(); }
+    { reduce_kernel<<<(unsigned)std::min<size_t>(148 * 16, (plane + 255) / 256), 256, 0, st>>>(M, N, used, part, rows, scale, D, ldd); count_launch(); }
     if (cudaGetLastError() != cudaSuccess) return DIAM_ECUDA;
     int status = 0;
     if (cudaMemcpyAsync(&status, &head->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return DIAM_ECUDA;

@@ -15,6 +15,18 @@ struct OpScratch {
     int info;
     double scale;
 };
+// Thread 0 spins until *flag == expected or limit SM clock cycles have passed; the outcome goes to *status.
+__global__ void wait_flag_kernel(const volatile int* flag, int expected, long long limit, int* status) {
+    const long long t0 = clock64();
+    int st = DEV_OK;
+    while (*flag != expected) {
+        if (clock64() - t0 > limit) {
+            st = DEV_TIMEOUT;
+            break;
+        }
+    }
+    *status = st;
+}
 }  // namespace ops_detail
 using namespace ops_detail;
 
@@ -44,6 +56,19 @@ diam_status diam_op_normals(uint64_t seed, uint32_t problem_id, int64_t t0, int3
     else if (kind == 1) { gen_w_kernel<double><<<g, 128, 0, st>>>(key, t0, P, d, ld, (double*)out); count_launch(); }
     else { gen_w_kernel<uint16_t><<<g, 128, 0, st>>>(key, t0, P, d, ld, (uint16_t*)out); count_launch(); }
     return cudaGetLastError() == cudaSuccess ? DIAM_OK : DIAM_ECUDA;
+}
+
+diam_status diam_op_wait_flag(const int32_t* flag, int32_t expected, int64_t limit_cycles, void* stream) {
+    if (!flag || limit_cycles < 0 || limit_cycles > (1ll << 33)) return DIAM_EINVAL;
+    OpScratch* sc = op_scratch();
+    if (!sc) return DIAM_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    { wait_flag_kernel<<<1, 1, 0, st>>>(flag, expected, (long long)limit_cycles, &sc->status); count_launch(); }
+    if (cudaGetLastError() != cudaSuccess) return DIAM_ECUDA;
+    int status = 0;
+    if (cudaMemcpyAsync(&status, &sc->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return DIAM_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return DIAM_ECUDA;
+    return status == DEV_TIMEOUT ? DIAM_ETIMEOUT : DIAM_OK;
 }
 
 diam_status diam_op_cholesky_f64(int32_t n, double* A, int32_t lda, int32_t* info_host, void* stream) {

@@ -17,6 +17,7 @@
 // A CTA keeps the 7 B slices of a 16-row tile in shared memory and walks a run of 128-row tiles of A, whose
 // slices stream through a four-stage ring; slice a of A meets B slices 0 .. 6 - a in one product of width
 // 16 (7 - a), and the 7 group accumulators of a tile fill one of two tensor-memory buffers.
+#include <mutex>
 #include "linalg.h"
 #include "ozaki_slice.cuh"
 #include "tc_common.cuh"
@@ -269,12 +270,19 @@ static cudaError_t launch_update(const uint16_t* SA, int Ma, const int* exA, con
                                  const int* exB, double* Cm, int ldc, int lower, int* status, cudaStream_t st) {
     CUtensorMap mA, mB;
     if (!make_map(&mA, SA, Ma, OZ_LD, 128) || !make_map(&mB, SB, Nb, OZ_LD, OZ_BN)) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(ozaki_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_smem());
-        if (e != cudaSuccess) return e;
-        attr = true;
+    // the dynamic shared-memory attribute applies to the current device only: set once per device
+    static std::mutex attr_mu;
+    static bool attr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> g(attr_mu);
+        if (!attr[dev]) {
+            cudaError_t e =
+                cudaFuncSetAttribute(ozaki_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_smem());
+            if (e != cudaSuccess) return e;
+            attr[dev] = true;
+        }
     }
     // A tiles per unit: about four units per SM over the whole update (two resident at a time), at most 8
     const int tiles = oz_units(Ma, Nb, lower, 1, 0, nullptr);

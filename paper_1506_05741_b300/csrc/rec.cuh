@@ -5,8 +5,9 @@
 // linear in x, so A x* = rho (A x) + (1 - rho) (A x_ref) + (A A_n) (beta alpha W): with M = A A_n formed once
 // per refresh and the products M W of a whole interval in one GEMM (Algorithm 1's batching of the noise
 // product, extended to the map), each step needs only O(d_y) work per chain instead of a d_y x d product.
-// A x of the current states is recomputed exactly at every interval start; accepted chains copy A x*.
-// M is kept as a two-term BF16 split (hi + lo, relative error ~2^-17), as the states are for A x.
+// A x of the current states is recomputed at every interval start from the states split into three BF16
+// terms (hi + lo + lo2 = x exactly; FP32 accumulation); accepted chains copy A x*. M is kept as a two-term
+// BF16 split (hi + lo, relative error ~2^-17): its error enters each step's map through beta alpha M W only.
 #pragma once
 #include "common.cuh"
 
@@ -23,6 +24,11 @@ __global__ void split_hi_lo_kernel(int rows, int cols, int ld, const float* __re
         hi[(size_t)r * ld + c] = h;
         lo[(size_t)r * ld + c] = f32_to_bf16_bits(v - bf16_bits_to_f32(h));
     }
+}
+
+// D[i] += E[i] for i < n (the last term of a product split over K passes)
+__global__ void add_f32_kernel(size_t n, float* __restrict__ D, const float* __restrict__ E) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) D[i] += E[i];
 }
 
 // axref[m] = sum_k A[m][k] x_ref[k] (A the BF16 map, stride ld), FP64 sums; one block per row.

@@ -232,11 +232,14 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
     }
 }
 
-// O(d) part of log pi for any state buffer (initial state, imported state); BF16 operand planes if asked.
+// O(d) part of log pi for any state buffer (initial state, imported state); BF16 operand planes if asked:
+// x = hi + lo to 16 bits of x's mantissa, and with op_lo2 also lo2 = bf16(x - hi - lo), so hi + lo + lo2 = x
+// exactly (FP32 x: 24 bits in three 8-bit pieces, each difference exact in FP32).
 template <typename T>
 __global__ void __launch_bounds__(256) od_terms_kernel(int d, const T* __restrict__ Xs, double* __restrict__ lpo,
                                                        TargetDev tg, uint16_t* __restrict__ op_hi,
-                                                       uint16_t* __restrict__ op_lo, int ldk) {
+                                                       uint16_t* __restrict__ op_lo, int ldk,
+                                                       uint16_t* __restrict__ op_lo2 = nullptr) {
     __shared__ double sh[32];
     const int p = blockIdx.x;
     const T* x = Xs + (size_t)p * d;
@@ -247,7 +250,10 @@ __global__ void __launch_bounds__(256) od_terms_kernel(int d, const T* __restric
         if (op_hi) {
             uint16_t h = f32_to_bf16_bits((float)v);
             op_hi[(size_t)p * ldk + i] = h;
-            op_lo[(size_t)p * ldk + i] = f32_to_bf16_bits((float)v - bf16_bits_to_f32(h));
+            const float r = (float)v - bf16_bits_to_f32(h);
+            const uint16_t l = f32_to_bf16_bits(r);
+            op_lo[(size_t)p * ldk + i] = l;
+            if (op_lo2) op_lo2[(size_t)p * ldk + i] = f32_to_bf16_bits(r - bf16_bits_to_f32(l));
         }
     }
     lacc = block_sum(lacc, sh);

@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------------------------------- host
+constexpr int kAttrDevices = 64;   // devices a process can drive (per-device launch attributes)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -265,11 +266,18 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
     size_t smem = 1024 + stages * stage + 256;
     const size_t red = (size_t)TC_BM * (BN + 1) * 4;
     if (smem < 1024 + red + 256) smem = 1024 + red + 256;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    // the 227 KB dynamic shared-memory attribute applies to the current device only: set once per device
+    static std::mutex attr_mu;
+    static bool attr_set[kAttrDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kAttrDevices) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> g(attr_mu);
+        if (!attr_set[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            if (e != cudaSuccess) return e;
+            attr_set[dev] = true;
+        }
     }
     const int nkb = K / TC_BK, ktot = two_pass ? 2 * nkb : nkb;
     int kb_split = 0;

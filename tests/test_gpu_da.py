@@ -49,6 +49,85 @@ def test_training_gradients_match_oracle_network():
         assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b), (k, np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def test_adam_kernel_matches_oracle_adam():
+    """The training's Adam kernel (diam_da_adam_step: FP32 masters and moments) against the oracle's adam_step
+    (FP64) over five steps with seeded gradients (rounded to FP32, as uploaded) and non-default lr, beta1, beta2
+    and eps: the weights' changes agree to FP32 accuracy, so a swapped beta, an off-by-one bias-correction
+    exponent or a misplaced eps would show."""
+    import paper_1506_05741_b300 as dm
+    d, h1, h2 = 192, 128, 128
+    ts = workloads.tanh_regression(d, 64, 23)
+    s = dm.Sampler(dm.default_config(d, 8, prec=dm.BF16, n_lag=8, seed=1), ts)
+    w = workloads.mlp_init(d, h1, h2, seed=7)
+    lr, b1, b2, eps = 3e-3, 0.8, 0.95, 1e-4
+    s.da_enable(dm.da_default_config(h1=h1, h2=h2, batch=128, ring=1000, lr=lr, beta1=b1, beta2=b2, adam_eps=eps), w)
+    f32 = lambda a: np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
+    params = {k: f32(v) for k, v in w.items()}
+    w0 = {k: v.copy() for k, v in params.items()}
+    m = {k: np.zeros_like(v) for k, v in params.items()}
+    v = {k: np.zeros_like(v) for k, v in params.items()}
+    rng = np.random.default_rng(8)
+    for t in range(1, 6):
+        grads = {k: f32(rng.standard_normal(np.shape(params[k])) * 10.0 ** rng.uniform(-3, 0)) for k in params}
+        s.da_adam_step(grads)
+        mlp.adam_step(params, grads, m, v, t, lr=lr, beta1=b1, beta2=b2, eps=eps)
+    got = s.da_weights()
+    for k in params:
+        dg = np.ravel(got[k]) - np.ravel(w0[k])
+        do = np.ravel(params[k]) - np.ravel(w0[k])
+        # |dW| ~ 5 lr; FP32 rounding of the weights themselves (|W| <= ~1) and of the update's terms
+        assert np.max(np.abs(dg - do)) <= 1e-5 * lr * 5 + 2e-7 * np.max(np.abs(np.ravel(w0[k])) + 1.0), k
+        assert np.max(np.abs(do)) > 0.3 * lr    # the steps did move the weights
+    s.close()
+
+
+def test_two_stage_decisions_match_oracle():
+    """The screen (stage 1) and the exact test (stage 2) of delayed acceptance against the FP64 reference of the
+    two-stage rule (oracle/da.py), with stage 1 on from the start (screen_from_start, the given network, no
+    training) and a fixed factor and beta: tanh regression d = 192, d_y = 64, eight chains, 64 steps. Every stage-1
+    pass and every final decision agree (a decision whose log u lies within 5e-3 of its log a on the oracle's side
+    ends that chain's comparison: the network's BF16 roundings may differ there); the stage-2 log ratios agree to
+    2e-3 of max(1, |log a2|) (the same BF16 roundings, and FP32 sums of the network and of the map terms)."""
+    import paper_1506_05741_b300 as dm
+    from oracle import da
+    d, dy, P, steps = 192, 64, 8, 64
+    ts = workloads.tanh_regression(d, dy, 24)
+    x0 = workloads.start_state(d, P, 3) * np.sqrt(ts.lam)
+    C0 = np.diag(ts.lam)
+    cfg = dm.default_config(d, P, prec=dm.BF16, n_lag=16, seed=13, beta0=0.3, adapt_beta=0, min_samples_refresh=10 ** 12)
+    cfg["trace_steps"] = steps
+    s = dm.Sampler(cfg, ts, x0=x0, C0=C0)
+    w = workloads.mlp_init(d, 128, 128, seed=7)
+    s.da_enable(dm.da_default_config(h1=128, h2=128, batch=128, ring=4096, first_train_min=10 ** 9,
+                                     retrain_every=10 ** 6, screen_from_start=1), w)
+    s.run(steps)
+    tg = s.trace(steps)
+    st = s.da_stats()
+    s.close()
+    target = oracle.Target(ts.kind, d, dy, lam=ts.lam, A=oracle.round_bf16(ts.A), y=ts.y, sigma=ts.sigma)
+    od = lambda v: -0.5 * float(np.sum(v * v / ts.lam))
+    Lq = oracle.round_bf16(oracle.cholesky(C0))
+    ref = da.run(target.logpi, od, da.Screen(w), x0, Lq, np.zeros(d), 0.3, 1.0, 13, 0, steps)
+    pass_g = np.isfinite(tg["loga"])
+    # s enters both ratios: the network's hidden activations are rounded to BF16 from FP32 pre-activations on the
+    # GPU and from FP64 ones here, so an activation that lies at a rounding boundary can round the other way,
+    # moving s by about |w3_o| 2^-8 |H_o| (~2e-4) per such activation; a margin of 5e-3 covers a few of them
+    tie = 5e-3
+    compared = 0
+    for p in range(P):
+        for t in range(steps):
+            if ref["m1"][t, p] < tie or ref["m2"][t, p] < tie:
+                break                                # a near tie: the chains may part here
+            assert pass_g[t, p] == ref["pass1"][t, p], (t, p)
+            assert tg["acc"][t, p] == ref["acc"][t, p], (t, p)
+            if ref["pass1"][t, p]:
+                assert abs(tg["loga"][t, p] - ref["loga2"][t, p]) <= 2e-3 * max(1.0, abs(ref["loga2"][t, p])), (t, p)
+            compared += 1
+    assert compared >= 0.9 * P * steps
+    assert 0.05 < ref["pass1"].mean() < 1.0 and ref["acc"].sum() > 0    # both stages decide something
+    assert st["stage1_tested"] == P * steps and st["stage1_passed"] == int(pass_g.sum())
+
+
 def test_delayed_acceptance_trains_and_screens():
     import paper_1506_05741_b300 as dm
     ts = workloads.tanh_regression(256, 128, 22)

@@ -81,11 +81,12 @@ def _callback_pair(G, P, steps, **kw):
     cfg = dm.default_config(d, P, n_lag=16, beta0=0.35, seed=44, min_samples_refresh=30, eps_jitter=1e-3)
     cfg["trace_steps"] = steps
     x0 = workloads.start_state(d, P, 4) * 0.05      # inside the poisoned callback's finite region
+    C0 = np.linalg.inv(G.T @ G)                     # the target's covariance: a factor the chains move with
     cb = _CallbackTarget(G, **kw)
-    g = dm.Sampler(cfg, cb, x0=x0)
+    g = dm.Sampler(cfg, cb, x0=x0, C0=C0)
     ocfg = oracle.default_config(**{k: cfg[k] for k in CFG_KEYS})
     ocfg.update(trace_steps=steps, threads=2)
-    o = oracle.Sampler(ocfg, oracle.Target(oracle.T_DENSE, d, G.shape[0], G=G), x0=x0)
+    o = oracle.Sampler(ocfg, oracle.Target(oracle.T_DENSE, d, G.shape[0], G=G), x0=x0, C0=C0)
     return g, o, cb
 
 
@@ -132,4 +133,28 @@ def test_callback_failure_stops_the_run(prec):
     with pytest.raises(dm.DiamError) as e2:
         s.run(1)
     assert e2.value.status == 7                      # DIAM_ESTATE: the context refuses further work
+    s.close()
+
+
+def test_bounded_device_wait_reports_timeout_and_leaves_the_device_usable():
+    """The bounded wait (diam_op_wait_flag) on a flag that nothing sets gives up after its short runtime limit
+    with DIAM_ETIMEOUT instead of hanging; nothing is left in flight (the device synchronises), the same wait
+    succeeds once the flag is set, and a sampler still runs afterwards."""
+    import torch
+    import paper_1506_05741_b300 as dm
+    l = dm.lib()
+    f = l.diam_op_wait_flag
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert f(flag.data_ptr(), 1, 2_000_000, None) == 5            # DIAM_ETIMEOUT after ~1 ms of clock
+    torch.cuda.synchronize()                                       # nothing left running
+    flag.fill_(1)
+    torch.cuda.synchronize()
+    assert f(flag.data_ptr(), 1, 2_000_000, None) == 0
+    assert f(flag.data_ptr(), 1, -1, None) == 1                   # DIAM_EINVAL: a negative limit
+    ts = workloads.dense_gaussian(32, 3)
+    s = dm.Sampler(dm.default_config(32, 4, n_lag=8, seed=5), ts, C0=ts.cov)
+    s.run(24)
+    assert s.stats()["steps"] == 24
     s.close()

@@ -418,3 +418,70 @@ def test_fixed_factor_chain_on_twisted_target_matches_closed_form_moments(j):
     q = scipy.stats.chi2.ppf(0.999, d)
     assert np.sum(((zm[:, 0] - ts.umean) / zm[:, 1]) ** 2) < q
     assert np.sum(((zv[:, 0] - ts.uvar) / zv[:, 1]) ** 2) < q
+
+
+# ------------------------------------------------------------------ reading R2: per-chain factors (Sec. 2.4.1)
+def test_per_chain_factors_with_one_chain_are_algorithm_1():
+    """Reading R2 with P = 1: the local view of the global moments (eq. (mom2pg), (mom1pg)) is the running
+    moment of the single chain, so R2 is Algorithm 1 itself: the same decisions, moments and factor as R1."""
+    ts = workloads.dense_gaussian(24, 8)
+    out = []
+    for mode in (0, 1):
+        cfg = oracle.default_config(d=24, P=1, n_lag=20, M=3, beta0=0.4, seed=5, min_samples_refresh=30,
+                                    eps_jitter=1e-3, trace_steps=401, moments_mode=mode)
+        s = oracle.Sampler(cfg, _spec_target(ts), C0=ts.cov)
+        s.run(401)   # one step into interval 20: R1 has applied interval 19's factor (R2 holds it from the end)
+        L = s.factor()[0] if mode == 0 else s.chain_factor(0)[0]
+        out.append((s.trace(), s.moments(), L, s.counts()))
+    (ta, (ma, Ca), La, ca), (tb, (mb, Cb), Lb, cb) = out
+    assert np.array_equal(ta["acc"], tb["acc"]) and ca["refreshes"] == cb["refreshes"] > 10
+    assert np.allclose(ma, mb, rtol=0, atol=1e-13) and np.allclose(Ca, Cb, rtol=0, atol=1e-13)
+    assert np.allclose(La, Lb, rtol=0, atol=1e-11)
+
+
+def test_per_chain_factor_is_cholesky_of_its_view_of_the_global_moments():
+    """Reading R2 with P = 4, M = 2 intervals per batch: after 5 intervals (two batches merged, one interval into
+    the third) chain p's factor is the jittered Cholesky (LAPACK) of C^{p,glob} = S^{p,glob} - m m^T built by brute
+    force from the recorded states: all chains' samples of the merged batches plus chain p's own samples since
+    (eq. (mom2pg), (mom1pg), (cov2pg)); the chains' factors differ."""
+    d, P, nl, M = 12, 4, 10, 2
+    ts = workloads.dense_gaussian(d, 9)
+    eps = 1e-3
+    cfg = oracle.default_config(d=d, P=P, n_lag=nl, M=M, beta0=0.5, seed=6, min_samples_refresh=10, eps_jitter=eps,
+                                moments_mode=1)
+    s = oracle.Sampler(cfg, _spec_target(ts), C0=ts.cov)
+    s.run(5 * nl, record=True)
+    X = s.trajectory()                               # (steps, P, d), post-step states
+    glob = X[: 4 * nl].reshape(-1, d)                # the two merged batches, every chain
+    Ls = []
+    for p in range(P):
+        V = np.concatenate([glob, X[4 * nl:, p, :]])
+        m = V.mean(axis=0)
+        Cm = V.T @ V / V.shape[0] - np.outer(m, m)
+        want = np.linalg.cholesky(Cm + eps * np.diag(np.diag(Cm)))
+        L, _, xr, _ = s.chain_factor(p)
+        assert np.allclose(L, want, rtol=1e-10, atol=1e-12), p
+        assert np.allclose(xr, m, rtol=1e-12, atol=1e-14)
+        Ls.append(L)
+    assert not np.allclose(Ls[0], Ls[1])
+
+
+def test_pooled_factor_converges_at_least_as_fast_as_per_chain_factors():
+    """Reading R1 (one factor from the moments of every chain, refreshed every interval) against the paper's
+    per-chain factors (R2, eq. (mom2pg) - (cov2pg), the chains' samples merged every M intervals), same chains and
+    streams: dense Gaussian d = 32, P = 8, n_lag = 16, M = 10, A_0 = Id, over-dispersed starts, 8000 steps. Both
+    converge, and the pooled covariance of R1 is at least as close to Sigma (relative Frobenius norm): under R1
+    every chain's proposal sees every chain's latest samples; under R2 only its own until the next merge."""
+    d, P, nl, M = 32, 8, 16, 10
+    ts = workloads.dense_gaussian(d, 44)
+    x0 = workloads.start_state(d, P, 2) * 2.0
+    err = []
+    for mode in (0, 1):
+        cfg = oracle.default_config(d=d, P=P, n_lag=nl, M=M, seed=9, min_samples_refresh=4 * d, burnin=10 * nl,
+                                    moments_mode=mode, threads=4)
+        s = oracle.Sampler(cfg, _spec_target(ts), x0=x0)
+        s.run(8000)
+        _, Cm = s.moments()
+        err.append(np.linalg.norm(Cm - ts.cov) / np.linalg.norm(ts.cov))
+    assert err[0] < 0.2 and err[1] < 0.25
+    assert err[0] <= err[1]

@@ -62,14 +62,15 @@ def diag_gaussian(d: int, power: float = 2.0) -> TargetSpec:
     return TargetSpec(TARGET_DIAG, d, lam=lam, cov=np.diag(lam), mean=np.zeros(d))
 
 
-def dense_gaussian(d: int, seed: int) -> TargetSpec:
-    """Sigma = Q diag(i^-1) Q^T with Q from QR of a seeded N(0,1) d x d FP64 matrix."""
+def dense_gaussian(d: int, seed: int, with_cov: bool = True) -> TargetSpec:
+    """Sigma = Q diag(i^-1) Q^T with Q from QR of a seeded N(0,1) d x d FP64 matrix (with_cov = False leaves
+    Sigma itself out: the sampler needs only G)."""
     rng = np.random.default_rng(seed)
     Z = rng.standard_normal((d, d))
     Q, _ = np.linalg.qr(Z)
     i = np.arange(1, d + 1, dtype=np.float64)
     G = np.sqrt(i)[:, None] * Q.T
-    cov = (Q * (1.0 / i)) @ Q.T
+    cov = (Q * (1.0 / i)) @ Q.T if with_cov else None
     return TargetSpec(TARGET_DENSE, d, d_y=d, G=np.ascontiguousarray(G), cov=cov, mean=np.zeros(d))
 
 
@@ -152,13 +153,13 @@ def tanh4096(d: int = 4096, d_y: int = 2048, P: int = 256, n_lag: int = 128) -> 
                    beta0=min(2.4 / math.sqrt(d), 0.5), n_steps=20 * 10 * n_lag, seed=3)
 
 
-def multi64(n_problems: int = 64, d_lo: int = 256, d_hi: int = 8192):
+def multi64(n_problems: int = 64, d_lo: int = 256, d_hi: int = 8192, with_cov: bool = True):
     """Problem sizes d_j = round(exp(U(ln d_lo, ln d_hi))) from seed 7; even j dense, odd j banana."""
     rng = np.random.default_rng(7)
     ds = np.rint(np.exp(rng.uniform(math.log(d_lo), math.log(d_hi), n_problems))).astype(int)
     specs = []
     for j, d in enumerate(ds):
-        t = dense_gaussian(int(d), 7000 + j) if j % 2 == 0 else banana(int(d))
+        t = dense_gaussian(int(d), 7000 + j, with_cov=with_cov) if j % 2 == 0 else banana(int(d))
         specs.append(RunSpec(f"multi{j}", t, P=32, n_lag=64, M=10, beta0=min(2.4 / math.sqrt(d), 0.5), seed=7 + j))
     return specs
 
