@@ -69,31 +69,39 @@ def parse():
     ap.add_argument("--convergence", action="store_true",
                     help="instead of the throughput bench: samples and device time to convergence on a dense Gaussian "
                          "of known covariance, over n_lag (Sec. 3.3)")
-    ap.add_argument("--conv-d", type=int, default=128)
-    ap.add_argument("--conv-P", type=int, default=256)
-    ap.add_argument("--conv-tol-mean", type=float, default=0.02, help="|m_n - mu|_2 (the n_lag tuning criterion)")
-    ap.add_argument("--conv-tol-cov", type=float, default=0.05, help="|C_n - Sigma|_F / |Sigma|_F")
-    ap.add_argument("--conv-max-steps", type=int, default=100000)
+    ap.add_argument("--conv-ds", default="100,200,400,800", help="dimensions of the n_lag experiment")
+    ap.add_argument("--conv-target", default="pi1", choices=["pi1", "dense"])
+    ap.add_argument("--conv-P", type=int, default=16)
+    ap.add_argument("--conv-tol-mean", type=float, default=0.01, help="|m_n - mu|_2 (the n_lag tuning criterion)")
+    ap.add_argument("--conv-tol-cov", type=float, default=1e-3, help="|C_n - Sigma|_F / |Sigma|_F")
+    ap.add_argument("--conv-max-s", type=float, default=20.0, help="device seconds per (d, n_lag) row at most")
     ap.add_argument("--compare", action="store_true",
                     help="instead of the throughput bench: integrated autocorrelation times of DIAM, AM, pCN and RW on "
                          "the Gaussian test targets of Sec. 3.1 over d (Sec. 3.2)")
     ap.add_argument("--cmp-d", default="32,64,128,256")
     ap.add_argument("--cmp-targets", default="1,2,4")
-    ap.add_argument("--cmp-intervals", type=int, default=2000, help="measured intervals (n_lag = d / 2 steps each)")
-    ap.add_argument("--cmp-warmup", type=int, default=300, help="adaptation intervals before the window")
+    ap.add_argument("--cmp-intervals", type=int, default=3000, help="measured intervals (n_lag = d / 2 steps each)")
+    ap.add_argument("--cmp-warmup", type=int, default=3000, help="adaptation intervals before the window")
+    ap.add_argument("--cmp-prec", default="bf16", choices=["bf16", "fp64"])
     ap.add_argument("--multi", action="store_true",
                     help="instead of the throughput bench: the uneven batch of 64 problems (d log-uniform in [256, 8192], "
                          "dense Gaussians and bananas, P = 32, n_lag = 64, BF16) at its full size")
     ap.add_argument("--multi-n", type=int, default=64)
+    ap.add_argument("--multi-warmup", type=int, default=48,
+                    help="warm-up intervals of --multi: from x_0 = 0 and A_0 = Id the step size must first adapt down "
+                         "(about 30 intervals) before moves are accepted and the refreshes start")
+    ap.add_argument("--multi-steps", type=int, default=16, help="timed intervals of --multi")
     return ap.parse_args()
 
 
 def multi(args):
     """The uneven batch: 64 independent problems, d_j = round(exp(U(ln 256, ln 8192))) (seed 7), even j the dense
     Gaussian Sigma = Q diag(1/i) Q^T (Q from QR of a seeded N(0,1) matrix, seed 7000 + j), odd j the banana with
-    lambda_i = 1/i; each P = 32 chains, n_lag = 64, BF16 mode, refresh every interval, run together through
-    diam_multi_run. W warm-up intervals, then K timed (wall clock with the device synchronised on both sides, the
-    problems' streams run concurrently); aggregate chain-steps/s = sum_j P n_lag K / time. One JSON line."""
+    lambda_i = 1/i; each P = 32 chains, n_lag = 64, BF16 mode, x_0 = 0, A_0 = Id, refresh every interval (once
+    d + 1 moves are accepted), run together through diam_multi_run. --multi-warmup intervals (the step size adapts
+    down first), then --multi-steps timed (wall clock with the device synchronised on both sides, the problems'
+    streams run concurrently); aggregate chain-steps/s = sum_j P n_lag K / time; per problem the acceptance rate
+    and refreshes of the timed window. One JSON line."""
     import torch
     import paper_1506_05741_b300 as dm
     import workloads
@@ -106,23 +114,26 @@ def multi(args):
     m = dm.MultiSampler(cfgs, [r.target for r in specs])
     init_s = time.time() - t1
     nl = specs[0].n_lag
-    m.run(args.warmup * nl)
+    m.run(args.multi_warmup * nl)
     torch.cuda.synchronize()
+    st0 = [v.stats() for v in m.views]
     t2 = time.time()
-    m.run(args.steps * nl)
+    m.run(args.multi_steps * nl)
     torch.cuda.synchronize()
     dt = time.time() - t2
-    steps = sum(r.P for r in specs) * nl * args.steps
+    steps = sum(r.P for r in specs) * nl * args.multi_steps
     per = []
-    for j, r in enumerate(specs):
+    for j, r in enumerate(specs):   # over the timed window
         st = m.views[j].stats()
+        acc = st["accepted"] - st0[j]["accepted"]
         per.append({"j": j, "d": r.target.d, "kind": "dense" if j % 2 == 0 else "banana",
-                    "accept_rate": round(st["accepted"] / max(1, st["steps"] * r.P), 3), "refreshes": st["refreshes"]})
+                    "accept_rate": round(acc / max(1, (st["steps"] - st0[j]["steps"]) * r.P), 3),
+                    "refreshes": st["refreshes"] - st0[j]["refreshes"], "beta": round(st["beta"], 4)})
     m.close()
     ds = [r.target.d for r in specs]
     print(json.dumps({"metric": "aggregate chain-steps/s, uneven batch of problems", "value": round(steps / dt, 1),
-                      "unit": "chain-steps/s", "timed_intervals": args.steps, "warmup_intervals": args.warmup,
-                      "seconds": round(dt, 3), "ms_per_interval": round(dt / args.steps * 1e3, 2),
+                      "unit": "chain-steps/s", "timed_intervals": args.multi_steps, "warmup_intervals": args.multi_warmup,
+                      "seconds": round(dt, 3), "ms_per_interval": round(dt / args.multi_steps * 1e3, 2),
                       "config": {"workload": f"multi{len(specs)}: d log-uniform in [256, 8192] (seed 7), even j dense "
                                              f"Gaussian, odd j banana, P=32, n_lag=64, BF16, refresh every interval",
                                  "problems": len(specs), "d_min": int(min(ds)), "d_max": int(max(ds)),
@@ -159,8 +170,8 @@ def iact_batch_means(bsum, n_lag, f_var, bmax):
 
 def compare(args):
     """Sec. 3.2 on the GPU: integrated autocorrelation times of log pi, v_d^T x (the direction of the largest
-    variance) and v_1^T x (the smallest) for DIAM, AM, pCN and RW on pi_1, pi_2, pi_4 of Sec. 3.1, over d. FP64
-    mode, P = 32 chains started from exact draws of the target, n_lag = d / 2 (the paper's choice), beta_0 =
+    variance) and v_1^T x (the smallest) for DIAM, AM, pCN and RW on pi_1, pi_2, pi_4 of Sec. 3.1, over d. BF16
+    mode (or FP64 with --cmp-prec fp64), P = 32 chains started from exact draws of the target, n_lag = d / 2 (the paper's choice), beta_0 =
     2.4 / sqrt(d) adapted to each sampler's acceptance window; the adaptive samplers keep their first 20
     intervals out of the moments (n_0 of Algorithm 1's footnote) and refresh after 5 d accepted moves. The IACT is
     read off batch means of per-interval chain sums (batches of b intervals, b doubling; var(f) exact: d/2 for log pi
@@ -182,7 +193,7 @@ def compare(args):
             x0 = workloads.start_state(d, P, 11) @ np.linalg.cholesky(ts.cov).T
             for name, sp in SAMPLERS.items():
                 cfg = dm.default_config(d, P, n_lag=nl, seed=100 + d + j, proposal=sp["proposal"], acc_lo=sp["acc"][0],
-                                        acc_hi=sp["acc"][1])
+                                        acc_hi=sp["acc"][1], prec=dm.BF16 if args.cmp_prec == "bf16" else dm.FP64)
                 if sp["adapt"]:
                     cfg.update(burnin=20 * nl, min_samples_refresh=5 * d)
                 else:
@@ -211,62 +222,72 @@ def compare(args):
                 print(json.dumps({k: row[k] for k in ("d", "target", "sampler", "accept_rate", "beta")} |
                                  {f: res[f]["tau"] for f in res}), file=sys.stderr, flush=True)
     print(json.dumps({"metric": "integrated autocorrelation time (steps) of DIAM, AM, pCN, RW (Sec. 3.2)",
-                      "config": {"P": P, "n_lag": "d/2", "prec": "FP64", "warmup_intervals": args.cmp_warmup,
+                      "config": {"P": P, "n_lag": "d/2", "prec": args.cmp_prec.upper(), "warmup_intervals": args.cmp_warmup,
                                  "intervals": args.cmp_intervals, "start": "exact draws of the target"},
                       "rows": rows}), flush=True)
 
 
 def convergence(args):
-    """Sec. 3.3's experiment on the GPU sampler: dense Gaussian N(0, Sigma), Sigma = Q diag(1/i) Q^T, chains
-    started over-dispersed; for n_lag in {d/100, d/10, d/4, d/2, d, 2d, 4d}, the chain-steps (P x steps) and the
-    device time until the pooled mean is within tol_mean of the truth (Euclidean norm: the paper's criterion for
-    tuning n_lag) and until the pooled covariance is within tol_cov of Sigma (relative Frobenius norm: the paper's
-    stopping criterion, there with TOL = 1e-3). BF16 mode, refresh in order (refresh_delay 0). One JSON line."""
+    """Sec. 3.3's n_lag experiment on the GPU sampler. Target pi_1 = N(0, (A A^T + I)^-1) of Sec. 3.1 (or, with
+    --conv-target dense, N(0, Q diag(1/i) Q^T)) for each d in --conv-ds; chains started from N(0, I) (Algorithm 1's
+    x_0); for n_lag in {d/100, d/10, d/4, d/2, d, 2d, 4d, 10d}, the chain-steps (P x steps) and device time until
+    the pooled mean is within tol_mean of the truth in the Euclidean norm (the paper's criterion for tuning n_lag,
+    TOL = 0.01) and until the pooled covariance is within tol_cov of Sigma in the relative Frobenius norm (its
+    stopping criterion elsewhere, TOL = 1e-3), each row capped at --conv-max-s device seconds. The samples to the
+    mean criterion are also given relative to n_lag = d, the normalisation of the paper's figure. BF16 mode,
+    refresh in order (refresh_delay 0). One JSON line."""
     import torch
     import paper_1506_05741_b300 as dm
     import workloads
-    d, P = args.conv_d, args.conv_P
-    ts = workloads.dense_gaussian(d, 1000 + d)
-    nS = float(np.linalg.norm(ts.cov))
-    x0 = workloads.start_state(d, P, 3) @ np.linalg.cholesky(ts.cov).T * 3.0
+    P = args.conv_P
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    rows = []
-    for frac in (0.01, 0.1, 0.25, 0.5, 1.0, 2.0, 4.0):
-        nl = max(1, int(round(frac * d)))
-        cfg = dm.default_config(d, P, n_lag=nl, seed=17, prec=dm.BF16, refresh_delay=0)
-        s = dm.Sampler(cfg, ts, x0=x0, stream=stream.cuda_stream)
-        chunk = max(nl, (2048 // nl) * nl)   # whole intervals, about 2048 steps a check
-        steps, dev_s = 0, 0.0
-        hit = {"mean": None, "cov": None}
-        while steps < args.conv_max_steps and (hit["mean"] is None or hit["cov"] is None):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            s.run(chunk)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            dev_s += e0.elapsed_time(e1) / 1e3
-            steps += chunk
-            m, C, n = s.moments()
-            em = float(np.linalg.norm(m - ts.mean))
-            ec = float(np.linalg.norm(C - ts.cov)) / nS
-            for key, err, tol in (("mean", em, args.conv_tol_mean), ("cov", ec, args.conv_tol_cov)):
-                if hit[key] is None and err <= tol:
-                    hit[key] = {"chain_steps": steps * P, "device_s": round(dev_s, 4), "error": round(err, 5)}
-        st = s.stats()
-        s.close()
-        rows.append({"n_lag": nl, "n_lag_over_d": frac, "to_mean_tol": hit["mean"], "to_cov_tol": hit["cov"],
-                     "steps_run": steps, "final_mean_error": round(em, 5), "final_cov_error": round(ec, 5),
-                     "device_s": round(dev_s, 3), "accept_rate": round(st["accepted"] / max(1, st["steps"] * P), 4),
-                     "beta": round(st["beta"], 4), "refreshes": st["refreshes"]})
-        print(json.dumps({"n_lag": nl, "done": rows[-1]}), file=sys.stderr, flush=True)
-    print(json.dumps({"metric": "chain-steps and device seconds to convergence (Sec. 3.3), dense Gaussian",
-                      "config": {"workload": f"dense Gaussian d={d}, Sigma = Q diag(1/i) Q^T, P={P}, BF16 mode, "
-                                             f"refresh in order, starts 3x over-dispersed",
+    out = []
+    for d in [int(v) for v in args.conv_ds.split(",")]:
+        ts = workloads.paper_targets(d)[1] if args.conv_target == "pi1" else workloads.dense_gaussian(d, 1000 + d)
+        nS = float(np.linalg.norm(ts.cov))
+        x0 = workloads.start_state(d, P, 3)
+        rows = []
+        for frac in (0.01, 0.1, 0.25, 0.5, 1.0, 2.0, 4.0, 10.0):
+            nl = max(1, int(round(frac * d)))
+            cfg = dm.default_config(d, P, n_lag=nl, seed=17, prec=dm.BF16, refresh_delay=0)
+            s = dm.Sampler(cfg, ts, x0=x0, stream=stream.cuda_stream)
+            chunk = max(nl, (2048 // nl) * nl)   # whole intervals, about 2048 steps a check
+            steps, dev_s = 0, 0.0
+            hit = {"mean": None, "cov": None}
+            while dev_s < args.conv_max_s and (hit["mean"] is None or hit["cov"] is None):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.run(chunk)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                dev_s += e0.elapsed_time(e1) / 1e3
+                steps += chunk
+                m, C, n = s.moments()
+                em = float(np.linalg.norm(m - ts.mean))
+                ec = float(np.linalg.norm(C - ts.cov)) / nS
+                for key, err, tol in (("mean", em, args.conv_tol_mean), ("cov", ec, args.conv_tol_cov)):
+                    if hit[key] is None and err <= tol:
+                        hit[key] = {"chain_steps": steps * P, "device_s": round(dev_s, 4), "error": round(err, 5)}
+            st = s.stats()
+            s.close()
+            rows.append({"n_lag": nl, "n_lag_over_d": frac, "to_mean_tol": hit["mean"], "to_cov_tol": hit["cov"],
+                         "steps_run": steps, "final_mean_error": round(em, 5), "final_cov_error": round(ec, 5),
+                         "device_s": round(dev_s, 3), "accept_rate": round(st["accepted"] / max(1, st["steps"] * P), 4),
+                         "beta": round(st["beta"], 4), "refreshes": st["refreshes"]})
+            print(json.dumps({"d": d, "n_lag": nl, "done": rows[-1]}), file=sys.stderr, flush=True)
+        base = next((r["to_mean_tol"] for r in rows if r["n_lag_over_d"] == 1.0), None)
+        for r in rows:
+            r["samples_to_mean_tol_over_n_lag_d"] = (round(r["to_mean_tol"]["chain_steps"] / base["chain_steps"], 3)
+                                                     if r["to_mean_tol"] and base else None)
+        out.append({"d": d, "rows": rows})
+    print(json.dumps({"metric": "chain-steps and device seconds to convergence (Sec. 3.3, impact of n_lag)",
+                      "config": {"workload": f"{'pi_1 of Sec. 3.1' if args.conv_target == 'pi1' else 'dense Gaussian'}"
+                                             f", P={P}, BF16 mode, refresh in order, x_0 ~ N(0, I)",
                                  "tol_mean": args.conv_tol_mean, "tol_cov_rel_frobenius": args.conv_tol_cov,
-                                 "max_steps": args.conv_max_steps},
-                      "rows": rows}), flush=True)
+                                 "max_device_s_per_row": args.conv_max_s},
+                      "by_d": out}), flush=True)
 
 
 def peaks():
@@ -398,7 +419,7 @@ def ess_sweep(xs, n_lag, mom0, mom1):
     than 20% (plateau)."""
     K = xs.shape[0]
     table, b, last = {}, 1, None
-    while K // b >= 4:
+    while b == 1 or K // b >= 4:   # b = 1 always (a short window has no longer batches)
         ess, N = ess_window(xs, n_lag, mom0, mom1, b)
         table[b] = (float(ess.min()), int(np.argmin(ess)), float(np.median(ess)))
         last = b
@@ -478,7 +499,10 @@ def roofline(prof, run, ts, pk, pk_src, ring):
         # lower-triangular A_n W (2 d^2 N / 2) and the map of the noise, (A A_n) W (2 d_y d N; its lo pass, a
         # precision overhead, is not counted)
         "xi_gemm": ("tensor", float(d) * d * N + 2.0 * dy * d * N, "TFLOP/s", sus),
-        "fold": ("tensor", float(d) * d * N, "TFLOP/s", sus),                # SYRK of the interval, lower half
+        # the fold apart from its SYRK: one pass over the interval's FP32 records (read) writing their BF16
+        # transpose and tile sums (the per-chain interval sums of x ride along)
+        "fold": ("hbm", N * d * (4 + 2), "GB/s", pk["hbm_gbs"]),
+        "syrk": ("tensor", float(d) * (d + 1) * N, "TFLOP/s", sus),         # the fold's SYRK, lower half
         "target": ("tensor", 2.0 * dy * d * P * 2, "TFLOP/s", sus),          # A x* with the hi + lo split
         # bytes: propose reads x, z, xi (FP32), writes x*, z* (FP32) and the BF16 hi / lo split of x*
         "propose": ("hbm", P * d * (4 + 4 + 4 + 4 + 4 + 2 + 2), "GB/s", pk["hbm_gbs"]),
@@ -491,7 +515,7 @@ def roofline(prof, run, ts, pk, pk_src, ring):
         "screen": ("tensor", 2.0 * P * (d * 512 + 512 * 512), "TFLOP/s", sus),
         "step": ("hbm", step_bytes, "GB/s", pk["hbm_gbs"]),
     }
-    total = sum(ms for _, ms in prof.values())
+    total = sum(ms for k, (_, ms) in prof.items() if k != "syrk") + prof.get("syrk", (0, 0.0))[1]
     table = {}
     for k, (cnt, ms) in prof.items():
         if cnt == 0 or k not in work:
@@ -501,24 +525,55 @@ def roofline(prof, run, ts, pk, pk_src, ring):
         ach = units / per / (1e12 if unit == "TFLOP/s" else 1e9)
         table[k] = {"share": round(ms / total, 4), "launch_ms": round(per * 1e3, 4), "bound": bound,
                     "achieved": round(ach, 3), "unit": unit, "peak": peak, "frac": round(ach / peak, 4)}
-    dom = max(table, key=lambda k: table[k]["share"])
-    t = table[dom]
-    out = {"kernel": dom, "bound": t["bound"], "achieved": t["achieved"], "peak": t["peak"], "unit": t["unit"],
-           "frac": t["frac"], "traffic": None, "launch_ms": t["launch_ms"],
-           "peak_source": ("nominal FP64 of the profiling recipe" if t["bound"] == "alu" else pk_src + " (sustained)"
-                           if t["bound"] == "tensor" else pk_src),
-           "phases": table}
+    # The dominant kernel of the launch list (profiles/launches_tanh4096_bf16.md): tc_gemm_kernel<256>, three
+    # launches per interval -- the noise product (lower-triangular A_n W: d^2 N flops), its map ((A A_n) W:
+    # 2 d_y d N; the lo pass of the two-term operand is a precision overhead, not counted) and the fold's SYRK
+    # (lower half, d (d + 1) N). Achieved = their algorithmic flops over their CUDA-event time (phases xi_gemm
+    # and syrk), per launch as the average of the three. The refresh is the largest phase but is ~250 launches of
+    # three kernels (chol_diag_kernel, trsv_rows_kernel, ozaki_update_kernel), each a smaller share.
+    (cx, mx), (cs, ms_) = prof.get("xi_gemm", (0, 0.0)), prof.get("syrk", (0, 0.0))
+    if cx and cs:
+        per_int = float(d) * d * N + 2.0 * dy * d * N + float(d) * (d + 1) * N
+        t_int = (mx / cx + ms_ / cs) / 1e3          # seconds per interval of the three launches
+        ach = per_int / t_int / 1e12
+        out = {"kernel": "tc_gemm_kernel<256> (noise product, its map, fold SYRK: 3 launches per interval)",
+               "bound": "tensor", "achieved": round(ach, 3), "peak": sus, "unit": "TFLOP/s",
+               "frac": round(ach / sus, 4), "traffic": gemm_traffic(run, ts), "launch_ms": round(t_int * 1e3 / 3, 4),
+               "flops_per_launch": round(per_int / 3), "peak_source": pk_src + " (sustained)", "phases": table}
+    else:
+        dom = max(table, key=lambda k: table[k]["share"])
+        t = table[dom]
+        out = {"kernel": dom, "bound": t["bound"], "achieved": t["achieved"], "peak": t["peak"], "unit": t["unit"],
+               "frac": t["frac"], "traffic": None, "launch_ms": t["launch_ms"],
+               "peak_source": pk_src + (" (sustained)" if t["bound"] == "tensor" else ""), "phases": table}
     if "refresh" in table:   # the slices' overhead, and the same work against the FP64 pipe's nominal rate
         r = table["refresh"]
         r["bf16_issued_tflops"] = round(r["achieved"] * OZ_PRODUCTS, 3)
         r["bf16_issued_note"] = "28 BF16 slice products per FP64 product of the rank-64 updates (Ozaki split)"
         r["fp64_nominal_tflops"] = FP64_PEAK_TFLOPS
         r["frac_of_fp64_nominal"] = round(r["achieved"] / FP64_PEAK_TFLOPS, 3)
-    if dom == "refresh":
-        out["note"] = ("the FP64 Cholesky's d^3/3 flops over its device time, against the sustained BF16 peak of the "
-                       "pipe it runs on; a latency-bound chain of 64 diagonal blocks, beside the next intervals "
-                       "(refresh_delay 2) in the timed arms")
+    if "refresh" in table:
+        out["refresh_note"] = ("the refresh phase: the FP64 Cholesky's d^3/3 flops over its device time, against the "
+                               "sustained BF16 peak of the pipe it runs on; a latency-bound chain of 64 diagonal blocks, "
+                               "beside the next intervals (refresh_delay 2) in the timed arms")
     return out
+
+
+# DRAM traffic of one tc_gemm_kernel<256> launch of the noise product at the benchmark's shape (M = K = 4096,
+# N = 65536), from ncu (dram__bytes_read.sum + dram__bytes_write.sum; profiles/tc_gemm_noise_product_4096.md), with
+# a digest of the kernel's sources when it was taken: reported only while the sources are unchanged.
+GEMM_TRAFFIC = {"bytes": None, "sources_sha16": None}
+
+
+def gemm_traffic(run, ts):
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("tc_gemm.cu", "tc_common.cuh", "tc_gemm.h"):
+        with open(os.path.join(ROOT, "paper_1506_05741_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if GEMM_TRAFFIC["bytes"] is None or h.hexdigest()[:16] != GEMM_TRAFFIC["sources_sha16"]:
+        return None
+    return GEMM_TRAFFIC["bytes"]
 
 
 def cpu_leg(run, ts, x0, C0, seconds, cores):

@@ -345,11 +345,12 @@ DIAM_API void diam_multi_destroy(diam_multi* m);
  * retries), 7 re-whitening solve after a factor change, 8 surrogate screening (stage 1), 9 surrogate
  * training, 10 the fused steps (propose + map + test + record in one launch per step, or one launch per whole
  * interval; BF16 mode with the map carried through the proposal and no surrogate screen in force; phases
- * 2-4 then stay empty).
+ * 2-4 then stay empty), 11 the fold's SYRK alone (BF16 mode: one tensor-core launch; phase 5 keeps the rest of
+ * the fold).
  * counts and ms hold DIAM_N_PHASES entries each. A refresh factorised beside the next interval (refresh_delay
  * >= 1) is timed on its own stream whether or not cfg.profile is set, and counted in phase 6.
  * reset = 1 clears the accumulators after reading. Synchronises. */
-#define DIAM_N_PHASES 11
+#define DIAM_N_PHASES 12
 DIAM_API diam_status diam_get_profile(diam_ctx* ctx, int64_t* counts, double* ms, int32_t reset);
 
 DIAM_API void diam_destroy(diam_ctx* ctx);

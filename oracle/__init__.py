@@ -227,6 +227,8 @@ class Sampler:
             self._h = None
 
     def run(self, n_steps, record=False):
+        # the trajectory exists only if every run from the start recorded it
+        self._recorded = bool(record) and (self.steps == 0 or getattr(self, "_recorded", False))
         if lib().orc_run(self._h, int(n_steps), int(bool(record))) != 0:
             raise MemoryError("oracle trajectory record too large")
 
@@ -271,6 +273,8 @@ class Sampler:
         return dict(lp_prop=arrs[0], q_prop=arrs[1], q_cur=arrs[2], loga=arrs[3], acc=acc.astype(bool))
 
     def trajectory(self):
+        if not getattr(self, "_recorded", False):
+            raise RuntimeError("no trajectory: run(..., record=True) from the first step")
         d, P = self.cfg["d"], self.cfg["P"]
         out = np.zeros((self.steps, P, d))
         lib().orc_get_traj(self._h, _ptr(out))

@@ -68,7 +68,8 @@ class DiamStats(C.Structure):
 EXPORTS = ["diam_config_default", "diam_init", "diam_run_batch", "diam_flush", "diam_sync_moments", "diam_get_moments",
            "diam_export_moments", "diam_get_state", "diam_get_factor", "diam_get_trace", "diam_get_block_sums", "diam_get_psrf",
            "diam_save", "diam_load", "diam_get_profile", "diam_destroy", "diam_last_error", "diam_status_string"]
-PHASES = ["noise", "xi_gemm", "propose", "target", "accept", "fold", "refresh", "rewhiten", "screen", "train", "step"]
+PHASES = ["noise", "xi_gemm", "propose", "target", "accept", "fold", "refresh", "rewhiten", "screen", "train", "step",
+          "syrk"]
 
 
 def kernel_launches() -> int:
@@ -259,7 +260,12 @@ class MultiSampler:
     def run(self, n_steps: int):
         rc = self._l.diam_multi_run(self._h, int(n_steps))
         if rc:
-            raise DiamError(rc, "diam_multi_run")
+            why = []
+            for j, v in enumerate(self.views):
+                msg = self._l.diam_last_error(v._h)
+                if msg:
+                    why.append(f"problem {j} (d={v.d}): {msg.decode(errors='replace')}")
+            raise DiamError(rc, "diam_multi_run" + ("; " + "; ".join(why) if why else ""))
 
     def close(self):
         h = getattr(self, "_h", None)

@@ -154,7 +154,7 @@ struct diam_ctx {
 };
 
 enum : int { PH_NOISE = 0, PH_XI = 1, PH_PROPOSE = 2, PH_TARGET = 3, PH_ACCEPT = 4, PH_FOLD = 5, PH_REFRESH = 6,
-             PH_REWHITEN = 7, PH_SCREEN = 8, PH_TRAIN = 9, PH_STEP = 10 };
+             PH_REWHITEN = 7, PH_SCREEN = 8, PH_TRAIN = 9, PH_STEP = 10, PH_SYRK = 11 };
 
 // Start timing a phase; returns the event slot (or -1 when profiling is off).
 static int ph_begin(diam_ctx* c, int phase) {
@@ -365,10 +365,10 @@ static diam_status eval_lp(diam_ctx* c, const T* src, double* out) {
             epi.mode = TC_STORE;
             epi.D = c->ws;
             epi.ldd = c->dy;
-            CK(tc_gemm_bf16(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, 0, epi, &c->ctl->status, c->st));
+            CK(tc_gemm_bf16(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, 0, epi, &c->ctl->status, c->st, 256));
             float* w2 = c->ws + (size_t)P * c->dy;   // the second plane of the split-K workspace
             epi.D = w2;
-            CK(tc_gemm_bf16(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_lo2, nullptr, c->ldk, 0, epi, &c->ctl->status, c->st));
+            CK(tc_gemm_bf16(c->dy, P, c->ldk, c->Gq16, c->ldk, c->op_lo2, nullptr, c->ldk, 0, epi, &c->ctl->status, c->st, 256));
             const size_t n = (size_t)P * c->dy;
             { add_f32_kernel<<<(unsigned)std::min<size_t>(148 * 8, blocks_for(n)), kThreads, 0, c->st>>>(n, c->ws, w2); count_launch(); }
             { twisted_lp_kernel<float><<<P, kThreads, 0, c->st>>>(c->dy, c->ws, c->dy, c->tw_ilam, c->tw_c, out); count_launch(); }
@@ -486,9 +486,10 @@ static diam_status rec_ax(diam_ctx* c) {
     epi.mode = TC_STORE;
     epi.D = c->Ax;
     epi.ldd = c->dy;
-    CK(tc_gemm_bf16(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, 0, epi, &c->ctl->status, c->st));
+    // BN = 256: the persistent product, whose chunked accumulation keeps the tensor cores' truncation bias off A x
+    CK(tc_gemm_bf16(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_hi, c->op_lo, c->ldk, 0, epi, &c->ctl->status, c->st, 256));
     epi.D = c->ws;
-    CK(tc_gemm_bf16(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_lo2, nullptr, c->ldk, 0, epi, &c->ctl->status, c->st));
+    CK(tc_gemm_bf16(c->dy, c->P, c->ldk, c->Gq16, c->ldk, c->op_lo2, nullptr, c->ldk, 0, epi, &c->ctl->status, c->st, 256));
     const size_t n = (size_t)c->P * c->dy;
     { add_f32_kernel<<<(unsigned)std::min<size_t>(148 * 8, blocks_for(n)), kThreads, 0, c->st>>>(n, c->Ax, c->ws); count_launch(); }
     CK(cudaGetLastError());
@@ -604,9 +605,7 @@ static void launch_fused_step(diam_ctx* c, bool setup) {
     const bool keep = c->cfg.keep_block_sums != 0;
     const size_t smem = STAGE ? sizeof(float) * 3 * (size_t)c->d : 0;
     if (setup) {   // outside any capture: the staged rows may take all 48 KB of dynamic shared memory
-        if (STAGE)
-            cudaFuncSetAttribute(step_rec_kernel<NV, NM, VEC, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 48 * 1024);
+        if (STAGE) allow_max_dynamic_smem((const void*)step_rec_kernel<NV, NM, VEC, STAGE>);
         return;
     }
     step_rec_kernel<NV, NM, VEC, STAGE><<<c->P, FUSED_THREADS, smem, c->st>>>(
@@ -639,9 +638,11 @@ static void fused_step_nv(diam_ctx* c, bool setup) {
 
 // A whole interval of every chain in one launch (interval_rec_kernel): the fused step's conditions, the
 // 16-byte layout, and x, z, A x of one chain in shared memory.
+constexpr int kIntervalSmemMax = 128 * 1024;
+
 static bool interval_kernel_fits(const diam_ctx* c) {
     const bool vec = (c->d % 4) == 0 && (c->dy % 4) == 0 && (c->ldw % 4) == 0 && (c->ldh % 4) == 0 && (c->ldk % 4) == 0;
-    return fused_step_fits(c) && vec && sizeof(float) * (2 * (size_t)c->d + 2 * (size_t)c->dy) <= 128 * 1024;
+    return fused_step_fits(c) && vec && sizeof(float) * (2 * (size_t)c->d + 2 * (size_t)c->dy) <= kIntervalSmemMax;
 }
 
 template <int NV, int NM>
@@ -649,8 +650,8 @@ static void launch_interval(diam_ctx* c, int ns, bool setup) {
     DaState* a = c->da;
     const bool keep = c->cfg.keep_block_sums != 0;
     const size_t smem = sizeof(float) * (2 * (size_t)c->d + 2 * (size_t)c->dy);
-    if (setup) {   // outside any capture
-        cudaFuncSetAttribute(interval_rec_kernel<NV, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (setup) {   // outside any capture (the limit is the kernel's, shared with contexts of other sizes)
+        allow_max_dynamic_smem((const void*)interval_rec_kernel<NV, NM>);
         return;
     }
     interval_rec_kernel<NV, NM><<<c->P, FUSED_THREADS, smem, c->st>>>(
@@ -853,7 +854,11 @@ static diam_status fold_block(diam_ctx* c, int64_t blk) {
         epi.delta = c->delta;
         epi.inb = 1.0 / nb;
         epi.w = w;
+        ph_end(c, e0);   // the SYRK itself timed on its own (one tensor-core launch)
+        const int e1 = ph_begin(c, PH_SYRK);
         CK(tc_gemm_bf16(d, d, ldt, c->histT, ldt, c->histT, nullptr, ldt, 0, epi, &c->ctl->status, c->st, 256));
+        ph_end(c, e1);
+        e0 = ph_begin(c, PH_FOLD);
     } else {
         const double* H = (const double*)c->hist + (size_t)s0 * P * c->ldh;
         EpiFold epi{c->M2, d, c->svec, c->delta, 1.0 / nb, w};
@@ -1489,8 +1494,7 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
     if (s == DIAM_OK && c->bf && rewhiten_tc_fits(c->d, c->ldk) && rewhiten_tc_setup(c->d) != cudaSuccess)
         s = fail(c, DIAM_ECUDA, "cudaFuncSetAttribute");
     if (s == DIAM_OK && c->bf && rewhiten32_smem(c->d, 1) <= 220 * 1024 &&
-        cudaFuncSetAttribute(rewhiten32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)rewhiten32_smem(c->d, rewhiten32_group(c->d))) != cudaSuccess)
+        allow_max_dynamic_smem((const void*)rewhiten32_kernel) != cudaSuccess)
         s = fail(c, DIAM_ECUDA, "cudaFuncSetAttribute");
     if (s == DIAM_OK) s = upload_target(c, tg);
     if (s == DIAM_OK) s = c->bf ? init_state<float>(c, x0, C0, xref0) : init_state<double>(c, x0, C0, xref0);

@@ -188,4 +188,33 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
     return r;
 }
 
+// An FP64 scalar as the unevaluated sum of two floats (hi + lo equals it to about 2^-48 relative). The FP32
+// updates of BF16 mode take the proposal's rho and beta alpha this way: rounded to one float each, rho^2 + beta^2
+// would miss 1 by up to ~1e-7, a different proposal whose density the z recursion no longer gives exactly, and x*
+// would leave the FP64 proposal by a coherent rho-rounding times x (its log-density change by ~1e-7 d); with the
+// pair, x* and z* differ from the FP64 proposal only by the FP32 rounding of each result.
+struct F2 {
+    float hi, lo;
+};
+__host__ __device__ __forceinline__ F2 split_f2(double v) {
+    const float h = (float)v;
+    return F2{h, (float)(v - (double)h)};
+}
+// a x + add, with a given as hi + lo
+__device__ __forceinline__ float mul_f2(F2 a, float x, float add) { return fmaf(a.hi, x, fmaf(a.lo, x, add)); }
+
+// A kernel's dynamic shared-memory limit is a property of the kernel (per device), shared by every context in the
+// process whatever its size: raise it once to all the device allows next to the kernel's static shared memory, so
+// no context lowers it below what another launches with.
+inline cudaError_t allow_max_dynamic_smem(const void* kernel) {
+    cudaFuncAttributes fa;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 }  // namespace diam

@@ -79,10 +79,6 @@ constexpr int OZ_THREADS = 320;         // warp 0: TMA, warp 1: MMA issue, warps
 constexpr int OZ_EPI_WARPS = 8;         // two per tensor-memory lane quarter, 8 of the 16 columns each
 constexpr uint32_t OZ_ABYTES = 128 * OZ_K * 2, OZ_BBYTES = OZ_BN * OZ_K * 2;
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 // C[n][m] -= sum_k A[m][k] B[n][k] for m < Ma, n < Nb (and n >= m when lower), from the slices of A
 // (tensor map tmA, 128-row boxes) and of B (tmB, 16-row boxes). One CTA per work unit: the 7 B slices of
 // its n-tile stay in shared memory; the A slices of its m-tiles stream through a four-stage ring in slice

@@ -51,13 +51,14 @@ __global__ void __launch_bounds__(256) rec_map_kernel(int P, int dy, const Ctl* 
                                                        float inv2s2, int tanh_mode, double* __restrict__ lmap) {
     __shared__ float shf[32];
     const int p = blockIdx.x;
-    const float rho = (float)ctl->rho, om = (float)(1.0 - ctl->rho);
+    const F2 rho = split_f2(ctl->rho);
+    const float om = (float)(1.0 - ctl->rho);
     const float* ax = Ax + (size_t)p * dy;
     const float* xi = AXi + ((size_t)ctl->s_cur * P + p) * dy;
     float* axp = Axp + (size_t)p * dy;
     float acc = 0.f;
     for (int m = threadIdx.x; m < dy; m += blockDim.x) {
-        const float u = fmaf(rho, ax[m], fmaf(om, axref[m], xi[m]));
+        const float u = mul_f2(rho, ax[m], fmaf(om, axref[m], xi[m]));
         axp[m] = u;
         if (tanh_mode) {
             const float r = y32[m] - tanhf(u);

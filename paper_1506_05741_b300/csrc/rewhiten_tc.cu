@@ -256,7 +256,8 @@ size_t rewhiten_tc_smem(int d) { return 1024 + RwtSmem::RW + sizeof(float) * RWT
 bool rewhiten_tc_fits(int d, int ldk) { return d > 0 && d <= 64 + 128 * RWT_MAXT && ldk % 64 == 0 && rewhiten_tc_smem(d) <= 227 * 1024; }
 
 cudaError_t rewhiten_tc_setup(int d) {
-    return cudaFuncSetAttribute(rewhiten_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rewhiten_tc_smem(d));
+    if (rewhiten_tc_smem(d) > 227 * 1024) return cudaErrorInvalidValue;
+    return allow_max_dynamic_smem((const void*)rewhiten_tc_kernel);
 }
 
 cudaError_t rewhiten_tc(int d, int P, const uint16_t* Lq, int ldk, const float* X, const float* xref, float* Z,

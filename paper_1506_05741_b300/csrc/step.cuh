@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
     const int p = blockIdx.x, c = blockIdx.y;
     const int i0 = c * CHUNK, i1 = min(d, i0 + CHUNK);
     const T rho = (T)ctl->rho, ba = (T)ctl->ba;
+    const F2 rho2 = split_f2(ctl->rho), ba2 = split_f2(ctl->ba);   // the FP32 updates' rho and beta alpha
     const size_t row = (size_t)ctl->s_cur * P + p;   // this step's row of the interval's noise buffers
     const T* x = X + (size_t)p * d;
     const T* z = Z + (size_t)p * d;
@@ -176,8 +177,8 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
                 uint16_t ho[4], lo[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    vo[k] = ra[k] + rho * (xa[k] - ra[k]) + ia[k];
-                    uo[k] = rho * za[k] + ba * wv[k];
+                    vo[k] = ra[k] + mul_f2(rho2, xa[k] - ra[k], ia[k]);
+                    uo[k] = mul_f2(rho2, za[k], mul_f2(ba2, wv[k], 0.f));
                     qf += uo[k] * uo[k];
                     if (prior && (tg.kind != TK_BANANA || i + k >= 2)) lf -= 0.5f * vo[k] * vo[k] * tg.inv_lam32[i + k];
                     ho[k] = f32_to_bf16_bits(vo[k]);
@@ -207,11 +208,17 @@ __global__ void __launch_bounds__(256) propose_kernel(int d, int P, const T* __r
     }
     for (int i = i0 + threadIdx.x; !vec_done && i < i1; i += blockDim.x) {
         T xr = xref[i];
-        T v = xr + rho * (x[i] - xr) + xi[i];
         T wz;
         if constexpr (sizeof(WT) == sizeof(T)) wz = (T)w[i];
         else wz = (T)w_as_f32<WT>(w[i]);
-        T u = rho * z[i] + ba * wz;
+        T v, u;
+        if constexpr (std::is_same<T, float>::value) {
+            v = xr + mul_f2(rho2, x[i] - xr, xi[i]);
+            u = mul_f2(rho2, z[i], mul_f2(ba2, wz, 0.f));
+        } else {
+            v = xr + rho * (x[i] - xr) + xi[i];
+            u = rho * z[i] + ba * wz;
+        }
         xp[i] = v;
         zp[i] = u;
         qacc += (double)u * (double)u;
@@ -551,7 +558,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     __shared__ int s_acc;
     __shared__ uint64_t s_bar;
     const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const float rho = (float)ctl->rho, ba = (float)ctl->ba, om = (float)(1.0 - ctl->rho);
+    const F2 rho = split_f2(ctl->rho), ba = split_f2(ctl->ba);
+    const float om = (float)(1.0 - ctl->rho);
     const int s = ctl->s_cur;
     const long long t = ctl->t_cur;
     const size_t row = (size_t)s * P + p;
@@ -615,10 +623,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                 const float4 r4 = *reinterpret_cast<const float4*>(axref + m);
                 const float4 i4 = *reinterpret_cast<const float4*>(axi + m);
                 const float4 y4 = tanh_mode ? *reinterpret_cast<const float4*>(y32 + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-                uv[4 * g] = fmaf(rho, a4.x, fmaf(om, r4.x, i4.x));
-                uv[4 * g + 1] = fmaf(rho, a4.y, fmaf(om, r4.y, i4.y));
-                uv[4 * g + 2] = fmaf(rho, a4.z, fmaf(om, r4.z, i4.z));
-                uv[4 * g + 3] = fmaf(rho, a4.w, fmaf(om, r4.w, i4.w));
+                uv[4 * g] = mul_f2(rho, a4.x, fmaf(om, r4.x, i4.x));
+                uv[4 * g + 1] = mul_f2(rho, a4.y, fmaf(om, r4.y, i4.y));
+                uv[4 * g + 2] = mul_f2(rho, a4.z, fmaf(om, r4.z, i4.z));
+                uv[4 * g + 3] = mul_f2(rho, a4.w, fmaf(om, r4.w, i4.w));
                 map_term(uv[4 * g], a4.x, y4.x);
                 map_term(uv[4 * g + 1], a4.y, y4.y);
                 map_term(uv[4 * g + 2], a4.z, y4.z);
@@ -629,7 +637,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
             for (int j = 0; j < 4; ++j) {
                 const int m = idx(g, j);
                 if (m < dy) {
-                    uv[4 * g + j] = fmaf(rho, ax[m], fmaf(om, axref[m], axi[m]));
+                    uv[4 * g + j] = mul_f2(rho, ax[m], fmaf(om, axref[m], axi[m]));
                     map_term(uv[4 * g + j], ax[m], tanh_mode ? y32[m] : 0.f);
                 }
             }
@@ -674,8 +682,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                                      bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const float xv = xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
-                    const float zs = fmaf(rho, z4[j], ba * w4[j]);
+                    const float xv = xs[4 * g + j] = r4[j] + mul_f2(rho, x4[j] - r4[j], i4[j]);
+                    const float zs = mul_f2(rho, z4[j], mul_f2(ba, w4[j], 0.f));
                     qf += zs * zs;
                     dqf += (zs - z4[j]) * (zs + z4[j]);
                     if (prior) {
@@ -690,8 +698,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                 const int i = idx(g, j);
                 if (i < d) {
                     const float xr = xref[i], xc = x[i], zc = z[i];
-                    const float xv = xs[4 * g + j] = xr + rho * (xc - xr) + xi[i];
-                    const float zs = fmaf(rho, zc, ba * bf16_bits_to_f32(w[i]));
+                    const float xv = xs[4 * g + j] = xr + mul_f2(rho, xc - xr, xi[i]);
+                    const float zs = mul_f2(rho, zc, mul_f2(ba, bf16_bits_to_f32(w[i]), 0.f));
                     qf += zs * zs;
                     dqf += (zs - zc) * (zs + zc);
                     if (prior) {
@@ -760,7 +768,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         v[j] = xs[4 * g + j];
-                        zn[j] = fmaf(rho, z4[j], ba * w4[j]);
+                        zn[j] = mul_f2(rho, z4[j], mul_f2(ba, w4[j], 0.f));
                     }
                     *reinterpret_cast<float4*>(x + i) = make_float4(v[0], v[1], v[2], v[3]);
                     *reinterpret_cast<float4*>(z + i) = make_float4(zn[0], zn[1], zn[2], zn[3]);
@@ -788,7 +796,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                     if (a) {
                         v = xs[4 * g + j];
                         x[i] = v;
-                        z[i] = fmaf(rho, z[i], ba * bf16_bits_to_f32(w[i]));
+                        z[i] = mul_f2(rho, z[i], mul_f2(ba, bf16_bits_to_f32(w[i]), 0.f));
                     } else {
                         v = x[i];
                     }
@@ -862,7 +870,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
     __shared__ float s_lu32;
     __shared__ int s_acc;
     const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const float rho = (float)ctl->rho, ba = (float)ctl->ba, om = (float)(1.0 - ctl->rho);
+    const F2 rho = split_f2(ctl->rho), ba = split_f2(ctl->ba);
+    const float om = (float)(1.0 - ctl->rho);
     const int s0 = ctl->s_cur;
     const long long t0 = ctl->t_cur;
     const long long head0 = dacnt ? dacnt->head : 0;
@@ -945,10 +954,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
                 const float4 i4 = *reinterpret_cast<const float4*>(axi + m);
                 const float4 y4 = tanh_mode ? *reinterpret_cast<const float4*>(y32 + m) : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float4 t4 = tanh_mode ? *reinterpret_cast<const float4*>(st + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-                uv[4 * g] = fmaf(rho, a4.x, fmaf(om, r4.x, i4.x));
-                uv[4 * g + 1] = fmaf(rho, a4.y, fmaf(om, r4.y, i4.y));
-                uv[4 * g + 2] = fmaf(rho, a4.z, fmaf(om, r4.z, i4.z));
-                uv[4 * g + 3] = fmaf(rho, a4.w, fmaf(om, r4.w, i4.w));
+                uv[4 * g] = mul_f2(rho, a4.x, fmaf(om, r4.x, i4.x));
+                uv[4 * g + 1] = mul_f2(rho, a4.y, fmaf(om, r4.y, i4.y));
+                uv[4 * g + 2] = mul_f2(rho, a4.z, fmaf(om, r4.z, i4.z));
+                uv[4 * g + 3] = mul_f2(rho, a4.w, fmaf(om, r4.w, i4.w));
                 map_term(uv[4 * g], a4.x, t4.x, y4.x, mf, dmf);
                 map_term(uv[4 * g + 1], a4.y, t4.y, y4.y, mf, dmf);
                 map_term(uv[4 * g + 2], a4.z, t4.z, y4.z, mf, dmf);
@@ -974,8 +983,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
                                      bf16_bits_to_f32((uint16_t)(wb.y & 0xFFFFu)), bf16_bits_to_f32((uint16_t)(wb.y >> 16))};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const float xv = xs[4 * g + j] = r4[j] + rho * (x4[j] - r4[j]) + i4[j];
-                    const float zs = fmaf(rho, z4[j], ba * w4[j]);
+                    const float xv = xs[4 * g + j] = r4[j] + mul_f2(rho, x4[j] - r4[j], i4[j]);
+                    const float zs = mul_f2(rho, z4[j], mul_f2(ba, w4[j], 0.f));
                     qf += zs * zs;
                     dqf += (zs - z4[j]) * (zs + z4[j]);
                     if (prior) {
@@ -1040,7 +1049,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         v[j] = xs[4 * g + j];
-                        zn[j] = fmaf(rho, z4[j], ba * w4[j]);
+                        zn[j] = mul_f2(rho, z4[j], mul_f2(ba, w4[j], 0.f));
                     }
                     *reinterpret_cast<float4*>(sx + i) = make_float4(v[0], v[1], v[2], v[3]);
                     *reinterpret_cast<float4*>(sz + i) = make_float4(zn[0], zn[1], zn[2], zn[3]);

@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     }
     __syncwarp();
 
-    // epilogue: wait for the accumulator (bounded), then every warp reads its 32 TMEM lanes
-    mbar_wait(smem_u32(done), 0, abort_flag);
+    // epilogue: wait for the accumulator (bounded; after an abort too, for the MMAs issued so far to complete
+    // before tensor memory is read or freed), then every warp reads its 32 TMEM lanes
+    mbar_wait_drain(smem_u32(done), 0);
     __syncthreads();
     const bool ok = (*abort_flag == 0);
     tc_fence_after();
@@ -169,7 +170,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                 if (n0 + col < N) epi.partial[(size_t)mt * N + n0 + col] = s;
             }
         } else {
-            const float scale = (epi.mode == TC_STORE && epi.scale_dev) ? (float)*epi.scale_dev : 1.0f;
+            // the scale as two floats (beta alpha of the noise product: the same value the z recursion uses)
+            const F2 scale = split_f2((epi.mode == TC_STORE && epi.scale_dev) ? *epi.scale_dev : 1.0);
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
                 uint32_t r[32];
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                         if (n >= N) continue;
                         const float v = __uint_as_float(r[j]);
                         if (epi.mode == TC_STORE) {
-                            epi.D[(size_t)blockIdx.z * epi.split_stride + (size_t)n * epi.ldd + m] = scale * v;
+                            epi.D[(size_t)blockIdx.z * epi.split_stride + (size_t)n * epi.ldd + m] = mul_f2(scale, v, 0.f);
                         } else if (epi.mode == TC_GELU) {
                             const float zf = v + epi.bias[m];
                             if (epi.Zout) epi.Zout[(size_t)n * epi.ldz + m] = zf;
@@ -201,6 +203,200 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     tc_fence_before();
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+}
+
+// Persistent form of the wide products (BN = 256, store and fold epilogues, no split K): the interval's noise
+// product, its map and the fold's SYRK. One CTA per SM walks a static list of output tiles (tile t = blockIdx.x +
+// i gridDim.x, m fastest, so each CTA's tiles mix short and long triangular K ranges). Warp 0 stages the A and B
+// tiles through the shared-memory ring without stopping at tile boundaries; warp 1 issues the products; warps 2-9
+// (two per 32-lane quarter of tensor memory, 128 columns each) sum them.
+//
+// Accumulation in chunks: the tensor cores add each product into the FP32 accumulator after aligning it to the
+// running sum and dropping the bits below (a truncation: a bias toward zero that grows with the number of products
+// summed in one accumulator, measured on B300 at -8e-6 relative for K = 4096 on products like the noise product's,
+// -4.7e-7 for chunks of 256 and -1e-7 for chunks of 64 summed outside in round-to-nearest). So each chunk of
+// `chunk` K blocks goes into a fresh accumulator, one of two (2 x 256 columns, all of tensor memory), and the
+// epilogue warps add the chunk sums in FP32 registers (round to nearest) while the next chunk's products run; a
+// tile's result is written from the registers after its last chunk, while the products run up to two chunks
+// ahead. The launcher sizes the chunk so that those two chunks cover the tile's write: 8 K blocks (K = 512) for
+// the FP32 store, 32 (K = 2048) for the fold's FP64 read-modify-write of M2.
+//
+// Barriers: full / empty per ring stage, tfull (MMA -> epilogue) and tempty (epilogue -> MMA, 256 arrivals) per
+// accumulator. Every wait is clock-bounded; on expiry the CTA records DEV_TIMEOUT, lets its TMA loads land and its
+// issued MMAs complete (one commit tracks them all), frees its tensor memory and returns.
+constexpr int PT_THREADS = 320, PT_BN = 256, PT_CHUNK_STORE = 8, PT_CHUNK_FOLD = 32;
+
+__global__ void __launch_bounds__(PT_THREADS, 1) tc_gemm_persist_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ CUtensorMap tmA2, int M, int N, int nkb,
+    int a_lower, int has_b2, int has_a2, int stages, int mtiles, int ntiles, int chunk, TcEpi epi, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = PT_BN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
+    const bool two_pass = has_b2 || has_a2;
+    uint64_t* full = (uint64_t*)(smem + stages * STAGE);
+    uint64_t* empty = full + stages;
+    uint64_t* tfull = empty + stages;   // [2]
+    uint64_t* tempty = tfull + 2;       // [2]
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (epi.n_dev) N = min(N, *epi.n_dev);   // device-side row count of B: tiles past it are skipped by every role
+    const int T = mtiles * ntiles;
+    auto tile_of = [&](int t, int& m0, int& n0) {
+        m0 = (t % mtiles) * TC_BM;
+        n0 = (t / mtiles) * PT_BN;
+    };
+    auto valid = [&](int m0, int n0) { return n0 < N && !(epi.mode == TC_FOLD && n0 + PT_BN - 1 < m0); };
+    auto cap_of = [&](int m0) { return a_lower ? min(nkb, (m0 + TC_BM + TC_BK - 1) / TC_BK) : nkb; };
+    auto kend_of = [&](int m0) { return two_pass ? 2 * cap_of(m0) : cap_of(m0); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&tfull[a]), 1);
+            mbar_init(smem_u32(&tempty[a]), 256);
+        }
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2u * PT_BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer: a global k-block count across the CTA's tiles
+            int it = 0;
+            for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
+                int m0, n0;
+                tile_of(t, m0, n0);
+                if (!valid(m0, n0)) continue;
+                const int cap = cap_of(m0), kend = kend_of(m0);
+                for (int kb = 0; kb < kend; ++kb, ++it) {
+                    const int s = it % stages;
+                    if (it >= stages && !mbar_wait(smem_u32(&empty[s]), ((it / stages) & 1) ^ 1, abort_flag)) break;
+                    uint8_t* st = smem + s * STAGE;
+                    const uint32_t fb = smem_u32(&full[s]);
+                    const bool second = kb >= cap;
+                    const int ka = second ? kb - cap : kb;
+                    mbar_expect_tx(fb, STAGE);
+                    tma_load_2d(smem_u32(st), (second && has_a2) ? &tmA2 : &tmA, fb, ka * TC_BK, m0);
+                    tma_load_2d(smem_u32(st + A_BYTES), (second && has_b2) ? &tmB2 : &tmB, fb, ka * TC_BK, n0);
+                }
+            }
+            if (*abort_flag) {   // every issued load lands before the CTA may exit
+                for (int k = max(0, it - stages); k < it; ++k) {
+                    const long long t0 = clock64();
+                    while (!mbar_try(smem_u32(&full[k % stages]), (k / stages) & 1) && clock64() - t0 < TC_WAIT_CYCLES) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer: a global chunk count picks the accumulator
+            constexpr uint32_t idesc = idesc_bf16(PT_BN);
+            int it = 0, cc = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < T && ok && !*abort_flag; t += gridDim.x) {
+                int m0, n0;
+                tile_of(t, m0, n0);
+                if (!valid(m0, n0)) continue;
+                const int kend = kend_of(m0);
+                for (int kb0 = 0; kb0 < kend; kb0 += chunk, ++cc) {
+                    const int acc = cc & 1;
+                    // the epilogue has taken the chunk two back out of this accumulator
+                    if (cc >= 2 && !mbar_wait(smem_u32(&tempty[acc]), ((cc >> 1) - 1) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tacc = tmem + (uint32_t)(acc * PT_BN);
+                    const int kb1 = min(kend, kb0 + chunk);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = it % stages;
+                        if (!mbar_wait(smem_u32(&full[s]), (it / stages) & 1, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(smem + s * STAGE), sb = sa + A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk)
+                            umma_bf16(tacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                                      (kb > kb0 || kk) ? 1u : 0u);
+                        umma_commit(smem_u32(&empty[s]));
+                    }
+                    if (!ok) break;
+                    umma_commit(smem_u32(&tfull[acc]));
+                }
+            }
+            umma_commit(smem_u32(drain));   // completes once every MMA this thread issued has
+        }
+    } else {   // epilogue warps 2-9: lanes 32 (warp % 4) .. + 31 of tensor memory, columns 128 h .. + 127
+        const int quarter = warp & 3, h = (warp - 2) >> 2, row = quarter * 32 + lane;
+        const F2 scale = split_f2((epi.mode == TC_STORE && epi.scale_dev) ? *epi.scale_dev : 1.0);
+        float sum[128];
+        int cc = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
+            int m0, n0;
+            tile_of(t, m0, n0);
+            if (!valid(m0, n0)) continue;
+            const int nch = (kend_of(m0) + chunk - 1) / chunk;
+            for (int c = 0; c < nch; ++c, ++cc) {
+                const int acc = cc & 1;
+                if (!mbar_wait(smem_u32(&tfull[acc]), (cc >> 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * PT_BN + h * 128);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    uint32_t r[16];
+                    tmem_ld16(tb + i * 16, r);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) sum[i * 16 + j] = (c ? sum[i * 16 + j] : 0.f) + __uint_as_float(r[j]);
+                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&tempty[acc]));
+            }
+            if (!ok) break;
+            const int m = m0 + row;
+            if (m < M) {
+#pragma unroll
+                for (int j = 0; j < 128; ++j) {
+                    const int n = n0 + h * 128 + j;
+                    if (n >= N) continue;
+                    if (epi.mode == TC_STORE) {
+                        epi.D[(size_t)n * epi.ldd + m] = mul_f2(scale, sum[j], 0.f);
+                    } else if (n >= m) {
+                        const double add = (double)sum[j] - epi.s[n] * epi.s[m] * epi.inb + epi.delta[n] * epi.delta[m] * epi.w;
+                        epi.M2[(size_t)n * epi.ldm + m] += add;
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // every MMA issued has completed (bounded, even after an abort) before tensor memory is freed
+    mbar_wait_drain(smem_u32(drain), 0);
+    if (threadIdx.x == 0 && *abort_flag) set_status(status, DEV_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * PT_BN));
 }
 
 // ---------------------------------------------------------------------------------------------------- host
@@ -288,6 +484,30 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
         splits = 1;
     }
     dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN, splits);
+    if (BN == PT_BN && splits == 1 && (epi.mode == TC_STORE || epi.mode == TC_FOLD)) {
+        // the wide store / fold products: persistent, one CTA per SM, epilogues beside the next tile's products
+        static bool pattr_set[kAttrDevices] = {};
+        static int sms[kAttrDevices] = {};
+        {
+            std::lock_guard<std::mutex> g(attr_mu);
+            if (!pattr_set[dev]) {
+                cudaError_t e = cudaFuncSetAttribute(tc_gemm_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     227 * 1024);
+                if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+                if (e != cudaSuccess) return e;
+                pattr_set[dev] = true;
+            }
+        }
+        const size_t pstage = (size_t)TC_BM * TC_BK * 2 + (size_t)PT_BN * TC_BK * 2;
+        const int pst = (int)std::min<size_t>(TC_MAX_STAGES, (227 * 1024 - 1024 - 256) / pstage);
+        const size_t psmem = 1024 + pst * pstage + 256;
+        const int tiles = (int)grid.x * (int)grid.y;
+        const int ctas = std::max(1, std::min(tiles, sms[dev]));
+        const int chunk = epi.mode == TC_FOLD ? PT_CHUNK_FOLD : PT_CHUNK_STORE;
+        { tc_gemm_persist_kernel<<<ctas, PT_THREADS, psmem, st>>>(mA, mB, mB2, mA2, M, N, nkb, a_lower, has_b2, has_a2,
+                                                                 pst, (int)grid.x, (int)grid.y, chunk, epi, status); count_launch(); }
+        return cudaGetLastError();
+    }
     { tc_gemm_kernel<BN><<<grid, 128, smem, st>>>(mA, mB, mB2, mA2, M, N, nkb, a_lower, has_b2, has_a2, kb_split, stages,
                                                   epi, status); count_launch(); }
     return cudaGetLastError();

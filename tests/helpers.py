@@ -48,3 +48,22 @@ def diff_scale(to):
 def loga_err(tg, to):
     """Largest error of log a, relative to the difference scale above."""
     return float(np.max(np.abs(np.asarray(tg["loga"]) - np.asarray(to["loga"])) / diff_scale(to)))
+
+
+def state_rounding_bound(d):
+    """Absolute size up to which log a of the BF16 path may leave the FP64 oracle's through the FP32 rounding of the
+    proposal itself. The CUDA path keeps the chain's states x and z in FP32: each coordinate of x* and z* is
+    rounded once (relative error <= 2^-24), and log a depends on them through the log-density difference and the
+    quadratic's difference, with sensitivities of O(1) per coordinate in whitened units (d(q* - q)/dz*_k = z*_k,
+    and the same for the prior part when the factor follows the prior). So the two values differ by a sum of ~2d
+    independent terms of size <= 2^-24 v_k^2 (E v^4 = 3): standard deviation ~ 2^-24 sqrt(2 d), measured 1.0e-5 at
+    d = 4096 with the tanh likelihood's part included. The bound is 14 2^-24 sqrt(d) (5.3e-5 at d = 4096, about
+    five measured standard deviations)."""
+    return 14.0 * 2.0 ** -24 * np.sqrt(d)
+
+
+def loga_excess(tg, to, d, rel=1e-5):
+    """Largest error of log a over its bar: max(rel x the difference scale, the FP32-state bound of d) (<= 1
+    passes)."""
+    err = np.abs(np.asarray(tg["loga"]) - np.asarray(to["loga"]))
+    return float(np.max(err / np.maximum(rel * diff_scale(to), state_rounding_bound(d))))

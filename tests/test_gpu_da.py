@@ -85,8 +85,9 @@ def test_two_stage_decisions_match_oracle():
     """The screen (stage 1) and the exact test (stage 2) of delayed acceptance against the FP64 reference of the
     two-stage rule (oracle/da.py), with stage 1 on from the start (screen_from_start, the given network, no
     training) and a fixed factor and beta: tanh regression d = 192, d_y = 64, eight chains, 64 steps. Every stage-1
-    pass and every final decision agree (a decision whose log u lies within 5e-3 of its log a on the oracle's side
-    ends that chain's comparison: the network's BF16 roundings may differ there); the stage-2 log ratios agree to
+    pass and every final decision agree (only a decision whose log u lies within 5e-3 of its log a on the oracle's
+    side may go the other way, the network's BF16 roundings may differ there, and then ends that chain's
+    comparison); the stage-2 log ratios agree to
     2e-3 of max(1, |log a2|) (the same BF16 roundings, and FP32 sums of the network and of the map terms)."""
     import paper_1506_05741_b300 as dm
     from oracle import da
@@ -116,8 +117,10 @@ def test_two_stage_decisions_match_oracle():
     compared = 0
     for p in range(P):
         for t in range(steps):
-            if ref["m1"][t, p] < tie or ref["m2"][t, p] < tie:
-                break                                # a near tie: the chains may part here
+            near = ref["m1"][t, p] < tie or ref["m2"][t, p] < tie
+            same = pass_g[t, p] == ref["pass1"][t, p] and tg["acc"][t, p] == ref["acc"][t, p]
+            if near and not same:
+                break                                # a near tie decided the other way: the chains part here
             assert pass_g[t, p] == ref["pass1"][t, p], (t, p)
             assert tg["acc"][t, p] == ref["acc"][t, p], (t, p)
             if ref["pass1"][t, p]:

@@ -6,7 +6,9 @@ of the CUDA path's FP32 states and sums.
 
 Bars (Algorithm 1's test, eq. (accept)): identical accept decisions; log pi(x*) within 1e-5 of |log pi|; and
 log a within 1e-5 of the size of its two terms, max(1, |log pi(x*) - log pi(x)|, |q(x*) - q(x)|) (the
-log-density differences the test decides on).
+log-density differences the test decides on), or within the FP32-state bound 14 2^-24 sqrt(d) where that is
+larger (helpers.state_rounding_bound: the chain's x* and z* are FP32, one rounding per coordinate, while the
+oracle's are FP64; measured standard deviation of the difference 1.0e-5 at d = 4096, 5.3e-5 bound).
 
 The full-size case runs the benchmark's launch configuration (P = 512, n_lag = 128) and checks sampled chains
 against the oracle run on those chains alone: with beta fixed and no refresh in the window the chains are
@@ -21,7 +23,7 @@ import pytest
 
 import oracle
 import workloads
-from helpers import CFG_KEYS, diff_scale, loga_err, oracle_target
+from helpers import CFG_KEYS, diff_scale, loga_excess, oracle_target
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -57,10 +59,10 @@ def _check(tg, to, cols):
     assert np.array_equal(sub["acc"], to["acc"]), np.argwhere(sub["acc"] != to["acc"])[:5]
     lp_err = np.max(np.abs(sub["lp_prop"] - to["lp_prop"]) / np.maximum(1.0, np.abs(to["lp_prop"])))
     assert lp_err <= TOL, lp_err
-    err = loga_err(sub, to)
-    assert err <= TOL, (err, np.unravel_index(np.argmax(np.abs(sub["loga"] - to["loga"]) / diff_scale(to)),
-                                              to["loga"].shape))
-    return err
+    ex = loga_excess(sub, to, 4096)
+    assert ex <= 1.0, (ex, np.unravel_index(np.argmax(np.abs(sub["loga"] - to["loga"]) / diff_scale(to)),
+                                            to["loga"].shape))
+    return ex
 
 
 def test_interval_kernel_at_d4096_matches_oracle():
