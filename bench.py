@@ -525,8 +525,8 @@ def roofline(prof, run, ts, pk, pk_src, ring):
         ach = units / per / (1e12 if unit == "TFLOP/s" else 1e9)
         table[k] = {"share": round(ms / total, 4), "launch_ms": round(per * 1e3, 4), "bound": bound,
                     "achieved": round(ach, 3), "unit": unit, "peak": peak, "frac": round(ach / peak, 4)}
-    # The dominant kernel of the launch list (profiles/launches_tanh4096_bf16.md): tc_gemm_kernel<256>, three
-    # launches per interval -- the noise product (lower-triangular A_n W: d^2 N flops), its map ((A A_n) W:
+    # The dominant kernel of the launch list (profiles/launches_tanh4096_bf16.md): tc_gemm_persist_kernel, three
+    # wide launches per interval -- the noise product (lower-triangular A_n W: d^2 N flops), its map ((A A_n) W:
     # 2 d_y d N; the lo pass of the two-term operand is a precision overhead, not counted) and the fold's SYRK
     # (lower half, d (d + 1) N). Achieved = their algorithmic flops over their CUDA-event time (phases xi_gemm
     # and syrk), per launch as the average of the three. The refresh is the largest phase but is ~250 launches of
@@ -536,7 +536,7 @@ def roofline(prof, run, ts, pk, pk_src, ring):
         per_int = float(d) * d * N + 2.0 * dy * d * N + float(d) * (d + 1) * N
         t_int = (mx / cx + ms_ / cs) / 1e3          # seconds per interval of the three launches
         ach = per_int / t_int / 1e12
-        out = {"kernel": "tc_gemm_kernel<256> (noise product, its map, fold SYRK: 3 launches per interval)",
+        out = {"kernel": "tc_gemm_persist_kernel (noise product, its map, fold SYRK: 3 launches per interval)",
                "bound": "tensor", "achieved": round(ach, 3), "peak": sus, "unit": "TFLOP/s",
                "frac": round(ach / sus, 4), "traffic": gemm_traffic(run, ts), "launch_ms": round(t_int * 1e3 / 3, 4),
                "flops_per_launch": round(per_int / 3), "peak_source": pk_src + " (sustained)", "phases": table}
@@ -559,10 +559,12 @@ def roofline(prof, run, ts, pk, pk_src, ring):
     return out
 
 
-# DRAM traffic of one tc_gemm_kernel<256> launch of the noise product at the benchmark's shape (M = K = 4096,
-# N = 65536), from ncu (dram__bytes_read.sum + dram__bytes_write.sum; profiles/tc_gemm_noise_product_4096.md), with
-# a digest of the kernel's sources when it was taken: reported only while the sources are unchanged.
-GEMM_TRAFFIC = {"bytes": None, "sources_sha16": None}
+# DRAM traffic per launch of tc_gemm_persist_kernel in the benchmark's interval: dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the benchmark itself (one pass per launch), averaged over the
+# noise product (2.468 GB), its map (1.690 GB) and the fold's SYRK (1.274 GB) of two intervals
+# (profiles/tc_gemm_persist_tanh4096.md), with a digest of the kernel's sources when it was taken: reported only
+# while the sources are unchanged.
+GEMM_TRAFFIC = {"bytes": 1810500000, "sources_sha16": "8891ab941cf8b54b"}
 
 
 def gemm_traffic(run, ts):

@@ -1742,6 +1742,12 @@ __global__ void convert_kernel(size_t n, const A* __restrict__ in, B* __restrict
         out[i] = (B)in[i];
 }
 
+// v <- its BF16 rounding (round to nearest even), kept in FP64.
+__global__ void round_bf16_kernel(size_t n, double* __restrict__ v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        v[i] = round_bf16(v[i]);
+}
+
 // Row-major d_y x d FP64 matrix -> BF16 bits (round to nearest even), ldk columns, zero padded.
 __global__ void to_bf16_rows_kernel(int rows, int d, const double* __restrict__ in, uint16_t* __restrict__ out, int ldk) {
     int i = blockIdx.y;

@@ -62,8 +62,18 @@ def state_rounding_bound(d):
     return 14.0 * 2.0 ** -24 * np.sqrt(d)
 
 
-def loga_excess(tg, to, d, rel=1e-5):
-    """Largest error of log a over its bar: max(rel x the difference scale, the FP32-state bound of d) (<= 1
-    passes)."""
+def fp32_value_bound(to):
+    """Absolute size up to which log a of the BF16 path may leave the oracle's where the CUDA path forms log pi(x*)
+    or q* as values in FP32 (a target evaluated whole, such as the twisted Gaussians, or a per-step product) rather
+    than as differences: each such value carries the FP32 rounding of its terms and sums, a relative error of a few
+    2^-24, so the bar is 4 2^-24 (|log pi(x*)| + |log pi(x)| + |q*| + |q|) of the oracle's trace."""
+    dq = np.asarray(to["q_prop"]) - np.asarray(to["q_cur"])
+    lp_cur = np.asarray(to["lp_prop"]) - (np.asarray(to["loga"]) - dq)
+    return 4.0 * 2.0 ** -24 * (np.abs(to["lp_prop"]) + np.abs(lp_cur) + np.abs(to["q_prop"]) + np.abs(to["q_cur"]))
+
+
+def loga_excess(tg, to, bound, rel=1e-5):
+    """Largest error of log a over its bar: max(rel x the difference scale, bound) (<= 1 passes); bound a number
+    (state_rounding_bound) or an array over the trace (fp32_value_bound)."""
     err = np.abs(np.asarray(tg["loga"]) - np.asarray(to["loga"]))
-    return float(np.max(err / np.maximum(rel * diff_scale(to), state_rounding_bound(d))))
+    return float(np.max(err / np.maximum(rel * diff_scale(to), bound)))

@@ -2,8 +2,8 @@
 sampler against the oracle run in its BF16 mode (same rounded factor A_q, same rounded noise W_q, same
 rounded linear map). The CUDA side keeps FP32 states and FP32 accumulation, so agreement is to the FP32
 level: log-densities and proposal quadratics within 1e-5 of max(1, |log pi|, |q|); log a within 1e-5 of
-max(1, |log pi(x*) - log pi(x)|, |q* - q|), or within the FP32-state bound of helpers.state_rounding_bound where
-that is larger; accept decisions identical over the compared steps."""
+max(1, |log pi(x*) - log pi(x)|, |q* - q|), or within the FP32 rounding of the values it is formed from
+(helpers.fp32_value_bound) where that is larger; accept decisions identical over the compared steps."""
 import ctypes
 
 import numpy as np
@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import workloads
-from helpers import diff_scale, loga_excess, make_pair, rel_err, trace_scale
+from helpers import fp32_value_bound, loga_excess, make_pair, rel_err, trace_scale
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -94,8 +94,8 @@ def test_bf16_steps_match_oracle_bf16_mode(kind):
     sc = trace_scale(to)
     for k in ("lp_prop", "q_prop", "q_cur"):   # values: against their own size
         assert rel_err(tg[k], to[k], sc) <= TOL, (k, rel_err(tg[k], to[k], sc))
-    # log a: against the size of its two differences, or the FP32-state bound (helpers.state_rounding_bound)
-    assert loga_excess(tg, to, d) <= 1.0, loga_excess(tg, to, d)
+    # log a: against the size of its two differences, or the FP32 rounding of the values they come from
+    assert loga_excess(tg, to, fp32_value_bound(to)) <= 1.0, loga_excess(tg, to, fp32_value_bound(to))
     L, Lq, xr, _ = g.factor()
     Lo, Lqo, xro = o.factor()
     assert np.array_equal(Lq, Lqo) and np.array_equal(xr, xro)
@@ -154,8 +154,8 @@ def test_refresh_delay_applies_the_factor_where_the_oracle_does(delay):
     sc = trace_scale(to)[:k]
     for key in ("lp_prop", "q_prop", "q_cur"):
         assert rel_err(tg[key][:k], to[key][:k], sc) <= TOL, (key, rel_err(tg[key][:k], to[key][:k], sc))
-    head = {key: v[:k] for key, v in tg.items()}
-    assert loga_excess(head, {key: v[:k] for key, v in to.items()}, 256) <= 1.0
+    head, ohead = {key: v[:k] for key, v in tg.items()}, {key: v[:k] for key, v in to.items()}
+    assert loga_excess(head, ohead, fp32_value_bound(ohead)) <= 1.0
     for tr in (tg, to):
         carried = np.where(tr["acc"], tr["q_prop"], tr["q_cur"])   # q of each step's outcome
         assert np.array_equal(tr["q_cur"][1:k], carried[:k - 1])   # no factor change before step 2 n_lag

@@ -23,7 +23,7 @@ import pytest
 
 import oracle
 import workloads
-from helpers import CFG_KEYS, diff_scale, loga_excess, oracle_target
+from helpers import CFG_KEYS, diff_scale, loga_excess, oracle_target, state_rounding_bound
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -59,7 +59,7 @@ def _check(tg, to, cols):
     assert np.array_equal(sub["acc"], to["acc"]), np.argwhere(sub["acc"] != to["acc"])[:5]
     lp_err = np.max(np.abs(sub["lp_prop"] - to["lp_prop"]) / np.maximum(1.0, np.abs(to["lp_prop"])))
     assert lp_err <= TOL, lp_err
-    ex = loga_excess(sub, to, 4096)
+    ex = loga_excess(sub, to, state_rounding_bound(4096))
     assert ex <= 1.0, (ex, np.unravel_index(np.argmax(np.abs(sub["loga"] - to["loga"]) / diff_scale(to)),
                                             to["loga"].shape))
     return ex
