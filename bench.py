@@ -86,6 +86,12 @@ def parse():
     ap.add_argument("--multi", action="store_true",
                     help="instead of the throughput bench: the uneven batch of 64 problems (d log-uniform in [256, 8192], "
                          "dense Gaussians and bananas, P = 32, n_lag = 64, BF16) at its full size")
+    ap.add_argument("--da-gain", action="store_true",
+                    help="instead of the throughput bench: delayed acceptance with and without the surrogate on the tanh "
+                         "regression with an expensive exact target (map carried off), over d")
+    ap.add_argument("--dag-ds", default="256,512,1024,2048,4096")
+    ap.add_argument("--dag-warmup", type=int, default=60)
+    ap.add_argument("--dag-steps", type=int, default=40)
     ap.add_argument("--multi-n", type=int, default=64)
     ap.add_argument("--multi-warmup", type=int, default=48,
                     help="warm-up intervals of --multi: from x_0 = 0 and A_0 = Id the step size must first adapt down "
@@ -224,6 +230,67 @@ def compare(args):
     print(json.dumps({"metric": "integrated autocorrelation time (steps) of DIAM, AM, pCN, RW (Sec. 3.2)",
                       "config": {"P": P, "n_lag": "d/2", "prec": args.cmp_prec.upper(), "warmup_intervals": args.cmp_warmup,
                                  "intervals": args.cmp_intervals, "start": "exact draws of the target"},
+                      "rows": rows}), flush=True)
+
+
+def da_gain(args):
+    """Delayed acceptance where the exact target is expensive: the tanh regression with the map carried off
+    (carry_map 0), so every exact log-density is a d_y x d product per chain-step on the tensor cores, against the
+    screen's 2 (d h + h^2) (h = the hidden width). For each d in --dag-ds (d_y = d / 2, prior N(0, diag(i^-2)),
+    P = 256 chains, n_lag = 64, BF16 mode, refresh every interval), the same chains from the same start with and
+    without the surrogate: --dag-warmup intervals (the surrogate trains after each synchronisation of M = 2
+    intervals once 4 intervals of pairs are in, with the real 0.5-nat gate), then --dag-steps timed intervals and
+    the ESS over them. Per d: device ms per interval, acceptance, min-ESS/s, and the screen's state (trainings,
+    held-out RMSE, active, stage-1 pass rate, exact evaluations per chain-step). One JSON line."""
+    import torch
+    import paper_1506_05741_b300 as dm
+    import workloads
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    P, nl = 256, 64
+    rows = []
+    for d in [int(v) for v in args.dag_ds.split(",")]:
+        ts = workloads.tanh_regression(d, d // 2, 2000 + d)
+        x0 = workloads.start_state(d, P, 5) * np.sqrt(ts.lam)
+        C0 = np.diag(ts.lam)
+        h = min(512, max(128, (d // 2) // 128 * 128))
+        for use in (False, True):
+            cfg = dm.default_config(d, P, n_lag=nl, M=2, beta0=min(2.4 / np.sqrt(d), 0.5), seed=41, prec=dm.BF16,
+                                    carry_map=0, refresh_delay=0)
+            cfg["keep_block_sums"] = 1
+            s = dm.Sampler(cfg, ts, x0=x0, C0=C0, stream=stream.cuda_stream)
+            if use:
+                dc = dm.da_default_config(h1=h, h2=h, retrain_every=1, first_train_min=4 * P * nl)
+                s.da_enable(dc, workloads.mlp_init(d, h, h, seed=11))
+            W, K = args.dag_warmup, args.dag_steps
+            s.run(W * nl)
+            mom0 = s.export_moments()
+            st0 = s.stats()
+            d0 = s.da_stats() if use else None
+            dt = time_intervals(s, nl, K, torch, stream)
+            mom1 = s.export_moments()
+            xs, _ = s.block_sums(W + K)
+            table, (min_ess, _, _), plateau, N = ess_sweep(xs[W:W + K], nl, mom0, mom1)
+            st = s.stats()
+            row = {"d": d, "d_y": d // 2, "surrogate": use, "ms_per_interval": round(dt / K * 1e3, 3),
+                   "chain_steps_per_s": round(P * nl * K / dt, 1),
+                   "accept_rate": round((st["accepted"] - st0["accepted"]) / max(1, (st["steps"] - st0["steps"]) * P), 4),
+                   "min_ess": round(min_ess, 1), "min_ess_per_s": round(min_ess / dt, 2), "ess_plateau": plateau}
+            if use:
+                ds = s.da_stats()
+                tested = ds["stage1_tested"] - d0["stage1_tested"]
+                row["da"] = {"hidden": h, "trainings": ds["trainings"], "last_rmse_nats": round(ds["last_rmse"], 3),
+                             "active_at_end": ds["active"],
+                             "stage1_pass_rate": round((ds["stage1_passed"] - d0["stage1_passed"]) / tested, 4) if tested else None,
+                             "exact_evals_per_chain_step": round((ds["exact_evals"] - d0["exact_evals"]) / (K * nl * P), 4)}
+            s.close()
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "delayed acceptance on an expensive exact target: ms per interval and min-ESS/s with and "
+                                "without the surrogate screen",
+                      "config": {"workload": "tanh regression, map carried off (a d_y x d product per exact evaluation), "
+                                             "P=256, n_lag=64, BF16, refresh every interval, rmse_bound 0.5",
+                                 "warmup_intervals": args.dag_warmup, "timed_intervals": args.dag_steps},
                       "rows": rows}), flush=True)
 
 
@@ -606,6 +673,9 @@ def main():
         return
     if args.multi:
         multi(args)
+        return
+    if args.da_gain:
+        da_gain(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

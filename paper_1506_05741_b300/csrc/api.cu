@@ -1230,7 +1230,7 @@ static diam_status alloc_all(diam_ctx* c) {
     CKS(dalloc(c, &c->lpart, sizeof(double) * (size_t)c->nchunk * P));
     CKS(dalloc(c, &c->accf, (size_t)P));
     CKS(dalloc(c, &c->s16, sizeof(double) * d));
-    if (c->bf && c->dy > 0) {
+    if (c->bf && c->dy > 0 && (c->kind == TK_DENSE || c->kind == TK_TANH)) {
         // split of the target product's K (the autotuner picks it with the tile width): room for 8 planes
         int tiles = ((c->dy + 127) / 128) * ((P + 127) / 128);
         c->tsplit = std::max(1, std::min(8, 148 / std::max(tiles, 1)));
@@ -1442,6 +1442,9 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
                       const double* xref0, void* stream, diam_ctx** out) {
     if (!cfg || !tg || !out) return DIAM_EINVAL;
     *out = nullptr;
+    // an error that an earlier, failed call left in this thread's CUDA error state (a rejected launch or argument;
+    // not a sticky device fault, which every call below would report again) is not this context's
+    (void)cudaGetLastError();
     if (cfg->d <= 0 || cfg->P <= 0 || cfg->n_lag <= 0 || !(cfg->infl > 0) || !(cfg->beta0 > 0 && cfg->beta0 < 1) ||
         cfg->refresh_delay < 0 || cfg->refresh_delay > 8 || (cfg->prec != DIAM_FP64 && cfg->prec != DIAM_BF16) ||
         tg->kind < 0 || tg->kind > DIAM_T_TWISTED || (tg->kind == DIAM_T_CALLBACK && !tg->fn) ||

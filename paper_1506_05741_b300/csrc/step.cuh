@@ -501,13 +501,14 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
 // 1e-3 nats). The same quantity in exact arithmetic. log u < log a is decided as in FP64: the FP32 log of u
 // (within 1e-5 of log u: u's rounding to FP32 and a few ulps of logf, |log u| <= 37) decides unless log a lies
 // within 1e-4 of it; then the FP64 log does. Writes the trace entry of (t, p) when it is kept.
-__device__ __forceinline__ int rec_test(float sq, float sl, float sm, float dsq, float dsl, float dsm, double inv_infl2,
+__device__ __forceinline__ int rec_test(float sm, float dsq, float dsl, float dsm, double inv_infl2, double lpc,
                                         double qc, double u, float lu32, long long t, int p, int P, const TraceDev& tr,
                                         double& lmap, double& lpp, double& qpp, bool& finite) {
     lmap = (double)sm;
-    lpp = (double)sl + lmap;
-    qpp = 0.5 * (double)sq * inv_infl2;
-    const double loga = ((double)dsl + (double)dsm) + 0.5 * (double)dsq * inv_infl2;
+    const double dlp = (double)dsl + (double)dsm, dq = 0.5 * (double)dsq * inv_infl2;
+    lpp = lpc + dlp;   // the proposal's values carried from the current state's by the differences
+    qpp = qc + dq;
+    const double loga = dlp + dq;
     finite = isfinite(lpp) && isfinite(qpp) && isfinite(loga);
     const double l32 = (double)lu32;
     int a = 0;
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     static_assert(!STAGE || VEC, "staging reads 16-byte vectors");
     constexpr int FT = FUSED_THREADS;
     extern __shared__ float4 stage_smem[];   // STAGE: x, z, xi of the chain (d floats each)
-    __shared__ float red[6][FT / 32];
+    __shared__ float red[4][FT / 32];
     __shared__ double s_u, s_lpc, s_qc;
     __shared__ float s_lu32;
     __shared__ int s_acc;
@@ -597,7 +598,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
         s_lpc = lp[p];
         s_qc = q[p];
     }
-    float qf = 0.f, lf = 0.f, mf = 0.f, dqf = 0.f, dlf = 0.f, dmf = 0.f;   // absolute sums; differences (rec_test)
+    // differences of q, of the prior terms and of the map terms (rec_test); the map terms of x* themselves only
+    // for the surrogate's ring
+    float mf = 0.f, dqf = 0.f, dlf = 0.f, dmf = 0.f;
+    const bool want_map = ring_x != nullptr;
     // the map of x* and its likelihood terms first (they need none of the chain's d-vectors)
     float uv[4 * NM];
     const float* ax = Ax + (size_t)p * dy;
@@ -606,11 +610,13 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     auto map_term = [&](float u, float uc, float yv) {
         if (tanh_mode) {
             const float tn = tanhf(u), tc = tanhf(uc);
-            const float r = yv - tn;
-            mf -= r * r * inv2s2;
+            if (want_map) {
+                const float r = yv - tn;
+                mf -= r * r * inv2s2;
+            }
             dmf -= (tc - tn) * (2.f * yv - tn - tc) * inv2s2;
         } else {
-            mf -= 0.5f * u * u;
+            if (want_map) mf -= 0.5f * u * u;
             dmf -= 0.5f * (u - uc) * (u + uc);
         }
     };
@@ -684,12 +690,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                 for (int j = 0; j < 4; ++j) {
                     const float xv = xs[4 * g + j] = r4[j] + mul_f2(rho, x4[j] - r4[j], i4[j]);
                     const float zs = mul_f2(rho, z4[j], mul_f2(ba, w4[j], 0.f));
-                    qf += zs * zs;
                     dqf += (zs - z4[j]) * (zs + z4[j]);
-                    if (prior) {
-                        lf -= 0.5f * xv * xv * tg.inv_lam32[i + j];
-                        dlf -= 0.5f * (xv - x4[j]) * (xv + x4[j]) * tg.inv_lam32[i + j];
-                    }
+                    if (prior) dlf -= 0.5f * (xv - x4[j]) * (xv + x4[j]) * tg.inv_lam32[i + j];
                 }
             }
         } else {
@@ -700,41 +702,33 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
                     const float xr = xref[i], xc = x[i], zc = z[i];
                     const float xv = xs[4 * g + j] = xr + mul_f2(rho, xc - xr, xi[i]);
                     const float zs = mul_f2(rho, zc, mul_f2(ba, bf16_bits_to_f32(w[i]), 0.f));
-                    qf += zs * zs;
                     dqf += (zs - zc) * (zs + zc);
-                    if (prior) {
-                        lf -= 0.5f * xv * xv * tg.inv_lam32[i];
-                        dlf -= 0.5f * (xv - xc) * (xv + xc) * tg.inv_lam32[i];
-                    }
+                    if (prior) dlf -= 0.5f * (xv - xc) * (xv + xc) * tg.inv_lam32[i];
                 }
             }
         }
     }
-    // the six sums over the block, then the test (Algorithm 1) in thread 0
-    qf = warp_sum(qf);
-    lf = warp_sum(lf);
+    // the four sums over the block, then the test (Algorithm 1) in thread 0
     mf = warp_sum(mf);
     dqf = warp_sum(dqf);
     dlf = warp_sum(dlf);
     dmf = warp_sum(dmf);
     if (lane == 0) {
-        red[0][wid] = qf;
-        red[1][wid] = lf;
-        red[2][wid] = mf;
-        red[3][wid] = dqf;
-        red[4][wid] = dlf;
-        red[5][wid] = dmf;
+        red[0][wid] = mf;
+        red[1][wid] = dqf;
+        red[2][wid] = dlf;
+        red[3][wid] = dmf;
     }
     __syncthreads();
     if (wid == 0) {
-        float sum6[6];
+        float sum4[4];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) sum6[k] = warp_sum(lane < FT / 32 ? red[k][lane] : 0.f);
+        for (int k = 0; k < 4; ++k) sum4[k] = warp_sum(lane < FT / 32 ? red[k][lane] : 0.f);
         if (lane == 0) {
             double lmap, lpp, qpp;
             bool finite;
-            const int a = rec_test(sum6[0], sum6[1], sum6[2], sum6[3], sum6[4], sum6[5], inv_infl2, s_qc, s_u, s_lu32, t, p,
-                                   P, tr, lmap, lpp, qpp, finite);
+            const int a = rec_test(sum4[0], sum4[1], sum4[2], sum4[3], inv_infl2, s_lpc, s_qc, s_u, s_lu32, t, p, P, tr,
+                                   lmap, lpp, qpp, finite);
             if (a) {
                 lp[p] = lpp;
                 q[p] = qpp;
@@ -865,7 +859,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
     int pf_l2) {
     constexpr int FT = FUSED_THREADS;
     extern __shared__ float4 ival_smem[];
-    __shared__ float red[6][FT / 32];
+    __shared__ float red[4][FT / 32];
     __shared__ double s_u;
     __shared__ float s_lu32;
     __shared__ int s_acc;
@@ -914,14 +908,17 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
         a_last = 0;
     }
     // u = (A x*)_m; uc = (A x)_m and tc = tanh(uc) of the current state: the term of x* and its difference
-    auto map_term = [&](float u, float uc, float tc, float yv, float& mf, float& dmf) {
+    const bool want_map = ring_x != nullptr;   // the map terms of x* themselves: only for the surrogate's ring
+    auto map_term = [&](float u, float uc, float tc, float yv, float& tn, float& mf, float& dmf) {
         if (tanh_mode) {
-            const float tn = tanhf(u);
-            const float r = yv - tn;
-            mf -= r * r * inv2s2;
+            tn = tanhf(u);
+            if (want_map) {
+                const float r = yv - tn;
+                mf -= r * r * inv2s2;
+            }
             dmf -= (tc - tn) * (2.f * yv - tn - tc) * inv2s2;
         } else {
-            mf -= 0.5f * u * u;
+            if (want_map) mf -= 0.5f * u * u;
             dmf -= 0.5f * (u - uc) * (u + uc);
         }
     };
@@ -943,8 +940,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
             l2_prefetch(W + rn * ldw, (uint32_t)ldw * 2u);
             l2_prefetch(AXi + rn * dy, (uint32_t)dy * 4u);
         }
-        float qf = 0.f, lf = 0.f, mf = 0.f, dqf = 0.f, dlf = 0.f, dmf = 0.f;   // absolute sums; differences
-        float uv[4 * NM];
+        float mf = 0.f, dqf = 0.f, dlf = 0.f, dmf = 0.f;   // the map terms of x* (ring only); differences
+        float uv[4 * NM], tnv[4 * NM];   // u = (A x*)_m and, tanh mode, tanh(u) (kept for an accepted step)
 #pragma unroll
         for (int g = 0; g < NM; ++g) {
             const int m = idx(g);
@@ -958,10 +955,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
                 uv[4 * g + 1] = mul_f2(rho, a4.y, fmaf(om, r4.y, i4.y));
                 uv[4 * g + 2] = mul_f2(rho, a4.z, fmaf(om, r4.z, i4.z));
                 uv[4 * g + 3] = mul_f2(rho, a4.w, fmaf(om, r4.w, i4.w));
-                map_term(uv[4 * g], a4.x, t4.x, y4.x, mf, dmf);
-                map_term(uv[4 * g + 1], a4.y, t4.y, y4.y, mf, dmf);
-                map_term(uv[4 * g + 2], a4.z, t4.z, y4.z, mf, dmf);
-                map_term(uv[4 * g + 3], a4.w, t4.w, y4.w, mf, dmf);
+                map_term(uv[4 * g], a4.x, t4.x, y4.x, tnv[4 * g], mf, dmf);
+                map_term(uv[4 * g + 1], a4.y, t4.y, y4.y, tnv[4 * g + 1], mf, dmf);
+                map_term(uv[4 * g + 2], a4.z, t4.z, y4.z, tnv[4 * g + 2], mf, dmf);
+                map_term(uv[4 * g + 3], a4.w, t4.w, y4.w, tnv[4 * g + 3], mf, dmf);
             }
         }
         float xs[4 * NV];
@@ -985,39 +982,31 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
                 for (int j = 0; j < 4; ++j) {
                     const float xv = xs[4 * g + j] = r4[j] + mul_f2(rho, x4[j] - r4[j], i4[j]);
                     const float zs = mul_f2(rho, z4[j], mul_f2(ba, w4[j], 0.f));
-                    qf += zs * zs;
                     dqf += (zs - z4[j]) * (zs + z4[j]);
-                    if (prior) {
-                        lf -= 0.5f * xv * xv * tg.inv_lam32[i + j];
-                        dlf -= 0.5f * (xv - x4[j]) * (xv + x4[j]) * tg.inv_lam32[i + j];
-                    }
+                    if (prior) dlf -= 0.5f * (xv - x4[j]) * (xv + x4[j]) * tg.inv_lam32[i + j];
                 }
             }
         }
-        qf = warp_sum(qf);
-        lf = warp_sum(lf);
         mf = warp_sum(mf);
         dqf = warp_sum(dqf);
         dlf = warp_sum(dlf);
         dmf = warp_sum(dmf);
         if (lane == 0) {
-            red[0][wid] = qf;
-            red[1][wid] = lf;
-            red[2][wid] = mf;
-            red[3][wid] = dqf;
-            red[4][wid] = dlf;
-            red[5][wid] = dmf;
+            red[0][wid] = mf;
+            red[1][wid] = dqf;
+            red[2][wid] = dlf;
+            red[3][wid] = dmf;
         }
         __syncthreads();
         if (wid == 0) {
-            float sum6[6];
+            float sum4[4];
 #pragma unroll
-            for (int k2 = 0; k2 < 6; ++k2) sum6[k2] = warp_sum(lane < FT / 32 ? red[k2][lane] : 0.f);
+            for (int k2 = 0; k2 < 4; ++k2) sum4[k2] = warp_sum(lane < FT / 32 ? red[k2][lane] : 0.f);
             if (lane == 0) {
                 double lmap, lpp, qpp;
                 bool finite;
-                const int a = rec_test(sum6[0], sum6[1], sum6[2], sum6[3], sum6[4], sum6[5], inv_infl2, qc, s_u, s_lu32, t,
-                                       p, P, tr, lmap, lpp, qpp, finite);
+                const int a = rec_test(sum4[0], sum4[1], sum4[2], sum4[3], inv_infl2, lpc, qc, s_u, s_lu32, t, p, P, tr,
+                                       lmap, lpp, qpp, finite);
                 if (a) {
                     lpc = lpp;
                     qc = qpp;
@@ -1074,8 +1063,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
                 if (m < dy) {
                     *reinterpret_cast<float4*>(su + m) = make_float4(uv[4 * g], uv[4 * g + 1], uv[4 * g + 2], uv[4 * g + 3]);
                     if (tanh_mode)
-                        *reinterpret_cast<float4*>(st + m) = make_float4(tanhf(uv[4 * g]), tanhf(uv[4 * g + 1]),
-                                                                         tanhf(uv[4 * g + 2]), tanhf(uv[4 * g + 3]));
+                        *reinterpret_cast<float4*>(st + m) = make_float4(tnv[4 * g], tnv[4 * g + 1], tnv[4 * g + 2],
+                                                                         tnv[4 * g + 3]);
                 }
             }
         }
