@@ -90,8 +90,8 @@ def parse():
                     help="instead of the throughput bench: delayed acceptance with and without the surrogate on the tanh "
                          "regression with an expensive exact target (map carried off), over d")
     ap.add_argument("--dag-ds", default="256,512,1024,2048,4096")
-    ap.add_argument("--dag-warmup", type=int, default=60)
-    ap.add_argument("--dag-steps", type=int, default=40)
+    ap.add_argument("--dag-warmup", type=int, default=50)
+    ap.add_argument("--dag-steps", type=int, default=48)
     ap.add_argument("--multi-n", type=int, default=64)
     ap.add_argument("--multi-warmup", type=int, default=48,
                     help="warm-up intervals of --multi: from x_0 = 0 and A_0 = Id the step size must first adapt down "
@@ -238,9 +238,10 @@ def da_gain(args):
     (carry_map 0), so every exact log-density is a d_y x d product per chain-step on the tensor cores, against the
     screen's 2 (d h + h^2) (h = the hidden width). For each d in --dag-ds (d_y = d / 2, prior N(0, diag(i^-2)),
     P = 256 chains, n_lag = 64, BF16 mode, refresh every interval), the same chains from the same start with and
-    without the surrogate: --dag-warmup intervals (the surrogate trains after each synchronisation of M = 2
-    intervals once 4 intervals of pairs are in, with the real 0.5-nat gate), then --dag-steps timed intervals and
-    the ESS over them. Per d: device ms per interval, acceptance, min-ESS/s, and the screen's state (trainings,
+    without the surrogate: --dag-warmup intervals of burn-in (the surrogate trained every 2 intervals once 4 intervals
+    of pairs are in), then --dag-steps timed intervals and the ESS over them, in which it retrains on its own
+    schedule (every 20 synchronisations of M = 2 intervals) with the real 0.5-nat gate deciding whether stage 1
+    runs. Per d: device ms per interval, acceptance, min-ESS/s, and the screen's state (trainings,
     held-out RMSE, active, stage-1 pass rate, exact evaluations per chain-step). One JSON line."""
     import torch
     import paper_1506_05741_b300 as dm
@@ -260,10 +261,17 @@ def da_gain(args):
             cfg["keep_block_sums"] = 1
             s = dm.Sampler(cfg, ts, x0=x0, C0=C0, stream=stream.cuda_stream)
             if use:
-                dc = dm.da_default_config(h1=h, h2=h, retrain_every=1, first_train_min=4 * P * nl)
+                dc = dm.da_default_config(h1=h, h2=h, first_train_min=4 * P * nl)
                 s.da_enable(dc, workloads.mlp_init(d, h, h, seed=11))
             W, K = args.dag_warmup, args.dag_steps
-            s.run(W * nl)
+            if use:   # burn-in: 4 intervals of pairs, then a training every 2 intervals (diam_da_train)
+                s.run(4 * nl)
+                for _ in range((W - 4) // 2):
+                    s.da_train()
+                    s.run(2 * nl)
+                s.run(((W - 4) % 2) * nl)
+            else:
+                s.run(W * nl)
             mom0 = s.export_moments()
             st0 = s.stats()
             d0 = s.da_stats() if use else None

@@ -36,9 +36,6 @@ DIAM_API diam_status diam_op_cholesky_f64(int32_t n, double* A, int32_t lda, int
  * splitting of Ozaki, Ogita, Oishi and Rump (2012): each 64-wide panel row is cut into 7 BF16 integer
  * slices under a power-of-two scale, slice products are summed exactly in FP32 tensor memory, grouped by
  * weight and combined as 64-bit integers (the dropped terms are of the size of an FP64 GEMM's rounding).
- * The 64 x 64 diagonal blocks are factored in double-float arithmetic (pairs of floats, unit roundoff about
- * 2^-48: B300 runs dependent FP64 operations at about 64 cycles each, and the chain of diagonal blocks sets the
- * pace), so the factor is accurate to a few units of 2^-48 rather than of 2^-53.
  * This is the factorisation the BF16 sampler mode uses for its refresh: the chain of 64 x 64 diagonal
  * blocks, the rest of each panel and the trailing updates run on three streams of its own, ordered after
  * the work already on `stream` and joined back to it. Allocates its workspace (the panels' slices, about

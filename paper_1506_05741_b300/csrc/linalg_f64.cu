@@ -172,137 +172,6 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(double* __restr
     if (pre && tid < nb) A[(size_t)(k0 + tid) * lda + k0 + nb] = dinv[tid];
 }
 
-// ---------------------------------------------------------------------------------------------------------------
-// The diagonal block in double-float arithmetic, for the tensor-core factorisation. On B300 a dependent FP64
-// instruction costs about 64 cycles and one SM retires about two FP64 fused multiply-adds per cycle, so the FP64
-// diagonal block above (one SM, 64 pivots in sequence) is bound by both; it sets the pace of the whole
-// factorisation. Here each value is an unevaluated sum of two floats (hi + lo, unit roundoff about 2^-48), and every
-// operation is built from FP32 ones with the classical error-free transformations -- Knuth's two-sum, Dekker's
-// fast two-sum (|a| >= |b|) and the product's exact error from one fused multiply-add -- so the pivot chain runs
-// at FP32 latency and the updates at the FP32 rate. The block is scaled by a power of four first (exact), so that
-// its entries, bounded by its largest diagonal entry, sit well inside the FP32 range. Output as chol_diag_kernel's:
-// L in the lower part (hi + lo is exact in FP64), and with pre, U^T and 1 / L_jj.
-struct DF {
-    float hi, lo;
-};
-
-__device__ __forceinline__ DF df_fast2(float a, float b) {   // |a| >= |b| (or a == 0)
-    const float s = a + b;
-    return DF{s, b - (s - a)};
-}
-
-__device__ __forceinline__ DF df_add(DF x, DF y) {
-    const float s = x.hi + y.hi;
-    const float bb = s - x.hi;
-    const float e = (x.hi - (s - bb)) + (y.hi - bb);   // two-sum: x.hi + y.hi = s + e exactly
-    return df_fast2(s, e + (x.lo + y.lo));
-}
-
-__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
-
-__device__ __forceinline__ DF df_mul(DF x, DF y) {
-    const float p = x.hi * y.hi;
-    float e = fmaf(x.hi, y.hi, -p);   // x.hi y.hi = p + e exactly
-    e = fmaf(x.hi, y.lo, e);
-    e = fmaf(x.lo, y.hi, e);
-    return df_fast2(p, e);
-}
-
-// sqrt(a), a > 0: s = sqrtf(a.hi), then one Newton correction from the exact residual a - s^2
-__device__ __forceinline__ DF df_sqrt(DF a) {
-    const float s = sqrtf(a.hi);
-    const float p = s * s;
-    const float pe = fmaf(s, s, -p);
-    const float r = ((a.hi - p) - pe) + a.lo;   // a.hi - p is exact (Sterbenz: p within a factor 2 of a.hi)
-    return df_fast2(s, r / (2.f * s));
-}
-
-// 1 / b, b > 0: q = 1 / b.hi rounded, then one Newton correction q (1 - b q) from the exact residual
-__device__ __forceinline__ DF df_recip(DF b) {
-    const float q = __frcp_rn(b.hi);
-    const float p = b.hi * q;
-    const float pe = fmaf(b.hi, q, -p);
-    const float r = ((1.f - p) - pe) - b.lo * q;   // 1 - p is exact (p within a factor 2 of 1)
-    return df_fast2(q, q * r);
-}
-
-__device__ __forceinline__ DF df_from(double v) {
-    const float h = __double2float_rn(v);
-    return DF{h, __double2float_rn(v - (double)h)};
-}
-
-__device__ __forceinline__ double df_to(DF x) { return (double)x.hi + (double)x.lo; }
-
-constexpr int DFD_THREADS = 256;
-
-__global__ void __launch_bounds__(DFD_THREADS) chol_diag_df_kernel(double* __restrict__ A, int lda, int k0, int nb,
-                                                                   int* info, int pre) {
-    __shared__ DF a[CH_NB][CH_NB + 1];
-    __shared__ DF inv[CH_NB];   // 1 / L_jj (scaled)
-    __shared__ int kexp;
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    if (w == 0) {   // the largest diagonal entry sets the scale 4^k
-        double m = 0.0;
-        for (int i = lane; i < nb; i += 32) m = fmax(m, A[(size_t)(k0 + i) * lda + k0 + i]);
-        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) {
-            int e = 0;
-            if (m > 0.0 && m < 1e300) frexp(m, &e);
-            kexp = e / 2;   // entries / 4^k <= 2
-        }
-    }
-    __syncthreads();
-    const int k = kexp;
-    const double sc = ldexp(1.0, -2 * k);
-    for (int idx = tid; idx < nb * nb; idx += DFD_THREADS) {
-        const int i = idx / nb, l = idx - i * nb;
-        a[i][l] = (l <= i) ? df_from(A[(size_t)(k0 + i) * lda + k0 + l] * sc) : DF{0.f, 0.f};
-    }
-    __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-        if (w == 0) {   // pivot j: L_jj = sqrt(a_jj), column j scaled by 1 / L_jj
-            DF ljj, r;
-            const DF d = a[j][j];
-            if (d.hi > 0.f && d.hi < 3.0e38f) {
-                ljj = df_sqrt(d);
-                r = df_recip(ljj);
-            } else {   // not positive definite: NaN propagates and the caller discards the factor
-                ljj = r = DF{__int_as_float(0x7fc00000), 0.f};
-                if (lane == 0 && info) atomicCAS(info, 0, k0 + j + 1);
-            }
-            for (int i = j + 1 + lane; i < nb; i += 32) a[i][j] = df_mul(a[i][j], r);
-            if (lane == 0) {
-                a[j][j] = ljj;
-                inv[j] = r;
-            }
-        }
-        __syncthreads();
-        // the trailing lower triangle of the block: a_il -= L_ij L_lj, j < l <= i (a row per warp, its columns
-        // over the lanes)
-        for (int i = j + 1 + w; i < nb; i += DFD_THREADS / 32) {
-            const DF lij = a[i][j];
-            for (int l = j + 1 + lane; l <= i; l += 32) a[i][l] = df_add(a[i][l], df_neg(df_mul(lij, a[l][j])));
-        }
-        __syncthreads();
-    }
-    const float up = ldexpf(1.f, k), dn = ldexpf(1.f, -k);   // L = 2^k L_s, 1 / L_jj = 2^-k / L_s,jj
-    for (int idx = tid; idx < nb * nb; idx += DFD_THREADS) {
-        const int i = idx / nb, l = idx - i * nb;
-        double v = 0.0;
-        if (l <= i) {
-            const DF x = a[i][l];
-            v = df_to(DF{x.hi * up, x.lo * up});
-        } else if (pre) {
-            v = df_to(df_mul(a[l][i], inv[i]));   // U_li = L_li / L_ii (scale-free), at (i, l)
-        }
-        A[(size_t)(k0 + i) * lda + k0 + l] = v;
-    }
-    if (pre && tid < nb) {
-        const DF r = inv[tid];
-        A[(size_t)(k0 + tid) * lda + k0 + nb] = df_to(DF{r.hi * dn, r.lo * dn});
-    }
-}
-
 // For each of nrows rows r: solve L y = b in place, b = B[r*ldb + 0 .. nb), L the nb x nb lower triangle
 // at Lkk (row stride ldl). With L = U D (U unit lower, D = diag L): U w = b by forward substitution, then
 // y = D^{-1} w. One warp per row; lane l holds entries l and l + 32.
@@ -428,7 +297,7 @@ static cudaError_t cholesky_ozaki(double* A, int n, int lda, int* info_dev, cuda
     bool rest_pending = false, mid_pending = false;
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         int nb = min(CH_NB, n - k0);
-        { chol_diag_df_kernel<<<1, DFD_THREADS, 0, hi>>>(A, lda, k0, nb, info_dev, k0 + nb < n); count_launch(); }
+        { chol_diag_kernel<<<1, DIAG_THREADS, 0, hi>>>(A, lda, k0, nb, info_dev, k0 + nb < n); count_launch(); }
         int k1 = k0 + nb, rest = n - k1;
         if (rest <= 0) break;
         double* T = A + (size_t)k1 * lda + k1;          // trailing block
