@@ -97,6 +97,8 @@ def parse():
                     help="warm-up intervals of --multi: from x_0 = 0 and A_0 = Id the step size must first adapt down "
                          "(about 30 intervals) before moves are accepted and the refreshes start")
     ap.add_argument("--multi-steps", type=int, default=16, help="timed intervals of --multi")
+    ap.add_argument("--multi-delay", type=int, default=2,
+                    help="refresh_delay of every problem (as the headline: each factorisation beside the next intervals)")
     return ap.parse_args()
 
 
@@ -104,7 +106,7 @@ def multi(args):
     """The uneven batch: 64 independent problems, d_j = round(exp(U(ln 256, ln 8192))) (seed 7), even j the dense
     Gaussian Sigma = Q diag(1/i) Q^T (Q from QR of a seeded N(0,1) matrix, seed 7000 + j), odd j the banana with
     lambda_i = 1/i; each P = 32 chains, n_lag = 64, BF16 mode, x_0 = 0, A_0 = Id, refresh every interval (once
-    d + 1 moves are accepted), run together through diam_multi_run. --multi-warmup intervals (the step size adapts
+    d + 1 moves are accepted; refresh_delay --multi-delay), run together through diam_multi_run. --multi-warmup intervals (the step size adapts
     down first), then --multi-steps timed (wall clock with the device synchronised on both sides, the problems'
     streams run concurrently); aggregate chain-steps/s = sum_j P n_lag K / time; per problem the acceptance rate
     and refreshes of the timed window. One JSON line."""
@@ -114,7 +116,8 @@ def multi(args):
     t0 = time.time()
     specs = workloads.multi64(args.multi_n, with_cov=False)
     gen_s = time.time() - t0
-    cfgs = [dm.default_config(r.target.d, r.P, n_lag=r.n_lag, beta0=r.beta0, seed=r.seed, problem_id=j, prec=dm.BF16)
+    cfgs = [dm.default_config(r.target.d, r.P, n_lag=r.n_lag, beta0=r.beta0, seed=r.seed, problem_id=j, prec=dm.BF16,
+                              refresh_delay=args.multi_delay)
             for j, r in enumerate(specs)]
     t1 = time.time()
     m = dm.MultiSampler(cfgs, [r.target for r in specs])
@@ -141,7 +144,8 @@ def multi(args):
                       "unit": "chain-steps/s", "timed_intervals": args.multi_steps, "warmup_intervals": args.multi_warmup,
                       "seconds": round(dt, 3), "ms_per_interval": round(dt / args.multi_steps * 1e3, 2),
                       "config": {"workload": f"multi{len(specs)}: d log-uniform in [256, 8192] (seed 7), even j dense "
-                                             f"Gaussian, odd j banana, P=32, n_lag=64, BF16, refresh every interval",
+                                             f"Gaussian, odd j banana, P=32, n_lag=64, BF16, refresh every interval, "
+                                             f"refresh_delay {args.multi_delay}",
                                  "problems": len(specs), "d_min": int(min(ds)), "d_max": int(max(ds)),
                                  "sum_d": int(sum(ds)), "timing": "wall clock, device synchronised on both sides"},
                       "generate_s": round(gen_s, 1), "init_s": round(init_s, 1), "problems": per}), flush=True)
@@ -636,10 +640,10 @@ def roofline(prof, run, ts, pk, pk_src, ring):
 
 # DRAM traffic per launch of tc_gemm_persist_kernel in the benchmark's interval: dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the benchmark itself (one pass per launch), averaged over the
-# noise product (2.468 GB), its map (1.690 GB) and the fold's SYRK (1.274 GB) of two intervals
+# noise product (2.266 GB), its map (1.599 GB) and the fold's SYRK (1.272 GB) of one interval
 # (profiles/tc_gemm_persist_tanh4096.md), with a digest of the kernel's sources when it was taken: reported only
 # while the sources are unchanged.
-GEMM_TRAFFIC = {"bytes": 1810500000, "sources_sha16": "8891ab941cf8b54b"}
+GEMM_TRAFFIC = {"bytes": 1712400000, "sources_sha16": "a6ad2960ae019dc2"}
 
 
 def gemm_traffic(run, ts):

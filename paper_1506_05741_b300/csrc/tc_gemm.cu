@@ -278,6 +278,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1) tc_gemm_persist_kernel(
 
     if (warp == 0) {
         if (lane == 0) {   // TMA producer: a global k-block count across the CTA's tiles
+            // the store products' A operand (the factor, the map: tens of MB, read by every n-column of tiles) is
+            // kept in L2 while B (the interval's noise, hundreds of MB) streams through it
+            const uint64_t pol_a = l2_policy_evict_last();
+            const bool hint_a = epi.mode == TC_STORE;
             int it = 0;
             for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
                 int m0, n0;
@@ -292,7 +296,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1) tc_gemm_persist_kernel(
                     const bool second = kb >= cap;
                     const int ka = second ? kb - cap : kb;
                     mbar_expect_tx(fb, STAGE);
-                    tma_load_2d(smem_u32(st), (second && has_a2) ? &tmA2 : &tmA, fb, ka * TC_BK, m0);
+                    const CUtensorMap* ma = (second && has_a2) ? &tmA2 : &tmA;
+                    if (hint_a) tma_load_2d_hint(smem_u32(st), ma, fb, ka * TC_BK, m0, pol_a);
+                    else tma_load_2d(smem_u32(st), ma, fb, ka * TC_BK, m0);
                     tma_load_2d(smem_u32(st + A_BYTES), (second && has_b2) ? &tmB2 : &tmB, fb, ka * TC_BK, n0);
                 }
             }
