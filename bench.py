@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--mixed-steps", type=int, default=-1, help="timed intervals of the mixed arm (-1: --steps, 0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed intervals of the plain FP64 arm (0: skip)")
     ap.add_argument("--fp64-warmup", type=int, default=-1, help="-1: the headline arm's warm-up (the same burn-in)")
-    ap.add_argument("--ess-intervals", type=int, default=96,
+    ap.add_argument("--ess-intervals", type=int, default=192,
                     help="intervals of the headline arm's ESS window (the timed intervals, continued)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -97,8 +97,9 @@ def parse():
                     help="warm-up intervals of --multi: from x_0 = 0 and A_0 = Id the step size must first adapt down "
                          "(about 30 intervals) before moves are accepted and the refreshes start")
     ap.add_argument("--multi-steps", type=int, default=16, help="timed intervals of --multi")
-    ap.add_argument("--multi-delay", type=int, default=2,
-                    help="refresh_delay of every problem (as the headline: each factorisation beside the next intervals)")
+    ap.add_argument("--multi-delay", type=int, default=0,
+                    help="refresh_delay of every problem (measured: 0 gives 1.16 M chain-steps/s, 2 gives 0.88 M: with "
+                         "64 problems the streams already overlap, and three more per problem only add contention)")
     return ap.parse_args()
 
 

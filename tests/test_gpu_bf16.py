@@ -248,15 +248,18 @@ def test_bf16_reference_gaussian_accepts_almost_every_proposal():
     assert g.stats()["refreshes"] >= 3
 
 
-def test_multi_problem_run_equals_each_problem_alone():
+@pytest.mark.parametrize("delay", [0, 2])
+def test_multi_problem_run_equals_each_problem_alone(delay):
     """Problems of uneven d (dense Gaussians and bananas, BF16 mode) run together; each result equals the
-    same problem run alone, bit for bit."""
+    same problem run alone, bit for bit (refresh_delay 2: each factorisation beside the next intervals, on the
+    problem's own streams, as the benchmark runs them)."""
     import paper_1506_05741_b300 as dm
     ds = [72, 200, 131, 64, 256, 97]
     targets, cfgs = [], []
     for j, d in enumerate(ds):
         targets.append(workloads.dense_gaussian(d, 900 + j) if j % 2 == 0 else workloads.banana(d))
-        cfgs.append(dm.default_config(d, 8, n_lag=16, seed=50 + j, problem_id=j, prec=dm.BF16, min_samples_refresh=40))
+        cfgs.append(dm.default_config(d, 8, n_lag=16, seed=50 + j, problem_id=j, prec=dm.BF16, min_samples_refresh=40,
+                                      refresh_delay=delay))
     m = dm.MultiSampler(cfgs, targets)
     m.run(16 * 4 + 5)
     for j in range(len(ds)):
