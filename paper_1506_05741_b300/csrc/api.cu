@@ -585,10 +585,13 @@ static diam_status ensure_bsum(diam_ctx* c, int64_t blk) {
     return DIAM_OK;
 }
 
-// The whole step in one launch (step_rec_kernel): BF16 mode, the target's map carried through the proposal
-// and no surrogate screen in force, for d, d_y <= 8192.
+// The whole step in one launch (step_rec_kernel): BF16 mode, the target's map carried through the proposal or a
+// target of O(d) terms only (the diagonal Gaussian; the banana in the 16-byte layout, where one thread holds both
+// coordinates of its head), no surrogate screen in force, for d, d_y <= 8192.
 static bool fused_step_fits(const diam_ctx* c) {
-    return c->bf && c->rec && (!c->da || !c->da->active) && c->d <= 4 * 8 * FUSED_THREADS &&
+    const bool vec = (c->d % 4) == 0 && (c->ldw % 4) == 0 && (c->ldh % 4) == 0 && (c->ldk % 4) == 0;
+    const bool od = c->kind == TK_DIAG || (c->kind == TK_BANANA && vec && c->d >= 2);
+    return c->bf && (c->rec || od) && (!c->da || !c->da->active) && c->d <= 4 * 8 * FUSED_THREADS &&
            c->dy <= 4 * 8 * FUSED_THREADS;
 }
 
@@ -1484,7 +1487,7 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
         return DIAM_ECUDA;
     }
     diam_status s = alloc_all(c);
-    if (s == DIAM_OK && c->bf && c->rec) s = fused_step(c, true);
+    if (s == DIAM_OK && fused_step_fits(c)) s = fused_step(c, true);
     if (s == DIAM_OK && interval_kernel_fits(c)) s = interval_steps(c, 0, true);
     if (s == DIAM_OK && c->bf && rewhiten_tc_fits(c->d, c->ldk) && rewhiten_tc_setup(c->d) != cudaSuccess)
         s = fail(c, DIAM_ECUDA, "cudaFuncSetAttribute");

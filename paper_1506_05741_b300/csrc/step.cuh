@@ -501,11 +501,11 @@ __global__ void __launch_bounds__(256) select_kernel(int d, int P, int nl, Ctl* 
 // 1e-3 nats). The same quantity in exact arithmetic. log u < log a is decided as in FP64: the FP32 log of u
 // (within 1e-5 of log u: u's rounding to FP32 and a few ulps of logf, |log u| <= 37) decides unless log a lies
 // within 1e-4 of it; then the FP64 log does. Writes the trace entry of (t, p) when it is kept.
-__device__ __forceinline__ int rec_test(float sm, float dsq, float dsl, float dsm, double inv_infl2, double lpc,
-                                        double qc, double u, float lu32, long long t, int p, int P, const TraceDev& tr,
-                                        double& lmap, double& lpp, double& qpp, bool& finite) {
+__device__ __forceinline__ int rec_test(float sm, float dsq, float dsl, float dsm, double dextra, double inv_infl2,
+                                        double lpc, double qc, double u, float lu32, long long t, int p, int P,
+                                        const TraceDev& tr, double& lmap, double& lpp, double& qpp, bool& finite) {
     lmap = (double)sm;
-    const double dlp = (double)dsl + (double)dsm, dq = 0.5 * (double)dsq * inv_infl2;
+    const double dlp = ((double)dsl + (double)dsm) + dextra, dq = 0.5 * (double)dsq * inv_infl2;
     lpp = lpc + dlp;   // the proposal's values carried from the current state's by the differences
     qpp = qc + dq;
     const double loga = dlp + dq;
@@ -589,7 +589,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
     const float* xsrc = STAGE ? sx : x;
     const float* zsrc = STAGE ? sz : z;
     const float* isrc = STAGE ? sxi : xi;
-    const bool prior = tg.kind == TK_TANH;   // the dense Gaussian's whole density is its map
+    // the O(d) terms: the tanh regression's prior, the diagonal Gaussian, the banana's coordinates past its head
+    // (their 1 / lambda are zero at 0 and 1); the dense Gaussian's whole density is its map
+    const bool prior = tg.kind == TK_TANH || tg.kind == TK_DIAG || tg.kind == TK_BANANA;
     auto idx = [&](int g, int j) { return VEC ? 4 * (tid + g * FT) + j : tid + (4 * g + j) * FT; };
     if (tid == FT - 32) {   // the test's other inputs, off the path of the sums: u, its FP32 log, log pi(x), q(x)
         const double u = uniform53(key, t, (uint32_t)p, TAG_U);
@@ -727,8 +729,12 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
         if (lane == 0) {
             double lmap, lpp, qpp;
             bool finite;
-            const int a = rec_test(sum4[0], sum4[1], sum4[2], sum4[3], inv_infl2, s_lpc, s_qc, s_u, s_lu32, t, p, P, tr,
-                                   lmap, lpp, qpp, finite);
+            // the banana's head (coordinates 0 and 1, both this thread's in the 16-byte layout) in FP64
+            const double dhead = tg.kind == TK_BANANA
+                                     ? banana_head(tg, (double)xs[0], (double)xs[1]) - banana_head(tg, (double)xsrc[0], (double)xsrc[1])
+                                     : 0.0;
+            const int a = rec_test(sum4[0], sum4[1], sum4[2], sum4[3], dhead, inv_infl2, s_lpc, s_qc, s_u, s_lu32, t, p, P,
+                                   tr, lmap, lpp, qpp, finite);
             if (a) {
                 lp[p] = lpp;
                 q[p] = qpp;
@@ -873,7 +879,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
     float* sz = sx + d;
     float* su = sz + d;
     float* st = su + dy;   // tanh of su (tanh mode)
-    const bool prior = tg.kind == TK_TANH;
+    const bool prior = tg.kind == TK_TANH || tg.kind == TK_DIAG || tg.kind == TK_BANANA;   // as step_rec_kernel
     auto idx = [&](int g) { return 4 * (tid + g * FT); };
     // the chain's state: every thread loads (and later stores) only its own entries, so no barrier is needed
 #pragma unroll
@@ -1005,8 +1011,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
             if (lane == 0) {
                 double lmap, lpp, qpp;
                 bool finite;
-                const int a = rec_test(sum4[0], sum4[1], sum4[2], sum4[3], inv_infl2, lpc, qc, s_u, s_lu32, t, p, P, tr,
-                                       lmap, lpp, qpp, finite);
+                const double dhead = tg.kind == TK_BANANA   // the banana's head (coordinates 0 and 1: this thread's)
+                                         ? banana_head(tg, (double)xs[0], (double)xs[1]) - banana_head(tg, (double)sx[0], (double)sx[1])
+                                         : 0.0;
+                const int a = rec_test(sum4[0], sum4[1], sum4[2], sum4[3], dhead, inv_infl2, lpc, qc, s_u, s_lu32, t, p, P,
+                                       tr, lmap, lpp, qpp, finite);
                 if (a) {
                     lpc = lpp;
                     qc = qpp;

@@ -62,12 +62,14 @@ def _bf16_pair(ts, P, steps, **kw):
     return make_pair(ts, P, trace_steps=steps, prec=_o.BF16, **kw)
 
 
-@pytest.mark.parametrize("kind", ["tanh", "dense", "diag", "tanh_vec", "dense_vec", "tanh4096", "twisted"])
+@pytest.mark.parametrize("kind", ["tanh", "dense", "diag", "tanh_vec", "dense_vec", "tanh4096", "twisted", "banana",
+                                  "banana_odd"])
 def test_bf16_steps_match_oracle_bf16_mode(kind):
     """The map-carrying targets run as one fused launch per step: scalar element layout for d or d_y not a
     multiple of 4 (tanh, dense), 16-byte vectors otherwise (tanh_vec, dense_vec, with d past one element
     group per thread), and the chain's rows staged in shared memory by bulk copies (the vector cases; at
-    d = 4096 they fill the 48 KB the kernel is set up for)."""
+    d = 4096 they fill the 48 KB the kernel is set up for). The O(d) targets take the same fused kernels (diag;
+    banana with d a multiple of 4, its head's two coordinates in one thread) or the per-step kernels (banana_odd)."""
     if kind == "tanh":
         ts, P = workloads.tanh_regression(200, 130, 31), 6
     elif kind == "dense":
@@ -80,6 +82,10 @@ def test_bf16_steps_match_oracle_bf16_mode(kind):
         ts, P = workloads.tanh_regression(4096, 2048, 40), 3
     elif kind == "twisted":    # pi_6 of Sec. 3.1: the map through the tensor-core product, the twist in FP64
         ts, P = workloads.paper_targets(128)[6], 5
+    elif kind == "banana":
+        ts, P = workloads.banana(120), 4
+    elif kind == "banana_odd":
+        ts, P = workloads.banana(70), 3
     else:
         ts, P = workloads.diag_gaussian(100), 3
     d = ts.d
