@@ -23,7 +23,7 @@ _lock = threading.Lock()
 _lib = None
 
 # prec codes shared with the C side of the oracle
-FP64, BF16 = 0, 2
+FP64, FP32, BF16 = 0, 1, 2   # FP32: the mixed mode with the factor quantised to TF32 instead of BF16
 # target kinds
 T_DIAG, T_DENSE, T_TANH, T_BANANA, T_REF, T_TWIST = 0, 1, 2, 3, 4, 6
 
@@ -74,6 +74,7 @@ def lib():
                 "orc_normals": (None, [U64, U32, I64, U32, I32, P]),
                 "orc_uniform": (D, [U64, U32, U32, I64, U32]),
                 "orc_round_bf16": (D, [D]),
+                "orc_round_tf32": (D, [D]),
                 "orc_round_f32": (D, [D]),
                 "orc_cholesky": (I32, [I32, P, P]),
                 "orc_forward_sub": (None, [I32, P, P, P]),
@@ -148,6 +149,11 @@ def uniform(seed, problem_id, tag, t, p):
 
 def round_bf16(v):
     f = np.vectorize(lambda z: lib().orc_round_bf16(float(z)), otypes=[np.float64])
+    return f(np.asarray(v, np.float64))
+
+
+def round_tf32(v):
+    f = np.vectorize(lambda z: lib().orc_round_tf32(float(z)), otypes=[np.float64])
     return f(np.asarray(v, np.float64))
 
 

@@ -183,6 +183,24 @@ ORC_EXPORT double orc_round_bf16(double v) {
 
 ORC_EXPORT double orc_round_f32(double v) { return (double)(float)v; }
 
+/* TF32: 10 explicit significand bits (FP32's exponent range), round to nearest, ties to even, from FP64. */
+ORC_EXPORT double orc_round_tf32(double v) {
+    uint64_t bits;
+    memcpy(&bits, &v, 8);
+    if (((bits >> 52) & 0x7FF) == 0x7FF) return v;            /* inf / nan */
+    uint64_t lsb = (bits >> 42) & 1u;
+    bits += ((uint64_t)1 << 41) - 1u + lsb;
+    bits &= ~(((uint64_t)1 << 42) - 1u);
+    double r;
+    memcpy(&r, &bits, 8);
+    return r;
+}
+
+/* The proposal factor's quantisation by precision mode: 0 FP64 (none), 1 TF32, 2 BF16. */
+static double orc_round_factor(int prec, double v) {
+    return prec == 2 ? orc_round_bf16(v) : prec == 1 ? orc_round_tf32(v) : v;
+}
+
 /* ------------------------------------------------------------------------------------------------ */
 /* Dense linear algebra, written as the textbook definitions.                                        */
 /* ------------------------------------------------------------------------------------------------ */
@@ -242,7 +260,8 @@ typedef struct {
     double acc_lo, acc_hi, beta_factor, beta_min, beta_max;
     double eps_jitter;
     int64_t min_samples_refresh;
-    int32_t refresh_delay, prec;        /* prec: 0 = FP64, 2 = BF16-quantised factor, noise and maps */
+    int32_t refresh_delay, prec;        /* prec: 0 = FP64; 2 = BF16-quantised factor, noise and maps; 1 = the
+                                           same with the factor quantised to TF32 instead */
     uint64_t seed;
     uint32_t problem_id;
     int32_t threads;
@@ -265,7 +284,7 @@ typedef struct {
 typedef struct {
     orc_config cfg;
     orc_target tgt;
-    double *lam, *G, *A, *y;            /* owned copies; G, A quantised when prec = BF16 */
+    double *lam, *G, *A, *y;            /* owned copies; G, A quantised to BF16 when prec != FP64 */
     /* chain state */
     double *x, *lp;                     /* P x d, P */
     double beta;
@@ -388,11 +407,11 @@ static double orc_quad(const orc_sampler* s, const double* Lq, const double* xre
 static void orc_set_quantised_factor(orc_sampler* s) {
     int d = s->cfg.d;
     size_t nn = (size_t)d * d;
-    for (size_t i = 0; i < nn; ++i) s->Lq[i] = s->cfg.prec == 2 ? orc_round_bf16(s->L[i]) : s->L[i];
+    for (size_t i = 0; i < nn; ++i) s->Lq[i] = orc_round_factor(s->cfg.prec, s->L[i]);
 }
 
 static void orc_set_xref(orc_sampler* s, const double* m) {
-    for (int i = 0; i < s->cfg.d; ++i) s->xref[i] = s->cfg.prec == 2 ? orc_round_f32(m[i]) : m[i];
+    for (int i = 0; i < s->cfg.d; ++i) s->xref[i] = s->cfg.prec != 0 ? orc_round_f32(m[i]) : m[i];
 }
 
 static void orc_recompute_lp(orc_sampler* s) {
@@ -412,11 +431,11 @@ ORC_EXPORT orc_sampler* orc_new(const orc_config* cfg, const orc_target* tgt, co
     if (tgt->lam) memcpy(s->lam, tgt->lam, sizeof(double) * nlam);
     if (tgt->G) {
         s->G = (double*)malloc(sizeof(double) * (size_t)dy * d);
-        for (size_t i = 0; i < (size_t)dy * d; ++i) s->G[i] = cfg->prec == 2 ? orc_round_bf16(tgt->G[i]) : tgt->G[i];
+        for (size_t i = 0; i < (size_t)dy * d; ++i) s->G[i] = cfg->prec != 0 ? orc_round_bf16(tgt->G[i]) : tgt->G[i];
     }
     if (tgt->A) {
         s->A = (double*)malloc(sizeof(double) * (size_t)dy * d);
-        for (size_t i = 0; i < (size_t)dy * d; ++i) s->A[i] = cfg->prec == 2 ? orc_round_bf16(tgt->A[i]) : tgt->A[i];
+        for (size_t i = 0; i < (size_t)dy * d; ++i) s->A[i] = cfg->prec != 0 ? orc_round_bf16(tgt->A[i]) : tgt->A[i];
     }
     if (tgt->y) {
         s->y = (double*)malloc(sizeof(double) * (size_t)dy);
@@ -552,9 +571,9 @@ static void orc_block_end_r2(orc_sampler* s, int64_t blk) {
                 double* Lp = s->Lp + (size_t)p * nn;
                 double* Lqp = s->Lqp + (size_t)p * nn;
                 memcpy(Lp, L, sizeof(double) * nn);
-                for (size_t k = 0; k < nn; ++k) Lqp[k] = c->prec == 2 ? orc_round_bf16(L[k]) : L[k];
+                for (size_t k = 0; k < nn; ++k) Lqp[k] = orc_round_factor(c->prec, L[k]);
                 if (c->xref_mode == 1 && c->proposal == 0)
-                    for (int i = 0; i < d; ++i) s->xrefp[(size_t)p * d + i] = c->prec == 2 ? orc_round_f32(m[i]) : m[i];
+                    for (int i = 0; i < d; ++i) s->xrefp[(size_t)p * d + i] = c->prec != 0 ? orc_round_f32(m[i]) : m[i];
                 any = 1;
             } else {
                 s->notspd++;
@@ -670,7 +689,7 @@ static void orc_step(orc_sampler* s) {
         const double rho = sqrt(1.0 - beta * beta), ba = beta * c->infl;
         float* Wf = (float*)malloc(sizeof(float) * d);
         orc_normals(c->seed, c->problem_id, t, c->chain0 + (uint32_t)p, d, Wf);
-        for (int i = 0; i < d; ++i) Wd[i] = c->prec == 2 ? orc_round_bf16((double)Wf[i]) : (double)Wf[i];
+        for (int i = 0; i < d; ++i) Wd[i] = c->prec != 0 ? orc_round_bf16((double)Wf[i]) : (double)Wf[i];
         free(Wf);
         const double* x = s->x + (size_t)p * d;
         /* DIAM: x* = x_ref + sqrt(1 - beta^2)(x_n - x_ref) + beta * infl * A_n W_n;  RW: x* = x_n + beta * infl * A_n W_n */

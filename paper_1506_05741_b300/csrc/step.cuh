@@ -541,8 +541,14 @@ __device__ __forceinline__ int rec_test(float sm, float dsq, float dsl, float ds
 // are in flight, and the second pass reads x or z from shared memory. The copy wait is clock-bounded.
 constexpr int FUSED_THREADS = 256;
 
+// Resident blocks per SM the fused kernels are compiled for: four (64 registers a thread) while a chain's vectors
+// fit the small instances; two (128 registers) for the instances with eight element groups per thread (d or d_y
+// past 4096), whose shared memory allows at most two or three blocks per SM anyway and whose register arrays would
+// otherwise spill.
+constexpr int fused_min_blocks(int nv, int nm) { return (nv >= 8 || nm >= 8) ? 2 : 4; }
+
 template <int NV, int NM, bool VEC, bool STAGE = false>
-__global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
+__global__ void __launch_bounds__(FUSED_THREADS, fused_min_blocks(NV, NM)) step_rec_kernel(
     int d, int P, int nl, int dy, Ctl* ctl, Key key, TargetDev tg, double inv_infl2,
     float* __restrict__ X, float* __restrict__ Z, const float* __restrict__ Xi, const uint16_t* __restrict__ W, int ldw,
     const float* __restrict__ xref, float* __restrict__ Ax,
@@ -855,7 +861,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 4) step_rec_kernel(
 // 16-byte aligned): thread 0 asks for the next step's xi, W and A xi rows to be brought into L2 at the start
 // of each step, so the HBM reads of a step overlap the previous step's reductions, test and stores.
 template <int NV, int NM>
-__global__ void __launch_bounds__(FUSED_THREADS, 4) interval_rec_kernel(
+__global__ void __launch_bounds__(FUSED_THREADS, fused_min_blocks(NV, NM)) interval_rec_kernel(
     int d, int P, int nl, int dy, int ns, Ctl* ctl, Key key, TargetDev tg, double inv_infl2,
     float* __restrict__ X, float* __restrict__ Z, const float* __restrict__ Xi, const uint16_t* __restrict__ W, int ldw,
     const float* __restrict__ xref, float* __restrict__ Ax, const float* __restrict__ axref,

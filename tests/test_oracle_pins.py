@@ -87,6 +87,43 @@ def test_bf16_rounding_ties_to_even():
     assert oracle.round_bf16(-3.0) == -3.0
 
 
+def test_tf32_rounding_is_round_to_nearest_even_at_11_significant_bits():
+    """TF32 keeps 11 significant bits: against an independent definition, v = m 2^e with m rounded by Python's
+    round() (ties to even) at 11 bits, on random values and hand-made ties."""
+    import math
+    from fractions import Fraction
+
+    def ref(v):
+        if v == 0.0:
+            return 0.0
+        e = math.frexp(v)[1] - 11          # v = f 2^(e + 11), 0.5 <= |f| < 1: 11 bits of f above 2^e
+        q = round(Fraction(v) / Fraction(2) ** e)
+        return float(q * Fraction(2) ** e)
+
+    rng = np.random.default_rng(3)
+    vals = list(rng.standard_normal(2000) * 10.0 ** rng.uniform(-6, 6, 2000))
+    one, ulp = 1.0, 2.0 ** -10
+    vals += [one + ulp / 2, one + 1.5 * ulp, one + ulp / 2 + 2.0 ** -40, -3.0, -(one + ulp / 2), 1e-30 * (one + ulp / 2)]
+    got = oracle.round_tf32(np.array(vals))
+    assert all(g == ref(v) for g, v in zip(got, vals))
+    assert oracle.round_tf32(one + ulp / 2) == one and oracle.round_tf32(one + 1.5 * ulp) == one + 2 * ulp
+
+
+def test_tf32_factor_mode_quantises_only_the_factor_to_tf32():
+    """prec FP32: the factor rounded to TF32, the noise and the maps to BF16 as in the BF16 mode; the same
+    quantised factor defines the proposal and its density (reference Gaussian: every move accepted)."""
+    d, P = 6, 2
+    T = oracle.Target(oracle.T_REF, d)
+    s = oracle.Sampler(oracle.default_config(d=d, P=P, n_lag=10, beta0=0.4, prec=oracle.FP32, trace_steps=60,
+                                             min_samples_refresh=5), T, x0=workloads.start_state(d, P, 3))
+    s.run(60)
+    L, Lq, xr = s.factor()
+    assert np.array_equal(Lq, oracle.round_tf32(L)) and not np.array_equal(Lq, oracle.round_bf16(L))
+    assert np.array_equal(xr, xr.astype(np.float32).astype(np.float64))
+    tr = s.trace()
+    assert tr["acc"].all() and np.abs(tr["loga"]).max() < 1e-9
+
+
 # ------------------------------------------------------------------ S11: Cholesky and substitution
 @pytest.mark.parametrize("d", [1, 3, 5, 17, 64])
 def test_cholesky_matches_lapack(d):
