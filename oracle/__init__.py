@@ -287,7 +287,7 @@ class Sampler:
         return out
 
     def chain_factor(self, p):
-        """Reading R2: chain p's factor, its quantised form, x_ref and beta."""
+        """Per-chain factors (Sec. 2.4.1): chain p's factor, its quantised form, x_ref and beta."""
         d = self.cfg["d"]
         L = np.zeros((d, d)); Lq = np.zeros((d, d)); xr = np.zeros(d); b = C.c_double()
         lib().orc_get_chain_factor(self._h, int(p), _ptr(L), _ptr(Lq), _ptr(xr), C.byref(b))

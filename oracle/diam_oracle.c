@@ -276,8 +276,8 @@ typedef struct {
                                            adaptive Metropolis (Sec. 2.3.3) when A_n is refreshed */
     int32_t pad2_;
     double eps_jitter_min;              /* floor of the first jitter of the refresh rule */
-    int32_t moments_mode;               /* 0: reading R1, one factor from the moments pooled over all chains;
-                                           1: reading R2, the per-chain factors of Sec. 2.4.1 (refresh_delay 0) */
+    int32_t moments_mode;               /* 0: one factor from the moments pooled over all chains;
+                                           1: the per-chain factors of Sec. 2.4.1 (refresh_delay 0) */
     int32_t pad3_;
 } orc_config;
 
@@ -308,7 +308,7 @@ typedef struct {
     double *blk_beta;
     int64_t nblk_rec;
     double *scratch;                    /* threads x (4 d) */
-    /* reading R2: chain p proposes with its own factor A_n^p, x_ref^p and beta^p, refreshed every interval from
+    /* per-chain factors (Sec. 2.4.1): chain p proposes with its own factor A_n^p, x_ref^p and beta^p, refreshed every interval from
      * its local view of the global moments, eq. (mom2pg), (mom1pg), (cov2pg): the raw sums of the batches merged
      * so far (every chain's samples, eq. (mom2g), (mom1g)) plus chain p's own samples of the current batch */
     double *Lp, *Lqp, *xrefp, *betap;   /* P x d x d, P x d x d, P x d, P */
@@ -529,7 +529,7 @@ static int orc_jittered_cholesky(orc_sampler* s, const double* C, double* L) {
     return ok;
 }
 
-/* Interval end under reading R2 (Sec. 2.4.1): each chain's beta rule on its own acceptance; each chain's factor from
+/* Interval end with per-chain factors (Sec. 2.4.1): each chain's beta rule on its own acceptance; each chain's factor from
  * its local view of the global moments, C^{p,glob} = S^{p,glob} - m^{p,glob} (m^{p,glob})^T, with
  * S^{p,glob} = (sum over the merged batches + chain p's sum over this batch) / (their sample count) -- the
  * weights k M P n_lag and m n_lag of eq. (mom2pg) as counts; after M intervals the batch's samples of every
@@ -682,7 +682,7 @@ static void orc_step(orc_sampler* s) {
         double* work = s->scratch + (size_t)tid * 4 * d;
         double* xp = work + 2 * d;
         double* Wd = work + 3 * d;
-        /* the proposal's factor, x_ref and beta: the pooled ones (R1) or chain p's own (R2) */
+        /* the proposal's factor, x_ref and beta: the pooled ones or chain p's own (Sec. 2.4.1) */
         const double* Lq = r2 ? s->Lqp + (size_t)p * d * d : s->Lq;
         const double* xref = r2 ? s->xrefp + (size_t)p * d : s->xref;
         const double beta = r2 ? s->betap[p] : s->beta;
@@ -786,7 +786,7 @@ ORC_EXPORT void orc_get_factor(const orc_sampler* s, double* L, double* Lq, doub
     if (Lq) memcpy(Lq, s->Lq, sizeof(double) * nn);
     if (xref) memcpy(xref, s->xref, sizeof(double) * s->cfg.d);
 }
-/* Reading R2: chain p's factor in use, its quantised form and x_ref, and its beta. */
+/* Per-chain factors (Sec. 2.4.1): chain p's factor in use, its quantised form and x_ref, and its beta. */
 ORC_EXPORT void orc_get_chain_factor(const orc_sampler* s, int p, double* L, double* Lq, double* xref, double* beta) {
     size_t nn = (size_t)s->cfg.d * s->cfg.d;
     if (!s->Lp || p < 0 || p >= s->cfg.P) return;

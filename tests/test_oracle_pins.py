@@ -457,17 +457,19 @@ def test_fixed_factor_chain_on_twisted_target_matches_closed_form_moments(j):
     assert np.sum(((zv[:, 0] - ts.uvar) / zv[:, 1]) ** 2) < q
 
 
-# ------------------------------------------------------------------ reading R2: per-chain factors (Sec. 2.4.1)
+# ------------------------------------------------------------------ per-chain factors (Sec. 2.4.1)
 def test_per_chain_factors_with_one_chain_are_algorithm_1():
-    """Reading R2 with P = 1: the local view of the global moments (eq. (mom2pg), (mom1pg)) is the running
-    moment of the single chain, so R2 is Algorithm 1 itself: the same decisions, moments and factor as R1."""
+    """Per-chain factors (Sec. 2.4.1) with P = 1: the local view of the global moments (eq. (mom2pg), (mom1pg)) is the running
+    moment of the single chain, so the per-chain form is Algorithm 1 itself: the same decisions, moments and factor
+    as the pooled one."""
     ts = workloads.dense_gaussian(24, 8)
     out = []
     for mode in (0, 1):
         cfg = oracle.default_config(d=24, P=1, n_lag=20, M=3, beta0=0.4, seed=5, min_samples_refresh=30,
                                     eps_jitter=1e-3, trace_steps=401, moments_mode=mode)
         s = oracle.Sampler(cfg, _spec_target(ts), C0=ts.cov)
-        s.run(401)   # one step into interval 20: R1 has applied interval 19's factor (R2 holds it from the end)
+        s.run(401)   # one step into interval 20: the pooled form has applied interval 19's factor (the per-chain form holds it from
+                     # the end)
         L = s.factor()[0] if mode == 0 else s.chain_factor(0)[0]
         out.append((s.trace(), s.moments(), L, s.counts()))
     (ta, (ma, Ca), La, ca), (tb, (mb, Cb), Lb, cb) = out
@@ -477,7 +479,7 @@ def test_per_chain_factors_with_one_chain_are_algorithm_1():
 
 
 def test_per_chain_factor_is_cholesky_of_its_view_of_the_global_moments():
-    """Reading R2 with P = 4, M = 2 intervals per batch: after 5 intervals (two batches merged, one interval into
+    """Per-chain factors (Sec. 2.4.1) with P = 4, M = 2 intervals per batch: after 5 intervals (two batches merged, one interval into
     the third) chain p's factor is the jittered Cholesky (LAPACK) of C^{p,glob} = S^{p,glob} - m m^T built by brute
     force from the recorded states: all chains' samples of the merged batches plus chain p's own samples since
     (eq. (mom2pg), (mom1pg), (cov2pg)); the chains' factors differ."""
@@ -504,11 +506,12 @@ def test_per_chain_factor_is_cholesky_of_its_view_of_the_global_moments():
 
 
 def test_pooled_factor_converges_at_least_as_fast_as_per_chain_factors():
-    """Reading R1 (one factor from the moments of every chain, refreshed every interval) against the paper's
-    per-chain factors (R2, eq. (mom2pg) - (cov2pg), the chains' samples merged every M intervals), same chains and
+    """The pooled factor (one factor from the moments of every chain, refreshed every interval) against the paper's
+    per-chain factors (eq. (mom2pg) - (cov2pg), the chains' samples merged every M intervals), same chains and
     streams: dense Gaussian d = 32, P = 8, n_lag = 16, M = 10, A_0 = Id, over-dispersed starts, 8000 steps. Both
-    converge, and the pooled covariance of R1 is at least as close to Sigma (relative Frobenius norm): under R1
-    every chain's proposal sees every chain's latest samples; under R2 only its own until the next merge."""
+    converge, and the pooled covariance of the pooled form is at least as close to Sigma (relative Frobenius norm):
+    there every chain's proposal sees every chain's latest samples; with per-chain factors only its own until the
+    next merge."""
     d, P, nl, M = 32, 8, 16, 10
     ts = workloads.dense_gaussian(d, 44)
     x0 = workloads.start_state(d, P, 2) * 2.0
