@@ -16,10 +16,11 @@ Arms, same workload and start:
   mixed     the same without the surrogate;
   mixed_da_delay1    the headline arm with refresh_delay 1 (one factorisation beside the next interval);
   mixed_da_in_order  the headline arm with refresh_delay 0 (each factor used right after its refresh);
+  mixed_tf32 the mixed arm with the factor quantised to TF32 instead of BF16 (prec FP32, no surrogate);
   fp64      the plain FP64 form (every kernel FP64, DFMA Cholesky).
 Metrics: chain-steps/s = P n_lag / device time of an interval (everything above included), and min-ESS/s =
-min over coordinates of the batch-means effective sample size of the timed window (batches = one interval
-of one chain) / the window's device time.
+min over coordinates of the batch-means effective sample size of the ESS window (batches of b intervals of
+one chain, b doubling while 4 batches per chain remain) / the window's device time.
 
 Prints one JSON line (rank 0). --impl reference times the CPU oracle (the reference arm: a plain FP64 CPU program).
 """
@@ -59,6 +60,8 @@ def parse():
                     help="timed intervals of the headline arm with refresh_delay 0 and 1 (-1: --steps, 0: skip)")
     ap.add_argument("--mixed-steps", type=int, default=-1, help="timed intervals of the mixed arm (-1: --steps, 0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed intervals of the plain FP64 arm (0: skip)")
+    ap.add_argument("--tf32-steps", type=int, default=8,
+                    help="timed intervals of the mixed arm with the factor quantised to TF32 (prec FP32; 0: skip)")
     ap.add_argument("--fp64-warmup", type=int, default=-1, help="-1: the headline arm's warm-up (the same burn-in)")
     ap.add_argument("--ess-intervals", type=int, default=192,
                     help="intervals of the headline arm's ESS window (the timed intervals, continued)")
@@ -69,12 +72,12 @@ def parse():
     ap.add_argument("--convergence", action="store_true",
                     help="instead of the throughput bench: samples and device time to convergence on a dense Gaussian "
                          "of known covariance, over n_lag (Sec. 3.3)")
-    ap.add_argument("--conv-ds", default="100,200,400,800", help="dimensions of the n_lag experiment")
+    ap.add_argument("--conv-ds", default="100,200,400", help="dimensions of the n_lag experiment")
     ap.add_argument("--conv-target", default="pi1", choices=["pi1", "dense"])
-    ap.add_argument("--conv-P", type=int, default=16)
+    ap.add_argument("--conv-P", type=int, default=64)
     ap.add_argument("--conv-tol-mean", type=float, default=0.01, help="|m_n - mu|_2 (the n_lag tuning criterion)")
     ap.add_argument("--conv-tol-cov", type=float, default=1e-3, help="|C_n - Sigma|_F / |Sigma|_F")
-    ap.add_argument("--conv-max-s", type=float, default=20.0, help="device seconds per (d, n_lag) row at most")
+    ap.add_argument("--conv-max-s", type=float, default=25.0, help="device seconds per (d, n_lag) row at most")
     ap.add_argument("--compare", action="store_true",
                     help="instead of the throughput bench: integrated autocorrelation times of DIAM, AM, pCN and RW on "
                          "the Gaussian test targets of Sec. 3.1 over d (Sec. 3.2)")
@@ -760,6 +763,9 @@ def main():
                 name = ("mixed_da" if da else "mixed") + suffix
                 arms[name], _, _, _ = run_arm(name, run, ts, x0, C0, dm.BF16, da, args.warmup, isteps, torch, stream,
                                               dm, delay=dly)
+        if args.tf32_steps > 0:   # the mixed mode with the factor quantised to TF32 (prec FP32), no surrogate
+            arms["mixed_tf32"], _, _, _ = run_arm("mixed_tf32", run, ts, x0, C0, dm.FP32, False, args.warmup,
+                                                  args.tf32_steps, torch, stream, dm, delay=args.refresh_delay)
         if args.fp64_steps > 0:
             fw = args.warmup if args.fp64_warmup < 0 else args.fp64_warmup
             arms["fp64"], _, _, _ = run_arm("fp64", run, ts, x0, C0, dm.FP64, False, fw, args.fp64_steps, torch,

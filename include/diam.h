@@ -59,8 +59,11 @@ typedef enum {
  * BF16: the factor A_n, the noise W and the target's linear map are rounded once (to nearest even) to
  * BF16 and those same rounded values define both the proposal and its density; the products run on the
  * tensor cores with FP32 accumulation, chain states are FP32, and the Cholesky refresh and the moment
- * accumulation stay in FP64. */
-typedef enum { DIAM_FP64 = 0, DIAM_BF16 = 2 } diam_prec;
+ * accumulation stay in FP64.
+ * FP32: the BF16 mode with the factor A_n rounded to TF32 instead (11 significant bits: a TF32-representable
+ * factor, exactly the sum of two BF16 values, whose products take a second tensor-core pass); W and the map stay
+ * BF16. The re-solve of z after a factor change is the FP64-accurate triangular solve. */
+typedef enum { DIAM_FP64 = 0, DIAM_FP32 = 1, DIAM_BF16 = 2 } diam_prec;
 
 /* Synthetic targets (log pi up to a constant, eq. (bayes)).
  *  DIAG_GAUSS : -sum_i x_i^2 / (2 lam_i)
@@ -140,7 +143,7 @@ typedef struct {
                                map of an interval's noise is one product at the interval start, O(d_y) per step);
                                0 evaluates A x* for every proposal (a tensor-core product per step) */
     double eps_jitter_min;  /* floor of the refresh rule's first jitter (0: none). The library's default is 0;
-                               BF16-mode callers set it (the tests and the benchmark use 1e-4, reading G8) */
+                               BF16-mode callers set it (the tests and the benchmark use 1e-4: the BF16 records' rounding in C_n defeats smaller loadings) */
     int32_t reserved[2];
 } diam_config;
 

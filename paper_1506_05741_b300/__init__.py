@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-FP64, BF16 = 0, 2
+FP64, FP32, BF16 = 0, 1, 2   # FP32: the BF16 mode with the factor quantised to TF32
 PROP_DIAM, PROP_RW = 0, 1
 T_DIAG, T_DENSE, T_TANH, T_BANANA, T_REF, T_CALLBACK, T_TWIST = 0, 1, 2, 3, 4, 5, 6
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
@@ -141,7 +141,7 @@ def _p(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
-# First jitter of the refresh rule in BF16 mode (reading G8): its C_n comes from the FP32-accumulated
+# First jitter of the refresh rule in BF16 mode (relative diagonal loading): its C_n comes from the FP32-accumulated
 # tensor-core fold, whose noise along near-null directions early in a run is 1e-5 to 1e-4 of the diagonal, so
 # smaller loadings fail and only cost retries. A config value (eps_jitter_min), read by the library and the
 # oracle alike; default_config applies it to BF16 configurations unless the caller gives eps_jitter_min.
@@ -158,7 +158,7 @@ def default_config(d: int, P: int, **kw) -> dict:
         if k not in cfg:
             raise KeyError(k)
         cfg[k] = v
-    if cfg["prec"] == BF16 and "eps_jitter_min" not in kw:
+    if cfg["prec"] in (BF16, FP32) and "eps_jitter_min" not in kw:
         cfg["eps_jitter_min"] = BF16_JITTER_MIN
     return cfg
 

@@ -131,6 +131,8 @@ struct diam_ctx {
     // A x of the states and of the proposals, A x_ref, the interval's products M W (scaled by beta alpha)
     bool rec = false, ax_dirty = true;
     uint16_t *Lt16 = nullptr, *ALh = nullptr, *ALl = nullptr;
+    uint16_t *Lq16lo = nullptr, *Lt16lo = nullptr;   // the TF32 factor's second BF16 term (prec DIAM_FP32)
+    bool tf32 = false;                              // prec DIAM_FP32: the factor quantised to TF32
     float *ALf = nullptr, *AXi = nullptr, *Ax = nullptr, *Axp = nullptr, *axref = nullptr;
     double* lmap = nullptr;
     uint16_t* Gq16 = nullptr;
@@ -392,13 +394,13 @@ template <typename T>
 static diam_status rewhiten(diam_ctx* c) {
     const int d = c->d, P = c->P;
     int e0 = ph_begin(c, PH_REWHITEN);
-    if (c->bf && rewhiten_tc_fits(d, c->ldk)) {   // FP32 forward substitution, panel updates on the tensor cores
+    if (c->bf && !c->tf32 && rewhiten_tc_fits(d, c->ldk)) {   // FP32 forward substitution, panel updates on the tensor cores
         CK(rewhiten_tc(d, P, c->Lq16, c->ldk, (const float*)c->X, (const float*)c->xref, (float*)c->Z, c->q, inv_infl2(c),
                        c->kind == TK_REF ? c->lp : nullptr, &c->ctl->status, c->st));
         ph_end(c, e0);
         return DIAM_OK;
     }
-    if (c->bf && rewhiten32_smem(d, 1) <= 220 * 1024) {   // FP32 forward substitution (reading G20)
+    if (c->bf && !c->tf32 && rewhiten32_smem(d, 1) <= 220 * 1024) {   // FP32 forward substitution (q to about 1e-6 of the FP64 solve)
         const int G = rewhiten32_group(d);
         { rewhiten32_kernel<<<(P + G - 1) / G, RW_THREADS, rewhiten32_smem(d, G), c->st>>>(
               d, P, G, c->Lq16, c->ldk, (const float*)c->X, (const float*)c->xref, (float*)c->Z, c->q, inv_infl2(c),
@@ -439,7 +441,7 @@ static void set_xref_from(diam_ctx* c, const double* src_dev) {
 static diam_status quantise(diam_ctx* c) {
     if (c->bf) {
         { quantise_factor_kernel<<<dim3(blocks_for(c->ldk), c->d), kThreads, 0, c->st>>>(c->d, c->L, c->d, c->Lq64, c->Lq16,
-                                                                                         c->ldk); count_launch(); }
+                                                                                         c->ldk, c->Lq16lo); count_launch(); }
         CK(cudaGetLastError());
     }
     return DIAM_OK;
@@ -455,7 +457,12 @@ static diam_status rec_factor(diam_ctx* c) {
     epi.mode = TC_STORE;
     epi.D = c->ALf;
     epi.ldd = ldk;
-    CK(tc_gemm_bf16(c->d, c->dy, ldk, c->Lt16, ldk, c->Gq16, nullptr, ldk, 0, epi, &c->ctl->status, c->st, 256));
+    if (c->tf32) {   // Lq = hi + lo (TF32): both terms' products, the lo one as a second K pass
+        { transpose_bf16_kernel<<<dim3(ldk / 32, ldk / 32), dim3(32, 8), 0, c->st>>>(c->Lq16lo, ldk, c->d, ldk, c->Lt16lo, ldk); count_launch(); }
+        CK(tc_gemm_bf16_a2(c->d, c->dy, ldk, c->Lt16, c->Lt16lo, ldk, c->Gq16, ldk, 0, epi, &c->ctl->status, c->st, 256));
+    } else {
+        CK(tc_gemm_bf16(c->d, c->dy, ldk, c->Lt16, ldk, c->Gq16, nullptr, ldk, 0, epi, &c->ctl->status, c->st, 256));
+    }
     { split_hi_lo_kernel<<<dim3(blocks_for(ldk), c->dy), kThreads, 0, c->st>>>(c->dy, ldk, ldk, c->ALf, c->ALh, c->ALl); count_launch(); }
     CK(cudaGetLastError());
     return DIAM_OK;
@@ -536,8 +543,12 @@ static diam_status prepare_block(diam_ctx* c, int64_t blk, cudaStream_t st) {
         epi.D = (float*)c->Xi;
         epi.ldd = d;
         epi.scale_dev = &c->ctl->ba;
-        CK(tc_gemm_bf16(d, (int)rows, c->ldk, c->Lq16, c->ldk, (const uint16_t*)c->W, nullptr, c->ldw, 1, epi,
-                        &c->ctl->status, st, c->bn_xi));
+        if (c->tf32)   // the TF32 factor as hi + lo: the lo term's products as a second K pass
+            CK(tc_gemm_bf16_a2(d, (int)rows, c->ldk, c->Lq16, c->Lq16lo, c->ldk, (const uint16_t*)c->W, c->ldw, 1, epi,
+                               &c->ctl->status, st, 256));
+        else
+            CK(tc_gemm_bf16(d, (int)rows, c->ldk, c->Lq16, c->ldk, (const uint16_t*)c->W, nullptr, c->ldw, 1, epi,
+                            &c->ctl->status, st, c->bn_xi));
         if (c->rec) {   // the map of every step's noise product: beta alpha (A Lq) W, in one GEMM
             TcEpi em{};
             em.mode = TC_STORE;
@@ -899,7 +910,7 @@ static diam_status refresh(diam_ctx* c, int64_t blk) {
     const int d = c->d;
     int e0 = ph_begin(c, PH_REFRESH);
     double inv_n = 1.0 / (double)c->n;
-    // the first attempt loads by max(eps_jitter, eps_jitter_min) (relative); the caller's floor (reading G8)
+    // the first attempt loads by max(eps_jitter, eps_jitter_min) (relative); the caller's floor
     double eps = std::max(c->cfg.eps_jitter, c->cfg.eps_jitter_min);
     bool ok = false;
     for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
@@ -1280,6 +1291,7 @@ static diam_status alloc_all(diam_ctx* c) {
         }
         CKS(dalloc(c, &c->Lq64, sizeof(double) * d * d));
         CKS(dalloc(c, &c->Lq16, sizeof(uint16_t) * (size_t)d * c->ldk));
+        if (c->tf32) CKS(dalloc(c, &c->Lq16lo, sizeof(uint16_t) * (size_t)d * c->ldk));
         CKS(dalloc(c, &c->op_hi, sizeof(uint16_t) * (size_t)P * c->ldk));
         CKS(dalloc(c, &c->op_lo, sizeof(uint16_t) * (size_t)P * c->ldk));
         CKS(dalloc(c, &c->op_lo2, sizeof(uint16_t) * (size_t)P * c->ldk));
@@ -1294,6 +1306,7 @@ static diam_status alloc_all(diam_ctx* c) {
             c->rec = true;
             const size_t dy = (size_t)std::max(c->dy, 1);
             CKS(dalloc(c, &c->Lt16, sizeof(uint16_t) * (size_t)c->ldk * c->ldk));
+            if (c->tf32) CKS(dalloc(c, &c->Lt16lo, sizeof(uint16_t) * (size_t)c->ldk * c->ldk));
             CKS(dalloc(c, &c->ALf, sizeof(float) * dy * c->ldk));
             CK(cudaMemsetAsync(c->ALf, 0, sizeof(float) * dy * c->ldk, c->st));   // padding columns stay zero
             CKS(dalloc(c, &c->ALh, sizeof(uint16_t) * dy * c->ldk));
@@ -1449,7 +1462,7 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
     // not a sticky device fault, which every call below would report again) is not this context's
     (void)cudaGetLastError();
     if (cfg->d <= 0 || cfg->P <= 0 || cfg->n_lag <= 0 || !(cfg->infl > 0) || !(cfg->beta0 > 0 && cfg->beta0 < 1) ||
-        cfg->refresh_delay < 0 || cfg->refresh_delay > 8 || (cfg->prec != DIAM_FP64 && cfg->prec != DIAM_BF16) ||
+        cfg->refresh_delay < 0 || cfg->refresh_delay > 8 || (cfg->prec != DIAM_FP64 && cfg->prec != DIAM_BF16 && cfg->prec != DIAM_FP32) ||
         tg->kind < 0 || tg->kind > DIAM_T_TWISTED || (tg->kind == DIAM_T_CALLBACK && !tg->fn) ||
         (int64_t)cfg->n_lag * cfg->P > (1 << 24) || cfg->trace_steps < 0 ||
         (cfg->proposal != DIAM_PROP_DIAM && cfg->proposal != DIAM_PROP_RW) ||
@@ -1464,7 +1477,8 @@ diam_status diam_init(const diam_config* cfg, const diam_target* tg, const doubl
     c->nl = cfg->n_lag;
     c->dy = (tg->kind == DIAM_T_DENSE_GAUSS || tg->kind == DIAM_T_TANH_REG || tg->kind == DIAM_T_TWISTED) ? tg->d_y : 0;
     c->ldk = (cfg->d + 63) / 64 * 64;
-    c->bf = cfg->prec == DIAM_BF16;
+    c->bf = cfg->prec != DIAM_FP64;   // the mixed modes: BF16, or BF16 with the factor quantised to TF32
+    c->tf32 = cfg->prec == DIAM_FP32;
     c->fn = tg->fn;
     c->user = tg->user;
     c->sigma = tg->sigma;

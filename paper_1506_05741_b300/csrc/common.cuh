@@ -149,6 +149,27 @@ __device__ __forceinline__ uint16_t f32_to_bf16_bits(float v) {
     return (uint16_t)(b >> 16);
 }
 
+// TF32: 11 significant bits (FP32's exponent range), round to nearest, ties to even, from FP64.
+__host__ __device__ inline double round_tf32(double v) {
+    unsigned long long bits;
+#ifdef __CUDA_ARCH__
+    bits = (unsigned long long)__double_as_longlong(v);
+#else
+    memcpy(&bits, &v, 8);
+#endif
+    if (((bits >> 52) & 0x7FFull) == 0x7FFull) return v;
+    const unsigned long long lsb = (bits >> 42) & 1ull;
+    bits += (1ull << 41) - 1ull + lsb;
+    bits &= ~((1ull << 42) - 1ull);
+    double r;
+#ifdef __CUDA_ARCH__
+    r = __longlong_as_double((long long)bits);
+#else
+    memcpy(&r, &bits, 8);
+#endif
+    return r;
+}
+
 // An FP64 value already at BF16 precision, as BF16 bits (exact).
 __device__ __forceinline__ uint16_t bf16_bits_of_rounded(double v) {
     return (uint16_t)(__float_as_uint((float)v) >> 16);

@@ -1534,13 +1534,18 @@ __global__ void build_c_kernel(int d, const double* __restrict__ M2, int ld, dou
 }
 
 // Quantised factor: Lq64 = round_bf16(L) and its BF16 bits (row-major, ldk columns, zero padded).
+// Lq = the factor rounded to BF16 (Lq16 its bits), or, with Lq16lo, to TF32: 11 significant bits, exactly the
+// sum of two BF16 values (Lq16 = the BF16 rounding of the TF32 value, Lq16lo = the rest, at most 3 bits).
 __global__ void quantise_factor_kernel(int d, const double* __restrict__ L, int ld, double* __restrict__ Lq64,
-                                       uint16_t* __restrict__ Lq16, int ldk) {
+                                       uint16_t* __restrict__ Lq16, int ldk, uint16_t* __restrict__ Lq16lo) {
     int i = blockIdx.y;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ldk; j += gridDim.x * blockDim.x) {
-        double v = (j < d) ? round_bf16(L[(size_t)i * ld + j]) : 0.0;
+        const double l = (j < d) ? L[(size_t)i * ld + j] : 0.0;
+        const double v = Lq16lo ? round_tf32(l) : round_bf16(l);
         if (j < d) Lq64[(size_t)i * ld + j] = v;
-        Lq16[(size_t)i * ldk + j] = bf16_bits_of_rounded(v);
+        const double h = round_bf16(v);
+        Lq16[(size_t)i * ldk + j] = bf16_bits_of_rounded(h);
+        if (Lq16lo) Lq16lo[(size_t)i * ldk + j] = bf16_bits_of_rounded(v - h);   // exact: v - h has <= 3 bits
     }
 }
 

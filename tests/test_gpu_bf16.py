@@ -107,6 +107,38 @@ def test_bf16_steps_match_oracle_bf16_mode(kind):
     assert np.array_equal(Lq, Lqo) and np.array_equal(xr, xro)
 
 
+@pytest.mark.parametrize("kind", ["tanh", "dense_vec", "diag"])
+def test_fp32_factor_mode_matches_oracle(kind):
+    """prec FP32: the factor quantised to TF32 (two BF16 terms, the second as an extra tensor-core K pass in the
+    noise product and in A A_n), W and the map BF16, z solved by the FP64-accurate triangular solve; against the
+    oracle's same mode over two intervals on the initial factor (C0's Cholesky factor quantised to TF32)."""
+    import oracle as _o
+    if kind == "tanh":
+        ts, P = workloads.tanh_regression(256, 128, 61), 6
+    elif kind == "dense_vec":
+        ts, P = workloads.dense_gaussian(160, 62), 5
+    else:
+        ts, P = workloads.diag_gaussian(100), 4
+    d, nl = ts.d, 8
+    steps = 2 * nl
+    C0 = np.diag(np.linspace(0.5, 1.5, d) * (ts.lam if ts.lam is not None else np.full(d, 0.01)))
+    x0 = workloads.start_state(d, P, 6, scale=np.sqrt(np.diag(C0)))
+    g, o = make_pair(ts, P, trace_steps=steps, prec=_o.FP32, n_lag=nl, beta0=0.3, seed=17, C0=C0, x0=x0,
+                     min_samples_refresh=10 ** 9)
+    L0, Lq0, _, _ = g.factor()
+    assert np.array_equal(Lq0, _o.round_tf32(L0))                   # TF32, not BF16
+    assert not np.array_equal(Lq0, _o.round_bf16(L0))
+    g.run(steps)
+    o.run(steps)
+    tg, to = g.trace(steps), o.trace()
+    assert np.array_equal(tg["acc"], to["acc"])
+    sc = trace_scale(to)
+    for k in ("lp_prop", "q_prop", "q_cur"):
+        assert rel_err(tg[k], to[k], sc) <= TOL, (k, rel_err(tg[k], to[k], sc))
+    assert loga_excess(tg, to, fp32_value_bound(to)) <= 1.0, loga_excess(tg, to, fp32_value_bound(to))
+    g.close()
+
+
 def test_bf16_refresh_and_moments_track_oracle():
     """One interval (64 steps of 16 chains: K = 1024 samples) folded by the BF16 tensor-core SYRK against the
     oracle's FP64 sums. The mean comes from the FP32 records: FP32 accuracy. The centred second moment multiplies
