@@ -78,6 +78,11 @@ def parse():
     ap.add_argument("--conv-tol-mean", type=float, default=0.01, help="|m_n - mu|_2 (the n_lag tuning criterion)")
     ap.add_argument("--conv-tol-cov", type=float, default=1e-3, help="|C_n - Sigma|_F / |Sigma|_F")
     ap.add_argument("--conv-max-s", type=float, default=25.0, help="device seconds per (d, n_lag) row at most")
+    ap.add_argument("--config2", action="store_true",
+                    help="instead of the throughput bench: the dense d=1024 multi-chain workload, 50 batches of 10 "
+                         "intervals, in the FP64, FP32 and BF16 modes (moment errors and chain-steps/s)")
+    ap.add_argument("--c2-modes", default="fp64,fp32,bf16")
+    ap.add_argument("--c2-batches", type=int, default=50)
     ap.add_argument("--compare", action="store_true",
                     help="instead of the throughput bench: integrated autocorrelation times of DIAM, AM, pCN and RW on "
                          "the Gaussian test targets of Sec. 3.1 over d (Sec. 3.2)")
@@ -371,6 +376,64 @@ def convergence(args):
                                  "tol_mean": args.conv_tol_mean, "tol_cov_rel_frobenius": args.conv_tol_cov,
                                  "max_device_s_per_row": args.conv_max_s},
                       "by_d": out}), flush=True)
+
+
+def config2(args):
+    """The dense d = 1024 workload as the paper's multi-chain setting runs it: Sigma = Q diag(1/i) Q^T (Q from the
+    QR of a seeded N(0, 1) matrix), P = 128 chains, n_lag = 64, 50 batches of M = 10 intervals (32 000 steps per
+    chain), A_0 = Id and x_0 ~ N(0, I) (Algorithm 1's start), beta adaptive, every interval's samples pooled into
+    the factor (the batch of M intervals is the reporting unit). Run in the plain FP64 mode and in the FP32 mode
+    (the factor quantised to TF32, tensor-core products, one launch per interval, graph-replayed refreshes), and
+    in the BF16 mode for comparison. Per mode: chain-steps/s over the 50 batches (CUDA events on the sampler's
+    stream, moments read between batches outside the timed spans), the moments' errors against Sigma at batch 1,
+    5, 10, 25, 50 (mean: Euclidean; covariance: relative Frobenius), and the PSRF of the second half."""
+    import torch
+    import paper_1506_05741_b300 as dm
+    import workloads
+    run = workloads.dense1024()
+    ts = run.target
+    d, P, nl, M = ts.d, run.P, run.n_lag, run.M
+    nS = float(np.linalg.norm(ts.cov))
+    x0 = workloads.start_state(d, P, 3)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    modes = {"fp64": dm.FP64, "fp32": dm.FP32, "bf16": dm.BF16}
+    out = {}
+    for name in args.c2_modes.split(","):
+        cfg = dm.default_config(d, P, n_lag=nl, beta0=run.beta0, seed=run.seed, prec=modes[name])
+        cfg["keep_block_sums"] = 1
+        s = dm.Sampler(cfg, ts, x0=x0, stream=stream.cuda_stream)
+        dev_s, traj = 0.0, []
+        for b in range(1, args.c2_batches + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s.run(M * nl)
+            s.flush()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dev_s += e0.elapsed_time(e1) / 1e3
+            if b in (1, 5, 10, 25, 50) or b == args.c2_batches:
+                m, C, n = s.moments()
+                traj.append({"batch": b, "mean_error": round(float(np.linalg.norm(m - ts.mean)), 5),
+                             "cov_error": round(float(np.linalg.norm(C - ts.cov)) / nS, 5)})
+        st = s.stats()
+        nb = args.c2_batches * M
+        r = s.psrf(nb // 2, nb - nb // 2)
+        s.close()
+        steps = args.c2_batches * M * nl
+        out[name] = {"chain_steps_per_s": round(steps * P / dev_s, 1), "device_s": round(dev_s, 3),
+                     "moments": traj, "accept_rate": round(st["accepted"] / max(1, st["steps"] * P), 4),
+                     "beta": round(st["beta"], 5), "refreshes": st["refreshes"],
+                     "psrf_max_second_half": round(float(np.max(r)), 4)}
+        print(json.dumps({"mode": name, "done": out[name]}), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "chain-steps/s and moment errors, dense d=1024 multi-chain workload",
+                      "unit": "chain-steps/s",
+                      "config": {"workload": "dense1024: d=1024, Sigma = Q diag(1/i) Q^T, P=128, n_lag=64, "
+                                             f"{args.c2_batches} batches of M={M} intervals, A_0 = Id, x_0 ~ N(0, I)",
+                                 "moments": "pooled over all chains every interval"},
+                      "data": "synthetic", "by_mode": out}), flush=True)
 
 
 def peaks():
@@ -692,6 +755,9 @@ def main():
         return
     if args.da_gain:
         da_gain(args)
+        return
+    if args.config2:
+        config2(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

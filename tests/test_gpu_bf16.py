@@ -401,8 +401,10 @@ def test_bf16_rewhitening_matches_fp64_solve():
     s.close()
 
 
-def test_bf16_dense1024_chain_matches_closed_form_moments():
-    """The dense1024 target (d = 1024, Sigma = Q diag(1/i) Q^T) in BF16 mode, P = 128, n_lag = 64, from exact
+@pytest.mark.parametrize("mode", ["bf16", "fp32"])
+def test_bf16_dense1024_chain_matches_closed_form_moments(mode):
+    """The dense1024 target (d = 1024, Sigma = Q diag(1/i) Q^T) in BF16 mode (and in the FP32 mode: the factor
+    quantised to TF32), P = 128, n_lag = 64, from exact
     draws of the target, with a fixed factor near Sigma (its eigenvalues scaled by seeded factors in [0.7, 1.4],
     so the quantised proposal is not reversible for the target and the test of eq. (accept) does the work), beta
     0.4, 400 intervals. The chains' states at the interval ends (second half, 25600 draws), rotated to Sigma's
@@ -421,8 +423,8 @@ def test_bf16_dense1024_chain_matches_closed_form_moments():
     sfac = np.exp(np.random.default_rng(5).uniform(np.log(0.7), np.log(1.4), d))
     C0 = (Q * (lam * sfac)) @ Q.T
     x0 = workloads.start_state(d, P, 3) @ np.linalg.cholesky(ts.cov).T
-    cfg = dm.default_config(d, P, n_lag=nl, beta0=0.4, seed=run.seed, prec=dm.BF16, adapt_beta=0, xref_mode=0,
-                            min_samples_refresh=10 ** 12)
+    cfg = dm.default_config(d, P, n_lag=nl, beta0=0.4, seed=run.seed, prec=dm.BF16 if mode == "bf16" else dm.FP32,
+                            adapt_beta=0, xref_mode=0, min_samples_refresh=10 ** 12)
     s = dm.Sampler(cfg, ts, x0=x0, C0=C0)
     Y = np.zeros((K, P, d), np.float32)
     for k in range(K):
