@@ -243,11 +243,30 @@ __global__ void __launch_bounds__(PT_THREADS, 1) tc_gemm_persist_kernel(
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (epi.n_dev) N = min(N, *epi.n_dev);   // device-side row count of B: tiles past it are skipped by every role
-    const int T = mtiles * ntiles;
+    // The tile list, n-column by n-column (the m-tiles of one column share its B tile in L2). The fold lists only
+    // the tiles that meet the lower triangle (n0 + 255 >= m0): column j holds the first min(mtiles, fold_rows(j)).
+    const bool fold = epi.mode == TC_FOLD;
+    auto fold_rows = [&](int j) { return min(mtiles, (j * PT_BN + PT_BN - 1) / TC_BM + 1); };
+    int T = mtiles * ntiles;
+    if (fold) {
+        T = 0;
+        for (int j = 0; j < ntiles; ++j) T += fold_rows(j);
+    }
     auto tile_of = [&](int t, int& m0, int& n0) {
-        m0 = (t % mtiles) * TC_BM;
-        n0 = (t / mtiles) * PT_BN;
+        if (!fold) {
+            m0 = (t % mtiles) * TC_BM;
+            n0 = (t / mtiles) * PT_BN;
+            return;
+        }
+        int j = 0;
+        while (t >= fold_rows(j)) t -= fold_rows(j++);
+        m0 = t * TC_BM;
+        n0 = j * PT_BN;
     };
+    // Round k of the CTAs takes tiles k G .. k G + G - 1, in reverse CTA order on odd rounds: with the noise
+    // product's triangular K ranges (m-tile i carries i + 1 units) every CTA then gets close to the mean work.
+    const int G = (int)gridDim.x, bx = (int)blockIdx.x;
+    auto tile_at = [&](int k) { return k * G + ((k & 1) ? G - 1 - bx : bx); };
     auto valid = [&](int m0, int n0) { return n0 < N && !(epi.mode == TC_FOLD && n0 + PT_BN - 1 < m0); };
     auto cap_of = [&](int m0) { return a_lower ? min(nkb, (m0 + TC_BM + TC_BK - 1) / TC_BK) : nkb; };
     auto kend_of = [&](int m0) { return two_pass ? 2 * cap_of(m0) : cap_of(m0); };
@@ -283,7 +302,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1) tc_gemm_persist_kernel(
             const uint64_t pol_a = l2_policy_evict_last();
             const bool hint_a = epi.mode == TC_STORE;
             int it = 0;
-            for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
+            for (int k = 0; k * G < T && !*abort_flag; ++k) {
+                const int t = tile_at(k);
+                if (t >= T) continue;
                 int m0, n0;
                 tile_of(t, m0, n0);
                 if (!valid(m0, n0)) continue;
@@ -315,7 +336,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1) tc_gemm_persist_kernel(
             constexpr uint32_t idesc = idesc_bf16(PT_BN);
             int it = 0, cc = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < T && ok && !*abort_flag; t += gridDim.x) {
+            for (int k = 0; k * G < T && ok && !*abort_flag; ++k) {
+                const int t = tile_at(k);
+                if (t >= T) continue;
                 int m0, n0;
                 tile_of(t, m0, n0);
                 if (!valid(m0, n0)) continue;
@@ -356,7 +379,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1) tc_gemm_persist_kernel(
         float sum[128];
         int cc = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
+        for (int k = 0; k * G < T && ok; ++k) {
+            const int t = tile_at(k);
+            if (t >= T) continue;
             int m0, n0;
             tile_of(t, m0, n0);
             if (!valid(m0, n0)) continue;
@@ -507,7 +532,11 @@ static cudaError_t launch_bn(int M, int N, int K, const uint16_t* A, int lda, co
         const size_t pstage = (size_t)TC_BM * TC_BK * 2 + (size_t)PT_BN * TC_BK * 2;
         const int pst = (int)std::min<size_t>(TC_MAX_STAGES, (227 * 1024 - 1024 - 256) / pstage);
         const size_t psmem = 1024 + pst * pstage + 256;
-        const int tiles = (int)grid.x * (int)grid.y;
+        int tiles = (int)grid.x * (int)grid.y;
+        if (epi.mode == TC_FOLD) {   // the tiles that meet the lower triangle (the kernel's list)
+            tiles = 0;
+            for (int j = 0; j < (int)grid.y; ++j) tiles += std::min((int)grid.x, (j * PT_BN + PT_BN - 1) / TC_BM + 1);
+        }
         const int ctas = std::max(1, std::min(tiles, sms[dev]));
         const int chunk = epi.mode == TC_FOLD ? PT_CHUNK_FOLD : PT_CHUNK_STORE;
         { tc_gemm_persist_kernel<<<ctas, PT_THREADS, psmem, st>>>(mA, mB, mB2, mA2, M, N, nkb, a_lower, has_b2, has_a2,
