@@ -280,9 +280,10 @@ static cudaError_t launch_update(const uint16_t* SA, int Ma, const int* exA, con
             attr[dev] = true;
         }
     }
-    // A tiles per unit: about four units per SM over the whole update (two resident at a time), at most 8
+    // A tiles per unit: about one wave of units over the SMs (two resident per SM), at most 16 tiles (a unit's
+    // B load, pipeline fill and drain cost about as much as two tiles; longer runs unbalance the triangle)
     const int tiles = oz_units(Ma, Nb, lower, 1, 0, nullptr);
-    const int ch = std::max(1, std::min(8, tiles / (4 * 148)));
+    const int ch = std::max(1, std::min(16, (tiles + 2 * 148 - 1) / (2 * 148)));
     const int units = oz_units(Ma, Nb, lower, ch, 0, nullptr);
     { ozaki_update_kernel<<<units, OZ_THREADS, update_smem(), st>>>(mA, mB, Ma, Nb, exA, exB, Cm, ldc, lower, ch, status); count_launch(); }
     return cudaGetLastError();
