@@ -36,8 +36,8 @@ struct RwtSmem {   // offsets (bytes) into the 1024-aligned dynamic shared memor
     static constexpr size_t B = LD + 2 * 8192;                       // 2 KB: the split solution (SW128)
     static constexpr size_t RD = B + RWT_BBYTES;                     // 64 floats: reciprocals of the diagonal
     static constexpr size_t Y = RD + 64 * 4;                         // 4 x 64 floats: the block's solution
-    static constexpr size_t BAR = Y + RWT_G * 64 * 4;                // mbarriers: full, empty (stages), done, ld (2)
-    static constexpr size_t MISC = BAR + (2 * RWT_STAGES + 3) * 8;   // tensor-memory slot, abort flag
+    static constexpr size_t BAR = Y + RWT_G * 64 * 4;                // mbarriers: full, empty (stages), done, ld (2), groups (4)
+    static constexpr size_t MISC = BAR + (2 * RWT_STAGES + 7) * 8;   // tensor-memory slot, abort flag
     static constexpr size_t RW = (MISC + 16 + 15) / 16 * 16;         // G x d floats: right-hand sides
 };
 
@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(RWT_THREADS, 1) rewhiten_tc_kernel(const __gri
     uint64_t* empty = full + RWT_STAGES;
     uint64_t* done = empty + RWT_STAGES;
     uint64_t* ldfull = done + 1;   // 2: the diagonal block's tile landed
+    uint64_t* tgrp = ldfull + 2;   // 4: the products of tiles 8 q .. 8 q + 7 of the block are complete
     uint32_t* tmem_slot = (uint32_t*)(sm + RwtSmem::MISC);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     float* rw = (float*)(sm + RwtSmem::RW);
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(RWT_THREADS, 1) rewhiten_tc_kernel(const __gri
         mbar_init(smem_u32(done), 1);
         mbar_init(smem_u32(&ldfull[0]), 1);
         mbar_init(smem_u32(&ldfull[1]), 1);
+        for (int q = 0; q < RWT_MAXT / 8; ++q) mbar_init(smem_u32(&tgrp[q]), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -182,35 +184,47 @@ __global__ void __launch_bounds__(RWT_THREADS, 1) rewhiten_tc_kernel(const __gri
                     umma_bf16(tmem + (uint32_t)(16 * t), sdesc_sw128(pa + kk * 32), sdesc_sw128(pb + kk * 32), idesc,
                               kk ? 1u : 0u);
                 umma_commit(smem_u32(&empty[s]));
+                if ((t & 7) == 7 || t == nt - 1) umma_commit(smem_u32(&tgrp[t >> 3]));   // a group of 8 tiles done
             }
             umma_commit(smem_u32(done));
         }
         __syncwarp();
-        mbar_wait(smem_u32(done), (uint32_t)(kb & 1), abort_flag);
-        tile_count += nt;
-        __syncthreads();
-        if (*abort_flag) break;   // uniform after the barrier
-        tc_fence_after();
-        if (warp < 4) {   // each warp its 32 rows of every tile: r -= hi + mid + lo, per chain
-            for (int t2 = 0; t2 < nt; t2 += 2) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * t2), v);
+        if (warp < 4) {   // each warp its 32 rows of every tile: r -= hi + mid + lo, per chain, a group of 8 tiles at a
+                          // time as soon as its products are complete (the later groups' copies and products go on)
+            for (int q = 0; q * 8 < nt; ++q) {
+                // a group is committed in every block whose panel reaches it, and panels only shrink: phase kb & 1
+                if (!mbar_wait(smem_u32(&tgrp[q]), (uint32_t)(kb & 1), abort_flag)) break;
+                tc_fence_after();
+                const int tq0 = 8 * q, tq1 = min(nt, tq0 + 8);
+                uint32_t v[4][32];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int row = r0 + 128 * (t2 + h) + 32 * warp + lane;
-                    if (t2 + h < nt && row < d) {
+                for (int pp = 0; pp < 4; ++pp)
+                    if (tq0 + 2 * pp < tq1)
+                        tmem_ld32_nowait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * (tq0 + 2 * pp)), v[pp]);
+                tmem_wait_ld();
 #pragma unroll
-                        for (int g = 0; g < RWT_G; ++g)
-                            if (g < ng)
-                                rw[(size_t)g * d + row] -= __uint_as_float(v[16 * h + 3 * g]) +
-                                                           __uint_as_float(v[16 * h + 3 * g + 1]) +
-                                                           __uint_as_float(v[16 * h + 3 * g + 2]);
+                for (int pp = 0; pp < 4; ++pp) {
+                    tmem_regs_ready(v[pp]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int t = tq0 + 2 * pp + h, row = r0 + 128 * t + 32 * warp + lane;
+                        if (t < tq1 && row < d) {
+#pragma unroll
+                            for (int g = 0; g < RWT_G; ++g)
+                                if (g < ng)
+                                    rw[(size_t)g * d + row] -= __uint_as_float(v[pp][16 * h + 3 * g]) +
+                                                               __uint_as_float(v[pp][16 * h + 3 * g + 1]) +
+                                                               __uint_as_float(v[pp][16 * h + 3 * g + 2]);
+                        }
                     }
                 }
             }
         }
+        mbar_wait(smem_u32(done), (uint32_t)(kb & 1), abort_flag);   // every product of the block is complete
+        tile_count += nt;
         tc_fence_before();
         __syncthreads();
+        if (*abort_flag) break;   // uniform after the barrier
     }
     __syncthreads();   // the last block's solve
     if (*abort_flag) {
