@@ -229,6 +229,38 @@ __global__ void __launch_bounds__(256) trsv_rows_kernel(const double* __restrict
     }
 }
 
+// The panel's top rows on the factorisation's critical path: trsv_rows_kernel's solve (pre: U and 1 / L_jj as
+// chol_diag_kernel left them) with one warp per CTA and U read from global memory (L2) as the substitution goes,
+// so that each row has an SM's FP64 pipe to itself and no CTA waits for a shared-memory copy of U. Slices as
+// trsv_rows_kernel's (nb = 64).
+__global__ void __launch_bounds__(32) trsv_top_kernel(const double* __restrict__ Lkk, int ldl, double* __restrict__ B,
+                                                      int ldb, int nrows, uint16_t* __restrict__ SL, int* __restrict__ ex) {
+    const int r = blockIdx.x, lane = threadIdx.x;
+    if (r >= nrows) return;
+    const double id0 = Lkk[(size_t)lane * ldl + CH_NB], id1 = Lkk[(size_t)(lane + 32) * ldl + CH_NB];
+    double* b = B + (size_t)r * ldb;
+    double v0 = b[lane], v1 = b[lane + 32];
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {   // U_ij for i > j is stored at (j, i)
+        const double u0 = Lkk[(size_t)j * ldl + lane], u1 = Lkk[(size_t)j * ldl + lane + 32];
+        const double wj = __shfl_sync(0xffffffffu, v0, j);
+        if (lane > j) v0 = fma(-u0, wj, v0);
+        v1 = fma(-u1, wj, v1);
+    }
+#pragma unroll 8
+    for (int j = 32; j < CH_NB; ++j) {
+        const double u1 = Lkk[(size_t)j * ldl + lane + 32];
+        const double wj = __shfl_sync(0xffffffffu, v1, j - 32);
+        if (lane + 32 > j) v1 = fma(-u1, wj, v1);
+    }
+    v0 *= id0;
+    v1 *= id1;
+    b[lane] = v0;
+    b[lane + 32] = v1;
+    const int e = ozaki_slice_row(v0, v1, lane, SL + (size_t)r * OZ_LD);
+    if (lane == 0) ex[r] = e;
+}
+
 __global__ void zero_upper_kernel(double* A, int lda, int n) {
     int i = blockIdx.y;
     for (int j = i + 1 + blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
@@ -310,7 +342,7 @@ static cudaError_t cholesky_ozaki(double* A, int n, int lda, int* info_dev, cuda
             int* exb = oz.ex + (size_t)buf * oz.cap_rows;
             // hi: the top rows of the panel (updated for this block by the previous block's mid work)
             if (mid_pending) LA_CK(cudaStreamWaitEvent(hi, oz.ev_mid, 0));
-            { trsv_rows_kernel<<<row_blocks(CH_NB), 256, 0, hi>>>(Lkk, lda, nb, Pn, lda, CH_NB, SLb, exb, 1); count_launch(); }
+            { trsv_top_kernel<<<CH_NB, 32, 0, hi>>>(Lkk, lda, Pn, lda, CH_NB, SLb, exb); count_launch(); }
             LA_CK(cudaEventRecord(oz.ev_diag, hi));
             // mid: the rest of the panel, then the rest of the next 64 columns
             LA_CK(cudaStreamWaitEvent(mid, oz.ev_diag, 0));
