@@ -32,6 +32,10 @@ struct DaState {
     float* cs_part;   // COLSUM_CHUNKS x max(h1, h2): the column sums' partial sums
     double *loss_parts, *sbatch, *stats;
     double* musig;   // device copy of (mu, sigma)
+    // a training's steps replayed as one captured step: the step counter (current, first) and the Adam bias
+    // corrections of every step of the training, computed on the host as the eager steps compute them
+    long long* tdev = nullptr;
+    float* c12 = nullptr;
     Key key{};
 };
 
@@ -118,18 +122,23 @@ static diam_status da_backward(diam_ctx* c) {
     return DIAM_OK;
 }
 
-static void da_adam(diam_ctx* c) {
+// graph: the bias corrections and the step are read from a->c12 / a->tdev (a step captured for replay); the caller
+// advances a->adam_t by the replays.
+static void da_adam(diam_ctx* c, bool graph = false) {
     DaState* a = c->da;
     const diam_da_config& g = a->cfg;
-    a->adam_t++;
-    const float c1 = (float)(1.0 - std::pow(g.beta1, (double)a->adam_t));
-    const float c2 = (float)(1.0 - std::pow(g.beta2, (double)a->adam_t));
+    if (!graph) a->adam_t++;
+    const float c1 = graph ? 0.f : (float)(1.0 - std::pow(g.beta1, (double)a->adam_t));
+    const float c2 = graph ? 0.f : (float)(1.0 - std::pow(g.beta2, (double)a->adam_t));
+    const float* c12 = graph ? a->c12 : nullptr;
+    const long long* tdev = graph ? a->tdev : nullptr;
     const float lr = (float)g.lr, b1 = (float)g.beta1, b2 = (float)g.beta2, ep = (float)g.adam_eps;
     const int h1 = a->h1, h2 = a->h2, d = c->d;
     auto launch = [&](int rows, int cols, float* th, const float* gr, int gt, int ldg, float* m, float* v, uint16_t* q, int ldq,
                       uint16_t* qt, int ldqt) {
         unsigned nb = std::min<unsigned>(148 * 8, blocks_for((size_t)rows * cols));
-        { adam_kernel<<<nb, kThreads, 0, c->st>>>(rows, cols, th, gr, gt, ldg, m, v, lr, b1, b2, ep, c1, c2, q, ldq, qt, ldqt); count_launch(); }
+        { adam_kernel<<<nb, kThreads, 0, c->st>>>(rows, cols, th, gr, gt, ldg, m, v, lr, b1, b2, ep, c1, c2, q, ldq, qt, ldqt,
+                                                  c12, tdev); count_launch(); }
     };
     launch(h1, d, a->W1, a->gW1T, 1, h1, a->mW1, a->vW1, a->W1q, c->ldk, nullptr, 0);
     launch(1, h1, a->b1, a->gb1, 0, 0, a->mb1, a->vb1, nullptr, 0, nullptr, 0);
@@ -137,6 +146,62 @@ static void da_adam(diam_ctx* c) {
     launch(1, h2, a->b2, a->gb2, 0, 0, a->mb2, a->vb2, nullptr, 0, nullptr, 0);
     launch(1, h2, a->w3, a->gw3, 0, 0, a->mw3, a->vw3, nullptr, 0, nullptr, 0);
     launch(1, 1, a->b3, a->gb3, 0, 0, a->mb3, a->vb3, nullptr, 0, nullptr, 0);
+}
+
+// The training's steps as one captured step replayed train_steps times (the same kernels and arguments as the
+// eager steps; the minibatch counter and the bias corrections come from device memory). *done false if the
+// context's stream cannot be captured: nothing was launched, and the caller runs the steps one by one.
+static diam_status da_train_graph(diam_ctx* c, bool* done) {
+    *done = false;
+    DaState* a = c->da;
+    const diam_da_config& g = a->cfg;
+    const int steps = g.train_steps;
+    if (steps <= 0) {
+        *done = true;
+        return DIAM_OK;
+    }
+    std::vector<float> cc(2 * (size_t)steps);
+    for (int s = 0; s < steps; ++s) {   // step s of the training is Adam step adam_t + s + 1
+        cc[2 * s] = (float)(1.0 - std::pow(g.beta1, (double)(a->adam_t + s + 1)));
+        cc[2 * s + 1] = (float)(1.0 - std::pow(g.beta2, (double)(a->adam_t + s + 1)));
+    }
+    const long long t0[2] = {a->adam_t, a->adam_t};
+    if (cudaMemcpyAsync(a->c12, cc.data(), sizeof(float) * cc.size(), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(a->tdev, t0, sizeof(t0), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess) {
+        cudaGetLastError();
+        return DIAM_OK;
+    }
+    cudaGraph_t gr = nullptr;
+    const unsigned long long l0 = g_launches.load();
+    if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return DIAM_OK;
+    }
+    { gather_batch_kernel<<<a->B, kThreads, 0, c->st>>>(a->key, 0, 0, 0, a->ring_x, a->ring_lp, a->cnt, c->d, c->ldk, a->shift,
+                                                      a->scale, a->mu, a->sigma, a->Xb, a->tb, nullptr, a->tdev); count_launch(); }
+    const diam_status bs = da_backward(c);
+    da_adam(c, true);
+    { step_count_kernel<<<1, 1, 0, c->st>>>(a->tdev); count_launch(); }
+    const cudaError_t ec = cudaStreamEndCapture(c->st, &gr);
+    const unsigned long long per = g_launches.load() - l0;
+    g_launches.fetch_sub(per);
+    cudaGraphExec_t ex = nullptr;
+    if (bs != DIAM_OK || ec != cudaSuccess || cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        return DIAM_OK;
+    }
+    cudaGraphDestroy(gr);
+    *done = true;   // from here on the training is this graph's, whether its launches succeed or not
+    cudaError_t el = cudaSuccess;
+    int s = 0;
+    for (; s < steps && el == cudaSuccess; ++s) el = cudaGraphLaunch(ex, c->st);
+    cudaGraphExecDestroy(ex);
+    g_launches.fetch_add(per * (unsigned long long)s);
+    a->adam_t += s;
+    if (el != cudaSuccess) return fail(c, DIAM_ECUDA, "diam_da_train", cudaGetErrorString(el));
+    return DIAM_OK;
 }
 
 static diam_status da_train_now(diam_ctx* c, double* rmse_out) {
@@ -160,11 +225,16 @@ static diam_status da_train_now(diam_ctx* c, double* rmse_out) {
     a->sigma = std::sqrt(std::max(1e-30, st3[1] / ntr - a->mu * a->mu));
     const double ms[2] = {a->mu, a->sigma};
     CK(cudaMemcpyAsync(a->musig, ms, sizeof(ms), cudaMemcpyHostToDevice, c->st));
-    for (int s = 0; s < a->cfg.train_steps; ++s) {
-        { gather_batch_kernel<<<a->B, kThreads, 0, c->st>>>(a->key, a->adam_t, 0, 0, a->ring_x, a->ring_lp, a->cnt, c->d, c->ldk,
-                                                          a->shift, a->scale, a->mu, a->sigma, a->Xb, a->tb, nullptr); count_launch(); }
-        CKS(da_backward(c));
-        da_adam(c);
+    bool graphed = false;
+    CKS(da_train_graph(c, &graphed));
+    if (!graphed) {   // the steps one by one (a stream that cannot be captured)
+        for (int s = 0; s < a->cfg.train_steps; ++s) {
+            { gather_batch_kernel<<<a->B, kThreads, 0, c->st>>>(a->key, a->adam_t, 0, 0, a->ring_x, a->ring_lp, a->cnt, c->d,
+                                                              c->ldk, a->shift, a->scale, a->mu, a->sigma, a->Xb, a->tb,
+                                                              nullptr); count_launch(); }
+            CKS(da_backward(c));
+            da_adam(c);
+        }
     }
     // held-out RMSE (slots 10 j + 9), in minibatch-sized chunks, at most 8 chunks
     CK(cudaMemsetAsync(a->stats, 0, sizeof(double), c->st));
@@ -290,6 +360,8 @@ static diam_status da_alloc(diam_ctx* c, const diam_da_config* g, const double* 
     CKS(F(&a->gW1T, (size_t)ldk * h1)); CKS(F(&a->gW2T, (size_t)h1 * h2)); CKS(F(&a->gb1, h1)); CKS(F(&a->gb2, h2));
     CKS(F(&a->gw3, h2)); CKS(F(&a->gb3, 1)); CKS(F(&a->cs_part, (size_t)COLSUM_CHUNKS * std::max(h1, h2)));
     CKS(D(&a->loss_parts, B)); CKS(D(&a->sbatch, B)); CKS(D(&a->stats, 4)); CKS(D(&a->musig, 2));
+    CKS(dalloc(c, &a->tdev, 2 * sizeof(long long)));
+    CKS(F(&a->c12, 2 * (size_t)std::max(1, g->train_steps)));
     {
         const double ms[2] = {a->mu, a->sigma};
         CK(cudaMemcpyAsync(a->musig, ms, sizeof(ms), cudaMemcpyHostToDevice, c->st));

@@ -203,12 +203,14 @@ __host__ __device__ inline long long n_train_slots(long long filled) {
 
 // Minibatch row b of Adam step a: a Philox-chosen training slot (tag 5), normalised and rounded to BF16;
 // target t_b = (log pi - mu) / sigma. held_out = 1: rows b of the held-out slots instead (slot 10 j + 9).
+// a_dev (optional): the draw's counter read from device memory instead of a (a training step replayed as a graph).
 __global__ void gather_batch_kernel(Key key, long long a, int held_out, long long first, const uint16_t* __restrict__ ring_x,
                                     const float* __restrict__ ring_lp, const DaCounters* cnt, int d, int ldk,
                                     const float* __restrict__ shift, const float* __restrict__ scale, double mu,
                                     double sigma, uint16_t* __restrict__ Xb, float* __restrict__ tb,
-                                    float* __restrict__ raw_lp) {
+                                    float* __restrict__ raw_lp, const long long* __restrict__ a_dev = nullptr) {
     const int b = blockIdx.x;
+    if (a_dev) a = a_dev[0];
     const long long filled = cnt->filled;
     long long slot;
     if (held_out) {
@@ -315,9 +317,17 @@ __global__ void colsum_final_kernel(int cols, int chunks, const float* __restric
 // One Adam step (Kingma & Ba) on a parameter tensor of rows x cols with FP32 master weights; the gradient
 // is g[r*cols + c] or, if g_t, g[c*ldg + r]. Writes the BF16 copies (row-major with ldq columns and/or
 // transposed with ldqt columns) when given.
+// c12, t_dev (optional, a training step replayed as a graph): the bias corrections of step s = t_dev[0] - t_dev[1] of
+// the training at c12[2 s], c12[2 s + 1] instead of c1, c2.
 __global__ void adam_kernel(int rows, int cols, float* __restrict__ th, const float* __restrict__ g, int g_t, int ldg,
                             float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2, float eps,
-                            float c1, float c2, uint16_t* __restrict__ q, int ldq, uint16_t* __restrict__ qt, int ldqt) {
+                            float c1, float c2, uint16_t* __restrict__ q, int ldq, uint16_t* __restrict__ qt, int ldqt,
+                            const float* __restrict__ c12 = nullptr, const long long* __restrict__ t_dev = nullptr) {
+    if (c12) {
+        const long long st = t_dev[0] - t_dev[1];
+        c1 = c12[2 * st];
+        c2 = c12[2 * st + 1];
+    }
     const size_t n = (size_t)rows * cols;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / cols), c = (int)(e % cols);
@@ -400,6 +410,9 @@ __global__ void sq_err_kernel(int rows, const double* __restrict__ s, const floa
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) out[0] += acc;
 }
+
+// The graph-replayed training step's counter: the next step.
+__global__ void step_count_kernel(long long* t_dev) { t_dev[0] += 1; }
 
 }  // namespace
 }  // namespace diam
