@@ -316,12 +316,14 @@ static diam_status da_step(diam_ctx* c) {
 static diam_status da_after_interval(diam_ctx* c) {
     DaState* a = c->da;
     a->intervals++;
-    DaCounters hc{};
-    CK(d2h(c, &hc, a->cnt, sizeof(hc)));
     const int64_t period = (int64_t)std::max(1, c->cfg.M) * std::max(1, a->cfg.retrain_every);
-    const bool first = a->trainings == 0 && hc.filled >= a->cfg.first_train_min;
-    const bool due = a->trainings > 0 && a->intervals % period == 0;
-    if (first || due) CKS(da_train_now(c, nullptr));
+    if (a->trainings == 0) {   // the first training waits for enough pairs: the ring's count, read back
+        DaCounters hc{};
+        CK(d2h(c, &hc, a->cnt, sizeof(hc)));
+        if (hc.filled >= a->cfg.first_train_min) CKS(da_train_now(c, nullptr));
+    } else if (a->intervals % period == 0) {   // later ones on the interval count alone: no read, no host wait
+        CKS(da_train_now(c, nullptr));
+    }
     return DIAM_OK;
 }
 
