@@ -36,10 +36,11 @@ def _headline(P, nl):
     return run, ts, x0, np.diag(ts.lam)
 
 
-def _gpu(run, ts, x0, C0, steps, profile=0):
+def _gpu(run, ts, x0, C0, steps, profile=0, prec=None):
     import paper_1506_05741_b300 as dm
-    cfg = dm.default_config(ts.d, run.P, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed, prec=dm.BF16,
-                            adapt_beta=0, min_samples_refresh=10 ** 12, profile=profile)
+    cfg = dm.default_config(ts.d, run.P, n_lag=run.n_lag, beta0=run.beta0, seed=run.seed,
+                            prec=dm.BF16 if prec is None else prec, adapt_beta=0, min_samples_refresh=10 ** 12,
+                            profile=profile)
     cfg["trace_steps"] = steps
     g = dm.Sampler(cfg, ts, x0=x0, C0=C0)
     g.run(steps)
@@ -71,6 +72,23 @@ def test_interval_kernel_at_d4096_matches_oracle():
     steps = 2 * run.n_lag
     g, cfg = _gpu(run, ts, x0, C0, steps, profile=1)
     assert g.profile()["step"][0] == 2          # one launch per whole interval
+    tg = g.trace(steps)
+    to = _oracle(cfg, ts, x0, C0, steps, 0, run.P)
+    _check(tg, to, slice(0, run.P))
+    assert 0 < tg["acc"].mean() < 1
+    g.close()
+
+
+def test_fp32_mode_interval_kernel_at_d4096_matches_oracle():
+    """The same two whole intervals with the factor quantised to TF32 (prec FP32: the noise product's second K
+    pass for the factor's lo term, the map A A_n from both terms) against the oracle's FP32 mode."""
+    import paper_1506_05741_b300 as dm
+    run, ts, x0, C0 = _headline(8, 16)
+    steps = 2 * run.n_lag
+    g, cfg = _gpu(run, ts, x0, C0, steps, profile=1, prec=dm.FP32)
+    assert g.profile()["step"][0] == 2          # one launch per whole interval
+    L, Lq, _, _ = g.factor()
+    assert np.array_equal(Lq, oracle.round_tf32(L))                 # TF32, not BF16
     tg = g.trace(steps)
     to = _oracle(cfg, ts, x0, C0, steps, 0, run.P)
     _check(tg, to, slice(0, run.P))
