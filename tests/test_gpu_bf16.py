@@ -378,22 +378,28 @@ def test_bf16_psrf_matches_the_states_read_back():
     s.close()
 
 
-def test_bf16_rewhitening_matches_fp64_solve():
+@pytest.mark.parametrize("mode", ["bf16", "fp32"])
+def test_bf16_rewhitening_matches_fp64_solve(mode):
     """After a refresh, BF16 mode re-solves z = Lq^{-1}(x - x_ref) in FP32 (the states' precision): q of every
     chain at the interval start agrees with the FP64 forward substitution on the same factor and states to
-    1e-5 relative (it is ~1e-6; the states themselves are FP32)."""
+    1e-5 relative (it is ~1e-6; the states themselves are FP32). The FP32 mode (the factor rounded to TF32, its
+    products from two BF16 terms, z re-solved by the FP64-accurate triangular solve) to the same bar, with the
+    refreshed factor rounded to TF32."""
     import scipy.linalg as sl
     import paper_1506_05741_b300 as dm
+    import oracle as _o
     d, P, nl = 512, 8, 16
     ts = workloads.tanh_regression(d, 256, 42)
-    cfg = dm.default_config(d, P, n_lag=nl, beta0=0.3, seed=12, prec=dm.BF16, min_samples_refresh=30)
+    cfg = dm.default_config(d, P, n_lag=nl, beta0=0.3, seed=12, prec=dm.BF16 if mode == "bf16" else dm.FP32,
+                            min_samples_refresh=30)
     cfg["trace_steps"] = 5 * nl + 1
     s = dm.Sampler(cfg, ts, x0=workloads.start_state(d, P, 5) * np.sqrt(ts.lam), C0=np.diag(ts.lam))
     s.run(4 * nl)
     x, _, _ = s.state()
     s.run(1)                               # the interval start applies the new factor and re-whitens
-    _, Lq, xr, _ = s.factor()
+    L, Lq, xr, _ = s.factor()
     assert s.stats()["refreshes"] >= 3
+    assert np.array_equal(Lq, _o.round_bf16(L) if mode == "bf16" else _o.round_tf32(L))
     z = sl.solve_triangular(Lq, (x - xr).T, lower=True)
     q64 = 0.5 * np.sum(z * z, axis=0)
     qg = s.trace(4 * nl + 1)["q_cur"][4 * nl]
