@@ -201,15 +201,17 @@ def test_refresh_delay_applies_the_factor_where_the_oracle_does(delay):
     assert g.stats()["refreshes"] == o.counts()["refreshes"] == 2 + delay
 
 
+@pytest.mark.parametrize("mode", ["bf16", "fp32"])
 @pytest.mark.parametrize("delay", [1, 2])
-def test_refresh_beside_the_next_interval_equals_refresh_in_order(delay):
+def test_refresh_beside_the_next_interval_equals_refresh_in_order(delay, mode):
     """The overlapped refreshes (graphs on; with delay 2 two are in flight) and the in-order ones (graphs off)
-    give bit-identical chains."""
+    give bit-identical chains, in BF16 mode and in the FP32 mode (the factor rounded to TF32)."""
     import paper_1506_05741_b300 as dm
     ts, P = workloads.tanh_regression(192, 64, 38), 6
     out = []
     for graphs in (0, 1):
-        cfg = dm.default_config(192, P, n_lag=8, beta0=0.3, seed=6, prec=dm.BF16, graphs=graphs,
+        cfg = dm.default_config(192, P, n_lag=8, beta0=0.3, seed=6, prec=dm.BF16 if mode == "bf16" else dm.FP32,
+                                graphs=graphs,
                                 min_samples_refresh=20, refresh_delay=delay)
         s = dm.Sampler(cfg, ts, x0=workloads.start_state(192, P, 2) * np.sqrt(ts.lam), C0=np.diag(ts.lam))
         s.run(8 * 12 + 3)
